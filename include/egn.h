@@ -1,0 +1,196 @@
+/*
+ * egn.h -- C ABI of the GB300 (sm_103a) ISRS EGN nonlinear-interference integrator.
+ *
+ * The library evaluates, for every channel of interest (COI) n of a WDM link,
+ *
+ *   P_NLI,n = sum over islands (n1, n2, n3) of P_n1 P_n2 P_n3 *
+ *             [ D + Phi_n1 d(n1,n3) E + Phi_n2 d(n2,n3) F + Phi_n1 d(n1,n2) G
+ *               + Psi_n1 d(n1,n2) d(n2,n3) H ]                    (Eq. 15)
+ *   eta_n   = P_NLI,n / P_n^3                                       (Eq. 11)
+ *
+ * where D..H are the 2-D (f1, f2) island integrals of Eq. 17-21 at f = the COI
+ * centre, the link function Upsilon is Eq. 22 with the segment closed form of
+ * the ISRS four-wave-mixing efficiency mu_s (Eq. 7-10) and the ISRS power
+ * profile of Eq. 25.  The islands are the (kappa1, kappa2, l) set of Eq. 16,
+ * generalised to arbitrary channel centres and rates.  Equations refer to
+ * arXiv 2412.11614 (Xia et al., "Acceleration and Parallelization Methods for
+ * ISRS EGN Model").
+ *
+ * Conventions
+ *   - Units at the boundary are SI, except the customary fibre units named in
+ *     egn_span.  Internally: THz, ps, km, W.
+ *   - Channel centres must be strictly increasing, with supports
+ *     R_n (1 + rolloff) that do not overlap.
+ *   - The spectral centre f_c = (f_min + f_max) / 2 of the channel centres is
+ *     the origin of the ISRS profile (Eq. 25) and of beta2/beta3 (Eq. 24);
+ *     B_tot = (f_max - f_min) N / (N - 1) (B_tot = R for one channel);
+ *     P_tot = sum of the launch powers.
+ *   - Spans: every span is restored by an ideal amplifier (the gain/ISRS
+ *     products of Eq. 22 equal 1).  Identical spans use the closed-form
+ *     phased-array sum of Eq. 22.
+ *   - Pulse spectra: raised cosine |S(f)|^2 = h(f)/R^2 with roll-off
+ *     `rolloff`; the COI integral over f is R times the value at the COI
+ *     centre (white NLI over the channel).
+ *
+ * Ownership: every input array is copied; the caller keeps ownership.  Host
+ * outputs are caller-allocated arrays of n_ch doubles.  An egn_link owns its
+ * device tables (cudaMalloc on the current device at egn_set_wdm) until
+ * egn_link_destroy.
+ *
+ * Errors: every entry point returns an egn_status; nothing is thrown across the
+ * ABI.  egn_last_error() returns a thread-local message for the last failure.
+ * A link is not thread-safe: calls on one link must be serialised by the caller.
+ */
+#ifndef EGN_H
+#define EGN_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct egn_link egn_link; /* opaque, library-owned */
+
+typedef enum {
+    EGN_OK = 0,
+    EGN_E_INVALID_ARG = 1, /* NULL pointer, NaN, non-positive rate/length/alpha, Cr < 0,
+                              unsorted or overlapping channels, bad option value */
+    EGN_E_UNSUPPORTED = 2, /* a valid request outside what this build evaluates */
+    EGN_E_NOMEM = 3,       /* host or device allocation failed */
+    EGN_E_CUDA = 4,        /* a CUDA runtime call or kernel launch failed */
+    EGN_E_TIMEOUT = 5,     /* the device did not finish within opts->timeout_ms */
+    EGN_E_STATE = 6,       /* call out of order (e.g. egn_nli_eta before egn_set_wdm) */
+    EGN_E_CAPACITY = 7     /* caller workspace smaller than egn_workspace_size() */
+} egn_status;
+
+/* One fibre span (Table I / Table II quantities).
+ *   alpha_db_per_km   power attenuation [dB/km], > 0
+ *   D_ps_nm_km        dispersion at lambda_ref_m [ps/nm/km]
+ *   S_ps_nm2_km       dispersion slope at lambda_ref_m [ps/nm^2/km]
+ *   lambda_ref_m      reference wavelength of D and S [m], > 0
+ *   gamma_per_w_km    nonlinear coefficient [1/W/km], >= 0
+ *   cr_per_w_km_thz   Raman gain slope Cr [1/W/km/THz], >= 0 (Eq. 25)
+ *   length_m          span length L_s [m], > 0
+ * beta2 = -D lambda^2 / (2 pi c), beta3 = (lambda^2 / (2 pi c))^2 (S + 2 D / lambda),
+ * and beta2 is moved to the spectral centre by beta2 + 2 pi beta3 (f_c - c/lambda). */
+typedef struct {
+    double alpha_db_per_km;
+    double D_ps_nm_km;
+    double S_ps_nm2_km;
+    double lambda_ref_m;
+    double gamma_per_w_km;
+    double cr_per_w_km_thz;
+    double length_m;
+} egn_span;
+
+enum { EGN_MU_SEGMENT = 0 };               /* Eq. 7-10; the only form on the GPU path */
+enum { EGN_PREC_FP64 = 0, EGN_PREC_FP32C = 1 };
+enum { EGN_TERMS_GN = 0, EGN_TERMS_EGN = 1 };
+enum { EGN_FMT_GAUSS = 0, EGN_FMT_QPSK = 1, EGN_FMT_16QAM = 2, EGN_FMT_64QAM = 3 };
+
+/* Evaluation options.
+ *   gl_order    n: each island is integrated with an n x n Gauss-Legendre rule
+ *               (outer range split at the kinks of the inner limits into P <= 3
+ *               panels of ceil(n/P) nodes, n inner nodes); 1 <= n <= 128.
+ *   dz_km       segment length bound Delta z [km]: K = ceil(L / dz) segments of
+ *               length L/K per span (Sec. II-C-2); K <= 1024.
+ *   mu_form     EGN_MU_SEGMENT.
+ *   precision   EGN_PREC_FP64: every step in FP64 (the plain baseline);
+ *               EGN_PREC_FP32C: FP32 integrand, phases reduced exactly with
+ *               FP64 island constants and compensated FP32 (double-float)
+ *               arithmetic, compensated island sums.
+ *   terms       EGN_TERMS_GN (D only) or EGN_TERMS_EGN (D + E, F, G, H).
+ *   timeout_ms  host-side wait limit for egn_nli_eta (0 = none) -> EGN_E_TIMEOUT.
+ *   stream      cudaStream_t to launch on (NULL = the legacy default stream). */
+typedef struct {
+    int gl_order;
+    double dz_km;
+    int mu_form;
+    int precision;
+    int terms;
+    int timeout_ms;
+    void* stream;
+} egn_opts;
+
+/* Create a link from n_spans >= 1 spans (copied).  Returns EGN_E_INVALID_ARG on
+ * bad parameters.  egn_nli_eta evaluates links of identical spans (the
+ * phased-array form of Eq. 22); a link whose spans differ is accepted here and
+ * refused by the evaluation calls with EGN_E_UNSUPPORTED. */
+egn_status egn_link_create(const egn_span* spans, int n_spans, egn_link** out);
+
+/* Release the link and its device tables.  NULL is ignored. */
+void egn_link_destroy(egn_link* link);
+
+/* Set the WDM comb (Eq. 15-16 inputs).  n_ch >= 1 channels with centre
+ * frequencies [Hz] (strictly increasing, non-overlapping supports), symbol rates
+ * [Baud], launch powers [W] (> 0), EGN modulation constants Phi and Psi per
+ * channel (see egn_format_moments), raised-cosine roll-off in [0, 1].
+ * Uploads the channel table to the current device and counts the islands on it.
+ * Mixed symbol rates with any Phi or Psi != 0 -> EGN_E_UNSUPPORTED (the paper
+ * gives the correction terms for one symbol rate only). */
+egn_status egn_set_wdm(egn_link* link, int n_ch, const double* centre_hz, const double* symbol_rate_baud,
+                       const double* launch_power_w, const double* phi, const double* psi, double rolloff);
+
+/* Bytes of device workspace egn_nli_eta_device needs for these options. */
+egn_status egn_workspace_size(const egn_link* link, const egn_opts* opts, size_t* bytes);
+
+/* Number of islands of the current comb: total, and per COI if per_coi != NULL
+ * (n_ch entries).  Optional E/F list sizes (islands with n1 == n3, n2 == n3). */
+egn_status egn_island_count(const egn_link* link, long long* total, long long* per_coi, long long* n_e,
+                            long long* n_f);
+
+/* eta_n [1/W^2] and P_NLI,n [W] for every channel into caller host arrays of
+ * n_ch doubles (either may be NULL).  Synchronous: plans the islands on the
+ * device, integrates, assembles, copies back.  Uses a library-owned device
+ * workspace that is kept between calls. */
+egn_status egn_nli_eta(egn_link* link, const egn_opts* opts, double* eta_per_w2, double* pnli_w);
+
+/* Device variant: same computation, asynchronous on opts->stream, writing
+ * eta_dev and pnli_dev (device arrays of n_ch doubles, either may be NULL) and
+ * using the caller's device workspace of at least egn_workspace_size() bytes
+ * (256-byte aligned).  Returns after the launches; errors found on the device
+ * are reported by the next call. */
+egn_status egn_nli_eta_device(egn_link* link, const egn_opts* opts, void* workspace, size_t workspace_bytes,
+                              double* eta_dev, double* pnli_dev);
+
+/* Per-island terms for parity checks on sampled islands: for each of n_isl
+ * islands given as 4 ints (coi, n1, n2, n3), writes 5 doubles (D, E, F, G, H)
+ * into terms_out (host), evaluated by the same device kernels as egn_nli_eta.
+ * Terms whose Kronecker delta in Eq. 15 is zero are written as 0 unless
+ * all_terms != 0.  A non-existent island yields zeros. */
+egn_status egn_island_terms(egn_link* link, const egn_opts* opts, int n_isl, const int* coi_n1_n2_n3,
+                            int all_terms, double* terms_out);
+
+/* The island list of the current comb as planned on the device (for tests):
+ * up to max entries of 4 ints (coi, n1, n2, n3) in the order the integrator
+ * visits them (COI, then n1, n2, n3 ascending).  *count gets the total. */
+egn_status egn_plan_islands(egn_link* link, long long max, int* coi_n1_n2_n3, long long* count);
+
+/* Per-stage device timing.  With profiling on, every evaluation records CUDA
+ * events on its stream around five stages; egn_last_timings waits for the last
+ * evaluation and writes up to max durations [ms] in the order: island planner,
+ * D/G/H pass, E pass, F pass, assembly.  *n gets the number written. */
+egn_status egn_set_profiling(egn_link* link, int enable);
+egn_status egn_last_timings(egn_link* link, double* ms, int max, int* n);
+
+/* EGN constants of a modulation format (EGN_FMT_*): Phi = mu4 - 2 and
+ * Psi = mu6 - 9 mu4 + 12 with mu_k = E|a|^k / (E|a|^2)^(k/2) of the
+ * equiprobable square QAM (0 for the Gaussian limit). */
+egn_status egn_format_moments(int fmt, double* phi, double* psi);
+
+/* Gauss-Legendre nodes (ascending) and weights on [-1, 1] of order n (1..4096),
+ * as used by the node rule; x and w hold n doubles each. */
+egn_status egn_gauss_legendre(int n, double* x, double* w);
+
+/* Thread-local message describing the last failure on this thread. */
+const char* egn_last_error(void);
+
+/* Library version string. */
+const char* egn_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* EGN_H */

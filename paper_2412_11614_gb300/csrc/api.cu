@@ -1,0 +1,742 @@
+// api.cu -- C ABI of the ISRS EGN integrator: validation, unit conversion, link
+// and segment tables, workspace management and the launch sequence
+//   plan (A1) -> integrate (A3-A8) -> assemble (A9)
+// on one CUDA stream.  See include/egn.h for the contract of every entry point.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "../../include/egn.h"
+#include "egn_internal.h"
+
+namespace {
+
+thread_local std::string g_last_error;
+
+egn_status fail(egn_status s, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_last_error = buf;
+  return s;
+}
+
+#define EGN_CUDA(call)                                                                          \
+  do {                                                                                          \
+    cudaError_t e_ = (call);                                                                    \
+    if (e_ != cudaSuccess) return fail(EGN_E_CUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+  } while (0)
+
+bool finite_pos(double x) { return std::isfinite(x) && x > 0.0; }
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// Device buffer owned by a link.
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+  cudaError_t ensure(size_t want) {
+    if (want <= bytes && p) return cudaSuccess;
+    if (p) cudaFree(p);
+    p = nullptr;
+    bytes = 0;
+    cudaError_t e = cudaMalloc(&p, want);
+    if (e == cudaSuccess) bytes = want;
+    return e;
+  }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    bytes = 0;
+  }
+};
+
+}  // namespace
+
+struct egn_link {
+  std::vector<egn_span> spans_si;
+  bool identical = true;
+  // comb (internal units)
+  int n_ch = 0;
+  double fc_hz = 0, btot = 0, ptot = 0, rolloff = 0;
+  std::vector<double> nu, R, W, P, phi, psi;
+  bool mixed_rates = false, any_corr = false;
+  long long n_isl = 0, n_e = 0, n_f = 0;
+  std::vector<long long> per_coi;
+  int device = -1;
+  DevBuf d_ch;  // 6 arrays of n_ch doubles
+  // cached tables for the last (dz, gl_order)
+  double tab_dz = -1.0;
+  int tab_gl = -1;
+  int K = 0;
+  egn::Span span{};
+  DevBuf d_seg, d_gl;
+  egn::SegmentTables seg{};
+  egn::GlTables gl{};
+  // optional per-stage device timing of the last evaluation
+  bool prof_on = false;
+  bool prof_valid = false;
+  cudaEvent_t prof_ev[6] = {};
+  // library-owned workspace and pinned staging for the host API
+  DevBuf ws;
+  double* h_stage = nullptr;  // [2 n_ch + 1]
+  DevBuf d_stage;
+  ~egn_link() {
+    d_ch.release();
+    d_seg.release();
+    d_gl.release();
+    ws.release();
+    d_stage.release();
+    if (h_stage) cudaFreeHost(h_stage);
+    for (auto& e : prof_ev)
+      if (e) cudaEventDestroy(e);
+  }
+};
+
+namespace egn {
+
+// Gauss-Legendre nodes and weights on [-1, 1] by Newton's method on P_n, started
+// from Tricomi's asymptotic node estimate; nodes ascending.
+void gauss_legendre(int n, double* x, double* w) {
+  for (int k = 1; k <= (n + 1) / 2; ++k) {
+    double th = kPi * (4.0 * k - 1.0) / (4.0 * n + 2.0);
+    double xk = (1.0 - 1.0 / (8.0 * n * n) + 1.0 / (8.0 * n * n * n)) * std::cos(th);
+    double dpn = 1.0;
+    for (int it = 0; it < 50; ++it) {
+      double pm1 = 1.0, pn = xk;  // P_0, P_1
+      for (int j = 1; j < n; ++j) {
+        double pp = ((2.0 * j + 1.0) * xk * pn - j * pm1) / (j + 1.0);
+        pm1 = pn;
+        pn = pp;
+      }
+      dpn = n * (pm1 - xk * pn) / (1.0 - xk * xk);
+      double step = pn / dpn;
+      xk -= step;
+      if (std::fabs(step) <= 1e-16) break;
+    }
+    {
+      double pm1 = 1.0, pn = xk;
+      for (int j = 1; j < n; ++j) {
+        double pp = ((2.0 * j + 1.0) * xk * pn - j * pm1) / (j + 1.0);
+        pm1 = pn;
+        pn = pp;
+      }
+      dpn = n * (pm1 - xk * pn) / (1.0 - xk * xk);
+    }
+    double wk = 2.0 / ((1.0 - xk * xk) * dpn * dpn);
+    // xk is the k-th largest node; mirror to the k-th smallest
+    x[n - k] = xk;
+    w[n - k] = wk;
+    x[k - 1] = -xk;
+    w[k - 1] = wk;
+  }
+  if (n % 2 == 1) x[n / 2] = 0.0;
+}
+
+size_t workspace_bytes(int n_ch, long long n_isl, long long n_e, long long n_f, int precision) {
+  size_t n_rows = (size_t)n_ch * n_ch;
+  size_t tsz = precision == EGN_PREC_FP64 ? sizeof(double) : sizeof(float);
+  size_t b = 0;
+  b += align256((size_t)n_isl * sizeof(uint64_t));
+  b += align256((size_t)n_e * sizeof(uint32_t));
+  b += align256((size_t)n_f * sizeof(uint32_t));
+  b += align256(3 * n_rows * sizeof(uint32_t));
+  b += align256(3 * (n_rows + 1) * sizeof(uint32_t));
+  b += align256(5 * (size_t)n_isl * tsz);
+  b += align256((size_t)n_ch * sizeof(double));
+  b += align256((size_t)n_ch * sizeof(double));
+  b += align256(sizeof(int));
+  return b;
+}
+
+Workspace carve_workspace(void* base, int n_ch, long long n_isl, long long n_e, long long n_f, int precision) {
+  size_t n_rows = (size_t)n_ch * n_ch;
+  size_t tsz = precision == EGN_PREC_FP64 ? sizeof(double) : sizeof(float);
+  char* p = (char*)base;
+  Workspace w{};
+  w.keys = (uint64_t*)p;
+  p += align256((size_t)n_isl * sizeof(uint64_t));
+  w.e_idx = (uint32_t*)p;
+  p += align256((size_t)n_e * sizeof(uint32_t));
+  w.f_idx = (uint32_t*)p;
+  p += align256((size_t)n_f * sizeof(uint32_t));
+  w.row_cnt = (uint32_t*)p;
+  p += align256(3 * n_rows * sizeof(uint32_t));
+  w.row_off = (uint32_t*)p;
+  p += align256(3 * (n_rows + 1) * sizeof(uint32_t));
+  w.terms = (void*)p;
+  p += align256(5 * (size_t)n_isl * tsz);
+  w.out_eta = (double*)p;
+  p += align256((size_t)n_ch * sizeof(double));
+  w.out_pnli = (double*)p;
+  p += align256((size_t)n_ch * sizeof(double));
+  w.status = (int*)p;
+  w.cap_isl = n_isl;
+  w.cap_e = n_e;
+  w.cap_f = n_f;
+  return w;
+}
+
+}  // namespace egn
+
+namespace {
+
+using namespace egn;
+
+// Span in internal units; beta2 moved to the spectral centre fc_hz (Eq. 24
+// frequencies are relative to f_c).
+Span to_internal(const egn_span& s, double fc_hz) {
+  Span o;
+  o.alpha = s.alpha_db_per_km * std::log(10.0) / 10.0;
+  double lam = s.lambda_ref_m;
+  double k = lam * lam / (2.0 * kPi * kC);                      // s m
+  double b2 = -(s.D_ps_nm_km * 1e-6) * k * 1e27;               // ps^2/km
+  double b3 = k * k * (s.S_ps_nm2_km * 1e3 + 2.0 * (s.D_ps_nm_km * 1e-6) / lam) * 1e39;  // ps^3/km
+  double df_thz = (fc_hz - kC / lam) * 1e-12;
+  o.beta2 = b2 + 2.0 * kPi * b3 * df_thz;
+  o.beta3 = b3;
+  o.gamma = s.gamma_per_w_km;
+  o.cr = s.cr_per_w_km_thz;
+  o.L = s.length_m * 1e-3;
+  return o;
+}
+
+egn_status check_opts(const egn_link* l, const egn_opts* o) {
+  if (!l || !o) return fail(EGN_E_INVALID_ARG, "null link or options");
+  if (l->n_ch <= 0) return fail(EGN_E_STATE, "egn_set_wdm has not been called");
+  if (o->gl_order < 1 || o->gl_order > kMaxGl) return fail(EGN_E_INVALID_ARG, "gl_order %d not in [1, %d]", o->gl_order, kMaxGl);
+  if (!finite_pos(o->dz_km)) return fail(EGN_E_INVALID_ARG, "dz_km must be positive");
+  if (o->mu_form != EGN_MU_SEGMENT) return fail(EGN_E_UNSUPPORTED, "only the segment form (Eq. 8-10) runs on the GPU");
+  if (o->precision != EGN_PREC_FP64 && o->precision != EGN_PREC_FP32C)
+    return fail(EGN_E_INVALID_ARG, "unknown precision %d", o->precision);
+  if (o->terms != EGN_TERMS_GN && o->terms != EGN_TERMS_EGN) return fail(EGN_E_INVALID_ARG, "unknown terms %d", o->terms);
+  if (o->timeout_ms < 0) return fail(EGN_E_INVALID_ARG, "timeout_ms < 0");
+  if (!l->identical) return fail(EGN_E_UNSUPPORTED, "spans differ: only identical spans are evaluated");
+  double L = l->spans_si[0].length_m * 1e-3;
+  double kk = std::ceil(L / o->dz_km);
+  if (kk > kMaxK) return fail(EGN_E_INVALID_ARG, "K = ceil(L/dz) = %.0f exceeds %d", kk, kMaxK);
+  if (o->terms == EGN_TERMS_EGN && l->mixed_rates && l->any_corr)
+    return fail(EGN_E_UNSUPPORTED, "EGN corrections with mixed symbol rates are not defined");
+  return EGN_OK;
+}
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    if (dev >= 0 && cudaGetDevice(&prev) == cudaSuccess && prev != dev) cudaSetDevice(dev); else prev = -1;
+  }
+  ~DeviceGuard() {
+    if (prev >= 0) cudaSetDevice(prev);
+  }
+};
+
+// (Re)build the segment and Gauss-Legendre tables for these options.
+egn_status ensure_tables(egn_link* l, const egn_opts* o) {
+  if (l->tab_dz != o->dz_km) {
+    Span s = to_internal(l->spans_si[0], l->fc_hz);
+    int K = (int)std::ceil(s.L / o->dz_km);
+    if (K < 1) K = 1;
+    std::vector<double> zeta(K), ck(K);
+    std::vector<float> zf(K), cf(K);
+    for (int k = 0; k < K; ++k) {
+      double z = (k + 0.5) / K * s.L;
+      double leff = -std::expm1(-s.alpha * z) / s.alpha;
+      zeta[k] = l->ptot * s.cr * leff;
+      double x = l->btot * zeta[k];
+      ck[k] = (x == 0.0) ? 1.0 : x / (2.0 * std::sinh(0.5 * x));
+      zf[k] = (float)(zeta[k] * 1.4426950408889634);  // log2(e)
+      cf[k] = (float)ck[k];
+    }
+    size_t bytes = align256(K * sizeof(double)) * 2 + align256(K * sizeof(float)) * 2;
+    EGN_CUDA(l->d_seg.ensure(bytes));
+    char* p = (char*)l->d_seg.p;
+    EGN_CUDA(cudaMemcpy(p, zeta.data(), K * sizeof(double), cudaMemcpyHostToDevice));
+    l->seg.zeta = (const double*)p;
+    p += align256(K * sizeof(double));
+    EGN_CUDA(cudaMemcpy(p, ck.data(), K * sizeof(double), cudaMemcpyHostToDevice));
+    l->seg.ck = (const double*)p;
+    p += align256(K * sizeof(double));
+    EGN_CUDA(cudaMemcpy(p, zf.data(), K * sizeof(float), cudaMemcpyHostToDevice));
+    l->seg.zeta_f = (const float*)p;
+    p += align256(K * sizeof(float));
+    EGN_CUDA(cudaMemcpy(p, cf.data(), K * sizeof(float), cudaMemcpyHostToDevice));
+    l->seg.ck_f = (const float*)p;
+    l->seg.K = K;
+    l->K = K;
+    l->span = s;
+    l->tab_dz = o->dz_km;
+  }
+  if (l->tab_gl != o->gl_order) {
+    int n = o->gl_order;
+    std::vector<char> host;
+    size_t off[4][7] = {};
+    size_t total = 0;
+    int ord[4] = {0, n, (n + 1) / 2, (n + 2) / 3};
+    for (int p = 1; p <= 3; ++p) {
+      int m = ord[p];
+      for (int a = 0; a < 2; ++a) { off[p][a] = total; total += align256(m * sizeof(double)); }
+      for (int a = 2; a < 7; ++a) { off[p][a] = total; total += align256(m * sizeof(float)); }
+    }
+    host.assign(total, 0);
+    for (int p = 1; p <= 3; ++p) {
+      int m = ord[p];
+      std::vector<double> x(m), w(m);
+      gauss_legendre(m, x.data(), w.data());
+      double* hx = (double*)(host.data() + off[p][0]);
+      double* hw = (double*)(host.data() + off[p][1]);
+      float* xh = (float*)(host.data() + off[p][2]);
+      float* xl = (float*)(host.data() + off[p][3]);
+      float* x2h = (float*)(host.data() + off[p][4]);
+      float* x2l = (float*)(host.data() + off[p][5]);
+      float* wf = (float*)(host.data() + off[p][6]);
+      for (int i = 0; i < m; ++i) {
+        hx[i] = x[i];
+        hw[i] = w[i];
+        xh[i] = (float)x[i];
+        xl[i] = (float)(x[i] - (double)xh[i]);
+        double x2 = x[i] * x[i];
+        x2h[i] = (float)x2;
+        x2l[i] = (float)(x2 - (double)x2h[i]);
+        wf[i] = (float)w[i];
+      }
+    }
+    EGN_CUDA(l->d_gl.ensure(total));
+    EGN_CUDA(cudaMemcpy(l->d_gl.p, host.data(), total, cudaMemcpyHostToDevice));
+    char* b = (char*)l->d_gl.p;
+    l->gl.n = n;
+    for (int p = 1; p <= 3; ++p) {
+      l->gl.order[p] = ord[p];
+      l->gl.x[p] = (const double*)(b + off[p][0]);
+      l->gl.w[p] = (const double*)(b + off[p][1]);
+      l->gl.xh[p] = (const float*)(b + off[p][2]);
+      l->gl.xl[p] = (const float*)(b + off[p][3]);
+      l->gl.x2h[p] = (const float*)(b + off[p][4]);
+      l->gl.x2l[p] = (const float*)(b + off[p][5]);
+      l->gl.wf[p] = (const float*)(b + off[p][6]);
+    }
+    l->gl.order[0] = 0;
+    l->tab_gl = n;
+  }
+  return EGN_OK;
+}
+
+ChannelTable channel_table(const egn_link* l) {
+  ChannelTable t;
+  const double* b = (const double*)l->d_ch.p;
+  size_t s = align256(l->n_ch * sizeof(double)) / sizeof(double);
+  t.n_ch = l->n_ch;
+  t.wmax = *std::max_element(l->W.begin(), l->W.end());
+  t.nu = b;
+  t.R = b + s;
+  t.W = b + 2 * s;
+  t.P = b + 3 * s;
+  t.phi = b + 4 * s;
+  t.psi = b + 5 * s;
+  return t;
+}
+
+LinkParams link_params(const egn_link* l, const egn_opts* o, int all_terms) {
+  LinkParams p{};
+  p.ch = channel_table(l);
+  p.gl = l->gl;
+  p.seg = l->seg;
+  p.n_spans = (int)l->spans_si.size();
+  p.alpha = l->span.alpha;
+  p.beta2 = l->span.beta2;
+  p.beta3 = l->span.beta3;
+  p.gamma = l->span.gamma;
+  p.L = l->span.L;
+  p.dz = l->span.L / l->K;
+  p.r = std::exp(-l->span.alpha * p.dz);
+  p.rolloff = l->rolloff;
+  p.terms = o->terms;
+  p.all_terms = all_terms;
+  return p;
+}
+
+// Integrator passes: D/G/H over all islands, then E and F over their lists
+// (or over every island when all_terms is set).  ev, if given, is recorded after
+// each pass.
+cudaError_t integrate(const LinkParams& p, int precision, const uint64_t* keys, long long n_isl,
+                      const uint32_t* e_idx, long long n_e, const uint32_t* f_idx, long long n_f, void* terms,
+                      cudaStream_t st, cudaEvent_t* ev) {
+  auto pass = [&](int ord, const uint32_t* list, long long n) {
+    return precision == EGN_PREC_FP64 ? launch_fp64_pass(ord, p, keys, list, n, (double*)terms, n_isl, st)
+                                      : launch_fp32c_pass(ord, p, keys, list, n, (float*)terms, n_isl, st);
+  };
+  bool corr = p.all_terms || p.terms;
+  const uint32_t* el = p.all_terms ? nullptr : e_idx;
+  const uint32_t* fl = p.all_terms ? nullptr : f_idx;
+  long long ne = p.all_terms ? n_isl : (corr ? n_e : 0);
+  long long nf = p.all_terms ? n_isl : (corr ? n_f : 0);
+  cudaError_t e = pass(0, nullptr, n_isl);
+  if (e == cudaSuccess && ev) e = cudaEventRecord(ev[0], st);
+  if (e == cudaSuccess) e = pass(1, el, ne);
+  if (e == cudaSuccess && ev) e = cudaEventRecord(ev[1], st);
+  if (e == cudaSuccess) e = pass(2, fl, nf);
+  if (e == cudaSuccess && ev) e = cudaEventRecord(ev[2], st);
+  return e;
+}
+
+// The whole step on one stream: plan -> integrate -> assemble.
+egn_status run_step(egn_link* l, const egn_opts* o, const Workspace& ws, double* eta, double* pnli) {
+  cudaStream_t st = (cudaStream_t)o->stream;
+  ChannelTable ch = channel_table(l);
+  cudaEvent_t* ev = nullptr;
+  l->prof_valid = false;
+  if (l->prof_on) {
+    for (auto& e : l->prof_ev)
+      if (!e) EGN_CUDA(cudaEventCreate(&e));
+    ev = l->prof_ev;
+    EGN_CUDA(cudaEventRecord(ev[0], st));
+  }
+  EGN_CUDA(cudaMemsetAsync(ws.status, 0, sizeof(int), st));
+  EGN_CUDA(launch_plan(ch, ws, st));
+  if (ev) EGN_CUDA(cudaEventRecord(ev[1], st));
+  LinkParams p = link_params(l, o, 0);
+  EGN_CUDA(integrate(p, o->precision, ws.keys, l->n_isl, ws.e_idx, l->n_e, ws.f_idx, l->n_f, ws.terms, st,
+                     ev ? ev + 2 : nullptr));
+  EGN_CUDA(launch_assemble(ch, ws.row_off, ws.keys, l->n_isl, ws.terms, o->precision, o->terms, eta, pnli, st));
+  if (ev) {
+    EGN_CUDA(cudaEventRecord(ev[5], st));
+    l->prof_valid = true;
+  }
+  return EGN_OK;
+}
+
+egn_status wait_event(cudaEvent_t ev, int timeout_ms) {
+  auto t0 = std::chrono::steady_clock::now();
+  for (;;) {
+    cudaError_t e = cudaEventQuery(ev);
+    if (e == cudaSuccess) return EGN_OK;
+    if (e != cudaErrorNotReady) return fail(EGN_E_CUDA, "device error: %s", cudaGetErrorString(e));
+    if (timeout_ms > 0) {
+      auto ms = std::chrono::duration_cast<std::chrono::milliseconds>(std::chrono::steady_clock::now() - t0).count();
+      if (ms > timeout_ms) return fail(EGN_E_TIMEOUT, "device work not finished after %d ms", timeout_ms);
+    }
+    std::this_thread::sleep_for(std::chrono::microseconds(200));
+  }
+}
+
+// Closed-form moments of an equiprobable square QAM with m levels per dimension
+// from its 1-D PAM levels +-1, +-3, ..., +-(m-1).
+void qam_moments(int m, double* phi, double* psi) {
+  double e2 = 0, e4 = 0, e6 = 0;
+  for (int i = 0; i < m; ++i) {
+    double a = 2.0 * i - (m - 1);
+    e2 += a * a;
+    e4 += a * a * a * a;
+    e6 += a * a * a * a * a * a;
+  }
+  e2 /= m;
+  e4 /= m;
+  e6 /= m;
+  // |x + iy|^{2k} moments with x, y independent PAM
+  double s2 = 2 * e2, s4 = 2 * e4 + 2 * e2 * e2, s6 = 2 * e6 + 6 * e4 * e2;
+  double mu4 = s4 / (s2 * s2), mu6 = s6 / (s2 * s2 * s2);
+  *phi = mu4 - 2.0;
+  *psi = mu6 - 9.0 * mu4 + 12.0;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* egn_last_error(void) { return g_last_error.c_str(); }
+
+const char* egn_version(void) { return "egn-gb300 0.1 (sm_103a)"; }
+
+egn_status egn_format_moments(int fmt, double* phi, double* psi) {
+  if (!phi || !psi) return fail(EGN_E_INVALID_ARG, "null output");
+  switch (fmt) {
+    case EGN_FMT_GAUSS: *phi = 0.0; *psi = 0.0; return EGN_OK;
+    case EGN_FMT_QPSK: qam_moments(2, phi, psi); return EGN_OK;
+    case EGN_FMT_16QAM: qam_moments(4, phi, psi); return EGN_OK;
+    case EGN_FMT_64QAM: qam_moments(8, phi, psi); return EGN_OK;
+    default: return fail(EGN_E_INVALID_ARG, "unknown format %d", fmt);
+  }
+}
+
+egn_status egn_gauss_legendre(int n, double* x, double* w) {
+  if (n < 1 || n > 4096 || !x || !w) return fail(EGN_E_INVALID_ARG, "bad Gauss-Legendre request");
+  egn::gauss_legendre(n, x, w);
+  return EGN_OK;
+}
+
+egn_status egn_link_create(const egn_span* spans, int n_spans, egn_link** out) {
+  if (!out) return fail(EGN_E_INVALID_ARG, "null output pointer");
+  *out = nullptr;
+  if (!spans || n_spans < 1) return fail(EGN_E_INVALID_ARG, "need at least one span");
+  for (int i = 0; i < n_spans; ++i) {
+    const egn_span& s = spans[i];
+    if (!finite_pos(s.alpha_db_per_km)) return fail(EGN_E_INVALID_ARG, "span %d: alpha must be > 0", i);
+    if (!finite_pos(s.lambda_ref_m)) return fail(EGN_E_INVALID_ARG, "span %d: lambda_ref must be > 0", i);
+    if (!finite_pos(s.length_m)) return fail(EGN_E_INVALID_ARG, "span %d: length must be > 0", i);
+    if (!std::isfinite(s.D_ps_nm_km) || !std::isfinite(s.S_ps_nm2_km))
+      return fail(EGN_E_INVALID_ARG, "span %d: D and S must be finite", i);
+    if (!(s.gamma_per_w_km >= 0.0) || !std::isfinite(s.gamma_per_w_km))
+      return fail(EGN_E_INVALID_ARG, "span %d: gamma must be >= 0", i);
+    if (!(s.cr_per_w_km_thz >= 0.0) || !std::isfinite(s.cr_per_w_km_thz))
+      return fail(EGN_E_INVALID_ARG, "span %d: Cr must be >= 0", i);
+  }
+  egn_link* l = new (std::nothrow) egn_link();
+  if (!l) return fail(EGN_E_NOMEM, "out of host memory");
+  l->spans_si.assign(spans, spans + n_spans);
+  for (int i = 1; i < n_spans; ++i)
+    if (std::memcmp(&spans[i], &spans[0], sizeof(egn_span)) != 0) l->identical = false;
+  *out = l;
+  return EGN_OK;
+}
+
+void egn_link_destroy(egn_link* link) {
+  if (!link) return;
+  DeviceGuard g(link->device);
+  delete link;
+}
+
+egn_status egn_set_wdm(egn_link* l, int n_ch, const double* centre_hz, const double* rate, const double* power,
+                       const double* phi, const double* psi, double rolloff) {
+  if (!l) return fail(EGN_E_INVALID_ARG, "null link");
+  if (n_ch < 1 || n_ch > 4096) return fail(EGN_E_INVALID_ARG, "n_ch %d not in [1, 4096]", n_ch);
+  if (!centre_hz || !rate || !power || !phi || !psi) return fail(EGN_E_INVALID_ARG, "null channel array");
+  if (!(rolloff >= 0.0 && rolloff <= 1.0)) return fail(EGN_E_INVALID_ARG, "rolloff must be in [0, 1]");
+  for (int i = 0; i < n_ch; ++i) {
+    if (!finite_pos(centre_hz[i]) || !finite_pos(rate[i]) || !finite_pos(power[i]))
+      return fail(EGN_E_INVALID_ARG, "channel %d: centre, rate and power must be positive and finite", i);
+    if (!std::isfinite(phi[i]) || !std::isfinite(psi[i])) return fail(EGN_E_INVALID_ARG, "channel %d: Phi/Psi not finite", i);
+    if (i > 0) {
+      if (!(centre_hz[i] > centre_hz[i - 1])) return fail(EGN_E_INVALID_ARG, "channel centres must increase");
+      double gap = centre_hz[i] - centre_hz[i - 1];
+      double need = 0.5 * (rate[i] + rate[i - 1]) * (1.0 + rolloff);
+      if (gap < need * (1.0 - 1e-9)) return fail(EGN_E_INVALID_ARG, "channels %d and %d overlap", i - 1, i);
+    }
+  }
+  int dev = 0;
+  EGN_CUDA(cudaGetDevice(&dev));
+  if (l->device >= 0 && l->device != dev) return fail(EGN_E_STATE, "link is bound to device %d", l->device);
+  l->device = dev;
+  l->n_ch = 0;  // invalid until complete
+  double fmin = centre_hz[0], fmax = centre_hz[n_ch - 1];
+  l->fc_hz = 0.5 * (fmin + fmax);
+  l->rolloff = rolloff;
+  l->nu.resize(n_ch);
+  l->R.resize(n_ch);
+  l->W.resize(n_ch);
+  l->P.assign(power, power + n_ch);
+  l->phi.assign(phi, phi + n_ch);
+  l->psi.assign(psi, psi + n_ch);
+  l->ptot = 0.0;
+  l->mixed_rates = false;
+  l->any_corr = false;
+  for (int i = 0; i < n_ch; ++i) {
+    l->nu[i] = (centre_hz[i] - l->fc_hz) * 1e-12;
+    l->R[i] = rate[i] * 1e-12;
+    l->W[i] = l->R[i] * (1.0 + rolloff);
+    l->ptot += power[i];
+    if (rate[i] != rate[0]) l->mixed_rates = true;
+    if (phi[i] != 0.0 || psi[i] != 0.0) l->any_corr = true;
+  }
+  l->btot = n_ch > 1 ? (fmax - fmin) * 1e-12 * n_ch / (n_ch - 1) : l->R[0];
+  // channel table
+  size_t s = align256(n_ch * sizeof(double));
+  EGN_CUDA(l->d_ch.ensure(6 * s));
+  const std::vector<double>* arr[6] = {&l->nu, &l->R, &l->W, &l->P, &l->phi, &l->psi};
+  for (int a = 0; a < 6; ++a)
+    EGN_CUDA(cudaMemcpy((char*)l->d_ch.p + a * s, arr[a]->data(), n_ch * sizeof(double), cudaMemcpyHostToDevice));
+  l->tab_dz = -1.0;  // P_tot and B_tot changed
+  // count islands on the device
+  l->n_ch = n_ch;
+  size_t n_rows = (size_t)n_ch * n_ch;
+  size_t cnt_b = align256(3 * n_rows * sizeof(uint32_t)), off_b = align256(3 * (n_rows + 1) * sizeof(uint32_t));
+  DevBuf tmp;
+  cudaError_t e = tmp.ensure(cnt_b + off_b);
+  if (e != cudaSuccess) { l->n_ch = 0; return fail(EGN_E_NOMEM, "cudaMalloc: %s", cudaGetErrorString(e)); }
+  Workspace w{};
+  w.row_cnt = (uint32_t*)tmp.p;
+  w.row_off = (uint32_t*)((char*)tmp.p + cnt_b);
+  e = launch_plan_count(channel_table(l), w, 0);
+  std::vector<uint32_t> off(3 * (n_rows + 1));
+  if (e == cudaSuccess) e = cudaMemcpy(off.data(), w.row_off, off.size() * sizeof(uint32_t), cudaMemcpyDeviceToHost);
+  tmp.release();
+  if (e != cudaSuccess) { l->n_ch = 0; return fail(EGN_E_CUDA, "island count: %s", cudaGetErrorString(e)); }
+  l->n_isl = off[n_rows];
+  l->n_e = off[(n_rows + 1) + n_rows];
+  l->n_f = off[2 * (n_rows + 1) + n_rows];
+  l->per_coi.resize(n_ch);
+  for (int c = 0; c < n_ch; ++c) l->per_coi[c] = (long long)off[(size_t)(c + 1) * n_ch] - off[(size_t)c * n_ch];
+  // pinned staging for host outputs
+  if (l->h_stage) cudaFreeHost(l->h_stage);
+  l->h_stage = nullptr;
+  EGN_CUDA(cudaMallocHost((void**)&l->h_stage, (2 * n_ch + 2) * sizeof(double)));
+  return EGN_OK;
+}
+
+egn_status egn_island_count(const egn_link* l, long long* total, long long* per_coi, long long* n_e, long long* n_f) {
+  if (!l) return fail(EGN_E_INVALID_ARG, "null link");
+  if (l->n_ch <= 0) return fail(EGN_E_STATE, "egn_set_wdm has not been called");
+  if (total) *total = l->n_isl;
+  if (n_e) *n_e = l->n_e;
+  if (n_f) *n_f = l->n_f;
+  if (per_coi) std::copy(l->per_coi.begin(), l->per_coi.end(), per_coi);
+  return EGN_OK;
+}
+
+egn_status egn_workspace_size(const egn_link* l, const egn_opts* o, size_t* bytes) {
+  if (!bytes) return fail(EGN_E_INVALID_ARG, "null output");
+  egn_status s = check_opts(l, o);
+  if (s != EGN_OK) return s;
+  *bytes = workspace_bytes(l->n_ch, l->n_isl, l->n_e, l->n_f, o->precision);
+  return EGN_OK;
+}
+
+egn_status egn_nli_eta_device(egn_link* l, const egn_opts* o, void* workspace, size_t workspace_bytes_,
+                              double* eta_dev, double* pnli_dev) {
+  egn_status s = check_opts(l, o);
+  if (s != EGN_OK) return s;
+  if (!workspace || ((uintptr_t)workspace & 255)) return fail(EGN_E_INVALID_ARG, "workspace must be 256-byte aligned");
+  size_t need = workspace_bytes(l->n_ch, l->n_isl, l->n_e, l->n_f, o->precision);
+  if (workspace_bytes_ < need) return fail(EGN_E_CAPACITY, "workspace %zu bytes < %zu needed", workspace_bytes_, need);
+  DeviceGuard g(l->device);
+  s = ensure_tables(l, o);
+  if (s != EGN_OK) return s;
+  Workspace ws = carve_workspace(workspace, l->n_ch, l->n_isl, l->n_e, l->n_f, o->precision);
+  return run_step(l, o, ws, eta_dev ? eta_dev : ws.out_eta, pnli_dev ? pnli_dev : ws.out_pnli);
+}
+
+egn_status egn_nli_eta(egn_link* l, const egn_opts* o, double* eta, double* pnli) {
+  egn_status s = check_opts(l, o);
+  if (s != EGN_OK) return s;
+  DeviceGuard g(l->device);
+  size_t need = workspace_bytes(l->n_ch, l->n_isl, l->n_e, l->n_f, o->precision);
+  cudaError_t e = l->ws.ensure(need);
+  if (e != cudaSuccess) return fail(EGN_E_NOMEM, "workspace cudaMalloc(%zu): %s", need, cudaGetErrorString(e));
+  s = egn_nli_eta_device(l, o, l->ws.p, l->ws.bytes, nullptr, nullptr);
+  if (s != EGN_OK) return s;
+  Workspace ws = carve_workspace(l->ws.p, l->n_ch, l->n_isl, l->n_e, l->n_f, o->precision);
+  cudaStream_t st = (cudaStream_t)o->stream;
+  int n = l->n_ch;
+  EGN_CUDA(cudaMemcpyAsync(l->h_stage, ws.out_eta, n * sizeof(double), cudaMemcpyDeviceToHost, st));
+  EGN_CUDA(cudaMemcpyAsync(l->h_stage + n, ws.out_pnli, n * sizeof(double), cudaMemcpyDeviceToHost, st));
+  EGN_CUDA(cudaMemcpyAsync(l->h_stage + 2 * n, ws.status, sizeof(int), cudaMemcpyDeviceToHost, st));
+  cudaEvent_t ev;
+  EGN_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+  cudaError_t re = cudaEventRecord(ev, st);
+  if (re != cudaSuccess) { cudaEventDestroy(ev); return fail(EGN_E_CUDA, "cudaEventRecord: %s", cudaGetErrorString(re)); }
+  s = wait_event(ev, o->timeout_ms);
+  cudaEventDestroy(ev);
+  if (s != EGN_OK) return s;
+  int status = 0;
+  std::memcpy(&status, l->h_stage + 2 * n, sizeof(int));
+  if (status) return fail(EGN_E_CUDA, "device planner overflow (status %d)", status);
+  if (eta) std::memcpy(eta, l->h_stage, n * sizeof(double));
+  if (pnli) std::memcpy(pnli, l->h_stage + n, n * sizeof(double));
+  return EGN_OK;
+}
+
+egn_status egn_set_profiling(egn_link* l, int enable) {
+  if (!l) return fail(EGN_E_INVALID_ARG, "null link");
+  l->prof_on = enable != 0;
+  l->prof_valid = false;
+  return EGN_OK;
+}
+
+egn_status egn_last_timings(egn_link* l, double* ms, int max, int* n) {
+  if (!l || !ms || !n) return fail(EGN_E_INVALID_ARG, "null argument");
+  if (!l->prof_valid) return fail(EGN_E_STATE, "no profiled evaluation since egn_set_profiling");
+  DeviceGuard g(l->device);
+  EGN_CUDA(cudaEventSynchronize(l->prof_ev[5]));
+  *n = 0;
+  for (int i = 0; i < 5 && i < max; ++i) {
+    float t = 0.0f;
+    EGN_CUDA(cudaEventElapsedTime(&t, l->prof_ev[i], l->prof_ev[i + 1]));
+    ms[i] = t;
+    *n = i + 1;
+  }
+  return EGN_OK;
+}
+
+egn_status egn_plan_islands(egn_link* l, long long max, int* out, long long* count) {
+  if (!l || !count) return fail(EGN_E_INVALID_ARG, "null argument");
+  if (l->n_ch <= 0) return fail(EGN_E_STATE, "egn_set_wdm has not been called");
+  DeviceGuard g(l->device);
+  size_t need = workspace_bytes(l->n_ch, l->n_isl, l->n_e, l->n_f, EGN_PREC_FP64);
+  cudaError_t e = l->ws.ensure(need);
+  if (e != cudaSuccess) return fail(EGN_E_NOMEM, "workspace cudaMalloc(%zu): %s", need, cudaGetErrorString(e));
+  Workspace ws = carve_workspace(l->ws.p, l->n_ch, l->n_isl, l->n_e, l->n_f, EGN_PREC_FP64);
+  EGN_CUDA(cudaMemset(ws.status, 0, sizeof(int)));
+  EGN_CUDA(launch_plan(channel_table(l), ws, 0));
+  std::vector<uint64_t> keys(l->n_isl);
+  EGN_CUDA(cudaMemcpy(keys.data(), ws.keys, keys.size() * sizeof(uint64_t), cudaMemcpyDeviceToHost));
+  *count = l->n_isl;
+  long long m = std::min<long long>(max, l->n_isl);
+  for (long long i = 0; out && i < m; ++i) {
+    int c, a, b, d;
+    unpack_key(keys[i], c, a, b, d);
+    out[4 * i] = c;
+    out[4 * i + 1] = a;
+    out[4 * i + 2] = b;
+    out[4 * i + 3] = d;
+  }
+  return EGN_OK;
+}
+
+egn_status egn_island_terms(egn_link* l, const egn_opts* o, int n_isl, const int* isl, int all_terms, double* out) {
+  egn_status s = check_opts(l, o);
+  if (s != EGN_OK) return s;
+  if (n_isl < 0 || (n_isl > 0 && (!isl || !out))) return fail(EGN_E_INVALID_ARG, "bad island list");
+  if (n_isl == 0) return EGN_OK;
+  DeviceGuard g(l->device);
+  s = ensure_tables(l, o);
+  if (s != EGN_OK) return s;
+  std::vector<uint64_t> keys(n_isl);
+  std::vector<uint32_t> e_list, f_list;
+  for (int i = 0; i < n_isl; ++i) {
+    const int* q = isl + 4 * i;
+    for (int a = 0; a < 4; ++a)
+      if (q[a] < 0 || q[a] >= l->n_ch) return fail(EGN_E_INVALID_ARG, "island %d: channel index out of range", i);
+    keys[i] = pack_key(q[0], q[1], q[2], q[3]);
+    if (o->terms && flag_e(q[1], q[2], q[3])) e_list.push_back(i);
+    if (o->terms && flag_f(q[1], q[2], q[3])) f_list.push_back(i);
+  }
+  size_t tsz = o->precision == EGN_PREC_FP64 ? sizeof(double) : sizeof(float);
+  size_t b_keys = align256(n_isl * sizeof(uint64_t)), b_e = align256(e_list.size() * 4 + 4),
+         b_f = align256(f_list.size() * 4 + 4), b_t = align256(5 * (size_t)n_isl * tsz);
+  DevBuf tmp;
+  cudaError_t e = tmp.ensure(b_keys + b_e + b_f + b_t);
+  if (e != cudaSuccess) return fail(EGN_E_NOMEM, "cudaMalloc: %s", cudaGetErrorString(e));
+  char* p = (char*)tmp.p;
+  uint64_t* d_keys = (uint64_t*)p;
+  uint32_t* d_e = (uint32_t*)(p + b_keys);
+  uint32_t* d_f = (uint32_t*)(p + b_keys + b_e);
+  void* d_t = p + b_keys + b_e + b_f;
+  egn_status rs = EGN_OK;
+  do {
+    if ((e = cudaMemcpy(d_keys, keys.data(), n_isl * sizeof(uint64_t), cudaMemcpyHostToDevice)) != cudaSuccess) break;
+    if (!e_list.empty() && (e = cudaMemcpy(d_e, e_list.data(), e_list.size() * 4, cudaMemcpyHostToDevice)) != cudaSuccess) break;
+    if (!f_list.empty() && (e = cudaMemcpy(d_f, f_list.data(), f_list.size() * 4, cudaMemcpyHostToDevice)) != cudaSuccess) break;
+    if ((e = cudaMemset(d_t, 0, 5 * (size_t)n_isl * tsz)) != cudaSuccess) break;
+    LinkParams prm = link_params(l, o, all_terms ? 1 : 0);
+    e = integrate(prm, o->precision, d_keys, n_isl, d_e, (long long)e_list.size(), d_f, (long long)f_list.size(), d_t,
+                  0, nullptr);
+    if (e != cudaSuccess) break;
+    if ((e = cudaDeviceSynchronize()) != cudaSuccess) break;
+    std::vector<char> h(5 * (size_t)n_isl * tsz);
+    if ((e = cudaMemcpy(h.data(), d_t, h.size(), cudaMemcpyDeviceToHost)) != cudaSuccess) break;
+    for (int i = 0; i < n_isl; ++i)
+      for (int t = 0; t < 5; ++t)
+        out[5 * i + t] = tsz == 8 ? ((double*)h.data())[(size_t)t * n_isl + i] : ((float*)h.data())[(size_t)t * n_isl + i];
+  } while (0);
+  tmp.release();
+  if (e != cudaSuccess) rs = fail(EGN_E_CUDA, "island terms: %s", cudaGetErrorString(e));
+  return rs;
+}
+
+}  // extern "C"

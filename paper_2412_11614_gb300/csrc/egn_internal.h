@@ -1,0 +1,134 @@
+// egn_internal.h -- library-internal types shared by the host API and the CUDA
+// kernels of the GB300 ISRS EGN integrator (not part of the C ABI).
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace egn {
+
+constexpr double kPi = 3.141592653589793238462643383279502884;
+constexpr double kC = 299792458.0;  // m/s
+constexpr int kMaxGl = 128;
+constexpr int kMaxK = 896;  // FP64 row tables: 32 lanes x K doubles of shared memory
+
+// Internal span: power attenuation [1/km], beta2 at the spectral centre
+// [ps^2/km], beta3 [ps^3/km], gamma [1/W/km], Cr [1/W/km/THz], length [km].
+struct Span {
+  double alpha, beta2, beta3, gamma, cr, L;
+};
+
+// Island key: COI, n1, n2, n3 packed in 16-bit fields (COI in the low bits).
+__host__ __device__ inline uint64_t pack_key(int coi, int n1, int n2, int n3) {
+  return (uint64_t)(uint16_t)coi | ((uint64_t)(uint16_t)n1 << 16) | ((uint64_t)(uint16_t)n2 << 32) |
+         ((uint64_t)(uint16_t)n3 << 48);
+}
+__host__ __device__ inline void unpack_key(uint64_t k, int& coi, int& n1, int& n2, int& n3) {
+  coi = (int)(k & 0xffff);
+  n1 = (int)((k >> 16) & 0xffff);
+  n2 = (int)((k >> 32) & 0xffff);
+  n3 = (int)((k >> 48) & 0xffff);
+}
+
+// Channel table on the device (structure of arrays, FP64).  nu is the centre
+// relative to the spectral centre [THz], R the symbol rate [THz], W = R (1 +
+// rolloff) the support width [THz], P the launch power [W].
+struct ChannelTable {
+  int n_ch;
+  double wmax;  // widest support [THz]
+  const double* nu;
+  const double* R;
+  const double* W;
+  const double* P;
+  const double* phi;
+  const double* psi;
+};
+
+// Gauss-Legendre tables for the three outer orders ceil(n/p), p = 1, 2, 3
+// (p = 1 is also the inner order n).  Nodes ascending on [-1, 1].
+struct GlTables {
+  int n;
+  int order[4];         // order[p] = ceil(n / p), p = 1..3
+  const double* x[4];   // FP64 nodes
+  const double* w[4];   // FP64 weights
+  const float* xh[4];   // FP32 head of the node
+  const float* xl[4];   // FP32 tail: x - (double)xh
+  const float* x2h[4];  // head of x^2
+  const float* x2l[4];  // tail of x^2
+  const float* wf[4];   // FP32 weights
+};
+
+// Per-span-type tables of the segment closed form (Eq. 8-10):
+// zeta_k = P_tot Cr L_eff(z_k), C_k = B_tot zeta_k / (2 sinh(B_tot zeta_k / 2)).
+struct SegmentTables {
+  int K;
+  const double* zeta;   // [K]
+  const double* ck;     // [K]
+  const float* zeta_f;  // [K] zeta_k * log2(e), FP32
+  const float* ck_f;    // [K]
+};
+
+// Everything an integrator launch needs, passed by value.
+struct LinkParams {
+  ChannelTable ch;
+  GlTables gl;
+  SegmentTables seg;
+  int n_spans;       // identical spans N_s
+  double alpha;      // [1/km]
+  double beta2;      // [ps^2/km] at the spectral centre
+  double beta3;      // [ps^3/km]
+  double gamma;      // [1/W/km]
+  double L;          // span length [km]
+  double dz;         // L / K [km]
+  double r;          // e^{-alpha dz}
+  double rolloff;
+  int terms;         // 0 GN, 1 EGN
+  int all_terms;     // evaluate E..H on every island (parity checks)
+};
+
+// Flags of an island (Kronecker deltas of Eq. 15).
+__host__ __device__ inline bool flag_e(int n1, int n2, int n3) { (void)n2; return n1 == n3; }
+__host__ __device__ inline bool flag_f(int n1, int n2, int n3) { (void)n1; return n2 == n3; }
+__host__ __device__ inline bool flag_g(int n1, int n2, int n3) { (void)n3; return n1 == n2; }
+__host__ __device__ inline bool flag_h(int n1, int n2, int n3) { return n1 == n2 && n2 == n3; }
+
+// Device workspace carve-up (byte offsets from the workspace base, 256-aligned).
+struct Workspace {
+  uint64_t* keys;       // [n_isl]
+  uint32_t* e_idx;      // [n_e] island indices with n1 == n3
+  uint32_t* f_idx;      // [n_f] island indices with n2 == n3
+  uint32_t* row_cnt;    // [3 * n_rows]
+  uint32_t* row_off;    // [3 * (n_rows + 1)]
+  void* terms;          // [5 * n_isl] of double (FP64) or float (FP32C), term-major
+  double* out_eta;      // [n_ch] scratch outputs when the caller passes none
+  double* out_pnli;     // [n_ch]
+  int* status;          // device error word
+  long long cap_isl, cap_e, cap_f;
+};
+
+size_t workspace_bytes(int n_ch, long long n_isl, long long n_e, long long n_f, int precision);
+Workspace carve_workspace(void* base, int n_ch, long long n_isl, long long n_e, long long n_f, int precision);
+
+// ---- launchers (defined in the .cu files) ----
+// Island planner (A1): counts per (COI, n1) row, scans, emits keys and E/F lists.
+cudaError_t launch_plan(const ChannelTable& ch, const Workspace& ws, cudaStream_t st);
+// Counting only (used by egn_set_wdm to size the workspace).
+cudaError_t launch_plan_count(const ChannelTable& ch, const Workspace& ws, cudaStream_t st);
+
+// Integrator passes.  ord = 0: D, G, H over `list` (DW order); ord = 1: E;
+// ord = 2: F.  list == nullptr means work item i is island i.
+cudaError_t launch_fp64_pass(int ord, const LinkParams& p, const uint64_t* keys, const uint32_t* list,
+                             long long n_items, double* terms, long long n_isl, cudaStream_t st);
+cudaError_t launch_fp32c_pass(int ord, const LinkParams& p, const uint64_t* keys, const uint32_t* list,
+                              long long n_items, float* terms, long long n_isl, cudaStream_t st);
+
+// Assembly (Eq. 11, 15): per-COI sums of the island contributions.
+cudaError_t launch_assemble(const ChannelTable& ch, const uint32_t* row_off, const uint64_t* keys,
+                            long long n_isl, const void* terms, int precision, int terms_mode, double* eta,
+                            double* pnli, cudaStream_t st);
+
+// Host Gauss-Legendre nodes on [-1, 1], ascending.
+void gauss_legendre(int n, double* x, double* w);
+
+}  // namespace egn

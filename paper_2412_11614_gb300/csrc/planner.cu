@@ -1,0 +1,189 @@
+// planner.cu -- island planner on the device (Eq. 15-16).
+//
+// For every COI n and every pair (n1, n2) the islands are the channels n3 whose
+// support meets the f3 = f1 + f2 - f range with positive area.  In the island's
+// local coordinates (u, v, w offsets of f1, f2, f3 from their channel centres,
+// w = u + v + d with d = (nu_n1 - nu_n) + (nu_n2 - nu_n3)) the (outer w, inner u)
+// region is non-empty iff
+//     min(W3/2, d + (W1 + W2)/2) > max(-W3/2, d - (W1 + W2)/2).
+// On a uniform grid this is the set T_kappa of Eq. 16 with n3 = n1 + n2 - n + l.
+//
+// Rows are (COI, n1) pairs (row = COI * n_ch + n1).  Three kernels: count per
+// row (one warp per row, lanes over n2), exclusive scan of the row counts (one
+// CTA), and emit (one warp per row, warp-scan of the per-lane counts), so that
+// the island list comes out in (COI, n1, n2, n3) lexicographic order together
+// with the compact lists of E (n1 == n3) and F (n2 == n3) islands.
+#include "egn_internal.h"
+
+namespace egn {
+namespace {
+
+constexpr int kPlanWarps = 8;  // warps per CTA in count/emit
+
+__device__ __forceinline__ bool island_exists(const ChannelTable& ch, int n, int n1, int n2, int n3) {
+  double d = (ch.nu[n1] - ch.nu[n]) + (ch.nu[n2] - ch.nu[n3]);
+  double hw = 0.5 * ch.W[n1] + 0.5 * ch.W[n2];
+  double a = 0.5 * ch.W[n3];
+  double lo = fmax(-a, d - hw);
+  double hi = fmin(a, d + hw);
+  return hi > lo;
+}
+
+// First channel index whose centre is >= x (channels sorted ascending).
+__device__ __forceinline__ int lower_bound(const double* nu, int n, double x) {
+  int lo = 0, hi = n;
+  while (lo < hi) {
+    int mid = (lo + hi) >> 1;
+    if (nu[mid] < x) lo = mid + 1; else hi = mid;
+  }
+  return lo;
+}
+
+// Visit the islands of (n, n1, n2) in ascending n3; f(n3) is called for each.
+template <class F>
+__device__ __forceinline__ void for_each_n3(const ChannelTable& ch, int n, int n1, int n2, F&& f) {
+  double t = (ch.nu[n1] - ch.nu[n]) + ch.nu[n2];
+  double reach = 0.5 * ch.W[n1] + 0.5 * ch.W[n2] + 0.5 * ch.wmax + 1e-6;
+  int i = lower_bound(ch.nu, ch.n_ch, t - reach);
+  for (; i < ch.n_ch && ch.nu[i] <= t + reach; ++i)
+    if (island_exists(ch, n, n1, n2, i)) f(i);
+}
+
+__global__ void plan_count_kernel(ChannelTable a, uint32_t* row_cnt, int n_rows) {
+  int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  int lane = threadIdx.x & 31;
+  if (warp >= n_rows) return;
+  int n = warp / a.n_ch, n1 = warp % a.n_ch;
+  uint32_t c = 0, ce = 0, cf = 0;
+  for (int n2 = lane; n2 < a.n_ch; n2 += 32) {
+    for_each_n3(a, n, n1, n2, [&](int n3) {
+      ++c;
+      ce += (n3 == n1);
+      cf += (n3 == n2);
+    });
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    c += __shfl_down_sync(0xffffffffu, c, o);
+    ce += __shfl_down_sync(0xffffffffu, ce, o);
+    cf += __shfl_down_sync(0xffffffffu, cf, o);
+  }
+  if (lane == 0) {
+    row_cnt[warp] = c;
+    row_cnt[n_rows + warp] = ce;
+    row_cnt[2 * n_rows + warp] = cf;
+  }
+}
+
+// Exclusive scan of the three count arrays (one CTA of 1024 threads, each thread
+// a contiguous chunk).  row_off[a * (n_rows + 1) + n_rows] is the total.
+__global__ void plan_scan_kernel(const uint32_t* row_cnt, uint32_t* row_off, int n_rows) {
+  __shared__ uint32_t warp_sum[32];
+  const int T = blockDim.x;
+  int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  int chunk = (n_rows + T - 1) / T;
+  for (int arr = 0; arr < 3; ++arr) {
+    const uint32_t* in = row_cnt + (size_t)arr * n_rows;
+    uint32_t* out = row_off + (size_t)arr * (n_rows + 1);
+    int b = tid * chunk, e = min(b + chunk, n_rows);
+    uint32_t s = 0;
+    for (int i = b; i < e; ++i) s += in[i];
+    // block exclusive scan of s
+    uint32_t x = s;
+    for (int o = 1; o < 32; o <<= 1) {
+      uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) warp_sum[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+      uint32_t v = (lane < (T >> 5)) ? warp_sum[lane] : 0;
+      for (int o = 1; o < 32; o <<= 1) {
+        uint32_t y = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += y;
+      }
+      warp_sum[lane] = v;  // inclusive warp totals
+    }
+    __syncthreads();
+    uint32_t base = (wid > 0 ? warp_sum[wid - 1] : 0) + x - s;
+    for (int i = b; i < e; ++i) {
+      out[i] = base;
+      base += in[i];
+    }
+    if (tid == T - 1) out[n_rows] = warp_sum[(T >> 5) - 1];
+    __syncthreads();
+  }
+}
+
+__global__ void plan_emit_kernel(ChannelTable a, const uint32_t* row_off, int n_rows, uint64_t* keys,
+                                 long long cap_isl, uint32_t* e_idx, long long cap_e, uint32_t* f_idx,
+                                 long long cap_f, int* status) {
+  int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  int lane = threadIdx.x & 31;
+  if (warp >= n_rows) return;
+  const int nch = a.n_ch;
+  int n = warp / nch, n1 = warp % nch;
+  uint32_t base = row_off[warp];
+  uint32_t base_e = row_off[(n_rows + 1) + warp];
+  uint32_t base_f = row_off[2 * (n_rows + 1) + warp];
+  for (int n2b = 0; n2b < nch; n2b += 32) {
+    int n2 = n2b + lane;
+    uint32_t c = 0, ce = 0, cf = 0;
+    if (n2 < nch)
+      for_each_n3(a, n, n1, n2, [&](int n3) {
+        ++c;
+        ce += (n3 == n1);
+        cf += (n3 == n2);
+      });
+    // warp exclusive scans
+    uint32_t ic = c, ie = ce, ifl = cf;
+    for (int o = 1; o < 32; o <<= 1) {
+      uint32_t y0 = __shfl_up_sync(0xffffffffu, ic, o);
+      uint32_t y1 = __shfl_up_sync(0xffffffffu, ie, o);
+      uint32_t y2 = __shfl_up_sync(0xffffffffu, ifl, o);
+      if (lane >= o) { ic += y0; ie += y1; ifl += y2; }
+    }
+    uint32_t pos = base + ic - c, pe = base_e + ie - ce, pf = base_f + ifl - cf;
+    if (n2 < nch)
+      for_each_n3(a, n, n1, n2, [&](int n3) {
+        if ((long long)pos < cap_isl) keys[pos] = pack_key(n, n1, n2, n3); else atomicOr(status, 1);
+        if (n3 == n1) {
+          if ((long long)pe < cap_e) e_idx[pe] = pos; else atomicOr(status, 2);
+          ++pe;
+        }
+        if (n3 == n2) {
+          if ((long long)pf < cap_f) f_idx[pf] = pos; else atomicOr(status, 4);
+          ++pf;
+        }
+        ++pos;
+      });
+    base += __shfl_sync(0xffffffffu, ic, 31);
+    base_e += __shfl_sync(0xffffffffu, ie, 31);
+    base_f += __shfl_sync(0xffffffffu, ifl, 31);
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_plan_count(const ChannelTable& ch, const Workspace& ws, cudaStream_t st) {
+  int n_rows = ch.n_ch * ch.n_ch;
+  int threads = kPlanWarps * 32;
+  int blocks = (n_rows + kPlanWarps - 1) / kPlanWarps;
+  plan_count_kernel<<<blocks, threads, 0, st>>>(ch, ws.row_cnt, n_rows);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  plan_scan_kernel<<<1, 1024, 0, st>>>(ws.row_cnt, ws.row_off, n_rows);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_plan(const ChannelTable& ch, const Workspace& ws, cudaStream_t st) {
+  cudaError_t e = launch_plan_count(ch, ws, st);
+  if (e != cudaSuccess) return e;
+  int n_rows = ch.n_ch * ch.n_ch;
+  int threads = kPlanWarps * 32;
+  int blocks = (n_rows + kPlanWarps - 1) / kPlanWarps;
+  plan_emit_kernel<<<blocks, threads, 0, st>>>(ch, ws.row_off, n_rows, ws.keys, ws.cap_isl, ws.e_idx, ws.cap_e,
+                                               ws.f_idx, ws.cap_f, ws.status);
+  return cudaGetLastError();
+}
+
+}  // namespace egn

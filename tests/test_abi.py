@@ -1,0 +1,113 @@
+"""CPU checks of the C ABI: the library builds and loads, exports every entry
+point include/egn.h declares, and its host-only logic (argument validation,
+format moments, Gauss-Legendre nodes) is right.  No compute call needs a GPU here."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def egn():
+    from paper_2412_11614_gb300 import _build
+    _build.build()
+    from paper_2412_11614_gb300 import egn as E
+    E.lib()
+    return E
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "egn.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(egn_[a-z_0-9]+)\s*\(", src)))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for must in ("egn_link_create", "egn_set_wdm", "egn_nli_eta", "egn_link_destroy", "egn_last_error",
+                 "egn_format_moments", "egn_nli_eta_device", "egn_workspace_size"):
+        assert must in names
+
+
+def test_every_declared_symbol_is_exported(egn):
+    L = egn.lib()
+    missing = [n for n in declared_functions() if not hasattr(L, n)]
+    assert not missing, missing
+
+
+def test_library_is_in_tree(egn):
+    assert os.path.commonpath([egn.library_path(), ROOT]) == ROOT
+
+
+def test_format_moments_match_oracle(egn, oracle_mod):
+    for f in ("QPSK", "16QAM", "64QAM", "GAUSS"):
+        a = egn.egn_format_moments(f)
+        b = oracle_mod.format_moments(f)
+        assert a == pytest.approx(b, abs=1e-13)
+
+
+def test_gauss_legendre_nodes(egn):
+    for n in (1, 2, 3, 11, 16, 32, 64, 128):
+        x, w = egn.egn_gauss_legendre(n)
+        xr, wr = np.polynomial.legendre.leggauss(n)
+        assert np.allclose(x, xr, atol=2e-15, rtol=0)
+        assert np.allclose(w, wr, atol=1e-14, rtol=0)
+
+
+def _bad_span(workloads, **kw):
+    s = workloads.config_small().spans[0]
+    for k, v in kw.items():
+        setattr(s, k, v)
+    return s
+
+
+@pytest.mark.parametrize("field,value", [("alpha_db_km", 0.0), ("alpha_db_km", float("nan")), ("length_m", -1.0),
+                                         ("cr_per_w_km_thz", -0.1), ("lambda_ref_m", 0.0),
+                                         ("gamma_per_w_km", float("inf"))])
+def test_link_create_rejects_bad_spans(egn, workloads, field, value):
+    with pytest.raises(egn.EgnError) as ei:
+        egn.Link([_bad_span(workloads, **{field: value})])
+    assert ei.value.status == egn.EGN_E_INVALID_ARG
+
+
+def test_link_create_rejects_empty(egn):
+    import ctypes as C
+    h = C.c_void_p()
+    assert egn.lib().egn_link_create(None, 0, C.byref(h)) == egn.EGN_E_INVALID_ARG
+    assert egn.lib().egn_link_create(None, 1, None) == egn.EGN_E_INVALID_ARG
+
+
+def test_set_wdm_rejects_bad_combs_before_touching_the_device(egn, workloads):
+    wl = workloads.config_small()
+    ln = egn.Link(wl.spans)
+    phi = [0.0] * 5
+    bad = [
+        dict(centre_hz=wl.centre_hz[::-1]),                                 # not increasing
+        dict(centre_hz=[wl.centre_hz[0] + 30e9 * k for k in range(5)]),     # overlapping
+        dict(symbol_rate_baud=[64e9, 64e9, -1.0, 64e9, 64e9]),
+        dict(launch_power_w=[1e-3, 1e-3, float("nan"), 1e-3, 1e-3]),
+    ]
+    for b in bad:
+        args = dict(centre_hz=wl.centre_hz, symbol_rate_baud=wl.symbol_rate_baud, launch_power_w=wl.launch_power_w)
+        args.update(b)
+        with pytest.raises(egn.EgnError) as ei:
+            ln.set_wdm(args["centre_hz"], args["symbol_rate_baud"], args["launch_power_w"], phi, phi, 0.01)
+        assert ei.value.status == egn.EGN_E_INVALID_ARG
+    with pytest.raises(egn.EgnError):
+        ln.set_wdm(wl.centre_hz, wl.symbol_rate_baud, wl.launch_power_w, phi, phi, 1.5)  # roll-off > 1
+
+
+def test_eta_before_set_wdm_is_a_state_error(egn, workloads):
+    ln = egn.Link(workloads.config_small().spans)
+    with pytest.raises(egn.EgnError) as ei:
+        ln.nli_eta(egn.make_opts())
+    assert ei.value.status == egn.EGN_E_STATE
+
+
+def test_last_error_is_informative(egn, workloads):
+    with pytest.raises(egn.EgnError) as ei:
+        egn.Link([_bad_span(workloads, length_m=0.0)])
+    assert "length" in str(ei.value)

@@ -1,0 +1,275 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 CPU oracle on the
+same seeded inputs.
+
+Tolerances (stated per test):
+  * island lists: bit-exact (the same set, in the same order);
+  * FP64 path: eta and per-island terms within 1e-9 relative (both sides FP64;
+    differences come from Horner vs term-by-term summation and node rounding);
+  * FP32C path: every channel within 0.01 dB of the oracle (the accuracy target),
+    and within 1e-3 dB on the small workloads.
+"""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+FP64_RTOL = 1e-9
+
+
+@pytest.fixture(scope="module")
+def egn():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA device required for -m gpu tests")
+    from paper_2412_11614_gb300 import _build
+    _build.build()
+    from paper_2412_11614_gb300 import egn as E
+    E.lib()
+    return E
+
+
+def _pair(egn, oracle_mod, wl, gl=None, terms=1):
+    ln = egn.link_from_workload(wl)
+    pb = oracle_mod.Problem(wl, gl_order=gl or wl.gl_order, terms=terms)
+    return ln, pb
+
+
+def _db(a, b):
+    return np.abs(10 * np.log10(np.asarray(a) / np.asarray(b)))
+
+
+# --------------------------------------------------------------------------- planner
+
+@pytest.mark.parametrize("n_ch", [1, 2, 5, 11])
+def test_island_list_bit_exact(egn, oracle_mod, workloads, n_ch):
+    wl = workloads.config_small(n_ch=n_ch, gl_order=8)
+    ln, pb = _pair(egn, oracle_mod, wl)
+    got = ln.plan_islands()
+    want = np.array([(n, *t) for n in range(n_ch) for t in pb.islands(n)], dtype=np.int32).reshape(-1, 4)
+    assert np.array_equal(got, want)
+    tot, per, ne, nf = ln.island_count()
+    assert tot == len(want)
+    assert ne == int(np.sum(want[:, 1] == want[:, 3])) and nf == int(np.sum(want[:, 2] == want[:, 3]))
+
+
+def test_island_list_irregular_comb(egn, oracle_mod, workloads):
+    wl = workloads.config_small(n_ch=6, gl_order=8)
+    base = wl.centre_hz[0]
+    wl.centre_hz = [base, base + 61e9, base + 140e9, base + 197e9, base + 262e9, base + 400e9]
+    wl.symbol_rate_baud = [40e9, 60e9, 32e9, 50e9, 64e9, 96e9]
+    wl.formats = ["GAUSS"] * 6
+    ln, pb = _pair(egn, oracle_mod, wl)
+    got = ln.plan_islands()
+    want = np.array([(n, *t) for n in range(6) for t in pb.islands(n)], dtype=np.int32).reshape(-1, 4)
+    assert np.array_equal(got, want)
+
+
+def test_island_count_config_cl(egn, workloads):
+    # 120 ch on a 75 GHz grid with 64.64 GHz supports: Eq. 16 counts
+    wl = workloads.config_cl()
+    ln = egn.link_from_workload(wl)
+    tot, per, ne, nf = ln.island_count()
+    M = 120
+    want = 0
+    for n in range(M):
+        for l in (-1, 0, 1):
+            for n1 in range(M):
+                lo, hi = max(0, n - l - n1), min(M - 1, M - 1 + n - l - n1)
+                want += max(0, hi - lo + 1)
+    assert tot == want == 3455880
+
+
+# --------------------------------------------------------------------------- FP64 path
+
+@pytest.mark.parametrize("terms", [0, 1])
+def test_fp64_eta_small(egn, oracle_mod, workloads, terms):
+    wl = workloads.config_small(gl_order=64)
+    ln, pb = _pair(egn, oracle_mod, wl, terms=terms)
+    got, gp = ln.nli_eta(egn.make_opts(gl_order=64, precision=egn.EGN_PREC_FP64, terms=terms))
+    want, wp = pb.eta()
+    assert np.allclose(got, want, rtol=FP64_RTOL, atol=0), (got / want - 1)
+    assert np.allclose(gp, wp, rtol=FP64_RTOL, atol=0)
+
+
+@pytest.mark.parametrize("gl", [1, 7, 13, 32])
+def test_fp64_island_terms_all(egn, oracle_mod, workloads, gl):
+    """All five terms on every island (ragged outer panels: ceil(n/2) nodes)."""
+    wl = workloads.config_small(gl_order=gl, n_ch=3)
+    ln, pb = _pair(egn, oracle_mod, wl, gl=gl)
+    isl = np.array([(n, *t) for n in range(3) for t in pb.islands(n)], dtype=np.int32)
+    got = ln.island_terms(egn.make_opts(gl_order=gl, precision=egn.EGN_PREC_FP64), isl, all_terms=True)
+    want = np.array([pb.island_terms(*row, all_terms=True) for row in isl])
+    assert np.allclose(got, want, rtol=FP64_RTOL, atol=1e-300)
+
+
+def test_fp64_multispan_and_mixed_widths(egn, oracle_mod, workloads):
+    """5 spans (phased array), irregular comb with three different widths (three
+    outer panels on some islands), GN terms (mixed rates)."""
+    wl = workloads.config_small(n_ch=4, gl_order=12, n_spans=5)
+    base = wl.centre_hz[0]
+    wl.centre_hz = [base, base + 61e9, base + 140e9, base + 197e9]
+    wl.symbol_rate_baud = [40e9, 60e9, 32e9, 50e9]
+    ln, pb = _pair(egn, oracle_mod, wl, terms=0)
+    got, _ = ln.nli_eta(egn.make_opts(gl_order=12, precision=egn.EGN_PREC_FP64, terms=0))
+    want, _ = pb.eta()
+    assert np.allclose(got, want, rtol=FP64_RTOL, atol=0)
+
+
+def test_fp64_single_channel_and_dz(egn, oracle_mod, workloads):
+    wl = workloads.config_small(n_ch=1, gl_order=16)
+    ln = egn.link_from_workload(wl)
+    for dz in (1.0, 0.7, 7.0):
+        pb = oracle_mod.Problem(wl, dz_km=dz)
+        got, _ = ln.nli_eta(egn.make_opts(gl_order=16, dz_km=dz, precision=egn.EGN_PREC_FP64))
+        want, _ = pb.eta()
+        assert np.allclose(got, want, rtol=FP64_RTOL, atol=0), dz
+
+
+def test_fp64_config_cl_sampled_islands(egn, oracle_mod, workloads):
+    """Full C+L workload (120 ch, 10 x 80 km, 32 x 32): per-island terms of a seeded
+    sample of islands (all COIs, all kinds) against the oracle one by one."""
+    wl = workloads.config_cl()
+    ln, pb = _pair(egn, oracle_mod, wl)
+    plan = ln.plan_islands()
+    rng = np.random.default_rng(7)
+    pick = np.concatenate([rng.choice(len(plan), 40, replace=False),
+                           np.flatnonzero(plan[:, 1] == plan[:, 3])[:: 5000],
+                           np.flatnonzero((plan[:, 1] == plan[:, 2]) & (plan[:, 2] == plan[:, 3]))[:: 40]])
+    isl = plan[pick]
+    got = ln.island_terms(egn.make_opts(gl_order=32, precision=egn.EGN_PREC_FP64), isl)
+    want = np.array([pb.island_terms(*row) for row in isl])
+    assert np.allclose(got, want, rtol=1e-8, atol=1e-300)
+
+
+def test_device_api_matches_host_api(egn, workloads):
+    import torch
+    wl = workloads.config_small(gl_order=16)
+    ln = egn.link_from_workload(wl)
+    s = torch.cuda.Stream()
+    opts = egn.make_opts(gl_order=16, precision=egn.EGN_PREC_FP64, stream=s.cuda_stream)
+    ws = torch.empty(ln.workspace_size(opts), dtype=torch.uint8, device="cuda")
+    eta = torch.empty(5, dtype=torch.float64, device="cuda")
+    pn = torch.empty(5, dtype=torch.float64, device="cuda")
+    ln.nli_eta_device(opts, ws, eta, pn)
+    s.synchronize()
+    h_eta, h_pn = ln.nli_eta(egn.make_opts(gl_order=16, precision=egn.EGN_PREC_FP64))
+    assert np.array_equal(eta.cpu().numpy(), h_eta)
+    assert np.array_equal(pn.cpu().numpy(), h_pn)
+
+
+def test_repeatable_bitwise(egn, workloads):
+    wl = workloads.config_small(gl_order=16)
+    ln = egn.link_from_workload(wl)
+    o = egn.make_opts(gl_order=16, precision=egn.EGN_PREC_FP64)
+    a, _ = ln.nli_eta(o)
+    b, _ = ln.nli_eta(o)
+    assert np.array_equal(a, b)
+
+
+def test_workspace_too_small_is_rejected(egn, workloads):
+    import torch
+    wl = workloads.config_small(gl_order=8)
+    ln = egn.link_from_workload(wl)
+    o = egn.make_opts(gl_order=8, precision=egn.EGN_PREC_FP64)
+    ws = torch.empty(ln.workspace_size(o) - 256, dtype=torch.uint8, device="cuda")
+    with pytest.raises(egn.EgnError) as ei:
+        ln.nli_eta_device(o, ws)
+    assert ei.value.status == egn.EGN_E_CAPACITY
+
+
+def test_heterogeneous_spans_unsupported(egn, workloads):
+    wl = workloads.config_small(n_spans=2)
+    wl.spans[1].length_m = 60e3
+    ln = egn.link_from_workload(wl)
+    with pytest.raises(egn.EgnError) as ei:
+        ln.nli_eta(egn.make_opts())
+    assert ei.value.status == egn.EGN_E_UNSUPPORTED
+
+
+# --------------------------------------------------------------------------- FP32C path
+
+FP32C_DB = 1e-3      # small workloads
+TARGET_DB = 0.01     # the accuracy target at full size
+
+
+@pytest.mark.parametrize("terms", [0, 1])
+def test_fp32c_eta_small(egn, oracle_mod, workloads, terms):
+    wl = workloads.config_small(gl_order=64)
+    ln, pb = _pair(egn, oracle_mod, wl, terms=terms)
+    got, gp = ln.nli_eta(egn.make_opts(gl_order=64, precision=egn.EGN_PREC_FP32C, terms=terms))
+    want, wp = pb.eta()
+    assert np.max(_db(got, want)) < FP32C_DB, _db(got, want)
+    assert np.max(_db(gp, wp)) < FP32C_DB
+
+
+@pytest.mark.parametrize("gl", [1, 7, 13, 32])
+def test_fp32c_island_terms_all(egn, oracle_mod, workloads, gl):
+    wl = workloads.config_small(gl_order=gl, n_ch=3, n_spans=3)
+    ln, pb = _pair(egn, oracle_mod, wl, gl=gl)
+    isl = np.array([(n, *t) for n in range(3) for t in pb.islands(n)], dtype=np.int32)
+    got = ln.island_terms(egn.make_opts(gl_order=gl, precision=egn.EGN_PREC_FP32C), isl, all_terms=True)
+    want = np.array([pb.island_terms(*row, all_terms=True) for row in isl])
+    scale = np.abs(want[:, :1])  # |D| of the island bounds every term's rounding
+    err = np.abs(got - want)
+    assert np.all(err <= 3e-4 * np.abs(want) + 3e-5 * scale), np.max(err / (np.abs(want) + 1e-300))
+
+
+def test_fp32c_multispan_mixed_widths(egn, oracle_mod, workloads):
+    wl = workloads.config_small(n_ch=4, gl_order=12, n_spans=5)
+    base = wl.centre_hz[0]
+    wl.centre_hz = [base, base + 61e9, base + 140e9, base + 197e9]
+    wl.symbol_rate_baud = [40e9, 60e9, 32e9, 50e9]
+    ln, pb = _pair(egn, oracle_mod, wl, terms=0)
+    got, _ = ln.nli_eta(egn.make_opts(gl_order=12, precision=egn.EGN_PREC_FP32C, terms=0))
+    want, _ = pb.eta()
+    assert np.max(_db(got, want)) < FP32C_DB
+
+
+@pytest.mark.parametrize("dz", [1.0, 0.7, 7.0, 80.0])
+def test_fp32c_segment_counts(egn, oracle_mod, workloads, dz):
+    """K = 80, 115 (K mod 4 = 3), 12, 1 segments."""
+    wl = workloads.config_small(n_ch=3, gl_order=16, n_spans=2)
+    ln = egn.link_from_workload(wl)
+    got, _ = ln.nli_eta(egn.make_opts(gl_order=16, dz_km=dz, precision=egn.EGN_PREC_FP32C))
+    want, _ = oracle_mod.Problem(wl, dz_km=dz).eta()
+    assert np.max(_db(got, want)) < FP32C_DB, dz
+
+
+def test_fp32c_single_channel(egn, oracle_mod, workloads):
+    wl = workloads.config_small(n_ch=1, gl_order=32)
+    ln, pb = _pair(egn, oracle_mod, wl)
+    got, _ = ln.nli_eta(egn.make_opts(gl_order=32, precision=egn.EGN_PREC_FP32C))
+    want, _ = pb.eta()
+    assert np.max(_db(got, want)) < FP32C_DB
+
+
+def test_fp32c_config_cl_sampled_islands(egn, oracle_mod, workloads):
+    wl = workloads.config_cl()
+    ln, pb = _pair(egn, oracle_mod, wl)
+    plan = ln.plan_islands()
+    rng = np.random.default_rng(11)
+    pick = np.concatenate([rng.choice(len(plan), 40, replace=False),
+                           np.flatnonzero(plan[:, 1] == plan[:, 3])[:: 5000],
+                           np.flatnonzero(plan[:, 2] == plan[:, 3])[:: 5000],
+                           np.flatnonzero((plan[:, 1] == plan[:, 2]) & (plan[:, 2] == plan[:, 3]))[:: 40]])
+    isl = plan[pick]
+    got = ln.island_terms(egn.make_opts(gl_order=32, precision=egn.EGN_PREC_FP32C), isl)
+    want = np.array([pb.island_terms(*row) for row in isl])
+    scale = np.abs(want[:, :1])
+    err = np.abs(got - want)
+    assert np.all(err <= 1e-3 * np.abs(want) + 1e-4 * scale), np.max(err / (np.abs(want) + 1e-300))
+
+
+def test_config_cl_full_size_sampled_channels(egn, oracle_mod, workloads):
+    """The benchmarked launch (120 ch, 10 x 80 km, 32 x 32, EGN) for all channels on
+    the GPU in both precisions; the oracle evaluates two full channels (edge and
+    centre), which it can do one by one."""
+    wl = workloads.config_cl()
+    ln, pb = _pair(egn, oracle_mod, wl)
+    e64, _ = ln.nli_eta(egn.make_opts(gl_order=32, precision=egn.EGN_PREC_FP64))
+    e32, _ = ln.nli_eta(egn.make_opts(gl_order=32, precision=egn.EGN_PREC_FP32C))
+    assert np.max(_db(e32, e64)) < TARGET_DB
+    cois = [0, 59]
+    want, _ = pb.eta(cois)
+    assert np.allclose(e64[cois], want, rtol=1e-8, atol=0)
+    assert np.max(_db(e32[cois], want)) < TARGET_DB

@@ -55,8 +55,10 @@ def test_mutant_is_caught(name):
         subprocess.run(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp", "-ffp-contract=off",
                         "-o", so, c, "-lm"], check=True)
         env = dict(os.environ, EGN_ORACLE_LIB=so, EGN_RUN_MUTANTS="0")
-        pins = [os.path.join(ROOT, "tests", f) for f in sorted(os.listdir(os.path.join(ROOT, "tests")))
-                if f.startswith("test_oracle_") and f != "test_oracle_mutants.py"]
-        r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider"] + pins,
-                           cwd=ROOT, env=env, capture_output=True, text=True, timeout=1800)
+        # fast pins first; a pin that runs away on a mutant counts as failing (per-test timeout)
+        order = ["test_oracle_isrs.py", "test_oracle_mu.py", "test_oracle_quadrature.py", "test_oracle_islands.py",
+                 "test_oracle_egn.py"]
+        pins = [os.path.join(ROOT, "tests", f) for f in order]
+        r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider", "--timeout", "120"]
+                           + pins, cwd=ROOT, env=env, capture_output=True, text=True, timeout=1800)
         assert r.returncode != 0, f"mutant {name} survived the pins"
