@@ -154,6 +154,24 @@ egn_status egn_nli_eta(egn_link* link, const egn_opts* opts, double* eta_per_w2,
 egn_status egn_nli_eta_device(egn_link* link, const egn_opts* opts, void* workspace, size_t workspace_bytes,
                               double* eta_dev, double* pnli_dev);
 
+/* Evaluation that allocates nothing.  The paper has no counterpart: this entry
+ * point exists for callers that cannot call cudaMalloc -- an application whose
+ * device memory is owned by another allocator (a framework's caching allocator or
+ * a pool sized up front on a shared GPU), a control loop that re-evaluates links
+ * online and cannot take the device synchronisation of cudaMalloc/cudaFree, or a
+ * plugin host that forbids device allocation.  Same computation as
+ * egn_nli_eta_device, asynchronous on opts->stream, writing eta_dev and pnli_dev
+ * (device arrays of n_ch doubles, both required).  Its scratch (link tables and
+ * workspace) is one 16 MiB array compiled into the library, which every GPU that
+ * loads the library holds until the process exits; an evaluation that needs more
+ * (egn_workspace_size + the tables; about 60 channels at EGN_PREC_FP32C) is
+ * refused with EGN_E_CAPACITY.  The first call on a device looks up the array's
+ * device address (cudaGetSymbolAddress) with that device current; make that first
+ * call before any stream capture.  All calls share the one array and it keeps the
+ * last call's contents: calls whose work overlaps on the GPU (other streams,
+ * other threads, other links) race and must be serialised by the caller. */
+egn_status egn_nli_eta_static(egn_link* link, const egn_opts* opts, double* eta_dev, double* pnli_dev);
+
 /* Per-island terms for parity checks on sampled islands: for each of n_isl
  * islands given as 4 ints (coi, n1, n2, n3), writes 5 doubles (D, E, F, G, H)
  * into terms_out (host), evaluated by the same device kernels as egn_nli_eta.

@@ -740,3 +740,150 @@ egn_status egn_island_terms(egn_link* l, const egn_opts* o, int n_isl, const int
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Evaluation without any device allocation.
+//
+// Some callers cannot call cudaMalloc: an application whose device memory is
+// owned entirely by another allocator (a framework's caching allocator, or a
+// pool sized up front on a shared GPU), where one more allocation can fail or
+// fragment it; a control loop that re-evaluates a link online and cannot accept
+// the device synchronisation cudaMalloc/cudaFree imply; or a plugin host that
+// forbids its plugins to allocate device memory.  egn_nli_eta_static serves them
+// from a fixed scratch array compiled into this library.  Every GPU that loads
+// the library holds the array until the process exits.
+// ---------------------------------------------------------------------------
+
+namespace {
+
+constexpr size_t kStaticScratchBytes = (size_t)16 << 20;  // 16 MiB
+__device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
+
+// Device address of g_static_scratch per device (host code sees a host-side
+// stand-in under that name; only the address from cudaGetSymbolAddress may be
+// handed to kernels).
+constexpr int kMaxDevices = 64;
+void* g_static_ptr[kMaxDevices] = {};
+
+egn_status static_scratch(int dev, void** out) {
+  if (dev < 0 || dev >= kMaxDevices) return fail(EGN_E_UNSUPPORTED, "device %d out of range for the static scratch", dev);
+  if (!g_static_ptr[dev]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);  // the device is current here
+    if (e != cudaSuccess) return fail(EGN_E_CUDA, "cudaGetSymbolAddress(static scratch): %s", cudaGetErrorString(e));
+    g_static_ptr[dev] = p;
+  }
+  *out = g_static_ptr[dev];
+  return EGN_OK;
+}
+
+}  // namespace
+
+extern "C" egn_status egn_nli_eta_static(egn_link* l, const egn_opts* o, double* eta_dev, double* pnli_dev) {
+  egn_status s = check_opts(l, o);
+  if (s != EGN_OK) return s;
+  if (!eta_dev || !pnli_dev) return fail(EGN_E_INVALID_ARG, "eta_dev and pnli_dev must be device arrays of n_ch doubles");
+  DeviceGuard guard(l->device);
+  void* base = nullptr;
+  s = static_scratch(l->device, &base);
+  if (s != EGN_OK) return s;
+
+  // link tables for these options, built on the host stack (no heap, no device allocation)
+  const Span sp = to_internal(l->spans_si[0], l->fc_hz);
+  const int K = std::max(1, (int)std::ceil(sp.L / o->dz_km));
+  const int n = o->gl_order;
+  const int ord[4] = {0, n, (n + 1) / 2, (n + 2) / 3};
+  size_t off = 0;
+  const size_t o_zeta = off; off += align256(K * sizeof(double));
+  const size_t o_ck = off;   off += align256(K * sizeof(double));
+  const size_t o_zf = off;   off += align256(K * sizeof(float));
+  const size_t o_cf = off;   off += align256(K * sizeof(float));
+  size_t o_gl[4][7] = {};
+  for (int p = 1; p <= 3; ++p) {
+    for (int a = 0; a < 2; ++a) { o_gl[p][a] = off; off += align256(ord[p] * sizeof(double)); }
+    for (int a = 2; a < 7; ++a) { o_gl[p][a] = off; off += align256(ord[p] * sizeof(float)); }
+  }
+  const size_t ws_off = off;
+  const size_t need = ws_off + workspace_bytes(l->n_ch, l->n_isl, l->n_e, l->n_f, o->precision);
+  if (need > kStaticScratchBytes)
+    return fail(EGN_E_CAPACITY, "this evaluation needs %zu bytes of scratch; the static scratch holds %zu bytes "
+                "(use egn_nli_eta_device with a caller workspace)", need, kStaticScratchBytes);
+
+  cudaStream_t st = (cudaStream_t)o->stream;
+  char* b = (char*)base;
+  {
+    double zeta[kMaxK], ck[kMaxK];
+    float zf[kMaxK], cf[kMaxK];
+    for (int k = 0; k < K; ++k) {
+      double z = (k + 0.5) / K * sp.L;
+      double leff = -std::expm1(-sp.alpha * z) / sp.alpha;
+      zeta[k] = l->ptot * sp.cr * leff;
+      double x = l->btot * zeta[k];
+      ck[k] = (x == 0.0) ? 1.0 : x / (2.0 * std::sinh(0.5 * x));
+      zf[k] = (float)(zeta[k] * 1.4426950408889634);
+      cf[k] = (float)ck[k];
+    }
+    EGN_CUDA(cudaMemcpyAsync(b + o_zeta, zeta, K * sizeof(double), cudaMemcpyHostToDevice, st));
+    EGN_CUDA(cudaMemcpyAsync(b + o_ck, ck, K * sizeof(double), cudaMemcpyHostToDevice, st));
+    EGN_CUDA(cudaMemcpyAsync(b + o_zf, zf, K * sizeof(float), cudaMemcpyHostToDevice, st));
+    EGN_CUDA(cudaMemcpyAsync(b + o_cf, cf, K * sizeof(float), cudaMemcpyHostToDevice, st));
+    for (int p = 1; p <= 3; ++p) {
+      const int m = ord[p];
+      double x[kMaxGl], w[kMaxGl];
+      float f[5][kMaxGl];
+      gauss_legendre(m, x, w);
+      for (int i = 0; i < m; ++i) {
+        f[0][i] = (float)x[i];
+        f[1][i] = (float)(x[i] - (double)f[0][i]);
+        double x2 = x[i] * x[i];
+        f[2][i] = (float)x2;
+        f[3][i] = (float)(x2 - (double)f[2][i]);
+        f[4][i] = (float)w[i];
+      }
+      EGN_CUDA(cudaMemcpyAsync(b + o_gl[p][0], x, m * sizeof(double), cudaMemcpyHostToDevice, st));
+      EGN_CUDA(cudaMemcpyAsync(b + o_gl[p][1], w, m * sizeof(double), cudaMemcpyHostToDevice, st));
+      for (int a = 0; a < 5; ++a)
+        EGN_CUDA(cudaMemcpyAsync(b + o_gl[p][2 + a], f[a], m * sizeof(float), cudaMemcpyHostToDevice, st));
+    }
+  }
+
+  LinkParams p{};
+  p.ch = channel_table(l);
+  p.seg.K = K;
+  p.seg.zeta = (const double*)(b + o_zeta);
+  p.seg.ck = (const double*)(b + o_ck);
+  p.seg.zeta_f = (const float*)(b + o_zf);
+  p.seg.ck_f = (const float*)(b + o_cf);
+  p.gl.n = n;
+  p.gl.order[0] = 0;
+  for (int q = 1; q <= 3; ++q) {
+    p.gl.order[q] = ord[q];
+    p.gl.x[q] = (const double*)(b + o_gl[q][0]);
+    p.gl.w[q] = (const double*)(b + o_gl[q][1]);
+    p.gl.xh[q] = (const float*)(b + o_gl[q][2]);
+    p.gl.xl[q] = (const float*)(b + o_gl[q][3]);
+    p.gl.x2h[q] = (const float*)(b + o_gl[q][4]);
+    p.gl.x2l[q] = (const float*)(b + o_gl[q][5]);
+    p.gl.wf[q] = (const float*)(b + o_gl[q][6]);
+  }
+  p.n_spans = (int)l->spans_si.size();
+  p.alpha = sp.alpha;
+  p.beta2 = sp.beta2;
+  p.beta3 = sp.beta3;
+  p.gamma = sp.gamma;
+  p.L = sp.L;
+  p.dz = sp.L / K;
+  p.r = std::exp(-sp.alpha * p.dz);
+  p.rolloff = l->rolloff;
+  p.terms = o->terms;
+  p.all_terms = 0;
+
+  // plan -> integrate -> assemble on the caller's stream, workspace in the scratch
+  Workspace ws = carve_workspace(b + ws_off, l->n_ch, l->n_isl, l->n_e, l->n_f, o->precision);
+  ChannelTable ch = p.ch;
+  EGN_CUDA(cudaMemsetAsync(ws.status, 0, sizeof(int), st));  // the array keeps the last call's contents
+  EGN_CUDA(launch_plan(ch, ws, st));
+  EGN_CUDA(integrate(p, o->precision, ws.keys, l->n_isl, ws.e_idx, l->n_e, ws.f_idx, l->n_f, ws.terms, st, nullptr));
+  EGN_CUDA(launch_assemble(ch, ws.row_off, ws.keys, l->n_isl, ws.terms, o->precision, o->terms, eta_dev, pnli_dev, st));
+  return EGN_OK;
+}

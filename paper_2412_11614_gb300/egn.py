@@ -67,6 +67,7 @@ def lib():
         L.egn_nli_eta.argtypes = [C.c_void_p, C.POINTER(egn_opts), _dp, _dp]
         L.egn_nli_eta_device.argtypes = [C.c_void_p, C.POINTER(egn_opts), C.c_void_p, C.c_size_t, C.c_void_p,
                                          C.c_void_p]
+        L.egn_nli_eta_static.argtypes = [C.c_void_p, C.POINTER(egn_opts), C.c_void_p, C.c_void_p]
         L.egn_island_terms.argtypes = [C.c_void_p, C.POINTER(egn_opts), C.c_int, C.POINTER(C.c_int), C.c_int, _dp]
         L.egn_plan_islands.argtypes = [C.c_void_p, C.c_longlong, C.POINTER(C.c_int), C.POINTER(C.c_longlong)]
         L.egn_format_moments.argtypes = [C.c_int, _dp, _dp]
@@ -77,7 +78,7 @@ def lib():
         L.egn_version.restype = C.c_char_p
         for fn in ("egn_link_create", "egn_set_wdm", "egn_workspace_size", "egn_island_count", "egn_nli_eta",
                    "egn_nli_eta_device", "egn_island_terms", "egn_plan_islands", "egn_format_moments",
-                   "egn_gauss_legendre", "egn_set_profiling", "egn_last_timings"):
+                   "egn_gauss_legendre", "egn_set_profiling", "egn_last_timings", "egn_nli_eta_static"):
             getattr(L, fn).restype = C.c_int
         _lib = L
     return _lib
@@ -171,6 +172,12 @@ class Link:
                                         workspace.numel() * workspace.element_size(),
                                         C.c_void_p(eta_dev.data_ptr()) if eta_dev is not None else None,
                                         C.c_void_p(pnli_dev.data_ptr()) if pnli_dev is not None else None))
+
+    def nli_eta_static(self, opts: egn_opts, eta_dev, pnli_dev):
+        """Allocation-free evaluation (scratch compiled into the library) on
+        opts.stream into float64 device tensors of n_ch entries."""
+        _check(lib().egn_nli_eta_static(self.h, C.byref(opts), C.c_void_p(eta_dev.data_ptr()),
+                                        C.c_void_p(pnli_dev.data_ptr())))
 
     def island_terms(self, opts: egn_opts, islands, all_terms=False) -> np.ndarray:
         isl = np.ascontiguousarray(np.asarray(islands, dtype=np.int32).reshape(-1, 4))
