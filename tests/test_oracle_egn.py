@@ -132,3 +132,56 @@ def test_segment_error_does_not_accumulate_over_spans(oracle_mod, workloads):
     ref, _ = oracle_mod.Problem(wl, mu_form=2, int_tol=1e-8).eta(cois)
     seg, _ = oracle_mod.Problem(wl, mu_form=0).eta(cois)
     assert np.mean(np.abs(10 * np.log10(seg / ref))) < 1e-3
+
+
+def test_interferer_format_enters_xci_corrections(oracle_mod, workloads):
+    """Two channels narrower than 2/3 of their spacing (only l = 0 islands), no
+    ISRS: the COI's own format changes only its SCI island, so the change of P_NLI
+    with the COI's Phi/Psi equals that of the COI alone; the interferer's format
+    enters only through the XCI islands where it appears twice (its Phi)."""
+    def problem(n_ch, phi, psi):
+        wl = workloads.config_small(n_ch=2, gl_order=16)
+        wl.centre_hz = wl.centre_hz[:n_ch]  # the COI sits at the same frequency in both combs
+        wl.symbol_rate_baud = [40e9] * n_ch
+        wl.launch_power_w = wl.launch_power_w[:n_ch]
+        wl.formats = wl.formats[:n_ch]
+        wl.spans[0].cr_per_w_km_thz = 0.0
+        return oracle_mod.Problem(wl, gl_order=16, phi=phi, psi=psi)
+    _, alone0 = problem(1, [0.0], [0.0]).eta([0])
+    _, alone1 = problem(1, [-1.0], [4.0]).eta([0])
+    _, both0 = problem(2, [0.0, 0.0], [0.0, 0.0]).eta([0])
+    _, coi1 = problem(2, [-1.0, 0.0], [4.0, 0.0]).eta([0])
+    _, int1 = problem(2, [0.0, -1.0], [0.0, 4.0]).eta([0])
+    assert coi1[0] - both0[0] == pytest.approx(alone1[0] - alone0[0], rel=1e-10)
+    # interferer format: the (B, A, B) E-island and (A, B, B) F-island of COI A
+    pb = problem(2, [0.0, -1.0], [0.0, 4.0])
+    t_e = pb.island_terms(0, 1, 0, 1, all_terms=True)[1]
+    t_f = pb.island_terms(0, 0, 1, 1, all_terms=True)[2]
+    P = 1e-3
+    assert int1[0] - both0[0] == pytest.approx(-1.0 * P ** 3 * (t_e + t_f), rel=1e-10)
+
+
+def test_each_correction_uses_its_repeated_channel(oracle_mod, workloads):
+    """d P_NLI / d Phi_m (finite difference of the oracle's eta) equals the sum of
+    the correction terms of the islands in which channel m appears twice: E where
+    n1 = n3 = m, F where n2 = n3 = m, G where n1 = n2 = m."""
+    wl = workloads.config_small(n_ch=5, gl_order=8)
+    base = [0.0] * 5
+    p0 = oracle_mod.Problem(wl, gl_order=8, phi=base, psi=base)
+    _, pn0 = p0.eta([2])
+    for m in range(5):
+        phi = list(base)
+        phi[m] = 1.0
+        pb = oracle_mod.Problem(wl, gl_order=8, phi=phi, psi=base)
+        _, pn1 = pb.eta([2])
+        want = 0.0
+        for n1, n2, n3 in pb.islands(2):
+            t = pb.island_terms(2, n1, n2, n3, all_terms=True)
+            w = wl.launch_power_w[n1] * wl.launch_power_w[n2] * wl.launch_power_w[n3]
+            if n1 == n3 == m:
+                want += w * t[1]
+            if n2 == n3 == m:
+                want += w * t[2]
+            if n1 == n2 == m:
+                want += w * t[3]
+        assert pn1[0] - pn0[0] == pytest.approx(want, rel=1e-9), m

@@ -170,3 +170,74 @@ def test_quadrature_order_convergence(oracle_mod, workloads):
     xci = [oracle_mod.Problem(wl, gl_order=g).island_terms(0, 0, 4, 4)[0] for g in (32, 256, 384)]
     assert xci[2] == pytest.approx(xci[1], rel=1e-5)
     assert abs(xci[0] / xci[2] - 1) > 0.2
+
+
+def test_d_rate_normalisation_split_channel(oracle_mod, workloads):
+    """D carries R_n / (R1 R2 R3) so that P_i / R_i is each channel's PSD: with
+    rectangular spectra, no dispersion and no ISRS, replacing an interferer of rate
+    2R and power 2P by two adjacent channels of rate R and power P (the same PSD)
+    leaves the COI's GN eta unchanged."""
+    def comb(split):
+        wl = workloads.config_small(n_ch=2, gl_order=8)
+        for s in wl.spans:
+            s.D_ps_nm_km = 0.0
+            s.S_ps_nm2_km = 0.0
+            s.cr_per_w_km_thz = 0.0
+        wl.rolloff = 0.0
+        c = 1.93e14
+        R = 40e9
+        if split:
+            wl.centre_hz = [c, c + 2.5 * R, c + 3.5 * R]
+            wl.symbol_rate_baud = [R, R, R]
+            wl.launch_power_w = [1e-3, 1e-3, 1e-3]
+            wl.formats = ["GAUSS"] * 3
+        else:
+            wl.centre_hz = [c, c + 3.0 * R]
+            wl.symbol_rate_baud = [R, 2 * R]
+            wl.launch_power_w = [1e-3, 2e-3]
+            wl.formats = ["GAUSS"] * 2
+        return wl
+    e1, p1 = oracle_mod.Problem(comb(False), gl_order=8, terms=0).eta([0])
+    e2, p2 = oracle_mod.Problem(comb(True), gl_order=8, terms=0).eta([0])
+    assert p1[0] == pytest.approx(p2[0], rel=1e-12)
+
+
+def test_dispersionless_mixed_widths_kinks(oracle_mod, workloads):
+    """Island with three different widths and d != 0 whose inner limits switch
+    inside the outer range: with Upsilon constant each term is a polygon area or the
+    integral of a squared piecewise-linear inner length, integrated here by scipy
+    from the supports alone (no panels)."""
+    wl = workloads.config_small(n_ch=4, gl_order=8)
+    for s in wl.spans:
+        s.D_ps_nm_km = 0.0
+        s.S_ps_nm2_km = 0.0
+        s.cr_per_w_km_thz = 0.0
+    wl.rolloff = 0.0
+    c = 1.93e14
+    wl.centre_hz = [c - 100e9, c, c + 100e9, c + 190e9]
+    wl.symbol_rate_baud = [40e9, 60e9, 30e9, 50e9]
+    wl.formats = ["GAUSS"] * 4
+    pb = oracle_mod.Problem(wl, gl_order=8)
+    Y = pb.spans[0].gamma * oracle_mod.leff(pb.spans[0].alpha, pb.spans[0].L)
+    n, n1, n2, n3 = 0, 1, 2, 3
+    W1, W2, W3 = pb.R[n1], pb.R[n2], pb.R[n3]
+    d = (pb.nu[n1] - pb.nu[n]) + (pb.nu[n2] - pb.nu[n3])
+    assert abs(d - 0.010) < 1e-12
+
+    def length(lo1, hi1, lo2, hi2):
+        return max(0.0, min(hi1, hi2) - max(lo1, lo2))
+
+    # inner lengths of the three evaluation orders, from the supports
+    lw = lambda w: length(-W1 / 2, W1 / 2, w - d - W2 / 2, w - d + W2 / 2)        # inner u at fixed w
+    lv = lambda v: length(-W1 / 2, W1 / 2, -W3 / 2 - v - d, W3 / 2 - v - d)      # inner u at fixed v
+    lu = lambda u: length(-W2 / 2, W2 / 2, -W3 / 2 - u - d, W3 / 2 - u - d)      # inner v at fixed u
+    q = lambda f, a, b: integrate.quad(f, a, b, limit=200, epsabs=0, epsrel=1e-13)[0]
+    area = q(lw, -W3 / 2, W3 / 2)
+    e_int = q(lambda v: lv(v) ** 2, -W2 / 2, W2 / 2)
+    f_int = q(lambda u: lu(u) ** 2, -W1 / 2, W1 / 2)
+    g_int = q(lambda w: lw(w) ** 2, -W3 / 2, W3 / 2)
+    R = pb.R[n]
+    want = np.array([16 / 27 * R / (W1 * W2 * W3) * area, 16 / 27 / R ** 3 * e_int, 32 / 81 / R ** 3 * f_int,
+                     16 / 81 / R ** 3 * g_int, 16 / 81 / R ** 4 * area ** 2]) * Y * Y
+    got = pb.island_terms(n, n1, n2, n3, all_terms=True)
+    assert np.allclose(got, want, rtol=1e-10, atol=0), (got / want - 1)
