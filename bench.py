@@ -238,7 +238,7 @@ def main():
     ln = egn.link_from_workload(wl)
     opts = egn.make_opts(gl_order=wl.gl_order, dz_km=wl.dz_km, precision=prec, terms=egn.EGN_TERMS_EGN,
                          stream=stream.cuda_stream)
-    n_isl, _, n_e, n_f = ln.island_count()
+    n_isl, _, n_half, n_e, n_f = ln.island_count()
     ws = torch.empty(ln.workspace_size(opts), dtype=torch.uint8, device="cuda")
     eta = torch.empty(n_ch, dtype=torch.float64, device="cuda")
     pnli = torch.empty(n_ch, dtype=torch.float64, device="cuda")
@@ -288,7 +288,7 @@ def main():
     # dominant kernel: the D/G/H integrator pass
     dgh_ms = statistics.mean(s["integrate_dgh"] for s in stage)
     n = wl.gl_order
-    points = n_isl * n * n  # every island of this comb has 1 or 2 outer panels: n x n points
+    points = n_half * n * n  # islands evaluated (n1 <= n2); each has 1 or 2 outer panels: n x n points
     K = math.ceil(80.0 / wl.dz_km)
     flops = points * flops_per_point(args.precision, K)
     clk = clocks.get("sm_max_mhz") or 2070.0
@@ -344,7 +344,7 @@ def main():
             "vs_baseline": None, "dtype": "f32" if args.precision == "fp32c" else "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD if n_ch == 120 else WORKLOAD.replace("120ch", f"{n_ch}ch"),
                        "precision": args.precision, "n_ch": n_ch, "islands": n_isl,
-                       "e_islands": n_e, "f_islands": n_f, "points_per_step": points, "segments_K": K,
+                       "islands_evaluated": n_half, "e_islands": n_e, "f_islands": n_f, "points_per_step": points, "segments_K": K,
                        "l2": "flushed between steps (256 MB write outside the per-step events)",
                        "parallelism": f"replicas x{world}"},
             "gpu_launches": 7 * args.steps,

@@ -136,9 +136,12 @@ egn_status egn_set_wdm(egn_link* link, int n_ch, const double* centre_hz, const 
 egn_status egn_workspace_size(const egn_link* link, const egn_opts* opts, size_t* bytes);
 
 /* Number of islands of the current comb: total, and per COI if per_coi != NULL
- * (n_ch entries).  Optional E/F list sizes (islands with n1 == n3, n2 == n3). */
-egn_status egn_island_count(const egn_link* link, long long* total, long long* per_coi, long long* n_e,
-                            long long* n_f);
+ * (n_ch entries).  Every island (n1, n2, n3) has a mirror (n2, n1, n3) under
+ * f1 <-> f2 with the same D, so the integrator evaluates only the islands with
+ * n1 <= n2 (*n_half); *n_e and *n_f are the sizes of the E list (n1 == n3,
+ * n1 <= n2) and of the F list (n2 == n3, n1 < n2).  Any output may be NULL. */
+egn_status egn_island_count(const egn_link* link, long long* total, long long* per_coi, long long* n_half,
+                            long long* n_e, long long* n_f);
 
 /* eta_n [1/W^2] and P_NLI,n [W] for every channel into caller host arrays of
  * n_ch doubles (either may be NULL).  Synchronous: plans the islands on the

@@ -69,7 +69,7 @@ struct egn_link {
   double fc_hz = 0, btot = 0, ptot = 0, rolloff = 0;
   std::vector<double> nu, R, W, P, phi, psi;
   bool mixed_rates = false, any_corr = false;
-  long long n_isl = 0, n_e = 0, n_f = 0;
+  egn::PlanCounts cnt{};
   std::vector<long long> per_coi;
   int device = -1;
   DevBuf d_ch;  // 6 arrays of n_ch doubles
@@ -141,47 +141,51 @@ void gauss_legendre(int n, double* x, double* w) {
   if (n % 2 == 1) x[n / 2] = 0.0;
 }
 
-size_t workspace_bytes(int n_ch, long long n_isl, long long n_e, long long n_f, int precision) {
+size_t workspace_bytes(int n_ch, const PlanCounts& c, int precision) {
   size_t n_rows = (size_t)n_ch * n_ch;
   size_t tsz = precision == EGN_PREC_FP64 ? sizeof(double) : sizeof(float);
   size_t b = 0;
-  b += align256((size_t)n_isl * sizeof(uint64_t));
-  b += align256((size_t)n_e * sizeof(uint32_t));
-  b += align256((size_t)n_f * sizeof(uint32_t));
-  b += align256(3 * n_rows * sizeof(uint32_t));
-  b += align256(3 * (n_rows + 1) * sizeof(uint32_t));
-  b += align256(5 * (size_t)n_isl * tsz);
+  b += align256((size_t)c.n_isl * sizeof(uint64_t));
+  b += align256((size_t)c.n_half * sizeof(uint32_t));
+  b += align256((size_t)c.n_e * sizeof(uint32_t));
+  b += align256((size_t)c.n_f * sizeof(uint32_t));
+  b += align256(4 * n_rows * sizeof(uint32_t));
+  b += align256(4 * (n_rows + 1) * sizeof(uint32_t));
+  b += align256(5 * (size_t)c.n_isl * tsz);
   b += align256((size_t)n_ch * sizeof(double));
   b += align256((size_t)n_ch * sizeof(double));
   b += align256(sizeof(int));
   return b;
 }
 
-Workspace carve_workspace(void* base, int n_ch, long long n_isl, long long n_e, long long n_f, int precision) {
+Workspace carve_workspace(void* base, int n_ch, const PlanCounts& c, int precision) {
   size_t n_rows = (size_t)n_ch * n_ch;
   size_t tsz = precision == EGN_PREC_FP64 ? sizeof(double) : sizeof(float);
   char* p = (char*)base;
   Workspace w{};
   w.keys = (uint64_t*)p;
-  p += align256((size_t)n_isl * sizeof(uint64_t));
+  p += align256((size_t)c.n_isl * sizeof(uint64_t));
+  w.h_idx = (uint32_t*)p;
+  p += align256((size_t)c.n_half * sizeof(uint32_t));
   w.e_idx = (uint32_t*)p;
-  p += align256((size_t)n_e * sizeof(uint32_t));
+  p += align256((size_t)c.n_e * sizeof(uint32_t));
   w.f_idx = (uint32_t*)p;
-  p += align256((size_t)n_f * sizeof(uint32_t));
+  p += align256((size_t)c.n_f * sizeof(uint32_t));
   w.row_cnt = (uint32_t*)p;
-  p += align256(3 * n_rows * sizeof(uint32_t));
+  p += align256(4 * n_rows * sizeof(uint32_t));
   w.row_off = (uint32_t*)p;
-  p += align256(3 * (n_rows + 1) * sizeof(uint32_t));
+  p += align256(4 * (n_rows + 1) * sizeof(uint32_t));
   w.terms = (void*)p;
-  p += align256(5 * (size_t)n_isl * tsz);
+  p += align256(5 * (size_t)c.n_isl * tsz);
   w.out_eta = (double*)p;
   p += align256((size_t)n_ch * sizeof(double));
   w.out_pnli = (double*)p;
   p += align256((size_t)n_ch * sizeof(double));
   w.status = (int*)p;
-  w.cap_isl = n_isl;
-  w.cap_e = n_e;
-  w.cap_f = n_f;
+  w.cap_isl = c.n_isl;
+  w.cap_half = c.n_half;
+  w.cap_e = c.n_e;
+  w.cap_f = c.n_f;
   return w;
 }
 
@@ -362,12 +366,12 @@ LinkParams link_params(const egn_link* l, const egn_opts* o, int all_terms) {
   return p;
 }
 
-// Integrator passes: D/G/H over all islands, then E and F over their lists
-// (or over every island when all_terms is set).  ev, if given, is recorded after
-// each pass.
+// Integrator passes: D/G/H over the half list (or every island of `keys` when
+// h_idx is null), then E and F over their lists (or over every island when
+// all_terms is set).  ev, if given, is recorded after each pass.
 cudaError_t integrate(const LinkParams& p, int precision, const uint64_t* keys, long long n_isl,
-                      const uint32_t* e_idx, long long n_e, const uint32_t* f_idx, long long n_f, void* terms,
-                      cudaStream_t st, cudaEvent_t* ev) {
+                      const uint32_t* h_idx, long long n_half, const uint32_t* e_idx, long long n_e,
+                      const uint32_t* f_idx, long long n_f, void* terms, cudaStream_t st, cudaEvent_t* ev) {
   auto pass = [&](int ord, const uint32_t* list, long long n) {
     return precision == EGN_PREC_FP64 ? launch_fp64_pass(ord, p, keys, list, n, (double*)terms, n_isl, st)
                                       : launch_fp32c_pass(ord, p, keys, list, n, (float*)terms, n_isl, st);
@@ -377,7 +381,7 @@ cudaError_t integrate(const LinkParams& p, int precision, const uint64_t* keys, 
   const uint32_t* fl = p.all_terms ? nullptr : f_idx;
   long long ne = p.all_terms ? n_isl : (corr ? n_e : 0);
   long long nf = p.all_terms ? n_isl : (corr ? n_f : 0);
-  cudaError_t e = pass(0, nullptr, n_isl);
+  cudaError_t e = pass(0, h_idx, h_idx ? n_half : n_isl);
   if (e == cudaSuccess && ev) e = cudaEventRecord(ev[0], st);
   if (e == cudaSuccess) e = pass(1, el, ne);
   if (e == cudaSuccess && ev) e = cudaEventRecord(ev[1], st);
@@ -385,6 +389,9 @@ cudaError_t integrate(const LinkParams& p, int precision, const uint64_t* keys, 
   if (e == cudaSuccess && ev) e = cudaEventRecord(ev[2], st);
   return e;
 }
+
+// Per-row offsets of the half list inside the planner's offset arrays.
+const uint32_t* half_offsets(const Workspace& ws, int n_ch) { return ws.row_off + ((size_t)n_ch * n_ch + 1); }
 
 // The whole step on one stream: plan -> integrate -> assemble.
 egn_status run_step(egn_link* l, const egn_opts* o, const Workspace& ws, double* eta, double* pnli) {
@@ -402,9 +409,10 @@ egn_status run_step(egn_link* l, const egn_opts* o, const Workspace& ws, double*
   EGN_CUDA(launch_plan(ch, ws, st));
   if (ev) EGN_CUDA(cudaEventRecord(ev[1], st));
   LinkParams p = link_params(l, o, 0);
-  EGN_CUDA(integrate(p, o->precision, ws.keys, l->n_isl, ws.e_idx, l->n_e, ws.f_idx, l->n_f, ws.terms, st,
-                     ev ? ev + 2 : nullptr));
-  EGN_CUDA(launch_assemble(ch, ws.row_off, ws.keys, l->n_isl, ws.terms, o->precision, o->terms, eta, pnli, st));
+  EGN_CUDA(integrate(p, o->precision, ws.keys, l->cnt.n_isl, ws.h_idx, l->cnt.n_half, ws.e_idx, l->cnt.n_e,
+                     ws.f_idx, l->cnt.n_f, ws.terms, st, ev ? ev + 2 : nullptr));
+  EGN_CUDA(launch_assemble(ch, half_offsets(ws, l->n_ch), ws.keys, ws.h_idx, l->cnt.n_isl, ws.terms, o->precision,
+                           o->terms, eta, pnli, st));
   if (ev) {
     EGN_CUDA(cudaEventRecord(ev[5], st));
     l->prof_valid = true;
@@ -555,7 +563,7 @@ egn_status egn_set_wdm(egn_link* l, int n_ch, const double* centre_hz, const dou
   // count islands on the device
   l->n_ch = n_ch;
   size_t n_rows = (size_t)n_ch * n_ch;
-  size_t cnt_b = align256(3 * n_rows * sizeof(uint32_t)), off_b = align256(3 * (n_rows + 1) * sizeof(uint32_t));
+  size_t cnt_b = align256(4 * n_rows * sizeof(uint32_t)), off_b = align256(4 * (n_rows + 1) * sizeof(uint32_t));
   DevBuf tmp;
   cudaError_t e = tmp.ensure(cnt_b + off_b);
   if (e != cudaSuccess) { l->n_ch = 0; return fail(EGN_E_NOMEM, "cudaMalloc: %s", cudaGetErrorString(e)); }
@@ -563,13 +571,14 @@ egn_status egn_set_wdm(egn_link* l, int n_ch, const double* centre_hz, const dou
   w.row_cnt = (uint32_t*)tmp.p;
   w.row_off = (uint32_t*)((char*)tmp.p + cnt_b);
   e = launch_plan_count(channel_table(l), w, 0);
-  std::vector<uint32_t> off(3 * (n_rows + 1));
+  std::vector<uint32_t> off(4 * (n_rows + 1));
   if (e == cudaSuccess) e = cudaMemcpy(off.data(), w.row_off, off.size() * sizeof(uint32_t), cudaMemcpyDeviceToHost);
   tmp.release();
   if (e != cudaSuccess) { l->n_ch = 0; return fail(EGN_E_CUDA, "island count: %s", cudaGetErrorString(e)); }
-  l->n_isl = off[n_rows];
-  l->n_e = off[(n_rows + 1) + n_rows];
-  l->n_f = off[2 * (n_rows + 1) + n_rows];
+  l->cnt.n_isl = off[n_rows];
+  l->cnt.n_half = off[(n_rows + 1) + n_rows];
+  l->cnt.n_e = off[2 * (n_rows + 1) + n_rows];
+  l->cnt.n_f = off[3 * (n_rows + 1) + n_rows];
   l->per_coi.resize(n_ch);
   for (int c = 0; c < n_ch; ++c) l->per_coi[c] = (long long)off[(size_t)(c + 1) * n_ch] - off[(size_t)c * n_ch];
   // pinned staging for host outputs
@@ -579,12 +588,14 @@ egn_status egn_set_wdm(egn_link* l, int n_ch, const double* centre_hz, const dou
   return EGN_OK;
 }
 
-egn_status egn_island_count(const egn_link* l, long long* total, long long* per_coi, long long* n_e, long long* n_f) {
+egn_status egn_island_count(const egn_link* l, long long* total, long long* per_coi, long long* n_half,
+                            long long* n_e, long long* n_f) {
   if (!l) return fail(EGN_E_INVALID_ARG, "null link");
   if (l->n_ch <= 0) return fail(EGN_E_STATE, "egn_set_wdm has not been called");
-  if (total) *total = l->n_isl;
-  if (n_e) *n_e = l->n_e;
-  if (n_f) *n_f = l->n_f;
+  if (total) *total = l->cnt.n_isl;
+  if (n_half) *n_half = l->cnt.n_half;
+  if (n_e) *n_e = l->cnt.n_e;
+  if (n_f) *n_f = l->cnt.n_f;
   if (per_coi) std::copy(l->per_coi.begin(), l->per_coi.end(), per_coi);
   return EGN_OK;
 }
@@ -593,7 +604,7 @@ egn_status egn_workspace_size(const egn_link* l, const egn_opts* o, size_t* byte
   if (!bytes) return fail(EGN_E_INVALID_ARG, "null output");
   egn_status s = check_opts(l, o);
   if (s != EGN_OK) return s;
-  *bytes = workspace_bytes(l->n_ch, l->n_isl, l->n_e, l->n_f, o->precision);
+  *bytes = workspace_bytes(l->n_ch, l->cnt, o->precision);
   return EGN_OK;
 }
 
@@ -602,12 +613,12 @@ egn_status egn_nli_eta_device(egn_link* l, const egn_opts* o, void* workspace, s
   egn_status s = check_opts(l, o);
   if (s != EGN_OK) return s;
   if (!workspace || ((uintptr_t)workspace & 255)) return fail(EGN_E_INVALID_ARG, "workspace must be 256-byte aligned");
-  size_t need = workspace_bytes(l->n_ch, l->n_isl, l->n_e, l->n_f, o->precision);
+  size_t need = workspace_bytes(l->n_ch, l->cnt, o->precision);
   if (workspace_bytes_ < need) return fail(EGN_E_CAPACITY, "workspace %zu bytes < %zu needed", workspace_bytes_, need);
   DeviceGuard g(l->device);
   s = ensure_tables(l, o);
   if (s != EGN_OK) return s;
-  Workspace ws = carve_workspace(workspace, l->n_ch, l->n_isl, l->n_e, l->n_f, o->precision);
+  Workspace ws = carve_workspace(workspace, l->n_ch, l->cnt, o->precision);
   return run_step(l, o, ws, eta_dev ? eta_dev : ws.out_eta, pnli_dev ? pnli_dev : ws.out_pnli);
 }
 
@@ -615,12 +626,12 @@ egn_status egn_nli_eta(egn_link* l, const egn_opts* o, double* eta, double* pnli
   egn_status s = check_opts(l, o);
   if (s != EGN_OK) return s;
   DeviceGuard g(l->device);
-  size_t need = workspace_bytes(l->n_ch, l->n_isl, l->n_e, l->n_f, o->precision);
+  size_t need = workspace_bytes(l->n_ch, l->cnt, o->precision);
   cudaError_t e = l->ws.ensure(need);
   if (e != cudaSuccess) return fail(EGN_E_NOMEM, "workspace cudaMalloc(%zu): %s", need, cudaGetErrorString(e));
   s = egn_nli_eta_device(l, o, l->ws.p, l->ws.bytes, nullptr, nullptr);
   if (s != EGN_OK) return s;
-  Workspace ws = carve_workspace(l->ws.p, l->n_ch, l->n_isl, l->n_e, l->n_f, o->precision);
+  Workspace ws = carve_workspace(l->ws.p, l->n_ch, l->cnt, o->precision);
   cudaStream_t st = (cudaStream_t)o->stream;
   int n = l->n_ch;
   EGN_CUDA(cudaMemcpyAsync(l->h_stage, ws.out_eta, n * sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -667,16 +678,16 @@ egn_status egn_plan_islands(egn_link* l, long long max, int* out, long long* cou
   if (!l || !count) return fail(EGN_E_INVALID_ARG, "null argument");
   if (l->n_ch <= 0) return fail(EGN_E_STATE, "egn_set_wdm has not been called");
   DeviceGuard g(l->device);
-  size_t need = workspace_bytes(l->n_ch, l->n_isl, l->n_e, l->n_f, EGN_PREC_FP64);
+  size_t need = workspace_bytes(l->n_ch, l->cnt, EGN_PREC_FP64);
   cudaError_t e = l->ws.ensure(need);
   if (e != cudaSuccess) return fail(EGN_E_NOMEM, "workspace cudaMalloc(%zu): %s", need, cudaGetErrorString(e));
-  Workspace ws = carve_workspace(l->ws.p, l->n_ch, l->n_isl, l->n_e, l->n_f, EGN_PREC_FP64);
+  Workspace ws = carve_workspace(l->ws.p, l->n_ch, l->cnt, EGN_PREC_FP64);
   EGN_CUDA(cudaMemset(ws.status, 0, sizeof(int)));
   EGN_CUDA(launch_plan(channel_table(l), ws, 0));
-  std::vector<uint64_t> keys(l->n_isl);
+  std::vector<uint64_t> keys(l->cnt.n_isl);
   EGN_CUDA(cudaMemcpy(keys.data(), ws.keys, keys.size() * sizeof(uint64_t), cudaMemcpyDeviceToHost));
-  *count = l->n_isl;
-  long long m = std::min<long long>(max, l->n_isl);
+  *count = l->cnt.n_isl;
+  long long m = std::min<long long>(max, l->cnt.n_isl);
   for (long long i = 0; out && i < m; ++i) {
     int c, a, b, d;
     unpack_key(keys[i], c, a, b, d);
@@ -724,8 +735,8 @@ egn_status egn_island_terms(egn_link* l, const egn_opts* o, int n_isl, const int
     if (!f_list.empty() && (e = cudaMemcpy(d_f, f_list.data(), f_list.size() * 4, cudaMemcpyHostToDevice)) != cudaSuccess) break;
     if ((e = cudaMemset(d_t, 0, 5 * (size_t)n_isl * tsz)) != cudaSuccess) break;
     LinkParams prm = link_params(l, o, all_terms ? 1 : 0);
-    e = integrate(prm, o->precision, d_keys, n_isl, d_e, (long long)e_list.size(), d_f, (long long)f_list.size(), d_t,
-                  0, nullptr);
+    e = integrate(prm, o->precision, d_keys, n_isl, nullptr, n_isl, d_e, (long long)e_list.size(), d_f,
+                  (long long)f_list.size(), d_t, 0, nullptr);
     if (e != cudaSuccess) break;
     if ((e = cudaDeviceSynchronize()) != cudaSuccess) break;
     std::vector<char> h(5 * (size_t)n_isl * tsz);
@@ -804,7 +815,7 @@ extern "C" egn_status egn_nli_eta_static(egn_link* l, const egn_opts* o, double*
     for (int a = 2; a < 7; ++a) { o_gl[p][a] = off; off += align256(ord[p] * sizeof(float)); }
   }
   const size_t ws_off = off;
-  const size_t need = ws_off + workspace_bytes(l->n_ch, l->n_isl, l->n_e, l->n_f, o->precision);
+  const size_t need = ws_off + workspace_bytes(l->n_ch, l->cnt, o->precision);
   if (need > kStaticScratchBytes)
     return fail(EGN_E_CAPACITY, "this evaluation needs %zu bytes of scratch; the static scratch holds %zu bytes "
                 "(use egn_nli_eta_device with a caller workspace)", need, kStaticScratchBytes);
@@ -879,11 +890,13 @@ extern "C" egn_status egn_nli_eta_static(egn_link* l, const egn_opts* o, double*
   p.all_terms = 0;
 
   // plan -> integrate -> assemble on the caller's stream, workspace in the scratch
-  Workspace ws = carve_workspace(b + ws_off, l->n_ch, l->n_isl, l->n_e, l->n_f, o->precision);
+  Workspace ws = carve_workspace(b + ws_off, l->n_ch, l->cnt, o->precision);
   ChannelTable ch = p.ch;
   EGN_CUDA(cudaMemsetAsync(ws.status, 0, sizeof(int), st));  // the array keeps the last call's contents
   EGN_CUDA(launch_plan(ch, ws, st));
-  EGN_CUDA(integrate(p, o->precision, ws.keys, l->n_isl, ws.e_idx, l->n_e, ws.f_idx, l->n_f, ws.terms, st, nullptr));
-  EGN_CUDA(launch_assemble(ch, ws.row_off, ws.keys, l->n_isl, ws.terms, o->precision, o->terms, eta_dev, pnli_dev, st));
+  EGN_CUDA(integrate(p, o->precision, ws.keys, l->cnt.n_isl, ws.h_idx, l->cnt.n_half, ws.e_idx, l->cnt.n_e, ws.f_idx,
+                     l->cnt.n_f, ws.terms, st, nullptr));
+  EGN_CUDA(launch_assemble(ch, half_offsets(ws, l->n_ch), ws.keys, ws.h_idx, l->cnt.n_isl, ws.terms, o->precision,
+                           o->terms, eta_dev, pnli_dev, st));
   return EGN_OK;
 }

@@ -93,22 +93,34 @@ __host__ __device__ inline bool flag_f(int n1, int n2, int n3) { (void)n1; retur
 __host__ __device__ inline bool flag_g(int n1, int n2, int n3) { (void)n3; return n1 == n2; }
 __host__ __device__ inline bool flag_h(int n1, int n2, int n3) { return n1 == n2 && n2 == n3; }
 
+// Island counts of a comb.  Every island (n1, n2, n3) has a mirror (n2, n1, n3)
+// (f1 <-> f2) with the same D and a mirror-image node set, so the integrator
+// evaluates the "half" list n1 <= n2 only; the E list is the islands with
+// n1 = n3 and n1 <= n2, the F list those with n2 = n3 and n1 < n2 (each E/F
+// mirror pair is evaluated once).
+struct PlanCounts {
+  long long n_isl, n_half, n_e, n_f;
+};
+
 // Device workspace carve-up (byte offsets from the workspace base, 256-aligned).
+// Row-count arrays hold four counters per (COI, n1) row: all islands, half
+// list, E list, F list.
 struct Workspace {
-  uint64_t* keys;       // [n_isl]
-  uint32_t* e_idx;      // [n_e] island indices with n1 == n3
-  uint32_t* f_idx;      // [n_f] island indices with n2 == n3
-  uint32_t* row_cnt;    // [3 * n_rows]
-  uint32_t* row_off;    // [3 * (n_rows + 1)]
+  uint64_t* keys;       // [n_isl] every island, (COI, n1, n2, n3) lexicographic
+  uint32_t* h_idx;      // [n_half] island indices with n1 <= n2
+  uint32_t* e_idx;      // [n_e]
+  uint32_t* f_idx;      // [n_f]
+  uint32_t* row_cnt;    // [4 * n_rows]
+  uint32_t* row_off;    // [4 * (n_rows + 1)]
   void* terms;          // [5 * n_isl] of double (FP64) or float (FP32C), term-major
   double* out_eta;      // [n_ch] scratch outputs when the caller passes none
   double* out_pnli;     // [n_ch]
   int* status;          // device error word
-  long long cap_isl, cap_e, cap_f;
+  long long cap_isl, cap_half, cap_e, cap_f;
 };
 
-size_t workspace_bytes(int n_ch, long long n_isl, long long n_e, long long n_f, int precision);
-Workspace carve_workspace(void* base, int n_ch, long long n_isl, long long n_e, long long n_f, int precision);
+size_t workspace_bytes(int n_ch, const PlanCounts& c, int precision);
+Workspace carve_workspace(void* base, int n_ch, const PlanCounts& c, int precision);
 
 // ---- launchers (defined in the .cu files) ----
 // Island planner (A1): counts per (COI, n1) row, scans, emits keys and E/F lists.
@@ -123,10 +135,11 @@ cudaError_t launch_fp64_pass(int ord, const LinkParams& p, const uint64_t* keys,
 cudaError_t launch_fp32c_pass(int ord, const LinkParams& p, const uint64_t* keys, const uint32_t* list,
                               long long n_items, float* terms, long long n_isl, cudaStream_t st);
 
-// Assembly (Eq. 11, 15): per-COI sums of the island contributions.
-cudaError_t launch_assemble(const ChannelTable& ch, const uint32_t* row_off, const uint64_t* keys,
-                            long long n_isl, const void* terms, int precision, int terms_mode, double* eta,
-                            double* pnli, cudaStream_t st);
+// Assembly (Eq. 11, 15): per-COI sums over the half list, each island weighted
+// for itself and its mirror.  half_off: per-row offsets of the half list.
+cudaError_t launch_assemble(const ChannelTable& ch, const uint32_t* half_off, const uint64_t* keys,
+                            const uint32_t* h_idx, long long n_isl, const void* terms, int precision, int terms_mode,
+                            double* eta, double* pnli, cudaStream_t st);
 
 // Host Gauss-Legendre nodes on [-1, 1], ascending.
 void gauss_legendre(int n, double* x, double* w);

@@ -12,7 +12,8 @@
 // row (one warp per row, lanes over n2), exclusive scan of the row counts (one
 // CTA), and emit (one warp per row, warp-scan of the per-lane counts), so that
 // the island list comes out in (COI, n1, n2, n3) lexicographic order together
-// with the compact lists of E (n1 == n3) and F (n2 == n3) islands.
+// with three index lists: the half list (n1 <= n2), the E list (n1 == n3,
+// n1 <= n2) and the F list (n2 == n3, n1 < n2).
 #include "egn_internal.h"
 
 namespace egn {
@@ -49,39 +50,53 @@ __device__ __forceinline__ void for_each_n3(const ChannelTable& ch, int n, int n
     if (island_exists(ch, n, n1, n2, i)) f(i);
 }
 
+struct Counts {
+  uint32_t a, h, e, f;
+};
+
+__device__ __forceinline__ Counts count_pair(const ChannelTable& ch, int n, int n1, int n2) {
+  Counts c = {0, 0, 0, 0};
+  for_each_n3(ch, n, n1, n2, [&](int n3) {
+    ++c.a;
+    c.h += (n1 <= n2);
+    c.e += (n3 == n1 && n1 <= n2);
+    c.f += (n3 == n2 && n1 < n2);
+  });
+  return c;
+}
+
 __global__ void plan_count_kernel(ChannelTable a, uint32_t* row_cnt, int n_rows) {
   int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   int lane = threadIdx.x & 31;
   if (warp >= n_rows) return;
   int n = warp / a.n_ch, n1 = warp % a.n_ch;
-  uint32_t c = 0, ce = 0, cf = 0;
+  Counts c = {0, 0, 0, 0};
   for (int n2 = lane; n2 < a.n_ch; n2 += 32) {
-    for_each_n3(a, n, n1, n2, [&](int n3) {
-      ++c;
-      ce += (n3 == n1);
-      cf += (n3 == n2);
-    });
+    Counts t = count_pair(a, n, n1, n2);
+    c.a += t.a; c.h += t.h; c.e += t.e; c.f += t.f;
   }
   for (int o = 16; o > 0; o >>= 1) {
-    c += __shfl_down_sync(0xffffffffu, c, o);
-    ce += __shfl_down_sync(0xffffffffu, ce, o);
-    cf += __shfl_down_sync(0xffffffffu, cf, o);
+    c.a += __shfl_down_sync(0xffffffffu, c.a, o);
+    c.h += __shfl_down_sync(0xffffffffu, c.h, o);
+    c.e += __shfl_down_sync(0xffffffffu, c.e, o);
+    c.f += __shfl_down_sync(0xffffffffu, c.f, o);
   }
   if (lane == 0) {
-    row_cnt[warp] = c;
-    row_cnt[n_rows + warp] = ce;
-    row_cnt[2 * n_rows + warp] = cf;
+    row_cnt[warp] = c.a;
+    row_cnt[n_rows + warp] = c.h;
+    row_cnt[2 * n_rows + warp] = c.e;
+    row_cnt[3 * n_rows + warp] = c.f;
   }
 }
 
-// Exclusive scan of the three count arrays (one CTA of 1024 threads, each thread
+// Exclusive scan of the four count arrays (one CTA of 1024 threads, each thread
 // a contiguous chunk).  row_off[a * (n_rows + 1) + n_rows] is the total.
 __global__ void plan_scan_kernel(const uint32_t* row_cnt, uint32_t* row_off, int n_rows) {
   __shared__ uint32_t warp_sum[32];
   const int T = blockDim.x;
   int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   int chunk = (n_rows + T - 1) / T;
-  for (int arr = 0; arr < 3; ++arr) {
+  for (int arr = 0; arr < 4; ++arr) {
     const uint32_t* in = row_cnt + (size_t)arr * n_rows;
     uint32_t* out = row_off + (size_t)arr * (n_rows + 1);
     int b = tid * chunk, e = min(b + chunk, n_rows);
@@ -114,51 +129,51 @@ __global__ void plan_scan_kernel(const uint32_t* row_cnt, uint32_t* row_off, int
   }
 }
 
-__global__ void plan_emit_kernel(ChannelTable a, const uint32_t* row_off, int n_rows, uint64_t* keys,
-                                 long long cap_isl, uint32_t* e_idx, long long cap_e, uint32_t* f_idx,
-                                 long long cap_f, int* status) {
+__global__ void plan_emit_kernel(ChannelTable a, const uint32_t* row_off, int n_rows, Workspace ws) {
   int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   int lane = threadIdx.x & 31;
   if (warp >= n_rows) return;
   const int nch = a.n_ch;
   int n = warp / nch, n1 = warp % nch;
   uint32_t base = row_off[warp];
-  uint32_t base_e = row_off[(n_rows + 1) + warp];
-  uint32_t base_f = row_off[2 * (n_rows + 1) + warp];
+  uint32_t base_h = row_off[(n_rows + 1) + warp];
+  uint32_t base_e = row_off[2 * (n_rows + 1) + warp];
+  uint32_t base_f = row_off[3 * (n_rows + 1) + warp];
   for (int n2b = 0; n2b < nch; n2b += 32) {
     int n2 = n2b + lane;
-    uint32_t c = 0, ce = 0, cf = 0;
-    if (n2 < nch)
-      for_each_n3(a, n, n1, n2, [&](int n3) {
-        ++c;
-        ce += (n3 == n1);
-        cf += (n3 == n2);
-      });
-    // warp exclusive scans
-    uint32_t ic = c, ie = ce, ifl = cf;
+    Counts c = {0, 0, 0, 0};
+    if (n2 < nch) c = count_pair(a, n, n1, n2);
+    // warp inclusive scans
+    Counts ic = c;
     for (int o = 1; o < 32; o <<= 1) {
-      uint32_t y0 = __shfl_up_sync(0xffffffffu, ic, o);
-      uint32_t y1 = __shfl_up_sync(0xffffffffu, ie, o);
-      uint32_t y2 = __shfl_up_sync(0xffffffffu, ifl, o);
-      if (lane >= o) { ic += y0; ie += y1; ifl += y2; }
+      uint32_t y0 = __shfl_up_sync(0xffffffffu, ic.a, o);
+      uint32_t y1 = __shfl_up_sync(0xffffffffu, ic.h, o);
+      uint32_t y2 = __shfl_up_sync(0xffffffffu, ic.e, o);
+      uint32_t y3 = __shfl_up_sync(0xffffffffu, ic.f, o);
+      if (lane >= o) { ic.a += y0; ic.h += y1; ic.e += y2; ic.f += y3; }
     }
-    uint32_t pos = base + ic - c, pe = base_e + ie - ce, pf = base_f + ifl - cf;
+    uint32_t pos = base + ic.a - c.a, ph = base_h + ic.h - c.h, pe = base_e + ic.e - c.e, pf = base_f + ic.f - c.f;
     if (n2 < nch)
       for_each_n3(a, n, n1, n2, [&](int n3) {
-        if ((long long)pos < cap_isl) keys[pos] = pack_key(n, n1, n2, n3); else atomicOr(status, 1);
-        if (n3 == n1) {
-          if ((long long)pe < cap_e) e_idx[pe] = pos; else atomicOr(status, 2);
+        if ((long long)pos < ws.cap_isl) ws.keys[pos] = pack_key(n, n1, n2, n3); else atomicOr(ws.status, 1);
+        if (n1 <= n2) {
+          if ((long long)ph < ws.cap_half) ws.h_idx[ph] = pos; else atomicOr(ws.status, 8);
+          ++ph;
+        }
+        if (n3 == n1 && n1 <= n2) {
+          if ((long long)pe < ws.cap_e) ws.e_idx[pe] = pos; else atomicOr(ws.status, 2);
           ++pe;
         }
-        if (n3 == n2) {
-          if ((long long)pf < cap_f) f_idx[pf] = pos; else atomicOr(status, 4);
+        if (n3 == n2 && n1 < n2) {
+          if ((long long)pf < ws.cap_f) ws.f_idx[pf] = pos; else atomicOr(ws.status, 4);
           ++pf;
         }
         ++pos;
       });
-    base += __shfl_sync(0xffffffffu, ic, 31);
-    base_e += __shfl_sync(0xffffffffu, ie, 31);
-    base_f += __shfl_sync(0xffffffffu, ifl, 31);
+    base += __shfl_sync(0xffffffffu, ic.a, 31);
+    base_h += __shfl_sync(0xffffffffu, ic.h, 31);
+    base_e += __shfl_sync(0xffffffffu, ic.e, 31);
+    base_f += __shfl_sync(0xffffffffu, ic.f, 31);
   }
 }
 
@@ -181,8 +196,7 @@ cudaError_t launch_plan(const ChannelTable& ch, const Workspace& ws, cudaStream_
   int n_rows = ch.n_ch * ch.n_ch;
   int threads = kPlanWarps * 32;
   int blocks = (n_rows + kPlanWarps - 1) / kPlanWarps;
-  plan_emit_kernel<<<blocks, threads, 0, st>>>(ch, ws.row_off, n_rows, ws.keys, ws.cap_isl, ws.e_idx, ws.cap_e,
-                                               ws.f_idx, ws.cap_f, ws.status);
+  plan_emit_kernel<<<blocks, threads, 0, st>>>(ch, ws.row_off, n_rows, ws);
   return cudaGetLastError();
 }
 

@@ -63,7 +63,7 @@ def lib():
         L.egn_set_wdm.argtypes = [C.c_void_p, C.c_int, _dp, _dp, _dp, _dp, _dp, C.c_double]
         L.egn_workspace_size.argtypes = [C.c_void_p, C.POINTER(egn_opts), C.POINTER(C.c_size_t)]
         L.egn_island_count.argtypes = [C.c_void_p, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong),
-                                       C.POINTER(C.c_longlong), C.POINTER(C.c_longlong)]
+                                       C.POINTER(C.c_longlong), C.POINTER(C.c_longlong), C.POINTER(C.c_longlong)]
         L.egn_nli_eta.argtypes = [C.c_void_p, C.POINTER(egn_opts), _dp, _dp]
         L.egn_nli_eta_device.argtypes = [C.c_void_p, C.POINTER(egn_opts), C.c_void_p, C.c_size_t, C.c_void_p,
                                          C.c_void_p]
@@ -148,10 +148,11 @@ class Link:
         self.n_ch = len(c)
 
     def island_count(self):
-        tot, ne, nf = C.c_longlong(), C.c_longlong(), C.c_longlong()
+        """(total, per-COI counts, half-list size, E-list size, F-list size)."""
+        tot, nh, ne, nf = C.c_longlong(), C.c_longlong(), C.c_longlong(), C.c_longlong()
         per = (C.c_longlong * self.n_ch)()
-        _check(lib().egn_island_count(self.h, C.byref(tot), per, C.byref(ne), C.byref(nf)))
-        return tot.value, np.array(per[:], dtype=np.int64), ne.value, nf.value
+        _check(lib().egn_island_count(self.h, C.byref(tot), per, C.byref(nh), C.byref(ne), C.byref(nf)))
+        return tot.value, np.array(per[:], dtype=np.int64), nh.value, ne.value, nf.value
 
     def workspace_size(self, opts: egn_opts) -> int:
         b = C.c_size_t()

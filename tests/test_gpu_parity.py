@@ -47,9 +47,14 @@ def test_island_list_bit_exact(egn, oracle_mod, workloads, n_ch):
     got = ln.plan_islands()
     want = np.array([(n, *t) for n in range(n_ch) for t in pb.islands(n)], dtype=np.int32).reshape(-1, 4)
     assert np.array_equal(got, want)
-    tot, per, ne, nf = ln.island_count()
+    tot, per, nh, ne, nf = ln.island_count()
     assert tot == len(want)
-    assert ne == int(np.sum(want[:, 1] == want[:, 3])) and nf == int(np.sum(want[:, 2] == want[:, 3]))
+    n1, n2, n3 = want[:, 1], want[:, 2], want[:, 3]
+    assert nh == int(np.sum(n1 <= n2))
+    assert ne == int(np.sum((n1 == n3) & (n1 <= n2))) and nf == int(np.sum((n2 == n3) & (n1 < n2)))
+    # every island's mirror (n2, n1, n3) is an island too
+    s = {tuple(r) for r in want}
+    assert all((c, b, a, d) in s for c, a, b, d in s)
 
 
 def test_island_list_irregular_comb(egn, oracle_mod, workloads):
@@ -68,7 +73,7 @@ def test_island_count_config_cl(egn, workloads):
     # 120 ch on a 75 GHz grid with 64.64 GHz supports: Eq. 16 counts
     wl = workloads.config_cl()
     ln = egn.link_from_workload(wl)
-    tot, per, ne, nf = ln.island_count()
+    tot, per, nh, ne, nf = ln.island_count()
     M = 120
     want = 0
     for n in range(M):
