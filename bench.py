@@ -209,6 +209,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=None)
     ap.add_argument("--n-ch", type=int, default=120, help="channels of the C+L grid (120 = the benchmark)")
+    ap.add_argument("--points-per-thread", type=int, default=4, choices=[4, 8],
+                    help="launch-shape tuning of the FP32C D/G/H pass")
     args = ap.parse_args()
     if args.warmup < 3:
         log("warmup raised to 3 (timing rule)")
@@ -244,6 +246,7 @@ def main():
     pnli = torch.empty(n_ch, dtype=torch.float64, device="cuda")
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")  # > 129 MB L2
     ln.set_profiling(True)
+    ln.set_tuning(egn.EGN_TUNE_FP32C_POINTS_PER_THREAD, args.points_per_thread)
 
     def step():
         ln.nli_eta_device(opts, ws, eta, pnli)
@@ -343,7 +346,8 @@ def main():
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32" if args.precision == "fp32c" else "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD if n_ch == 120 else WORKLOAD.replace("120ch", f"{n_ch}ch"),
-                       "precision": args.precision, "n_ch": n_ch, "islands": n_isl,
+                       "precision": args.precision, "points_per_thread": args.points_per_thread, "n_ch": n_ch,
+                       "islands": n_isl,
                        "islands_evaluated": n_half, "e_islands": n_e, "f_islands": n_f, "points_per_step": points, "segments_K": K,
                        "l2": "flushed between steps (256 MB write outside the per-step events)",
                        "parallelism": f"replicas x{world}"},

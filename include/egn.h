@@ -188,6 +188,12 @@ egn_status egn_island_terms(egn_link* link, const egn_opts* opts, int n_isl, con
  * visits them (COI, then n1, n2, n3 ascending).  *count gets the total. */
 egn_status egn_plan_islands(egn_link* link, long long max, int* coi_n1_n2_n3, long long* count);
 
+/* Tuning of the kernels' launch shape (results do not change beyond rounding).
+ *   EGN_TUNE_FP32C_POINTS_PER_THREAD: quadrature points per thread in the FP32C
+ *   D/G/H pass, 4 (default) or 8. */
+enum { EGN_TUNE_FP32C_POINTS_PER_THREAD = 1 };
+egn_status egn_set_tuning(egn_link* link, int param, int value);
+
 /* Per-stage device timing.  With profiling on, every evaluation records CUDA
  * events on its stream around five stages; egn_last_timings waits for the last
  * evaluation and writes up to max durations [ms] in the order: island planner,

@@ -81,6 +81,7 @@ struct egn_link {
   DevBuf d_seg, d_gl;
   egn::SegmentTables seg{};
   egn::GlTables gl{};
+  int fp32c_kp = 4;  // tuning: points per thread of the FP32C D/G/H pass
   // optional per-stage device timing of the last evaluation
   bool prof_on = false;
   bool prof_valid = false;
@@ -363,6 +364,7 @@ LinkParams link_params(const egn_link* l, const egn_opts* o, int all_terms) {
   p.rolloff = l->rolloff;
   p.terms = o->terms;
   p.all_terms = all_terms;
+  p.fp32c_kp = l->fp32c_kp;
   return p;
 }
 
@@ -652,6 +654,18 @@ egn_status egn_nli_eta(egn_link* l, const egn_opts* o, double* eta, double* pnli
   return EGN_OK;
 }
 
+egn_status egn_set_tuning(egn_link* l, int param, int value) {
+  if (!l) return fail(EGN_E_INVALID_ARG, "null link");
+  switch (param) {
+    case EGN_TUNE_FP32C_POINTS_PER_THREAD:
+      if (value != 4 && value != 8) return fail(EGN_E_INVALID_ARG, "points per thread must be 4 or 8");
+      l->fp32c_kp = value;
+      return EGN_OK;
+    default:
+      return fail(EGN_E_INVALID_ARG, "unknown tuning parameter %d", param);
+  }
+}
+
 egn_status egn_set_profiling(egn_link* l, int enable) {
   if (!l) return fail(EGN_E_INVALID_ARG, "null link");
   l->prof_on = enable != 0;
@@ -888,6 +902,7 @@ extern "C" egn_status egn_nli_eta_static(egn_link* l, const egn_opts* o, double*
   p.rolloff = l->rolloff;
   p.terms = o->terms;
   p.all_terms = 0;
+  p.fp32c_kp = l->fp32c_kp;
 
   // plan -> integrate -> assemble on the caller's stream, workspace in the scratch
   Workspace ws = carve_workspace(b + ws_off, l->n_ch, l->cnt, o->precision);

@@ -85,6 +85,7 @@ struct LinkParams {
   double rolloff;
   int terms;         // 0 GN, 1 EGN
   int all_terms;     // evaluate E..H on every island (parity checks)
+  int fp32c_kp;      // points per thread of the FP32C D/G/H pass (4 or 8)
 };
 
 // Flags of an island (Kronecker deltas of Eq. 15).

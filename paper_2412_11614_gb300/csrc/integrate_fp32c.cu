@@ -10,20 +10,23 @@
 //     double-float arithmetic (FP32 only) -- the cubic phase polynomial in the
 //     inner node, Q0 reduced modulo K -- and, in the DW order, the row's table
 //     c_k = C_k e^{-zeta_k f3} in shared memory.
-//  3. Per point (4 per thread, one row): phase, segment sum, Upsilon, weights.
+//  3. Per point (KP per thread, one row): phase, segment sum, Upsilon, weights.
 //
 // Arithmetic per point:
 //  * Phase.  Theta(x) = chi L / 2 pi = 2 pi L (f1 - f)(f2 - f)[beta2 + pi beta3 (f1 + f2)]
-//    (Eq. 5, 24) is a cubic in the inner Gauss-Legendre coordinate x along a row.
-//    Q1 x and Q2 x^2 are exact FP32 products (error-free FMA product plus tail
-//    cross terms), reduced modulo K exactly (the FMA residual p - K n is exact),
-//    and summed with error-free two-sums; this yields theta = chi L/K and
-//    phi = chi L, both in turns modulo 1, to ~1e-7 turns.
+//    (Eq. 5, 24) is a cubic in the inner Gauss-Legendre coordinate x along a row,
+//    Theta = Q0 + Q1 x + Q2 x^2 + Q3 x^3 (turns of one span).  Q1 x and Q2 x^2 are
+//    formed as exact FP32 products (error-free FMA product plus tail cross terms)
+//    and Q1 x is reduced modulo K exactly (the FMA residual p - K n is exact).
+//    phi = chi L modulo 1 is the sum of the exact fractional parts of the terms
+//    (~1e-7 turns); theta = chi L / K modulo 1 takes the rounded sum of the
+//    reduced terms divided by K (~1e-5 / K turns).
 //  * Segment sum (Eq. 8-10).  mu = (w - 1)/(i chi - alpha) sum_k c_k w^k,
 //    w = r e^{i theta}; the real-coefficient polynomial is evaluated by the
 //    second-order real recurrence b_k = c_k + p b_{k+1} - q b_{k+2} (p = 2 Re w,
 //    q = |w|^2), sum = b_0 - conj(w) b_1: Horner's rule rewritten exactly, 2 FMA
-//    per segment instead of 4; |w| < 1 bounds its error growth.
+//    per segment instead of 4; |w| < 1 bounds its error growth.  In the DW order
+//    two points share one fma.rn.f32x2 instruction.
 //  * Phased array (Eq. 22): ratio sin(N pi phi)/sin(pi phi); near phi = 0 the
 //    sines use their Taylor series (|argument| < 0.05, relative error < 1e-12).
 //    Hardware sin/cos (MUFU, absolute error ~4e-7 on [-pi, pi]) elsewhere.
@@ -36,7 +39,6 @@ namespace {
 
 constexpr int kThreads = 128;
 constexpr int kBatch = kThreads;   // islands per batch, one per thread in the set-up
-constexpr int kP = 4;              // points per thread (same row)
 constexpr int kRowsMax = 64;       // rows per chunk held in shared memory
 constexpr int kTabFloats = 5376;   // DW c_k table budget (21 KB), each c_k stored twice (f32x2)
 
@@ -133,24 +135,32 @@ struct BatchSm {  // one entry per island of the batch
   float cf0[kBatch], cf1[kBatch], cf2[kBatch];          // D, G, H (DW) or the E / F coefficient
 };
 
+// Row constants, four per float4 so that a point pass loads them with 16-byte loads.
 struct RowSm {
-  float q0h[kRowsMax], q0l[kRowsMax], q1h[kRowsMax], q1l[kRowsMax], q2h[kRowsMax], q2l[kRowsMax], q3[kRowsMax];
-  float a0[kRowsMax], a1[kRowsMax], b0[kRowsMax], b1[kRowsMax];  // f1 - f, f2 - f = a0 + a1 x, b0 + b1 x
-  float bc0[kRowsMax], bc1[kRowsMax];                            // beta2 + pi beta3 (f1 + f2) = bc0 + bc1 x
-  float im[kRowsMax], ih[kRowsMax];                              // inner variable = im + ih x
-  float o[kRowsMax];                                             // outer variable
-  float wo[kRowsMax];                                            // outer weight
-  float hout[kRowsMax];                                          // shape of the outer variable's channel
-  float f30[kRowsMax], f31[kRowsMax];                            // f3 = f30 + f31 x
+  float4 qa[kRowsMax];  // q0h, q0l, q1h, q1l              (phase, turns; Q0 modulo K)
+  float4 qb[kRowsMax];  // q2h, q2l, q3, frac(q0h)
+  float4 ab[kRowsMax];  // a0, a1, b0, b1                  (f1 - f = a0 + a1 x, f2 - f = b0 + b1 x)
+  float4 kc[kRowsMax];  // 4 pi^2 bc0, 4 pi^2 bc1, im, ih   (bc = beta2 + pi beta3 (f1 + f2); inner = im + ih x)
+  float4 ow[kRowsMax];  // o - d (DW) or o, wo ih hout, wo ih, hout   (wo outer weight, hout outer shape)
+  float4 f3[kRowsMax];  // f30, f31, wo, 0                  (f3 = f30 + f31 x)
 };
 
-template <int ORD>
-__global__ void __launch_bounds__(kThreads, 4)
+// Inner Gauss-Legendre nodes of the launch: {x head, x tail, x^2 head, x^2 tail}, {x^3, w}.
+struct NodeSm {
+  float4 x4[kMaxGl];
+  float2 x2[kMaxGl];
+};
+
+template <int ORD, int KP>
+__global__ void __launch_bounds__(kThreads, KP == 8 ? 3 : 4)
 integrate_fp32c_kernel(LinkParams p, const uint64_t* __restrict__ keys, const uint32_t* __restrict__ list,
                        long long n_items, float* __restrict__ terms, long long n_isl, int rows_per_chunk, int kpad,
                        Df G0, Df G1) {
+  static_assert(KP % 2 == 0, "points per thread come in f32x2 pairs");
+  constexpr int NPAIR = KP / 2;
   __shared__ BatchSm bs;
   __shared__ RowSm rs;
+  __shared__ NodeSm ns;
   __shared__ float red[4][kThreads / 32];
   extern __shared__ __align__(16) float2 tab[];  // [rows_per_chunk][kpad] pairs (c_k, c_k) (DW only)
 
@@ -163,6 +173,7 @@ integrate_fp32c_kernel(LinkParams p, const uint64_t* __restrict__ keys, const ui
   const float r = (float)p.r;
   const float one_m_r = (float)(-expm1(-p.alpha * p.dz));
   const float q = r * r;
+  const float m2r = -2.0f * r;
   const float N = (float)p.n_spans;
   const float gam = (float)p.gamma;
   const float g2 = gam * gam;
@@ -171,21 +182,15 @@ integrate_fp32c_kernel(LinkParams p, const uint64_t* __restrict__ keys, const ui
   const float pi_f = 3.14159265358979f;
   // threads per row (power of two), row slot and point slot of this thread
   int tpr = 1;
-  while (tpr * kP < n) tpr <<= 1;
+  while (tpr * KP < n) tpr <<= 1;
   const int rows_per_pass = kThreads / tpr;
   const int lr = tid & (tpr - 1);
   const int rsub = tid / tpr;
-  // this thread's inner nodes (fixed for the whole launch)
-  float nxh[kP], nxl[kP], nwf[kP];
-  bool jok[kP];
-#pragma unroll
-  for (int m = 0; m < kP; ++m) {
-    int j = lr + tpr * m;
-    jok[m] = j < n;
-    int jj = jok[m] ? j : 0;
-    nxh[m] = p.gl.xh[1][jj];
-    nxl[m] = p.gl.xl[1][jj];
-    nwf[m] = jok[m] ? p.gl.wf[1][jj] : 0.0f;
+
+  for (int j = tid; j < n; j += kThreads) {
+    const float xh = p.gl.xh[1][j], xl = p.gl.xl[1][j];
+    ns.x4[j] = make_float4(xh, xl, p.gl.x2h[1][j], p.gl.x2l[1][j]);
+    ns.x2[j] = make_float2(xh * p.gl.x2h[1][j], p.gl.wf[1][j]);
   }
 
   for (long long b0 = (long long)blockIdx.x * kBatch; b0 < n_items; b0 += (long long)gridDim.x * kBatch) {
@@ -254,10 +259,9 @@ integrate_fp32c_kernel(LinkParams p, const uint64_t* __restrict__ keys, const ui
       const int rows = np * no;
       for (int c0 = 0; c0 < rows; c0 += rows_per_chunk) {
         const int rc = min(rows_per_chunk, rows - c0);
-        // ---- row constants in double-float; rows spread over the four warps
+        // ---- row constants in double-float; slot rr = 32 (tid mod 4) + tid / 4 (a
+        // bijection on 0..127) spreads the first 32 rows of a chunk over the four warps
         {
-          // slot rr = 32 (tid mod 4) + tid / 4 (a bijection on 0..127): the first 32 rows
-          // of a chunk go to 8 lanes of each warp, so all four warps share the work
           const int rr = (tid & 3) * 32 + (tid >> 2);
           if (rr < rc) {
             const int row = c0 + rr;
@@ -297,22 +301,18 @@ integrate_fp32c_kernel(LinkParams p, const uint64_t* __restrict__ keys, const ui
             // Q0 modulo K (the FMA residual is exact)
             const float r0 = fmaf(-Kf, rintf(Q0.hi * invK), Q0.hi);
             const Df Q0r = quick(r0, Q0.lo);
-            rs.q0h[rr] = Q0r.hi; rs.q0l[rr] = Q0r.lo;
-            rs.q1h[rr] = Q1.hi; rs.q1l[rr] = Q1.lo;
-            rs.q2h[rr] = Q2.hi; rs.q2l[rr] = Q2.lo;
-            rs.q3[rr] = Q3;
-            rs.a0[rr] = dval(a0); rs.a1[rr] = dval(a1);
-            rs.b0[rr] = dval(b0_); rs.b1[rr] = dval(b1);
             const float s0f = dval(s0), s1f = dval(s1);
-            rs.bc0[rr] = fmaf(pib3, s0f, b2f);
-            rs.bc1[rr] = pib3 * s1f;
             const float imf = dval(im), ihf = dval(ih), of = dval(o);
-            rs.im[rr] = imf; rs.ih[rr] = ihf; rs.o[rr] = of;
-            rs.wo[rr] = dval(ph) * p.gl.wf[np][i];
-            rs.hout[rr] = ORD == ORD_DW ? rc_f(of, R3f, beta) : (ORD == ORD_E ? rc_f(of, R2f, beta) : rc_f(of, R1f, beta));
+            const float wo = dval(ph) * p.gl.wf[np][i];
+            const float hout = ORD == ORD_DW ? rc_f(of, R3f, beta) : (ORD == ORD_E ? rc_f(of, R2f, beta) : rc_f(of, R1f, beta));
+            rs.qa[rr] = make_float4(Q0r.hi, Q0r.lo, Q1.hi, Q1.lo);
+            rs.qb[rr] = make_float4(Q2.hi, Q2.lo, Q3, Q0r.hi - rintf(Q0r.hi));
+            rs.ab[rr] = make_float4(dval(a0), dval(a1), dval(b0_), dval(b1));
+            rs.kc[rr] = make_float4(k4 * fmaf(pib3, s0f, b2f), k4 * pib3 * s1f, imf, ihf);
+            rs.ow[rr] = make_float4(ORD == ORD_DW ? of - dfl : of, wo * ihf * hout, wo * ihf, hout);
             const float nu3 = bs.nu3[ib];
-            if (ORD == ORD_DW) { rs.f30[rr] = nu3 + of; rs.f31[rr] = 0.0f; }
-            else { rs.f30[rr] = nu3 + (imf + of + dfl); rs.f31[rr] = ihf; }
+            if (ORD == ORD_DW) rs.f3[rr] = make_float4(nu3 + of, 0.0f, wo, 0.0f);
+            else rs.f3[rr] = make_float4(nu3 + (imf + of + dfl), ihf, wo, 0.0f);
           }
         }
         __syncthreads();
@@ -321,7 +321,7 @@ integrate_fp32c_kernel(LinkParams p, const uint64_t* __restrict__ keys, const ui
           for (int k = tid; k < K; k += kThreads) {
             const float ck = p.seg.ck_f[k], zk = p.seg.zeta_f[k];
             for (int rr = 0; rr < rc; ++rr) {
-              const float c = ck * ex2_approx(-zk * rs.f30[rr]);
+              const float c = ck * ex2_approx(-zk * rs.f3[rr].x);
               tab[rr * kpad + k] = make_float2(c, c);
             }
           }
@@ -332,104 +332,117 @@ integrate_fp32c_kernel(LinkParams p, const uint64_t* __restrict__ keys, const ui
           const int rr = rb + rsub;
           const bool row_ok = rr < rc;
           const int rrc = row_ok ? rr : 0;
+          const float4 qa = rs.qa[rrc], qb = rs.qb[rrc], ab = rs.ab[rrc], kc = rs.kc[rrc], ow = rs.ow[rrc];
+          const float4 f3r = rs.f3[rrc];
+          const float q0h = qa.x, q0l = qa.y, q1h = qa.z, q1l = qa.w;
+          const float q2h = qb.x, q2l = qb.y, q3 = qb.z, fq0 = qb.w;
+          const float im = kc.z, ih = kc.w;
+          const float wrowh = row_ok ? ow.y : 0.0f, wrow = row_ok ? ow.z : 0.0f;
           float gre = 0.0f, gim = 0.0f;
-          float p_[kP], b1_[kP], b2_[kP], f3_[kP];
-          float wm1_[kP], wi_[kP], chi_[kP], phi_[kP], wgt_[kP], s12_[kP], s123_[kP];
-          const float q0h = rs.q0h[rrc], q0l = rs.q0l[rrc], q1h = rs.q1h[rrc], q1l = rs.q1l[rrc];
-          const float q2h = rs.q2h[rrc], q2l = rs.q2l[rrc], q3 = rs.q3[rrc];
-          const float a0 = rs.a0[rrc], a1 = rs.a1[rrc], b0 = rs.b0[rrc], b1 = rs.b1[rrc];
-          const float bc0 = rs.bc0[rrc], bc1 = rs.bc1[rrc], im = rs.im[rrc], ih = rs.ih[rrc], of = rs.o[rrc];
-          const float wo = rs.wo[rrc], hout = rs.hout[rrc], f30 = rs.f30[rrc], f31 = rs.f31[rrc];
+          float p_[KP], b1_[KP], b2_[KP], f3_[KP];
+          float wm1_[KP], wi_[KP], chi_[KP], phi_[KP], wgt_[KP], s12_[KP], s123_[KP];
 #pragma unroll
-          for (int m = 0; m < kP; ++m) {
-            const bool ok = row_ok && jok[m];
-            const float xh = nxh[m], xl = nxl[m];
-            // x^2 as a double-float
-            const float x2h = xh * xh, x2l = fmaf(xh, xh, -x2h) + 2.0f * xh * xl;
-            // phase modulo K: Q0 + Q1 x + Q2 x^2 + Q3 x^3 with exact products and sums
+          for (int m = 0; m < KP; ++m) {
+            const int j = lr + tpr * m;
+            const bool jok = j < n;
+            const int jj = jok ? j : 0;
+            const float4 x4 = ns.x4[jj];
+            const float2 x2 = ns.x2[jj];
+            const float xh = x4.x, xl = x4.y, x2h = x4.z, x2l = x4.w, xc = x2.x;
+            const float wnode = jok ? x2.y : 0.0f;
+            // phase: exact products, Q1 x reduced modulo K
             const float p1 = q1h * xh, e1 = fmaf(q1h, xh, -p1);
             const float t1 = fmaf(q1h, xl, fmaf(q1l, xh, e1));
             const float p2 = q2h * x2h, e2 = fmaf(q2h, x2h, -p2);
             const float t2 = fmaf(q2h, x2l, fmaf(q2l, x2h, e2));
             const float r1 = fmaf(-Kf, rintf(p1 * invK), p1);
-            const float r2 = fmaf(-Kf, rintf(p2 * invK), p2);
-            float s1, s2, ea, eb;
-            two_sum(q0h, r1, s1, ea);
-            two_sum(s1, r2, s2, eb);
-            const float tail = ((ea + eb) + (q0l + t1 + t2)) + q3 * (xh * x2h);
-            float th = fmaf(s2, invK, tail * invK);
-            th -= rintf(th);                     // theta in turns, [-1/2, 1/2]
-            float ph = (s2 - rintf(s2)) + tail;  // phi in turns
-            ph -= rintf(ph);
-            // w = r e^{2 pi i th} from the half angle: keeps w - 1 accurate
+            const float tail = (q0l + t1) + fmaf(q3, xc, t2);
+            float th = fmaf((q0h + r1) + p2, invK, tail * invK);
+            th -= rintf(th);                                           // theta (turns)
+            float ph = (fq0 + (r1 - rintf(r1))) + ((p2 - rintf(p2)) + tail);
+            ph -= rintf(ph);                                           // phi (turns)
+            // w = r e^{2 pi i th} from the half angle (keeps w - 1 accurate)
             const float ah = pi_f * th;
             const float sh = __sinf(ah), chh = __cosf(ah);
-            const float wr = r * fmaf(-2.0f * sh, sh, 1.0f);
-            p_[m] = 2.0f * wr;
-            wm1_[m] = -one_m_r - 2.0f * r * sh * sh;  // Re(w - 1)
-            wi_[m] = 2.0f * r * sh * chh;
+            const float t2r = m2r * sh;
+            const float wm1 = fmaf(t2r, sh, -one_m_r);                 // Re(w - 1)
+            p_[m] = fmaf(2.0f, wm1, 2.0f);                            // 2 Re(w)
+            wm1_[m] = wm1;
+            wi_[m] = -t2r * chh;                                      // Im(w)
             phi_[m] = ph;
             // chi [rad/km] for (i chi - alpha)
-            const float a = fmaf(a1, xh, a0), b = fmaf(b1, xh, b0), bc = fmaf(bc1, xh, bc0);
-            chi_[m] = k4 * a * b * bc;
+            chi_[m] = fmaf(ab.y, xh, ab.x) * fmaf(ab.w, xh, ab.z) * fmaf(kc.y, xh, kc.x);
             // spectral shapes and weights
             const float t = fmaf(ih, xh, im);
             float u, v, h3;
-            if (ORD == ORD_DW) { u = t; v = of - t - dfl; h3 = hout; }
+            if (ORD == ORD_DW) { u = t; v = ow.x - t; h3 = 1.0f; }  // h3(w) is folded into wrowh
             else {
-              if (ORD == ORD_E) { v = of; u = t; } else { u = of; v = t; }
+              if (ORD == ORD_E) { v = ow.x; u = t; } else { u = ow.x; v = t; }
               h3 = rc_f(u + v + dfl, R3f, beta);
             }
             const float h1 = rc_f(u, R1f, beta), h2 = rc_f(v, R2f, beta);
-            const float wij = ok ? wo * ih * nwf[m] : 0.0f;
-            wgt_[m] = wij * h1 * h2 * h3;
+            wgt_[m] = (ORD == ORD_DW ? wrowh : wrow) * wnode * h1 * h2 * h3;
             s12_[m] = 0.0f;
             s123_[m] = 0.0f;
             if (cplx) {
               if (ORD == ORD_DW) {
-                s12_[m] = ok ? nwf[m] * sqrtf(h1 * h2) : 0.0f;
-                s123_[m] = wij * sqrtf(h1 * h2 * h3);
+                s12_[m] = (row_ok ? wnode : 0.0f) * sqrtf(h1 * h2);
+                s123_[m] = wrow * wnode * sqrtf(h1 * h2 * ow.w);
               } else {
-                s12_[m] = ok ? nwf[m] * ih * sqrtf(ORD == ORD_E ? h1 * h3 : h2 * h3) : 0.0f;
+                s12_[m] = (row_ok ? wnode : 0.0f) * ih * sqrtf(ORD == ORD_E ? h1 * h3 : h2 * h3);
               }
             }
-            f3_[m] = fmaf(f31, xh, f30);
+            f3_[m] = fmaf(f3r.y, xh, f3r.x);
             b1_[m] = 0.0f;
             b2_[m] = 0.0f;
           }
           // ---- segment sum by the real recurrence, k = K-1 .. 0
           if (ORD == ORD_DW) {
-            // points (0, 1) and (2, 3) as f32x2 pairs; the table holds (c_k, c_k)
             const float2* trow = tab + rrc * kpad;
             const f32x2 nq2 = pack2(-q, -q);
-            const f32x2 pA = pack2(p_[0], p_[1]), pB = pack2(p_[2], p_[3]);
-            f32x2 b1A = 0ull, b2A = 0ull, b1B = 0ull, b2B = 0ull;
+            f32x2 pp[NPAIR], b1p[NPAIR], b2p[NPAIR];
+#pragma unroll
+            for (int a = 0; a < NPAIR; ++a) {
+              pp[a] = pack2(p_[2 * a], p_[2 * a + 1]);
+              b1p[a] = 0ull;
+              b2p[a] = 0ull;
+            }
             int k = K - 1;
             if (K & 1) {  // peel so that the 16-byte loads below are aligned
               const f32x2 c = *reinterpret_cast<const f32x2*>(trow + k);
-              f32x2 nA = ffma2(nq2, b2A, ffma2(pA, b1A, c));
-              f32x2 nB = ffma2(nq2, b2B, ffma2(pB, b1B, c));
-              b2A = b1A; b1A = nA; b2B = b1B; b1B = nB;
+#pragma unroll
+              for (int a = 0; a < NPAIR; ++a) {
+                const f32x2 nb = ffma2(nq2, b2p[a], ffma2(pp[a], b1p[a], c));
+                b2p[a] = b1p[a];
+                b1p[a] = nb;
+              }
               --k;
             }
             for (; k >= 1; k -= 2) {
               const ulonglong2 cc = *reinterpret_cast<const ulonglong2*>(trow + k - 1);  // (c_{k-1}, c_k) pairs
-              f32x2 nA = ffma2(nq2, b2A, ffma2(pA, b1A, cc.y));
-              f32x2 nB = ffma2(nq2, b2B, ffma2(pB, b1B, cc.y));
-              b2A = b1A; b1A = nA; b2B = b1B; b1B = nB;
-              nA = ffma2(nq2, b2A, ffma2(pA, b1A, cc.x));
-              nB = ffma2(nq2, b2B, ffma2(pB, b1B, cc.x));
-              b2A = b1A; b1A = nA; b2B = b1B; b1B = nB;
+#pragma unroll
+              for (int a = 0; a < NPAIR; ++a) {
+                const f32x2 nb = ffma2(nq2, b2p[a], ffma2(pp[a], b1p[a], cc.y));
+                b2p[a] = b1p[a];
+                b1p[a] = nb;
+              }
+#pragma unroll
+              for (int a = 0; a < NPAIR; ++a) {
+                const f32x2 nb = ffma2(nq2, b2p[a], ffma2(pp[a], b1p[a], cc.x));
+                b2p[a] = b1p[a];
+                b1p[a] = nb;
+              }
             }
-            unpack2(b1A, b1_[0], b1_[1]);
-            unpack2(b2A, b2_[0], b2_[1]);
-            unpack2(b1B, b1_[2], b1_[3]);
-            unpack2(b2B, b2_[2], b2_[3]);
+#pragma unroll
+            for (int a = 0; a < NPAIR; ++a) {
+              unpack2(b1p[a], b1_[2 * a], b1_[2 * a + 1]);
+              unpack2(b2p[a], b2_[2 * a], b2_[2 * a + 1]);
+            }
           } else {
             for (int k = K - 1; k >= 0; --k) {
               const float ck = p.seg.ck_f[k], zk = p.seg.zeta_f[k];
 #pragma unroll
-              for (int m = 0; m < kP; ++m) {
+              for (int m = 0; m < KP; ++m) {
                 const float c = ck * ex2_approx(-zk * f3_[m]);
                 float bn = fmaf(p_[m], b1_[m], c);
                 bn = fmaf(-q, b2_[m], bn);
@@ -440,16 +453,15 @@ integrate_fp32c_kernel(LinkParams p, const uint64_t* __restrict__ keys, const ui
           }
           // ---- mu, Upsilon and the sums
 #pragma unroll
-          for (int m = 0; m < kP; ++m) {
+          for (int m = 0; m < KP; ++m) {
             // after the loop b1 = b_0 and b2 = b_1: sum = b_0 - conj(w) b_1
-            const float wr = 0.5f * p_[m], wi = wi_[m];
-            const float sre = fmaf(-wr, b2_[m], b1_[m]);
+            const float wm1 = wm1_[m], wi = wi_[m], chi = chi_[m];
+            const float sre = fmaf(-(wm1 + 1.0f), b2_[m], b1_[m]);
             const float sim = wi * b2_[m];
             // (w - 1)/(i chi - alpha) = (w - 1)(-alpha - i chi)/(alpha^2 + chi^2)
-            const float xr = wm1_[m], chi = chi_[m];
             const float inv = rcp_approx(fmaf(chi, chi, alpha2));
-            const float qr = fmaf(-alpha, xr, chi * wi) * inv;
-            const float qi = fmaf(-chi, xr, -alpha * wi) * inv;
+            const float qr = fmaf(-alpha, wm1, chi * wi) * inv;
+            const float qi = fmaf(-chi, wm1, -alpha * wi) * inv;
             const float mre = fmaf(sre, qr, -sim * qi);
             const float mim = fmaf(sre, qi, sim * qr);
             // phased array: sin(N pi phi) / sin(pi phi)
@@ -463,14 +475,14 @@ integrate_fp32c_kernel(LinkParams p, const uint64_t* __restrict__ keys, const ui
               ratio = (x == 0.0f) ? N : snum * rcp_approx(sin_small(x));
             }
             if (!cplx) {
-              dsum = fmaf(wgt_[m], (mre * mre + mim * mim) * (ratio * ratio), dsum);
+              dsum = fmaf(wgt_[m], fmaf(mre, mre, mim * mim) * (ratio * ratio), dsum);
             } else {
               const float ang = (N - 1.0f) * x;
               const float sp = __sinf(ang), cp = __cosf(ang);
               const float yre = ratio * fmaf(mre, cp, -mim * sp);  // Upsilon / gamma
               const float yim = ratio * fmaf(mre, sp, mim * cp);
               if (ORD == ORD_DW) {
-                dsum = fmaf(wgt_[m], yre * yre + yim * yim, dsum);
+                dsum = fmaf(wgt_[m], fmaf(yre, yre, yim * yim), dsum);
                 hre = fmaf(s123_[m], yre, hre);
                 him = fmaf(s123_[m], yim, him);
               }
@@ -487,31 +499,42 @@ integrate_fp32c_kernel(LinkParams p, const uint64_t* __restrict__ keys, const ui
             if (lr == 0 && row_ok) {
               const float ihr = (ORD == ORD_DW) ? ih : 1.0f;
               const float gr_ = gre * ihr, gi_ = gim * ihr;
-              csum = fmaf(wo * hout, gr_ * gr_ + gi_ * gi_, csum);
+              csum = fmaf(f3r.z * ow.w, gr_ * gr_ + gi_ * gi_, csum);
             }
           }
         }
         __syncthreads();  // rows and tables are rewritten by the next chunk
       }
       // ---- island reduction (fixed order); every sum above is of Upsilon / gamma
-      float vals[4] = {dsum, csum, hre, him};
+      if (!cplx) {
+        float v = dsum;
+        for (int o_ = 16; o_ > 0; o_ >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o_);
+        if (lane == 0) red[0][wid] = v;
+      } else {
+        float vals[4] = {dsum, csum, hre, him};
 #pragma unroll
-      for (int a = 0; a < 4; ++a)
-        for (int o_ = 16; o_ > 0; o_ >>= 1) vals[a] += __shfl_xor_sync(0xffffffffu, vals[a], o_);
-      if (lane == 0)
+        for (int a = 0; a < 4; ++a)
+          for (int o_ = 16; o_ > 0; o_ >>= 1) vals[a] += __shfl_xor_sync(0xffffffffu, vals[a], o_);
+        if (lane == 0)
 #pragma unroll
-        for (int a = 0; a < 4; ++a) red[a][wid] = vals[a];
+          for (int a = 0; a < 4; ++a) red[a][wid] = vals[a];
+      }
       __syncthreads();
       if (tid == 0) {
-        float t[4];
-        for (int a = 0; a < 4; ++a) t[a] = (red[a][0] + red[a][1]) + (red[a][2] + red[a][3]);
         const long long isl = bs.isl[ib];
+        const float t0 = (red[0][0] + red[0][1]) + (red[0][2] + red[0][3]);
         if (ORD == ORD_DW) {
-          terms[isl] = bs.cf0[ib] * g2 * t[0];
-          if (want_g) terms[3 * n_isl + isl] = bs.cf1[ib] * g2 * t[1];
-          if (want_h) terms[4 * n_isl + isl] = bs.cf2[ib] * g2 * (t[2] * t[2] + t[3] * t[3]);
+          terms[isl] = bs.cf0[ib] * g2 * t0;
+          if (cplx) {
+            const float t1 = (red[1][0] + red[1][1]) + (red[1][2] + red[1][3]);
+            const float t2 = (red[2][0] + red[2][1]) + (red[2][2] + red[2][3]);
+            const float t3 = (red[3][0] + red[3][1]) + (red[3][2] + red[3][3]);
+            if (want_g) terms[3 * n_isl + isl] = bs.cf1[ib] * g2 * t1;
+            if (want_h) terms[4 * n_isl + isl] = bs.cf2[ib] * g2 * (t2 * t2 + t3 * t3);
+          }
         } else {
-          terms[(ORD == ORD_E ? 1 : 2) * n_isl + isl] = bs.cf0[ib] * g2 * t[1];
+          const float t1 = (red[1][0] + red[1][1]) + (red[1][2] + red[1][3]);
+          terms[(ORD == ORD_E ? 1 : 2) * n_isl + isl] = bs.cf0[ib] * g2 * t1;
         }
       }
       __syncthreads();
@@ -519,7 +542,7 @@ integrate_fp32c_kernel(LinkParams p, const uint64_t* __restrict__ keys, const ui
   }
 }
 
-template <int ORD>
+template <int ORD, int KP>
 cudaError_t launch_one(const LinkParams& p, const uint64_t* keys, const uint32_t* list, long long n_items, float* terms,
                        long long n_isl, cudaStream_t st) {
   if (n_items <= 0) return cudaSuccess;
@@ -536,15 +559,23 @@ cudaError_t launch_one(const LinkParams& p, const uint64_t* keys, const uint32_t
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  // static shared memory + the c_k table exceed the 48 KB default: opt in once per device
+  static unsigned long long attr_done = 0;
+  if (!(attr_done >> (dev & 63) & 1ull)) {
+    cudaError_t e = cudaFuncSetAttribute(integrate_fp32c_kernel<ORD, KP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         kTabFloats * (int)sizeof(float));
+    if (e != cudaSuccess) return e;
+    attr_done |= 1ull << (dev & 63);
+  }
   long long batches = (n_items + kBatch - 1) / kBatch;
-  long long blocks = (long long)sms * 4;
+  long long blocks = (long long)sms * (KP == 8 ? 3 : 4);
   if (blocks > batches) blocks = batches;
   // 2 pi L beta2 and 2 pi^2 L beta3 as double-floats
   double g0 = 2.0 * kPi * p.L * p.beta2, g1 = 2.0 * kPi * kPi * p.L * p.beta3;
   float g0h = (float)g0, g1h = (float)g1;
   Df G0 = {g0h, (float)(g0 - (double)g0h)}, G1 = {g1h, (float)(g1 - (double)g1h)};
-  integrate_fp32c_kernel<ORD><<<(unsigned)blocks, kThreads, smem, st>>>(p, keys, list, n_items, terms, n_isl, rows,
-                                                                       kpad, G0, G1);
+  integrate_fp32c_kernel<ORD, KP><<<(unsigned)blocks, kThreads, smem, st>>>(p, keys, list, n_items, terms, n_isl,
+                                                                           rows, kpad, G0, G1);
   return cudaGetLastError();
 }
 
@@ -552,9 +583,12 @@ cudaError_t launch_one(const LinkParams& p, const uint64_t* keys, const uint32_t
 
 cudaError_t launch_fp32c_pass(int ord, const LinkParams& p, const uint64_t* keys, const uint32_t* list,
                               long long n_items, float* terms, long long n_isl, cudaStream_t st) {
-  if (ord == ORD_DW) return launch_one<ORD_DW>(p, keys, list, n_items, terms, n_isl, st);
-  if (ord == ORD_E) return launch_one<ORD_E>(p, keys, list, n_items, terms, n_isl, st);
-  return launch_one<ORD_F>(p, keys, list, n_items, terms, n_isl, st);
+  if (ord == ORD_DW) {
+    if (p.fp32c_kp == 8) return launch_one<ORD_DW, 8>(p, keys, list, n_items, terms, n_isl, st);
+    return launch_one<ORD_DW, 4>(p, keys, list, n_items, terms, n_isl, st);
+  }
+  if (ord == ORD_E) return launch_one<ORD_E, 4>(p, keys, list, n_items, terms, n_isl, st);
+  return launch_one<ORD_F, 4>(p, keys, list, n_items, terms, n_isl, st);
 }
 
 }  // namespace egn

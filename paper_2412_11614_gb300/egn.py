@@ -19,6 +19,7 @@ EGN_MU_SEGMENT = 0
 EGN_PREC_FP64, EGN_PREC_FP32C = 0, 1
 EGN_TERMS_GN, EGN_TERMS_EGN = 0, 1
 EGN_FMT = {"GAUSS": 0, "QPSK": 1, "16QAM": 2, "64QAM": 3}
+EGN_TUNE_FP32C_POINTS_PER_THREAD = 1
 STATUS_NAMES = {0: "EGN_OK", 1: "EGN_E_INVALID_ARG", 2: "EGN_E_UNSUPPORTED", 3: "EGN_E_NOMEM", 4: "EGN_E_CUDA",
                 5: "EGN_E_TIMEOUT", 6: "EGN_E_STATE", 7: "EGN_E_CAPACITY"}
 
@@ -73,12 +74,13 @@ def lib():
         L.egn_format_moments.argtypes = [C.c_int, _dp, _dp]
         L.egn_gauss_legendre.argtypes = [C.c_int, _dp, _dp]
         L.egn_set_profiling.argtypes = [C.c_void_p, C.c_int]
+        L.egn_set_tuning.argtypes = [C.c_void_p, C.c_int, C.c_int]
         L.egn_last_timings.argtypes = [C.c_void_p, _dp, C.c_int, C.POINTER(C.c_int)]
         L.egn_last_error.restype = C.c_char_p
         L.egn_version.restype = C.c_char_p
         for fn in ("egn_link_create", "egn_set_wdm", "egn_workspace_size", "egn_island_count", "egn_nli_eta",
                    "egn_nli_eta_device", "egn_island_terms", "egn_plan_islands", "egn_format_moments",
-                   "egn_gauss_legendre", "egn_set_profiling", "egn_last_timings", "egn_nli_eta_static"):
+                   "egn_gauss_legendre", "egn_set_profiling", "egn_last_timings", "egn_nli_eta_static", "egn_set_tuning"):
             getattr(L, fn).restype = C.c_int
         _lib = L
     return _lib
@@ -186,6 +188,9 @@ class Link:
         _check(lib().egn_island_terms(self.h, C.byref(opts), len(isl), isl.ctypes.data_as(C.POINTER(C.c_int)),
                                       int(bool(all_terms)), out.ctypes.data_as(_dp)))
         return out
+
+    def set_tuning(self, param: int, value: int):
+        _check(lib().egn_set_tuning(self.h, int(param), int(value)))
 
     def set_profiling(self, on: bool):
         _check(lib().egn_set_profiling(self.h, int(bool(on))))
