@@ -115,6 +115,25 @@ def gpu_id_for_smi(local_rank: int) -> str:
     return str(local_rank)
 
 
+# --------------------------------------------------------------------------- ranks
+
+def aggregate_ranks(ms_local: float, evals_local: int, device=None):
+    """Replicas: every rank evaluated its own link.  Returns (max-over-ranks step
+    time [ms], channel-evals of all ranks per second, world size).  Works with any
+    initialised torch.distributed backend (NCCL on GPUs, gloo on CPU)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()):
+        return ms_local, evals_local / (ms_local * 1e-3), 1
+    world = dist.get_world_size()
+    t = torch.tensor([ms_local], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    e = torch.tensor([float(evals_local)], dtype=torch.float64, device=device)
+    dist.all_reduce(e, op=dist.ReduceOp.SUM)
+    ms = float(t.item())
+    return ms, float(e.item()) / (ms * 1e-3), world
+
+
 # --------------------------------------------------------------------------- oracle timing
 
 def oracle_rate(wl, target_s: float, seed: int = 0):
@@ -281,12 +300,7 @@ def main():
         dist.barrier()
     clocks = smi.stop()
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
-    ms = statistics.mean(step_ms)
-    if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * n_ch / (ms * 1e-3)
+    ms, value, _ = aggregate_ranks(statistics.mean(step_ms), n_ch, device="cuda")
 
     # dominant kernel: the D/G/H integrator pass
     dgh_ms = statistics.mean(s["integrate_dgh"] for s in stage)
@@ -323,15 +337,12 @@ def main():
     for _ in range(e2e_steps):
         ln2.set_wdm(*(host_in[k].numpy() for k in ("c", "r", "p", "phi", "psi")), wl.rolloff)
         e_host, _ = ln2.nli_eta(hopts)
-    e2e_s = (time.perf_counter() - t0) / e2e_steps
-    if world > 1:
-        t = torch.tensor([e2e_s], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_ms, e2e_value, _ = aggregate_ranks(1e3 * (time.perf_counter() - t0) / e2e_steps, n_ch, device="cuda")
+    e2e_s = e2e_ms * 1e-3
     n_rows = n_ch * n_ch
     h2d = 5 * n_ch * 8 + 6 * n_ch * 8 + 2 * K * 8 + 2 * K * 4  # inputs + channel table + segment tables
     d2h = 3 * (n_rows + 1) * 4 + 2 * n_ch * 8 + 4             # island counts + eta, P_NLI + status
-    e2e = {"value": world * n_ch / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+    e2e = {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
            "ms_per_step": e2e_s * 1e3, "api": "egn_set_wdm + egn_nli_eta (host buffers)"}
     ln2.close()
 

@@ -27,7 +27,9 @@
  *     P_tot = sum of the launch powers.
  *   - Spans: every span is restored by an ideal amplifier (the gain/ISRS
  *     products of Eq. 22 equal 1).  Identical spans use the closed-form
- *     phased-array sum of Eq. 22.
+ *     phased-array sum of Eq. 22; a link whose spans differ (at most 4
+ *     distinct span types, at most 64 spans) sums Eq. 22 span by span with
+ *     one mu per span type and the accumulated dispersion phase.
  *   - Pulse spectra: raised cosine |S(f)|^2 = h(f)/R^2 with roll-off
  *     `rolloff`; the COI integral over f is R times the value at the COI
  *     centre (white NLI over the channel).
@@ -114,9 +116,10 @@ typedef struct {
 } egn_opts;
 
 /* Create a link from n_spans >= 1 spans (copied).  Returns EGN_E_INVALID_ARG on
- * bad parameters.  egn_nli_eta evaluates links of identical spans (the
- * phased-array form of Eq. 22); a link whose spans differ is accepted here and
- * refused by the evaluation calls with EGN_E_UNSUPPORTED. */
+ * bad parameters.  Identical spans use the phased-array closed form of Eq. 22;
+ * spans that differ (fibre or length) use the explicit coherent sum of Eq. 22,
+ * for at most 4 distinct span types and 64 spans (larger heterogeneous links are
+ * refused by the evaluation calls with EGN_E_UNSUPPORTED). */
 egn_status egn_link_create(const egn_span* spans, int n_spans, egn_link** out);
 
 /* Release the link and its device tables.  NULL is ignored. */

@@ -64,6 +64,8 @@ struct DevBuf {
 struct egn_link {
   std::vector<egn_span> spans_si;
   bool identical = true;
+  std::vector<egn_span> type_si;      // distinct span types, in order of first appearance
+  std::vector<unsigned char> span_type;
   // comb (internal units)
   int n_ch = 0;
   double fc_hz = 0, btot = 0, ptot = 0, rolloff = 0;
@@ -78,6 +80,7 @@ struct egn_link {
   int tab_gl = -1;
   int K = 0;
   egn::Span span{};
+  egn::SpanType types[egn::kMaxTypes] = {};
   DevBuf d_seg, d_gl;
   egn::SegmentTables seg{};
   egn::GlTables gl{};
@@ -224,10 +227,19 @@ egn_status check_opts(const egn_link* l, const egn_opts* o) {
     return fail(EGN_E_INVALID_ARG, "unknown precision %d", o->precision);
   if (o->terms != EGN_TERMS_GN && o->terms != EGN_TERMS_EGN) return fail(EGN_E_INVALID_ARG, "unknown terms %d", o->terms);
   if (o->timeout_ms < 0) return fail(EGN_E_INVALID_ARG, "timeout_ms < 0");
-  if (!l->identical) return fail(EGN_E_UNSUPPORTED, "spans differ: only identical spans are evaluated");
-  double L = l->spans_si[0].length_m * 1e-3;
-  double kk = std::ceil(L / o->dz_km);
-  if (kk > kMaxK) return fail(EGN_E_INVALID_ARG, "K = ceil(L/dz) = %.0f exceeds %d", kk, kMaxK);
+  if (!l->identical) {
+    if ((int)l->type_si.size() > kMaxTypes || (int)l->spans_si.size() > kMaxSpans)
+      return fail(EGN_E_UNSUPPORTED, "heterogeneous links are limited to %d span types and %d spans", kMaxTypes,
+                  kMaxSpans);
+  }
+  double ksum = 0.0;
+  for (const egn_span& t : l->type_si) {
+    double kk = std::ceil(t.length_m * 1e-3 / o->dz_km);
+    if (kk > kMaxK) return fail(EGN_E_INVALID_ARG, "K = ceil(L/dz) = %.0f exceeds %d", kk, kMaxK);
+    ksum += kk;
+  }
+  if (!l->identical && ksum > kMaxKSum)
+    return fail(EGN_E_INVALID_ARG, "the span types need %.0f segments in all, more than %d", ksum, kMaxKSum);
   if (o->terms == EGN_TERMS_EGN && l->mixed_rates && l->any_corr)
     return fail(EGN_E_UNSUPPORTED, "EGN corrections with mixed symbol rates are not defined");
   return EGN_OK;
@@ -246,37 +258,56 @@ struct DeviceGuard {
 // (Re)build the segment and Gauss-Legendre tables for these options.
 egn_status ensure_tables(egn_link* l, const egn_opts* o) {
   if (l->tab_dz != o->dz_km) {
-    Span s = to_internal(l->spans_si[0], l->fc_hz);
-    int K = (int)std::ceil(s.L / o->dz_km);
-    if (K < 1) K = 1;
-    std::vector<double> zeta(K), ck(K);
-    std::vector<float> zf(K), cf(K);
-    for (int k = 0; k < K; ++k) {
-      double z = (k + 0.5) / K * s.L;
-      double leff = -std::expm1(-s.alpha * z) / s.alpha;
-      zeta[k] = l->ptot * s.cr * leff;
-      double x = l->btot * zeta[k];
-      ck[k] = (x == 0.0) ? 1.0 : x / (2.0 * std::sinh(0.5 * x));
-      zf[k] = (float)(zeta[k] * 1.4426950408889634);  // log2(e)
-      cf[k] = (float)ck[k];
+    const int nt = (int)l->type_si.size();
+    Span sp[kMaxTypes];
+    int Ks[kMaxTypes];
+    size_t bytes = 0;
+    for (int t = 0; t < nt && t < kMaxTypes; ++t) {
+      sp[t] = to_internal(l->type_si[t], l->fc_hz);
+      Ks[t] = std::max(1, (int)std::ceil(sp[t].L / o->dz_km));
+      bytes += align256(Ks[t] * sizeof(double)) * 2 + align256(Ks[t] * sizeof(float)) * 2;
     }
-    size_t bytes = align256(K * sizeof(double)) * 2 + align256(K * sizeof(float)) * 2;
     EGN_CUDA(l->d_seg.ensure(bytes));
     char* p = (char*)l->d_seg.p;
-    EGN_CUDA(cudaMemcpy(p, zeta.data(), K * sizeof(double), cudaMemcpyHostToDevice));
-    l->seg.zeta = (const double*)p;
-    p += align256(K * sizeof(double));
-    EGN_CUDA(cudaMemcpy(p, ck.data(), K * sizeof(double), cudaMemcpyHostToDevice));
-    l->seg.ck = (const double*)p;
-    p += align256(K * sizeof(double));
-    EGN_CUDA(cudaMemcpy(p, zf.data(), K * sizeof(float), cudaMemcpyHostToDevice));
-    l->seg.zeta_f = (const float*)p;
-    p += align256(K * sizeof(float));
-    EGN_CUDA(cudaMemcpy(p, cf.data(), K * sizeof(float), cudaMemcpyHostToDevice));
-    l->seg.ck_f = (const float*)p;
-    l->seg.K = K;
-    l->K = K;
-    l->span = s;
+    for (int t = 0; t < nt && t < kMaxTypes; ++t) {
+      const Span& s = sp[t];
+      const int K = Ks[t];
+      std::vector<double> zeta(K), ck(K);
+      std::vector<float> zf(K), cf(K);
+      for (int k = 0; k < K; ++k) {
+        double z = (k + 0.5) / K * s.L;
+        double leff = -std::expm1(-s.alpha * z) / s.alpha;
+        zeta[k] = l->ptot * s.cr * leff;
+        double x = l->btot * zeta[k];
+        ck[k] = (x == 0.0) ? 1.0 : x / (2.0 * std::sinh(0.5 * x));
+        zf[k] = (float)(zeta[k] * 1.4426950408889634);  // log2(e)
+        cf[k] = (float)ck[k];
+      }
+      SpanType& ty = l->types[t];
+      ty.alpha = s.alpha;
+      ty.beta2 = s.beta2;
+      ty.beta3 = s.beta3;
+      ty.gamma = s.gamma;
+      ty.L = s.L;
+      ty.dz = s.L / K;
+      ty.r = std::exp(-s.alpha * ty.dz);
+      ty.seg.K = K;
+      EGN_CUDA(cudaMemcpy(p, zeta.data(), K * sizeof(double), cudaMemcpyHostToDevice));
+      ty.seg.zeta = (const double*)p;
+      p += align256(K * sizeof(double));
+      EGN_CUDA(cudaMemcpy(p, ck.data(), K * sizeof(double), cudaMemcpyHostToDevice));
+      ty.seg.ck = (const double*)p;
+      p += align256(K * sizeof(double));
+      EGN_CUDA(cudaMemcpy(p, zf.data(), K * sizeof(float), cudaMemcpyHostToDevice));
+      ty.seg.zeta_f = (const float*)p;
+      p += align256(K * sizeof(float));
+      EGN_CUDA(cudaMemcpy(p, cf.data(), K * sizeof(float), cudaMemcpyHostToDevice));
+      ty.seg.ck_f = (const float*)p;
+      p += align256(K * sizeof(float));
+    }
+    l->seg = l->types[0].seg;
+    l->K = l->types[0].seg.K;
+    l->span = sp[0];
     l->tab_dz = o->dz_km;
   }
   if (l->tab_gl != o->gl_order) {
@@ -365,6 +396,9 @@ LinkParams link_params(const egn_link* l, const egn_opts* o, int all_terms) {
   p.terms = o->terms;
   p.all_terms = all_terms;
   p.fp32c_kp = l->fp32c_kp;
+  p.n_types = l->identical ? 1 : (int)l->type_si.size();
+  for (int t = 0; t < p.n_types && t < kMaxTypes; ++t) p.types[t] = l->types[t];
+  for (int s = 0; s < (int)l->span_type.size() && s < kMaxSpans; ++s) p.span_type[s] = l->span_type[s];
   return p;
 }
 
@@ -500,8 +534,13 @@ egn_status egn_link_create(const egn_span* spans, int n_spans, egn_link** out) {
   egn_link* l = new (std::nothrow) egn_link();
   if (!l) return fail(EGN_E_NOMEM, "out of host memory");
   l->spans_si.assign(spans, spans + n_spans);
-  for (int i = 1; i < n_spans; ++i)
+  for (int i = 0; i < n_spans; ++i) {
     if (std::memcmp(&spans[i], &spans[0], sizeof(egn_span)) != 0) l->identical = false;
+    int t = 0;
+    while (t < (int)l->type_si.size() && std::memcmp(&spans[i], &l->type_si[t], sizeof(egn_span)) != 0) ++t;
+    if (t == (int)l->type_si.size()) l->type_si.push_back(spans[i]);
+    l->span_type.push_back((unsigned char)std::min(t, 255));
+  }
   *out = l;
   return EGN_OK;
 }
@@ -814,15 +853,23 @@ extern "C" egn_status egn_nli_eta_static(egn_link* l, const egn_opts* o, double*
   if (s != EGN_OK) return s;
 
   // link tables for these options, built on the host stack (no heap, no device allocation)
-  const Span sp = to_internal(l->spans_si[0], l->fc_hz);
-  const int K = std::max(1, (int)std::ceil(sp.L / o->dz_km));
+  const int nt = l->identical ? 1 : (int)l->type_si.size();
+  Span sps[kMaxTypes];
+  int Ks[kMaxTypes];
+  size_t o_zeta[kMaxTypes], o_ck[kMaxTypes], o_zf[kMaxTypes], o_cf[kMaxTypes];
+  size_t off = 0;
+  for (int t = 0; t < nt; ++t) {
+    sps[t] = to_internal(l->type_si[t], l->fc_hz);
+    Ks[t] = std::max(1, (int)std::ceil(sps[t].L / o->dz_km));
+    o_zeta[t] = off; off += align256(Ks[t] * sizeof(double));
+    o_ck[t] = off;   off += align256(Ks[t] * sizeof(double));
+    o_zf[t] = off;   off += align256(Ks[t] * sizeof(float));
+    o_cf[t] = off;   off += align256(Ks[t] * sizeof(float));
+  }
+  const Span& sp = sps[0];
+  const int K = Ks[0];
   const int n = o->gl_order;
   const int ord[4] = {0, n, (n + 1) / 2, (n + 2) / 3};
-  size_t off = 0;
-  const size_t o_zeta = off; off += align256(K * sizeof(double));
-  const size_t o_ck = off;   off += align256(K * sizeof(double));
-  const size_t o_zf = off;   off += align256(K * sizeof(float));
-  const size_t o_cf = off;   off += align256(K * sizeof(float));
   size_t o_gl[4][7] = {};
   for (int p = 1; p <= 3; ++p) {
     for (int a = 0; a < 2; ++a) { o_gl[p][a] = off; off += align256(ord[p] * sizeof(double)); }
@@ -839,19 +886,24 @@ extern "C" egn_status egn_nli_eta_static(egn_link* l, const egn_opts* o, double*
   {
     double zeta[kMaxK], ck[kMaxK];
     float zf[kMaxK], cf[kMaxK];
-    for (int k = 0; k < K; ++k) {
-      double z = (k + 0.5) / K * sp.L;
-      double leff = -std::expm1(-sp.alpha * z) / sp.alpha;
-      zeta[k] = l->ptot * sp.cr * leff;
-      double x = l->btot * zeta[k];
-      ck[k] = (x == 0.0) ? 1.0 : x / (2.0 * std::sinh(0.5 * x));
-      zf[k] = (float)(zeta[k] * 1.4426950408889634);
-      cf[k] = (float)ck[k];
+    for (int t = 0; t < nt; ++t) {
+      const Span& st_ = sps[t];
+      const int Kt = Ks[t];
+      for (int k = 0; k < Kt; ++k) {
+        double z = (k + 0.5) / Kt * st_.L;
+        double leff = -std::expm1(-st_.alpha * z) / st_.alpha;
+        zeta[k] = l->ptot * st_.cr * leff;
+        double x = l->btot * zeta[k];
+        ck[k] = (x == 0.0) ? 1.0 : x / (2.0 * std::sinh(0.5 * x));
+        zf[k] = (float)(zeta[k] * 1.4426950408889634);
+        cf[k] = (float)ck[k];
+      }
+      // pageable source: each copy has left the stack buffers before it returns
+      EGN_CUDA(cudaMemcpyAsync(b + o_zeta[t], zeta, Kt * sizeof(double), cudaMemcpyHostToDevice, st));
+      EGN_CUDA(cudaMemcpyAsync(b + o_ck[t], ck, Kt * sizeof(double), cudaMemcpyHostToDevice, st));
+      EGN_CUDA(cudaMemcpyAsync(b + o_zf[t], zf, Kt * sizeof(float), cudaMemcpyHostToDevice, st));
+      EGN_CUDA(cudaMemcpyAsync(b + o_cf[t], cf, Kt * sizeof(float), cudaMemcpyHostToDevice, st));
     }
-    EGN_CUDA(cudaMemcpyAsync(b + o_zeta, zeta, K * sizeof(double), cudaMemcpyHostToDevice, st));
-    EGN_CUDA(cudaMemcpyAsync(b + o_ck, ck, K * sizeof(double), cudaMemcpyHostToDevice, st));
-    EGN_CUDA(cudaMemcpyAsync(b + o_zf, zf, K * sizeof(float), cudaMemcpyHostToDevice, st));
-    EGN_CUDA(cudaMemcpyAsync(b + o_cf, cf, K * sizeof(float), cudaMemcpyHostToDevice, st));
     for (int p = 1; p <= 3; ++p) {
       const int m = ord[p];
       double x[kMaxGl], w[kMaxGl];
@@ -874,11 +926,24 @@ extern "C" egn_status egn_nli_eta_static(egn_link* l, const egn_opts* o, double*
 
   LinkParams p{};
   p.ch = channel_table(l);
-  p.seg.K = K;
-  p.seg.zeta = (const double*)(b + o_zeta);
-  p.seg.ck = (const double*)(b + o_ck);
-  p.seg.zeta_f = (const float*)(b + o_zf);
-  p.seg.ck_f = (const float*)(b + o_cf);
+  p.n_types = nt;
+  for (int t = 0; t < nt; ++t) {
+    SpanType& ty = p.types[t];
+    ty.alpha = sps[t].alpha;
+    ty.beta2 = sps[t].beta2;
+    ty.beta3 = sps[t].beta3;
+    ty.gamma = sps[t].gamma;
+    ty.L = sps[t].L;
+    ty.dz = sps[t].L / Ks[t];
+    ty.r = std::exp(-sps[t].alpha * ty.dz);
+    ty.seg.K = Ks[t];
+    ty.seg.zeta = (const double*)(b + o_zeta[t]);
+    ty.seg.ck = (const double*)(b + o_ck[t]);
+    ty.seg.zeta_f = (const float*)(b + o_zf[t]);
+    ty.seg.ck_f = (const float*)(b + o_cf[t]);
+  }
+  for (int q = 0; q < (int)l->span_type.size() && q < kMaxSpans; ++q) p.span_type[q] = l->span_type[q];
+  p.seg = p.types[0].seg;
   p.gl.n = n;
   p.gl.order[0] = 0;
   for (int q = 1; q <= 3; ++q) {

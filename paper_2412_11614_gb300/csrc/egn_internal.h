@@ -11,7 +11,8 @@ namespace egn {
 constexpr double kPi = 3.141592653589793238462643383279502884;
 constexpr double kC = 299792458.0;  // m/s
 constexpr int kMaxGl = 128;
-constexpr int kMaxK = 896;  // FP64 row tables: 32 lanes x K doubles of shared memory
+constexpr int kMaxK = 896;     // FP64 row tables: 32 lanes x K doubles of shared memory
+constexpr int kMaxKSum = 880;  // heterogeneous links: segments of all span types together
 
 // Internal span: power attenuation [1/km], beta2 at the spectral centre
 // [ps^2/km], beta3 [ps^3/km], gamma [1/W/km], Cr [1/W/km/THz], length [km].
@@ -69,7 +70,21 @@ struct SegmentTables {
   const float* ck_f;    // [K]
 };
 
-// Everything an integrator launch needs, passed by value.
+// Distinct span types of a heterogeneous link (Eq. 22 with different fibres or
+// lengths): at most kMaxTypes types and kMaxSpans spans.
+constexpr int kMaxTypes = 4;
+constexpr int kMaxSpans = 64;
+struct SpanType {
+  double alpha, beta2, beta3, gamma, L;
+  double dz;  // L / K
+  double r;   // e^{-alpha dz}
+  SegmentTables seg;
+};
+
+// Everything an integrator launch needs, passed by value.  With n_types == 1
+// (identical spans) the single-type fields below describe the span and the
+// phased-array closed form of Eq. 22 applies; otherwise types[] and span_type[]
+// give the explicit coherent sum over spans.
 struct LinkParams {
   ChannelTable ch;
   GlTables gl;
@@ -86,6 +101,9 @@ struct LinkParams {
   int terms;         // 0 GN, 1 EGN
   int all_terms;     // evaluate E..H on every island (parity checks)
   int fp32c_kp;      // points per thread of the FP32C D/G/H pass (4 or 8)
+  int n_types;                       // distinct span types (1 = identical spans)
+  SpanType types[kMaxTypes];
+  unsigned char span_type[kMaxSpans];  // type of span s, s = 0 .. n_spans - 1
 };
 
 // Flags of an island (Kronecker deltas of Eq. 15).

@@ -1,0 +1,100 @@
+// fp32c_common.cuh -- device helpers of the FP32 integrators: double-float
+// ("df", an unevaluated FP32 head + tail) arithmetic, packed FP32x2 FMA, exact
+// rounding to an integer, hardware-approximation wrappers, small-angle sine and
+// the raised-cosine shape.
+#pragma once
+
+#include "egn_internal.h"
+
+namespace egn {
+namespace fp32c {
+
+struct Df {
+  float hi, lo;
+};
+
+__device__ __forceinline__ Df df_of(double x) {
+  float h = (float)x;
+  return {h, (float)(x - (double)h)};
+}
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = a + b;
+  float bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+__device__ __forceinline__ Df quick(float s, float e) {
+  float h = s + e;
+  return {h, e - (h - s)};
+}
+__device__ __forceinline__ Df dadd(Df a, Df b) {
+  float s, e;
+  two_sum(a.hi, b.hi, s, e);
+  e += a.lo + b.lo;
+  return quick(s, e);
+}
+__device__ __forceinline__ Df dneg(Df a) { return {-a.hi, -a.lo}; }
+__device__ __forceinline__ Df dsub(Df a, Df b) { return dadd(a, dneg(b)); }
+__device__ __forceinline__ Df dmul(Df a, Df b) {
+  float p = a.hi * b.hi;
+  float e = fmaf(a.hi, b.hi, -p);
+  e = fmaf(a.hi, b.lo, fmaf(a.lo, b.hi, e));
+  return quick(p, e);
+}
+__device__ __forceinline__ Df dhalf(Df a) { return {0.5f * a.hi, 0.5f * a.lo}; }
+__device__ __forceinline__ bool dgt(Df a, Df b) { return a.hi > b.hi || (a.hi == b.hi && a.lo > b.lo); }
+__device__ __forceinline__ Df dmax(Df a, Df b) { return dgt(a, b) ? a : b; }
+__device__ __forceinline__ Df dmin(Df a, Df b) { return dgt(a, b) ? b : a; }
+__device__ __forceinline__ float dval(Df a) { return a.hi + a.lo; }
+
+__device__ __forceinline__ float ex2_approx(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float rcp_approx(float x) {
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+// Packed FP32x2: two lanes of FP32 in one 64-bit register, one FMA instruction
+// for both (fma.rn.f32x2), which halves the issue slots of the segment recurrence.
+typedef unsigned long long f32x2;
+__device__ __forceinline__ f32x2 pack2(float lo, float hi) {
+  f32x2 r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+  return r;
+}
+__device__ __forceinline__ void unpack2(f32x2 v, float& lo, float& hi) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+__device__ __forceinline__ f32x2 ffma2(f32x2 a, f32x2 b, f32x2 c) {
+  f32x2 d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+
+// Round to nearest (ties to even) by adding and subtracting 1.5 * 2^23; exact for
+// |x| < 2^22, two FP32 additions on the FMA pipe.
+__device__ __forceinline__ float rint_fast(float x) {
+  const float M = 12582912.0f;
+  return (x + M) - M;
+}
+
+// sin(x) for |x| < 0.05 by its Taylor series to x^7 (relative error < 1e-12).
+__device__ __forceinline__ float sin_small(float x) {
+  float x2 = x * x;
+  return x * fmaf(x2, fmaf(x2, fmaf(x2, -1.0f / 5040.0f, 1.0f / 120.0f), -1.0f / 6.0f), 1.0f);
+}
+
+// Raised-cosine shape in FP32.
+__device__ __forceinline__ float rc_f(float x, float R, float beta) {
+  float ax = fabsf(x);
+  float a = 0.5f * (1.0f - beta) * R, b = 0.5f * (1.0f + beta) * R;
+  if (ax <= a) return 1.0f;
+  if (ax >= b) return 0.0f;
+  return 0.5f * (1.0f + __cosf(3.14159265f * (ax - a) / (beta * R)));
+}
+
+}  // namespace fp32c
+}  // namespace egn

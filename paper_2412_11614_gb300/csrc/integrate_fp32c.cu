@@ -32,96 +32,18 @@
 //    Hardware sin/cos (MUFU, absolute error ~4e-7 on [-pi, pi]) elsewhere.
 // Island sums: FP32 per thread, fixed-order shuffle and shared-memory trees.
 #include "egn_internal.h"
+#include "fp32c_common.cuh"
 #include "island_geom.cuh"
 
 namespace egn {
 namespace {
 
+using namespace fp32c;
+
 constexpr int kThreads = 128;
 constexpr int kBatch = kThreads;   // islands per batch, one per thread in the set-up
 constexpr int kRowsMax = 64;       // rows per chunk held in shared memory
 constexpr int kTabFloats = 5376;   // DW c_k table budget (21 KB), each c_k stored twice (f32x2)
-
-// ---------------------------------------------------------------- double-float
-struct Df {
-  float hi, lo;
-};
-
-__device__ __forceinline__ Df df_of(double x) {
-  float h = (float)x;
-  return {h, (float)(x - (double)h)};
-}
-__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
-  s = a + b;
-  float bb = s - a;
-  e = (a - (s - bb)) + (b - bb);
-}
-__device__ __forceinline__ Df quick(float s, float e) {
-  float h = s + e;
-  return {h, e - (h - s)};
-}
-__device__ __forceinline__ Df dadd(Df a, Df b) {
-  float s, e;
-  two_sum(a.hi, b.hi, s, e);
-  e += a.lo + b.lo;
-  return quick(s, e);
-}
-__device__ __forceinline__ Df dneg(Df a) { return {-a.hi, -a.lo}; }
-__device__ __forceinline__ Df dsub(Df a, Df b) { return dadd(a, dneg(b)); }
-__device__ __forceinline__ Df dmul(Df a, Df b) {
-  float p = a.hi * b.hi;
-  float e = fmaf(a.hi, b.hi, -p);
-  e = fmaf(a.hi, b.lo, fmaf(a.lo, b.hi, e));
-  return quick(p, e);
-}
-__device__ __forceinline__ Df dhalf(Df a) { return {0.5f * a.hi, 0.5f * a.lo}; }
-__device__ __forceinline__ bool dgt(Df a, Df b) { return a.hi > b.hi || (a.hi == b.hi && a.lo > b.lo); }
-__device__ __forceinline__ Df dmax(Df a, Df b) { return dgt(a, b) ? a : b; }
-__device__ __forceinline__ Df dmin(Df a, Df b) { return dgt(a, b) ? b : a; }
-__device__ __forceinline__ float dval(Df a) { return a.hi + a.lo; }
-
-__device__ __forceinline__ float ex2_approx(float x) {
-  float y;
-  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-  return y;
-}
-__device__ __forceinline__ float rcp_approx(float x) {
-  float y;
-  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-  return y;
-}
-
-// Packed FP32x2: two lanes of FP32 in one 64-bit register, one FMA instruction
-// for both (fma.rn.f32x2), which halves the issue slots of the segment recurrence.
-typedef unsigned long long f32x2;
-__device__ __forceinline__ f32x2 pack2(float lo, float hi) {
-  f32x2 r;
-  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
-  return r;
-}
-__device__ __forceinline__ void unpack2(f32x2 v, float& lo, float& hi) {
-  asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
-}
-__device__ __forceinline__ f32x2 ffma2(f32x2 a, f32x2 b, f32x2 c) {
-  f32x2 d;
-  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
-  return d;
-}
-
-// sin(x) for |x| < 0.05 by its Taylor series to x^7 (relative error < 1e-12).
-__device__ __forceinline__ float sin_small(float x) {
-  float x2 = x * x;
-  return x * fmaf(x2, fmaf(x2, fmaf(x2, -1.0f / 5040.0f, 1.0f / 120.0f), -1.0f / 6.0f), 1.0f);
-}
-
-// Raised-cosine shape in FP32.
-__device__ __forceinline__ float rc_f(float x, float R, float beta) {
-  float ax = fabsf(x);
-  float a = 0.5f * (1.0f - beta) * R, b = 0.5f * (1.0f + beta) * R;
-  if (ax <= a) return 1.0f;
-  if (ax >= b) return 0.0f;
-  return 0.5f * (1.0f + __cosf(3.14159265f * (ax - a) / (beta * R)));
-}
 
 // ---------------------------------------------------------------- shared state
 struct BatchSm {  // one entry per island of the batch
@@ -150,6 +72,126 @@ struct NodeSm {
   float4 x4[kMaxGl];
   float2 x2[kMaxGl];
 };
+
+// Batch set-up (FP64, one island per thread): node-rule geometry and island
+// constants of item b0 + tid, rounded to double-floats.
+template <int ORD>
+__device__ __forceinline__ void batch_setup(const LinkParams& p, const uint64_t* __restrict__ keys,
+                                            const uint32_t* __restrict__ list, long long n_items, long long b0,
+                                            BatchSm& bs, int tid) {
+    long long it = b0 + tid;
+    int np = 0, flags = 0;
+    long long isl = -1;
+    if (it < n_items) {
+      isl = list ? (long long)list[it] : it;
+      int coi, n1, n2, n3;
+      unpack_key(keys[isl], coi, n1, n2, n3);
+      const ChannelTable& ch = p.ch;
+      double nu = ch.nu[coi], nu1 = ch.nu[n1], nu2 = ch.nu[n2], nu3 = ch.nu[n3];
+      double R = ch.R[coi], R1 = ch.R[n1], R2 = ch.R[n2], R3 = ch.R[n3];
+      double d = (nu1 - nu) + (nu2 - nu3);
+      Ordering g = make_ordering(ORD, ch.W[n1], ch.W[n2], ch.W[n3], d);
+      double e[4];
+      np = outer_panels(g, e);
+      for (int q_ = 0; q_ < 3; ++q_) {
+        double pm = 0.0, ph = 0.0;
+        if (q_ < np) { pm = 0.5 * (e[q_] + e[q_ + 1]); ph = 0.5 * (e[q_ + 1] - e[q_]); }
+        bs.pm[q_][tid] = df_of(pm);
+        bs.ph[q_][tid] = df_of(ph);
+      }
+      bs.Bv[tid] = df_of(g.B);
+      bs.Cv[tid] = df_of(g.C);
+      bs.cv[tid] = df_of(g.c);
+      bs.F1[tid] = df_of(nu1 - nu);
+      bs.F2[tid] = df_of(nu2 - nu);
+      bs.S12[tid] = df_of(nu1 + nu2);
+      bs.dd[tid] = df_of(d);
+      bs.R1[tid] = (float)R1;
+      bs.R2[tid] = (float)R2;
+      bs.R3[tid] = (float)R3;
+      bs.nu3[tid] = (float)nu3;
+      double cf[5];
+      term_coefs(R, R1, R2, R3, cf);
+      if (ORD == ORD_DW) {
+        bool wg = p.all_terms || (p.terms && flag_g(n1, n2, n3));
+        bool wh = p.all_terms || (p.terms && flag_h(n1, n2, n3));
+        flags = (wg ? 1 : 0) | (wh ? 2 : 0);
+        bs.cf0[tid] = (float)cf[0];
+        bs.cf1[tid] = (float)cf[3];
+        bs.cf2[tid] = (float)cf[4];
+      } else {
+        bs.cf0[tid] = (float)(ORD == ORD_E ? cf[1] : cf[2]);
+      }
+    }
+    bs.isl[tid] = isl;
+    bs.np[tid] = np;
+    bs.flags[tid] = flags;
+  }
+
+// Row geometry in double-float: outer node o, inner interval im +- ih and the
+// linear forms f1 - f = a0 + a1 x, f2 - f = b0 + b1 x, f1 + f2 = s0 + s1 x of the
+// inner Gauss-Legendre coordinate x (frequencies relative to the spectral centre).
+struct RowGeo {
+  Df o, im, ih, a0, a1, b0, b1, s0, s1, ph;
+};
+
+template <int ORD>
+__device__ __forceinline__ RowGeo row_geometry(const LinkParams& p, const BatchSm& bs, int ib, int np, int pi,
+                                               int i) {
+  RowGeo r;
+  const Df y = {p.gl.xh[np][i], p.gl.xl[np][i]};
+  const Df pm = bs.pm[pi][ib];
+  r.ph = bs.ph[pi][ib];
+  r.o = dadd(pm, dmul(r.ph, y));
+  const Df m = (ORD == ORD_DW) ? dadd(r.o, bs.cv[ib]) : dsub(bs.cv[ib], r.o);
+  const Df Bv = bs.Bv[ib], Cv = bs.Cv[ib];
+  const Df lo = dmax(dneg(Bv), dsub(m, Cv));
+  const Df hi = dmin(Bv, dadd(m, Cv));
+  r.im = dhalf(dadd(lo, hi));
+  r.ih = dhalf(dsub(hi, lo));
+  const Df zero = {0.0f, 0.0f};
+  r.a1 = zero;
+  r.b1 = zero;
+  r.s1 = zero;
+  if (ORD == ORD_DW) {  // w = o, u = im + ih x, v = w - u - d
+    r.a0 = dadd(bs.F1[ib], r.im); r.a1 = r.ih;
+    r.b0 = dadd(bs.F2[ib], dsub(dsub(r.o, r.im), bs.dd[ib])); r.b1 = dneg(r.ih);
+    r.s0 = dadd(bs.S12[ib], dsub(r.o, bs.dd[ib]));
+  } else if (ORD == ORD_E) {  // v = o, u = im + ih x
+    r.a0 = dadd(bs.F1[ib], r.im); r.a1 = r.ih;
+    r.b0 = dadd(bs.F2[ib], r.o);
+    r.s0 = dadd(bs.S12[ib], dadd(r.im, r.o)); r.s1 = r.ih;
+  } else {  // u = o, v = im + ih x
+    r.a0 = dadd(bs.F1[ib], r.o);
+    r.b0 = dadd(bs.F2[ib], r.im); r.b1 = r.ih;
+    r.s0 = dadd(bs.S12[ib], dadd(r.o, r.im)); r.s1 = r.ih;
+  }
+  return r;
+}
+
+// Phase polynomial of a row for one span type, in turns of that span:
+// Theta(x) = Q0 + Q1 x + Q2 x^2 + Q3 x^3 with Q0 reduced modulo K.
+// G0 = 2 pi L beta2, G1 = 2 pi^2 L beta3 (double-floats).
+struct RowPhase {
+  Df Q0r, Q1, Q2;
+  float Q3;
+};
+
+__device__ __forceinline__ RowPhase row_phase(const RowGeo& r, Df G0, Df G1, float Kf, float invK) {
+  const Df g0 = dadd(G0, dmul(G1, r.s0));   // 2 pi L (beta2 + pi beta3 s0)
+  const Df g1 = dmul(G1, r.s1);             // 2 pi L pi beta3 s1
+  const Df ab0 = dmul(r.a0, r.b0);
+  const Df ab1 = dadd(dmul(r.a0, r.b1), dmul(r.a1, r.b0));
+  const Df ab2 = dmul(r.a1, r.b1);
+  const Df Q0 = dmul(g0, ab0);
+  RowPhase q;
+  q.Q1 = dadd(dmul(g0, ab1), dmul(g1, ab0));
+  q.Q2 = dadd(dmul(g0, ab2), dmul(g1, ab1));
+  q.Q3 = dval(g1) * dval(ab2);
+  const float r0 = fmaf(-Kf, rint_fast(Q0.hi * invK), Q0.hi);  // the FMA residual is exact
+  q.Q0r = quick(r0, Q0.lo);
+  return q;
+}
 
 template <int ORD, int KP>
 __global__ void __launch_bounds__(kThreads, KP == 8 ? 3 : 4)
@@ -195,55 +237,7 @@ integrate_fp32c_kernel(LinkParams p, const uint64_t* __restrict__ keys, const ui
 
   for (long long b0 = (long long)blockIdx.x * kBatch; b0 < n_items; b0 += (long long)gridDim.x * kBatch) {
     // ---------------- 1. batch set-up, FP64, one island per thread
-    {
-      long long it = b0 + tid;
-      int np = 0, flags = 0;
-      long long isl = -1;
-      if (it < n_items) {
-        isl = list ? (long long)list[it] : it;
-        int coi, n1, n2, n3;
-        unpack_key(keys[isl], coi, n1, n2, n3);
-        const ChannelTable& ch = p.ch;
-        double nu = ch.nu[coi], nu1 = ch.nu[n1], nu2 = ch.nu[n2], nu3 = ch.nu[n3];
-        double R = ch.R[coi], R1 = ch.R[n1], R2 = ch.R[n2], R3 = ch.R[n3];
-        double d = (nu1 - nu) + (nu2 - nu3);
-        Ordering g = make_ordering(ORD, ch.W[n1], ch.W[n2], ch.W[n3], d);
-        double e[4];
-        np = outer_panels(g, e);
-        for (int q_ = 0; q_ < 3; ++q_) {
-          double pm = 0.0, ph = 0.0;
-          if (q_ < np) { pm = 0.5 * (e[q_] + e[q_ + 1]); ph = 0.5 * (e[q_ + 1] - e[q_]); }
-          bs.pm[q_][tid] = df_of(pm);
-          bs.ph[q_][tid] = df_of(ph);
-        }
-        bs.Bv[tid] = df_of(g.B);
-        bs.Cv[tid] = df_of(g.C);
-        bs.cv[tid] = df_of(g.c);
-        bs.F1[tid] = df_of(nu1 - nu);
-        bs.F2[tid] = df_of(nu2 - nu);
-        bs.S12[tid] = df_of(nu1 + nu2);
-        bs.dd[tid] = df_of(d);
-        bs.R1[tid] = (float)R1;
-        bs.R2[tid] = (float)R2;
-        bs.R3[tid] = (float)R3;
-        bs.nu3[tid] = (float)nu3;
-        double cf[5];
-        term_coefs(R, R1, R2, R3, cf);
-        if (ORD == ORD_DW) {
-          bool wg = p.all_terms || (p.terms && flag_g(n1, n2, n3));
-          bool wh = p.all_terms || (p.terms && flag_h(n1, n2, n3));
-          flags = (wg ? 1 : 0) | (wh ? 2 : 0);
-          bs.cf0[tid] = (float)cf[0];
-          bs.cf1[tid] = (float)cf[3];
-          bs.cf2[tid] = (float)cf[4];
-        } else {
-          bs.cf0[tid] = (float)(ORD == ORD_E ? cf[1] : cf[2]);
-        }
-      }
-      bs.isl[tid] = isl;
-      bs.np[tid] = np;
-      bs.flags[tid] = flags;
-    }
+    batch_setup<ORD>(p, keys, list, n_items, b0, bs, tid);
     __syncthreads();
     const int nb = (int)min((long long)kBatch, n_items - b0);
     // ---------------- 2./3. the islands of the batch, one after the other
@@ -266,47 +260,18 @@ integrate_fp32c_kernel(LinkParams p, const uint64_t* __restrict__ keys, const ui
           if (rr < rc) {
             const int row = c0 + rr;
             const int pi = row / no, i = row - pi * no;
-            const Df y = {p.gl.xh[np][i], p.gl.xl[np][i]};
-            const Df pm = bs.pm[pi][ib], ph = bs.ph[pi][ib];
-            const Df o = dadd(pm, dmul(ph, y));
-            const Df m = (ORD == ORD_DW) ? dadd(o, bs.cv[ib]) : dsub(bs.cv[ib], o);
-            const Df Bv = bs.Bv[ib], Cv = bs.Cv[ib];
-            const Df lo = dmax(dneg(Bv), dsub(m, Cv));
-            const Df hi = dmin(Bv, dadd(m, Cv));
-            const Df im = dhalf(dadd(lo, hi)), ih = dhalf(dsub(hi, lo));
-            const Df zero = {0.0f, 0.0f};
-            Df a0, b0_, s0, a1 = zero, b1 = zero, s1 = zero;
-            if (ORD == ORD_DW) {  // w = o, u = im + ih x, v = w - u - d
-              a0 = dadd(bs.F1[ib], im); a1 = ih;
-              b0_ = dadd(bs.F2[ib], dsub(dsub(o, im), bs.dd[ib])); b1 = dneg(ih);
-              s0 = dadd(bs.S12[ib], dsub(o, bs.dd[ib]));
-            } else if (ORD == ORD_E) {  // v = o, u = im + ih x
-              a0 = dadd(bs.F1[ib], im); a1 = ih;
-              b0_ = dadd(bs.F2[ib], o);
-              s0 = dadd(bs.S12[ib], dadd(im, o)); s1 = ih;
-            } else {  // u = o, v = im + ih x
-              a0 = dadd(bs.F1[ib], o);
-              b0_ = dadd(bs.F2[ib], im); b1 = ih;
-              s0 = dadd(bs.S12[ib], dadd(o, im)); s1 = ih;
-            }
-            const Df g0 = dadd(G0, dmul(G1, s0));   // 2 pi L (beta2 + pi beta3 s0)
-            const Df g1 = dmul(G1, s1);             // 2 pi L pi beta3 s1
-            const Df ab0 = dmul(a0, b0_);
-            const Df ab1 = dadd(dmul(a0, b1), dmul(a1, b0_));
-            const Df ab2 = dmul(a1, b1);
-            const Df Q0 = dmul(g0, ab0);
-            const Df Q1 = dadd(dmul(g0, ab1), dmul(g1, ab0));
-            const Df Q2 = dadd(dmul(g0, ab2), dmul(g1, ab1));
-            const float Q3 = dval(g1) * dval(ab2);
-            // Q0 modulo K (the FMA residual is exact)
-            const float r0 = fmaf(-Kf, rintf(Q0.hi * invK), Q0.hi);
-            const Df Q0r = quick(r0, Q0.lo);
+            const RowGeo g = row_geometry<ORD>(p, bs, ib, np, pi, i);
+            const RowPhase q = row_phase(g, G0, G1, Kf, invK);
+            const Df Q0r = q.Q0r, Q1 = q.Q1, Q2 = q.Q2;
+            const float Q3 = q.Q3;
+            const Df a0 = g.a0, a1 = g.a1, b0_ = g.b0, b1 = g.b1, s0 = g.s0, s1 = g.s1, im = g.im, ih = g.ih, o = g.o,
+                     ph = g.ph;
             const float s0f = dval(s0), s1f = dval(s1);
             const float imf = dval(im), ihf = dval(ih), of = dval(o);
             const float wo = dval(ph) * p.gl.wf[np][i];
             const float hout = ORD == ORD_DW ? rc_f(of, R3f, beta) : (ORD == ORD_E ? rc_f(of, R2f, beta) : rc_f(of, R1f, beta));
             rs.qa[rr] = make_float4(Q0r.hi, Q0r.lo, Q1.hi, Q1.lo);
-            rs.qb[rr] = make_float4(Q2.hi, Q2.lo, Q3, Q0r.hi - rintf(Q0r.hi));
+            rs.qb[rr] = make_float4(Q2.hi, Q2.lo, Q3, Q0r.hi - rint_fast(Q0r.hi));
             rs.ab[rr] = make_float4(dval(a0), dval(a1), dval(b0_), dval(b1));
             rs.kc[rr] = make_float4(k4 * fmaf(pib3, s0f, b2f), k4 * pib3 * s1f, imf, ihf);
             rs.ow[rr] = make_float4(ORD == ORD_DW ? of - dfl : of, wo * ihf * hout, wo * ihf, hout);
@@ -355,12 +320,12 @@ integrate_fp32c_kernel(LinkParams p, const uint64_t* __restrict__ keys, const ui
             const float t1 = fmaf(q1h, xl, fmaf(q1l, xh, e1));
             const float p2 = q2h * x2h, e2 = fmaf(q2h, x2h, -p2);
             const float t2 = fmaf(q2h, x2l, fmaf(q2l, x2h, e2));
-            const float r1 = fmaf(-Kf, rintf(p1 * invK), p1);
+            const float r1 = fmaf(-Kf, rint_fast(p1 * invK), p1);
             const float tail = (q0l + t1) + fmaf(q3, xc, t2);
             float th = fmaf((q0h + r1) + p2, invK, tail * invK);
-            th -= rintf(th);                                           // theta (turns)
-            float ph = (fq0 + (r1 - rintf(r1))) + ((p2 - rintf(p2)) + tail);
-            ph -= rintf(ph);                                           // phi (turns)
+            th -= rint_fast(th);                                           // theta (turns)
+            float ph = (fq0 + (r1 - rint_fast(r1))) + ((p2 - rint_fast(p2)) + tail);
+            ph -= rint_fast(ph);                                           // phi (turns)
             // w = r e^{2 pi i th} from the half angle (keeps w - 1 accurate)
             const float ah = pi_f * th;
             const float sh = __sinf(ah), chh = __cosf(ah);
@@ -579,10 +544,361 @@ cudaError_t launch_one(const LinkParams& p, const uint64_t* keys, const uint32_t
   return cudaGetLastError();
 }
 
+
+// ---------------------------------------------------------------------------
+// Links whose spans differ (Eq. 22 written out).  Same node rule, batch set-up
+// and row geometry as above; per row and span type t the phase polynomial and
+// the c_k table; per point mu_t, phi_t for every type and the coherent sum
+// Y = sum_s gamma_t(s) mu_t(s) e^{i Phi_s}, Phi_{s+1} = Phi_s + phi_t(s) (turns,
+// by complex multiplication with e^{2 pi i phi_t}).  Two points per thread,
+// scalar recurrences.
+// ---------------------------------------------------------------------------
+
+constexpr int kGRows = 32;   // rows per chunk, general links
+constexpr int kGTab = 10240; // c_k tables of all types, floats (40 KB)
+
+struct GenTypes {
+  Df G0[kMaxTypes], G1[kMaxTypes];  // 2 pi L_t beta2_t, 2 pi^2 L_t beta3_t
+  int koff[kMaxTypes];              // offset of type t in a table row
+  int ktot;                         // table row stride (floats)
+};
+
+struct GenRowSm {
+  float4 qa[kMaxTypes][kGRows];  // q0h, q0l, q1h, q1l of type t
+  float4 qb[kMaxTypes][kGRows];  // q2h, q2l, q3, frac(q0h)
+  float2 kc[kMaxTypes][kGRows];  // 4 pi^2 (beta2_t + pi beta3_t s0), 4 pi^2 pi beta3_t s1
+  float4 ab[kGRows];             // a0, a1, b0, b1
+  float4 ow[kGRows];             // o - d (DW) or o, wo ih hout, wo ih, hout
+  float4 f3[kGRows];             // f30, f31, wo, im
+  float ih[kGRows];
+};
+
+template <int ORD>
+__global__ void __launch_bounds__(kThreads, 3)
+integrate_fp32c_general_kernel(LinkParams p, const uint64_t* __restrict__ keys, const uint32_t* __restrict__ list,
+                               long long n_items, float* __restrict__ terms, long long n_isl, int rows_per_chunk,
+                               GenTypes gt) {
+  constexpr int KP = 2;
+  __shared__ BatchSm bs;
+  __shared__ GenRowSm rs;
+  __shared__ NodeSm ns;
+  __shared__ float red[4][kThreads / 32];
+  __shared__ float tyf[kMaxTypes][6];  // K, 1/K, alpha, r, 1 - r, gamma
+  extern __shared__ __align__(16) float tabg[];  // [rows_per_chunk][ktot]
+
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const int n = p.gl.n;
+  const int T = p.n_types;
+  const float beta = (float)p.rolloff;
+  const float k4 = (float)(4.0 * kPi * kPi);
+  const float pi_f = 3.14159265358979f;
+  int tpr = 1;
+  while (tpr * KP < n) tpr <<= 1;
+  const int rows_per_pass = kThreads / tpr;
+  const int lr = tid & (tpr - 1);
+  const int rsub = tid / tpr;
+  for (int j = tid; j < n; j += kThreads) {
+    const float xh = p.gl.xh[1][j], xl = p.gl.xl[1][j];
+    ns.x4[j] = make_float4(xh, xl, p.gl.x2h[1][j], p.gl.x2l[1][j]);
+    ns.x2[j] = make_float2(xh * p.gl.x2h[1][j], p.gl.wf[1][j]);
+  }
+  if (tid < T) {
+    const SpanType& ty = p.types[tid];
+    tyf[tid][0] = (float)ty.seg.K;
+    tyf[tid][1] = 1.0f / (float)ty.seg.K;
+    tyf[tid][2] = (float)ty.alpha;
+    tyf[tid][3] = (float)ty.r;
+    tyf[tid][4] = (float)(-expm1(-ty.alpha * ty.dz));
+    tyf[tid][5] = (float)ty.gamma;
+  }
+  __syncthreads();
+
+  for (long long b0 = (long long)blockIdx.x * kBatch; b0 < n_items; b0 += (long long)gridDim.x * kBatch) {
+    batch_setup<ORD>(p, keys, list, n_items, b0, bs, tid);
+    __syncthreads();
+    const int nb = (int)min((long long)kBatch, n_items - b0);
+    for (int ib = 0; ib < nb; ++ib) {
+      const int np = bs.np[ib];
+      const int flags = bs.flags[ib];
+      const bool want_g = flags & 1, want_h = flags & 2;
+      const float R1f = bs.R1[ib], R2f = bs.R2[ib], R3f = bs.R3[ib];
+      const float dfl = dval(bs.dd[ib]);
+      float dsum = 0.0f, csum = 0.0f, hre = 0.0f, him = 0.0f;
+      const int no = np > 0 ? p.gl.order[np] : 0;
+      const int rows = np * no;
+      for (int c0 = 0; c0 < rows; c0 += rows_per_chunk) {
+        const int rc = min(rows_per_chunk, rows - c0);
+        // ---- row constants: geometry once, phase per type (slot = row, type)
+        for (int slot = tid; slot < rc * T; slot += kThreads) {
+          const int rr = slot % rc, t = slot / rc;
+          const int row = c0 + rr;
+          const int pi = row / no, i = row - pi * no;
+          const RowGeo g = row_geometry<ORD>(p, bs, ib, np, pi, i);
+          const RowPhase q = row_phase(g, gt.G0[t], gt.G1[t], tyf[t][0], tyf[t][1]);
+          rs.qa[t][rr] = make_float4(q.Q0r.hi, q.Q0r.lo, q.Q1.hi, q.Q1.lo);
+          rs.qb[t][rr] = make_float4(q.Q2.hi, q.Q2.lo, q.Q3, q.Q0r.hi - rint_fast(q.Q0r.hi));
+          const float pib3 = (float)(kPi * p.types[t].beta3);
+          rs.kc[t][rr] = make_float2(k4 * fmaf(pib3, dval(g.s0), (float)p.types[t].beta2), k4 * pib3 * dval(g.s1));
+          if (t == 0) {
+            const float imf = dval(g.im), ihf = dval(g.ih), of = dval(g.o);
+            const float wo = dval(g.ph) * p.gl.wf[np][i];
+            const float hout =
+                ORD == ORD_DW ? rc_f(of, R3f, beta) : (ORD == ORD_E ? rc_f(of, R2f, beta) : rc_f(of, R1f, beta));
+            rs.ab[rr] = make_float4(dval(g.a0), dval(g.a1), dval(g.b0), dval(g.b1));
+            rs.ow[rr] = make_float4(ORD == ORD_DW ? of - dfl : of, wo * ihf * hout, wo * ihf, hout);
+            const float nu3 = bs.nu3[ib];
+            if (ORD == ORD_DW) rs.f3[rr] = make_float4(nu3 + of, 0.0f, wo, imf);
+            else rs.f3[rr] = make_float4(nu3 + (imf + of + dfl), ihf, wo, imf);
+            rs.ih[rr] = ihf;
+          }
+        }
+        __syncthreads();
+        if (ORD == ORD_DW) {  // c_k tables, all types
+          for (int t = 0; t < T; ++t) {
+            const int K = p.types[t].seg.K;
+            for (int k = tid; k < K; k += kThreads) {
+              const float ck = p.types[t].seg.ck_f[k], zk = p.types[t].seg.zeta_f[k];
+              for (int rr = 0; rr < rc; ++rr) tabg[rr * gt.ktot + gt.koff[t] + k] = ck * ex2_approx(-zk * rs.f3[rr].x);
+            }
+          }
+          __syncthreads();
+        }
+        for (int rb = 0; rb < rc; rb += rows_per_pass) {
+          const int rr = rb + rsub;
+          const bool row_ok = rr < rc;
+          const int rrc = row_ok ? rr : 0;
+          const float4 ab = rs.ab[rrc], ow = rs.ow[rrc], f3r = rs.f3[rrc];
+          const float im = f3r.w, ih = rs.ih[rrc];
+          const float wrowh = row_ok ? ow.y : 0.0f, wrow = row_ok ? ow.z : 0.0f;
+          float xh_[KP], wnode_[KP], yre_[KP], yim_[KP];
+          float zre_[KP], zim_[KP];
+#pragma unroll
+          for (int m = 0; m < KP; ++m) {
+            const int j = lr + tpr * m;
+            const bool jok = j < n;
+            xh_[m] = ns.x4[jok ? j : 0].x;
+            wnode_[m] = jok ? ns.x2[j].y : 0.0f;
+            yre_[m] = 0.0f;
+            yim_[m] = 0.0f;
+          }
+          // per span type: mu_t and e^{2 pi i phi_t}, kept for the span sum
+          float mre_[kMaxTypes][KP], mim_[kMaxTypes][KP], ere_[kMaxTypes][KP], eim_[kMaxTypes][KP];
+#pragma unroll
+          for (int t = 0; t < kMaxTypes; ++t) {
+            if (t >= T) break;
+            const float4 qa = rs.qa[t][rrc], qb = rs.qb[t][rrc];
+            const float2 kc = rs.kc[t][rrc];
+            const float Kf = tyf[t][0], invK = tyf[t][1], alpha = tyf[t][2], r = tyf[t][3], omr = tyf[t][4],
+                        gam = tyf[t][5];
+            const int K = (int)Kf;
+            float p_[KP], wm1_[KP], wi_[KP], chi_[KP], b1_[KP], b2_[KP], f3_[KP];
+#pragma unroll
+            for (int m = 0; m < KP; ++m) {
+              const int j = lr + tpr * m;
+              const int jj = j < n ? j : 0;
+              const float4 x4 = ns.x4[jj];
+              const float xh = x4.x, xl = x4.y, x2h = x4.z, x2l = x4.w, xc = ns.x2[jj].x;
+              const float p1 = qa.z * xh, e1 = fmaf(qa.z, xh, -p1);
+              const float t1 = fmaf(qa.z, xl, fmaf(qa.w, xh, e1));
+              const float p2 = qb.x * x2h, e2 = fmaf(qb.x, x2h, -p2);
+              const float t2 = fmaf(qb.x, x2l, fmaf(qb.y, x2h, e2));
+              const float r1 = fmaf(-Kf, rint_fast(p1 * invK), p1);
+              const float tail = (qa.y + t1) + fmaf(qb.z, xc, t2);
+              float th = fmaf((qa.x + r1) + p2, invK, tail * invK);
+              th -= rint_fast(th);
+              float ph = (qb.w + (r1 - rint_fast(r1))) + ((p2 - rint_fast(p2)) + tail);
+              ph -= rint_fast(ph);
+              const float ah = pi_f * th;
+              const float sh = __sinf(ah), chh = __cosf(ah);
+              const float t2r = -2.0f * r * sh;
+              wm1_[m] = fmaf(t2r, sh, -omr);
+              p_[m] = fmaf(2.0f, wm1_[m], 2.0f);
+              wi_[m] = -t2r * chh;
+              chi_[m] = fmaf(ab.y, xh, ab.x) * fmaf(ab.w, xh, ab.z) * fmaf(kc.y, xh, kc.x);
+              const float ang = 2.0f * pi_f * ph;
+              ere_[t][m] = __cosf(ang);
+              eim_[t][m] = __sinf(ang);
+              f3_[m] = fmaf(f3r.y, xh, f3r.x);
+              b1_[m] = 0.0f;
+              b2_[m] = 0.0f;
+            }
+            const float q = r * r;
+            if (ORD == ORD_DW) {
+              const float* trow = tabg + rrc * gt.ktot + gt.koff[t];
+              for (int k = K - 1; k >= 0; --k) {
+                const float c = trow[k];
+#pragma unroll
+                for (int m = 0; m < KP; ++m) {
+                  const float bn = fmaf(-q, b2_[m], fmaf(p_[m], b1_[m], c));
+                  b2_[m] = b1_[m];
+                  b1_[m] = bn;
+                }
+              }
+            } else {
+              for (int k = K - 1; k >= 0; --k) {
+                const float ck = p.types[t].seg.ck_f[k], zk = p.types[t].seg.zeta_f[k];
+#pragma unroll
+                for (int m = 0; m < KP; ++m) {
+                  const float c = ck * ex2_approx(-zk * f3_[m]);
+                  const float bn = fmaf(-q, b2_[m], fmaf(p_[m], b1_[m], c));
+                  b2_[m] = b1_[m];
+                  b1_[m] = bn;
+                }
+              }
+            }
+#pragma unroll
+            for (int m = 0; m < KP; ++m) {
+              const float wm1 = wm1_[m], wi = wi_[m], chi = chi_[m];
+              const float sre = fmaf(-(wm1 + 1.0f), b2_[m], b1_[m]);
+              const float sim = wi * b2_[m];
+              const float inv = rcp_approx(fmaf(chi, chi, alpha * alpha)) * gam;
+              const float qr = fmaf(-alpha, wm1, chi * wi) * inv;
+              const float qi = fmaf(-chi, wm1, -alpha * wi) * inv;
+              mre_[t][m] = fmaf(sre, qr, -sim * qi);  // gamma_t mu_t
+              mim_[t][m] = fmaf(sre, qi, sim * qr);
+            }
+          }
+          // coherent sum over the spans
+#pragma unroll
+          for (int m = 0; m < KP; ++m) {
+            zre_[m] = 1.0f;
+            zim_[m] = 0.0f;
+          }
+          for (int sp = 0; sp < p.n_spans; ++sp) {
+            const int t = p.span_type[sp];
+#pragma unroll
+            for (int m = 0; m < KP; ++m) {
+              float mr = 0.0f, mi = 0.0f, er = 1.0f, ei = 0.0f;
+#pragma unroll
+              for (int u = 0; u < kMaxTypes; ++u)
+                if (u == t) { mr = mre_[u][m]; mi = mim_[u][m]; er = ere_[u][m]; ei = eim_[u][m]; }
+              yre_[m] = fmaf(mr, zre_[m], fmaf(-mi, zim_[m], yre_[m]));
+              yim_[m] = fmaf(mr, zim_[m], fmaf(mi, zre_[m], yim_[m]));
+              const float zr = fmaf(zre_[m], er, -zim_[m] * ei);
+              zim_[m] = fmaf(zre_[m], ei, zim_[m] * er);
+              zre_[m] = zr;
+            }
+          }
+          // weights and sums (Upsilon itself, gamma included)
+          float gre = 0.0f, gim = 0.0f;
+#pragma unroll
+          for (int m = 0; m < KP; ++m) {
+            const float xh = xh_[m];
+            const float tt = fmaf(ih, xh, im);
+            float u, v, h3;
+            if (ORD == ORD_DW) { u = tt; v = ow.x - tt; h3 = 1.0f; }
+            else {
+              if (ORD == ORD_E) { v = ow.x; u = tt; } else { u = ow.x; v = tt; }
+              h3 = rc_f(u + v + dfl, R3f, beta);
+            }
+            const float h1 = rc_f(u, R1f, beta), h2 = rc_f(v, R2f, beta);
+            const float yre = yre_[m], yim = yim_[m];
+            if (ORD == ORD_DW) {
+              dsum = fmaf((wrowh * wnode_[m]) * (h1 * h2), fmaf(yre, yre, yim * yim), dsum);
+              if (want_g) {
+                const float a12 = (row_ok ? wnode_[m] : 0.0f) * sqrtf(h1 * h2);
+                gre = fmaf(a12, yre, gre);
+                gim = fmaf(a12, yim, gim);
+              }
+              if (want_h) {
+                const float a123 = wrow * wnode_[m] * sqrtf(h1 * h2 * ow.w);
+                hre = fmaf(a123, yre, hre);
+                him = fmaf(a123, yim, him);
+              }
+            } else {
+              const float a = (row_ok ? wnode_[m] : 0.0f) * ih * sqrtf(ORD == ORD_E ? h1 * h3 : h2 * h3);
+              gre = fmaf(a, yre, gre);
+              gim = fmaf(a, yim, gim);
+            }
+          }
+          if (ORD != ORD_DW || want_g) {
+            for (int o_ = tpr >> 1; o_ > 0; o_ >>= 1) {
+              gre += __shfl_xor_sync(0xffffffffu, gre, o_);
+              gim += __shfl_xor_sync(0xffffffffu, gim, o_);
+            }
+            if (lr == 0 && row_ok) {
+              const float ihr = (ORD == ORD_DW) ? ih : 1.0f;
+              const float gr_ = gre * ihr, gi_ = gim * ihr;
+              csum = fmaf(f3r.z * ow.w, gr_ * gr_ + gi_ * gi_, csum);
+            }
+          }
+        }
+        __syncthreads();
+      }
+      float vals[4] = {dsum, csum, hre, him};
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+        for (int o_ = 16; o_ > 0; o_ >>= 1) vals[a] += __shfl_xor_sync(0xffffffffu, vals[a], o_);
+      if (lane == 0)
+#pragma unroll
+        for (int a = 0; a < 4; ++a) red[a][wid] = vals[a];
+      __syncthreads();
+      if (tid == 0) {
+        float t[4];
+        for (int a = 0; a < 4; ++a) t[a] = (red[a][0] + red[a][1]) + (red[a][2] + red[a][3]);
+        const long long isl = bs.isl[ib];
+        if (ORD == ORD_DW) {
+          terms[isl] = bs.cf0[ib] * t[0];
+          if (want_g) terms[3 * n_isl + isl] = bs.cf1[ib] * t[1];
+          if (want_h) terms[4 * n_isl + isl] = bs.cf2[ib] * (t[2] * t[2] + t[3] * t[3]);
+        } else {
+          terms[(ORD == ORD_E ? 1 : 2) * n_isl + isl] = bs.cf0[ib] * t[1];
+        }
+      }
+      __syncthreads();
+    }
+  }
+}
+
+template <int ORD>
+cudaError_t launch_general(const LinkParams& p, const uint64_t* keys, const uint32_t* list, long long n_items,
+                           float* terms, long long n_isl, cudaStream_t st) {
+  if (n_items <= 0) return cudaSuccess;
+  GenTypes gt{};
+  int ktot = 0;
+  for (int t = 0; t < p.n_types; ++t) {
+    const SpanType& ty = p.types[t];
+    double g0 = 2.0 * kPi * ty.L * ty.beta2, g1 = 2.0 * kPi * kPi * ty.L * ty.beta3;
+    float g0h = (float)g0, g1h = (float)g1;
+    gt.G0[t] = {g0h, (float)(g0 - (double)g0h)};
+    gt.G1[t] = {g1h, (float)(g1 - (double)g1h)};
+    gt.koff[t] = ktot;
+    ktot += ty.seg.K;
+  }
+  gt.ktot = ktot;
+  int rows = kGRows;
+  if (ORD == ORD_DW) {
+    rows = kGTab / ktot;
+    if (rows > kGRows) rows = kGRows;
+    if (rows < 1) rows = 1;
+  }
+  size_t smem = ORD == ORD_DW ? (size_t)rows * ktot * sizeof(float) : 0;
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  static unsigned long long attr_done = 0;
+  if (!(attr_done >> (dev & 63) & 1ull)) {
+    cudaError_t e = cudaFuncSetAttribute(integrate_fp32c_general_kernel<ORD>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, kGTab * (int)sizeof(float));
+    if (e != cudaSuccess) return e;
+    attr_done |= 1ull << (dev & 63);
+  }
+  long long batches = (n_items + kBatch - 1) / kBatch;
+  long long blocks = (long long)sms * 3;
+  if (blocks > batches) blocks = batches;
+  integrate_fp32c_general_kernel<ORD><<<(unsigned)blocks, kThreads, smem, st>>>(p, keys, list, n_items, terms, n_isl,
+                                                                               rows, gt);
+  return cudaGetLastError();
+}
 }  // namespace
 
 cudaError_t launch_fp32c_pass(int ord, const LinkParams& p, const uint64_t* keys, const uint32_t* list,
                               long long n_items, float* terms, long long n_isl, cudaStream_t st) {
+  if (p.n_types > 1) {
+    if (ord == ORD_DW) return launch_general<ORD_DW>(p, keys, list, n_items, terms, n_isl, st);
+    if (ord == ORD_E) return launch_general<ORD_E>(p, keys, list, n_items, terms, n_isl, st);
+    return launch_general<ORD_F>(p, keys, list, n_items, terms, n_isl, st);
+  }
   if (ord == ORD_DW) {
     if (p.fp32c_kp == 8) return launch_one<ORD_DW, 8>(p, keys, list, n_items, terms, n_isl, st);
     return launch_one<ORD_DW, 4>(p, keys, list, n_items, terms, n_isl, st);

@@ -68,6 +68,49 @@ __device__ __forceinline__ Cd upsilon_fp64(const LinkParams& p, double f1, doubl
   return {g * y.re, g * y.im};
 }
 
+// Upsilon of a link whose spans differ (Eq. 22 written out): mu_t and the span
+// phase phi_t = chi_t L_t of every span type t, then the coherent sum
+// Y = sum_s gamma_{t(s)} mu_{t(s)} e^{i Phi_s}, Phi_{s+1} = Phi_s + phi_{t(s)}.
+// ck (row tables, stride 32, type t at offset koff[t]) or null (c_k on the fly).
+__device__ __forceinline__ Cd upsilon_fp64_general(const LinkParams& p, double f1, double f2, double f,
+                                                   const double* ck, const int* koff, double f3) {
+  Cd mu[kMaxTypes], ph[kMaxTypes];
+  const double a = f1 - f, b = f2 - f;
+  for (int t = 0; t < p.n_types; ++t) {
+    const SpanType& ty = p.types[t];
+    const double chi = 4.0 * kPi * kPi * a * b * (ty.beta2 + kPi * ty.beta3 * (f1 + f2));
+    double tt = chi * (ty.dz / (2.0 * kPi));
+    tt -= rint(tt);
+    double s, c;
+    sincospi(2.0 * tt, &s, &c);
+    const Cd w = {ty.r * c, ty.r * s};
+    Cd acc = {0.0, 0.0};
+    const int K = ty.seg.K;
+    for (int k = K - 1; k >= 0; --k) {
+      acc = cmul(acc, w);
+      acc.re += ck ? ck[(koff[t] + k) * 32] : ty.seg.ck[k] * exp(-ty.seg.zeta[k] * f3);
+    }
+    const double xr = w.re - 1.0, xi = w.im;
+    const double den = ty.alpha * ty.alpha + chi * chi;
+    const Cd q = {(-ty.alpha * xr + chi * xi) / den, (-chi * xr - ty.alpha * xi) / den};
+    const Cd m = cmul(acc, q);
+    mu[t] = {ty.gamma * m.re, ty.gamma * m.im};
+    double tp = chi * (ty.L / (2.0 * kPi));
+    tp -= rint(tp);
+    sincospi(2.0 * tp, &s, &c);
+    ph[t] = {c, s};
+  }
+  Cd z = {1.0, 0.0}, Y = {0.0, 0.0};
+  for (int sp = 0; sp < p.n_spans; ++sp) {
+    const int t = p.span_type[sp];
+    const Cd v = cmul(mu[t], z);
+    Y.re += v.re;
+    Y.im += v.im;
+    z = cmul(z, ph[t]);
+  }
+  return Y;
+}
+
 __device__ __forceinline__ double warp_sum(double v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
@@ -79,8 +122,13 @@ template <int ORD>
 __global__ void __launch_bounds__(32) integrate_fp64_kernel(LinkParams p, const uint64_t* __restrict__ keys,
                                                             const uint32_t* __restrict__ list, long long n_items,
                                                             double* __restrict__ terms, long long n_isl) {
-  extern __shared__ double ck_s[];  // [K][32] (DW order only)
+  extern __shared__ double ck_s[];  // [K][32] (DW order only); general links: types one after the other
   const int lane = threadIdx.x;
+  int koff[kMaxTypes];
+  for (int t = 0, o = 0; t < kMaxTypes; ++t) {
+    koff[t] = o;
+    if (t < p.n_types) o += p.types[t].seg.K;
+  }
   const ChannelTable& ch = p.ch;
   const int n = p.gl.n;
   for (long long it = blockIdx.x; it < n_items; it += gridDim.x) {
@@ -118,8 +166,15 @@ __global__ void __launch_bounds__(32) integrate_fp64_kernel(LinkParams p, const 
         double outer_h;
         if (ORD == ORD_DW) {
           double f3 = nu3 + o;
-          if (active)
-            for (int k = 0; k < p.seg.K; ++k) ck_s[k * 32 + lane] = p.seg.ck[k] * exp(-p.seg.zeta[k] * f3);
+          if (active) {
+            if (p.n_types == 1) {
+              for (int k = 0; k < p.seg.K; ++k) ck_s[k * 32 + lane] = p.seg.ck[k] * exp(-p.seg.zeta[k] * f3);
+            } else {
+              for (int t = 0; t < p.n_types; ++t)
+                for (int k = 0; k < p.types[t].seg.K; ++k)
+                  ck_s[(koff[t] + k) * 32 + lane] = p.types[t].seg.ck[k] * exp(-p.types[t].seg.zeta[k] * f3);
+            }
+          }
           ckrow = ck_s + lane;
           outer_h = rc_shape(o, R3, p.rolloff);
         } else if (ORD == ORD_E) {
@@ -139,12 +194,14 @@ __global__ void __launch_bounds__(32) integrate_fp64_kernel(LinkParams p, const 
             double h1 = rc_shape(u, R1, p.rolloff), h2 = rc_shape(v, R2, p.rolloff), h3 = rc_shape(w, R3, p.rolloff);
             double f1 = nu1 + u, f2 = nu2 + v;
             double af2;
-            if (ORD == ORD_DW && !want_g && !want_h) {
+            if (p.n_types == 1 && ORD == ORD_DW && !want_g && !want_h) {
               Cd mu = upsilon_fp64(p, f1, f2, nu, ckrow, 32, 0.0, &af2, false);
               double y2 = p.gamma * p.gamma * (mu.re * mu.re + mu.im * mu.im) * af2;
               dsum += wo * wi * h1 * h2 * h3 * y2;
             } else {
-              Cd Y = upsilon_fp64(p, f1, f2, nu, ckrow, 32, nu3 + w, &af2, true);
+              Cd Y = p.n_types == 1 ? upsilon_fp64(p, f1, f2, nu, ckrow, 32, nu3 + w, &af2, true)
+                                    : upsilon_fp64_general(p, f1, f2, nu, ORD == ORD_DW ? ck_s + lane : nullptr,
+                                                           koff, nu3 + w);
               if (ORD == ORD_DW) {
                 dsum += wo * wi * h1 * h2 * h3 * (Y.re * Y.re + Y.im * Y.im);
                 double a12 = wi * sqrt(h1 * h2);
@@ -189,7 +246,12 @@ template <int ORD>
 cudaError_t launch_one(const LinkParams& p, const uint64_t* keys, const uint32_t* list, long long n_items,
                        double* terms, long long n_isl, cudaStream_t st) {
   if (n_items <= 0) return cudaSuccess;
-  size_t smem = (ORD == ORD_DW) ? (size_t)p.seg.K * 32 * sizeof(double) : 0;
+  int ksum = p.seg.K;
+  if (p.n_types > 1) {
+    ksum = 0;
+    for (int t = 0; t < p.n_types; ++t) ksum += p.types[t].seg.K;
+  }
+  size_t smem = (ORD == ORD_DW) ? (size_t)ksum * 32 * sizeof(double) : 0;
   static bool attr_set[3] = {false, false, false};
   if (smem > 48 * 1024 && !attr_set[ORD]) {
     cudaError_t e = cudaFuncSetAttribute(integrate_fp64_kernel<ORD>, cudaFuncAttributeMaxDynamicSharedMemorySize,

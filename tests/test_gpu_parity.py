@@ -182,9 +182,51 @@ def test_workspace_too_small_is_rejected(egn, workloads):
     assert ei.value.status == egn.EGN_E_CAPACITY
 
 
-def test_heterogeneous_spans_unsupported(egn, workloads):
-    wl = workloads.config_small(n_spans=2)
-    wl.spans[1].length_m = 60e3
+def _mixed_link(workloads, n_ch=3, gl=12):
+    """Four spans of two fibre types and three lengths (three span types)."""
+    wl = workloads.config_small(n_ch=n_ch, gl_order=gl, n_spans=4)
+    pscf = dict(alpha_db_km=0.16, D_ps_nm_km=21.0, gamma_per_w_km=0.8)
+    for k, v in pscf.items():
+        setattr(wl.spans[1], k, v)
+        setattr(wl.spans[3], k, v)
+    wl.spans[2].length_m = 55e3
+    wl.spans[3].length_m = 101e3
+    return wl
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32c"])
+def test_heterogeneous_spans_eta(egn, oracle_mod, workloads, prec):
+    """Eq. 22 as an explicit coherent sum over spans of different fibres and lengths."""
+    wl = _mixed_link(workloads)
+    ln, pb = _pair(egn, oracle_mod, wl)
+    p = egn.EGN_PREC_FP64 if prec == "fp64" else egn.EGN_PREC_FP32C
+    got, _ = ln.nli_eta(egn.make_opts(gl_order=12, precision=p))
+    want, _ = pb.eta()
+    if prec == "fp64":
+        assert np.allclose(got, want, rtol=FP64_RTOL, atol=0), got / want - 1
+    else:
+        assert np.max(_db(got, want)) < 1e-3, _db(got, want)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32c"])
+def test_heterogeneous_spans_island_terms(egn, oracle_mod, workloads, prec):
+    wl = _mixed_link(workloads, gl=9)
+    ln, pb = _pair(egn, oracle_mod, wl, gl=9)
+    isl = np.array([(n, *t) for n in range(3) for t in pb.islands(n)], dtype=np.int32)
+    p = egn.EGN_PREC_FP64 if prec == "fp64" else egn.EGN_PREC_FP32C
+    got = ln.island_terms(egn.make_opts(gl_order=9, precision=p), isl, all_terms=True)
+    want = np.array([pb.island_terms(*row, all_terms=True) for row in isl])
+    if prec == "fp64":
+        assert np.allclose(got, want, rtol=FP64_RTOL, atol=1e-300)
+    else:
+        err = np.abs(got - want)
+        assert np.all(err <= 3e-4 * np.abs(want) + 3e-5 * np.abs(want[:, :1]))
+
+
+def test_too_many_span_types_unsupported(egn, workloads):
+    wl = workloads.config_small(n_spans=5)
+    for i, s in enumerate(wl.spans):
+        s.length_m = (60 + 5 * i) * 1e3
     ln = egn.link_from_workload(wl)
     with pytest.raises(egn.EgnError) as ei:
         ln.nli_eta(egn.make_opts())
