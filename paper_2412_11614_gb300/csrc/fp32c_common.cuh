@@ -81,19 +81,29 @@ __device__ __forceinline__ float rint_fast(float x) {
   return (x + M) - M;
 }
 
-// sin(x) for |x| < 0.05 by its Taylor series to x^7 (relative error < 1e-12).
+// sin(x) for |x| < 0.05 by its Taylor series to x^5 (relative error < 4e-12).
 __device__ __forceinline__ float sin_small(float x) {
-  float x2 = x * x;
-  return x * fmaf(x2, fmaf(x2, fmaf(x2, -1.0f / 5040.0f, 1.0f / 120.0f), -1.0f / 6.0f), 1.0f);
+  const float x2 = x * x;
+  return x * fmaf(x2, fmaf(x2, 1.0f / 120.0f, -1.0f / 6.0f), 1.0f);
 }
 
-// Raised-cosine shape in FP32.
-__device__ __forceinline__ float rc_f(float x, float R, float beta) {
-  float ax = fabsf(x);
-  float a = 0.5f * (1.0f - beta) * R, b = 0.5f * (1.0f + beta) * R;
-  if (ax <= a) return 1.0f;
-  if (ax >= b) return 0.0f;
-  return 0.5f * (1.0f + __cosf(3.14159265f * (ax - a) / (beta * R)));
+// Phased-array ratio sin(N x) / sin(x) of Eq. 22 (x = pi phi, |x| <= pi / 2).
+// Hardware sines (absolute error ~4e-7) away from zero; within |.| < 0.05 the
+// Taylor series keeps the relative error small where the ratio peaks at N.
+// Both forms are evaluated and selected, so the warp does not diverge.
+__device__ __forceinline__ float array_ratio(float x, float N) {
+  const float Nx = N * x;
+  const float sd = fabsf(x) < 0.05f ? sin_small(x) : __sinf(x);
+  const float sn = fabsf(Nx) < 0.05f ? sin_small(Nx) : __sinf(Nx);
+  return x == 0.0f ? N : sn * rcp_approx(sd);
+}
+
+// Raised-cosine shape in FP32 without branches: a = (1 - beta) R / 2 is the knee
+// and inv = 1 / (beta R) (0 when beta = 0, where every node lies in the flat
+// part).  t = clamp((|x| - a) / (beta R), 0, 1), h = (1 + cos(pi t)) / 2.
+__device__ __forceinline__ float rc_f(float x, float a, float inv) {
+  const float t = __saturatef((fabsf(x) - a) * inv);
+  return fmaf(0.5f, __cosf(3.14159265f * t), 0.5f);
 }
 
 }  // namespace fp32c

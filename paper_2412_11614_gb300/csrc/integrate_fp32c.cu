@@ -28,7 +28,7 @@
 //    per segment instead of 4; |w| < 1 bounds its error growth.  In the DW order
 //    two points share one fma.rn.f32x2 instruction.
 //  * Phased array (Eq. 22): ratio sin(N pi phi)/sin(pi phi); near phi = 0 the
-//    sines use their Taylor series (|argument| < 0.05, relative error < 1e-12).
+//    sines use their Taylor series (|argument| < 0.05, relative error < 4e-12).
 //    Hardware sin/cos (MUFU, absolute error ~4e-7 on [-pi, pi]) elsewhere.
 // Island sums: FP32 per thread, fixed-order shuffle and shared-memory trees.
 #include "egn_internal.h"
@@ -53,7 +53,8 @@ struct BatchSm {  // one entry per island of the batch
   Df pm[3][kBatch], ph[3][kBatch];                      // panel midpoints and half-widths
   Df Bv[kBatch], Cv[kBatch], cv[kBatch];                // node-rule constants
   Df F1[kBatch], F2[kBatch], S12[kBatch], dd[kBatch];   // nu1 - nu, nu2 - nu, nu1 + nu2, d
-  float R1[kBatch], R2[kBatch], R3[kBatch], nu3[kBatch];
+  float ra[3][kBatch], ri[3][kBatch];                   // raised-cosine knee and 1/(beta R) of n1, n2, n3
+  float nu3[kBatch];
   float cf0[kBatch], cf1[kBatch], cf2[kBatch];          // D, G, H (DW) or the E / F coefficient
 };
 
@@ -106,9 +107,11 @@ __device__ __forceinline__ void batch_setup(const LinkParams& p, const uint64_t*
       bs.F2[tid] = df_of(nu2 - nu);
       bs.S12[tid] = df_of(nu1 + nu2);
       bs.dd[tid] = df_of(d);
-      bs.R1[tid] = (float)R1;
-      bs.R2[tid] = (float)R2;
-      bs.R3[tid] = (float)R3;
+      const double Rs[3] = {R1, R2, R3};
+      for (int q_ = 0; q_ < 3; ++q_) {
+        bs.ra[q_][tid] = (float)(0.5 * (1.0 - p.rolloff) * Rs[q_]);
+        bs.ri[q_][tid] = p.rolloff > 0.0 ? (float)(1.0 / (p.rolloff * Rs[q_])) : 0.0f;
+      }
       bs.nu3[tid] = (float)nu3;
       double cf[5];
       term_coefs(R, R1, R2, R3, cf);
@@ -210,7 +213,6 @@ integrate_fp32c_kernel(LinkParams p, const uint64_t* __restrict__ keys, const ui
   const int n = p.gl.n;
   const int K = p.seg.K;
   const float Kf = (float)K, invK = 1.0f / (float)K;
-  const float beta = (float)p.rolloff;
   const float alpha = (float)p.alpha, alpha2 = alpha * alpha;
   const float r = (float)p.r;
   const float one_m_r = (float)(-expm1(-p.alpha * p.dz));
@@ -246,7 +248,8 @@ integrate_fp32c_kernel(LinkParams p, const uint64_t* __restrict__ keys, const ui
       const int flags = bs.flags[ib];
       const bool want_g = flags & 1, want_h = flags & 2;
       const bool cplx = ORD != ORD_DW || flags != 0;
-      const float R1f = bs.R1[ib], R2f = bs.R2[ib], R3f = bs.R3[ib];
+      const float sa1 = bs.ra[0][ib], sa2 = bs.ra[1][ib], sa3 = bs.ra[2][ib];
+      const float si1 = bs.ri[0][ib], si2 = bs.ri[1][ib], si3 = bs.ri[2][ib];
       const float dfl = dval(bs.dd[ib]);
       float dsum = 0.0f, csum = 0.0f, hre = 0.0f, him = 0.0f;
       const int no = np > 0 ? p.gl.order[np] : 0;
@@ -269,7 +272,7 @@ integrate_fp32c_kernel(LinkParams p, const uint64_t* __restrict__ keys, const ui
             const float s0f = dval(s0), s1f = dval(s1);
             const float imf = dval(im), ihf = dval(ih), of = dval(o);
             const float wo = dval(ph) * p.gl.wf[np][i];
-            const float hout = ORD == ORD_DW ? rc_f(of, R3f, beta) : (ORD == ORD_E ? rc_f(of, R2f, beta) : rc_f(of, R1f, beta));
+            const float hout = ORD == ORD_DW ? rc_f(of, sa3, si3) : (ORD == ORD_E ? rc_f(of, sa2, si2) : rc_f(of, sa1, si1));
             rs.qa[rr] = make_float4(Q0r.hi, Q0r.lo, Q1.hi, Q1.lo);
             rs.qb[rr] = make_float4(Q2.hi, Q2.lo, Q3, Q0r.hi - rint_fast(Q0r.hi));
             rs.ab[rr] = make_float4(dval(a0), dval(a1), dval(b0_), dval(b1));
@@ -343,9 +346,9 @@ integrate_fp32c_kernel(LinkParams p, const uint64_t* __restrict__ keys, const ui
             if (ORD == ORD_DW) { u = t; v = ow.x - t; h3 = 1.0f; }  // h3(w) is folded into wrowh
             else {
               if (ORD == ORD_E) { v = ow.x; u = t; } else { u = ow.x; v = t; }
-              h3 = rc_f(u + v + dfl, R3f, beta);
+              h3 = rc_f(u + v + dfl, sa3, si3);
             }
-            const float h1 = rc_f(u, R1f, beta), h2 = rc_f(v, R2f, beta);
+            const float h1 = rc_f(u, sa1, si1), h2 = rc_f(v, sa2, si2);
             wgt_[m] = (ORD == ORD_DW ? wrowh : wrow) * wnode * h1 * h2 * h3;
             s12_[m] = 0.0f;
             s123_[m] = 0.0f;
@@ -383,6 +386,7 @@ integrate_fp32c_kernel(LinkParams p, const uint64_t* __restrict__ keys, const ui
               }
               --k;
             }
+#pragma unroll 4
             for (; k >= 1; k -= 2) {
               const ulonglong2 cc = *reinterpret_cast<const ulonglong2*>(trow + k - 1);  // (c_{k-1}, c_k) pairs
 #pragma unroll
@@ -431,14 +435,7 @@ integrate_fp32c_kernel(LinkParams p, const uint64_t* __restrict__ keys, const ui
             const float mim = fmaf(sre, qi, sim * qr);
             // phased array: sin(N pi phi) / sin(pi phi)
             const float x = pi_f * phi_[m];
-            const float Nx = N * x;
-            float ratio;
-            if (fabsf(x) >= 0.05f) {
-              ratio = __sinf(Nx) * rcp_approx(__sinf(x));
-            } else {  // near the array-factor peak: series for the small sines
-              const float snum = fabsf(Nx) < 0.05f ? sin_small(Nx) : __sinf(Nx);
-              ratio = (x == 0.0f) ? N : snum * rcp_approx(sin_small(x));
-            }
+            const float ratio = array_ratio(x, N);
             if (!cplx) {
               dsum = fmaf(wgt_[m], fmaf(mre, mre, mim * mim) * (ratio * ratio), dsum);
             } else {
@@ -589,7 +586,6 @@ integrate_fp32c_general_kernel(LinkParams p, const uint64_t* __restrict__ keys, 
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const int n = p.gl.n;
   const int T = p.n_types;
-  const float beta = (float)p.rolloff;
   const float k4 = (float)(4.0 * kPi * kPi);
   const float pi_f = 3.14159265358979f;
   int tpr = 1;
@@ -621,7 +617,8 @@ integrate_fp32c_general_kernel(LinkParams p, const uint64_t* __restrict__ keys, 
       const int np = bs.np[ib];
       const int flags = bs.flags[ib];
       const bool want_g = flags & 1, want_h = flags & 2;
-      const float R1f = bs.R1[ib], R2f = bs.R2[ib], R3f = bs.R3[ib];
+      const float sa1 = bs.ra[0][ib], sa2 = bs.ra[1][ib], sa3 = bs.ra[2][ib];
+      const float si1 = bs.ri[0][ib], si2 = bs.ri[1][ib], si3 = bs.ri[2][ib];
       const float dfl = dval(bs.dd[ib]);
       float dsum = 0.0f, csum = 0.0f, hre = 0.0f, him = 0.0f;
       const int no = np > 0 ? p.gl.order[np] : 0;
@@ -643,7 +640,7 @@ integrate_fp32c_general_kernel(LinkParams p, const uint64_t* __restrict__ keys, 
             const float imf = dval(g.im), ihf = dval(g.ih), of = dval(g.o);
             const float wo = dval(g.ph) * p.gl.wf[np][i];
             const float hout =
-                ORD == ORD_DW ? rc_f(of, R3f, beta) : (ORD == ORD_E ? rc_f(of, R2f, beta) : rc_f(of, R1f, beta));
+                ORD == ORD_DW ? rc_f(of, sa3, si3) : (ORD == ORD_E ? rc_f(of, sa2, si2) : rc_f(of, sa1, si1));
             rs.ab[rr] = make_float4(dval(g.a0), dval(g.a1), dval(g.b0), dval(g.b1));
             rs.ow[rr] = make_float4(ORD == ORD_DW ? of - dfl : of, wo * ihf * hout, wo * ihf, hout);
             const float nu3 = bs.nu3[ib];
@@ -789,9 +786,9 @@ integrate_fp32c_general_kernel(LinkParams p, const uint64_t* __restrict__ keys, 
             if (ORD == ORD_DW) { u = tt; v = ow.x - tt; h3 = 1.0f; }
             else {
               if (ORD == ORD_E) { v = ow.x; u = tt; } else { u = ow.x; v = tt; }
-              h3 = rc_f(u + v + dfl, R3f, beta);
+              h3 = rc_f(u + v + dfl, sa3, si3);
             }
-            const float h1 = rc_f(u, R1f, beta), h2 = rc_f(v, R2f, beta);
+            const float h1 = rc_f(u, sa1, si1), h2 = rc_f(v, sa2, si2);
             const float yre = yre_[m], yim = yim_[m];
             if (ORD == ORD_DW) {
               dsum = fmaf((wrowh * wnode_[m]) * (h1 * h2), fmaf(yre, yre, yim * yim), dsum);
