@@ -87,15 +87,25 @@ __device__ __forceinline__ float sin_small(float x) {
   return x * fmaf(x2, fmaf(x2, 1.0f / 120.0f, -1.0f / 6.0f), 1.0f);
 }
 
-// Phased-array ratio sin(N x) / sin(x) of Eq. 22 (x = pi phi, |x| <= pi / 2).
-// Hardware sines (absolute error ~4e-7) away from zero; within |.| < 0.05 the
-// Taylor series keeps the relative error small where the ratio peaks at N.
-// Both forms are evaluated and selected, so the warp does not diverge.
-__device__ __forceinline__ float array_ratio(float x, float N) {
+// Phased-array sines of Eq. 22: sd = sin(x), sn = sin(N x) for x = pi phi,
+// |x| <= pi / 2, so that the ratio is sn / sd.  Hardware sines (absolute error
+// ~4e-7) away from zero; within |.| < 0.05 the Taylor series keeps the relative
+// error small where the ratio peaks at N.  Both forms are evaluated and
+// selected, so the warp does not diverge.  Below |x| = 1e-12 the pair is
+// (1, N): the ratio is N to within (N x)^2 and no reciprocal of a vanishing
+// sine is taken.
+__device__ __forceinline__ void array_sines(float x, float N, float& sd, float& sn) {
   const float Nx = N * x;
-  const float sd = fabsf(x) < 0.05f ? sin_small(x) : __sinf(x);
-  const float sn = fabsf(Nx) < 0.05f ? sin_small(Nx) : __sinf(Nx);
-  return x == 0.0f ? N : sn * rcp_approx(sd);
+  const float d = fabsf(x) < 0.05f ? sin_small(x) : __sinf(x);
+  const float nn = fabsf(Nx) < 0.05f ? sin_small(Nx) : __sinf(Nx);
+  const bool z = fabsf(x) < 1e-12f;
+  sd = z ? 1.0f : d;
+  sn = z ? N : nn;
+}
+__device__ __forceinline__ float array_ratio(float x, float N) {
+  float sd, sn;
+  array_sines(x, N, sd, sn);
+  return sn * rcp_approx(sd);
 }
 
 // Raised-cosine shape in FP32 without branches: a = (1 - beta) R / 2 is the knee

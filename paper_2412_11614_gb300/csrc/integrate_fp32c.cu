@@ -43,7 +43,7 @@ using namespace fp32c;
 constexpr int kThreads = 128;
 constexpr int kBatch = kThreads;   // islands per batch, one per thread in the set-up
 constexpr int kRowsMax = 64;       // rows per chunk held in shared memory
-constexpr int kTabFloats = 5376;   // DW c_k table budget (21 KB), each c_k stored twice (f32x2)
+constexpr int kTabFloats = 2688;   // DW c_k table budget (10.5 KB): [rows][kpad] floats
 
 // ---------------------------------------------------------------- shared state
 struct BatchSm {  // one entry per island of the batch
@@ -196,8 +196,64 @@ __device__ __forceinline__ RowPhase row_phase(const RowGeo& r, Df G0, Df G1, flo
   return q;
 }
 
+// Phase of one point of a row: theta (turns of one segment, chi L / (2 pi K))
+// and phi (turns of the span, chi L / (2 pi)), both reduced to [-1/2, 1/2].
+// qa = {q0h, q0l, q1h, q1l}, qb = {q2h, q2l, q3, frac(q0h)}, x4 = {x, x tail,
+// x^2, x^2 tail}, xc = x^3.  Q1 x and Q2 x^2 are exact FP32 products (head by
+// FMA residual, tails by the cross terms); Q1 x is reduced modulo K exactly.
+__device__ __forceinline__ void point_phase(const float4& qa, const float4& qb, const float4& x4, float xc, float Kf,
+                                            float invK, float& th, float& ph) {
+  const float p1 = qa.z * x4.x, e1 = fmaf(qa.z, x4.x, -p1);
+  const float t1 = fmaf(qa.z, x4.y, fmaf(qa.w, x4.x, e1));
+  const float p2 = qb.x * x4.z, e2 = fmaf(qb.x, x4.z, -p2);
+  const float t2 = fmaf(qb.x, x4.w, fmaf(qb.y, x4.z, e2));
+  const float r1 = fmaf(-Kf, rint_fast(p1 * invK), p1);
+  const float tail = (qa.y + t1) + fmaf(qb.z, xc, t2);
+  th = fmaf((qa.x + r1) + p2, invK, tail * invK);
+  th -= rint_fast(th);
+  ph = (qb.w + (r1 - rint_fast(r1))) + ((p2 - rint_fast(p2)) + tail);
+  ph -= rint_fast(ph);
+}
+
+// Segment sum of NPAIR point pairs of one row by the second-order real
+// recurrence b_k = c_k + p b_{k+1} - q b_{k+2}, k = K-1 .. 0, two points per
+// fma.rn.f32x2.  It is evaluated as p b_{k+1} + (c_k - q b_{k+2}): the inner FMA
+// does not wait for the previous step, so one FMA per step is on the dependency
+// chain.  trow holds the row's c_k, 16-byte aligned; each c_k is paired with
+// itself in registers.  On return b1p = b_0 and b2p = b_1.
+template <int NPAIR>
+__device__ __forceinline__ void dw_step(float c, f32x2 nq2, const f32x2* pp, f32x2* b1p, f32x2* b2p) {
+  const f32x2 cc = pack2(c, c);
+#pragma unroll
+  for (int a = 0; a < NPAIR; ++a) {
+    const f32x2 nb = ffma2(pp[a], b1p[a], ffma2(nq2, b2p[a], cc));
+    b2p[a] = b1p[a];
+    b1p[a] = nb;
+  }
+}
+
+template <int NPAIR>
+__device__ __forceinline__ void dw_recurrence(const float* __restrict__ trow, int K, f32x2 nq2, const f32x2* pp,
+                                              f32x2* b1p, f32x2* b2p) {
+#pragma unroll
+  for (int a = 0; a < NPAIR; ++a) {
+    b1p[a] = 0ull;
+    b2p[a] = 0ull;
+  }
+  int k = K - 1;
+  for (int e = K & 3; e > 0; --e, --k) dw_step<NPAIR>(trow[k], nq2, pp, b1p, b2p);  // peel: k + 1 = 0 (mod 4)
+#pragma unroll 2
+  for (; k >= 3; k -= 4) {
+    const float4 c4 = *reinterpret_cast<const float4*>(trow + k - 3);  // c_{k-3} .. c_k
+    dw_step<NPAIR>(c4.w, nq2, pp, b1p, b2p);
+    dw_step<NPAIR>(c4.z, nq2, pp, b1p, b2p);
+    dw_step<NPAIR>(c4.y, nq2, pp, b1p, b2p);
+    dw_step<NPAIR>(c4.x, nq2, pp, b1p, b2p);
+  }
+}
+
 template <int ORD, int KP>
-__global__ void __launch_bounds__(kThreads, KP == 8 ? 3 : 4)
+__global__ void __launch_bounds__(kThreads, KP == 8 ? 3 : (ORD == ORD_DW ? 5 : 4))
 integrate_fp32c_kernel(LinkParams p, const uint64_t* __restrict__ keys, const uint32_t* __restrict__ list,
                        long long n_items, float* __restrict__ terms, long long n_isl, int rows_per_chunk, int kpad,
                        Df G0, Df G1) {
@@ -207,7 +263,7 @@ integrate_fp32c_kernel(LinkParams p, const uint64_t* __restrict__ keys, const ui
   __shared__ RowSm rs;
   __shared__ NodeSm ns;
   __shared__ float red[4][kThreads / 32];
-  extern __shared__ __align__(16) float2 tab[];  // [rows_per_chunk][kpad] pairs (c_k, c_k) (DW only)
+  extern __shared__ __align__(16) float tab[];  // [rows_per_chunk][kpad] c_k of the chunk's rows (DW only)
 
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const int n = p.gl.n;
@@ -218,6 +274,7 @@ integrate_fp32c_kernel(LinkParams p, const uint64_t* __restrict__ keys, const ui
   const float one_m_r = (float)(-expm1(-p.alpha * p.dz));
   const float q = r * r;
   const float m2r = -2.0f * r;
+  const float c2r = 2.0f * r, c4r = 4.0f * r, omr2 = one_m_r * one_m_r;
   const float N = (float)p.n_spans;
   const float gam = (float)p.gamma;
   const float g2 = gam * gam;
@@ -288,9 +345,9 @@ integrate_fp32c_kernel(LinkParams p, const uint64_t* __restrict__ keys, const ui
         if (ORD == ORD_DW) {
           for (int k = tid; k < K; k += kThreads) {
             const float ck = p.seg.ck_f[k], zk = p.seg.zeta_f[k];
+#pragma unroll 8
             for (int rr = 0; rr < rc; ++rr) {
-              const float c = ck * ex2_approx(-zk * rs.f3[rr].x);
-              tab[rr * kpad + k] = make_float2(c, c);
+              tab[rr * kpad + k] = ck * ex2_approx(-zk * rs.f3[rr].x);
             }
           }
           __syncthreads();
@@ -302,10 +359,55 @@ integrate_fp32c_kernel(LinkParams p, const uint64_t* __restrict__ keys, const ui
           const int rrc = row_ok ? rr : 0;
           const float4 qa = rs.qa[rrc], qb = rs.qb[rrc], ab = rs.ab[rrc], kc = rs.kc[rrc], ow = rs.ow[rrc];
           const float4 f3r = rs.f3[rrc];
-          const float q0h = qa.x, q0l = qa.y, q1h = qa.z, q1l = qa.w;
-          const float q2h = qb.x, q2l = qb.y, q3 = qb.z, fq0 = qb.w;
           const float im = kc.z, ih = kc.w;
           const float wrowh = row_ok ? ow.y : 0.0f, wrow = row_ok ? ow.z : 0.0f;
+          if (ORD == ORD_DW && !cplx) {
+            // D only.  |Upsilon / gamma|^2 = |sum|^2 |w - 1|^2 / (alpha^2 + chi^2) * (sn / sd)^2
+            // with 2 Re w = 2r - 4r sin^2(pi theta), |w - 1|^2 = (1 - r)^2 + 4r sin^2(pi theta)
+            // and |sum|^2 = |b_0 - conj(w) b_1|^2 = b_0 (b_0 - 2 Re(w) b_1) + r^2 b_1^2.
+            float pv[KP], wa_[KP], chi_[KP], phi_[KP], wgt_[KP];
+#pragma unroll
+            for (int m = 0; m < KP; ++m) {
+              const int j = lr + tpr * m;
+              const bool jok = j < n;
+              const int jj = jok ? j : 0;
+              const float4 x4 = ns.x4[jj];
+              const float2 x2 = ns.x2[jj];
+              float th, ph;
+              point_phase(qa, qb, x4, x2.x, Kf, invK, th, ph);
+              const float sh = __sinf(pi_f * th);
+              const float s2 = sh * sh;
+              pv[m] = fmaf(-c4r, s2, c2r);
+              wa_[m] = fmaf(c4r, s2, omr2);
+              phi_[m] = ph;
+              const float xh = x4.x;
+              chi_[m] = fmaf(ab.y, xh, ab.x) * fmaf(ab.w, xh, ab.z) * fmaf(kc.y, xh, kc.x);
+              const float t = fmaf(ih, xh, im);
+              wgt_[m] = (jok ? x2.y : 0.0f) * rc_f(t, sa1, si1) * rc_f(ow.x - t, sa2, si2);
+            }
+            f32x2 pp[NPAIR], b1p[NPAIR], b2p[NPAIR];
+#pragma unroll
+            for (int a = 0; a < NPAIR; ++a) pp[a] = pack2(pv[2 * a], pv[2 * a + 1]);
+            dw_recurrence<NPAIR>(tab + rrc * kpad, K, pack2(-q, -q), pp, b1p, b2p);
+            float acc = 0.0f;
+#pragma unroll
+            for (int a = 0; a < NPAIR; ++a) {
+              float b0v[2], b1v[2];
+              unpack2(b1p[a], b0v[0], b0v[1]);
+              unpack2(b2p[a], b1v[0], b1v[1]);
+#pragma unroll
+              for (int e = 0; e < 2; ++e) {
+                const int m = 2 * a + e;
+                const float s2sum = fmaf(b0v[e], fmaf(-pv[m], b1v[e], b0v[e]), q * b1v[e] * b1v[e]);
+                float sd, sn;
+                array_sines(pi_f * phi_[m], N, sd, sn);
+                const float den = (sd * sd) * fmaf(chi_[m], chi_[m], alpha2);
+                acc = fmaf(wgt_[m] * s2sum * wa_[m], (sn * sn) * rcp_approx(den), acc);
+              }
+            }
+            dsum = fmaf(wrowh, acc, dsum);
+            continue;
+          }
           float gre = 0.0f, gim = 0.0f;
           float p_[KP], b1_[KP], b2_[KP], f3_[KP];
           float wm1_[KP], wi_[KP], chi_[KP], phi_[KP], wgt_[KP], s12_[KP], s123_[KP];
@@ -316,19 +418,10 @@ integrate_fp32c_kernel(LinkParams p, const uint64_t* __restrict__ keys, const ui
             const int jj = jok ? j : 0;
             const float4 x4 = ns.x4[jj];
             const float2 x2 = ns.x2[jj];
-            const float xh = x4.x, xl = x4.y, x2h = x4.z, x2l = x4.w, xc = x2.x;
+            const float xh = x4.x;
             const float wnode = jok ? x2.y : 0.0f;
-            // phase: exact products, Q1 x reduced modulo K
-            const float p1 = q1h * xh, e1 = fmaf(q1h, xh, -p1);
-            const float t1 = fmaf(q1h, xl, fmaf(q1l, xh, e1));
-            const float p2 = q2h * x2h, e2 = fmaf(q2h, x2h, -p2);
-            const float t2 = fmaf(q2h, x2l, fmaf(q2l, x2h, e2));
-            const float r1 = fmaf(-Kf, rint_fast(p1 * invK), p1);
-            const float tail = (q0l + t1) + fmaf(q3, xc, t2);
-            float th = fmaf((q0h + r1) + p2, invK, tail * invK);
-            th -= rint_fast(th);                                           // theta (turns)
-            float ph = (fq0 + (r1 - rint_fast(r1))) + ((p2 - rint_fast(p2)) + tail);
-            ph -= rint_fast(ph);                                           // phi (turns)
+            float th, ph;
+            point_phase(qa, qb, x4, x2.x, Kf, invK, th, ph);
             // w = r e^{2 pi i th} from the half angle (keeps w - 1 accurate)
             const float ah = pi_f * th;
             const float sh = __sinf(ah), chh = __cosf(ah);
@@ -366,42 +459,10 @@ integrate_fp32c_kernel(LinkParams p, const uint64_t* __restrict__ keys, const ui
           }
           // ---- segment sum by the real recurrence, k = K-1 .. 0
           if (ORD == ORD_DW) {
-            const float2* trow = tab + rrc * kpad;
-            const f32x2 nq2 = pack2(-q, -q);
             f32x2 pp[NPAIR], b1p[NPAIR], b2p[NPAIR];
 #pragma unroll
-            for (int a = 0; a < NPAIR; ++a) {
-              pp[a] = pack2(p_[2 * a], p_[2 * a + 1]);
-              b1p[a] = 0ull;
-              b2p[a] = 0ull;
-            }
-            int k = K - 1;
-            if (K & 1) {  // peel so that the 16-byte loads below are aligned
-              const f32x2 c = *reinterpret_cast<const f32x2*>(trow + k);
-#pragma unroll
-              for (int a = 0; a < NPAIR; ++a) {
-                const f32x2 nb = ffma2(nq2, b2p[a], ffma2(pp[a], b1p[a], c));
-                b2p[a] = b1p[a];
-                b1p[a] = nb;
-              }
-              --k;
-            }
-#pragma unroll 4
-            for (; k >= 1; k -= 2) {
-              const ulonglong2 cc = *reinterpret_cast<const ulonglong2*>(trow + k - 1);  // (c_{k-1}, c_k) pairs
-#pragma unroll
-              for (int a = 0; a < NPAIR; ++a) {
-                const f32x2 nb = ffma2(nq2, b2p[a], ffma2(pp[a], b1p[a], cc.y));
-                b2p[a] = b1p[a];
-                b1p[a] = nb;
-              }
-#pragma unroll
-              for (int a = 0; a < NPAIR; ++a) {
-                const f32x2 nb = ffma2(nq2, b2p[a], ffma2(pp[a], b1p[a], cc.x));
-                b2p[a] = b1p[a];
-                b1p[a] = nb;
-              }
-            }
+            for (int a = 0; a < NPAIR; ++a) pp[a] = pack2(p_[2 * a], p_[2 * a + 1]);
+            dw_recurrence<NPAIR>(tab + rrc * kpad, K, pack2(-q, -q), pp, b1p, b2p);
 #pragma unroll
             for (int a = 0; a < NPAIR; ++a) {
               unpack2(b1p[a], b1_[2 * a], b1_[2 * a + 1]);
@@ -413,8 +474,7 @@ integrate_fp32c_kernel(LinkParams p, const uint64_t* __restrict__ keys, const ui
 #pragma unroll
               for (int m = 0; m < KP; ++m) {
                 const float c = ck * ex2_approx(-zk * f3_[m]);
-                float bn = fmaf(p_[m], b1_[m], c);
-                bn = fmaf(-q, b2_[m], bn);
+                const float bn = fmaf(p_[m], b1_[m], fmaf(-q, b2_[m], c));
                 b2_[m] = b1_[m];
                 b1_[m] = bn;
               }
@@ -510,14 +570,14 @@ cudaError_t launch_one(const LinkParams& p, const uint64_t* keys, const uint32_t
   if (n_items <= 0) return cudaSuccess;
   const int K = p.seg.K;
   int kpad = (K + 3) & ~3;
-  if ((kpad & 7) == 0) kpad += 4;  // row stride 2 kpad = 8 (mod 16) words: 4 rows' 16-byte loads hit distinct banks
+  if ((kpad & 7) == 0) kpad += 4;  // row stride = 4 (mod 8) words: 4 rows' 16-byte loads hit distinct banks
   int rows = kRowsMax;
   if (ORD == ORD_DW) {
-    rows = kTabFloats / (2 * kpad);
+    rows = kTabFloats / kpad;
     if (rows > kRowsMax) rows = kRowsMax;
     if (rows < 1) rows = 1;
   }
-  size_t smem = ORD == ORD_DW ? (size_t)rows * kpad * sizeof(float2) : 0;
+  size_t smem = ORD == ORD_DW ? (size_t)rows * kpad * sizeof(float) : 0;
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -530,7 +590,7 @@ cudaError_t launch_one(const LinkParams& p, const uint64_t* keys, const uint32_t
     attr_done |= 1ull << (dev & 63);
   }
   long long batches = (n_items + kBatch - 1) / kBatch;
-  long long blocks = (long long)sms * (KP == 8 ? 3 : 4);
+  long long blocks = (long long)sms * (KP == 8 ? 3 : (ORD == ORD_DW ? 5 : 4));
   if (blocks > batches) blocks = batches;
   // 2 pi L beta2 and 2 pi^2 L beta3 as double-floats
   double g0 = 2.0 * kPi * p.L * p.beta2, g1 = 2.0 * kPi * kPi * p.L * p.beta3;
@@ -726,7 +786,7 @@ integrate_fp32c_general_kernel(LinkParams p, const uint64_t* __restrict__ keys, 
                 const float c = trow[k];
 #pragma unroll
                 for (int m = 0; m < KP; ++m) {
-                  const float bn = fmaf(-q, b2_[m], fmaf(p_[m], b1_[m], c));
+                  const float bn = fmaf(p_[m], b1_[m], fmaf(-q, b2_[m], c));
                   b2_[m] = b1_[m];
                   b1_[m] = bn;
                 }
@@ -737,7 +797,7 @@ integrate_fp32c_general_kernel(LinkParams p, const uint64_t* __restrict__ keys, 
 #pragma unroll
                 for (int m = 0; m < KP; ++m) {
                   const float c = ck * ex2_approx(-zk * f3_[m]);
-                  const float bn = fmaf(-q, b2_[m], fmaf(p_[m], b1_[m], c));
+                  const float bn = fmaf(p_[m], b1_[m], fmaf(-q, b2_[m], c));
                   b2_[m] = b1_[m];
                   b1_[m] = bn;
                 }
