@@ -41,31 +41,35 @@ namespace {
 using namespace fp32c;
 
 constexpr int kThreads = 128;
+constexpr int kDwThreads = 64;     // CTA size of the D/G/H pass
 constexpr int kBatch = kThreads;   // islands per batch, one per thread in the set-up
 constexpr int kRowsMax = 64;       // rows per chunk held in shared memory
 constexpr int kTabFloats = 2688;   // DW c_k table budget (10.5 KB): [rows][kpad] floats
 
 // ---------------------------------------------------------------- shared state
-struct BatchSm {  // one entry per island of the batch
-  long long isl[kBatch];
-  int np[kBatch];
-  int flags[kBatch];  // bit0 G wanted, bit1 H wanted
-  Df pm[3][kBatch], ph[3][kBatch];                      // panel midpoints and half-widths
-  Df Bv[kBatch], Cv[kBatch], cv[kBatch];                // node-rule constants
-  Df F1[kBatch], F2[kBatch], S12[kBatch], dd[kBatch];   // nu1 - nu, nu2 - nu, nu1 + nu2, d
-  float ra[3][kBatch], ri[3][kBatch];                   // raised-cosine knee and 1/(beta R) of n1, n2, n3
-  float nu3[kBatch];
-  float cf0[kBatch], cf1[kBatch], cf2[kBatch];          // D, G, H (DW) or the E / F coefficient
+template <int NB>
+struct BatchSmT {  // one entry per island of the batch
+  long long isl[NB];
+  int np[NB];
+  int flags[NB];  // bit0 G wanted, bit1 H wanted
+  Df pm[3][NB], ph[3][NB];                      // panel midpoints and half-widths
+  Df Bv[NB], Cv[NB], cv[NB];                    // node-rule constants
+  Df F1[NB], F2[NB], S12[NB], dd[NB];           // nu1 - nu, nu2 - nu, nu1 + nu2, d
+  float ra[3][NB], ri[3][NB];                   // raised-cosine knee and 1/(beta R) of n1, n2, n3
+  float nu3[NB];
+  float cf0[NB], cf1[NB], cf2[NB];              // D, G, H (DW) or the E / F coefficient
 };
+using BatchSm = BatchSmT<kBatch>;
 
 // Row constants, four per float4 so that a point pass loads them with 16-byte loads.
+template <int RM>
 struct RowSm {
-  float4 qa[kRowsMax];  // q0h, q0l, q1h, q1l              (phase, turns; Q0 modulo K)
-  float4 qb[kRowsMax];  // q2h, q2l, q3, frac(q0h)
-  float4 ab[kRowsMax];  // a0, a1, b0, b1                  (f1 - f = a0 + a1 x, f2 - f = b0 + b1 x)
-  float4 kc[kRowsMax];  // 4 pi^2 bc0, 4 pi^2 bc1, im, ih   (bc = beta2 + pi beta3 (f1 + f2); inner = im + ih x)
-  float4 ow[kRowsMax];  // o - d (DW) or o, wo ih hout, wo ih, hout   (wo outer weight, hout outer shape)
-  float4 f3[kRowsMax];  // f30, f31, wo, 0                  (f3 = f30 + f31 x)
+  float4 qa[RM];  // q0h, q0l, q1h, q1l              (phase, turns; Q0 modulo K)
+  float4 qb[RM];  // q2h, q2l, q3, frac(q0h)
+  float4 ab[RM];  // a0, a1, b0, b1                  (f1 - f = a0 + a1 x, f2 - f = b0 + b1 x)
+  float4 kc[RM];  // 4 pi^2 bc0, 4 pi^2 bc1, im, ih   (bc = beta2 + pi beta3 (f1 + f2); inner = im + ih x)
+  float4 ow[RM];  // o - d (DW) or o, wo ih hout, wo ih, hout   (wo outer weight, hout outer shape)
+  float4 f3[RM];  // f30, f31, wo, 0                  (f3 = f30 + f31 x)
 };
 
 // Inner Gauss-Legendre nodes of the launch: {x head, x tail, x^2 head, x^2 tail}, {x^3, w}.
@@ -76,10 +80,10 @@ struct NodeSm {
 
 // Batch set-up (FP64, one island per thread): node-rule geometry and island
 // constants of item b0 + tid, rounded to double-floats.
-template <int ORD>
+template <int ORD, class BS>
 __device__ __forceinline__ void batch_setup(const LinkParams& p, const uint64_t* __restrict__ keys,
                                             const uint32_t* __restrict__ list, long long n_items, long long b0,
-                                            BatchSm& bs, int tid) {
+                                            BS& bs, int tid) {
     long long it = b0 + tid;
     int np = 0, flags = 0;
     long long isl = -1;
@@ -138,8 +142,8 @@ struct RowGeo {
   Df o, im, ih, a0, a1, b0, b1, s0, s1, ph;
 };
 
-template <int ORD>
-__device__ __forceinline__ RowGeo row_geometry(const LinkParams& p, const BatchSm& bs, int ib, int np, int pi,
+template <int ORD, class BS>
+__device__ __forceinline__ RowGeo row_geometry(const LinkParams& p, const BS& bs, int ib, int np, int pi,
                                                int i) {
   RowGeo r;
   const Df y = {p.gl.xh[np][i], p.gl.xl[np][i]};
@@ -252,17 +256,36 @@ __device__ __forceinline__ void dw_recurrence(const float* __restrict__ trow, in
   }
 }
 
-template <int ORD, int KP>
-__global__ void __launch_bounds__(kThreads, KP == 8 ? 3 : (ORD == ORD_DW ? 5 : 4))
+// Launch shape of the main kernel: NT threads (and NT islands per batch) per
+// CTA, min_ctas resident CTAs per SM (the register budget follows from it) and
+// rows_max rows of constants per chunk.
+__host__ __device__ constexpr int min_ctas(int ord, int kp, int nt) {
+  return nt == 64 ? 8 : (kp == 8 ? 3 : (ord == ORD_DW ? 5 : 4));
+}
+__host__ __device__ constexpr int rows_max(int nt) { return nt == 64 ? 32 : kRowsMax; }
+
+// Fixed-order sum of the per-warp partial sums of a CTA.
+template <int NW>
+__device__ __forceinline__ float warp_sum(const float* r) {
+  if (NW == 4) return (r[0] + r[1]) + (r[2] + r[3]);
+  float t = r[0];
+#pragma unroll
+  for (int w = 1; w < NW; ++w) t += r[w];
+  return t;
+}
+
+template <int ORD, int KP, int NT>
+__global__ void __launch_bounds__(NT, min_ctas(ORD, KP, NT))
 integrate_fp32c_kernel(LinkParams p, const uint64_t* __restrict__ keys, const uint32_t* __restrict__ list,
                        long long n_items, float* __restrict__ terms, long long n_isl, int rows_per_chunk, int kpad,
                        Df G0, Df G1) {
   static_assert(KP % 2 == 0, "points per thread come in f32x2 pairs");
   constexpr int NPAIR = KP / 2;
-  __shared__ BatchSm bs;
-  __shared__ RowSm rs;
+  __shared__ BatchSmT<NT> bs;
+  __shared__ RowSm<rows_max(NT)> rs;
   __shared__ NodeSm ns;
-  __shared__ float red[4][kThreads / 32];
+  constexpr int NW = NT / 32;
+  __shared__ float red[4][NW];
   extern __shared__ __align__(16) float tab[];  // [rows_per_chunk][kpad] c_k of the chunk's rows (DW only)
 
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
@@ -284,21 +307,21 @@ integrate_fp32c_kernel(LinkParams p, const uint64_t* __restrict__ keys, const ui
   // threads per row (power of two), row slot and point slot of this thread
   int tpr = 1;
   while (tpr * KP < n) tpr <<= 1;
-  const int rows_per_pass = kThreads / tpr;
+  const int rows_per_pass = NT / tpr;
   const int lr = tid & (tpr - 1);
   const int rsub = tid / tpr;
 
-  for (int j = tid; j < n; j += kThreads) {
+  for (int j = tid; j < n; j += NT) {
     const float xh = p.gl.xh[1][j], xl = p.gl.xl[1][j];
     ns.x4[j] = make_float4(xh, xl, p.gl.x2h[1][j], p.gl.x2l[1][j]);
     ns.x2[j] = make_float2(xh * p.gl.x2h[1][j], p.gl.wf[1][j]);
   }
 
-  for (long long b0 = (long long)blockIdx.x * kBatch; b0 < n_items; b0 += (long long)gridDim.x * kBatch) {
+  for (long long b0 = (long long)blockIdx.x * NT; b0 < n_items; b0 += (long long)gridDim.x * NT) {
     // ---------------- 1. batch set-up, FP64, one island per thread
     batch_setup<ORD>(p, keys, list, n_items, b0, bs, tid);
     __syncthreads();
-    const int nb = (int)min((long long)kBatch, n_items - b0);
+    const int nb = (int)min((long long)NT, n_items - b0);
     // ---------------- 2./3. the islands of the batch, one after the other
     for (int ib = 0; ib < nb; ++ib) {
       const int np = bs.np[ib];
@@ -313,10 +336,10 @@ integrate_fp32c_kernel(LinkParams p, const uint64_t* __restrict__ keys, const ui
       const int rows = np * no;
       for (int c0 = 0; c0 < rows; c0 += rows_per_chunk) {
         const int rc = min(rows_per_chunk, rows - c0);
-        // ---- row constants in double-float; slot rr = 32 (tid mod 4) + tid / 4 (a
-        // bijection on 0..127) spreads the first 32 rows of a chunk over the four warps
+        // ---- row constants in double-float; slot rr = 32 (tid mod NW) + tid / NW (a
+        // bijection on 0..NT-1) spreads the first 32 rows of a chunk over the warps
         {
-          const int rr = (tid & 3) * 32 + (tid >> 2);
+          const int rr = (tid % NW) * 32 + tid / NW;
           if (rr < rc) {
             const int row = c0 + rr;
             const int pi = row / no, i = row - pi * no;
@@ -342,12 +365,17 @@ integrate_fp32c_kernel(LinkParams p, const uint64_t* __restrict__ keys, const ui
         }
         __syncthreads();
         // ---- c_k tables of the chunk's rows (DW): C_k 2^{-zeta_k log2(e) f3}
+        // Rounds of up to NT columns k; a round of nk < NT columns gives each column
+        // NT / nk threads that split the rows.  c_k and zeta_k stay in registers.
         if (ORD == ORD_DW) {
-          for (int k = tid; k < K; k += kThreads) {
-            const float ck = p.seg.ck_f[k], zk = p.seg.zeta_f[k];
+          for (int kb = 0; kb < K; kb += NT) {
+            const int nk = min(NT, K - kb);
+            const int g = NT / nk, col = tid % nk, grp = tid / nk;
+            if (grp < g) {
+              const int k = kb + col;
+              const float ck = p.seg.ck_f[k], zk = p.seg.zeta_f[k];
 #pragma unroll 8
-            for (int rr = 0; rr < rc; ++rr) {
-              tab[rr * kpad + k] = ck * ex2_approx(-zk * rs.f3[rr].x);
+              for (int rr = grp; rr < rc; rr += g) tab[rr * kpad + k] = ck * ex2_approx(-zk * rs.f3[rr].x);
             }
           }
           __syncthreads();
@@ -544,18 +572,18 @@ integrate_fp32c_kernel(LinkParams p, const uint64_t* __restrict__ keys, const ui
       __syncthreads();
       if (tid == 0) {
         const long long isl = bs.isl[ib];
-        const float t0 = (red[0][0] + red[0][1]) + (red[0][2] + red[0][3]);
+        const float t0 = warp_sum<NW>(red[0]);
         if (ORD == ORD_DW) {
           terms[isl] = bs.cf0[ib] * g2 * t0;
           if (cplx) {
-            const float t1 = (red[1][0] + red[1][1]) + (red[1][2] + red[1][3]);
-            const float t2 = (red[2][0] + red[2][1]) + (red[2][2] + red[2][3]);
-            const float t3 = (red[3][0] + red[3][1]) + (red[3][2] + red[3][3]);
+            const float t1 = warp_sum<NW>(red[1]);
+            const float t2 = warp_sum<NW>(red[2]);
+            const float t3 = warp_sum<NW>(red[3]);
             if (want_g) terms[3 * n_isl + isl] = bs.cf1[ib] * g2 * t1;
             if (want_h) terms[4 * n_isl + isl] = bs.cf2[ib] * g2 * (t2 * t2 + t3 * t3);
           }
         } else {
-          const float t1 = (red[1][0] + red[1][1]) + (red[1][2] + red[1][3]);
+          const float t1 = warp_sum<NW>(red[1]);
           terms[(ORD == ORD_E ? 1 : 2) * n_isl + isl] = bs.cf0[ib] * g2 * t1;
         }
       }
@@ -564,17 +592,17 @@ integrate_fp32c_kernel(LinkParams p, const uint64_t* __restrict__ keys, const ui
   }
 }
 
-template <int ORD, int KP>
+template <int ORD, int KP, int NT>
 cudaError_t launch_one(const LinkParams& p, const uint64_t* keys, const uint32_t* list, long long n_items, float* terms,
                        long long n_isl, cudaStream_t st) {
   if (n_items <= 0) return cudaSuccess;
   const int K = p.seg.K;
   int kpad = (K + 3) & ~3;
   if ((kpad & 7) == 0) kpad += 4;  // row stride = 4 (mod 8) words: 4 rows' 16-byte loads hit distinct banks
-  int rows = kRowsMax;
+  int rows = rows_max(NT);
   if (ORD == ORD_DW) {
     rows = kTabFloats / kpad;
-    if (rows > kRowsMax) rows = kRowsMax;
+    if (rows > rows_max(NT)) rows = rows_max(NT);
     if (rows < 1) rows = 1;
   }
   size_t smem = ORD == ORD_DW ? (size_t)rows * kpad * sizeof(float) : 0;
@@ -584,20 +612,20 @@ cudaError_t launch_one(const LinkParams& p, const uint64_t* keys, const uint32_t
   // static shared memory + the c_k table exceed the 48 KB default: opt in once per device
   static unsigned long long attr_done = 0;
   if (!(attr_done >> (dev & 63) & 1ull)) {
-    cudaError_t e = cudaFuncSetAttribute(integrate_fp32c_kernel<ORD, KP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(integrate_fp32c_kernel<ORD, KP, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          kTabFloats * (int)sizeof(float));
     if (e != cudaSuccess) return e;
     attr_done |= 1ull << (dev & 63);
   }
-  long long batches = (n_items + kBatch - 1) / kBatch;
-  long long blocks = (long long)sms * (KP == 8 ? 3 : (ORD == ORD_DW ? 5 : 4));
+  long long batches = (n_items + NT - 1) / NT;
+  long long blocks = (long long)sms * min_ctas(ORD, KP, NT);
   if (blocks > batches) blocks = batches;
   // 2 pi L beta2 and 2 pi^2 L beta3 as double-floats
   double g0 = 2.0 * kPi * p.L * p.beta2, g1 = 2.0 * kPi * kPi * p.L * p.beta3;
   float g0h = (float)g0, g1h = (float)g1;
   Df G0 = {g0h, (float)(g0 - (double)g0h)}, G1 = {g1h, (float)(g1 - (double)g1h)};
-  integrate_fp32c_kernel<ORD, KP><<<(unsigned)blocks, kThreads, smem, st>>>(p, keys, list, n_items, terms, n_isl,
-                                                                           rows, kpad, G0, G1);
+  integrate_fp32c_kernel<ORD, KP, NT><<<(unsigned)blocks, NT, smem, st>>>(p, keys, list, n_items, terms, n_isl,
+                                                                             rows, kpad, G0, G1);
   return cudaGetLastError();
 }
 
@@ -957,11 +985,11 @@ cudaError_t launch_fp32c_pass(int ord, const LinkParams& p, const uint64_t* keys
     return launch_general<ORD_F>(p, keys, list, n_items, terms, n_isl, st);
   }
   if (ord == ORD_DW) {
-    if (p.fp32c_kp == 8) return launch_one<ORD_DW, 8>(p, keys, list, n_items, terms, n_isl, st);
-    return launch_one<ORD_DW, 4>(p, keys, list, n_items, terms, n_isl, st);
+    if (p.fp32c_kp == 8) return launch_one<ORD_DW, 8, 128>(p, keys, list, n_items, terms, n_isl, st);
+    return launch_one<ORD_DW, 4, kDwThreads>(p, keys, list, n_items, terms, n_isl, st);
   }
-  if (ord == ORD_E) return launch_one<ORD_E, 4>(p, keys, list, n_items, terms, n_isl, st);
-  return launch_one<ORD_F, 4>(p, keys, list, n_items, terms, n_isl, st);
+  if (ord == ORD_E) return launch_one<ORD_E, 4, 128>(p, keys, list, n_items, terms, n_isl, st);
+  return launch_one<ORD_F, 4, 128>(p, keys, list, n_items, terms, n_isl, st);
 }
 
 }  // namespace egn
