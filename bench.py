@@ -218,6 +218,59 @@ def flops_per_point(precision: str, K: int) -> float:
     return 8.0 * K
 
 
+def run_mu_compare(args):
+    """The three forms of mu on the same GPU (Sec. III): FP64 integral form (Eq. 23,
+    the paper's numerical reference), FP64 segment (Eq. 7-10) and Maclaurin
+    (Eq. 4-6) closed forms, and the FP32C segment path, on Table I links of
+    n_ch channels of the 10.1 GHz grid around 1550 nm.  Prints one JSON line per
+    link: device ms per evaluation, the time reduction of each closed form
+    against the integral form, and the per-channel error of each closed form
+    against the integral form in dB (Fig. 8-10 analogues)."""
+    import numpy as np
+    import torch
+    from paper_2412_11614_gb300 import _build, egn, workloads as W
+    _build.build()
+    torch.cuda.set_device(0)
+    stream = torch.cuda.Stream()
+    for n_spans, cr in ((1, 0.28), (1, 1.12), (10, 1.12)):
+        wl = W.table1(n_spans=n_spans, cr=cr, fmt="QPSK", gl_order=args.mu_gl, n_ch=args.mu_n_ch)
+        ln = egn.link_from_workload(wl)
+        res, ms = {}, {}
+        for name, form, prec in (("fp64_integral", egn.EGN_MU_INTEGRAL, egn.EGN_PREC_FP64),
+                                 ("fp64_segment", egn.EGN_MU_SEGMENT, egn.EGN_PREC_FP64),
+                                 ("fp64_maclaurin", egn.EGN_MU_MACLAURIN, egn.EGN_PREC_FP64),
+                                 ("fp32c_segment", egn.EGN_MU_SEGMENT, egn.EGN_PREC_FP32C)):
+            opts = egn.make_opts(gl_order=wl.gl_order, dz_km=wl.dz_km, precision=prec, terms=egn.EGN_TERMS_EGN,
+                                 stream=stream.cuda_stream, mu_form=form)
+            ws = torch.empty(ln.workspace_size(opts), dtype=torch.uint8, device="cuda")
+            eta = torch.empty(wl.n_ch, dtype=torch.float64, device="cuda")
+            pn = torch.empty(wl.n_ch, dtype=torch.float64, device="cuda")
+            reps = 1 if form == egn.EGN_MU_INTEGRAL else 5
+            with torch.cuda.stream(stream):
+                if form != egn.EGN_MU_INTEGRAL:
+                    ln.nli_eta_device(opts, ws, eta, pn)
+                t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                t0.record(stream)
+                for _ in range(reps):
+                    ln.nli_eta_device(opts, ws, eta, pn)
+                t1.record(stream)
+            t1.synchronize()
+            ms[name] = t0.elapsed_time(t1) / reps
+            res[name] = eta.cpu().numpy()
+        ref = 10 * np.log10(res["fp64_integral"])
+        err = {k: 10 * np.log10(v) - ref for k, v in res.items() if k != "fp64_integral"}
+        line = {"workload": f"Table I: {wl.n_ch} ch x 10 GBd at 10.1 GHz, {n_spans} x 100 km, Cr {cr}, QPSK, "
+                            f"{wl.gl_order} x {wl.gl_order} Gauss-Legendre, dz 1 km",
+                "ms_per_eval": ms,
+                "time_reduction_vs_integral": {k: 1.0 - ms[k] / ms["fp64_integral"] for k in ms if k != "fp64_integral"},
+                "mae_db_vs_integral": {k: float(np.mean(np.abs(v))) for k, v in err.items()},
+                "max_abs_db_vs_integral": {k: float(np.max(np.abs(v))) for k, v in err.items()},
+                "islands": ln.island_count()[0]}
+        print(json.dumps(line), flush=True)
+        ln.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -230,7 +283,13 @@ def main():
     ap.add_argument("--n-ch", type=int, default=120, help="channels of the C+L grid (120 = the benchmark)")
     ap.add_argument("--points-per-thread", type=int, default=4, choices=[4, 8],
                     help="launch-shape tuning of the FP32C D/G/H pass")
+    ap.add_argument("--mu-compare", action="store_true",
+                    help="time and compare the integral, segment and Maclaurin forms of mu (Table I links)")
+    ap.add_argument("--mu-n-ch", type=int, default=31)
+    ap.add_argument("--mu-gl", type=int, default=16)
     args = ap.parse_args()
+    if args.mu_compare:
+        return run_mu_compare(args)
     if args.warmup < 3:
         log("warmup raised to 3 (timing rule)")
         args.warmup = 3

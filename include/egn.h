@@ -86,7 +86,11 @@ typedef struct {
     double length_m;
 } egn_span;
 
-enum { EGN_MU_SEGMENT = 0 };               /* Eq. 7-10; the only form on the GPU path */
+enum {
+  EGN_MU_SEGMENT = 0,   /* segment closed form, Eq. 7-10 (both precisions) */
+  EGN_MU_MACLAURIN = 1, /* Maclaurin closed form, Eq. 4-6 (FP64 only) */
+  EGN_MU_INTEGRAL = 2   /* numerical integral of Eq. 23, the reference form (FP64 only) */
+};
 enum { EGN_PREC_FP64 = 0, EGN_PREC_FP32C = 1 };
 enum { EGN_TERMS_GN = 0, EGN_TERMS_EGN = 1 };
 enum { EGN_FMT_GAUSS = 0, EGN_FMT_QPSK = 1, EGN_FMT_16QAM = 2, EGN_FMT_64QAM = 3 };
@@ -97,7 +101,12 @@ enum { EGN_FMT_GAUSS = 0, EGN_FMT_QPSK = 1, EGN_FMT_16QAM = 2, EGN_FMT_64QAM = 3
  *               panels of ceil(n/P) nodes, n inner nodes); 1 <= n <= 128.
  *   dz_km       segment length bound Delta z [km]: K = ceil(L / dz) segments of
  *               length L/K per span (Sec. II-C-2); K <= 1024.
- *   mu_form     EGN_MU_SEGMENT.
+ *   mu_form     EGN_MU_SEGMENT (Eq. 7-10, segments of length L/K), or, with
+ *               EGN_PREC_FP64 only, EGN_MU_MACLAURIN (Eq. 4-6) or
+ *               EGN_MU_INTEGRAL (Eq. 23 integrated numerically: 10-point
+ *               Gauss-Legendre on equal pieces of at most a quarter period
+ *               pi / (2 |chi|) of the phase factor; dz_km is then unused but
+ *               must be valid).  Other combinations: EGN_E_UNSUPPORTED.
  *   precision   EGN_PREC_FP64: every step in FP64 (the plain baseline);
  *               EGN_PREC_FP32C: FP32 integrand, phases reduced exactly with
  *               FP64 island constants and compensated FP32 (double-float)

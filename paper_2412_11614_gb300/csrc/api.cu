@@ -222,9 +222,12 @@ egn_status check_opts(const egn_link* l, const egn_opts* o) {
   if (l->n_ch <= 0) return fail(EGN_E_STATE, "egn_set_wdm has not been called");
   if (o->gl_order < 1 || o->gl_order > kMaxGl) return fail(EGN_E_INVALID_ARG, "gl_order %d not in [1, %d]", o->gl_order, kMaxGl);
   if (!finite_pos(o->dz_km)) return fail(EGN_E_INVALID_ARG, "dz_km must be positive");
-  if (o->mu_form != EGN_MU_SEGMENT) return fail(EGN_E_UNSUPPORTED, "only the segment form (Eq. 8-10) runs on the GPU");
+  if (o->mu_form != EGN_MU_SEGMENT && o->mu_form != EGN_MU_MACLAURIN && o->mu_form != EGN_MU_INTEGRAL)
+    return fail(EGN_E_INVALID_ARG, "unknown mu_form %d", o->mu_form);
   if (o->precision != EGN_PREC_FP64 && o->precision != EGN_PREC_FP32C)
     return fail(EGN_E_INVALID_ARG, "unknown precision %d", o->precision);
+  if (o->mu_form != EGN_MU_SEGMENT && o->precision != EGN_PREC_FP64)
+    return fail(EGN_E_UNSUPPORTED, "the Maclaurin and integral forms of mu run in FP64 only");
   if (o->terms != EGN_TERMS_GN && o->terms != EGN_TERMS_EGN) return fail(EGN_E_INVALID_ARG, "unknown terms %d", o->terms);
   if (o->timeout_ms < 0) return fail(EGN_E_INVALID_ARG, "timeout_ms < 0");
   if (!l->identical) {
@@ -291,6 +294,7 @@ egn_status ensure_tables(egn_link* l, const egn_opts* o) {
       ty.L = s.L;
       ty.dz = s.L / K;
       ty.r = std::exp(-s.alpha * ty.dz);
+      ty.pcr = l->ptot * s.cr;
       ty.seg.K = K;
       EGN_CUDA(cudaMemcpy(p, zeta.data(), K * sizeof(double), cudaMemcpyHostToDevice));
       ty.seg.zeta = (const double*)p;
@@ -379,6 +383,21 @@ ChannelTable channel_table(const egn_link* l) {
   return t;
 }
 
+// Form of mu and the constants of its Maclaurin and integral variants.
+void set_mu_params(LinkParams& p, const egn_link* l, const egn_opts* o) {
+  p.mu_form = o->mu_form;
+  p.btot = l->btot;
+  struct Rule {
+    double x[kMuGl], w[kMuGl];
+    Rule() { gauss_legendre(kMuGl, x, w); }
+  };
+  static const Rule rule;  // initialised once, thread-safe
+  for (int j = 0; j < kMuGl; ++j) {
+    p.mgx[j] = rule.x[j];
+    p.mgw[j] = rule.w[j];
+  }
+}
+
 LinkParams link_params(const egn_link* l, const egn_opts* o, int all_terms) {
   LinkParams p{};
   p.ch = channel_table(l);
@@ -396,6 +415,7 @@ LinkParams link_params(const egn_link* l, const egn_opts* o, int all_terms) {
   p.terms = o->terms;
   p.all_terms = all_terms;
   p.fp32c_kp = l->fp32c_kp;
+  set_mu_params(p, l, o);
   p.n_types = l->identical ? 1 : (int)l->type_si.size();
   for (int t = 0; t < p.n_types && t < kMaxTypes; ++t) p.types[t] = l->types[t];
   for (int s = 0; s < (int)l->span_type.size() && s < kMaxSpans; ++s) p.span_type[s] = l->span_type[s];
@@ -936,6 +956,7 @@ extern "C" egn_status egn_nli_eta_static(egn_link* l, const egn_opts* o, double*
     ty.L = sps[t].L;
     ty.dz = sps[t].L / Ks[t];
     ty.r = std::exp(-sps[t].alpha * ty.dz);
+    ty.pcr = l->ptot * sps[t].cr;
     ty.seg.K = Ks[t];
     ty.seg.zeta = (const double*)(b + o_zeta[t]);
     ty.seg.ck = (const double*)(b + o_ck[t]);
@@ -968,6 +989,7 @@ extern "C" egn_status egn_nli_eta_static(egn_link* l, const egn_opts* o, double*
   p.terms = o->terms;
   p.all_terms = 0;
   p.fp32c_kp = l->fp32c_kp;
+  set_mu_params(p, l, o);
 
   // plan -> integrate -> assemble on the caller's stream, workspace in the scratch
   Workspace ws = carve_workspace(b + ws_off, l->n_ch, l->cnt, o->precision);

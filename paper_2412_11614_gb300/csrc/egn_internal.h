@@ -76,10 +76,15 @@ constexpr int kMaxTypes = 4;
 constexpr int kMaxSpans = 64;
 struct SpanType {
   double alpha, beta2, beta3, gamma, L;
-  double dz;  // L / K
-  double r;   // e^{-alpha dz}
+  double dz;   // L / K
+  double r;    // e^{-alpha dz}
+  double pcr;  // P_tot Cr [1/(THz km)], the ISRS slope of Eq. 4 and Eq. 25
   SegmentTables seg;
 };
+
+// Forms of the FWM efficiency mu (egn_opts.mu_form).
+enum { MU_SEGMENT = 0, MU_MACLAURIN = 1, MU_INTEGRAL = 2 };
+constexpr int kMuGl = 10;  // Gauss-Legendre order per quarter period of the integral form
 
 // Everything an integrator launch needs, passed by value.  With n_types == 1
 // (identical spans) the single-type fields below describe the span and the
@@ -101,6 +106,9 @@ struct LinkParams {
   int terms;         // 0 GN, 1 EGN
   int all_terms;     // evaluate E..H on every island (parity checks)
   int fp32c_kp;      // points per thread of the FP32C D/G/H pass (4 or 8)
+  int mu_form;       // MU_SEGMENT, MU_MACLAURIN or MU_INTEGRAL (the last two: FP64 path)
+  double btot;       // B_tot [THz] of Eq. 25
+  double mgx[kMuGl], mgw[kMuGl];  // Gauss-Legendre rule of the integral form on [-1, 1]
   int n_types;                       // distinct span types (1 = identical spans)
   SpanType types[kMaxTypes];
   unsigned char span_type[kMaxSpans];  // type of span s, s = 0 .. n_spans - 1

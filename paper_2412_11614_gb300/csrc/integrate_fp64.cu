@@ -24,39 +24,110 @@ struct Cd {
 
 __device__ __forceinline__ Cd cmul(Cd a, Cd b) { return {a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re}; }
 
-// Upsilon at one point.  ck points at this row's c_k (stride ck_stride) or is
-// null, in which case c_k is formed from f3 on the fly.
+// (e^{(i chi - a) L} - 1) / (i chi - a) with the span phase chi L given in turns
+// reduced modulo 1 (tp), so that a large chi L loses no accuracy.
+__device__ __forceinline__ Cd lossy_closed_form(double chi, double a, double L, double tp) {
+  double s, c;
+  sincospi(2.0 * tp, &s, &c);
+  const double e = exp(-a * L);
+  const double xr = e * c - 1.0, xi = e * s;
+  const double den = a * a + chi * chi;
+  // (x)(-a - i chi) / (a^2 + chi^2)
+  return {(-a * xr + chi * xi) / den, (-chi * xr - a * xi) / den};
+}
+
+// Maclaurin closed form, Eq. 4-6: first order in e^{-zeta f} and second order in
+// the sinh normalisation of Eq. 25 give
+//   mu = eta_1 - (P_tot Cr f3 / alpha) (eta_1 - eta_2),
+//   eta_m = (e^{(i chi - m alpha) L} - 1) / (i chi - m alpha).
+__device__ __forceinline__ Cd mu_maclaurin(double chi, double f3, double alpha, double L, double pcr, double tp) {
+  const Cd e1 = lossy_closed_form(chi, alpha, L, tp);
+  const Cd e2 = lossy_closed_form(chi, 2.0 * alpha, L, tp);
+  const double k = pcr * f3 / alpha;
+  return {e1.re - k * (e1.re - e2.re), e1.im - k * (e1.im - e2.im)};
+}
+
+// Normalised ISRS power profile rho(z, f3) of Eq. 25 (with Eq. 14).
+__device__ __forceinline__ double rho_isrs(double z, double f3, double alpha, double pcr, double btot) {
+  const double zeta = pcr * (-expm1(-alpha * z) / alpha);
+  const double x = btot * zeta;
+  const double g = (x == 0.0) ? 1.0 : x * exp(-zeta * f3) / (2.0 * sinh(0.5 * x));
+  return g * exp(-alpha * z);
+}
+
+// Integral form, Eq. 23: mu = int_0^L rho(z, f3) e^{i chi z} dz by Gauss-Legendre
+// (order kMuGl) on npieces equal pieces, each at most a quarter period
+// pi / (2 |chi|) of the phase factor long.  Phases are taken in turns, chi z /
+// 2 pi, reduced modulo 1.
+__device__ __forceinline__ Cd mu_integral(const LinkParams& p, double chi, double f3, double alpha, double L,
+                                          double pcr) {
+  const double quarter = (chi != 0.0) ? kPi / (2.0 * fabs(chi)) : L;
+  long long np = (long long)ceil(L / quarter);
+  if (np < 1) np = 1;
+  const double h = L / (double)np, hh = 0.5 * h;
+  const double cturn = chi / (2.0 * kPi);
+  Cd sum = {0.0, 0.0};
+  for (long long q = 0; q < np; ++q) {
+    const double m = ((double)q + 0.5) * h;
+    Cd ps = {0.0, 0.0};
+    for (int j = 0; j < kMuGl; ++j) {
+      const double z = m + hh * p.mgx[j];
+      double t = cturn * z;
+      t -= rint(t);
+      double s, c;
+      sincospi(2.0 * t, &s, &c);
+      const double v = p.mgw[j] * rho_isrs(z, f3, alpha, pcr, p.btot);
+      ps.re += v * c;
+      ps.im += v * s;
+    }
+    sum.re += ps.re;
+    sum.im += ps.im;
+  }
+  return {sum.re * hh, sum.im * hh};
+}
+
+// Upsilon at one point.  Segment form: ck points at this row's c_k (stride
+// ck_stride) or is null, in which case c_k is formed from f3 on the fly.  The
+// Maclaurin and integral forms use f3 directly.
 __device__ __forceinline__ Cd upsilon_fp64(const LinkParams& p, double f1, double f2, double f, const double* ck,
                                            int ck_stride, double f3, double* af2_out, bool need_phase) {
   const int K = p.seg.K;
   double a = f1 - f, b = f2 - f;
   double bc = p.beta2 + kPi * p.beta3 * (f1 + f2);
   double chi = 4.0 * kPi * kPi * a * b * bc;
-  double tt = chi * (p.dz / (2.0 * kPi));
-  tt -= rint(tt);
-  double s, c;
-  sincospi(2.0 * tt, &s, &c);
-  Cd w = {p.r * c, p.r * s};
-  Cd acc = {0.0, 0.0};
-  if (ck) {
-    for (int k = K - 1; k >= 0; --k) {
-      acc = cmul(acc, w);
-      acc.re += ck[k * ck_stride];
-    }
-  } else {
-    for (int k = K - 1; k >= 0; --k) {
-      acc = cmul(acc, w);
-      acc.re += p.seg.ck[k] * exp(-p.seg.zeta[k] * f3);
-    }
-  }
-  // (w - 1)/(i chi - alpha) = (w - 1)(-alpha - i chi)/(alpha^2 + chi^2)
-  double xr = w.re - 1.0, xi = w.im;
-  double den = p.alpha * p.alpha + chi * chi;
-  Cd q = {(-p.alpha * xr + chi * xi) / den, (-chi * xr - p.alpha * xi) / den};
-  Cd mu = cmul(acc, q);
-  // phased array of N identical spans
+  // span phase chi L in turns (phased array, closed forms)
   double tp = chi * (p.L / (2.0 * kPi));
   tp -= rint(tp);
+  Cd mu;
+  if (p.mu_form == MU_MACLAURIN) {
+    mu = mu_maclaurin(chi, f3, p.alpha, p.L, p.types[0].pcr, tp);
+  } else if (p.mu_form == MU_INTEGRAL) {
+    mu = mu_integral(p, chi, f3, p.alpha, p.L, p.types[0].pcr);
+  } else {
+    double tt = chi * (p.dz / (2.0 * kPi));
+    tt -= rint(tt);
+    double s, c;
+    sincospi(2.0 * tt, &s, &c);
+    Cd w = {p.r * c, p.r * s};
+    Cd acc = {0.0, 0.0};
+    if (ck) {
+      for (int k = K - 1; k >= 0; --k) {
+        acc = cmul(acc, w);
+        acc.re += ck[k * ck_stride];
+      }
+    } else {
+      for (int k = K - 1; k >= 0; --k) {
+        acc = cmul(acc, w);
+        acc.re += p.seg.ck[k] * exp(-p.seg.zeta[k] * f3);
+      }
+    }
+    // (w - 1)/(i chi - alpha) = (w - 1)(-alpha - i chi)/(alpha^2 + chi^2)
+    double xr = w.re - 1.0, xi = w.im;
+    double den = p.alpha * p.alpha + chi * chi;
+    Cd q = {(-p.alpha * xr + chi * xi) / den, (-chi * xr - p.alpha * xi) / den};
+    mu = cmul(acc, q);
+  }
+  // phased array of N identical spans
   double N = (double)p.n_spans;
   double ratio = (tp == 0.0) ? N : sinpi(N * tp) / sinpi(tp);
   *af2_out = ratio * ratio;
@@ -79,24 +150,31 @@ __device__ __forceinline__ Cd upsilon_fp64_general(const LinkParams& p, double f
   for (int t = 0; t < p.n_types; ++t) {
     const SpanType& ty = p.types[t];
     const double chi = 4.0 * kPi * kPi * a * b * (ty.beta2 + kPi * ty.beta3 * (f1 + f2));
-    double tt = chi * (ty.dz / (2.0 * kPi));
-    tt -= rint(tt);
-    double s, c;
-    sincospi(2.0 * tt, &s, &c);
-    const Cd w = {ty.r * c, ty.r * s};
-    Cd acc = {0.0, 0.0};
-    const int K = ty.seg.K;
-    for (int k = K - 1; k >= 0; --k) {
-      acc = cmul(acc, w);
-      acc.re += ck ? ck[(koff[t] + k) * 32] : ty.seg.ck[k] * exp(-ty.seg.zeta[k] * f3);
-    }
-    const double xr = w.re - 1.0, xi = w.im;
-    const double den = ty.alpha * ty.alpha + chi * chi;
-    const Cd q = {(-ty.alpha * xr + chi * xi) / den, (-chi * xr - ty.alpha * xi) / den};
-    const Cd m = cmul(acc, q);
-    mu[t] = {ty.gamma * m.re, ty.gamma * m.im};
     double tp = chi * (ty.L / (2.0 * kPi));
     tp -= rint(tp);
+    double s, c;
+    Cd m;
+    if (p.mu_form == MU_MACLAURIN) {
+      m = mu_maclaurin(chi, f3, ty.alpha, ty.L, ty.pcr, tp);
+    } else if (p.mu_form == MU_INTEGRAL) {
+      m = mu_integral(p, chi, f3, ty.alpha, ty.L, ty.pcr);
+    } else {
+      double tt = chi * (ty.dz / (2.0 * kPi));
+      tt -= rint(tt);
+      sincospi(2.0 * tt, &s, &c);
+      const Cd w = {ty.r * c, ty.r * s};
+      Cd acc = {0.0, 0.0};
+      const int K = ty.seg.K;
+      for (int k = K - 1; k >= 0; --k) {
+        acc = cmul(acc, w);
+        acc.re += ck ? ck[(koff[t] + k) * 32] : ty.seg.ck[k] * exp(-ty.seg.zeta[k] * f3);
+      }
+      const double xr = w.re - 1.0, xi = w.im;
+      const double den = ty.alpha * ty.alpha + chi * chi;
+      const Cd q = {(-ty.alpha * xr + chi * xi) / den, (-chi * xr - ty.alpha * xi) / den};
+      m = cmul(acc, q);
+    }
+    mu[t] = {ty.gamma * m.re, ty.gamma * m.im};
     sincospi(2.0 * tp, &s, &c);
     ph[t] = {c, s};
   }
@@ -166,7 +244,7 @@ __global__ void __launch_bounds__(32) integrate_fp64_kernel(LinkParams p, const 
         double outer_h;
         if (ORD == ORD_DW) {
           double f3 = nu3 + o;
-          if (active) {
+          if (active && p.mu_form == MU_SEGMENT) {
             if (p.n_types == 1) {
               for (int k = 0; k < p.seg.K; ++k) ck_s[k * 32 + lane] = p.seg.ck[k] * exp(-p.seg.zeta[k] * f3);
             } else {
@@ -195,7 +273,7 @@ __global__ void __launch_bounds__(32) integrate_fp64_kernel(LinkParams p, const 
             double f1 = nu1 + u, f2 = nu2 + v;
             double af2;
             if (p.n_types == 1 && ORD == ORD_DW && !want_g && !want_h) {
-              Cd mu = upsilon_fp64(p, f1, f2, nu, ckrow, 32, 0.0, &af2, false);
+              Cd mu = upsilon_fp64(p, f1, f2, nu, ckrow, 32, nu3 + w, &af2, false);
               double y2 = p.gamma * p.gamma * (mu.re * mu.re + mu.im * mu.im) * af2;
               dsum += wo * wi * h1 * h2 * h3 * y2;
             } else {

@@ -16,6 +16,8 @@ from . import _build
 
 EGN_OK, EGN_E_INVALID_ARG, EGN_E_UNSUPPORTED, EGN_E_NOMEM, EGN_E_CUDA, EGN_E_TIMEOUT, EGN_E_STATE, EGN_E_CAPACITY = range(8)
 EGN_MU_SEGMENT = 0
+EGN_MU_MACLAURIN = 1
+EGN_MU_INTEGRAL = 2
 EGN_PREC_FP64, EGN_PREC_FP32C = 0, 1
 EGN_TERMS_GN, EGN_TERMS_EGN = 0, 1
 EGN_FMT = {"GAUSS": 0, "QPSK": 1, "16QAM": 2, "64QAM": 3}
@@ -114,8 +116,8 @@ def egn_gauss_legendre(n: int):
 
 
 def make_opts(gl_order=32, dz_km=1.0, precision=EGN_PREC_FP32C, terms=EGN_TERMS_EGN, timeout_ms=0,
-              stream: Optional[int] = None) -> egn_opts:
-    return egn_opts(int(gl_order), float(dz_km), EGN_MU_SEGMENT, int(precision), int(terms), int(timeout_ms),
+              stream: Optional[int] = None, mu_form=EGN_MU_SEGMENT) -> egn_opts:
+    return egn_opts(int(gl_order), float(dz_km), int(mu_form), int(precision), int(terms), int(timeout_ms),
                     C.c_void_p(stream) if stream else None)
 
 
