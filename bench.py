@@ -271,6 +271,58 @@ def run_mu_compare(args):
     return 0
 
 
+def run_batch_compare(args):
+    """Many links at once (egn_batch_*): the same links evaluated one after the
+    other through egn_nli_eta_device on one stream, against one launch of the
+    batch's CUDA graph (every link an independent branch).  Links: the C+L grid
+    cut to 8..48 channels, 1..10 spans, FP32C.  Prints one JSON line."""
+    import numpy as np
+    import torch
+    from paper_2412_11614_gb300 import _build, egn, workloads as W
+    _build.build()
+    torch.cuda.set_device(0)
+    stream = torch.cuda.Stream()
+    wls = []
+    for i in range(args.batch_links):
+        wl = W.config_cl(n_ch=8 + 8 * (i % 6), n_spans=1 + (i % 10), seed=i)
+        wls.append(wl)
+    links = [egn.link_from_workload(w) for w in wls]
+    opts = egn.make_opts(gl_order=32, precision=egn.EGN_PREC_FP32C, stream=stream.cuda_stream)
+    ws = [torch.empty(ln.workspace_size(opts), dtype=torch.uint8, device="cuda") for ln in links]
+    outs = [(torch.empty(ln.n_ch, dtype=torch.float64, device="cuda"),
+             torch.empty(ln.n_ch, dtype=torch.float64, device="cuda")) for ln in links]
+
+    def one_by_one():
+        for ln, w, (e, p) in zip(links, ws, outs):
+            ln.nli_eta_device(opts, w, e, p)
+
+    b = egn.Batch(links, opts)
+
+    def timed(fn, reps):
+        with torch.cuda.stream(stream):
+            for _ in range(3):
+                fn()
+            t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            t0.record(stream)
+            for _ in range(reps):
+                fn()
+            t1.record(stream)
+        t1.synchronize()
+        return t0.elapsed_time(t1) / reps
+
+    seq_ms = timed(one_by_one, args.steps)
+    graph_ms = timed(lambda: b.launch(stream.cuda_stream), args.steps)
+    got = b.read(stream.cuda_stream)
+    same = all(np.array_equal(g[0], o[0].cpu().numpy()) for g, o in zip(got, outs))
+    n_ch = int(b.offsets[-1])
+    print(json.dumps({"links": len(links), "channels": n_ch,
+                      "workload": "C+L grid cut to 8..48 channels, 1..10 x 80 km, 32 x 32 GL, FP32C, EGN",
+                      "ms_one_by_one": seq_ms, "ms_graph": graph_ms, "speedup": seq_ms / graph_ms,
+                      "channel_evals_per_s_graph": n_ch / (graph_ms * 1e-3), "results_identical": same}), flush=True)
+    b.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -287,9 +339,14 @@ def main():
                     help="time and compare the integral, segment and Maclaurin forms of mu (Table I links)")
     ap.add_argument("--mu-n-ch", type=int, default=31)
     ap.add_argument("--mu-gl", type=int, default=16)
+    ap.add_argument("--batch", action="store_true",
+                    help="time a batch of small links: one by one vs one graph launch")
+    ap.add_argument("--batch-links", type=int, default=24)
     args = ap.parse_args()
     if args.mu_compare:
         return run_mu_compare(args)
+    if args.batch:
+        return run_batch_compare(args)
     if args.warmup < 3:
         log("warmup raised to 3 (timing rule)")
         args.warmup = 3

@@ -187,6 +187,45 @@ egn_status egn_nli_eta_device(egn_link* link, const egn_opts* opts, void* worksp
  * other threads, other links) race and must be serialised by the caller. */
 egn_status egn_nli_eta_static(egn_link* link, const egn_opts* opts, double* eta_dev, double* pnli_dev);
 
+/* ------------------------------------------------------------------ batches
+ * Many links evaluated together (the paper evaluates one link at a time; its
+ * parallel strategy distributes the islands of one link over workers).
+ *
+ * egn_batch_create snapshots n_links >= 1 links that have a comb
+ * (egn_set_wdm) and share a device: each link's channel, segment and
+ * Gauss-Legendre tables for `opts` are copied into batch-owned device memory,
+ * so later egn_set_wdm calls or egn_link_destroy on the links do not affect
+ * the batch.  It allocates one workspace per link and the outputs of all
+ * links, runs the whole evaluation once (validation; egn_batch_read can read
+ * its results), and captures it into a CUDA graph in which every link's chain
+ * (island planner, integrator passes, assembly) is an independent branch.
+ * opts->stream is ignored; opts->timeout_ms applies to egn_batch_read.
+ * Errors as egn_nli_eta (the first failing link is reported).
+ *
+ * egn_batch_launch enqueues one evaluation of every link (one graph launch) on
+ * `stream` (NULL = legacy default stream); asynchronous.  Launches on one
+ * batch must not overlap on the GPU (they share the batch's workspaces).
+ *
+ * egn_batch_outputs gives the device arrays eta and P_NLI of all channels,
+ * link after link, and the host array offsets[0..n_links] of each link's
+ * first channel (offsets[n_links] = all channels); valid until destroy.
+ *
+ * egn_batch_read waits (opts->timeout_ms) for the work queued on `stream`,
+ * checks every link's device status and copies eta and P_NLI of all channels
+ * to host arrays of offsets[n_links] doubles (either may be NULL).
+ *
+ * egn_nli_eta_batch: one evaluation of n links without a graph; eta[i] and
+ * pnli[i] are host arrays of link i's n_ch doubles (NULL entries skipped). */
+typedef struct egn_batch egn_batch;
+egn_status egn_batch_create(egn_link* const* links, int n_links, const egn_opts* opts, egn_batch** out);
+egn_status egn_batch_launch(egn_batch* batch, void* stream);
+egn_status egn_batch_outputs(const egn_batch* batch, const double** eta_dev, const double** pnli_dev,
+                             const long long** offsets);
+egn_status egn_batch_read(egn_batch* batch, void* stream, double* eta, double* pnli);
+void egn_batch_destroy(egn_batch* batch);
+egn_status egn_nli_eta_batch(egn_link* const* links, int n_links, const egn_opts* opts, double* const* eta,
+                             double* const* pnli);
+
 /* Per-island terms for parity checks on sampled islands: for each of n_isl
  * islands given as 4 ints (coi, n1, n2, n3), writes 5 doubles (D, E, F, G, H)
  * into terms_out (host), evaluated by the same device kernels as egn_nli_eta.
@@ -205,6 +244,24 @@ egn_status egn_plan_islands(egn_link* link, long long max, int* coi_n1_n2_n3, lo
  *   D/G/H pass, 4 (default) or 8. */
 enum { EGN_TUNE_FP32C_POINTS_PER_THREAD = 1 };
 egn_status egn_set_tuning(egn_link* link, int param, int value);
+
+/* Autotuning (Sec. III-D, Fig. 11: Delta z trades accuracy for time).  With
+ * opts (segment form) as the base, evaluates the link at dz_ref_km, then the
+ * n_candidates segment bounds dz_candidates from the coarsest down, and picks
+ * the coarsest whose worst channel differs from the reference by at most
+ * target_db (no candidate qualifies: dz_ref_km itself, error 0).  For
+ * EGN_PREC_FP32C it then times 4 and 8 points per thread of the D/G/H pass at
+ * the chosen Delta z (median of 5 device-timed evaluations each) and sets the
+ * faster on the link (egn_set_tuning).  Synchronous; the link's own workspace
+ * and a private stream are used.  Candidates finer than dz_ref_km are skipped. */
+typedef struct {
+    double dz_km;          /* chosen segment-length bound */
+    int points_per_thread; /* FP32C D/G/H launch shape now set on the link */
+    double max_err_db;     /* worst channel |10 log10(eta(dz) / eta(dz_ref))| */
+    double ms;             /* device ms of one evaluation with the choice */
+} egn_tune_result;
+egn_status egn_autotune(egn_link* link, const egn_opts* opts, double target_db, const double* dz_candidates,
+                        int n_candidates, double dz_ref_km, egn_tune_result* out);
 
 /* Per-stage device timing.  With profiling on, every evaluation records CUDA
  * events on its stream around five stages; egn_last_timings waits for the last

@@ -12,10 +12,9 @@
 #include <thread>
 #include <vector>
 
-#include "../../include/egn.h"
-#include "egn_internal.h"
+#include "link.h"
 
-namespace {
+namespace egn_host {
 
 thread_local std::string g_last_error;
 
@@ -29,81 +28,10 @@ egn_status fail(egn_status s, const char* fmt, ...) {
   return s;
 }
 
-#define EGN_CUDA(call)                                                                          \
-  do {                                                                                          \
-    cudaError_t e_ = (call);                                                                    \
-    if (e_ != cudaSuccess) return fail(EGN_E_CUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
-  } while (0)
+}  // namespace egn_host
 
-bool finite_pos(double x) { return std::isfinite(x) && x > 0.0; }
+using namespace egn_host;
 
-size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
-
-// Device buffer owned by a link.
-struct DevBuf {
-  void* p = nullptr;
-  size_t bytes = 0;
-  cudaError_t ensure(size_t want) {
-    if (want <= bytes && p) return cudaSuccess;
-    if (p) cudaFree(p);
-    p = nullptr;
-    bytes = 0;
-    cudaError_t e = cudaMalloc(&p, want);
-    if (e == cudaSuccess) bytes = want;
-    return e;
-  }
-  void release() {
-    if (p) cudaFree(p);
-    p = nullptr;
-    bytes = 0;
-  }
-};
-
-}  // namespace
-
-struct egn_link {
-  std::vector<egn_span> spans_si;
-  bool identical = true;
-  std::vector<egn_span> type_si;      // distinct span types, in order of first appearance
-  std::vector<unsigned char> span_type;
-  // comb (internal units)
-  int n_ch = 0;
-  double fc_hz = 0, btot = 0, ptot = 0, rolloff = 0;
-  std::vector<double> nu, R, W, P, phi, psi;
-  bool mixed_rates = false, any_corr = false;
-  egn::PlanCounts cnt{};
-  std::vector<long long> per_coi;
-  int device = -1;
-  DevBuf d_ch;  // 6 arrays of n_ch doubles
-  // cached tables for the last (dz, gl_order)
-  double tab_dz = -1.0;
-  int tab_gl = -1;
-  int K = 0;
-  egn::Span span{};
-  egn::SpanType types[egn::kMaxTypes] = {};
-  DevBuf d_seg, d_gl;
-  egn::SegmentTables seg{};
-  egn::GlTables gl{};
-  int fp32c_kp = 4;  // tuning: points per thread of the FP32C D/G/H pass
-  // optional per-stage device timing of the last evaluation
-  bool prof_on = false;
-  bool prof_valid = false;
-  cudaEvent_t prof_ev[6] = {};
-  // library-owned workspace and pinned staging for the host API
-  DevBuf ws;
-  double* h_stage = nullptr;  // [2 n_ch + 1]
-  DevBuf d_stage;
-  ~egn_link() {
-    d_ch.release();
-    d_seg.release();
-    d_gl.release();
-    ws.release();
-    d_stage.release();
-    if (h_stage) cudaFreeHost(h_stage);
-    for (auto& e : prof_ev)
-      if (e) cudaEventDestroy(e);
-  }
-};
 
 namespace egn {
 
@@ -195,7 +123,7 @@ Workspace carve_workspace(void* base, int n_ch, const PlanCounts& c, int precisi
 
 }  // namespace egn
 
-namespace {
+namespace egn_host {
 
 using namespace egn;
 
@@ -248,15 +176,6 @@ egn_status check_opts(const egn_link* l, const egn_opts* o) {
   return EGN_OK;
 }
 
-struct DeviceGuard {
-  int prev = -1;
-  explicit DeviceGuard(int dev) {
-    if (dev >= 0 && cudaGetDevice(&prev) == cudaSuccess && prev != dev) cudaSetDevice(dev); else prev = -1;
-  }
-  ~DeviceGuard() {
-    if (prev >= 0) cudaSetDevice(prev);
-  }
-};
 
 // (Re)build the segment and Gauss-Legendre tables for these options.
 egn_status ensure_tables(egn_link* l, const egn_opts* o) {
@@ -510,7 +429,7 @@ void qam_moments(int m, double* phi, double* psi) {
   *psi = mu6 - 9.0 * mu4 + 12.0;
 }
 
-}  // namespace
+}  // namespace egn_host
 
 extern "C" {
 

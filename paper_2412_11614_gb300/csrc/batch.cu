@@ -1,0 +1,291 @@
+// batch.cu -- many links evaluated by one CUDA graph.
+//
+// egn_batch_create snapshots every link (its channel, segment and
+// Gauss-Legendre tables are copied into batch-owned device memory, so later
+// egn_set_wdm calls or egn_link_destroy do not touch the batch), sizes one
+// workspace per link in a single allocation, runs the whole evaluation once
+// without capture (which validates it and completes every lazy launch set-up),
+// then captures the same sequence into a CUDA graph.  In the graph each link's
+// chain -- status reset, planner, integrator passes, assembly -- is an
+// independent branch on one of up to kStreams capture streams, so links that
+// underfill the GPU run side by side.  egn_batch_launch replays the graph with
+// one call; outputs of all links are concatenated in link order.
+#include <algorithm>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "link.h"
+
+using namespace egn_host;
+using egn::ChannelTable;
+using egn::LinkParams;
+using egn::PlanCounts;
+using egn::Workspace;
+
+namespace {
+
+constexpr int kStreams = 8;  // capture streams: concurrent branches of the graph
+
+// Snapshot of one link inside a batch.
+struct BatchLink {
+  int n_ch = 0;
+  PlanCounts cnt{};
+  LinkParams p{};       // pointers rebased into the batch's table copy
+  ChannelTable ch{};    // = p.ch
+  size_t tab_off = 0;   // offset of this link's table copy in d_tab
+  size_t ws_off = 0;    // offset of its workspace in d_ws
+};
+
+// Move q from [old, old + bytes) to the same offset after nb.
+template <class T>
+void rebase(const T*& q, const void* old, size_t bytes, const void* nb) {
+  const char* c = (const char*)q;
+  if (q && c >= (const char*)old && c < (const char*)old + bytes) q = (const T*)((const char*)nb + (c - (const char*)old));
+}
+
+void rebase_params(LinkParams& p, const egn_link* l, char* ch_copy, char* seg_copy, char* gl_copy) {
+  ChannelTable& c = p.ch;
+  for (const double** q : {&c.nu, &c.R, &c.W, &c.P, &c.phi, &c.psi}) rebase(*q, l->d_ch.p, l->d_ch.bytes, ch_copy);
+  auto seg = [&](egn::SegmentTables& t) {
+    rebase(t.zeta, l->d_seg.p, l->d_seg.bytes, seg_copy);
+    rebase(t.ck, l->d_seg.p, l->d_seg.bytes, seg_copy);
+    rebase(t.zeta_f, l->d_seg.p, l->d_seg.bytes, seg_copy);
+    rebase(t.ck_f, l->d_seg.p, l->d_seg.bytes, seg_copy);
+  };
+  seg(p.seg);
+  for (int t = 0; t < egn::kMaxTypes; ++t) seg(p.types[t].seg);
+  for (int q = 0; q < 4; ++q) {
+    rebase(p.gl.x[q], l->d_gl.p, l->d_gl.bytes, gl_copy);
+    rebase(p.gl.w[q], l->d_gl.p, l->d_gl.bytes, gl_copy);
+    rebase(p.gl.xh[q], l->d_gl.p, l->d_gl.bytes, gl_copy);
+    rebase(p.gl.xl[q], l->d_gl.p, l->d_gl.bytes, gl_copy);
+    rebase(p.gl.x2h[q], l->d_gl.p, l->d_gl.bytes, gl_copy);
+    rebase(p.gl.x2l[q], l->d_gl.p, l->d_gl.bytes, gl_copy);
+    rebase(p.gl.wf[q], l->d_gl.p, l->d_gl.bytes, gl_copy);
+  }
+}
+
+}  // namespace
+
+struct egn_batch {
+  int device = -1;
+  egn_opts opts{};
+  std::vector<BatchLink> links;
+  std::vector<long long> off;  // channel offsets, off[n] = all channels
+  DevBuf d_tab, d_ws, d_out;   // table copies; workspaces; eta | pnli | status
+  double* h_stage = nullptr;   // pinned: eta | pnli | status of every link
+  cudaStream_t cap = nullptr;
+  cudaStream_t st[kStreams] = {};
+  cudaEvent_t fork = nullptr, join[kStreams] = {};
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  long long total() const { return off.back(); }
+  double* eta() const { return (double*)d_out.p; }
+  double* pnli() const { return (double*)d_out.p + total(); }
+  int* status() const { return (int*)((double*)d_out.p + 2 * total()); }
+  ~egn_batch() {
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+    for (auto& e : join)
+      if (e) cudaEventDestroy(e);
+    if (fork) cudaEventDestroy(fork);
+    for (auto& s : st)
+      if (s) cudaStreamDestroy(s);
+    if (cap) cudaStreamDestroy(cap);
+    if (h_stage) cudaFreeHost(h_stage);
+    d_tab.release();
+    d_ws.release();
+    d_out.release();
+  }
+};
+
+namespace {
+
+// The whole evaluation of the batch: fork from `root`, one branch per link on
+// st[i mod kStreams], join back into `root`.
+egn_status enqueue(egn_batch* b, cudaStream_t root) {
+  const int ns = std::min<int>(kStreams, (int)b->links.size());
+  EGN_CUDA(cudaEventRecord(b->fork, root));
+  for (int j = 0; j < ns; ++j) EGN_CUDA(cudaStreamWaitEvent(b->st[j], b->fork, 0));
+  for (size_t i = 0; i < b->links.size(); ++i) {
+    const BatchLink& L = b->links[i];
+    cudaStream_t s = b->st[i % ns];
+    Workspace ws = egn::carve_workspace((char*)b->d_ws.p + L.ws_off, L.n_ch, L.cnt, b->opts.precision);
+    EGN_CUDA(cudaMemsetAsync(ws.status, 0, sizeof(int), s));
+    EGN_CUDA(egn::launch_plan(L.ch, ws, s));
+    EGN_CUDA(integrate(L.p, b->opts.precision, ws.keys, L.cnt.n_isl, ws.h_idx, L.cnt.n_half, ws.e_idx, L.cnt.n_e,
+                       ws.f_idx, L.cnt.n_f, ws.terms, s, nullptr));
+    EGN_CUDA(egn::launch_assemble(L.ch, half_offsets(ws, L.n_ch), ws.keys, ws.h_idx, L.cnt.n_isl, ws.terms,
+                                  b->opts.precision, b->opts.terms, b->eta() + b->off[i], b->pnli() + b->off[i], s));
+    EGN_CUDA(cudaMemcpyAsync(b->status() + i, ws.status, sizeof(int), cudaMemcpyDeviceToDevice, s));
+  }
+  for (int j = 0; j < ns; ++j) {
+    EGN_CUDA(cudaEventRecord(b->join[j], b->st[j]));
+    EGN_CUDA(cudaStreamWaitEvent(root, b->join[j], 0));
+  }
+  return EGN_OK;
+}
+
+// Copy outputs and statuses to the pinned stage on `st` and wait (timeout).
+egn_status stage_and_check(egn_batch* b, cudaStream_t st) {
+  const long long n = b->total();
+  const size_t bytes = (size_t)(2 * n) * sizeof(double) + b->links.size() * sizeof(int);
+  EGN_CUDA(cudaMemcpyAsync(b->h_stage, b->d_out.p, bytes, cudaMemcpyDeviceToHost, st));
+  cudaEvent_t ev;
+  EGN_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+  cudaError_t re = cudaEventRecord(ev, st);
+  if (re != cudaSuccess) { cudaEventDestroy(ev); return fail(EGN_E_CUDA, "cudaEventRecord: %s", cudaGetErrorString(re)); }
+  egn_status s = wait_event(ev, b->opts.timeout_ms);
+  cudaEventDestroy(ev);
+  if (s != EGN_OK) return s;
+  const int* stat = (const int*)(b->h_stage + 2 * n);
+  for (size_t i = 0; i < b->links.size(); ++i)
+    if (stat[i]) return fail(EGN_E_CUDA, "device planner overflow in link %zu (status %d)", i, stat[i]);
+  return EGN_OK;
+}
+
+egn_status create(egn_link* const* links, int n_links, const egn_opts* o, bool capture, egn_batch* b) {
+  if (!links || n_links <= 0 || !o) return fail(EGN_E_INVALID_ARG, "need n_links >= 1 links and options");
+  b->opts = *o;
+  b->opts.stream = nullptr;
+  b->device = links[0] ? links[0]->device : -1;
+  size_t tab = 0, ws = 0;
+  b->off.assign(1, 0);
+  for (int i = 0; i < n_links; ++i) {
+    egn_link* l = links[i];
+    if (!l) return fail(EGN_E_INVALID_ARG, "link %d is null", i);
+    egn_status s = check_opts(l, o);
+    if (s != EGN_OK) return s;
+    if (l->device != b->device) return fail(EGN_E_INVALID_ARG, "links of one batch must share a device");
+    DeviceGuard g(l->device);
+    s = ensure_tables(l, o);
+    if (s != EGN_OK) return s;
+    BatchLink L;
+    L.n_ch = l->n_ch;
+    L.cnt = l->cnt;
+    L.tab_off = tab;
+    tab += align256(l->d_ch.bytes) + align256(l->d_seg.bytes) + align256(l->d_gl.bytes);
+    L.ws_off = ws;
+    ws += align256(egn::workspace_bytes(l->n_ch, l->cnt, o->precision));
+    b->links.push_back(L);
+    b->off.push_back(b->off.back() + l->n_ch);
+  }
+  DeviceGuard g(b->device);
+  EGN_CUDA(cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking));
+  for (auto& s : b->st) EGN_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+  EGN_CUDA(cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming));
+  for (auto& e : b->join) EGN_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+  cudaError_t e = b->d_tab.ensure(tab);
+  if (e == cudaSuccess) e = b->d_ws.ensure(ws);
+  const size_t out_b = (size_t)(2 * b->total()) * sizeof(double) + (size_t)n_links * sizeof(int);
+  if (e == cudaSuccess) e = b->d_out.ensure(out_b);
+  if (e != cudaSuccess) return fail(EGN_E_NOMEM, "batch cudaMalloc: %s", cudaGetErrorString(e));
+  EGN_CUDA(cudaMallocHost((void**)&b->h_stage, out_b));
+  // table snapshot (device to device), launch parameters rebased onto it
+  for (int i = 0; i < n_links; ++i) {
+    egn_link* l = links[i];
+    BatchLink& L = b->links[i];
+    char* base = (char*)b->d_tab.p + L.tab_off;
+    char* ch_c = base;
+    char* seg_c = ch_c + align256(l->d_ch.bytes);
+    char* gl_c = seg_c + align256(l->d_seg.bytes);
+    EGN_CUDA(cudaMemcpyAsync(ch_c, l->d_ch.p, l->d_ch.bytes, cudaMemcpyDeviceToDevice, b->cap));
+    EGN_CUDA(cudaMemcpyAsync(seg_c, l->d_seg.p, l->d_seg.bytes, cudaMemcpyDeviceToDevice, b->cap));
+    EGN_CUDA(cudaMemcpyAsync(gl_c, l->d_gl.p, l->d_gl.bytes, cudaMemcpyDeviceToDevice, b->cap));
+    L.p = link_params(l, o, 0);
+    rebase_params(L.p, l, ch_c, seg_c, gl_c);
+    L.ch = L.p.ch;
+  }
+  // one plain run: validates the batch and completes lazy launch set-up
+  egn_status s = enqueue(b, b->cap);
+  if (s != EGN_OK) return s;
+  s = stage_and_check(b, b->cap);
+  if (s != EGN_OK || !capture) return s;
+  // capture
+  EGN_CUDA(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal));
+  s = enqueue(b, b->cap);
+  cudaGraph_t gr = nullptr;
+  cudaError_t ce = cudaStreamEndCapture(b->cap, &gr);
+  if (s != EGN_OK) {
+    if (gr) cudaGraphDestroy(gr);
+    return s;
+  }
+  if (ce != cudaSuccess) return fail(EGN_E_CUDA, "graph capture: %s", cudaGetErrorString(ce));
+  b->graph = gr;
+  EGN_CUDA(cudaGraphInstantiate(&b->exec, b->graph, 0));
+  return EGN_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+egn_status egn_batch_create(egn_link* const* links, int n_links, const egn_opts* opts, egn_batch** out) {
+  if (!out) return fail(EGN_E_INVALID_ARG, "out is null");
+  *out = nullptr;
+  egn_batch* b = new (std::nothrow) egn_batch();
+  if (!b) return fail(EGN_E_NOMEM, "out of host memory");
+  egn_status s = create(links, n_links, opts, true, b);
+  if (s != EGN_OK) {
+    delete b;
+    return s;
+  }
+  *out = b;
+  return EGN_OK;
+}
+
+egn_status egn_batch_launch(egn_batch* b, void* stream) {
+  if (!b || !b->exec) return fail(EGN_E_INVALID_ARG, "batch is null");
+  DeviceGuard g(b->device);
+  EGN_CUDA(cudaGraphLaunch(b->exec, (cudaStream_t)stream));
+  return EGN_OK;
+}
+
+egn_status egn_batch_outputs(const egn_batch* b, const double** eta_dev, const double** pnli_dev,
+                             const long long** offsets) {
+  if (!b) return fail(EGN_E_INVALID_ARG, "batch is null");
+  if (eta_dev) *eta_dev = b->eta();
+  if (pnli_dev) *pnli_dev = b->pnli();
+  if (offsets) *offsets = b->off.data();
+  return EGN_OK;
+}
+
+egn_status egn_batch_read(egn_batch* b, void* stream, double* eta, double* pnli) {
+  if (!b) return fail(EGN_E_INVALID_ARG, "batch is null");
+  DeviceGuard g(b->device);
+  egn_status s = stage_and_check(b, (cudaStream_t)stream);
+  if (s != EGN_OK) return s;
+  const long long n = b->total();
+  if (eta) std::memcpy(eta, b->h_stage, n * sizeof(double));
+  if (pnli) std::memcpy(pnli, b->h_stage + n, n * sizeof(double));
+  return EGN_OK;
+}
+
+void egn_batch_destroy(egn_batch* b) {
+  if (!b) return;
+  DeviceGuard g(b->device);
+  cudaStreamSynchronize(b->cap);
+  delete b;
+}
+
+egn_status egn_nli_eta_batch(egn_link* const* links, int n, const egn_opts* opts, double* const* eta,
+                             double* const* pnli) {
+  egn_batch* b = new (std::nothrow) egn_batch();
+  if (!b) return fail(EGN_E_NOMEM, "out of host memory");
+  egn_status s = create(links, n, opts, false, b);  // one plain run, no graph
+  if (s != EGN_OK) {
+    delete b;
+    return s;
+  }
+  const long long tot = b->total();
+  for (int i = 0; i < n; ++i) {
+    const long long o = b->off[i], m = b->off[i + 1] - o;
+    if (eta && eta[i]) std::memcpy(eta[i], b->h_stage + o, m * sizeof(double));
+    if (pnli && pnli[i]) std::memcpy(pnli[i], b->h_stage + tot + o, m * sizeof(double));
+  }
+  egn_batch_destroy(b);
+  return EGN_OK;
+}
+
+}  // extern "C"

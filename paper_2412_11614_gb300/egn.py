@@ -38,6 +38,10 @@ class egn_span(C.Structure):
                 ("length_m", C.c_double)]
 
 
+class egn_tune_result(C.Structure):
+    _fields_ = [("dz_km", C.c_double), ("points_per_thread", C.c_int), ("max_err_db", C.c_double), ("ms", C.c_double)]
+
+
 class egn_opts(C.Structure):
     _fields_ = [("gl_order", C.c_int), ("dz_km", C.c_double), ("mu_form", C.c_int), ("precision", C.c_int),
                 ("terms", C.c_int), ("timeout_ms", C.c_int), ("stream", C.c_void_p)]
@@ -78,11 +82,24 @@ def lib():
         L.egn_set_profiling.argtypes = [C.c_void_p, C.c_int]
         L.egn_set_tuning.argtypes = [C.c_void_p, C.c_int, C.c_int]
         L.egn_last_timings.argtypes = [C.c_void_p, _dp, C.c_int, C.POINTER(C.c_int)]
+        L.egn_batch_create.argtypes = [C.POINTER(C.c_void_p), C.c_int, C.POINTER(egn_opts), C.POINTER(C.c_void_p)]
+        L.egn_batch_launch.argtypes = [C.c_void_p, C.c_void_p]
+        L.egn_batch_outputs.argtypes = [C.c_void_p, C.POINTER(C.c_void_p), C.POINTER(C.c_void_p),
+                                        C.POINTER(C.POINTER(C.c_longlong))]
+        L.egn_batch_read.argtypes = [C.c_void_p, C.c_void_p, _dp, _dp]
+        L.egn_batch_destroy.argtypes = [C.c_void_p]
+        L.egn_batch_destroy.restype = None
+        L.egn_nli_eta_batch.argtypes = [C.POINTER(C.c_void_p), C.c_int, C.POINTER(egn_opts), C.POINTER(_dp),
+                                        C.POINTER(_dp)]
+        L.egn_autotune.argtypes = [C.c_void_p, C.POINTER(egn_opts), C.c_double, _dp, C.c_int, C.c_double,
+                                   C.POINTER(egn_tune_result)]
         L.egn_last_error.restype = C.c_char_p
         L.egn_version.restype = C.c_char_p
         for fn in ("egn_link_create", "egn_set_wdm", "egn_workspace_size", "egn_island_count", "egn_nli_eta",
                    "egn_nli_eta_device", "egn_island_terms", "egn_plan_islands", "egn_format_moments",
-                   "egn_gauss_legendre", "egn_set_profiling", "egn_last_timings", "egn_nli_eta_static", "egn_set_tuning"):
+                   "egn_gauss_legendre", "egn_set_profiling", "egn_last_timings", "egn_nli_eta_static", "egn_set_tuning",
+                   "egn_batch_create", "egn_batch_launch", "egn_batch_outputs", "egn_batch_read", "egn_nli_eta_batch",
+                   "egn_autotune"):
             getattr(L, fn).restype = C.c_int
         _lib = L
     return _lib
@@ -191,6 +208,15 @@ class Link:
                                       int(bool(all_terms)), out.ctypes.data_as(_dp)))
         return out
 
+    def autotune(self, opts: egn_opts, target_db: float, dz_candidates, dz_ref_km: float) -> dict:
+        """egn_autotune: coarsest segment bound within target_db of the reference,
+        and the faster FP32C launch shape (set on the link)."""
+        cand = _arr(dz_candidates)
+        r = egn_tune_result()
+        _check(lib().egn_autotune(self.h, C.byref(opts), float(target_db), cand.ctypes.data_as(_dp), len(cand),
+                                  float(dz_ref_km), C.byref(r)))
+        return {"dz_km": r.dz_km, "points_per_thread": r.points_per_thread, "max_err_db": r.max_err_db, "ms": r.ms}
+
     def set_tuning(self, param: int, value: int):
         _check(lib().egn_set_tuning(self.h, int(param), int(value)))
 
@@ -210,6 +236,64 @@ class Link:
         cnt = C.c_longlong()
         _check(lib().egn_plan_islands(self.h, tot, out.ctypes.data_as(C.POINTER(C.c_int)), C.byref(cnt)))
         return out[: cnt.value]
+
+
+def _handles(links) -> "C.Array":
+    arr = (C.c_void_p * len(links))()
+    for i, ln in enumerate(links):
+        arr[i] = ln.h
+    return arr
+
+
+class Batch:
+    """An egn_batch handle: links snapshotted for repeated evaluation by one CUDA
+    graph (egn_batch_create / egn_batch_launch / egn_batch_read)."""
+
+    def __init__(self, links: Sequence[Link], opts: egn_opts):
+        h = C.c_void_p()
+        _check(lib().egn_batch_create(_handles(links), len(links), C.byref(opts), C.byref(h)))
+        self.h = h
+        off = C.POINTER(C.c_longlong)()
+        _check(lib().egn_batch_outputs(self.h, None, None, C.byref(off)))
+        self.offsets = np.array(off[: len(links) + 1], dtype=np.int64)
+
+    def launch(self, stream: Optional[int] = None):
+        _check(lib().egn_batch_launch(self.h, C.c_void_p(stream) if stream else None))
+
+    def outputs(self):
+        """Device addresses of eta and P_NLI of all channels (link after link)."""
+        e, p = C.c_void_p(), C.c_void_p()
+        _check(lib().egn_batch_outputs(self.h, C.byref(e), C.byref(p), None))
+        return e.value, p.value
+
+    def read(self, stream: Optional[int] = None):
+        """Wait for the work on `stream`, then [(eta, P_NLI) per link] on the host."""
+        n = int(self.offsets[-1])
+        eta, pn = np.zeros(n), np.zeros(n)
+        _check(lib().egn_batch_read(self.h, C.c_void_p(stream) if stream else None, eta.ctypes.data_as(_dp),
+                                    pn.ctypes.data_as(_dp)))
+        o = self.offsets
+        return [(eta[o[i]:o[i + 1]], pn[o[i]:o[i + 1]]) for i in range(len(o) - 1)]
+
+    def close(self):
+        if self.h:
+            lib().egn_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def nli_eta_batch(links: Sequence[Link], opts: egn_opts):
+    """One evaluation of several links (egn_nli_eta_batch): [(eta, P_NLI) per link]."""
+    outs = [(np.zeros(ln.n_ch), np.zeros(ln.n_ch)) for ln in links]
+    ep = (_dp * len(links))(*[o[0].ctypes.data_as(_dp) for o in outs])
+    pp = (_dp * len(links))(*[o[1].ctypes.data_as(_dp) for o in outs])
+    _check(lib().egn_nli_eta_batch(_handles(links), len(links), C.byref(opts), ep, pp))
+    return outs
 
 
 def link_from_workload(wl, phi=None, psi=None) -> Link:

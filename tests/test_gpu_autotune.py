@@ -1,0 +1,65 @@
+"""egn_autotune: the chosen segment bound is the coarsest candidate whose worst
+channel stays within the target of the fine-Delta-z reference (checked by
+evaluating every candidate directly), and the chosen FP32C launch shape is set
+on the link."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def egn():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA device required for -m gpu tests")
+    from paper_2412_11614_gb300 import _build
+    _build.build()
+    from paper_2412_11614_gb300 import egn as E
+    E.lib()
+    return E
+
+
+CANDS = [1.0, 2.0, 5.0, 10.0, 25.0, 50.0, 100.0]
+
+
+def _max_db(a, b):
+    return float(np.max(np.abs(10 * np.log10(a / b))))
+
+
+@pytest.mark.parametrize("prec,target", [("fp64", 0.01), ("fp64", 0.001), ("fp32c", 0.01)])
+def test_autotune_coarsest_within_target(egn, workloads, prec, target):
+    # strong ISRS (Table I, Cr = 1.12) so that Delta z matters
+    wl = workloads.table1(n_spans=2, cr=1.12, fmt="QPSK", gl_order=12, n_ch=9)
+    ln = egn.link_from_workload(wl)
+    p = egn.EGN_PREC_FP64 if prec == "fp64" else egn.EGN_PREC_FP32C
+    opts = lambda dz: egn.make_opts(gl_order=12, dz_km=dz, precision=p)  # noqa: E731
+    r = ln.autotune(opts(1.0), target, CANDS, 0.25)
+    # autotune searched with the default launch shape; check with the same one
+    # (the shape changes FP32C results at the rounding level)
+    kp = r["points_per_thread"]
+    ln.set_tuning(egn.EGN_TUNE_FP32C_POINTS_PER_THREAD, 4)
+    ref, _ = ln.nli_eta(opts(0.25))
+    errs = {c: _max_db(ln.nli_eta(opts(c))[0], ref) for c in CANDS}
+    ok = [c for c in CANDS if errs[c] <= target]
+    want = max(ok) if ok else 0.25
+    assert r["dz_km"] == want, (r, errs)
+    assert abs(r["max_err_db"] - (errs[want] if ok else 0.0)) <= 1e-12
+    assert r["ms"] > 0
+    if prec == "fp32c":
+        assert kp in (4, 8)
+    # coarse segments must actually cost accuracy here, or the test proves nothing
+    assert errs[100.0] > target
+
+
+def test_autotune_rejects_bad_arguments(egn, workloads):
+    ln = egn.link_from_workload(workloads.config_small(n_ch=2, gl_order=8))
+    o = egn.make_opts(gl_order=8)
+    for args in ((0.0, CANDS, 0.25), (0.01, [], 0.25), (0.01, [1.0, -2.0], 0.25), (0.01, CANDS, 0.0)):
+        with pytest.raises(egn.EgnError) as ei:
+            ln.autotune(o, *args)
+        assert ei.value.status == egn.EGN_E_INVALID_ARG
+    with pytest.raises(egn.EgnError) as ei:
+        ln.autotune(egn.make_opts(gl_order=8, precision=egn.EGN_PREC_FP64, mu_form=egn.EGN_MU_MACLAURIN),
+                    0.01, CANDS, 0.25)
+    assert ei.value.status == egn.EGN_E_INVALID_ARG
