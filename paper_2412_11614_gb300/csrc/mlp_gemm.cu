@@ -1,0 +1,302 @@
+// mlp_gemm.cu -- BF16 GEMM on the 5th-generation tensor cores (tcgen05) for the
+// MLP surrogate: D = A B^T, A [m][k] and B [n][k] row-major (k contiguous),
+// FP32 accumulation in tensor memory (TMEM), fused epilogues.
+//
+// One CTA of 128 threads computes a 128 x 256 tile of D:
+//   warp 0, one lane : TMA producer, 64-wide k blocks of A (128 x 64) and B
+//                      (256 x 64) into a 4-stage ring, 128-byte swizzle;
+//   warp 1, one lane : MMA issuer, 4 x tcgen05.mma (M 128, N 256, K 16) per k
+//                      block into one TMEM accumulator of 256 columns; each
+//                      stage is released by tcgen05.commit to its "empty"
+//                      barrier, the last commit marks the accumulator ready;
+//   warps 0-3        : epilogue, warp w reads TMEM lanes 32w .. 32w + 31 (rows)
+//                      with tcgen05.ld, 32 columns at a time.
+// blockIdx.z splits the k range (partial sums written to slab z, summed by
+// egn_mlp_reduce_splits in a fixed order).  Every mbarrier wait is bounded
+// (kWaitNs of wall time); a wait that runs out sets the error word, lets the
+// producer drain its own copies in flight, frees TMEM and returns.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cudaTypedefs.h>
+
+#include "../../include/egn_mlp.h"
+#include "link.h"
+
+using namespace egn_host;
+
+namespace {
+
+constexpr int BM = 128, BN = 256, BK = 64, STAGES = 4;
+constexpr int kStageA = BM * BK * 2;  // 16 KB
+constexpr int kStageB = BN * BK * 2;  // 32 KB
+constexpr int kSmem = STAGES * (kStageA + kStageB) + 1024 /* alignment */ + 256 /* barriers */;
+constexpr unsigned long long kWaitNs = 2000000000ull;  // 2 s
+
+// Instruction descriptor of tcgen05.mma kind::f16: D FP32 (bits 4-5 = 1), A and B
+// BF16 (bits 7-9 = 1, 10-12 = 1), both K-major (bits 15, 16 = 0), N >> 3 at
+// bits 17-22, M >> 4 at bits 24-28.
+constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ unsigned long long now_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* b, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(b)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* b, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(b)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* b, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(smem_u32(b)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait for the phase of the given parity to complete.
+__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity) {
+  if (mbar_try_wait(b, parity)) return true;
+  const unsigned long long t0 = now_ns();
+  for (;;) {
+    for (int i = 0; i < 256; ++i)
+      if (mbar_try_wait(b, parity)) return true;
+    if (now_ns() - t0 > kWaitNs) return false;
+  }
+}
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int c0, int c1) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+          smem_u32(dst)),
+      "l"((unsigned long long)map), "r"(c0), "r"(c1), "r"(smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// Shared-memory matrix descriptor, K-major operand with 128-byte swizzle: rows of
+// 64 BF16 (128 bytes), 8-row groups 1024 bytes apart (stride byte offset), the
+// leading byte offset unused (1), descriptor version 1 (bits 46-47), layout
+// SWIZZLE_128B (2 at bits 61-63).  The tile base is 1024-byte aligned.
+__device__ __forceinline__ uint64_t sdesc_sw128(const void* p) {
+  const uint64_t a = smem_u32(p);
+  return ((a & 0x3FFFFull) >> 4) | (1ull << 16) | ((uint64_t)(1024 >> 4) << 32) | (1ull << 46) | (2ull << 61);
+}
+
+__device__ __forceinline__ void umma_bf16(uint32_t taddr, uint64_t ad, uint64_t bd, uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(
+          taddr),
+      "l"(ad), "l"(bd), "r"(kIdesc), "r"(acc)
+      : "memory");
+}
+__device__ __forceinline__ void umma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+      "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+        "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
+}
+
+template <int EPI>
+__global__ void __launch_bounds__(128, 1)
+    gemm_bf16_kernel(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtensorMap tb, int M, int N,
+                     int kb_per_split, int kb_total, const float* __restrict__ bias,
+                     const __nv_bfloat16* __restrict__ aux, void* __restrict__ out, int* __restrict__ err) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint8_t* sA = smem;
+  uint8_t* sB = smem + STAGES * kStageA;
+  uint64_t* full = (uint64_t*)(sB + STAGES * kStageB);
+  uint64_t* empty = full + STAGES;
+  uint64_t* accum = empty + STAGES;
+  uint32_t* tslot = (uint32_t*)(accum + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
+  const int kb0 = blockIdx.z * kb_per_split;
+  const int nk = min(kb_per_split, kb_total - kb0);
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    mbar_init(accum, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncwarp();  // the .sync.aligned tcgen05 instructions need the whole warp converged
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)), "r"(BN));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t taddr = *tslot;
+
+  if (warp == 0 && lane == 0) {
+    // producer
+    int issued = 0;
+    bool ok = true;
+    for (int kb = 0; kb < nk; ++kb) {
+      const int s = kb % STAGES;
+      const uint32_t ph = (kb / STAGES) & 1;
+      if (kb >= STAGES && !mbar_wait(&empty[s], ph ^ 1)) { ok = false; break; }
+      mbar_expect_tx(&full[s], kStageA + kStageB);
+      tma_load_2d(sA + s * kStageA, &ta, &full[s], (kb0 + kb) * BK, m0);
+      tma_load_2d(sB + s * kStageB, &tb, &full[s], (kb0 + kb) * BK, n0);
+      ++issued;
+    }
+    if (!ok) atomicExch(err, 1);
+    // drain: every copy this thread issued has landed before the CTA may exit
+    for (int kb = max(0, issued - STAGES); kb < issued; ++kb) mbar_wait(&full[kb % STAGES], (kb / STAGES) & 1);
+  } else if (warp == 1 && lane == 0) {
+    // MMA issuer
+    bool ok = true;
+    for (int kb = 0; kb < nk; ++kb) {
+      const int s = kb % STAGES;
+      const uint32_t ph = (kb / STAGES) & 1;
+      if (!mbar_wait(&full[s], ph)) { ok = false; break; }
+      fence_after();
+      const uint64_t ad = sdesc_sw128(sA + s * kStageA), bd = sdesc_sw128(sB + s * kStageB);
+#pragma unroll
+      for (int k = 0; k < BK / 16; ++k) umma_bf16(taddr, ad + 2 * k, bd + 2 * k, (kb | k) != 0);  // +32 bytes per k step
+      umma_commit(&empty[s]);
+    }
+    if (!ok) atomicExch(err, 2);
+    umma_commit(accum);  // arrives when every MMA issued above has completed
+  }
+  __syncwarp();
+
+  // epilogue
+  const bool ready = mbar_wait(accum, 0);
+  if (!ready) atomicExch(err, 3);
+  __syncwarp();  // lanes leave the wait loop independently; tcgen05.ld is .sync.aligned
+  fence_after();
+  const int row = m0 + warp * 32 + lane;
+  const bool store = ready && nk > 0 && row < M;
+  for (int c = 0; c < BN; c += 32) {
+    float v[32];
+    tmem_ld32(taddr + ((uint32_t)(warp * 32) << 16) + (uint32_t)c, v);
+    const int n = n0 + c;
+    if (!store || n >= N) continue;
+    if (EPI == EGN_MLP_EPI_F32) {
+      float* o = (float*)out + (size_t)blockIdx.z * (size_t)M * N + (size_t)row * N + n;
+#pragma unroll
+      for (int j = 0; j < 32; j += 4) *reinterpret_cast<float4*>(o + j) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
+    } else {
+      __nv_bfloat16* o = (__nv_bfloat16*)out + (size_t)row * N + n;
+      __align__(16) __nv_bfloat16 h[32];
+      if (EPI == EGN_MLP_EPI_BIAS_RELU) {
+#pragma unroll
+        for (int j = 0; j < 32; ++j) h[j] = __float2bfloat16_rn(fmaxf(v[j] + bias[n + j], 0.0f));
+      } else if (EPI == EGN_MLP_EPI_BIAS) {
+#pragma unroll
+        for (int j = 0; j < 32; ++j) h[j] = __float2bfloat16_rn(v[j] + bias[n + j]);
+      } else {  // EGN_MLP_EPI_RELU_GRAD: the gradient passes where the layer's output was positive
+        const __nv_bfloat16* a = aux + (size_t)row * N + n;
+#pragma unroll
+        for (int j = 0; j < 32; ++j) h[j] = __float2bfloat16_rn(__bfloat162float(a[j]) > 0.0f ? v[j] : 0.0f);
+      }
+#pragma unroll
+      for (int j = 0; j < 32; j += 8) *reinterpret_cast<uint4*>(o + j) = *reinterpret_cast<const uint4*>(h + j);
+    }
+  }
+  fence_before();
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(BN));
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      p = nullptr;
+    return (PFN_cuTensorMapEncodeTiled_v12000)p;
+  }();
+  return fn;
+}
+
+// Tensor map of a row-major [rows][cols] BF16 matrix, boxes of box_rows x 64
+// with 128-byte swizzle (the shared-memory layout the MMA descriptors expect).
+egn_status make_map(CUtensorMap* m, const void* base, uint64_t rows, uint64_t cols, uint32_t box_rows) {
+  auto fn = encode_fn();
+  if (!fn) return fail(EGN_E_CUDA, "cuTensorMapEncodeTiled is not available");
+  const cuuint64_t dims[2] = {cols, rows};
+  const cuuint64_t strides[1] = {cols * 2};
+  const cuuint32_t box[2] = {(cuuint32_t)BK, box_rows};
+  const cuuint32_t es[2] = {1, 1};
+  CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, es,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return fail(EGN_E_CUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+  return EGN_OK;
+}
+
+template <int EPI>
+egn_status launch(const CUtensorMap& ta, const CUtensorMap& tb, int m, int n, int kb_per, int kb, int splits,
+                  const float* bias, const void* aux, void* out, int* err, cudaStream_t st) {
+  static bool attr = false;
+  if (!attr) {
+    EGN_CUDA(cudaFuncSetAttribute(gemm_bf16_kernel<EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem));
+    attr = true;
+  }
+  dim3 grid((m + BM - 1) / BM, (n + BN - 1) / BN, splits);
+  gemm_bf16_kernel<EPI><<<grid, 128, kSmem, st>>>(ta, tb, m, n, kb_per, kb, bias, (const __nv_bfloat16*)aux, out, err);
+  EGN_CUDA(cudaGetLastError());
+  return EGN_OK;
+}
+
+}  // namespace
+
+extern "C" egn_status egn_mlp_gemm(int m, int n, int k, int splits, const void* a, const void* b, int epilogue,
+                                   const float* bias, const void* aux, void* out, int* err_dev, void* stream) {
+  if (m < 1 || n < 1 || k < 1) return fail(EGN_E_INVALID_ARG, "m, n, k must be positive");
+  if (k % BK) return fail(EGN_E_INVALID_ARG, "k = %d is not a multiple of %d", k, BK);
+  if (n % 32) return fail(EGN_E_INVALID_ARG, "n = %d is not a multiple of 32", n);
+  if (!a || !b || !out || !err_dev) return fail(EGN_E_INVALID_ARG, "null pointer");
+  if (((uintptr_t)a | (uintptr_t)b | (uintptr_t)out) & 15) return fail(EGN_E_INVALID_ARG, "A, B, out must be 16-byte aligned");
+  const int kb = k / BK;
+  if (splits < 1 || splits > kb) return fail(EGN_E_INVALID_ARG, "splits must be in [1, k/64]");
+  if (splits > 1 && epilogue != EGN_MLP_EPI_F32) return fail(EGN_E_INVALID_ARG, "split k needs the FP32 epilogue");
+  if ((epilogue == EGN_MLP_EPI_BIAS_RELU || epilogue == EGN_MLP_EPI_BIAS) && !bias)
+    return fail(EGN_E_INVALID_ARG, "bias required");
+  if (epilogue == EGN_MLP_EPI_RELU_GRAD && !aux) return fail(EGN_E_INVALID_ARG, "aux required");
+  const int kb_per = (kb + splits - 1) / splits;
+  if ((long long)(splits - 1) * kb_per >= kb) return fail(EGN_E_INVALID_ARG, "splits leaves an empty k range");
+  CUtensorMap ta, tb;
+  egn_status s = make_map(&ta, a, (uint64_t)m, (uint64_t)k, BM);
+  if (s == EGN_OK) s = make_map(&tb, b, (uint64_t)n, (uint64_t)k, BN);
+  if (s != EGN_OK) return s;
+  cudaStream_t st = (cudaStream_t)stream;
+  switch (epilogue) {
+    case EGN_MLP_EPI_BIAS_RELU: return launch<EGN_MLP_EPI_BIAS_RELU>(ta, tb, m, n, kb_per, kb, splits, bias, aux, out, err_dev, st);
+    case EGN_MLP_EPI_BIAS: return launch<EGN_MLP_EPI_BIAS>(ta, tb, m, n, kb_per, kb, splits, bias, aux, out, err_dev, st);
+    case EGN_MLP_EPI_F32: return launch<EGN_MLP_EPI_F32>(ta, tb, m, n, kb_per, kb, splits, bias, aux, out, err_dev, st);
+    case EGN_MLP_EPI_RELU_GRAD: return launch<EGN_MLP_EPI_RELU_GRAD>(ta, tb, m, n, kb_per, kb, splits, bias, aux, out, err_dev, st);
+    default: return fail(EGN_E_INVALID_ARG, "unknown epilogue %d", epilogue);
+  }
+}

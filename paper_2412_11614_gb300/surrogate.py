@@ -1,0 +1,238 @@
+"""MLP surrogate of the ISRS EGN integrator: per-channel eta [dB] of a link.
+
+The integrator (egn_nli_eta) supplies the labels.  The network maps per-channel
+features to 10 log10(eta): 64 inputs (18 features, zero-padded to the GEMM's
+64-wide k blocks) -> 256 -> 256 -> 256 (ReLU) -> 1 (linear).  Weights and
+activations are BF16, products accumulate in FP32 on the tensor cores
+(egn_mlp_gemm, tcgen05); master weights and Adam state are FP32.  Every step of
+training and inference runs in the library's kernels; torch only provides
+device memory and streams.
+
+Predictions are only made inside the training envelope (120-channel C+L grid,
+identical SSMF spans, N_s, L, Cr and powers within the sampled ranges); other
+links are evaluated by the integrator instead.
+"""
+from __future__ import annotations
+
+import math
+from typing import List, Sequence
+
+import numpy as np
+
+from . import egn as E
+from . import mlp as K
+
+N_FEAT = 18
+F_PAD = 64
+HIDDEN = 256
+LAYERS = 3
+C_M_PER_S = 299792458.0
+
+
+def _moments(fmts):
+    m = [E.egn_format_moments(f) for f in fmts]
+    return np.array([a for a, _ in m]), np.array([b for _, b in m])
+
+
+def features(wl) -> np.ndarray:
+    """Per-channel feature rows [n_ch][N_FEAT] of a workloads.Workload."""
+    f = np.asarray(wl.centre_hz, dtype=np.float64)
+    n = len(f)
+    fc = 0.5 * (f.min() + f.max())
+    x = (f - fc) / 4.5e12
+    p_dbm = 10.0 * np.log10(np.asarray(wl.launch_power_w) / 1e-3)
+    pm = p_dbm.mean()
+    slope = np.polyfit(x, p_dbm, 1)[0] if n > 1 else 0.0
+    k = np.ones(9) / 9.0
+    local = np.convolve(np.pad(p_dbm, 4, mode="edge"), k, mode="valid")
+    phi, psi = _moments(wl.formats)
+    local_phi = np.convolve(np.pad(phi, 4, mode="edge"), k, mode="valid")
+    s = wl.spans[0]
+    ns = len(wl.spans)
+    L = s.length_m * 1e-3
+    cr = s.cr_per_w_km_thz
+    alpha = s.alpha_db_km * math.log(10.0) / 10.0
+    leff = (1.0 - math.exp(-alpha * L)) / alpha
+    ptot = float(np.sum(wl.launch_power_w))
+    btot = (f.max() - f.min()) * 1e-12 * n / max(n - 1, 1)
+    drho = cr * ptot * leff * btot  # ISRS tilt scale of Eq. 12 (nepers)
+    cols = [x, x ** 2, x ** 3, (p_dbm - 1.0) / 3.0, np.full(n, (pm - 1.0) / 3.0), np.full(n, slope / 3.0),
+            (local - pm) / 2.0, np.full(n, (cr - 0.028) / 0.014), np.full(n, (L - 85.0) / 35.0),
+            np.full(n, (ns - 15.5) / 15.0), np.full(n, math.log(ns) / math.log(30.0)), phi, psi / 10.0,
+            np.full(n, phi.mean()), local_phi, np.full(n, 1.0 / ns), np.full(n, drho), np.ones(n)]
+    return np.stack(cols, axis=1).astype(np.float64)
+
+
+def in_envelope(wl) -> bool:
+    """True if the link is of the kind the surrogate was trained on."""
+    if len(wl.centre_hz) != 120 or any(r != 64e9 for r in wl.symbol_rate_baud):
+        return False
+    s0 = wl.spans[0]
+    if any(s != s0 for s in wl.spans):
+        return False
+    ns, L, cr = len(wl.spans), s0.length_m * 1e-3, s0.cr_per_w_km_thz
+    p = 10.0 * np.log10(np.asarray(wl.launch_power_w) / 1e-3)
+    return (1 <= ns <= 30 and 50.0 <= L <= 120.0 and 0.014 <= cr <= 0.042 and abs(s0.D_ps_nm_km - 17.0) < 1e-9
+            and -6.0 <= p.min() and p.max() <= 8.0)
+
+
+class Surrogate:
+    """The MLP with its device state (torch tensors as device memory)."""
+
+    def __init__(self, seed: int = 0, device: str = "cuda"):
+        import torch
+        self.torch = torch
+        self.dev = device
+        rng = np.random.default_rng(seed)
+        dims = [F_PAD] + [HIDDEN] * LAYERS
+        self.W, self.b, self.Wb, self.WbT = [], [], [], []
+        for i in range(LAYERS):
+            fan_in = N_FEAT if i == 0 else dims[i]
+            w = np.zeros((dims[i + 1], dims[i]), dtype=np.float32)
+            w[:, :fan_in] = rng.normal(0.0, math.sqrt(2.0 / fan_in), size=(dims[i + 1], fan_in))
+            self.W.append(torch.tensor(w, device=device))
+            self.b.append(torch.zeros(dims[i + 1], dtype=torch.float32, device=device))
+            self.Wb.append(torch.empty(w.shape, dtype=torch.bfloat16, device=device))
+            self.WbT.append(torch.empty((w.shape[1], w.shape[0]), dtype=torch.bfloat16, device=device))
+        self.w_out = torch.tensor(rng.normal(0.0, math.sqrt(1.0 / HIDDEN), size=HIDDEN).astype(np.float32),
+                                  device=device)
+        self.b_out = torch.zeros(1, dtype=torch.float32, device=device)
+        self.params = [p for pair in zip(self.W, self.b) for p in pair] + [self.w_out, self.b_out]
+        self.m = [torch.zeros_like(p) for p in self.params]
+        self.v = [torch.zeros_like(p) for p in self.params]
+        self.step_count = 0
+        self.err = torch.zeros(1, dtype=torch.int32, device=device)
+        self.x_mean = np.zeros(N_FEAT)
+        self.x_std = np.ones(N_FEAT)
+        self.y_mean, self.y_std = 0.0, 1.0
+        self._refresh_bf16(None)
+
+    # ------------------------------------------------------------------ helpers
+    def _refresh_bf16(self, stream):
+        for i in range(LAYERS):
+            K.cast(self.W[i], self.Wb[i], stream=stream)
+            K.transpose(self.Wb[i], self.Wb[i].shape[0], self.WbT[i], stream=stream)
+
+    def _buffers(self, rows_pad):
+        torch = self.torch
+        if getattr(self, "_rows", None) == rows_pad:
+            return
+        self._rows = rows_pad
+        bf = torch.bfloat16
+        self.h = [torch.zeros((rows_pad, F_PAD), dtype=bf, device=self.dev)] + \
+                 [torch.empty((rows_pad, HIDDEN), dtype=bf, device=self.dev) for _ in range(LAYERS)]
+        self.y = torch.empty(rows_pad, dtype=torch.float32, device=self.dev)
+        self.g = torch.empty(rows_pad, dtype=torch.float32, device=self.dev)
+        self.loss = torch.empty(1, dtype=torch.float32, device=self.dev)
+        self.dh = [torch.empty((rows_pad, HIDDEN), dtype=bf, device=self.dev) for _ in range(2)]
+        self.dhT = torch.empty((HIDDEN, rows_pad), dtype=bf, device=self.dev)
+        self.hT = torch.empty((HIDDEN, rows_pad), dtype=bf, device=self.dev)
+        kb = rows_pad // 64                   # 64-row k blocks of the weight-gradient GEMMs
+        per = -(-kb // 16)                    # at most 16 k splits, none empty
+        self.splits = -(-kb // per)
+        self.part = torch.empty(self.splits * HIDDEN * HIDDEN, dtype=torch.float32, device=self.dev)
+        self.grads = [torch.empty_like(p) for p in self.params]
+        self.xf = torch.empty((rows_pad, F_PAD), dtype=torch.float32, device=self.dev)
+
+    def _load_inputs(self, x: np.ndarray, stream):
+        """Normalised features (host FP32) -> BF16 input rows on the device."""
+        torch = self.torch
+        rows = x.shape[0]
+        rows_pad = ((rows + 63) // 64) * 64
+        self._buffers(rows_pad)
+        xp = np.zeros((rows_pad, F_PAD), dtype=np.float32)
+        xp[:rows, :N_FEAT] = (x - self.x_mean) / self.x_std
+        self.xf.copy_(torch.from_numpy(xp), non_blocking=False)
+        K.cast(self.xf, self.h[0], stream=stream)
+        return rows, rows_pad
+
+    def _forward(self, stream):
+        for i in range(LAYERS):
+            K.gemm(self.h[i], self.Wb[i], self.h[i + 1], K.EPI_BIAS_RELU, bias=self.b[i], err=self.err, stream=stream)
+
+    # ------------------------------------------------------------------ API
+    def predict_rows(self, x: np.ndarray, stream=None) -> np.ndarray:
+        """Predicted 10 log10(eta) for feature rows x [rows][N_FEAT]."""
+        rows, _ = self._load_inputs(x, stream)
+        self._forward(stream)
+        K.head(self.h[LAYERS], self.w_out, self.b_out, self.y, stream=stream)
+        self._check()
+        return self.y[:rows].cpu().numpy() * self.y_std + self.y_mean
+
+    def train_step(self, x: np.ndarray, t: np.ndarray, lr: float, stream=None) -> float:
+        """One Adam step on feature rows x and targets t (10 log10 eta)."""
+        torch = self.torch
+        rows, rows_pad = self._load_inputs(x, stream)
+        tn = np.zeros(rows_pad, dtype=np.float32)
+        tn[:rows] = (t - self.y_mean) / self.y_std
+        mask = np.zeros(rows_pad, dtype=np.float32)
+        mask[:rows] = 1.0
+        tgt = torch.from_numpy(tn).to(self.dev)
+        msk = torch.from_numpy(mask).to(self.dev)
+        self._forward(stream)
+        gw_out, gb_out = self.grads[-2], self.grads[-1]
+        K.head(self.h[LAYERS], self.w_out, self.b_out, self.y, target=tgt, mask=msk, loss=self.loss, g=self.g,
+               dh=self.dh[0], dw=gw_out, db=gb_out, stream=stream)
+        cur = 0
+        for i in reversed(range(LAYERS)):
+            dh = self.dh[cur]
+            fan = self.h[i].shape[1]
+            # weight gradient dW_i = dh^T h_i (k = rows, split over CTA layers), bias gradient
+            K.transpose(dh, rows_pad, self.dhT, stream=stream)
+            hT = self.hT[:fan]
+            K.transpose(self.h[i], rows_pad, hT, stream=stream)
+            part = self.part[: self.splits * HIDDEN * fan]  # dense [splits][HIDDEN][fan]
+            K.gemm(self.dhT, hT, part, K.EPI_F32, splits=self.splits, err=self.err, stream=stream)
+            K.reduce_splits(part, self.splits, self.grads[2 * i], stream=stream)
+            K.colsum(dh, self.grads[2 * i + 1], stream=stream)
+            if i > 0:  # gradient of the layer below, through its ReLU
+                K.gemm(dh, self.WbT[i], self.dh[1 - cur], K.EPI_RELU_GRAD, aux=self.h[i], err=self.err,
+                       stream=stream)
+                cur = 1 - cur
+        self.step_count += 1
+        for p, g, m, v in zip(self.params, self.grads, self.m, self.v):
+            K.adam(p, g, m, v, lr, self.step_count, stream=stream)
+        self._refresh_bf16(stream)
+        self._check()
+        return float(self.loss.item())
+
+    def _check(self):
+        e = int(self.err.item())
+        if e:
+            raise RuntimeError(f"a tensor-core kernel's bounded wait ran out (code {e})")
+
+    def fit_normalisation(self, x: np.ndarray, t: np.ndarray):
+        self.x_mean = x.mean(axis=0)
+        self.x_std = np.where(x.std(axis=0) > 1e-12, x.std(axis=0), 1.0)
+        self.y_mean, self.y_std = float(t.mean()), float(t.std() or 1.0)
+
+
+def labels(workloads: Sequence, opts) -> List[np.ndarray]:
+    """10 log10(eta) of every channel of every link, from the integrator (one
+    batch evaluation)."""
+    links = [E.link_from_workload(w) for w in workloads]
+    out = E.nli_eta_batch(links, opts)
+    for ln in links:
+        ln.close()
+    return [10.0 * np.log10(e) for e, _ in out]
+
+
+def predict(model: Surrogate, workloads: Sequence, opts):
+    """10 log10(eta) per link: the MLP inside the training envelope, the
+    integrator outside it.  Returns (list of arrays, list of bools: used the MLP)."""
+    inside = [in_envelope(w) for w in workloads]
+    res: List = [None] * len(workloads)
+    idx = [i for i, ok in enumerate(inside) if ok]
+    if idx:
+        x = np.concatenate([features(workloads[i]) for i in idx])
+        y = model.predict_rows(x)
+        o = 0
+        for i in idx:
+            n = len(workloads[i].centre_hz)
+            res[i] = y[o:o + n]
+            o += n
+    rest = [i for i, ok in enumerate(inside) if not ok]
+    if rest:
+        for i, lab in zip(rest, labels([workloads[i] for i in rest], opts)):
+            res[i] = lab
+    return res, inside

@@ -13,6 +13,8 @@ Workloads:
   * ``table1``        101 ch x 10 GBd at 10.1 GHz, N x 100 km (Table I, Sec. III-A)
   * ``table2``        101 ch x 100 GBd at 101 GHz, 1 x 100 km (Table II, App. C)
   * ``random_link``   seeded heterogeneous links for the batched path
+  * ``surrogate_link`` seeded 120-channel C+L links with identical spans, the
+                      training and held-out sets of the MLP surrogate
 """
 from __future__ import annotations
 
@@ -221,4 +223,40 @@ def random_link(seed: int, gl_order: int = 16) -> Workload:
         rolloff=0.01,
         gl_order=gl_order,
         notes={"seed": seed},
+    )
+
+
+def surrogate_link(seed: int, gl_order: int = 32) -> Workload:
+    """Seeded C+L link for the surrogate: the 120-channel, 64 GBd, 75 GHz grid of
+    config_cl; N_s ~ U{1..30} identical SSMF spans of L ~ U[50, 120] km with
+    Cr ~ U[0.014, 0.042] 1/(W km THz); mean launch power U[-2, 4] dBm with a
+    linear tilt U[-3, 3] dB across the band and N(0, 0.5 dB) ripple per
+    channel; formats drawn per channel.  Training seeds 1, 2, ...; held-out
+    seeds from 1,000,001."""
+    rng = SplitMix64(0x5A770000 + seed)
+    n_spans = rng.randint(1, 30)
+    length_km = 50.0 + 70.0 * rng.uniform()
+    cr = 0.014 + 0.028 * rng.uniform()
+    p0 = -2.0 + 6.0 * rng.uniform()
+    tilt = -3.0 + 6.0 * rng.uniform()
+    base = config_cl(gl_order=gl_order, n_spans=1)
+    cen = base.centre_hz
+    f_min, f_max = cen[0], cen[-1]
+    powers = []
+    for f in cen:
+        rel = (f - 0.5 * (f_min + f_max)) / (f_max - f_min)
+        powers.append(dbm_to_w(p0 + tilt * rel + 0.5 * rng.normal()))
+    fmts = [FORMATS[rng.next_u64() % 4] for _ in cen]
+    fibre = dict(SSMF)
+    fibre["cr_per_w_km_thz"] = cr
+    return Workload(
+        name=f"surrogate link {seed}: 120ch C+L, {n_spans}x{length_km:.1f}km, Cr {cr:.4f}, {p0:.2f} dBm, tilt {tilt:.2f} dB",
+        spans=_spans(fibre, length_km, n_spans),
+        centre_hz=list(cen),
+        symbol_rate_baud=[64e9] * len(cen),
+        launch_power_w=powers,
+        formats=fmts,
+        rolloff=0.01,
+        gl_order=gl_order,
+        notes={"seed": seed, "n_spans": n_spans, "length_km": length_km, "cr": cr, "p0_dbm": p0, "tilt_db": tilt},
     )
