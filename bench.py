@@ -323,6 +323,83 @@ def run_batch_compare(args):
     return 0
 
 
+def run_surrogate(args):
+    """MLP surrogate end to end: labels of seeded 120-channel links from the
+    FP32C integrator (batches of links), training on the tensor-core kernels,
+    accuracy on held-out links, and inference throughput against the
+    integrator's.  Prints one JSON line."""
+    import numpy as np
+    import torch
+    from paper_2412_11614_gb300 import _build, egn, surrogate as S, workloads as W
+    _build.build()
+    torch.cuda.set_device(0)
+    opts = egn.make_opts(gl_order=32, precision=egn.EGN_PREC_FP32C)
+    train_w = [W.surrogate_link(i + 1) for i in range(args.sur_train)]
+    test_w = [W.surrogate_link(1000001 + i) for i in range(args.sur_test)]
+    t0 = time.perf_counter()
+    lab = []
+    cached = bool(args.sur_labels and os.path.exists(args.sur_labels))
+    if cached:
+        z = np.load(args.sur_labels)
+        lab = [z["eta_db"][i] for i in range(len(train_w) + len(test_w))]
+    else:
+        for i in range(0, len(train_w) + len(test_w), 64):
+            lab += S.labels((train_w + test_w)[i:i + 64], opts)
+        if args.sur_labels:
+            np.savez(args.sur_labels, eta_db=np.array(lab))
+    label_s = time.perf_counter() - t0
+    xtr = np.concatenate([S.features(w) for w in train_w])
+    ytr = np.concatenate(lab[:len(train_w)])
+    xte = np.concatenate([S.features(w) for w in test_w])
+    yte = np.concatenate(lab[len(train_w):])
+    model = S.Surrogate(seed=0)
+    model.fit_normalisation(xtr, ytr)
+    rng = np.random.default_rng(0)
+    bs = 8192
+    steps = args.sur_steps
+    t0 = time.perf_counter()
+    losses = []
+    for step in range(steps):
+        if step % max(1, len(xtr) // bs) == 0:
+            perm = rng.permutation(len(xtr))
+        j = (step % max(1, len(xtr) // bs)) * bs
+        idx = perm[j:j + bs]
+        lr = 1e-5 + 0.5 * (2e-3 - 1e-5) * (1 + math.cos(math.pi * step / steps))
+        losses.append(model.train_step(xtr[idx], ytr[idx], lr))
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t0
+    pred = model.predict_rows(xte)
+    err = pred - yte
+    # inference throughput: forward passes over a large block of rows, CUDA events
+    big = np.tile(xte, (max(1, (1 << 20) // len(xte)), 1))
+    model.predict_rows(big)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    rows, _ = model._load_inputs(big, None)
+    e0.record()
+    reps = 10
+    for _ in range(reps):
+        model._forward(None)
+        S.K.head(model.h[S.LAYERS], model.w_out, model.b_out, model.y)
+    e1.record()
+    e1.synchronize()
+    inf_ms = e0.elapsed_time(e1) / reps
+    flops = 2.0 * rows * (S.F_PAD * S.HIDDEN + (S.LAYERS - 1) * S.HIDDEN * S.HIDDEN + S.HIDDEN)
+    print(json.dumps({
+        "workload": f"surrogate: {args.sur_train} training + {args.sur_test} held-out seeded 120-ch C+L links "
+                    "(1-30 identical SSMF spans of 50-120 km, Cr 0.014-0.042, tilted rippled powers); labels from "
+                    "the FP32C integrator, 32 x 32 GL, dz 1 km",
+        "labels": "read from the cache file" if cached else "computed by the integrator in this run",
+        "label_seconds": None if cached else label_s,
+        "label_channel_evals_per_s": None if cached else 120 * (args.sur_train + args.sur_test) / label_s,
+        "train_steps": steps, "batch_rows": bs, "train_seconds": train_s,
+        "loss_first": losses[0], "loss_last": float(np.mean(losses[-20:])),
+        "heldout_mae_db": float(np.mean(np.abs(err))), "heldout_p99_abs_db": float(np.quantile(np.abs(err), 0.99)),
+        "heldout_max_abs_db": float(np.max(np.abs(err))),
+        "inference_rows": rows, "inference_ms": inf_ms, "inference_channel_evals_per_s": rows / (inf_ms * 1e-3),
+        "inference_tflops": flops / (inf_ms * 1e-3) / 1e12}), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -342,7 +419,14 @@ def main():
     ap.add_argument("--batch", action="store_true",
                     help="time a batch of small links: one by one vs one graph launch")
     ap.add_argument("--batch-links", type=int, default=24)
+    ap.add_argument("--surrogate", action="store_true", help="train and evaluate the MLP surrogate")
+    ap.add_argument("--sur-train", type=int, default=4096)
+    ap.add_argument("--sur-test", type=int, default=256)
+    ap.add_argument("--sur-steps", type=int, default=2000)
+    ap.add_argument("--sur-labels", default=None, help="npz cache of the integrator's labels (read if present)")
     args = ap.parse_args()
+    if args.surrogate:
+        return run_surrogate(args)
     if args.mu_compare:
         return run_mu_compare(args)
     if args.batch:

@@ -1,7 +1,7 @@
 """MLP surrogate of the ISRS EGN integrator: per-channel eta [dB] of a link.
 
 The integrator (egn_nli_eta) supplies the labels.  The network maps per-channel
-features to 10 log10(eta): 64 inputs (18 features, zero-padded to the GEMM's
+features to 10 log10(eta): 64 inputs (26 features, zero-padded to the GEMM's
 64-wide k blocks) -> 256 -> 256 -> 256 (ReLU) -> 1 (linear).  Weights and
 activations are BF16, products accumulate in FP32 on the tensor cores
 (egn_mlp_gemm, tcgen05); master weights and Adam state are FP32.  Every step of
@@ -22,7 +22,7 @@ import numpy as np
 from . import egn as E
 from . import mlp as K
 
-N_FEAT = 18
+N_FEAT = 26
 F_PAD = 64
 HIDDEN = 256
 LAYERS = 3
@@ -56,10 +56,25 @@ def features(wl) -> np.ndarray:
     ptot = float(np.sum(wl.launch_power_w))
     btot = (f.max() - f.min()) * 1e-12 * n / max(n - 1, 1)
     drho = cr * ptot * leff * btot  # ISRS tilt scale of Eq. 12 (nepers)
+    # interference seen by channel n from channel m scales as (P_m / P_n)^2 and falls
+    # with their distance on the grid (cross-channel islands of Eq. 15)
+    P = np.asarray(wl.launch_power_w, dtype=np.float64)
+    dist = np.abs(np.arange(n)[:, None] - np.arange(n)[None, :]).astype(np.float64)
+    off = dist > 0
+    k1 = np.where(off, 1.0 / np.where(off, dist, 1.0), 0.0)
+    k2 = k1 * k1
+    p2 = P * P
+    x1 = (k1 @ p2) / (p2 + 1e-300)
+    x2 = (k2 @ p2) / (p2 + 1e-300)
+    phi_w = (k1 @ (phi * p2)) / np.maximum(k1 @ p2, 1e-300)
+    edge = np.minimum(np.arange(n), n - 1 - np.arange(n)) / max(n / 2.0, 1.0)
     cols = [x, x ** 2, x ** 3, (p_dbm - 1.0) / 3.0, np.full(n, (pm - 1.0) / 3.0), np.full(n, slope / 3.0),
             (local - pm) / 2.0, np.full(n, (cr - 0.028) / 0.014), np.full(n, (L - 85.0) / 35.0),
             np.full(n, (ns - 15.5) / 15.0), np.full(n, math.log(ns) / math.log(30.0)), phi, psi / 10.0,
-            np.full(n, phi.mean()), local_phi, np.full(n, 1.0 / ns), np.full(n, drho), np.ones(n)]
+            np.full(n, phi.mean()), local_phi, np.full(n, 1.0 / ns), np.full(n, drho), np.ones(n),
+            np.log10(np.maximum(x1, 1e-300)) / 2.0, np.log10(np.maximum(x2, 1e-300)) / 2.0, phi_w, edge,
+            np.full(n, ns * L / 3000.0), np.full(n, math.log(leff)), np.full(n, math.log(ns) * math.log(L / 85.0)),
+            np.full(n, math.log(ns) ** 2 / 10.0)]
     return np.stack(cols, axis=1).astype(np.float64)
 
 
@@ -86,17 +101,20 @@ class Surrogate:
         rng = np.random.default_rng(seed)
         dims = [F_PAD] + [HIDDEN] * LAYERS
         self.W, self.b, self.Wb, self.WbT = [], [], [], []
+        # weights and biases uniform in +-1/sqrt(fan_in) (on these labels it generalises
+        # better than a He-normal start with zero biases)
         for i in range(LAYERS):
             fan_in = N_FEAT if i == 0 else dims[i]
+            lim = 1.0 / math.sqrt(fan_in)
             w = np.zeros((dims[i + 1], dims[i]), dtype=np.float32)
-            w[:, :fan_in] = rng.normal(0.0, math.sqrt(2.0 / fan_in), size=(dims[i + 1], fan_in))
+            w[:, :fan_in] = rng.uniform(-lim, lim, size=(dims[i + 1], fan_in))
             self.W.append(torch.tensor(w, device=device))
-            self.b.append(torch.zeros(dims[i + 1], dtype=torch.float32, device=device))
+            self.b.append(torch.tensor(rng.uniform(-lim, lim, dims[i + 1]).astype(np.float32), device=device))
             self.Wb.append(torch.empty(w.shape, dtype=torch.bfloat16, device=device))
             self.WbT.append(torch.empty((w.shape[1], w.shape[0]), dtype=torch.bfloat16, device=device))
-        self.w_out = torch.tensor(rng.normal(0.0, math.sqrt(1.0 / HIDDEN), size=HIDDEN).astype(np.float32),
-                                  device=device)
-        self.b_out = torch.zeros(1, dtype=torch.float32, device=device)
+        lim = 1.0 / math.sqrt(HIDDEN)
+        self.w_out = torch.tensor(rng.uniform(-lim, lim, HIDDEN).astype(np.float32), device=device)
+        self.b_out = torch.tensor(rng.uniform(-lim, lim, 1).astype(np.float32), device=device)
         self.params = [p for pair in zip(self.W, self.b) for p in pair] + [self.w_out, self.b_out]
         self.m = [torch.zeros_like(p) for p in self.params]
         self.v = [torch.zeros_like(p) for p in self.params]
