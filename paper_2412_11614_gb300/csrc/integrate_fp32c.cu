@@ -42,6 +42,8 @@ using namespace fp32c;
 
 constexpr int kThreads = 128;
 constexpr int kDwThreads = 64;     // CTA size of the D/G/H pass
+constexpr int kDwCtas = 10;        // its resident CTAs per SM
+constexpr int kDwBatch = 32;       // its islands per batch
 constexpr int kBatch = kThreads;   // islands per batch, one per thread in the set-up
 constexpr int kRowsMax = 64;       // rows per chunk held in shared memory
 constexpr int kTabFloats = 2688;   // DW c_k table budget (10.5 KB): [rows][kpad] floats
@@ -260,8 +262,11 @@ __device__ __forceinline__ void dw_recurrence(const float* __restrict__ trow, in
 // CTA, min_ctas resident CTAs per SM (the register budget follows from it) and
 // rows_max rows of constants per chunk.
 __host__ __device__ constexpr int min_ctas(int ord, int kp, int nt) {
-  return nt == 64 ? 8 : (kp == 8 ? 3 : (ord == ORD_DW ? 5 : 4));
+  return nt == 64 ? kDwCtas : (kp == 8 ? 3 : (ord == ORD_DW ? 5 : 4));
 }
+// Islands per batch (FP64 set-up, one island per thread): fewer than NT keeps the
+// batch arrays small enough for kDwCtas CTAs per SM.
+__host__ __device__ constexpr int batch_of(int nt) { return nt == 64 ? kDwBatch : nt; }
 __host__ __device__ constexpr int rows_max(int nt) { return nt == 64 ? 32 : kRowsMax; }
 
 // Fixed-order sum of the per-warp partial sums of a CTA.
@@ -281,7 +286,8 @@ integrate_fp32c_kernel(LinkParams p, const uint64_t* __restrict__ keys, const ui
                        Df G0, Df G1) {
   static_assert(KP % 2 == 0, "points per thread come in f32x2 pairs");
   constexpr int NPAIR = KP / 2;
-  __shared__ BatchSmT<NT> bs;
+  constexpr int NB = batch_of(NT);
+  __shared__ BatchSmT<NB> bs;
   __shared__ RowSm<rows_max(NT)> rs;
   __shared__ NodeSm ns;
   constexpr int NW = NT / 32;
@@ -317,11 +323,11 @@ integrate_fp32c_kernel(LinkParams p, const uint64_t* __restrict__ keys, const ui
     ns.x2[j] = make_float2(xh * p.gl.x2h[1][j], p.gl.wf[1][j]);
   }
 
-  for (long long b0 = (long long)blockIdx.x * NT; b0 < n_items; b0 += (long long)gridDim.x * NT) {
+  for (long long b0 = (long long)blockIdx.x * NB; b0 < n_items; b0 += (long long)gridDim.x * NB) {
     // ---------------- 1. batch set-up, FP64, one island per thread
-    batch_setup<ORD>(p, keys, list, n_items, b0, bs, tid);
+    if (tid < NB) batch_setup<ORD>(p, keys, list, n_items, b0, bs, tid);
     __syncthreads();
-    const int nb = (int)min((long long)NT, n_items - b0);
+    const int nb = (int)min((long long)NB, n_items - b0);
     // ---------------- 2./3. the islands of the batch, one after the other
     for (int ib = 0; ib < nb; ++ib) {
       const int np = bs.np[ib];
@@ -617,7 +623,7 @@ cudaError_t launch_one(const LinkParams& p, const uint64_t* keys, const uint32_t
     if (e != cudaSuccess) return e;
     attr_done |= 1ull << (dev & 63);
   }
-  long long batches = (n_items + NT - 1) / NT;
+  long long batches = (n_items + batch_of(NT) - 1) / batch_of(NT);
   long long blocks = (long long)sms * min_ctas(ORD, KP, NT);
   if (blocks > batches) blocks = batches;
   // 2 pi L beta2 and 2 pi^2 L beta3 as double-floats

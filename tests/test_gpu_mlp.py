@@ -4,8 +4,11 @@ BF16 values, and the surrogate's gradients against a CPU FP64 MLP.
 Tolerances: FP32-epilogue GEMM within 1e-5 of the FP64 product relative to
 sum |a||b| (FP32 accumulation over k <= 1024); BF16 epilogues within one BF16
 rounding (2^-8 relative) of the rounded FP64 result; whole-network gradients
-within 3e-2 relative (Frobenius): the network stores its activations and their
-gradients in BF16, the reference keeps FP64 throughout.
+within 1e-2 relative (Frobenius) of an FP64 reference that rounds to BF16 where
+the kernels store activations and their gradients (what remains: FP32 against
+FP64 accumulation and the odd BF16 tie), and within 1e-1 of the unrounded FP64
+reference (the size of the BF16 storage effect on a random-target problem,
+where the gradients are small residuals).
 """
 import numpy as np
 import pytest
@@ -143,24 +146,31 @@ def test_small_kernels(K):
     assert torch.equal(wt.cpu(), wb.cpu().T.contiguous())
 
 
-def _fp64_mlp_grads(x, Ws, bs, w_out, b_out, t, mask):
+def _round_bf16(a):
+    import torch
+    return torch.tensor(np.asarray(a, dtype=np.float64)).to(torch.bfloat16).double().numpy()
+
+
+def _fp64_mlp_grads(x, Ws, bs, w_out, b_out, t, mask, bf16_storage=False):
     """Plain FP64 forward/backward of the surrogate's network (ReLU MLP + linear
-    output, masked mean-squared loss)."""
+    output, masked mean-squared loss).  With bf16_storage the activations and
+    their gradients are rounded to BF16 where the device kernels store them."""
+    q = _round_bf16 if bf16_storage else (lambda a: a)
     hs = [x]
     for W, b in zip(Ws, bs):
-        hs.append(np.maximum(hs[-1] @ W.T + b, 0.0))
+        hs.append(q(np.maximum(hs[-1] @ W.T + b, 0.0)))
     y = hs[-1] @ w_out + b_out
     msum = mask.sum()
     loss = np.sum(mask * (y - t) ** 2) / msum
     g = 2 * mask * (y - t) / msum
     dW, db = [None] * len(Ws), [None] * len(Ws)
     dw_out, db_out = g @ hs[-1], g.sum()
-    d = np.outer(g, w_out) * (hs[-1] > 0)
+    d = q(np.outer(g, w_out) * (hs[-1] > 0))
     for i in reversed(range(len(Ws))):
         dW[i] = d.T @ hs[i]
         db[i] = d.sum(0)
         if i > 0:
-            d = (d @ Ws[i]) * (hs[i] > 0)
+            d = q((d @ Ws[i]) * (hs[i] > 0))
     return loss, dW, db, dw_out, db_out
 
 
@@ -181,17 +191,25 @@ def test_surrogate_gradients_match_fp64_mlp(K):
     xn[:, :S.N_FEAT] = (x - model.x_mean) / model.x_std
     xn = torch.tensor(xn, dtype=torch.float32).to(torch.bfloat16).double().numpy()
     tn = (t - model.y_mean) / model.y_std
-    lw, dW, db, dwo, dbo = _fp64_mlp_grads(xn, Ws, bs, w_out, b_out, tn, np.ones(rows))
-    assert abs(loss - lw) <= 1e-2 * lw
 
     def rel(a, b):
         return np.linalg.norm(a - b) / np.linalg.norm(b)
 
     g = [p.cpu().double().numpy() for p in model.grads]
+    # (1) the same arithmetic with BF16 storage where the kernels store: tight
+    lw, dW, db, dwo, dbo = _fp64_mlp_grads(xn, Ws, bs, w_out, b_out, tn, np.ones(rows), bf16_storage=True)
+    assert abs(loss - lw) <= 1e-3 * lw
     for i in range(S.LAYERS):
-        assert rel(g[2 * i], dW[i]) < 3e-2, (i, rel(g[2 * i], dW[i]))
-        assert rel(g[2 * i + 1], db[i]) < 3e-2
-    assert rel(g[-2], dwo) < 3e-2 and abs(g[-1][0] - dbo) <= 3e-2 * abs(dbo) + 1e-6
+        assert rel(g[2 * i], dW[i]) < 1e-2, (i, rel(g[2 * i], dW[i]))
+        assert rel(g[2 * i + 1], db[i]) < 1e-2, (i, rel(g[2 * i + 1], db[i]))
+    assert rel(g[-2], dwo) < 1e-3 and abs(g[-1][0] - dbo) <= 1e-3 * abs(dbo) + 1e-6
+    # (2) full FP64: the size of the BF16 storage effect on the gradients
+    lw, dW, db, dwo, dbo = _fp64_mlp_grads(xn, Ws, bs, w_out, b_out, tn, np.ones(rows))
+    assert abs(loss - lw) <= 1e-2 * lw
+    for i in range(S.LAYERS):
+        assert rel(g[2 * i], dW[i]) < 1e-1, (i, rel(g[2 * i], dW[i]))
+        assert rel(g[2 * i + 1], db[i]) < 1e-1
+    assert rel(g[-2], dwo) < 3e-2
 
 
 def test_surrogate_learns_a_smooth_map(K):
