@@ -516,8 +516,14 @@ def main():
         peak = 1.25
         peak_note = "FP64: 1.25 TFLOP/s nominal GB300 (no measured FP64 peak)"
     achieved = flops / (dgh_ms * 1e-3) / 1e12
+    # DRAM bytes (read + write) of one FP32C D/G/H launch on the 120-channel
+    # workload, from one ncu capture of that launch (dram__bytes_read.sum +
+    # dram__bytes_write.sum); island keys and lists are read once, the terms
+    # written stay in L2.  Valid for this kernel version only.
+    traffic = 22216704 + 18688 if (args.precision == "fp32c" and n_ch == 120) else None
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": None, "kernel": "integrate D/G/H pass", "peak_note": peak_note,
+                "traffic": traffic, "traffic_unit": "bytes per launch", "kernel": "integrate D/G/H pass",
+                "peak_note": peak_note,
                 "kernel_ms": dgh_ms, "flops_per_launch": flops,
                 "stage_ms": {k: statistics.mean(s[k] for s in stage) for k in stage[0]}}
 

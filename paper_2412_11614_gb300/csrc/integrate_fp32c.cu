@@ -41,9 +41,9 @@ namespace {
 using namespace fp32c;
 
 constexpr int kThreads = 128;
-constexpr int kDwThreads = 64;     // CTA size of the D/G/H pass
-constexpr int kDwCtas = 10;        // its resident CTAs per SM
-constexpr int kDwBatch = 32;       // its islands per batch
+constexpr int kDwThreads = 64;     // CTA size of the D/G/H, E and F passes
+constexpr int kDwCtas = 10;        // their resident CTAs per SM
+constexpr int kDwBatch = 32;       // their islands per batch
 constexpr int kBatch = kThreads;   // islands per batch, one per thread in the set-up
 constexpr int kRowsMax = 64;       // rows per chunk held in shared memory
 constexpr int kTabFloats = 2688;   // DW c_k table budget (10.5 KB): [rows][kpad] floats
@@ -994,8 +994,8 @@ cudaError_t launch_fp32c_pass(int ord, const LinkParams& p, const uint64_t* keys
     if (p.fp32c_kp == 8) return launch_one<ORD_DW, 8, 128>(p, keys, list, n_items, terms, n_isl, st);
     return launch_one<ORD_DW, 4, kDwThreads>(p, keys, list, n_items, terms, n_isl, st);
   }
-  if (ord == ORD_E) return launch_one<ORD_E, 4, 128>(p, keys, list, n_items, terms, n_isl, st);
-  return launch_one<ORD_F, 4, 128>(p, keys, list, n_items, terms, n_isl, st);
+  if (ord == ORD_E) return launch_one<ORD_E, 4, kDwThreads>(p, keys, list, n_items, terms, n_isl, st);
+  return launch_one<ORD_F, 4, kDwThreads>(p, keys, list, n_items, terms, n_isl, st);
 }
 
 }  // namespace egn
