@@ -27,9 +27,9 @@
  *     P_tot = sum of the launch powers.
  *   - Spans: every span is restored by an ideal amplifier (the gain/ISRS
  *     products of Eq. 22 equal 1).  Identical spans use the closed-form
- *     phased-array sum of Eq. 22; a link whose spans differ (at most 4
- *     distinct span types, at most 64 spans) sums Eq. 22 span by span with
- *     one mu per span type and the accumulated dispersion phase.
+ *     phased-array sum of Eq. 22; a link whose spans differ (at most 64
+ *     spans) sums Eq. 22 span by span with one mu per span type and the
+ *     accumulated dispersion phase.
  *   - Pulse spectra: raised cosine |S(f)|^2 = h(f)/R^2 with roll-off
  *     `rolloff`; the COI integral over f is R times the value at the COI
  *     centre (white NLI over the channel).
@@ -126,9 +126,12 @@ typedef struct {
 
 /* Create a link from n_spans >= 1 spans (copied).  Returns EGN_E_INVALID_ARG on
  * bad parameters.  Identical spans use the phased-array closed form of Eq. 22;
- * spans that differ (fibre or length) use the explicit coherent sum of Eq. 22,
- * for at most 4 distinct span types and 64 spans (larger heterogeneous links are
- * refused by the evaluation calls with EGN_E_UNSUPPORTED). */
+ * spans that differ (fibre or length) use the explicit coherent sum of Eq. 22
+ * for up to 64 spans (longer heterogeneous links are refused by the evaluation
+ * calls with EGN_E_UNSUPPORTED).  Up to 4 distinct span types evaluate each
+ * type's mu once per point with shared-memory c_k tables (their segments
+ * together at most 880); more types walk the spans in order, forming c_k on the
+ * fly, and egn_nli_eta_static refuses them (EGN_E_UNSUPPORTED). */
 egn_status egn_link_create(const egn_span* spans, int n_spans, egn_link** out);
 
 /* Release the link and its device tables.  NULL is ignored. */

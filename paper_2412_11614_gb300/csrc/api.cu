@@ -158,18 +158,16 @@ egn_status check_opts(const egn_link* l, const egn_opts* o) {
     return fail(EGN_E_UNSUPPORTED, "the Maclaurin and integral forms of mu run in FP64 only");
   if (o->terms != EGN_TERMS_GN && o->terms != EGN_TERMS_EGN) return fail(EGN_E_INVALID_ARG, "unknown terms %d", o->terms);
   if (o->timeout_ms < 0) return fail(EGN_E_INVALID_ARG, "timeout_ms < 0");
-  if (!l->identical) {
-    if ((int)l->type_si.size() > kMaxTypes || (int)l->spans_si.size() > kMaxSpans)
-      return fail(EGN_E_UNSUPPORTED, "heterogeneous links are limited to %d span types and %d spans", kMaxTypes,
-                  kMaxSpans);
-  }
+  if (!l->identical && (int)l->spans_si.size() > kMaxSpans)
+    return fail(EGN_E_UNSUPPORTED, "links whose spans differ are limited to %d spans", kMaxSpans);
   double ksum = 0.0;
   for (const egn_span& t : l->type_si) {
     double kk = std::ceil(t.length_m * 1e-3 / o->dz_km);
     if (kk > kMaxK) return fail(EGN_E_INVALID_ARG, "K = ceil(L/dz) = %.0f exceeds %d", kk, kMaxK);
     ksum += kk;
   }
-  if (!l->identical && ksum > kMaxKSum)
+  // up to kMaxTypes types keep every type's c_k table of a row in shared memory
+  if (!l->identical && (int)l->type_si.size() <= kMaxTypes && ksum > kMaxKSum)
     return fail(EGN_E_INVALID_ARG, "the span types need %.0f segments in all, more than %d", ksum, kMaxKSum);
   if (o->terms == EGN_TERMS_EGN && l->mixed_rates && l->any_corr)
     return fail(EGN_E_UNSUPPORTED, "EGN corrections with mixed symbol rates are not defined");
@@ -181,21 +179,27 @@ egn_status check_opts(const egn_link* l, const egn_opts* o) {
 egn_status ensure_tables(egn_link* l, const egn_opts* o) {
   if (l->tab_dz != o->dz_km) {
     const int nt = (int)l->type_si.size();
-    Span sp[kMaxTypes];
-    int Ks[kMaxTypes];
+    std::vector<Span> sp(nt);
+    std::vector<int> Ks(nt);
     size_t bytes = 0;
-    for (int t = 0; t < nt && t < kMaxTypes; ++t) {
+    for (int t = 0; t < nt; ++t) {
       sp[t] = to_internal(l->type_si[t], l->fc_hz);
       Ks[t] = std::max(1, (int)std::ceil(sp[t].L / o->dz_km));
       bytes += align256(Ks[t] * sizeof(double)) * 2 + align256(Ks[t] * sizeof(float)) * 2;
     }
     EGN_CUDA(l->d_seg.ensure(bytes));
-    char* p = (char*)l->d_seg.p;
-    for (int t = 0; t < nt && t < kMaxTypes; ++t) {
+    // every type's tables staged on the host and copied in one transfer
+    std::vector<char> host(bytes, 0);
+    char* base = (char*)l->d_seg.p;
+    size_t off = 0;
+    l->types.assign(nt, SpanType{});
+    for (int t = 0; t < nt; ++t) {
       const Span& s = sp[t];
       const int K = Ks[t];
-      std::vector<double> zeta(K), ck(K);
-      std::vector<float> zf(K), cf(K);
+      double* zeta = (double*)(host.data() + off);
+      double* ck = (double*)(host.data() + off + align256(K * sizeof(double)));
+      float* zf = (float*)(host.data() + off + 2 * align256(K * sizeof(double)));
+      float* cf = (float*)(host.data() + off + 2 * align256(K * sizeof(double)) + align256(K * sizeof(float)));
       for (int k = 0; k < K; ++k) {
         double z = (k + 0.5) / K * s.L;
         double leff = -std::expm1(-s.alpha * z) / s.alpha;
@@ -215,18 +219,16 @@ egn_status ensure_tables(egn_link* l, const egn_opts* o) {
       ty.r = std::exp(-s.alpha * ty.dz);
       ty.pcr = l->ptot * s.cr;
       ty.seg.K = K;
-      EGN_CUDA(cudaMemcpy(p, zeta.data(), K * sizeof(double), cudaMemcpyHostToDevice));
-      ty.seg.zeta = (const double*)p;
-      p += align256(K * sizeof(double));
-      EGN_CUDA(cudaMemcpy(p, ck.data(), K * sizeof(double), cudaMemcpyHostToDevice));
-      ty.seg.ck = (const double*)p;
-      p += align256(K * sizeof(double));
-      EGN_CUDA(cudaMemcpy(p, zf.data(), K * sizeof(float), cudaMemcpyHostToDevice));
-      ty.seg.zeta_f = (const float*)p;
-      p += align256(K * sizeof(float));
-      EGN_CUDA(cudaMemcpy(p, cf.data(), K * sizeof(float), cudaMemcpyHostToDevice));
-      ty.seg.ck_f = (const float*)p;
-      p += align256(K * sizeof(float));
+      ty.seg.zeta = (const double*)(base + ((char*)zeta - host.data()));
+      ty.seg.ck = (const double*)(base + ((char*)ck - host.data()));
+      ty.seg.zeta_f = (const float*)(base + ((char*)zf - host.data()));
+      ty.seg.ck_f = (const float*)(base + ((char*)cf - host.data()));
+      off += align256(K * sizeof(double)) * 2 + align256(K * sizeof(float)) * 2;
+    }
+    EGN_CUDA(cudaMemcpy(base, host.data(), bytes, cudaMemcpyHostToDevice));
+    if (nt > kMaxTypes) {
+      EGN_CUDA(l->d_types.ensure(nt * sizeof(SpanType)));
+      EGN_CUDA(cudaMemcpy(l->d_types.p, l->types.data(), nt * sizeof(SpanType), cudaMemcpyHostToDevice));
     }
     l->seg = l->types[0].seg;
     l->K = l->types[0].seg.K;
@@ -337,6 +339,7 @@ LinkParams link_params(const egn_link* l, const egn_opts* o, int all_terms) {
   set_mu_params(p, l, o);
   p.n_types = l->identical ? 1 : (int)l->type_si.size();
   for (int t = 0; t < p.n_types && t < kMaxTypes; ++t) p.types[t] = l->types[t];
+  p.types_dev = p.n_types > kMaxTypes ? (const SpanType*)l->d_types.p : nullptr;
   for (int s = 0; s < (int)l->span_type.size() && s < kMaxSpans; ++s) p.span_type[s] = l->span_type[s];
   return p;
 }
@@ -793,6 +796,8 @@ extern "C" egn_status egn_nli_eta_static(egn_link* l, const egn_opts* o, double*
 
   // link tables for these options, built on the host stack (no heap, no device allocation)
   const int nt = l->identical ? 1 : (int)l->type_si.size();
+  if (nt > kMaxTypes)
+    return fail(EGN_E_UNSUPPORTED, "the static scratch path takes at most %d span types (this link has %d)", kMaxTypes, nt);
   Span sps[kMaxTypes];
   int Ks[kMaxTypes];
   size_t o_zeta[kMaxTypes], o_ck[kMaxTypes], o_zf[kMaxTypes], o_cf[kMaxTypes];

@@ -165,7 +165,8 @@ egn_status create(egn_link* const* links, int n_links, const egn_opts* o, bool c
     L.n_ch = l->n_ch;
     L.cnt = l->cnt;
     L.tab_off = tab;
-    tab += align256(l->d_ch.bytes) + align256(l->d_seg.bytes) + align256(l->d_gl.bytes);
+    tab += align256(l->d_ch.bytes) + align256(l->d_seg.bytes) + align256(l->d_gl.bytes) +
+           align256(l->types.size() > (size_t)egn::kMaxTypes ? l->types.size() * sizeof(egn::SpanType) : 0);
     L.ws_off = ws;
     ws += align256(egn::workspace_bytes(l->n_ch, l->cnt, o->precision));
     b->links.push_back(L);
@@ -195,6 +196,19 @@ egn_status create(egn_link* const* links, int n_links, const egn_opts* o, bool c
     EGN_CUDA(cudaMemcpyAsync(gl_c, l->d_gl.p, l->d_gl.bytes, cudaMemcpyDeviceToDevice, b->cap));
     L.p = link_params(l, o, 0);
     rebase_params(L.p, l, ch_c, seg_c, gl_c);
+    if (L.p.n_types > egn::kMaxTypes) {  // the device array of span types, its tables rebased too
+      std::vector<egn::SpanType> ty(l->types);
+      for (auto& t : ty) {
+        rebase(t.seg.zeta, l->d_seg.p, l->d_seg.bytes, seg_c);
+        rebase(t.seg.ck, l->d_seg.p, l->d_seg.bytes, seg_c);
+        rebase(t.seg.zeta_f, l->d_seg.p, l->d_seg.bytes, seg_c);
+        rebase(t.seg.ck_f, l->d_seg.p, l->d_seg.bytes, seg_c);
+      }
+      char* ty_c = gl_c + align256(l->d_gl.bytes);
+      EGN_CUDA(cudaMemcpyAsync(ty_c, ty.data(), ty.size() * sizeof(egn::SpanType), cudaMemcpyHostToDevice, b->cap));
+      EGN_CUDA(cudaStreamSynchronize(b->cap));  // ty is a host temporary
+      L.p.types_dev = (const egn::SpanType*)ty_c;
+    }
     L.ch = L.p.ch;
   }
   // one plain run: validates the batch and completes lazy launch set-up

@@ -12,7 +12,7 @@ constexpr double kPi = 3.141592653589793238462643383279502884;
 constexpr double kC = 299792458.0;  // m/s
 constexpr int kMaxGl = 128;
 constexpr int kMaxK = 896;     // FP64 row tables: 32 lanes x K doubles of shared memory
-constexpr int kMaxKSum = 880;  // heterogeneous links: segments of all span types together
+constexpr int kMaxKSum = 880;  // links with 2..kMaxTypes span types: segments of all types together
 
 // Internal span: power attenuation [1/km], beta2 at the spectral centre
 // [ps^2/km], beta3 [ps^3/km], gamma [1/W/km], Cr [1/W/km/THz], length [km].
@@ -71,7 +71,9 @@ struct SegmentTables {
 };
 
 // Distinct span types of a heterogeneous link (Eq. 22 with different fibres or
-// lengths): at most kMaxTypes types and kMaxSpans spans.
+// lengths): up to kMaxSpans spans, any number of types.  Up to kMaxTypes types
+// travel in the launch parameters (the fast general path); links with more
+// types pass all of them in device memory (LinkParams::types_dev).
 constexpr int kMaxTypes = 4;
 constexpr int kMaxSpans = 64;
 struct SpanType {
@@ -110,9 +112,15 @@ struct LinkParams {
   double btot;       // B_tot [THz] of Eq. 25
   double mgx[kMuGl], mgw[kMuGl];  // Gauss-Legendre rule of the integral form on [-1, 1]
   int n_types;                       // distinct span types (1 = identical spans)
-  SpanType types[kMaxTypes];
+  SpanType types[kMaxTypes];         // the first kMaxTypes of them
+  const SpanType* types_dev;         // all n_types in device memory when n_types > kMaxTypes
   unsigned char span_type[kMaxSpans];  // type of span s, s = 0 .. n_spans - 1
 };
+
+// Span type t of a launch (either array).
+__host__ __device__ inline const SpanType& span_type_of(const LinkParams& p, int t) {
+  return p.n_types > kMaxTypes ? p.types_dev[t] : p.types[t];
+}
 
 // Flags of an island (Kronecker deltas of Eq. 15).
 __host__ __device__ inline bool flag_e(int n1, int n2, int n3) { (void)n2; return n1 == n3; }

@@ -981,10 +981,305 @@ cudaError_t launch_general(const LinkParams& p, const uint64_t* keys, const uint
                                                                                rows, gt);
   return cudaGetLastError();
 }
+// ---------------------------------------------------------------------------
+// Links with more than kMaxTypes span types (Eq. 22 span by span).  The span
+// types come from device memory; per row and type the phase polynomial lives in
+// dynamic shared memory; per point the spans are walked in order and a type's
+// gamma mu and e^{2 pi i phi} are recomputed only when the type changes from one
+// span to the next, with c_k formed on the fly (one ex2 per segment).  Two
+// points per thread, scalar recurrences.
+// ---------------------------------------------------------------------------
+
+constexpr int kSpanTypeFloats = 12;  // per type: G0 (df), G1 (df), K, 1/K, alpha, r, 1 - r, gamma, beta2, pi beta3
+
+template <int ORD>
+__global__ void __launch_bounds__(kThreads, 2)
+integrate_fp32c_spans_kernel(LinkParams p, const uint64_t* __restrict__ keys, const uint32_t* __restrict__ list,
+                             long long n_items, float* __restrict__ terms, long long n_isl, int rows_per_chunk) {
+  constexpr int KP = 2;
+  __shared__ BatchSm bs;
+  __shared__ float4 g_ab[kGRows], g_ow[kGRows], g_f3[kGRows];
+  __shared__ float g_ih[kGRows];
+  __shared__ NodeSm ns;
+  __shared__ float red[4][kThreads / 32];
+  extern __shared__ __align__(16) float dyn[];
+  const int T = p.n_types, R = rows_per_chunk;
+  float4* sqa = reinterpret_cast<float4*>(dyn);  // [T][R]
+  float4* sqb = sqa + T * R;                     // [T][R]
+  float2* skc = reinterpret_cast<float2*>(sqb + T * R);  // [T][R]
+  float* tyc = reinterpret_cast<float*>(skc + T * R);     // [T][kSpanTypeFloats]
+
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const int n = p.gl.n;
+  const float k4 = (float)(4.0 * kPi * kPi);
+  const float pi_f = 3.14159265358979f;
+  int tpr = 1;
+  while (tpr * KP < n) tpr <<= 1;
+  const int rows_per_pass = kThreads / tpr;
+  const int lr = tid & (tpr - 1);
+  const int rsub = tid / tpr;
+  for (int j = tid; j < n; j += kThreads) {
+    const float xh = p.gl.xh[1][j], xl = p.gl.xl[1][j];
+    ns.x4[j] = make_float4(xh, xl, p.gl.x2h[1][j], p.gl.x2l[1][j]);
+    ns.x2[j] = make_float2(xh * p.gl.x2h[1][j], p.gl.wf[1][j]);
+  }
+  for (int t = tid; t < T; t += kThreads) {
+    const SpanType& ty = p.types_dev[t];
+    const double g0 = 2.0 * kPi * ty.L * ty.beta2, g1 = 2.0 * kPi * kPi * ty.L * ty.beta3;
+    float* c = tyc + kSpanTypeFloats * t;
+    c[0] = (float)g0;
+    c[1] = (float)(g0 - (double)c[0]);
+    c[2] = (float)g1;
+    c[3] = (float)(g1 - (double)c[2]);
+    c[4] = (float)ty.seg.K;
+    c[5] = 1.0f / (float)ty.seg.K;
+    c[6] = (float)ty.alpha;
+    c[7] = (float)ty.r;
+    c[8] = (float)(-expm1(-ty.alpha * ty.dz));
+    c[9] = (float)ty.gamma;
+    c[10] = (float)ty.beta2;
+    c[11] = (float)(kPi * ty.beta3);
+  }
+  __syncthreads();
+
+  for (long long b0 = (long long)blockIdx.x * kBatch; b0 < n_items; b0 += (long long)gridDim.x * kBatch) {
+    batch_setup<ORD>(p, keys, list, n_items, b0, bs, tid);
+    __syncthreads();
+    const int nb = (int)min((long long)kBatch, n_items - b0);
+    for (int ib = 0; ib < nb; ++ib) {
+      const int np = bs.np[ib];
+      const int flags = bs.flags[ib];
+      const bool want_g = flags & 1, want_h = flags & 2;
+      const float sa1 = bs.ra[0][ib], sa2 = bs.ra[1][ib], sa3 = bs.ra[2][ib];
+      const float si1 = bs.ri[0][ib], si2 = bs.ri[1][ib], si3 = bs.ri[2][ib];
+      const float dfl = dval(bs.dd[ib]);
+      float dsum = 0.0f, csum = 0.0f, hre = 0.0f, him = 0.0f;
+      const int no = np > 0 ? p.gl.order[np] : 0;
+      const int rows = np * no;
+      for (int c0 = 0; c0 < rows; c0 += R) {
+        const int rc = min(R, rows - c0);
+        // ---- row constants: phase per (row, type); the geometry by the type-0 slots
+        for (int slot = tid; slot < rc * T; slot += kThreads) {
+          const int rr = slot % rc, t = slot / rc;
+          const int row = c0 + rr;
+          const int pi = row / no, i = row - pi * no;
+          const RowGeo g = row_geometry<ORD>(p, bs, ib, np, pi, i);
+          const float* c = tyc + kSpanTypeFloats * t;
+          const RowPhase q = row_phase(g, Df{c[0], c[1]}, Df{c[2], c[3]}, c[4], c[5]);
+          sqa[t * R + rr] = make_float4(q.Q0r.hi, q.Q0r.lo, q.Q1.hi, q.Q1.lo);
+          sqb[t * R + rr] = make_float4(q.Q2.hi, q.Q2.lo, q.Q3, q.Q0r.hi - rint_fast(q.Q0r.hi));
+          skc[t * R + rr] = make_float2(k4 * fmaf(c[11], dval(g.s0), c[10]), k4 * c[11] * dval(g.s1));
+          if (t == 0) {
+            const float imf = dval(g.im), ihf = dval(g.ih), of = dval(g.o);
+            const float wo = dval(g.ph) * p.gl.wf[np][i];
+            const float hout =
+                ORD == ORD_DW ? rc_f(of, sa3, si3) : (ORD == ORD_E ? rc_f(of, sa2, si2) : rc_f(of, sa1, si1));
+            g_ab[rr] = make_float4(dval(g.a0), dval(g.a1), dval(g.b0), dval(g.b1));
+            g_ow[rr] = make_float4(ORD == ORD_DW ? of - dfl : of, wo * ihf * hout, wo * ihf, hout);
+            const float nu3 = bs.nu3[ib];
+            if (ORD == ORD_DW) g_f3[rr] = make_float4(nu3 + of, 0.0f, wo, imf);
+            else g_f3[rr] = make_float4(nu3 + (imf + of + dfl), ihf, wo, imf);
+            g_ih[rr] = ihf;
+          }
+        }
+        __syncthreads();
+        for (int rb = 0; rb < rc; rb += rows_per_pass) {
+          const int rr = rb + rsub;
+          const bool row_ok = rr < rc;
+          const int rrc = row_ok ? rr : 0;
+          const float4 ab = g_ab[rrc], ow = g_ow[rrc], f3r = g_f3[rrc];
+          const float im = f3r.w, ih = g_ih[rrc];
+          const float wrowh = row_ok ? ow.y : 0.0f, wrow = row_ok ? ow.z : 0.0f;
+          float xh_[KP], wnode_[KP], f3_[KP], yre_[KP], yim_[KP], zre_[KP], zim_[KP];
+          float mre_[KP], mim_[KP], ere_[KP], eim_[KP];
+#pragma unroll
+          for (int m = 0; m < KP; ++m) {
+            const int j = lr + tpr * m;
+            const bool jok = j < n;
+            xh_[m] = ns.x4[jok ? j : 0].x;
+            wnode_[m] = jok ? ns.x2[j].y : 0.0f;
+            f3_[m] = fmaf(f3r.y, xh_[m], f3r.x);
+            yre_[m] = yim_[m] = 0.0f;
+            zre_[m] = 1.0f;
+            zim_[m] = 0.0f;
+            mre_[m] = mim_[m] = 0.0f;
+            ere_[m] = 1.0f;
+            eim_[m] = 0.0f;
+          }
+          int prev = -1;
+          for (int sp = 0; sp < p.n_spans; ++sp) {
+            const int t = p.span_type[sp];
+            if (t != prev) {  // gamma_t mu_t and e^{2 pi i phi_t} of this span's type
+              prev = t;
+              const float4 qa = sqa[t * R + rrc], qb = sqb[t * R + rrc];
+              const float2 kc = skc[t * R + rrc];
+              const float* c = tyc + kSpanTypeFloats * t;
+              const float Kf = c[4], invK = c[5], alpha = c[6], r = c[7], omr = c[8], gam = c[9];
+              const int K = (int)Kf;
+              float p_[KP], wm1_[KP], wi_[KP], chi_[KP], b1_[KP], b2_[KP];
+#pragma unroll
+              for (int m = 0; m < KP; ++m) {
+                const int j = lr + tpr * m;
+                const int jj = j < n ? j : 0;
+                float th, ph;
+                point_phase(qa, qb, ns.x4[jj], ns.x2[jj].x, Kf, invK, th, ph);
+                const float ah = pi_f * th;
+                const float sh = __sinf(ah), chh = __cosf(ah);
+                const float t2r = -2.0f * r * sh;
+                wm1_[m] = fmaf(t2r, sh, -omr);
+                p_[m] = fmaf(2.0f, wm1_[m], 2.0f);
+                wi_[m] = -t2r * chh;
+                const float xh = xh_[m];
+                chi_[m] = fmaf(ab.y, xh, ab.x) * fmaf(ab.w, xh, ab.z) * fmaf(kc.y, xh, kc.x);
+                const float ang = 2.0f * pi_f * ph;
+                ere_[m] = __cosf(ang);
+                eim_[m] = __sinf(ang);
+                b1_[m] = 0.0f;
+                b2_[m] = 0.0f;
+              }
+              const float q = r * r;
+              const float* ckf = p.types_dev[t].seg.ck_f;
+              const float* zkf = p.types_dev[t].seg.zeta_f;
+              for (int k = K - 1; k >= 0; --k) {
+                const float ck = __ldg(ckf + k), zk = __ldg(zkf + k);
+#pragma unroll
+                for (int m = 0; m < KP; ++m) {
+                  const float cc = ck * ex2_approx(-zk * f3_[m]);
+                  const float bn = fmaf(p_[m], b1_[m], fmaf(-q, b2_[m], cc));
+                  b2_[m] = b1_[m];
+                  b1_[m] = bn;
+                }
+              }
+#pragma unroll
+              for (int m = 0; m < KP; ++m) {
+                const float wm1 = wm1_[m], wi = wi_[m], chi = chi_[m];
+                const float sre = fmaf(-(wm1 + 1.0f), b2_[m], b1_[m]);
+                const float sim = wi * b2_[m];
+                const float inv = rcp_approx(fmaf(chi, chi, alpha * alpha)) * gam;
+                const float qr = fmaf(-alpha, wm1, chi * wi) * inv;
+                const float qi = fmaf(-chi, wm1, -alpha * wi) * inv;
+                mre_[m] = fmaf(sre, qr, -sim * qi);  // gamma_t mu_t
+                mim_[m] = fmaf(sre, qi, sim * qr);
+              }
+            }
+#pragma unroll
+            for (int m = 0; m < KP; ++m) {
+              yre_[m] = fmaf(mre_[m], zre_[m], fmaf(-mim_[m], zim_[m], yre_[m]));
+              yim_[m] = fmaf(mre_[m], zim_[m], fmaf(mim_[m], zre_[m], yim_[m]));
+              const float zr = fmaf(zre_[m], ere_[m], -zim_[m] * eim_[m]);
+              zim_[m] = fmaf(zre_[m], eim_[m], zim_[m] * ere_[m]);
+              zre_[m] = zr;
+            }
+          }
+          // weights and sums (Upsilon itself, gamma included)
+          float gre = 0.0f, gim = 0.0f;
+#pragma unroll
+          for (int m = 0; m < KP; ++m) {
+            const float tt = fmaf(ih, xh_[m], im);
+            float u, v, h3;
+            if (ORD == ORD_DW) { u = tt; v = ow.x - tt; h3 = 1.0f; }
+            else {
+              if (ORD == ORD_E) { v = ow.x; u = tt; } else { u = ow.x; v = tt; }
+              h3 = rc_f(u + v + dfl, sa3, si3);
+            }
+            const float h1 = rc_f(u, sa1, si1), h2 = rc_f(v, sa2, si2);
+            const float yre = yre_[m], yim = yim_[m];
+            if (ORD == ORD_DW) {
+              dsum = fmaf((wrowh * wnode_[m]) * (h1 * h2), fmaf(yre, yre, yim * yim), dsum);
+              if (want_g) {
+                const float a12 = (row_ok ? wnode_[m] : 0.0f) * sqrtf(h1 * h2);
+                gre = fmaf(a12, yre, gre);
+                gim = fmaf(a12, yim, gim);
+              }
+              if (want_h) {
+                const float a123 = wrow * wnode_[m] * sqrtf(h1 * h2 * ow.w);
+                hre = fmaf(a123, yre, hre);
+                him = fmaf(a123, yim, him);
+              }
+            } else {
+              const float a = (row_ok ? wnode_[m] : 0.0f) * ih * sqrtf(ORD == ORD_E ? h1 * h3 : h2 * h3);
+              gre = fmaf(a, yre, gre);
+              gim = fmaf(a, yim, gim);
+            }
+          }
+          if (ORD != ORD_DW || want_g) {
+            for (int o_ = tpr >> 1; o_ > 0; o_ >>= 1) {
+              gre += __shfl_xor_sync(0xffffffffu, gre, o_);
+              gim += __shfl_xor_sync(0xffffffffu, gim, o_);
+            }
+            if (lr == 0 && row_ok) {
+              const float ihr = (ORD == ORD_DW) ? ih : 1.0f;
+              const float gr_ = gre * ihr, gi_ = gim * ihr;
+              csum = fmaf(f3r.z * ow.w, gr_ * gr_ + gi_ * gi_, csum);
+            }
+          }
+        }
+        __syncthreads();
+      }
+      float vals[4] = {dsum, csum, hre, him};
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+        for (int o_ = 16; o_ > 0; o_ >>= 1) vals[a] += __shfl_xor_sync(0xffffffffu, vals[a], o_);
+      if (lane == 0)
+#pragma unroll
+        for (int a = 0; a < 4; ++a) red[a][wid] = vals[a];
+      __syncthreads();
+      if (tid == 0) {
+        float t[4];
+        for (int a = 0; a < 4; ++a) t[a] = warp_sum<kThreads / 32>(red[a]);
+        const long long isl = bs.isl[ib];
+        if (ORD == ORD_DW) {
+          terms[isl] = bs.cf0[ib] * t[0];
+          if (want_g) terms[3 * n_isl + isl] = bs.cf1[ib] * t[1];
+          if (want_h) terms[4 * n_isl + isl] = bs.cf2[ib] * (t[2] * t[2] + t[3] * t[3]);
+        } else {
+          terms[(ORD == ORD_E ? 1 : 2) * n_isl + isl] = bs.cf0[ib] * t[1];
+        }
+      }
+      __syncthreads();
+    }
+  }
+}
+
+constexpr int kSpansDynBytes = 48 * 1024;  // per-type constants and row phases
+
+template <int ORD>
+cudaError_t launch_spans(const LinkParams& p, const uint64_t* keys, const uint32_t* list, long long n_items,
+                         float* terms, long long n_isl, cudaStream_t st) {
+  if (n_items <= 0) return cudaSuccess;
+  const int T = p.n_types;
+  const int per_type = (int)(2 * sizeof(float4) + sizeof(float2));
+  int rows = (kSpansDynBytes - T * kSpanTypeFloats * (int)sizeof(float)) / (T * per_type);
+  if (rows > kGRows) rows = kGRows;
+  if (rows < 1) return cudaErrorInvalidValue;  // not reached: T <= kMaxSpans leaves at least 16 rows
+  const size_t smem = (size_t)T * rows * per_type + (size_t)T * kSpanTypeFloats * sizeof(float);
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  static unsigned long long attr_done = 0;
+  if (!(attr_done >> (dev & 63) & 1ull)) {
+    cudaError_t e = cudaFuncSetAttribute(integrate_fp32c_spans_kernel<ORD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         kSpansDynBytes);
+    if (e != cudaSuccess) return e;
+    attr_done |= 1ull << (dev & 63);
+  }
+  long long batches = (n_items + kBatch - 1) / kBatch;
+  long long blocks = (long long)sms * 2;
+  if (blocks > batches) blocks = batches;
+  integrate_fp32c_spans_kernel<ORD><<<(unsigned)blocks, kThreads, smem, st>>>(p, keys, list, n_items, terms, n_isl,
+                                                                             rows);
+  return cudaGetLastError();
+}
+
 }  // namespace
 
 cudaError_t launch_fp32c_pass(int ord, const LinkParams& p, const uint64_t* keys, const uint32_t* list,
                               long long n_items, float* terms, long long n_isl, cudaStream_t st) {
+  if (p.n_types > kMaxTypes) {
+    if (ord == ORD_DW) return launch_spans<ORD_DW>(p, keys, list, n_items, terms, n_isl, st);
+    if (ord == ORD_E) return launch_spans<ORD_E>(p, keys, list, n_items, terms, n_isl, st);
+    return launch_spans<ORD_F>(p, keys, list, n_items, terms, n_isl, st);
+  }
   if (p.n_types > 1) {
     if (ord == ORD_DW) return launch_general<ORD_DW>(p, keys, list, n_items, terms, n_isl, st);
     if (ord == ORD_E) return launch_general<ORD_E>(p, keys, list, n_items, terms, n_isl, st);

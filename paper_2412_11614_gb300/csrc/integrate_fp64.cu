@@ -139,46 +139,66 @@ __device__ __forceinline__ Cd upsilon_fp64(const LinkParams& p, double f1, doubl
   return {g * y.re, g * y.im};
 }
 
+// gamma_t mu_t and e^{i phi_t} (phi_t = chi_t L_t) of span type t at one point.
+// ck: this row's c_k of type t (stride 32) or null (c_k formed from f3).
+__device__ __forceinline__ void type_mu(const LinkParams& p, const SpanType& ty, double a, double b, double f1,
+                                        double f2, const double* ck, double f3, Cd& gmu, Cd& eph) {
+  const double chi = 4.0 * kPi * kPi * a * b * (ty.beta2 + kPi * ty.beta3 * (f1 + f2));
+  double tp = chi * (ty.L / (2.0 * kPi));
+  tp -= rint(tp);
+  double s, c;
+  Cd m;
+  if (p.mu_form == MU_MACLAURIN) {
+    m = mu_maclaurin(chi, f3, ty.alpha, ty.L, ty.pcr, tp);
+  } else if (p.mu_form == MU_INTEGRAL) {
+    m = mu_integral(p, chi, f3, ty.alpha, ty.L, ty.pcr);
+  } else {
+    double tt = chi * (ty.dz / (2.0 * kPi));
+    tt -= rint(tt);
+    sincospi(2.0 * tt, &s, &c);
+    const Cd w = {ty.r * c, ty.r * s};
+    Cd acc = {0.0, 0.0};
+    const int K = ty.seg.K;
+    for (int k = K - 1; k >= 0; --k) {
+      acc = cmul(acc, w);
+      acc.re += ck ? ck[k * 32] : ty.seg.ck[k] * exp(-ty.seg.zeta[k] * f3);
+    }
+    const double xr = w.re - 1.0, xi = w.im;
+    const double den = ty.alpha * ty.alpha + chi * chi;
+    const Cd q = {(-ty.alpha * xr + chi * xi) / den, (-chi * xr - ty.alpha * xi) / den};
+    m = cmul(acc, q);
+  }
+  gmu = {ty.gamma * m.re, ty.gamma * m.im};
+  sincospi(2.0 * tp, &s, &c);
+  eph = {c, s};
+}
+
 // Upsilon of a link whose spans differ (Eq. 22 written out): mu_t and the span
 // phase phi_t = chi_t L_t of every span type t, then the coherent sum
 // Y = sum_s gamma_{t(s)} mu_{t(s)} e^{i Phi_s}, Phi_{s+1} = Phi_s + phi_{t(s)}.
-// ck (row tables, stride 32, type t at offset koff[t]) or null (c_k on the fly).
+// Up to kMaxTypes types: each type once per point, ck the row tables (stride
+// 32, type t at offset koff[t]) or null.  More types: span by span, c_k formed
+// on the fly, a type's mu reused while consecutive spans share it.
 __device__ __forceinline__ Cd upsilon_fp64_general(const LinkParams& p, double f1, double f2, double f,
                                                    const double* ck, const int* koff, double f3) {
-  Cd mu[kMaxTypes], ph[kMaxTypes];
   const double a = f1 - f, b = f2 - f;
-  for (int t = 0; t < p.n_types; ++t) {
-    const SpanType& ty = p.types[t];
-    const double chi = 4.0 * kPi * kPi * a * b * (ty.beta2 + kPi * ty.beta3 * (f1 + f2));
-    double tp = chi * (ty.L / (2.0 * kPi));
-    tp -= rint(tp);
-    double s, c;
-    Cd m;
-    if (p.mu_form == MU_MACLAURIN) {
-      m = mu_maclaurin(chi, f3, ty.alpha, ty.L, ty.pcr, tp);
-    } else if (p.mu_form == MU_INTEGRAL) {
-      m = mu_integral(p, chi, f3, ty.alpha, ty.L, ty.pcr);
-    } else {
-      double tt = chi * (ty.dz / (2.0 * kPi));
-      tt -= rint(tt);
-      sincospi(2.0 * tt, &s, &c);
-      const Cd w = {ty.r * c, ty.r * s};
-      Cd acc = {0.0, 0.0};
-      const int K = ty.seg.K;
-      for (int k = K - 1; k >= 0; --k) {
-        acc = cmul(acc, w);
-        acc.re += ck ? ck[(koff[t] + k) * 32] : ty.seg.ck[k] * exp(-ty.seg.zeta[k] * f3);
-      }
-      const double xr = w.re - 1.0, xi = w.im;
-      const double den = ty.alpha * ty.alpha + chi * chi;
-      const Cd q = {(-ty.alpha * xr + chi * xi) / den, (-chi * xr - ty.alpha * xi) / den};
-      m = cmul(acc, q);
-    }
-    mu[t] = {ty.gamma * m.re, ty.gamma * m.im};
-    sincospi(2.0 * tp, &s, &c);
-    ph[t] = {c, s};
-  }
   Cd z = {1.0, 0.0}, Y = {0.0, 0.0};
+  if (p.n_types > kMaxTypes) {
+    Cd m = {0.0, 0.0}, e = {1.0, 0.0};
+    int prev = -1;
+    for (int sp = 0; sp < p.n_spans; ++sp) {
+      const int t = p.span_type[sp];
+      if (t != prev) type_mu(p, p.types_dev[t], a, b, f1, f2, nullptr, f3, m, e);
+      prev = t;
+      const Cd v = cmul(m, z);
+      Y.re += v.re;
+      Y.im += v.im;
+      z = cmul(z, e);
+    }
+    return Y;
+  }
+  Cd mu[kMaxTypes], ph[kMaxTypes];
+  for (int t = 0; t < p.n_types; ++t) type_mu(p, p.types[t], a, b, f1, f2, ck ? ck + koff[t] * 32 : nullptr, f3, mu[t], ph[t]);
   for (int sp = 0; sp < p.n_spans; ++sp) {
     const int t = p.span_type[sp];
     const Cd v = cmul(mu[t], z);
@@ -202,10 +222,12 @@ __global__ void __launch_bounds__(32) integrate_fp64_kernel(LinkParams p, const 
                                                             double* __restrict__ terms, long long n_isl) {
   extern __shared__ double ck_s[];  // [K][32] (DW order only); general links: types one after the other
   const int lane = threadIdx.x;
+  // c_k row tables of up to kMaxTypes span types (more types form c_k on the fly)
+  const bool tables = p.n_types <= kMaxTypes && p.mu_form == MU_SEGMENT;
   int koff[kMaxTypes];
   for (int t = 0, o = 0; t < kMaxTypes; ++t) {
     koff[t] = o;
-    if (t < p.n_types) o += p.types[t].seg.K;
+    if (t < p.n_types && tables) o += p.types[t].seg.K;
   }
   const ChannelTable& ch = p.ch;
   const int n = p.gl.n;
@@ -244,7 +266,7 @@ __global__ void __launch_bounds__(32) integrate_fp64_kernel(LinkParams p, const 
         double outer_h;
         if (ORD == ORD_DW) {
           double f3 = nu3 + o;
-          if (active && p.mu_form == MU_SEGMENT) {
+          if (active && tables) {
             if (p.n_types == 1) {
               for (int k = 0; k < p.seg.K; ++k) ck_s[k * 32 + lane] = p.seg.ck[k] * exp(-p.seg.zeta[k] * f3);
             } else {
@@ -278,7 +300,7 @@ __global__ void __launch_bounds__(32) integrate_fp64_kernel(LinkParams p, const 
               dsum += wo * wi * h1 * h2 * h3 * y2;
             } else {
               Cd Y = p.n_types == 1 ? upsilon_fp64(p, f1, f2, nu, ckrow, 32, nu3 + w, &af2, true)
-                                    : upsilon_fp64_general(p, f1, f2, nu, ORD == ORD_DW ? ck_s + lane : nullptr,
+                                    : upsilon_fp64_general(p, f1, f2, nu, (ORD == ORD_DW && tables) ? ck_s + lane : nullptr,
                                                            koff, nu3 + w);
               if (ORD == ORD_DW) {
                 dsum += wo * wi * h1 * h2 * h3 * (Y.re * Y.re + Y.im * Y.im);
@@ -324,10 +346,11 @@ template <int ORD>
 cudaError_t launch_one(const LinkParams& p, const uint64_t* keys, const uint32_t* list, long long n_items,
                        double* terms, long long n_isl, cudaStream_t st) {
   if (n_items <= 0) return cudaSuccess;
-  int ksum = p.seg.K;
+  int ksum = p.mu_form == MU_SEGMENT ? p.seg.K : 0;
   if (p.n_types > 1) {
     ksum = 0;
-    for (int t = 0; t < p.n_types; ++t) ksum += p.types[t].seg.K;
+    if (p.n_types <= kMaxTypes && p.mu_form == MU_SEGMENT)
+      for (int t = 0; t < p.n_types; ++t) ksum += p.types[t].seg.K;
   }
   size_t smem = (ORD == ORD_DW) ? (size_t)ksum * 32 * sizeof(double) : 0;
   static bool attr_set[3] = {false, false, false};

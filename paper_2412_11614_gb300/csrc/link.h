@@ -77,7 +77,8 @@ struct egn_link {
   int tab_gl = -1;
   int K = 0;
   egn::Span span{};
-  egn::SpanType types[egn::kMaxTypes] = {};
+  std::vector<egn::SpanType> types;  // every span type's tables (device pointers)
+  egn_host::DevBuf d_types;          // the same array in device memory (more than kMaxTypes types)
   egn_host::DevBuf d_seg, d_gl;
   egn::SegmentTables seg{};
   egn::GlTables gl{};
@@ -94,6 +95,7 @@ struct egn_link {
     d_ch.release();
     d_seg.release();
     d_gl.release();
+    d_types.release();
     ws.release();
     d_stage.release();
     if (h_stage) cudaFreeHost(h_stage);

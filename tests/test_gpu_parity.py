@@ -223,10 +223,66 @@ def test_heterogeneous_spans_island_terms(egn, oracle_mod, workloads, prec):
         assert np.all(err <= 3e-4 * np.abs(want) + 3e-5 * np.abs(want[:, :1]))
 
 
-def test_too_many_span_types_unsupported(egn, workloads):
-    wl = workloads.config_small(n_spans=5)
+def _many_types_link(workloads, n_ch=3, gl=10):
+    """Seven spans of six types: lengths 55..115 km, SSMF and PSCF, the first
+    type again at the end (a type that recurs after others)."""
+    wl = workloads.config_small(n_ch=n_ch, gl_order=gl, n_spans=7)
+    for i, s in enumerate(wl.spans[:6]):
+        s.length_m = (55 + 12 * i) * 1e3
+        if i % 2:
+            s.alpha_db_km, s.D_ps_nm_km, s.gamma_per_w_km = 0.16, 21.0, 0.8
+    last = wl.spans[6]
+    for k, v in wl.spans[0].__dict__.items():
+        setattr(last, k, v)
+    return wl
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32c"])
+def test_many_span_types_eta(egn, oracle_mod, workloads, prec):
+    """More than four span types: Eq. 22 walked span by span (c_k on the fly)."""
+    wl = _many_types_link(workloads)
+    ln, pb = _pair(egn, oracle_mod, wl)
+    p = egn.EGN_PREC_FP64 if prec == "fp64" else egn.EGN_PREC_FP32C
+    got, _ = ln.nli_eta(egn.make_opts(gl_order=10, precision=p))
+    want, _ = pb.eta()
+    if prec == "fp64":
+        assert np.allclose(got, want, rtol=FP64_RTOL, atol=0), got / want - 1
+    else:
+        assert np.max(_db(got, want)) < 1e-3, _db(got, want)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32c"])
+def test_many_span_types_island_terms(egn, oracle_mod, workloads, prec):
+    wl = _many_types_link(workloads, gl=7)
+    ln, pb = _pair(egn, oracle_mod, wl, gl=7)
+    isl = np.array([(n, *t) for n in range(3) for t in pb.islands(n)], dtype=np.int32)
+    p = egn.EGN_PREC_FP64 if prec == "fp64" else egn.EGN_PREC_FP32C
+    got = ln.island_terms(egn.make_opts(gl_order=7, precision=p), isl, all_terms=True)
+    want = np.array([pb.island_terms(*row, all_terms=True) for row in isl])
+    if prec == "fp64":
+        assert np.allclose(got, want, rtol=FP64_RTOL, atol=1e-300)
+    else:
+        err = np.abs(got - want)
+        assert np.all(err <= 3e-4 * np.abs(want) + 3e-5 * np.abs(want[:, :1]))
+
+
+@pytest.mark.parametrize("seed", [1, 2, 5])
+def test_random_link_spans(egn, oracle_mod, workloads, seed):
+    """The spans of the seeded random links (up to 30, each length drawn) on a
+    4-channel comb of the link's rate, FP32C against the oracle."""
+    rl = workloads.random_link(seed)
+    wl = workloads.config_small(n_ch=4, gl_order=8)
+    wl.spans = rl.spans
+    ln, pb = _pair(egn, oracle_mod, wl)
+    got, _ = ln.nli_eta(egn.make_opts(gl_order=8, precision=egn.EGN_PREC_FP32C))
+    want, _ = pb.eta()
+    assert np.max(_db(got, want)) < 1e-3, (len(rl.spans), _db(got, want))
+
+
+def test_more_than_64_differing_spans_unsupported(egn, workloads):
+    wl = workloads.config_small(n_spans=65)
     for i, s in enumerate(wl.spans):
-        s.length_m = (60 + 5 * i) * 1e3
+        s.length_m = (50 + i) * 1e3
     ln = egn.link_from_workload(wl)
     with pytest.raises(egn.EgnError) as ei:
         ln.nli_eta(egn.make_opts())

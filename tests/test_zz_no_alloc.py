@@ -83,3 +83,17 @@ def test_static_refuses_oversized_evaluation(egn, workloads):
     assert ei.value.status == egn.EGN_E_CAPACITY
     assert "static scratch" in str(ei.value)
     ln.close()
+
+
+def test_static_refuses_many_span_types(egn, workloads):
+    import torch
+    wl = workloads.config_small(n_ch=2, gl_order=8, n_spans=5)
+    for i, s in enumerate(wl.spans):
+        s.length_m = (60 + 7 * i) * 1e3
+    ln = egn.link_from_workload(wl)
+    eta = torch.empty(2, dtype=torch.float64, device="cuda")
+    pn = torch.empty(2, dtype=torch.float64, device="cuda")
+    with pytest.raises(egn.EgnError) as ei:
+        ln.nli_eta_static(egn.make_opts(gl_order=8), eta, pn)
+    assert ei.value.status == egn.EGN_E_UNSUPPORTED
+    ln.close()
