@@ -282,12 +282,17 @@ def run_batch_compare(args):
     _build.build()
     torch.cuda.set_device(0)
     stream = torch.cuda.Stream()
-    wls = []
-    for i in range(args.batch_links):
-        wl = W.config_cl(n_ch=8 + 8 * (i % 6), n_spans=1 + (i % 10), seed=i)
-        wls.append(wl)
+    if args.batch_random:  # seeded heterogeneous links: 20-200 ch, 1-30 spans of drawn lengths and fibres
+        gl = 16
+        wls = [W.random_link(i + 1, gl_order=gl) for i in range(args.batch_links)]
+        desc = (f"{len(wls)} seeded random links (20-200 ch, 32-96 GBd, 1-30 SSMF/PSCF spans of 50-120 km, "
+                f"tilted rippled powers), {gl} x {gl} GL, FP32C, EGN")
+    else:
+        gl = 32
+        wls = [W.config_cl(n_ch=8 + 8 * (i % 6), n_spans=1 + (i % 10), seed=i) for i in range(args.batch_links)]
+        desc = "C+L grid cut to 8..48 channels, 1..10 x 80 km, 32 x 32 GL, FP32C, EGN"
     links = [egn.link_from_workload(w) for w in wls]
-    opts = egn.make_opts(gl_order=32, precision=egn.EGN_PREC_FP32C, stream=stream.cuda_stream)
+    opts = egn.make_opts(gl_order=gl, precision=egn.EGN_PREC_FP32C, stream=stream.cuda_stream)
     ws = [torch.empty(ln.workspace_size(opts), dtype=torch.uint8, device="cuda") for ln in links]
     outs = [(torch.empty(ln.n_ch, dtype=torch.float64, device="cuda"),
              torch.empty(ln.n_ch, dtype=torch.float64, device="cuda")) for ln in links]
@@ -300,7 +305,7 @@ def run_batch_compare(args):
 
     def timed(fn, reps):
         with torch.cuda.stream(stream):
-            for _ in range(3):
+            for _ in range(1 if args.batch_random else 3):
                 fn()
             t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             t0.record(stream)
@@ -310,13 +315,15 @@ def run_batch_compare(args):
         t1.synchronize()
         return t0.elapsed_time(t1) / reps
 
-    seq_ms = timed(one_by_one, args.steps)
-    graph_ms = timed(lambda: b.launch(stream.cuda_stream), args.steps)
+    reps = 2 if args.batch_random else args.steps
+    seq_ms = timed(one_by_one, reps)
+    graph_ms = timed(lambda: b.launch(stream.cuda_stream), reps)
     got = b.read(stream.cuda_stream)
     same = all(np.array_equal(g[0], o[0].cpu().numpy()) for g, o in zip(got, outs))
     n_ch = int(b.offsets[-1])
     print(json.dumps({"links": len(links), "channels": n_ch,
-                      "workload": "C+L grid cut to 8..48 channels, 1..10 x 80 km, 32 x 32 GL, FP32C, EGN",
+                      "span_types": [len({(s.length_m, s.alpha_db_km, s.D_ps_nm_km) for s in w.spans}) for w in wls],
+                      "workload": desc,
                       "ms_one_by_one": seq_ms, "ms_graph": graph_ms, "speedup": seq_ms / graph_ms,
                       "channel_evals_per_s_graph": n_ch / (graph_ms * 1e-3), "results_identical": same}), flush=True)
     b.close()
@@ -419,6 +426,7 @@ def main():
     ap.add_argument("--batch", action="store_true",
                     help="time a batch of small links: one by one vs one graph launch")
     ap.add_argument("--batch-links", type=int, default=24)
+    ap.add_argument("--batch-random", action="store_true", help="the batch is seeded heterogeneous random links")
     ap.add_argument("--surrogate", action="store_true", help="train and evaluate the MLP surrogate")
     ap.add_argument("--sur-train", type=int, default=4096)
     ap.add_argument("--sur-test", type=int, default=256)

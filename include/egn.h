@@ -200,8 +200,9 @@ egn_status egn_nli_eta_static(egn_link* link, const egn_opts* opts, double* eta_
  * so later egn_set_wdm calls or egn_link_destroy on the links do not affect
  * the batch.  It allocates one workspace per link and the outputs of all
  * links, runs the whole evaluation once (validation; egn_batch_read can read
- * its results), and captures it into a CUDA graph in which every link's chain
- * (island planner, integrator passes, assembly) is an independent branch.
+ * its results), and captures it into a CUDA graph of every link's chain
+ * (island planner, integrator passes, assembly): links too small to fill the
+ * GPU are concurrent branches, links that fill it run one after the other.
  * opts->stream is ignored; opts->timeout_ms applies to egn_batch_read.
  * Errors as egn_nli_eta (the first failing link is reported).
  *

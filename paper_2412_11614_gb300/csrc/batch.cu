@@ -6,11 +6,15 @@
 // workspace per link in a single allocation, runs the whole evaluation once
 // without capture (which validates it and completes every lazy launch set-up),
 // then captures the same sequence into a CUDA graph.  In the graph each link's
-// chain -- status reset, planner, integrator passes, assembly -- is an
-// independent branch on one of up to kStreams capture streams, so links that
-// underfill the GPU run side by side.  egn_batch_launch replays the graph with
-// one call; outputs of all links are concatenated in link order.
+// chain -- status reset, planner, integrator passes, assembly -- is captured
+// in two phases: links too small to fill the GPU as concurrent branches on up to
+// kStreams streams, then the links that fill it on their own ("heavy":
+// estimated point-segment work above kHeavyWork) one after the other, because
+// heavy links sharing the GPU were measured to slow each other down.
+// egn_batch_launch replays the graph with one call; outputs of all links are
+// concatenated in link order.
 #include <algorithm>
+#include <cmath>
 #include <cstring>
 #include <new>
 #include <vector>
@@ -25,7 +29,9 @@ using egn::Workspace;
 
 namespace {
 
-constexpr int kStreams = 8;  // capture streams: concurrent branches of the graph
+constexpr int kStreams = 8;             // capture streams: concurrent branches of the graph
+constexpr double kHeavyWork = 2e10;     // point x segment steps of a link that fills the GPU (a few ms)
+constexpr double kSpanSerialCost = 5.0; // relative cost of a step on the span-serial path (MUFU-bound)
 
 // Snapshot of one link inside a batch.
 struct BatchLink {
@@ -35,7 +41,23 @@ struct BatchLink {
   ChannelTable ch{};    // = p.ch
   size_t tab_off = 0;   // offset of this link's table copy in d_tab
   size_t ws_off = 0;    // offset of its workspace in d_ws
+  bool heavy = false;   // fills the GPU on its own: serial branch
 };
+
+// Estimated work of one evaluation: quadrature points of the half list times
+// segment steps per point (every span's on the span-serial path).
+double link_work(const egn_link* l, const egn_opts* o) {
+  const double pts = (double)l->cnt.n_half * o->gl_order * o->gl_order;
+  double steps = 0.0;
+  const int nt = (int)l->type_si.size();
+  if (nt > egn::kMaxTypes) {
+    for (const egn_span& s : l->spans_si) steps += std::ceil(s.length_m * 1e-3 / o->dz_km);
+    steps *= kSpanSerialCost;
+  } else {
+    for (const egn_span& s : l->type_si) steps += std::ceil(s.length_m * 1e-3 / o->dz_km);
+  }
+  return pts * steps;
+}
 
 // Move q from [old, old + bytes) to the same offset after nb.
 template <class T>
@@ -102,28 +124,46 @@ struct egn_batch {
 
 namespace {
 
-// The whole evaluation of the batch: fork from `root`, one branch per link on
-// st[i mod kStreams], join back into `root`.
+// One link's chain on stream s.
+egn_status enqueue_link(egn_batch* b, size_t i, cudaStream_t s) {
+  const BatchLink& L = b->links[i];
+  Workspace ws = egn::carve_workspace((char*)b->d_ws.p + L.ws_off, L.n_ch, L.cnt, b->opts.precision);
+  EGN_CUDA(cudaMemsetAsync(ws.status, 0, sizeof(int), s));
+  EGN_CUDA(egn::launch_plan(L.ch, ws, s));
+  EGN_CUDA(integrate(L.p, b->opts.precision, ws.keys, L.cnt.n_isl, ws.h_idx, L.cnt.n_half, ws.e_idx, L.cnt.n_e,
+                     ws.f_idx, L.cnt.n_f, ws.terms, s, nullptr));
+  EGN_CUDA(egn::launch_assemble(L.ch, half_offsets(ws, L.n_ch), ws.keys, ws.h_idx, L.cnt.n_isl, ws.terms,
+                                b->opts.precision, b->opts.terms, b->eta() + b->off[i], b->pnli() + b->off[i], s));
+  EGN_CUDA(cudaMemcpyAsync(b->status() + i, ws.status, sizeof(int), cudaMemcpyDeviceToDevice, s));
+  return EGN_OK;
+}
+
+// The whole evaluation of the batch on `root`: first the light links as
+// concurrent branches (round-robin over up to kStreams streams, joined back),
+// then the heavy links one after the other, so heavy work never shares the GPU.
 egn_status enqueue(egn_batch* b, cudaStream_t root) {
-  const int ns = std::min<int>(kStreams, (int)b->links.size());
-  EGN_CUDA(cudaEventRecord(b->fork, root));
-  for (int j = 0; j < ns; ++j) EGN_CUDA(cudaStreamWaitEvent(b->st[j], b->fork, 0));
-  for (size_t i = 0; i < b->links.size(); ++i) {
-    const BatchLink& L = b->links[i];
-    cudaStream_t s = b->st[i % ns];
-    Workspace ws = egn::carve_workspace((char*)b->d_ws.p + L.ws_off, L.n_ch, L.cnt, b->opts.precision);
-    EGN_CUDA(cudaMemsetAsync(ws.status, 0, sizeof(int), s));
-    EGN_CUDA(egn::launch_plan(L.ch, ws, s));
-    EGN_CUDA(integrate(L.p, b->opts.precision, ws.keys, L.cnt.n_isl, ws.h_idx, L.cnt.n_half, ws.e_idx, L.cnt.n_e,
-                       ws.f_idx, L.cnt.n_f, ws.terms, s, nullptr));
-    EGN_CUDA(egn::launch_assemble(L.ch, half_offsets(ws, L.n_ch), ws.keys, ws.h_idx, L.cnt.n_isl, ws.terms,
-                                  b->opts.precision, b->opts.terms, b->eta() + b->off[i], b->pnli() + b->off[i], s));
-    EGN_CUDA(cudaMemcpyAsync(b->status() + i, ws.status, sizeof(int), cudaMemcpyDeviceToDevice, s));
+  int n_light = 0;
+  for (const BatchLink& L : b->links) n_light += !L.heavy;
+  if (n_light) {
+    const int ns = std::min<int>(kStreams, n_light);
+    EGN_CUDA(cudaEventRecord(b->fork, root));
+    for (int j = 0; j < ns; ++j) EGN_CUDA(cudaStreamWaitEvent(b->st[j], b->fork, 0));
+    int k = 0;
+    for (size_t i = 0; i < b->links.size(); ++i)
+      if (!b->links[i].heavy) {
+        egn_status s = enqueue_link(b, i, b->st[(k++) % ns]);
+        if (s != EGN_OK) return s;
+      }
+    for (int j = 0; j < ns; ++j) {
+      EGN_CUDA(cudaEventRecord(b->join[j], b->st[j]));
+      EGN_CUDA(cudaStreamWaitEvent(root, b->join[j], 0));
+    }
   }
-  for (int j = 0; j < ns; ++j) {
-    EGN_CUDA(cudaEventRecord(b->join[j], b->st[j]));
-    EGN_CUDA(cudaStreamWaitEvent(root, b->join[j], 0));
-  }
+  for (size_t i = 0; i < b->links.size(); ++i)
+    if (b->links[i].heavy) {
+      egn_status s = enqueue_link(b, i, root);
+      if (s != EGN_OK) return s;
+    }
   return EGN_OK;
 }
 
@@ -168,6 +208,7 @@ egn_status create(egn_link* const* links, int n_links, const egn_opts* o, bool c
     tab += align256(l->d_ch.bytes) + align256(l->d_seg.bytes) + align256(l->d_gl.bytes) +
            align256(l->types.size() > (size_t)egn::kMaxTypes ? l->types.size() * sizeof(egn::SpanType) : 0);
     L.ws_off = ws;
+    L.heavy = link_work(l, o) >= kHeavyWork;
     ws += align256(egn::workspace_bytes(l->n_ch, l->cnt, o->precision));
     b->links.push_back(L);
     b->off.push_back(b->off.back() + l->n_ch);
