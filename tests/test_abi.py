@@ -1,6 +1,7 @@
 """CPU checks of the C ABI: the library builds and loads, exports every entry
-point include/egn.h declares, and its host-only logic (argument validation,
-format moments, Gauss-Legendre nodes) is right.  No compute call needs a GPU here."""
+point the headers under include/ declare, and its host-only logic (argument
+validation, format moments, Gauss-Legendre nodes) is right.  No compute call
+needs a GPU here."""
 import os
 import re
 
@@ -20,15 +21,20 @@ def egn():
 
 
 def declared_functions():
-    src = open(os.path.join(ROOT, "include", "egn.h")).read()
-    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"\b(egn_[a-z_0-9]+)\s*\(", src)))
+    names = set()
+    inc = os.path.join(ROOT, "include")
+    for h in sorted(os.listdir(inc)):
+        if h.endswith(".h"):
+            src = re.sub(r"/\*.*?\*/", "", open(os.path.join(inc, h)).read(), flags=re.S)
+            names |= set(re.findall(r"\b(egn_[a-z_0-9]+)\s*\(", src))
+    return sorted(names)
 
 
 def test_header_declares_the_boundary():
     names = declared_functions()
     for must in ("egn_link_create", "egn_set_wdm", "egn_nli_eta", "egn_link_destroy", "egn_last_error",
-                 "egn_format_moments", "egn_nli_eta_device", "egn_workspace_size"):
+                 "egn_format_moments", "egn_nli_eta_device", "egn_workspace_size", "egn_batch_create",
+                 "egn_autotune", "egn_mlp_gemm", "egn_mlp_adam"):
         assert must in names
 
 
@@ -111,3 +117,30 @@ def test_last_error_is_informative(egn, workloads):
     with pytest.raises(egn.EgnError) as ei:
         egn.Link([_bad_span(workloads, length_m=0.0)])
     assert "length" in str(ei.value)
+
+
+def test_new_entry_points_validate_before_launching(egn):
+    """Bad shapes and null arguments are refused before any device work (no GPU here)."""
+    import ctypes as C
+    from paper_2412_11614_gb300 import mlp
+    L = mlp._lib()
+    fake = C.c_void_p(0x10000)  # never dereferenced: validation fails first
+    # k not a multiple of 64, n not a multiple of 32, splits without the FP32 epilogue, misaligned A
+    assert L.egn_mlp_gemm(64, 32, 96, 1, fake, fake, mlp.EPI_F32, None, None, fake, fake, None) == egn.EGN_E_INVALID_ARG
+    assert L.egn_mlp_gemm(64, 40, 64, 1, fake, fake, mlp.EPI_F32, None, None, fake, fake, None) == egn.EGN_E_INVALID_ARG
+    assert L.egn_mlp_gemm(64, 32, 128, 2, fake, fake, mlp.EPI_BIAS, fake, None, fake, fake, None) == egn.EGN_E_INVALID_ARG
+    assert L.egn_mlp_gemm(64, 32, 64, 1, C.c_void_p(0x10004), fake, mlp.EPI_F32, None, None, fake, fake,
+                          None) == egn.EGN_E_INVALID_ARG
+    assert L.egn_mlp_gemm(64, 32, 64, 1, fake, fake, mlp.EPI_RELU_GRAD, None, None, fake, fake, None) == egn.EGN_E_INVALID_ARG
+    assert L.egn_mlp_adam(None, None, None, None, 4, 1e-3, 0.9, 0.999, 1e-8, 1, None, None, 1, 4, None) == egn.EGN_E_INVALID_ARG
+    assert L.egn_mlp_head(fake, 10, 40, fake, fake, fake, None, None, None, None, None, None, None, None) == \
+        egn.EGN_E_INVALID_ARG  # hid not a multiple of 32
+    # batches and the autotuner
+    lib = egn.lib()
+    opts = egn.make_opts()
+    out = C.c_void_p()
+    assert lib.egn_batch_create((C.c_void_p * 1)(), 0, C.byref(opts), C.byref(out)) == egn.EGN_E_INVALID_ARG
+    res = egn.egn_tune_result()
+    cand = (C.c_double * 1)(1.0)
+    assert lib.egn_autotune(None, C.byref(opts), 0.01, cand, 1, 0.5, C.byref(res)) == egn.EGN_E_INVALID_ARG
+    assert "null" in lib.egn_last_error().decode()
