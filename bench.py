@@ -407,6 +407,61 @@ def run_surrogate(args):
     return 0
 
 
+def run_dz_sweep(args):
+    """The segment length trade-off of Sec. III-D on the GPU (Fig. 11 and 12
+    analogues).  Table I links (31 central channels, Cr 1.12, QPSK, 1 and 10
+    spans): the segment form at dz = 1..7 km in FP64 and FP32C and the Maclaurin
+    form, each against the FP64 integral form.  Table II (101 ch x 100 GBd, about
+    10 THz): the same against the FP64 segment form at dz = 0.125 km (the integral
+    form's quarter-period pieces number ~1e6 per point there).  Errors per channel
+    in dB, device ms per evaluation.  One JSON line per link."""
+    import numpy as np
+    import torch
+    from paper_2412_11614_gb300 import _build, egn, workloads as W
+    _build.build()
+    torch.cuda.set_device(0)
+    stream = torch.cuda.Stream()
+
+    def evaluate(ln, n_ch, reps, **kw):
+        opts = egn.make_opts(gl_order=16, stream=stream.cuda_stream, **kw)
+        ws = torch.empty(ln.workspace_size(opts), dtype=torch.uint8, device="cuda")
+        eta = torch.empty(n_ch, dtype=torch.float64, device="cuda")
+        pn = torch.empty(n_ch, dtype=torch.float64, device="cuda")
+        with torch.cuda.stream(stream):
+            if reps > 1:
+                ln.nli_eta_device(opts, ws, eta, pn)
+            t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            t0.record(stream)
+            for _ in range(reps):
+                ln.nli_eta_device(opts, ws, eta, pn)
+            t1.record(stream)
+        t1.synchronize()
+        return eta.cpu().numpy(), t0.elapsed_time(t1) / reps
+
+    cases = [("Table I, 31 ch, 1 x 100 km, Cr 1.12, QPSK", W.table1(n_spans=1, cr=1.12, fmt="QPSK", gl_order=16, n_ch=31),
+              dict(mu_form=egn.EGN_MU_INTEGRAL, precision=egn.EGN_PREC_FP64), "FP64 integral form"),
+             ("Table I, 31 ch, 10 x 100 km, Cr 1.12, QPSK", W.table1(n_spans=10, cr=1.12, fmt="QPSK", gl_order=16, n_ch=31),
+              dict(mu_form=egn.EGN_MU_INTEGRAL, precision=egn.EGN_PREC_FP64), "FP64 integral form"),
+             ("Table II, 101 ch x 100 GBd at 101 GHz, 1 x 100 km, QPSK", W.table2(fmt="QPSK", gl_order=16),
+              dict(dz_km=0.125, precision=egn.EGN_PREC_FP64), "FP64 segment form, dz 0.125 km")]
+    for name, wl, ref_kw, ref_name in cases:
+        ln = egn.link_from_workload(wl)
+        n = wl.n_ch
+        ref, ref_ms = evaluate(ln, n, 1, **ref_kw)
+        rdb = 10 * np.log10(ref)
+        rows = {}
+        for label, kw in ([(f"segment fp64 dz {d}", dict(dz_km=float(d), precision=egn.EGN_PREC_FP64)) for d in range(1, 8)] +
+                          [(f"segment fp32c dz {d}", dict(dz_km=float(d), precision=egn.EGN_PREC_FP32C)) for d in range(1, 8)] +
+                          [("maclaurin fp64", dict(mu_form=egn.EGN_MU_MACLAURIN, precision=egn.EGN_PREC_FP64))]):
+            eta, ms = evaluate(ln, n, 3, **kw)
+            err = 10 * np.log10(eta) - rdb
+            rows[label] = {"ms": ms, "mae_db": float(np.mean(np.abs(err))), "max_abs_db": float(np.max(np.abs(err)))}
+        print(json.dumps({"workload": name + ", 16 x 16 Gauss-Legendre, EGN", "reference": ref_name,
+                          "reference_ms": ref_ms, "results": rows}), flush=True)
+        ln.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -427,6 +482,7 @@ def main():
                     help="time a batch of small links: one by one vs one graph launch")
     ap.add_argument("--batch-links", type=int, default=24)
     ap.add_argument("--batch-random", action="store_true", help="the batch is seeded heterogeneous random links")
+    ap.add_argument("--dz-sweep", action="store_true", help="segment length trade-off on Table I and II links")
     ap.add_argument("--surrogate", action="store_true", help="train and evaluate the MLP surrogate")
     ap.add_argument("--sur-train", type=int, default=4096)
     ap.add_argument("--sur-test", type=int, default=256)
@@ -435,6 +491,8 @@ def main():
     args = ap.parse_args()
     if args.surrogate:
         return run_surrogate(args)
+    if args.dz_sweep:
+        return run_dz_sweep(args)
     if args.mu_compare:
         return run_mu_compare(args)
     if args.batch:
