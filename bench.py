@@ -391,6 +391,28 @@ def run_surrogate(args):
     e1.synchronize()
     inf_ms = e0.elapsed_time(e1) / reps
     flops = 2.0 * rows * (S.F_PAD * S.HIDDEN + (S.LAYERS - 1) * S.HIDDEN * S.HIDDEN + S.HIDDEN)
+    # the tensor-core GEMM on its own: 8192^3 BF16, FP32 accumulation, BF16 output
+    g = 8192
+    ga = torch.randn((g, g), device="cuda").to(torch.bfloat16)
+    gb = torch.randn((g, g), device="cuda").to(torch.bfloat16)
+    gout = torch.empty((g, g), dtype=torch.bfloat16, device="cuda")
+    gbias = torch.zeros(g, dtype=torch.float32, device="cuda")
+    S.K.gemm(ga, gb, gout, S.K.EPI_BIAS, bias=gbias, err=model.err)
+    e0.record()
+    for _ in range(5):
+        S.K.gemm(ga, gb, gout, S.K.EPI_BIAS, bias=gbias, err=model.err)
+    e1.record()
+    e1.synchronize()
+    model._check()
+    gemm_ms = e0.elapsed_time(e1) / 5
+    gemm_tflops = 2.0 * g ** 3 / (gemm_ms * 1e-3) / 1e12
+    peaks = {}
+    try:
+        with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")) as f:
+            peaks = json.load(f)
+    except (OSError, ValueError):
+        pass
+    bf16_peak = peaks.get("bf16_tflops")
     print(json.dumps({
         "workload": f"surrogate: {args.sur_train} training + {args.sur_test} held-out seeded 120-ch C+L links "
                     "(1-30 identical SSMF spans of 50-120 km, Cr 0.014-0.042, tilted rippled powers); labels from "
@@ -403,7 +425,11 @@ def run_surrogate(args):
         "heldout_mae_db": float(np.mean(np.abs(err))), "heldout_p99_abs_db": float(np.quantile(np.abs(err), 0.99)),
         "heldout_max_abs_db": float(np.max(np.abs(err))),
         "inference_rows": rows, "inference_ms": inf_ms, "inference_channel_evals_per_s": rows / (inf_ms * 1e-3),
-        "inference_tflops": flops / (inf_ms * 1e-3) / 1e12}), flush=True)
+        "inference_tflops": flops / (inf_ms * 1e-3) / 1e12,
+        "gemm_8192_ms": gemm_ms, "gemm_8192_tflops": gemm_tflops,
+        "gemm_roofline": {"bound": "tensor", "achieved": gemm_tflops, "peak": bf16_peak, "unit": "TFLOP/s",
+                          "frac": gemm_tflops / bf16_peak if bf16_peak else None,
+                          "peak_note": "measured cuBLAS bf16 burst" if bf16_peak else "no measured peak"}}), flush=True)
     return 0
 
 
