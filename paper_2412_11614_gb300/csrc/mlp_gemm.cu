@@ -2,19 +2,23 @@
 // MLP surrogate: D = A B^T, A [m][k] and B [n][k] row-major (k contiguous),
 // FP32 accumulation in tensor memory (TMEM), fused epilogues.
 //
-// One CTA of 128 threads computes a 128 x 256 tile of D:
+// Persistent warp-specialised kernel, one CTA of 192 threads per SM, tiles of
+// 128 x 256 of D taken round-robin:
 //   warp 0, one lane : TMA producer, 64-wide k blocks of A (128 x 64) and B
-//                      (256 x 64) into a 4-stage ring, 128-byte swizzle;
+//                      (256 x 64) into a 4-stage ring, 128-byte swizzle, running
+//                      ahead across tiles;
 //   warp 1, one lane : MMA issuer, 4 x tcgen05.mma (M 128, N 256, K 16) per k
-//                      block into one TMEM accumulator of 256 columns; each
-//                      stage is released by tcgen05.commit to its "empty"
-//                      barrier, the last commit marks the accumulator ready;
-//   warps 0-3        : epilogue, warp w reads TMEM lanes 32w .. 32w + 31 (rows)
-//                      with tcgen05.ld, 32 columns at a time.
-// blockIdx.z splits the k range (partial sums written to slab z, summed by
+//                      block into one of two TMEM accumulators (2 x 256 columns);
+//                      tcgen05.commit releases each stage and marks a finished
+//                      accumulator;
+//   warps 2-5        : epilogue, warp w reads TMEM lanes 32 (w mod 4) .. + 31
+//                      (rows) with tcgen05.ld, 32 columns at a time, then hands
+//                      the accumulator back: the next tile's MMAs overlap it.
+// The k range may be split (partial sums written to slab z, summed by
 // egn_mlp_reduce_splits in a fixed order).  Every mbarrier wait is bounded
-// (kWaitNs of wall time); a wait that runs out sets the error word, lets the
-// producer drain its own copies in flight, frees TMEM and returns.
+// (kWaitNs of wall time); a wait that runs out sets the error word and a shared
+// abort flag that stops every role, the producer drains its own copies in
+// flight, the MMA issuer waits for its MMAs, TMEM is freed and the CTA returns.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cudaTypedefs.h>
@@ -30,6 +34,7 @@ constexpr int BM = 128, BN = 256, BK = 64, STAGES = 4;
 constexpr int kStageA = BM * BK * 2;  // 16 KB
 constexpr int kStageB = BN * BK * 2;  // 32 KB
 constexpr int kSmem = STAGES * (kStageA + kStageB) + 1024 /* alignment */ + 256 /* barriers */;
+constexpr int kGemmThreads = 192;  // warp 0 TMA, warp 1 MMA, warps 2-5 epilogue
 constexpr unsigned long long kWaitNs = 2000000000ull;  // 2 s
 
 // Instruction descriptor of tcgen05.mma kind::f16: D FP32 (bits 4-5 = 1), A and B
@@ -118,10 +123,45 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
   for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
 }
 
+__device__ __forceinline__ void mbar_arrive(uint64_t* b) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(b)) : "memory");
+}
+
+// Epilogue of one accumulator row chunk: 32 columns n .. n + 31 of row `row`.
 template <int EPI>
-__global__ void __launch_bounds__(128, 1)
+__device__ __forceinline__ void store_chunk(const float (&v)[32], int row, int n, int M, int N, int z,
+                                            const float* __restrict__ bias, const __nv_bfloat16* __restrict__ aux,
+                                            void* __restrict__ out) {
+  if (EPI == EGN_MLP_EPI_F32) {
+    float* o = (float*)out + (size_t)z * (size_t)M * N + (size_t)row * N + n;
+#pragma unroll
+    for (int j = 0; j < 32; j += 4) *reinterpret_cast<float4*>(o + j) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
+  } else {
+    __nv_bfloat16* o = (__nv_bfloat16*)out + (size_t)row * N + n;
+    __align__(16) __nv_bfloat16 h[32];
+    if (EPI == EGN_MLP_EPI_BIAS_RELU) {
+#pragma unroll
+      for (int j = 0; j < 32; ++j) h[j] = __float2bfloat16_rn(fmaxf(v[j] + bias[n + j], 0.0f));
+    } else if (EPI == EGN_MLP_EPI_BIAS) {
+#pragma unroll
+      for (int j = 0; j < 32; ++j) h[j] = __float2bfloat16_rn(v[j] + bias[n + j]);
+    } else {  // EGN_MLP_EPI_RELU_GRAD: the gradient passes where the layer's output was positive
+      const __nv_bfloat16* a = aux + (size_t)row * N + n;
+#pragma unroll
+      for (int j = 0; j < 32; ++j) h[j] = __float2bfloat16_rn(__bfloat162float(a[j]) > 0.0f ? v[j] : 0.0f);
+    }
+#pragma unroll
+    for (int j = 0; j < 32; j += 8) *reinterpret_cast<uint4*>(o + j) = *reinterpret_cast<const uint4*>(h + j);
+  }
+}
+
+// Persistent: CTA b takes tiles b, b + gridDim.x, ... (m fastest, then n, then the
+// k split).  Two TMEM accumulators (2 x 256 columns): the MMA issuer fills one
+// while the epilogue warps drain the other.
+template <int EPI>
+__global__ void __launch_bounds__(kGemmThreads, 1)
     gemm_bf16_kernel(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtensorMap tb, int M, int N,
-                     int kb_per_split, int kb_total, const float* __restrict__ bias,
+                     int kb_per_split, int kb_total, int splits, const float* __restrict__ bias,
                      const __nv_bfloat16* __restrict__ aux, void* __restrict__ out, int* __restrict__ err) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -129,25 +169,46 @@ __global__ void __launch_bounds__(128, 1)
   uint8_t* sB = smem + STAGES * kStageA;
   uint64_t* full = (uint64_t*)(sB + STAGES * kStageB);
   uint64_t* empty = full + STAGES;
-  uint64_t* accum = empty + STAGES;
-  uint32_t* tslot = (uint32_t*)(accum + 1);
+  uint64_t* accf = empty + STAGES;  // [2] accumulator b holds a finished tile
+  uint64_t* acce = accf + 2;        // [2] accumulator b has been read out
+  uint64_t* drain = acce + 2;       // the MMA issuer's last commit
+  uint32_t* tslot = (uint32_t*)(drain + 1);
+  volatile int* abort_flag = (volatile int*)(tslot + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
-  const int kb0 = blockIdx.z * kb_per_split;
-  const int nk = min(kb_per_split, kb_total - kb0);
+  const int tm = (M + BM - 1) / BM, tn = (N + BN - 1) / BN;
+  const long long total = (long long)tm * tn * splits;
+  auto decode = [&](long long t, int& m0, int& n0, int& z, int& kb0, int& nk) {
+    const int mi = (int)(t % tm);
+    const long long r = t / tm;
+    m0 = mi * BM;
+    n0 = (int)(r % tn) * BN;
+    z = (int)(r / tn);
+    kb0 = z * kb_per_split;
+    nk = min(kb_per_split, kb_total - kb0);
+  };
+  auto fail = [&](int code) {
+    *abort_flag = 1;
+    atomicExch(err, code);
+  };
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
     }
-    mbar_init(accum, 1);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&accf[b], 1);
+      mbar_init(&acce[b], kGemmThreads / 32 - 2);  // one arrival per epilogue warp
+    }
+    mbar_init(drain, 1);
+    *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncwarp();  // the .sync.aligned tcgen05 instructions need the whole warp converged
   if (warp == 0) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)), "r"(BN));
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
+                 "r"(2 * BN));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   fence_before();
@@ -155,77 +216,83 @@ __global__ void __launch_bounds__(128, 1)
   fence_after();
   const uint32_t taddr = *tslot;
 
-  if (warp == 0 && lane == 0) {
-    // producer
-    int issued = 0;
-    bool ok = true;
-    for (int kb = 0; kb < nk; ++kb) {
-      const int s = kb % STAGES;
-      const uint32_t ph = (kb / STAGES) & 1;
-      if (kb >= STAGES && !mbar_wait(&empty[s], ph ^ 1)) { ok = false; break; }
-      mbar_expect_tx(&full[s], kStageA + kStageB);
-      tma_load_2d(sA + s * kStageA, &ta, &full[s], (kb0 + kb) * BK, m0);
-      tma_load_2d(sB + s * kStageB, &tb, &full[s], (kb0 + kb) * BK, n0);
-      ++issued;
-    }
-    if (!ok) atomicExch(err, 1);
-    // drain: every copy this thread issued has landed before the CTA may exit
-    for (int kb = max(0, issued - STAGES); kb < issued; ++kb) mbar_wait(&full[kb % STAGES], (kb / STAGES) & 1);
-  } else if (warp == 1 && lane == 0) {
-    // MMA issuer
-    bool ok = true;
-    for (int kb = 0; kb < nk; ++kb) {
-      const int s = kb % STAGES;
-      const uint32_t ph = (kb / STAGES) & 1;
-      if (!mbar_wait(&full[s], ph)) { ok = false; break; }
-      fence_after();
-      const uint64_t ad = sdesc_sw128(sA + s * kStageA), bd = sdesc_sw128(sB + s * kStageB);
-#pragma unroll
-      for (int k = 0; k < BK / 16; ++k) umma_bf16(taddr, ad + 2 * k, bd + 2 * k, (kb | k) != 0);  // +32 bytes per k step
-      umma_commit(&empty[s]);
-    }
-    if (!ok) atomicExch(err, 2);
-    umma_commit(accum);  // arrives when every MMA issued above has completed
-  }
-  __syncwarp();
-
-  // epilogue
-  const bool ready = mbar_wait(accum, 0);
-  if (!ready) atomicExch(err, 3);
-  __syncwarp();  // lanes leave the wait loop independently; tcgen05.ld is .sync.aligned
-  fence_after();
-  const int row = m0 + warp * 32 + lane;
-  const bool store = ready && nk > 0 && row < M;
-  for (int c = 0; c < BN; c += 32) {
-    float v[32];
-    tmem_ld32(taddr + ((uint32_t)(warp * 32) << 16) + (uint32_t)c, v);
-    const int n = n0 + c;
-    if (!store || n >= N) continue;
-    if (EPI == EGN_MLP_EPI_F32) {
-      float* o = (float*)out + (size_t)blockIdx.z * (size_t)M * N + (size_t)row * N + n;
-#pragma unroll
-      for (int j = 0; j < 32; j += 4) *reinterpret_cast<float4*>(o + j) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
-    } else {
-      __nv_bfloat16* o = (__nv_bfloat16*)out + (size_t)row * N + n;
-      __align__(16) __nv_bfloat16 h[32];
-      if (EPI == EGN_MLP_EPI_BIAS_RELU) {
-#pragma unroll
-        for (int j = 0; j < 32; ++j) h[j] = __float2bfloat16_rn(fmaxf(v[j] + bias[n + j], 0.0f));
-      } else if (EPI == EGN_MLP_EPI_BIAS) {
-#pragma unroll
-        for (int j = 0; j < 32; ++j) h[j] = __float2bfloat16_rn(v[j] + bias[n + j]);
-      } else {  // EGN_MLP_EPI_RELU_GRAD: the gradient passes where the layer's output was positive
-        const __nv_bfloat16* a = aux + (size_t)row * N + n;
-#pragma unroll
-        for (int j = 0; j < 32; ++j) h[j] = __float2bfloat16_rn(__bfloat162float(a[j]) > 0.0f ? v[j] : 0.0f);
+  if (warp == 0) {
+    if (lane == 0) {  // TMA producer: k blocks of every tile through the ring
+      long long g = 0;
+      for (long long t = blockIdx.x; t < total && !*abort_flag; t += gridDim.x) {
+        int m0, n0, z, kb0, nk;
+        decode(t, m0, n0, z, kb0, nk);
+        bool ok = true;
+        for (int kb = 0; kb < nk; ++kb, ++g) {
+          const int s = (int)(g % STAGES);
+          const uint32_t ph = (uint32_t)((g / STAGES) & 1);
+          if (g >= STAGES && !mbar_wait(&empty[s], ph ^ 1)) { ok = false; break; }
+          mbar_expect_tx(&full[s], kStageA + kStageB);
+          tma_load_2d(sA + s * kStageA, &ta, &full[s], (kb0 + kb) * BK, m0);
+          tma_load_2d(sB + s * kStageB, &tb, &full[s], (kb0 + kb) * BK, n0);
+        }
+        if (!ok) { fail(1); break; }
       }
+      // every copy issued has landed before the CTA may exit
+      for (long long gg = g > STAGES ? g - STAGES : 0; gg < g; ++gg) mbar_wait(&full[gg % STAGES], (gg / STAGES) & 1);
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {  // MMA issuer
+      long long g = 0;
+      int i = 0;
+      for (long long t = blockIdx.x; t < total && !*abort_flag; t += gridDim.x, ++i) {
+        int m0, n0, z, kb0, nk;
+        decode(t, m0, n0, z, kb0, nk);
+        const int b = i & 1;
+        if (i >= 2 && !mbar_wait(&acce[b], ((i >> 1) & 1) ^ 1)) { fail(2); break; }
+        fence_after();
+        const uint32_t acc = taddr + (uint32_t)(b * BN);
+        bool ok = true;
+        for (int kb = 0; kb < nk; ++kb, ++g) {
+          const int s = (int)(g % STAGES);
+          const uint32_t ph = (uint32_t)((g / STAGES) & 1);
+          if (!mbar_wait(&full[s], ph)) { ok = false; break; }
+          fence_after();
+          const uint64_t ad = sdesc_sw128(sA + s * kStageA), bd = sdesc_sw128(sB + s * kStageB);
 #pragma unroll
-      for (int j = 0; j < 32; j += 8) *reinterpret_cast<uint4*>(o + j) = *reinterpret_cast<const uint4*>(h + j);
+          for (int k = 0; k < BK / 16; ++k) umma_bf16(acc, ad + 2 * k, bd + 2 * k, (kb | k) != 0);  // +32 B per k step
+          umma_commit(&empty[s]);
+        }
+        if (!ok) { fail(2); break; }
+        umma_commit(&accf[b]);
+      }
+      umma_commit(drain);  // arrives when every MMA issued above has completed
+      mbar_wait(drain, 0);
+    }
+  } else {  // epilogue warps 2..5: warp w reads TMEM lanes 32 (w mod 4) .. + 31
+    const int grp = warp & 3;
+    int i = 0;
+    for (long long t = blockIdx.x; t < total; t += gridDim.x, ++i) {
+      if (*abort_flag) break;
+      int m0, n0, z, kb0, nk;
+      decode(t, m0, n0, z, kb0, nk);
+      const int b = i & 1;
+      const bool ready = __all_sync(0xffffffffu, mbar_wait(&accf[b], (i >> 1) & 1));
+      if (!ready) {
+        if (lane == 0) fail(3);
+        break;
+      }
+      fence_after();
+      const int row = m0 + grp * 32 + lane;
+      for (int c = 0; c < BN; c += 32) {
+        float v[32];
+        tmem_ld32(taddr + ((uint32_t)(grp * 32) << 16) + (uint32_t)(b * BN + c), v);
+        if (row < M && n0 + c < N) store_chunk<EPI>(v, row, n0 + c, M, N, z, bias, aux, out);
+      }
+      fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&acce[b]);
     }
   }
   fence_before();
   __syncthreads();
-  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(BN));
+  __syncwarp();  // the producer lane rejoins its warp before the .sync.aligned dealloc
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(2 * BN));
 }
 
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
@@ -264,8 +331,13 @@ egn_status launch(const CUtensorMap& ta, const CUtensorMap& tb, int m, int n, in
     EGN_CUDA(cudaFuncSetAttribute(gemm_bf16_kernel<EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem));
     attr = true;
   }
-  dim3 grid((m + BM - 1) / BM, (n + BN - 1) / BN, splits);
-  gemm_bf16_kernel<EPI><<<grid, 128, kSmem, st>>>(ta, tb, m, n, kb_per, kb, bias, (const __nv_bfloat16*)aux, out, err);
+  int dev = 0, sms = 0;
+  EGN_CUDA(cudaGetDevice(&dev));
+  EGN_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  const long long tiles = (long long)((m + BM - 1) / BM) * ((n + BN - 1) / BN) * splits;
+  const unsigned grid = (unsigned)(tiles < sms ? tiles : sms);  // persistent: one CTA per SM
+  gemm_bf16_kernel<EPI><<<grid, kGemmThreads, kSmem, st>>>(ta, tb, m, n, kb_per, kb, splits, bias,
+                                                            (const __nv_bfloat16*)aux, out, err);
   EGN_CUDA(cudaGetLastError());
   return EGN_OK;
 }
