@@ -330,6 +330,41 @@ def run_batch_compare(args):
     return 0
 
 
+def gemm_roofline(g: int, reps: int) -> dict:
+    """The surrogate's tensor-core GEMM on its own: g^3 BF16 (random inputs),
+    FP32 accumulation, BF16 output with a bias, CUDA-event time per launch
+    against the measured BF16 peak."""
+    import torch
+    from paper_2412_11614_gb300 import mlp
+    err = torch.zeros(1, dtype=torch.int32, device="cuda")
+    ga = torch.randn((g, g), device="cuda").to(torch.bfloat16)
+    gb = torch.randn((g, g), device="cuda").to(torch.bfloat16)
+    gout = torch.empty((g, g), dtype=torch.bfloat16, device="cuda")
+    gbias = torch.zeros(g, dtype=torch.float32, device="cuda")
+    for _ in range(3):
+        mlp.gemm(ga, gb, gout, mlp.EPI_BIAS, bias=gbias, err=err)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        mlp.gemm(ga, gb, gout, mlp.EPI_BIAS, bias=gbias, err=err)
+    e1.record()
+    e1.synchronize()
+    if int(err.item()):
+        raise RuntimeError("a bounded wait of the GEMM ran out")
+    ms = e0.elapsed_time(e1) / reps
+    tflops = 2.0 * g ** 3 / (ms * 1e-3) / 1e12
+    peaks = {}
+    try:
+        with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")) as f:
+            peaks = json.load(f)
+    except (OSError, ValueError):
+        pass
+    peak = peaks.get("bf16_tflops")
+    return {"m_n_k": g, "ms": ms, "roofline": {"bound": "tensor", "achieved": tflops, "peak": peak, "unit": "TFLOP/s",
+                                              "frac": tflops / peak if peak else None,
+                                              "peak_note": "measured cuBLAS bf16 burst" if peak else "no measured peak"}}
+
+
 def run_surrogate(args):
     """MLP surrogate end to end: labels of seeded 120-channel links from the
     FP32C integrator (batches of links), training on the tensor-core kernels,
@@ -391,28 +426,7 @@ def run_surrogate(args):
     e1.synchronize()
     inf_ms = e0.elapsed_time(e1) / reps
     flops = 2.0 * rows * (S.F_PAD * S.HIDDEN + (S.LAYERS - 1) * S.HIDDEN * S.HIDDEN + S.HIDDEN)
-    # the tensor-core GEMM on its own: 8192^3 BF16, FP32 accumulation, BF16 output
-    g = 8192
-    ga = torch.randn((g, g), device="cuda").to(torch.bfloat16)
-    gb = torch.randn((g, g), device="cuda").to(torch.bfloat16)
-    gout = torch.empty((g, g), dtype=torch.bfloat16, device="cuda")
-    gbias = torch.zeros(g, dtype=torch.float32, device="cuda")
-    S.K.gemm(ga, gb, gout, S.K.EPI_BIAS, bias=gbias, err=model.err)
-    e0.record()
-    for _ in range(5):
-        S.K.gemm(ga, gb, gout, S.K.EPI_BIAS, bias=gbias, err=model.err)
-    e1.record()
-    e1.synchronize()
-    model._check()
-    gemm_ms = e0.elapsed_time(e1) / 5
-    gemm_tflops = 2.0 * g ** 3 / (gemm_ms * 1e-3) / 1e12
-    peaks = {}
-    try:
-        with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")) as f:
-            peaks = json.load(f)
-    except (OSError, ValueError):
-        pass
-    bf16_peak = peaks.get("bf16_tflops")
+    gemm = gemm_roofline(8192, 5)
     print(json.dumps({
         "workload": f"surrogate: {args.sur_train} training + {args.sur_test} held-out seeded 120-ch C+L links "
                     "(1-30 identical SSMF spans of 50-120 km, Cr 0.014-0.042, tilted rippled powers); labels from "
@@ -426,10 +440,7 @@ def run_surrogate(args):
         "heldout_max_abs_db": float(np.max(np.abs(err))),
         "inference_rows": rows, "inference_ms": inf_ms, "inference_channel_evals_per_s": rows / (inf_ms * 1e-3),
         "inference_tflops": flops / (inf_ms * 1e-3) / 1e12,
-        "gemm_8192_ms": gemm_ms, "gemm_8192_tflops": gemm_tflops,
-        "gemm_roofline": {"bound": "tensor", "achieved": gemm_tflops, "peak": bf16_peak, "unit": "TFLOP/s",
-                          "frac": gemm_tflops / bf16_peak if bf16_peak else None,
-                          "peak_note": "measured cuBLAS bf16 burst" if bf16_peak else "no measured peak"}}), flush=True)
+        "gemm_8192": gemm}), flush=True)
     return 0
 
 
@@ -509,6 +520,7 @@ def main():
     ap.add_argument("--batch-links", type=int, default=24)
     ap.add_argument("--batch-random", action="store_true", help="the batch is seeded heterogeneous random links")
     ap.add_argument("--dz-sweep", action="store_true", help="segment length trade-off on Table I and II links")
+    ap.add_argument("--gemm", type=int, default=0, metavar="G", help="time the surrogate's G^3 tensor-core GEMM")
     ap.add_argument("--surrogate", action="store_true", help="train and evaluate the MLP surrogate")
     ap.add_argument("--sur-train", type=int, default=4096)
     ap.add_argument("--sur-test", type=int, default=256)
@@ -519,6 +531,13 @@ def main():
         return run_surrogate(args)
     if args.dz_sweep:
         return run_dz_sweep(args)
+    if args.gemm:
+        import torch
+        from paper_2412_11614_gb300 import _build
+        _build.build()
+        torch.cuda.set_device(0)
+        print(json.dumps(gemm_roofline(args.gemm, args.steps)), flush=True)
+        return 0
     if args.mu_compare:
         return run_mu_compare(args)
     if args.batch:
