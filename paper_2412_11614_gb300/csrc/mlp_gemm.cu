@@ -3,7 +3,7 @@
 // FP32 accumulation in tensor memory (TMEM), fused epilogues.
 //
 // Persistent warp-specialised kernel, one CTA of 192 threads per SM, tiles of
-// 128 x 256 of D taken round-robin:
+// 128 x 256 of D taken round-robin in groups of 8 m-tiles by every n-tile:
 //   warp 0, one lane : TMA producer, 64-wide k blocks of A (128 x 64) and B
 //                      (256 x 64) into a 4-stage ring, 128-byte swizzle, running
 //                      ahead across tiles;
@@ -35,6 +35,7 @@ constexpr int kStageA = BM * BK * 2;  // 16 KB
 constexpr int kStageB = BN * BK * 2;  // 32 KB
 constexpr int kSmem = STAGES * (kStageA + kStageB) + 1024 /* alignment */ + 256 /* barriers */;
 constexpr int kGemmThreads = 192;  // warp 0 TMA, warp 1 MMA, warps 2-5 epilogue
+constexpr int kGroupM = 8;         // m-tiles per group of the tile order
 constexpr unsigned long long kWaitNs = 2000000000ull;  // 2 s
 
 // Instruction descriptor of tcgen05.mma kind::f16: D FP32 (bits 4-5 = 1), A and B
@@ -155,8 +156,7 @@ __device__ __forceinline__ void store_chunk(const float (&v)[32], int row, int n
   }
 }
 
-// Persistent: CTA b takes tiles b, b + gridDim.x, ... (m fastest, then n, then the
-// k split).  Two TMEM accumulators (2 x 256 columns): the MMA issuer fills one
+// Persistent: CTA b takes tiles b, b + gridDim.x, ... (grouped order, see decode).  Two TMEM accumulators (2 x 256 columns): the MMA issuer fills one
 // while the epilogue warps drain the other.
 template <int EPI>
 __global__ void __launch_bounds__(kGemmThreads, 1)
@@ -178,12 +178,16 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int tm = (M + BM - 1) / BM, tn = (N + BN - 1) / BN;
   const long long total = (long long)tm * tn * splits;
+  // tile t -> (m, n, split): within a split, groups of kGroupM m-tiles by every
+  // n-tile, m fastest inside a group, so one wave's A and B blocks fit in L2 together
   auto decode = [&](long long t, int& m0, int& n0, int& z, int& kb0, int& nk) {
-    const int mi = (int)(t % tm);
-    const long long r = t / tm;
-    m0 = mi * BM;
-    n0 = (int)(r % tn) * BN;
-    z = (int)(r / tn);
+    const long long per = (long long)tm * tn;
+    z = (int)(t / per);
+    const int r = (int)(t - (long long)z * per);
+    const int g = r / (kGroupM * tn), first = g * kGroupM, gm = min(kGroupM, tm - first);
+    const int l = r - g * kGroupM * tn;
+    m0 = (first + l % gm) * BM;
+    n0 = (l / gm) * BN;
     kb0 = z * kb_per_split;
     nk = min(kb_per_split, kb_total - kb0);
   };
