@@ -146,6 +146,35 @@ def test_fp64_config_cl_sampled_islands(egn, oracle_mod, workloads):
     assert np.allclose(got, want, rtol=1e-8, atol=1e-300)
 
 
+@pytest.mark.parametrize("prec", ["fp64", "fp32c"])
+def test_200_channel_link_sampled_islands(egn, oracle_mod, workloads, prec):
+    """The largest comb of the seeded random links: 200 channels x 32 GBd on a 50 GHz
+    grid (10 THz), 6 x 80 km; per-island terms of a seeded sample (all kinds) against
+    the oracle one by one, and the planned list's size against the island count."""
+    wl = workloads.config_small(n_ch=200, gl_order=12, n_spans=6)
+    base = wl.centre_hz[100]
+    wl.centre_hz = [base + (k - 99.5) * 50e9 for k in range(200)]
+    wl.symbol_rate_baud = [32e9] * 200
+    rng = np.random.default_rng(3)
+    wl.formats = [("QPSK", "16QAM", "64QAM", "GAUSS")[i] for i in rng.integers(0, 4, 200)]
+    ln, pb = _pair(egn, oracle_mod, wl, gl=12)
+    plan = ln.plan_islands()
+    assert len(plan) == ln.island_count()[0] and len(plan) > 4_000_000
+    pick = np.concatenate([rng.choice(len(plan), 30, replace=False),
+                           np.flatnonzero(plan[:, 1] == plan[:, 3])[:: 20000],
+                           np.flatnonzero(plan[:, 1] == plan[:, 2])[:: 20000],
+                           np.flatnonzero((plan[:, 1] == plan[:, 2]) & (plan[:, 2] == plan[:, 3]))[:: 50]])
+    isl = plan[pick]
+    p = egn.EGN_PREC_FP64 if prec == "fp64" else egn.EGN_PREC_FP32C
+    got = ln.island_terms(egn.make_opts(gl_order=12, precision=p), isl)
+    want = np.array([pb.island_terms(*row) for row in isl])
+    if prec == "fp64":
+        assert np.allclose(got, want, rtol=1e-8, atol=1e-300)
+    else:
+        err = np.abs(got - want)
+        assert np.all(err <= 3e-4 * np.abs(want) + 3e-5 * np.abs(want[:, :1]))
+
+
 def test_device_api_matches_host_api(egn, workloads):
     import torch
     wl = workloads.config_small(gl_order=16)
