@@ -379,16 +379,14 @@ def run_surrogate(args):
     train_w = [W.surrogate_link(i + 1) for i in range(args.sur_train)]
     test_w = [W.surrogate_link(1000001 + i) for i in range(args.sur_test)]
     t0 = time.perf_counter()
-    lab = []
-    cached = bool(args.sur_labels and os.path.exists(args.sur_labels))
-    if cached:
-        z = np.load(args.sur_labels)
-        lab = [z["eta_db"][i] for i in range(len(train_w) + len(test_w))]
+    seeds = [i + 1 for i in range(args.sur_train)] + [1000001 + i for i in range(args.sur_test)]
+    cached = bool(args.sur_labels and os.path.exists(os.path.join(args.sur_labels, "index.json")))
+    if args.sur_labels:  # sharded label files with a resume index
+        lab = list(S.generate_labels(args.sur_labels, seeds, opts))
     else:
+        lab = []
         for i in range(0, len(train_w) + len(test_w), 64):
             lab += S.labels((train_w + test_w)[i:i + 64], opts)
-        if args.sur_labels:
-            np.savez(args.sur_labels, eta_db=np.array(lab))
     label_s = time.perf_counter() - t0
     xtr = np.concatenate([S.features(w) for w in train_w])
     ytr = np.concatenate(lab[:len(train_w)])
@@ -396,18 +394,10 @@ def run_surrogate(args):
     yte = np.concatenate(lab[len(train_w):])
     model = S.Surrogate(seed=0)
     model.fit_normalisation(xtr, ytr)
-    rng = np.random.default_rng(0)
     bs = 8192
     steps = args.sur_steps
     t0 = time.perf_counter()
-    losses = []
-    for step in range(steps):
-        if step % max(1, len(xtr) // bs) == 0:
-            perm = rng.permutation(len(xtr))
-        j = (step % max(1, len(xtr) // bs)) * bs
-        idx = perm[j:j + bs]
-        lr = 1e-5 + 0.5 * (2e-3 - 1e-5) * (1 + math.cos(math.pi * step / steps))
-        losses.append(model.train_step(xtr[idx], ytr[idx], lr))
+    losses = S.train(model, xtr, ytr, steps, batch_rows=bs, seed=0)
     torch.cuda.synchronize()
     train_s = time.perf_counter() - t0
     pred = model.predict_rows(xte)
@@ -431,7 +421,7 @@ def run_surrogate(args):
         "workload": f"surrogate: {args.sur_train} training + {args.sur_test} held-out seeded 120-ch C+L links "
                     "(1-30 identical SSMF spans of 50-120 km, Cr 0.014-0.042, tilted rippled powers); labels from "
                     "the FP32C integrator, 32 x 32 GL, dz 1 km",
-        "labels": "read from the cache file" if cached else "computed by the integrator in this run",
+        "labels": "read (or resumed) from the label directory" if cached else "computed by the integrator in this run",
         "label_seconds": None if cached else label_s,
         "label_channel_evals_per_s": None if cached else 120 * (args.sur_train + args.sur_test) / label_s,
         "train_steps": steps, "batch_rows": bs, "train_seconds": train_s,
@@ -525,7 +515,8 @@ def main():
     ap.add_argument("--sur-train", type=int, default=4096)
     ap.add_argument("--sur-test", type=int, default=256)
     ap.add_argument("--sur-steps", type=int, default=2000)
-    ap.add_argument("--sur-labels", default=None, help="npz cache of the integrator's labels (read if present)")
+    ap.add_argument("--sur-labels", default=None,
+                    help="directory of sharded label files with a resume index (labels computed only where missing)")
     args = ap.parse_args()
     if args.surrogate:
         return run_surrogate(args)

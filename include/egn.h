@@ -42,6 +42,18 @@
  * Errors: every entry point returns an egn_status; nothing is thrown across the
  * ABI.  egn_last_error() returns a thread-local message for the last failure.
  * A link is not thread-safe: calls on one link must be serialised by the caller.
+ * A failed call leaves the link usable: a failed allocation keeps the previous
+ * buffer, tables whose upload failed are rebuilt by the next call, and a failed
+ * egn_set_wdm leaves the link in the "no WDM set" state (EGN_E_STATE until the
+ * next successful egn_set_wdm).
+ *
+ * Fault injection (testing the error paths without a device fault): while the
+ * environment variable EGN_FAULT holds a comma-separated subset of
+ *   alloc   every device and pinned host allocation fails    -> EGN_E_NOMEM
+ *   h2d     every host-to-device copy fails                  -> EGN_E_CUDA
+ *   launch  every evaluation's launch sequence fails          -> EGN_E_CUDA
+ * the failure is returned before anything reaches the device.  The variable is
+ * read on every call.
  */
 #ifndef EGN_H
 #define EGN_H
@@ -113,6 +125,9 @@ enum { EGN_FMT_GAUSS = 0, EGN_FMT_QPSK = 1, EGN_FMT_16QAM = 2, EGN_FMT_64QAM = 3
  *               arithmetic, compensated island sums.
  *   terms       EGN_TERMS_GN (D only) or EGN_TERMS_EGN (D + E, F, G, H).
  *   timeout_ms  host-side wait limit for egn_nli_eta (0 = none) -> EGN_E_TIMEOUT.
+ *               The queued work then still runs to completion on `stream`; the
+ *               outputs are not written; the link stays valid and a later call
+ *               on the same stream is ordered after the timed-out work.
  *   stream      cudaStream_t to launch on (NULL = the legacy default stream). */
 typedef struct {
     int gl_order;

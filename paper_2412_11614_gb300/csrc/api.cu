@@ -7,6 +7,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <thread>
@@ -26,6 +27,23 @@ egn_status fail(egn_status s, const char* fmt, ...) {
   va_end(ap);
   g_last_error = buf;
   return s;
+}
+
+unsigned fault_mask() {
+  const char* v = std::getenv("EGN_FAULT");
+  if (!v || !*v) return 0;
+  unsigned m = 0;
+  const std::string s(v);
+  for (size_t i = 0; i <= s.size();) {
+    size_t j = s.find(',', i);
+    if (j == std::string::npos) j = s.size();
+    const std::string w = s.substr(i, j - i);
+    if (w == "alloc") m |= kFaultAlloc;
+    else if (w == "h2d") m |= kFaultH2D;
+    else if (w == "launch") m |= kFaultLaunch;
+    i = j + 1;
+  }
+  return m;
 }
 
 }  // namespace egn_host
@@ -178,6 +196,7 @@ egn_status check_opts(const egn_link* l, const egn_opts* o) {
 // (Re)build the segment and Gauss-Legendre tables for these options.
 egn_status ensure_tables(egn_link* l, const egn_opts* o) {
   if (l->tab_dz != o->dz_km) {
+    l->tab_dz = -1.0;  // invalid until every table is uploaded
     const int nt = (int)l->type_si.size();
     std::vector<Span> sp(nt);
     std::vector<int> Ks(nt);
@@ -187,7 +206,7 @@ egn_status ensure_tables(egn_link* l, const egn_opts* o) {
       Ks[t] = std::max(1, (int)std::ceil(sp[t].L / o->dz_km));
       bytes += align256(Ks[t] * sizeof(double)) * 2 + align256(Ks[t] * sizeof(float)) * 2;
     }
-    EGN_CUDA(l->d_seg.ensure(bytes));
+    EGN_ALLOC(l->d_seg.ensure(bytes));
     // every type's tables staged on the host and copied in one transfer
     std::vector<char> host(bytes, 0);
     char* base = (char*)l->d_seg.p;
@@ -225,10 +244,10 @@ egn_status ensure_tables(egn_link* l, const egn_opts* o) {
       ty.seg.ck_f = (const float*)(base + ((char*)cf - host.data()));
       off += align256(K * sizeof(double)) * 2 + align256(K * sizeof(float)) * 2;
     }
-    EGN_CUDA(cudaMemcpy(base, host.data(), bytes, cudaMemcpyHostToDevice));
+    EGN_CUDA(h2d(base, host.data(), bytes));
     if (nt > kMaxTypes) {
-      EGN_CUDA(l->d_types.ensure(nt * sizeof(SpanType)));
-      EGN_CUDA(cudaMemcpy(l->d_types.p, l->types.data(), nt * sizeof(SpanType), cudaMemcpyHostToDevice));
+      EGN_ALLOC(l->d_types.ensure(nt * sizeof(SpanType)));
+      EGN_CUDA(h2d(l->d_types.p, l->types.data(), nt * sizeof(SpanType)));
     }
     l->seg = l->types[0].seg;
     l->K = l->types[0].seg.K;
@@ -236,6 +255,7 @@ egn_status ensure_tables(egn_link* l, const egn_opts* o) {
     l->tab_dz = o->dz_km;
   }
   if (l->tab_gl != o->gl_order) {
+    l->tab_gl = -1;
     int n = o->gl_order;
     std::vector<char> host;
     size_t off[4][7] = {};
@@ -269,8 +289,8 @@ egn_status ensure_tables(egn_link* l, const egn_opts* o) {
         wf[i] = (float)w[i];
       }
     }
-    EGN_CUDA(l->d_gl.ensure(total));
-    EGN_CUDA(cudaMemcpy(l->d_gl.p, host.data(), total, cudaMemcpyHostToDevice));
+    EGN_ALLOC(l->d_gl.ensure(total));
+    EGN_CUDA(h2d(l->d_gl.p, host.data(), total));
     char* b = (char*)l->d_gl.p;
     l->gl.n = n;
     for (int p = 1; p <= 3; ++p) {
@@ -373,6 +393,7 @@ const uint32_t* half_offsets(const Workspace& ws, int n_ch) { return ws.row_off 
 
 // The whole step on one stream: plan -> integrate -> assemble.
 egn_status run_step(egn_link* l, const egn_opts* o, const Workspace& ws, double* eta, double* pnli) {
+  NvtxRange range("egn::run_step");
   cudaStream_t st = (cudaStream_t)o->stream;
   ChannelTable ch = channel_table(l);
   cudaEvent_t* ev = nullptr;
@@ -383,6 +404,7 @@ egn_status run_step(egn_link* l, const egn_opts* o, const Workspace& ws, double*
     ev = l->prof_ev;
     EGN_CUDA(cudaEventRecord(ev[0], st));
   }
+  EGN_LAUNCH_GATE();
   EGN_CUDA(cudaMemsetAsync(ws.status, 0, sizeof(int), st));
   EGN_CUDA(launch_plan(ch, ws, st));
   if (ev) EGN_CUDA(cudaEventRecord(ev[1], st));
@@ -538,10 +560,10 @@ egn_status egn_set_wdm(egn_link* l, int n_ch, const double* centre_hz, const dou
   l->btot = n_ch > 1 ? (fmax - fmin) * 1e-12 * n_ch / (n_ch - 1) : l->R[0];
   // channel table
   size_t s = align256(n_ch * sizeof(double));
-  EGN_CUDA(l->d_ch.ensure(6 * s));
+  EGN_ALLOC(l->d_ch.ensure(6 * s));
   const std::vector<double>* arr[6] = {&l->nu, &l->R, &l->W, &l->P, &l->phi, &l->psi};
   for (int a = 0; a < 6; ++a)
-    EGN_CUDA(cudaMemcpy((char*)l->d_ch.p + a * s, arr[a]->data(), n_ch * sizeof(double), cudaMemcpyHostToDevice));
+    EGN_CUDA(h2d((char*)l->d_ch.p + a * s, arr[a]->data(), n_ch * sizeof(double)));
   l->tab_dz = -1.0;  // P_tot and B_tot changed
   // count islands on the device
   l->n_ch = n_ch;
@@ -567,7 +589,12 @@ egn_status egn_set_wdm(egn_link* l, int n_ch, const double* centre_hz, const dou
   // pinned staging for host outputs
   if (l->h_stage) cudaFreeHost(l->h_stage);
   l->h_stage = nullptr;
-  EGN_CUDA(cudaMallocHost((void**)&l->h_stage, (2 * n_ch + 2) * sizeof(double)));
+  e = pinned_alloc((void**)&l->h_stage, (2 * n_ch + 2) * sizeof(double));
+  if (e != cudaSuccess) {
+    l->h_stage = nullptr;
+    l->n_ch = 0;
+    return fail(EGN_E_NOMEM, "cudaMallocHost: %s", cudaGetErrorString(e));
+  }
   return EGN_OK;
 }
 
@@ -606,6 +633,7 @@ egn_status egn_nli_eta_device(egn_link* l, const egn_opts* o, void* workspace, s
 }
 
 egn_status egn_nli_eta(egn_link* l, const egn_opts* o, double* eta, double* pnli) {
+  NvtxRange range("egn_nli_eta");
   egn_status s = check_opts(l, o);
   if (s != EGN_OK) return s;
   DeviceGuard g(l->device);
@@ -677,6 +705,7 @@ egn_status egn_plan_islands(egn_link* l, long long max, int* out, long long* cou
   cudaError_t e = l->ws.ensure(need);
   if (e != cudaSuccess) return fail(EGN_E_NOMEM, "workspace cudaMalloc(%zu): %s", need, cudaGetErrorString(e));
   Workspace ws = carve_workspace(l->ws.p, l->n_ch, l->cnt, EGN_PREC_FP64);
+  EGN_LAUNCH_GATE();
   EGN_CUDA(cudaMemset(ws.status, 0, sizeof(int)));
   EGN_CUDA(launch_plan(channel_table(l), ws, 0));
   std::vector<uint64_t> keys(l->cnt.n_isl);
@@ -725,10 +754,11 @@ egn_status egn_island_terms(egn_link* l, const egn_opts* o, int n_isl, const int
   void* d_t = p + b_keys + b_e + b_f;
   egn_status rs = EGN_OK;
   do {
-    if ((e = cudaMemcpy(d_keys, keys.data(), n_isl * sizeof(uint64_t), cudaMemcpyHostToDevice)) != cudaSuccess) break;
-    if (!e_list.empty() && (e = cudaMemcpy(d_e, e_list.data(), e_list.size() * 4, cudaMemcpyHostToDevice)) != cudaSuccess) break;
-    if (!f_list.empty() && (e = cudaMemcpy(d_f, f_list.data(), f_list.size() * 4, cudaMemcpyHostToDevice)) != cudaSuccess) break;
+    if ((e = h2d(d_keys, keys.data(), n_isl * sizeof(uint64_t))) != cudaSuccess) break;
+    if (!e_list.empty() && (e = h2d(d_e, e_list.data(), e_list.size() * 4)) != cudaSuccess) break;
+    if (!f_list.empty() && (e = h2d(d_f, f_list.data(), f_list.size() * 4)) != cudaSuccess) break;
     if ((e = cudaMemset(d_t, 0, 5 * (size_t)n_isl * tsz)) != cudaSuccess) break;
+    if ((e = inject(kFaultLaunch, cudaErrorLaunchOutOfResources)) != cudaSuccess) break;
     LinkParams prm = link_params(l, o, all_terms ? 1 : 0);
     e = integrate(prm, o->precision, d_keys, n_isl, nullptr, n_isl, d_e, (long long)e_list.size(), d_f,
                   (long long)f_list.size(), d_t, 0, nullptr);
@@ -843,10 +873,10 @@ extern "C" egn_status egn_nli_eta_static(egn_link* l, const egn_opts* o, double*
         cf[k] = (float)ck[k];
       }
       // pageable source: each copy has left the stack buffers before it returns
-      EGN_CUDA(cudaMemcpyAsync(b + o_zeta[t], zeta, Kt * sizeof(double), cudaMemcpyHostToDevice, st));
-      EGN_CUDA(cudaMemcpyAsync(b + o_ck[t], ck, Kt * sizeof(double), cudaMemcpyHostToDevice, st));
-      EGN_CUDA(cudaMemcpyAsync(b + o_zf[t], zf, Kt * sizeof(float), cudaMemcpyHostToDevice, st));
-      EGN_CUDA(cudaMemcpyAsync(b + o_cf[t], cf, Kt * sizeof(float), cudaMemcpyHostToDevice, st));
+      EGN_CUDA(h2d_async(b + o_zeta[t], zeta, Kt * sizeof(double), st));
+      EGN_CUDA(h2d_async(b + o_ck[t], ck, Kt * sizeof(double), st));
+      EGN_CUDA(h2d_async(b + o_zf[t], zf, Kt * sizeof(float), st));
+      EGN_CUDA(h2d_async(b + o_cf[t], cf, Kt * sizeof(float), st));
     }
     for (int p = 1; p <= 3; ++p) {
       const int m = ord[p];
@@ -861,10 +891,10 @@ extern "C" egn_status egn_nli_eta_static(egn_link* l, const egn_opts* o, double*
         f[3][i] = (float)(x2 - (double)f[2][i]);
         f[4][i] = (float)w[i];
       }
-      EGN_CUDA(cudaMemcpyAsync(b + o_gl[p][0], x, m * sizeof(double), cudaMemcpyHostToDevice, st));
-      EGN_CUDA(cudaMemcpyAsync(b + o_gl[p][1], w, m * sizeof(double), cudaMemcpyHostToDevice, st));
+      EGN_CUDA(h2d_async(b + o_gl[p][0], x, m * sizeof(double), st));
+      EGN_CUDA(h2d_async(b + o_gl[p][1], w, m * sizeof(double), st));
       for (int a = 0; a < 5; ++a)
-        EGN_CUDA(cudaMemcpyAsync(b + o_gl[p][2 + a], f[a], m * sizeof(float), cudaMemcpyHostToDevice, st));
+        EGN_CUDA(h2d_async(b + o_gl[p][2 + a], f[a], m * sizeof(float), st));
     }
   }
 
@@ -918,6 +948,7 @@ extern "C" egn_status egn_nli_eta_static(egn_link* l, const egn_opts* o, double*
   // plan -> integrate -> assemble on the caller's stream, workspace in the scratch
   Workspace ws = carve_workspace(b + ws_off, l->n_ch, l->cnt, o->precision);
   ChannelTable ch = p.ch;
+  EGN_LAUNCH_GATE();
   EGN_CUDA(cudaMemsetAsync(ws.status, 0, sizeof(int), st));  // the array keeps the last call's contents
   EGN_CUDA(launch_plan(ch, ws, st));
   EGN_CUDA(integrate(p, o->precision, ws.keys, l->cnt.n_isl, ws.h_idx, l->cnt.n_half, ws.e_idx, l->cnt.n_e, ws.f_idx,

@@ -128,6 +128,7 @@ namespace {
 egn_status enqueue_link(egn_batch* b, size_t i, cudaStream_t s) {
   const BatchLink& L = b->links[i];
   Workspace ws = egn::carve_workspace((char*)b->d_ws.p + L.ws_off, L.n_ch, L.cnt, b->opts.precision);
+  EGN_LAUNCH_GATE();
   EGN_CUDA(cudaMemsetAsync(ws.status, 0, sizeof(int), s));
   EGN_CUDA(egn::launch_plan(L.ch, ws, s));
   EGN_CUDA(integrate(L.p, b->opts.precision, ws.keys, L.cnt.n_isl, ws.h_idx, L.cnt.n_half, ws.e_idx, L.cnt.n_e,
@@ -223,7 +224,7 @@ egn_status create(egn_link* const* links, int n_links, const egn_opts* o, bool c
   const size_t out_b = (size_t)(2 * b->total()) * sizeof(double) + (size_t)n_links * sizeof(int);
   if (e == cudaSuccess) e = b->d_out.ensure(out_b);
   if (e != cudaSuccess) return fail(EGN_E_NOMEM, "batch cudaMalloc: %s", cudaGetErrorString(e));
-  EGN_CUDA(cudaMallocHost((void**)&b->h_stage, out_b));
+  EGN_ALLOC(pinned_alloc((void**)&b->h_stage, out_b));
   // table snapshot (device to device), launch parameters rebased onto it
   for (int i = 0; i < n_links; ++i) {
     egn_link* l = links[i];
@@ -246,7 +247,7 @@ egn_status create(egn_link* const* links, int n_links, const egn_opts* o, bool c
         rebase(t.seg.ck_f, l->d_seg.p, l->d_seg.bytes, seg_c);
       }
       char* ty_c = gl_c + align256(l->d_gl.bytes);
-      EGN_CUDA(cudaMemcpyAsync(ty_c, ty.data(), ty.size() * sizeof(egn::SpanType), cudaMemcpyHostToDevice, b->cap));
+      EGN_CUDA(h2d_async(ty_c, ty.data(), ty.size() * sizeof(egn::SpanType), b->cap));
       EGN_CUDA(cudaStreamSynchronize(b->cap));  // ty is a host temporary
       L.p.types_dev = (const egn::SpanType*)ty_c;
     }
@@ -291,6 +292,7 @@ egn_status egn_batch_create(egn_link* const* links, int n_links, const egn_opts*
 }
 
 egn_status egn_batch_launch(egn_batch* b, void* stream) {
+  NvtxRange range("egn_batch_launch");
   if (!b || !b->exec) return fail(EGN_E_INVALID_ARG, "batch is null");
   DeviceGuard g(b->device);
   EGN_CUDA(cudaGraphLaunch(b->exec, (cudaStream_t)stream));
@@ -307,6 +309,7 @@ egn_status egn_batch_outputs(const egn_batch* b, const double** eta_dev, const d
 }
 
 egn_status egn_batch_read(egn_batch* b, void* stream, double* eta, double* pnli) {
+  NvtxRange range("egn_batch_read");
   if (!b) return fail(EGN_E_INVALID_ARG, "batch is null");
   DeviceGuard g(b->device);
   egn_status s = stage_and_check(b, (cudaStream_t)stream);

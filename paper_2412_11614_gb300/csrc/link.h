@@ -7,6 +7,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/egn.h"
 #include "egn_internal.h"
 
@@ -19,12 +21,46 @@ inline bool finite_pos(double x) { return std::isfinite(x) && x > 0.0; }
 
 inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
+// Host-side fault injection for the failure tests.  The environment variable
+// EGN_FAULT holds a comma-separated subset of "alloc", "h2d" and "launch"; while
+// it names a kind, every device or pinned allocation, every host-to-device copy
+// or every launch sequence of an evaluation fails with the error the real
+// failure returns (cudaErrorMemoryAllocation, cudaErrorInvalidValue,
+// cudaErrorLaunchOutOfResources) before anything reaches the device, so the
+// link or batch stays usable once the variable is cleared.  Read on every call.
+enum : unsigned { kFaultAlloc = 1u, kFaultH2D = 2u, kFaultLaunch = 4u };
+unsigned fault_mask();
+inline cudaError_t inject(unsigned kind, cudaError_t as) { return (fault_mask() & kind) ? as : cudaSuccess; }
+
+inline cudaError_t h2d(void* dst, const void* src, size_t n) {
+  if (cudaError_t f = inject(kFaultH2D, cudaErrorInvalidValue)) return f;
+  return cudaMemcpy(dst, src, n, cudaMemcpyHostToDevice);
+}
+inline cudaError_t h2d_async(void* dst, const void* src, size_t n, cudaStream_t st) {
+  if (cudaError_t f = inject(kFaultH2D, cudaErrorInvalidValue)) return f;
+  return cudaMemcpyAsync(dst, src, n, cudaMemcpyHostToDevice, st);
+}
+inline cudaError_t pinned_alloc(void** p, size_t n) {
+  if (cudaError_t f = inject(kFaultAlloc, cudaErrorMemoryAllocation)) return f;
+  return cudaMallocHost(p, n);
+}
+
+// NVTX range over a scope (host side: the enqueue of a phase); a no-op unless a
+// profiler is attached, and the ranges let ncu --nvtx filter the phases.
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
+
 // Device buffer owned by a link or a batch.
 struct DevBuf {
   void* p = nullptr;
   size_t bytes = 0;
   cudaError_t ensure(size_t want) {
     if (want <= bytes && p) return cudaSuccess;
+    if (cudaError_t f = inject(kFaultAlloc, cudaErrorMemoryAllocation)) return f;  // the old buffer stays
     if (p) cudaFree(p);
     p = nullptr;
     bytes = 0;
@@ -57,6 +93,16 @@ struct DeviceGuard {
     cudaError_t e_ = (call);                                                                              \
     if (e_ != cudaSuccess) return egn_host::fail(EGN_E_CUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
   } while (0)
+
+// An allocation: failure is EGN_E_NOMEM.
+#define EGN_ALLOC(call)                                                                                    \
+  do {                                                                                                     \
+    cudaError_t e_ = (call);                                                                               \
+    if (e_ != cudaSuccess) return egn_host::fail(EGN_E_NOMEM, "%s: %s", #call, cudaGetErrorString(e_)); \
+  } while (0)
+
+// The start of every evaluation's launch sequence (plan -> integrate -> assemble).
+#define EGN_LAUNCH_GATE() EGN_CUDA(egn_host::inject(egn_host::kFaultLaunch, cudaErrorLaunchOutOfResources))
 
 struct egn_link {
   std::vector<egn_span> spans_si;

@@ -14,8 +14,11 @@ links are evaluated by the integrator instead.
 """
 from __future__ import annotations
 
+import hashlib
+import json
 import math
-from typing import List, Sequence
+import os
+from typing import Callable, List, Optional, Sequence
 
 import numpy as np
 
@@ -224,6 +227,81 @@ class Surrogate:
         self.x_std = np.where(x.std(axis=0) > 1e-12, x.std(axis=0), 1.0)
         self.y_mean, self.y_std = float(t.mean()), float(t.std() or 1.0)
 
+    # ------------------------------------------------------------------ checkpoints
+    def state(self) -> dict:
+        """Host copy of everything training needs to continue: FP32 master
+        weights, Adam moments, step count and the normalisation."""
+        st = {"step_count": np.int64(self.step_count), "x_mean": self.x_mean, "x_std": self.x_std,
+              "y_norm": np.array([self.y_mean, self.y_std])}
+        for j, (p, m, v) in enumerate(zip(self.params, self.m, self.v)):
+            st[f"p{j}"] = p.cpu().numpy()
+            st[f"m{j}"] = m.cpu().numpy()
+            st[f"v{j}"] = v.cpu().numpy()
+        return st
+
+    def load_state(self, st) -> None:
+        torch = self.torch
+        for j, (p, m, v) in enumerate(zip(self.params, self.m, self.v)):
+            for dst, key in ((p, f"p{j}"), (m, f"m{j}"), (v, f"v{j}")):
+                src = np.asarray(st[key])
+                if src.shape != tuple(dst.shape):
+                    raise ValueError(f"checkpoint {key}: shape {src.shape}, model {tuple(dst.shape)}")
+                dst.copy_(torch.from_numpy(src))
+        self.step_count = int(st["step_count"])
+        self.x_mean, self.x_std = np.asarray(st["x_mean"]), np.asarray(st["x_std"])
+        self.y_mean, self.y_std = (float(a) for a in np.asarray(st["y_norm"]))
+        self._refresh_bf16(None)
+
+
+def _save_atomic(path: str, arrays: dict) -> None:
+    tmp = path + ".tmp"
+    with open(tmp, "wb") as f:
+        np.savez(f, **arrays)
+    os.replace(tmp, path)
+
+
+def train(model: Surrogate, x: np.ndarray, t: np.ndarray, steps: int, batch_rows: int = 8192,
+          lr_max: float = 2e-3, lr_min: float = 1e-5, seed: int = 0, checkpoint: Optional[str] = None,
+          every: int = 0, on_step: Optional[Callable[[int, float], None]] = None) -> List[float]:
+    """Adam on minibatches of rows (a fresh permutation every epoch, cosine
+    learning rate from lr_max to lr_min).  With `checkpoint`, the model, the
+    sampler's state and the step are saved there every `every` steps and at the
+    end, and a run that finds the file continues from it: the result is bit for
+    bit that of an uninterrupted run.  Returns the losses of the steps run here."""
+    rng = np.random.default_rng(seed)
+    per_epoch = max(1, len(x) // batch_rows)
+    perm = None
+    start = 0
+    if checkpoint and os.path.exists(checkpoint):
+        with np.load(checkpoint, allow_pickle=False) as z:
+            model.load_state(z)
+            start = int(z["next_step"])
+            rng.bit_generator.state = json.loads(str(z["rng"]))
+            perm = z["perm"] if z["perm"].size else None
+    losses = []
+
+    def save(next_step):
+        st = model.state()
+        st.update(next_step=np.int64(next_step), rng=np.array(json.dumps(rng.bit_generator.state)),
+                  perm=perm if perm is not None else np.zeros(0, dtype=np.int64))
+        _save_atomic(checkpoint, st)
+
+    for step in range(start, steps):
+        if step % per_epoch == 0:
+            perm = rng.permutation(len(x))
+        j = (step % per_epoch) * batch_rows
+        idx = perm[j:j + batch_rows]
+        lr = lr_min + 0.5 * (lr_max - lr_min) * (1 + math.cos(math.pi * step / steps))
+        loss = model.train_step(x[idx], t[idx], lr)
+        losses.append(loss)
+        if checkpoint and every and (step + 1) % every == 0:
+            save(step + 1)
+        if on_step:
+            on_step(step, loss)
+    if checkpoint and start < steps:
+        save(steps)
+    return losses
+
 
 def labels(workloads: Sequence, opts) -> List[np.ndarray]:
     """10 log10(eta) of every channel of every link, from the integrator (one
@@ -233,6 +311,59 @@ def labels(workloads: Sequence, opts) -> List[np.ndarray]:
     for ln in links:
         ln.close()
     return [10.0 * np.log10(e) for e, _ in out]
+
+
+def generate_labels(directory: str, seeds: Sequence[int], opts, shard_links: int = 256,
+                    label_fn: Optional[Callable] = None, make_link: Optional[Callable] = None) -> np.ndarray:
+    """Labels of the seeded links, written shard by shard under `directory`.
+
+    shard_NNNNN.npy holds the [links][channels] float64 array of 10 log10 eta for
+    seeds[k * shard_links : (k + 1) * shard_links]; index.json records the run
+    (a hash of the seed list, the options, the shard size) and the shards that
+    are complete.  A shard file is written first and entered in the index after,
+    both by atomic rename, so a run that is killed loses at most the shard in
+    progress and a rerun with the same arguments computes only the shards the
+    index does not list.  Files of a different run (other seeds or options) are
+    refused.  label_fn(workloads) -> list of per-channel arrays (default: the
+    integrator, batches of 64 links); make_link(seed) -> workload (default: the
+    seeded 120-channel training links).  Returns all labels, [links][channels]."""
+    if make_link is None:
+        from .workloads import surrogate_link as make_link
+    if label_fn is None:
+        def label_fn(wls):
+            out = []
+            for i in range(0, len(wls), 64):
+                out += labels(wls[i:i + 64], opts)
+            return out
+    seeds = [int(s) for s in seeds]
+    key = {"seeds_sha256": hashlib.sha256(np.asarray(seeds, dtype=np.int64).tobytes()).hexdigest(),
+           "n_links": len(seeds), "shard_links": int(shard_links),
+           "opts": {f: getattr(opts, f) for f in ("gl_order", "dz_km", "mu_form", "precision", "terms")}
+           if opts is not None else None}
+    os.makedirs(directory, exist_ok=True)
+    index_path = os.path.join(directory, "index.json")
+    done = set()
+    if os.path.exists(index_path):
+        with open(index_path) as f:
+            idx = json.load(f)
+        if idx.get("run") != key:
+            raise ValueError(f"{directory} holds labels of another run: {idx.get('run')} != {key}")
+        done = set(idx["done"])
+    n_shards = -(-len(seeds) // shard_links)
+    for k in range(n_shards):
+        if k in done:
+            continue
+        part = seeds[k * shard_links:(k + 1) * shard_links]
+        lab = np.asarray(label_fn([make_link(s) for s in part]), dtype=np.float64)
+        shard = os.path.join(directory, f"shard_{k:05d}.npy")
+        with open(shard + ".tmp", "wb") as f:
+            np.save(f, lab)
+        os.replace(shard + ".tmp", shard)
+        done.add(k)
+        with open(index_path + ".tmp", "w") as f:
+            json.dump({"run": key, "done": sorted(done)}, f)
+        os.replace(index_path + ".tmp", index_path)
+    return np.concatenate([np.load(os.path.join(directory, f"shard_{k:05d}.npy")) for k in range(n_shards)])
 
 
 def predict(model: Surrogate, workloads: Sequence, opts):

@@ -226,3 +226,44 @@ def test_surrogate_learns_a_smooth_map(K):
     assert last < 0.1 * first
     pred = model.predict_rows(x[:512])
     assert np.sqrt(np.mean((pred - t[:512]) ** 2)) < 0.3 * np.std(t)
+
+
+class _Crash(Exception):
+    pass
+
+
+def test_training_checkpoint_resume_is_bit_identical(K, tmp_path):
+    """A training run that dies after step 4 (checkpoints every 3 steps) and is
+    resumed from its checkpoint by a fresh model ends with exactly the weights,
+    Adam moments and predictions of an uninterrupted run (all kernels are
+    deterministic, the sampler state is in the checkpoint)."""
+    from paper_2412_11614_gb300 import surrogate as S
+    rng = np.random.default_rng(5)
+    x = rng.uniform(-1, 1, (3000, S.N_FEAT))
+    t = np.cos(3 * x[:, 0]) + x[:, 4] * x[:, 5]
+    ref = S.Surrogate(seed=3)
+    ref.fit_normalisation(x, t)
+    ref_losses = S.train(ref, x, t, steps=8, batch_rows=1024, seed=9)   # 2 batches per epoch, 4 epochs
+
+    ck = str(tmp_path / "ck.npz")
+
+    def die(step, loss):
+        if step == 4:
+            raise _Crash()
+
+    a = S.Surrogate(seed=3)
+    a.fit_normalisation(x, t)
+    with pytest.raises(_Crash):
+        S.train(a, x, t, steps=8, batch_rows=1024, seed=9, checkpoint=ck, every=3, on_step=die)
+    b = S.Surrogate(seed=11)  # other initial weights: everything must come from the checkpoint
+    losses = S.train(b, x, t, steps=8, batch_rows=1024, seed=9, checkpoint=ck, every=3)
+    assert losses == ref_losses[3:]
+    sa, sb = ref.state(), b.state()
+    assert sa.keys() == sb.keys()
+    for key in sa:
+        assert np.array_equal(sa[key], sb[key]), key
+    assert np.array_equal(ref.predict_rows(x[:500]), b.predict_rows(x[:500]))
+    # the finished checkpoint holds the final step: a rerun trains nothing
+    c = S.Surrogate(seed=12)
+    assert S.train(c, x, t, steps=8, batch_rows=1024, seed=9, checkpoint=ck, every=3) == []
+    assert np.array_equal(c.predict_rows(x[:500]), b.predict_rows(x[:500]))

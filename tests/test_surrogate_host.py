@@ -70,3 +70,43 @@ def test_drho_feature_is_eq12_scale(S, workloads):
     btot = (f.max() - f.min()) * 1e-12 * 120 / 119
     want = s.cr_per_w_km_thz * sum(w.launch_power_w) * leff * btot
     assert np.isclose(S.features(w)[0, 16], want)
+
+
+class _Crash(Exception):
+    pass
+
+
+def test_label_shards_resume_after_a_crash(S, tmp_path):
+    """generate_labels writes shard after shard; a run that dies in the third
+    shard resumes at it, computes only what is missing and returns the same array."""
+    seeds = list(range(100, 110))
+    calls = []
+
+    def fake(wls, crash_at=None):
+        calls.append(list(wls))
+        if crash_at is not None and len(calls) == crash_at:
+            raise _Crash()
+        return [np.full(4, float(s)) + np.arange(4) for s in wls]
+
+    d = str(tmp_path / "labels")
+    with pytest.raises(_Crash):
+        S.generate_labels(d, seeds, None, shard_links=3, label_fn=lambda w: fake(w, crash_at=3), make_link=int)
+    import json, os
+    idx = json.load(open(os.path.join(d, "index.json")))
+    assert idx["done"] == [0, 1]
+    calls.clear()
+    got = S.generate_labels(d, seeds, None, shard_links=3, label_fn=fake, make_link=int)
+    assert calls == [[106, 107, 108], [109]]                  # only the missing shards
+    assert np.array_equal(got, np.array([np.full(4, float(s)) + np.arange(4) for s in seeds]))
+    calls.clear()
+    assert np.array_equal(S.generate_labels(d, seeds, None, shard_links=3, label_fn=fake, make_link=int), got)
+    assert calls == []                                          # complete: nothing recomputed
+    # a shard file that exists but was never entered in the index is recomputed
+    idx = json.load(open(os.path.join(d, "index.json")))
+    idx["done"].remove(1)
+    json.dump(idx, open(os.path.join(d, "index.json"), "w"))
+    np.save(os.path.join(d, "shard_00001.npy"), np.zeros((3, 4)))
+    assert np.array_equal(S.generate_labels(d, seeds, None, shard_links=3, label_fn=fake, make_link=int), got)
+    assert calls == [[103, 104, 105]]
+    with pytest.raises(ValueError):                             # files of another run are not mixed in
+        S.generate_labels(d, seeds[:-1], None, shard_links=3, label_fn=fake, make_link=int)
