@@ -42,8 +42,11 @@ using namespace fp32c;
 
 constexpr int kThreads = 128;
 constexpr int kDwThreads = 64;     // CTA size of the D/G/H, E and F passes
-constexpr int kDwCtas = 10;        // their resident CTAs per SM
-constexpr int kDwBatch = 32;       // their islands per batch
+constexpr int kDwCtas = 10;        // resident CTAs per SM of the D/G/H pass
+constexpr int kEfCtas = 10;        // and of the E and F passes
+constexpr int kDwBatch = 32;       // islands per batch of the D/G/H pass
+constexpr int kEfBatch = 16;       // and of the E and F passes (short lists: smaller
+                                   // batches spread them over more CTAs)
 constexpr int kBatch = kThreads;   // islands per batch, one per thread in the set-up
 constexpr int kRowsMax = 64;       // rows per chunk held in shared memory
 constexpr int kTabFloats = 2688;   // DW c_k table budget (10.5 KB): [rows][kpad] floats
@@ -262,12 +265,17 @@ __device__ __forceinline__ void dw_recurrence(const float* __restrict__ trow, in
 // CTA, min_ctas resident CTAs per SM (the register budget follows from it) and
 // rows_max rows of constants per chunk.
 __host__ __device__ constexpr int min_ctas(int ord, int kp, int nt) {
-  return nt == 64 ? kDwCtas : (kp == 8 ? 3 : (ord == ORD_DW ? 5 : 4));
+  return nt == 64 ? (ord == ORD_DW ? kDwCtas : kEfCtas) : (kp == 8 ? 3 : (ord == ORD_DW ? 5 : 4));
 }
 // Islands per batch (FP64 set-up, one island per thread): fewer than NT keeps the
 // batch arrays small enough for kDwCtas CTAs per SM.
-__host__ __device__ constexpr int batch_of(int nt) { return nt == 64 ? kDwBatch : nt; }
+__host__ __device__ constexpr int batch_of(int ord, int nt) {
+  return nt == 64 ? (ord == ORD_DW ? kDwBatch : kEfBatch) : nt;
+}
 __host__ __device__ constexpr int rows_max(int nt) { return nt == 64 ? 32 : kRowsMax; }
+// Floats of the inner-node arrays at the head of the main kernel's dynamic shared
+// memory (6 per node, rounded up to 16 bytes).
+__host__ __device__ constexpr int node_floats(int n) { return (6 * n + 3) & ~3; }
 
 // Fixed-order sum of the per-warp partial sums of a CTA.
 template <int NW>
@@ -286,13 +294,17 @@ integrate_fp32c_kernel(LinkParams p, const uint64_t* __restrict__ keys, const ui
                        Df G0, Df G1) {
   static_assert(KP % 2 == 0, "points per thread come in f32x2 pairs");
   constexpr int NPAIR = KP / 2;
-  constexpr int NB = batch_of(NT);
+  constexpr int NB = batch_of(ORD, NT);
   __shared__ BatchSmT<NB> bs;
   __shared__ RowSm<rows_max(NT)> rs;
-  __shared__ NodeSm ns;
   constexpr int NW = NT / 32;
   __shared__ float red[4][NW];
-  extern __shared__ __align__(16) float tab[];  // [rows_per_chunk][kpad] c_k of the chunk's rows (DW only)
+  // dynamic: inner nodes {x head, x tail, x^2 head, x^2 tail}[n], {x^3, w}[n], then
+  // (DW only) the [rows_per_chunk][kpad] c_k of the chunk's rows, 16-byte aligned
+  extern __shared__ __align__(16) float dyn[];
+  float4* const nx4 = reinterpret_cast<float4*>(dyn);
+  float2* const nx2 = reinterpret_cast<float2*>(dyn + 4 * p.gl.n);
+  float* const tab = dyn + node_floats(p.gl.n);
 
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const int n = p.gl.n;
@@ -319,8 +331,8 @@ integrate_fp32c_kernel(LinkParams p, const uint64_t* __restrict__ keys, const ui
 
   for (int j = tid; j < n; j += NT) {
     const float xh = p.gl.xh[1][j], xl = p.gl.xl[1][j];
-    ns.x4[j] = make_float4(xh, xl, p.gl.x2h[1][j], p.gl.x2l[1][j]);
-    ns.x2[j] = make_float2(xh * p.gl.x2h[1][j], p.gl.wf[1][j]);
+    nx4[j] = make_float4(xh, xl, p.gl.x2h[1][j], p.gl.x2l[1][j]);
+    nx2[j] = make_float2(xh * p.gl.x2h[1][j], p.gl.wf[1][j]);
   }
 
   for (long long b0 = (long long)blockIdx.x * NB; b0 < n_items; b0 += (long long)gridDim.x * NB) {
@@ -342,10 +354,10 @@ integrate_fp32c_kernel(LinkParams p, const uint64_t* __restrict__ keys, const ui
       const int rows = np * no;
       for (int c0 = 0; c0 < rows; c0 += rows_per_chunk) {
         const int rc = min(rows_per_chunk, rows - c0);
-        // ---- row constants in double-float; slot rr = 32 (tid mod NW) + tid / NW (a
-        // bijection on 0..NT-1) spreads the first 32 rows of a chunk over the warps
+        // ---- row constants in double-float, one row per thread: the rows fill whole
+        // warps (rc <= NT), so the idle warps issue nothing
         {
-          const int rr = (tid % NW) * 32 + tid / NW;
+          const int rr = tid;
           if (rr < rc) {
             const int row = c0 + rr;
             const int pi = row / no, i = row - pi * no;
@@ -371,17 +383,33 @@ integrate_fp32c_kernel(LinkParams p, const uint64_t* __restrict__ keys, const ui
         }
         __syncthreads();
         // ---- c_k tables of the chunk's rows (DW): C_k 2^{-zeta_k log2(e) f3}
-        // Rounds of up to NT columns k; a round of nk < NT columns gives each column
-        // NT / nk threads that split the rows.  c_k and zeta_k stay in registers.
+        // A task is four consecutive columns of one row (one 16-byte store); rounds
+        // of up to NT column groups, and a round of gn < NT groups gives each group
+        // NT / gn threads that split the rows.  The four C_k and zeta_k stay in
+        // registers; columns K..kpad-1 (padding, never read) get C_k = 0.
         if (ORD == ORD_DW) {
-          for (int kb = 0; kb < K; kb += NT) {
-            const int nk = min(NT, K - kb);
-            const int g = NT / nk, col = tid % nk, grp = tid / nk;
-            if (grp < g) {
-              const int k = kb + col;
-              const float ck = p.seg.ck_f[k], zk = p.seg.zeta_f[k];
-#pragma unroll 8
-              for (int rr = grp; rr < rc; rr += g) tab[rr * kpad + k] = ck * ex2_approx(-zk * rs.f3[rr].x);
+          const int ng = kpad >> 2;
+          for (int g0 = 0; g0 < ng; g0 += NT) {
+            const int gn = min(NT, ng - g0);
+            const int rstep = NT / gn, g4 = g0 + tid % gn, r0 = tid / gn;
+            if (r0 < rstep) {
+              float c4[4], z4[4];
+#pragma unroll
+              for (int e = 0; e < 4; ++e) {
+                const int k = 4 * g4 + e;
+                c4[e] = k < K ? p.seg.ck_f[k] : 0.0f;
+                z4[e] = k < K ? p.seg.zeta_f[k] : 0.0f;
+              }
+#pragma unroll 4
+              for (int rr = r0; rr < rc; rr += rstep) {
+                const float f3 = rs.f3[rr].x;
+                float4 v;
+                v.x = c4[0] * ex2_approx(-z4[0] * f3);
+                v.y = c4[1] * ex2_approx(-z4[1] * f3);
+                v.z = c4[2] * ex2_approx(-z4[2] * f3);
+                v.w = c4[3] * ex2_approx(-z4[3] * f3);
+                *reinterpret_cast<float4*>(tab + rr * kpad + 4 * g4) = v;
+              }
             }
           }
           __syncthreads();
@@ -399,25 +427,30 @@ integrate_fp32c_kernel(LinkParams p, const uint64_t* __restrict__ keys, const ui
             // D only.  |Upsilon / gamma|^2 = |sum|^2 |w - 1|^2 / (alpha^2 + chi^2) * (sn / sd)^2
             // with 2 Re w = 2r - 4r sin^2(pi theta), |w - 1|^2 = (1 - r)^2 + 4r sin^2(pi theta)
             // and |sum|^2 = |b_0 - conj(w) b_1|^2 = b_0 (b_0 - 2 Re(w) b_1) + r^2 b_1^2.
-            float pv[KP], wa_[KP], chi_[KP], phi_[KP], wgt_[KP];
+            // Every factor but |sum|^2 is formed before the recurrence, so that one value
+            // per point (with 2 Re w) stays live across it.
+            float pv[KP], fac[KP];
 #pragma unroll
             for (int m = 0; m < KP; ++m) {
               const int j = lr + tpr * m;
               const bool jok = j < n;
               const int jj = jok ? j : 0;
-              const float4 x4 = ns.x4[jj];
-              const float2 x2 = ns.x2[jj];
+              const float4 x4 = nx4[jj];
+              const float2 x2 = nx2[jj];
               float th, ph;
               point_phase(qa, qb, x4, x2.x, Kf, invK, th, ph);
               const float sh = __sinf(pi_f * th);
               const float s2 = sh * sh;
               pv[m] = fmaf(-c4r, s2, c2r);
-              wa_[m] = fmaf(c4r, s2, omr2);
-              phi_[m] = ph;
+              const float wa = fmaf(c4r, s2, omr2);
               const float xh = x4.x;
-              chi_[m] = fmaf(ab.y, xh, ab.x) * fmaf(ab.w, xh, ab.z) * fmaf(kc.y, xh, kc.x);
+              const float chi = fmaf(ab.y, xh, ab.x) * fmaf(ab.w, xh, ab.z) * fmaf(kc.y, xh, kc.x);
               const float t = fmaf(ih, xh, im);
-              wgt_[m] = (jok ? x2.y : 0.0f) * rc_f(t, sa1, si1) * rc_f(ow.x - t, sa2, si2);
+              const float wgt = (jok ? x2.y : 0.0f) * rc_f(t, sa1, si1) * rc_f(ow.x - t, sa2, si2);
+              float sd, sn;
+              array_sines(pi_f * ph, N, sd, sn);
+              const float den = (sd * sd) * fmaf(chi, chi, alpha2);
+              fac[m] = (wgt * wa) * ((sn * sn) * rcp_approx(den));
             }
             f32x2 pp[NPAIR], b1p[NPAIR], b2p[NPAIR];
 #pragma unroll
@@ -433,10 +466,7 @@ integrate_fp32c_kernel(LinkParams p, const uint64_t* __restrict__ keys, const ui
               for (int e = 0; e < 2; ++e) {
                 const int m = 2 * a + e;
                 const float s2sum = fmaf(b0v[e], fmaf(-pv[m], b1v[e], b0v[e]), q * b1v[e] * b1v[e]);
-                float sd, sn;
-                array_sines(pi_f * phi_[m], N, sd, sn);
-                const float den = (sd * sd) * fmaf(chi_[m], chi_[m], alpha2);
-                acc = fmaf(wgt_[m] * s2sum * wa_[m], (sn * sn) * rcp_approx(den), acc);
+                acc = fmaf(fac[m], s2sum, acc);
               }
             }
             dsum = fmaf(wrowh, acc, dsum);
@@ -450,8 +480,8 @@ integrate_fp32c_kernel(LinkParams p, const uint64_t* __restrict__ keys, const ui
             const int j = lr + tpr * m;
             const bool jok = j < n;
             const int jj = jok ? j : 0;
-            const float4 x4 = ns.x4[jj];
-            const float2 x2 = ns.x2[jj];
+            const float4 x4 = nx4[jj];
+            const float2 x2 = nx2[jj];
             const float xh = x4.x;
             const float wnode = jok ? x2.y : 0.0f;
             float th, ph;
@@ -611,7 +641,7 @@ cudaError_t launch_one(const LinkParams& p, const uint64_t* keys, const uint32_t
     if (rows > rows_max(NT)) rows = rows_max(NT);
     if (rows < 1) rows = 1;
   }
-  size_t smem = ORD == ORD_DW ? (size_t)rows * kpad * sizeof(float) : 0;
+  size_t smem = ((size_t)node_floats(p.gl.n) + (ORD == ORD_DW ? (size_t)rows * kpad : 0)) * sizeof(float);
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -619,11 +649,11 @@ cudaError_t launch_one(const LinkParams& p, const uint64_t* keys, const uint32_t
   static unsigned long long attr_done = 0;
   if (!(attr_done >> (dev & 63) & 1ull)) {
     cudaError_t e = cudaFuncSetAttribute(integrate_fp32c_kernel<ORD, KP, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         kTabFloats * (int)sizeof(float));
+                                         (node_floats(kMaxGl) + kTabFloats) * (int)sizeof(float));
     if (e != cudaSuccess) return e;
     attr_done |= 1ull << (dev & 63);
   }
-  long long batches = (n_items + batch_of(NT) - 1) / batch_of(NT);
+  long long batches = (n_items + batch_of(ORD, NT) - 1) / batch_of(ORD, NT);
   long long blocks = (long long)sms * min_ctas(ORD, KP, NT);
   if (blocks > batches) blocks = batches;
   // 2 pi L beta2 and 2 pi^2 L beta3 as double-floats
