@@ -321,6 +321,14 @@ ChannelTable channel_table(const egn_link* l) {
   t.P = b + 3 * s;
   t.phi = b + 4 * s;
   t.psi = b + 5 * s;
+  t.nu_f = (const float*)(b + 6 * s);  // the seventh array holds nu_f[n_ch] then hw_f[n_ch]
+  t.hw_f = t.nu_f + l->n_ch;
+  t.hwmax_f = 0.5f * (float)t.wmax;
+  double numax = 0.0;
+  for (double x : l->nu) numax = std::max(numax, std::fabs(x));
+  // FP32 rounding of four centres, three half supports and five operations on
+  // values up to 3 numax + 1.5 wmax: well inside 4e-6 (numax + wmax)
+  t.plan_margin = (float)(4e-6 * (numax + t.wmax)) + 1e-30f;
   return t;
 }
 
@@ -560,10 +568,18 @@ egn_status egn_set_wdm(egn_link* l, int n_ch, const double* centre_hz, const dou
   l->btot = n_ch > 1 ? (fmax - fmin) * 1e-12 * n_ch / (n_ch - 1) : l->R[0];
   // channel table
   size_t s = align256(n_ch * sizeof(double));
-  EGN_ALLOC(l->d_ch.ensure(6 * s));
+  EGN_ALLOC(l->d_ch.ensure(7 * s));
   const std::vector<double>* arr[6] = {&l->nu, &l->R, &l->W, &l->P, &l->phi, &l->psi};
   for (int a = 0; a < 6; ++a)
     EGN_CUDA(h2d((char*)l->d_ch.p + a * s, arr[a]->data(), n_ch * sizeof(double)));
+  {
+    std::vector<float> f32(2 * (size_t)n_ch);
+    for (int i = 0; i < n_ch; ++i) {
+      f32[i] = (float)l->nu[i];
+      f32[n_ch + i] = 0.5f * (float)l->W[i];
+    }
+    EGN_CUDA(h2d((char*)l->d_ch.p + 6 * s, f32.data(), f32.size() * sizeof(float)));
+  }
   l->tab_dz = -1.0;  // P_tot and B_tot changed
   // count islands on the device
   l->n_ch = n_ch;

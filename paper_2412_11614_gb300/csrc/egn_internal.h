@@ -44,6 +44,13 @@ struct ChannelTable {
   const double* P;
   const double* phi;
   const double* psi;
+  // FP32 copies for the planner's candidate search and pre-test: centres and
+  // half supports W/2, the widest half support and the bound on the FP32 error of
+  // (W1 + W2 + W3) / 2 - |d| (outside +-plan_margin the FP32 sign is exact)
+  const float* nu_f;
+  const float* hw_f;
+  float hwmax_f;
+  float plan_margin;
 };
 
 // Gauss-Legendre tables for the three outer orders ceil(n/p), p = 1, 2, 3

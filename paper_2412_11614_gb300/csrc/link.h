@@ -117,7 +117,7 @@ struct egn_link {
   egn::PlanCounts cnt{};
   std::vector<long long> per_coi;
   int device = -1;
-  egn_host::DevBuf d_ch;  // 6 arrays of n_ch doubles
+  egn_host::DevBuf d_ch;  // 6 arrays of n_ch doubles, then nu and W/2 as floats
   // cached tables for the last (dz, gl_order)
   double tab_dz = -1.0;
   int tab_gl = -1;

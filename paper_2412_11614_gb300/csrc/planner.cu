@@ -30,8 +30,8 @@ __device__ __forceinline__ bool island_exists(const ChannelTable& ch, int n, int
   return hi > lo;
 }
 
-// First channel index whose centre is >= x (channels sorted ascending).
-__device__ __forceinline__ int lower_bound(const double* nu, int n, double x) {
+// First channel index whose centre is >= x (centres non-decreasing).
+__device__ __forceinline__ int lower_bound_f(const float* nu, int n, float x) {
   int lo = 0, hi = n;
   while (lo < hi) {
     int mid = (lo + hi) >> 1;
@@ -41,13 +41,22 @@ __device__ __forceinline__ int lower_bound(const double* nu, int n, double x) {
 }
 
 // Visit the islands of (n, n1, n2) in ascending n3; f(n3) is called for each.
+// The candidates n3 (centres within the reach of f1 + f2 - f) are found in FP32
+// with the error bound added to the reach, so they include every island.  Each
+// candidate is decided by g = (W1 + W2 + W3) / 2 - |d| in FP32 where |g| exceeds
+// its error bound, else by the FP64 test: the same islands as the FP64 test
+// alone, with a fraction of the FP64 work.
 template <class F>
 __device__ __forceinline__ void for_each_n3(const ChannelTable& ch, int n, int n1, int n2, F&& f) {
-  double t = (ch.nu[n1] - ch.nu[n]) + ch.nu[n2];
-  double reach = 0.5 * ch.W[n1] + 0.5 * ch.W[n2] + 0.5 * ch.wmax + 1e-6;
-  int i = lower_bound(ch.nu, ch.n_ch, t - reach);
-  for (; i < ch.n_ch && ch.nu[i] <= t + reach; ++i)
-    if (island_exists(ch, n, n1, n2, i)) f(i);
+  const float t = (ch.nu_f[n1] - ch.nu_f[n]) + ch.nu_f[n2];
+  const float hw12 = ch.hw_f[n1] + ch.hw_f[n2];
+  const float m = ch.plan_margin;
+  const float reach = (hw12 + ch.hwmax_f) + 2.0f * m + 1e-6f;
+  int i = lower_bound_f(ch.nu_f, ch.n_ch, t - reach);
+  for (; i < ch.n_ch && ch.nu_f[i] <= t + reach; ++i) {
+    const float g = (hw12 + ch.hw_f[i]) - fabsf(t - ch.nu_f[i]);
+    if (g > m || (g >= -m && island_exists(ch, n, n1, n2, i))) f(i);
+  }
 }
 
 struct Counts {
