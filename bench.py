@@ -209,13 +209,11 @@ def run_reference(args):
 # --------------------------------------------------------------------------- our arm
 
 def flops_per_point(precision: str, K: int) -> float:
-    """Algorithmic FLOPs per quadrature point of the D/G/H pass (FMA = 2 FLOPs).
-    FP32C: the segment sum by the real second-order recurrence, 2 FMA per segment
-    (4 K), plus the point prologue/epilogue counted in the design doc (see kernel).
-    FP64: Horner's complex rule, 4 FMA-class ops per segment (8 K)."""
-    if precision == "fp32c":
-        return 4.0 * K
-    return 8.0 * K
+    """Algorithmic FLOPs per quadrature point of the D/G/H pass (FMA = 2 FLOPs):
+    the segment sum of Eq. 8 by the real second-order recurrence, 2 FMA per
+    segment (4 K), in both precisions.  The per-point phase, trigonometry and
+    weights are not counted."""
+    return 4.0 * K
 
 
 def run_mu_compare(args):

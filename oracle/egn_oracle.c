@@ -20,9 +20,21 @@
  *   - sigma^2_NLI and eta                                        [Eq. 11, 15]
  *   - modulation-format moments Phi, Psi (enumerated constellations)
  *
- * Readings of the paper where it is silent or garbled (white-NLI 2-D domain,
- * raised-cosine S(f), Phi/Psi definitions, ideal per-span gain, ISRS origin,
- * beta reference shift, Cr = 0 limit, tie-breaks) are listed in the design doc.
+ * Readings taken where the paper is silent or garbled:
+ *   - the NLI PSD is evaluated at the COI centre and integrated over the COI
+ *     as R times that value (2-D islands in f1, f2; white NLI);
+ *   - |S(f)|^2 = h(f) / R^2 with h the raised-cosine shape of roll-off beta;
+ *   - Phi = mu4 - 2, Psi = mu6 - 9 mu4 + 12 from the moments of the
+ *     equiprobable unit-energy constellation (Gaussian: 0, 0);
+ *   - every amplifier restores its span exactly (the gain/ISRS products of
+ *     Eq. 22 are 1);
+ *   - the ISRS profile (Eq. 25) and beta2/beta3 are taken about the spectral
+ *     centre (f_min + f_max) / 2, with B_tot = (f_max - f_min) N / (N - 1);
+ *   - beta2, beta3 follow from D, S at the reference wavelength, beta2 shifted
+ *     by 2 pi beta3 (f_c - f_ref);
+ *   - at Cr = 0 (0/0 in Eq. 25) C_k takes its limit 1;
+ *   - an island exists only if its overlap has positive area (strict
+ *     inequality); E and F coefficients 16/27 and 32/81 as printed.
  *
  * Internal units: frequency THz, time ps, length km, power W.  Then
  * beta2 [ps^2/km] * f^2 [THz^2] is rad/km and zeta = Ptot*Cr*Leff is 1/THz.
@@ -480,7 +492,7 @@ static void or_walk(const or_problem* pb, int n, int n1, int n2, int n3, int ord
 }
 
 /* D, E, F, G, H of island (n1, n2, n3) for COI n (Eq. 17-21 with the readings
- * of the design doc).  With all = 0 only the terms selected by the Kronecker deltas of
+ * in the header of this file).  With all = 0 only the terms selected by the Kronecker deltas of
  * Eq. 15 are evaluated (others set to 0); with all = 1 every term is evaluated. */
 void or_island_terms(const or_problem* pb, int n, int n1, int n2, int n3, int all, double* out)
 {

@@ -6,7 +6,8 @@
 //   w      = e^{(i chi - alpha) L/K}
 //   mu     = (w - 1)/(i chi - alpha) * sum_k c_k w^k,                       (Eq. 8-10)
 //            c_k = C_k e^{-zeta_k f3}, the k-th midpoint SRS gain (Eq. 14),
-//            summed by Horner's rule from k = K - 1 down to 0
+//            summed by the second-order real recurrence (Goertzel's) from
+//            k = K - 1 down to 0
 //   Y      = gamma mu e^{i (N-1) phi/2} sin(N phi/2) / sin(phi/2), phi = chi L   (Eq. 22)
 // The segment form is Eq. 8 exactly: I_k = w^k (w - 1)/(i chi - alpha).  Phases
 // are reduced in turns (chi L/K / 2 pi and chi L / 2 pi modulo 1) before
@@ -23,6 +24,21 @@ struct Cd {
 };
 
 __device__ __forceinline__ Cd cmul(Cd a, Cd b) { return {a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re}; }
+
+// sum_k c_k w^k (k = 0 .. K-1, real c_k = ck(k), |w|^2 = r2) by the second-order
+// real recurrence b_k = c_k + 2 Re(w) b_{k+1} - |w|^2 b_{k+2} from b_K = b_{K+1} = 0,
+// then sum = b_0 - conj(w) b_1: two FMAs per segment instead of a complex product.
+template <class C>
+__device__ __forceinline__ Cd segment_sum(Cd w, double r2, int K, C&& ck) {
+  const double p2 = 2.0 * w.re;
+  double b1 = 0.0, b2 = 0.0;
+  for (int k = K - 1; k >= 0; --k) {
+    const double b0 = fma(p2, b1, fma(-r2, b2, ck(k)));
+    b2 = b1;
+    b1 = b0;
+  }
+  return {b1 - w.re * b2, w.im * b2};
+}
 
 // (e^{(i chi - a) L} - 1) / (i chi - a) with the span phase chi L given in turns
 // reduced modulo 1 (tp), so that a large chi L loses no accuracy.
@@ -109,18 +125,10 @@ __device__ __forceinline__ Cd upsilon_fp64(const LinkParams& p, double f1, doubl
     double s, c;
     sincospi(2.0 * tt, &s, &c);
     Cd w = {p.r * c, p.r * s};
-    Cd acc = {0.0, 0.0};
-    if (ck) {
-      for (int k = K - 1; k >= 0; --k) {
-        acc = cmul(acc, w);
-        acc.re += ck[k * ck_stride];
-      }
-    } else {
-      for (int k = K - 1; k >= 0; --k) {
-        acc = cmul(acc, w);
-        acc.re += p.seg.ck[k] * exp(-p.seg.zeta[k] * f3);
-      }
-    }
+    const double r2 = p.r * p.r;
+    Cd acc;
+    if (ck) acc = segment_sum(w, r2, K, [&](int k) { return ck[k * ck_stride]; });
+    else acc = segment_sum(w, r2, K, [&](int k) { return p.seg.ck[k] * exp(-p.seg.zeta[k] * f3); });
     // (w - 1)/(i chi - alpha) = (w - 1)(-alpha - i chi)/(alpha^2 + chi^2)
     double xr = w.re - 1.0, xi = w.im;
     double den = p.alpha * p.alpha + chi * chi;
@@ -157,12 +165,8 @@ __device__ __forceinline__ void type_mu(const LinkParams& p, const SpanType& ty,
     tt -= rint(tt);
     sincospi(2.0 * tt, &s, &c);
     const Cd w = {ty.r * c, ty.r * s};
-    Cd acc = {0.0, 0.0};
-    const int K = ty.seg.K;
-    for (int k = K - 1; k >= 0; --k) {
-      acc = cmul(acc, w);
-      acc.re += ck ? ck[k * 32] : ty.seg.ck[k] * exp(-ty.seg.zeta[k] * f3);
-    }
+    const Cd acc = segment_sum(w, ty.r * ty.r, ty.seg.K,
+                               [&](int k) { return ck ? ck[k * 32] : ty.seg.ck[k] * exp(-ty.seg.zeta[k] * f3); });
     const double xr = w.re - 1.0, xi = w.im;
     const double den = ty.alpha * ty.alpha + chi * chi;
     const Cd q = {(-ty.alpha * xr + chi * xi) / den, (-chi * xr - ty.alpha * xi) / den};
