@@ -487,6 +487,38 @@ def run_dz_sweep(args):
     return 0
 
 
+def run_f3d(args):
+    """The f-integrated (3-D) EGN of Eq. 17-21 on the 120-channel link: n_f
+    Gauss-Legendre nodes over each COI band, each a full evaluation with the
+    islands planned at that frequency (egn_nli_eta_3d, host API, wall clock),
+    and its difference from the white-NLI value.  One JSON line."""
+    import numpy as np
+    import torch
+    from paper_2412_11614_gb300 import _build, egn, workloads as W
+    _build.build()
+    torch.cuda.set_device(0)
+    wl = W.config_cl(n_ch=args.n_ch)
+    ln = egn.link_from_workload(wl)
+    prec = egn.EGN_PREC_FP32C if args.precision == "fp32c" else egn.EGN_PREC_FP64
+    opts = egn.make_opts(gl_order=wl.gl_order, dz_km=wl.dz_km, precision=prec, terms=egn.EGN_TERMS_EGN)
+    white, _ = ln.nli_eta(opts)
+    ln.nli_eta_3d(opts, args.f3d)  # warm-up (tables, workspace)
+    reps = max(1, args.steps)
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        e3, _ = ln.nli_eta_3d(opts, args.f3d)
+    dt = (time.perf_counter() - t0) / reps
+    diff = 10 * np.log10(e3 / white)
+    print(json.dumps({
+        "workload": f"{wl.n_ch}ch C+L link of the benchmark, f-integrated EGN, {args.f3d} Gauss-Legendre nodes "
+                    f"per COI band, {args.precision}",
+        "n_f": args.f3d, "seconds_per_evaluation": dt, "channel_evals_per_s": wl.n_ch / dt,
+        "f3d_minus_white_db": {"mean": float(diff.mean()), "min": float(diff.min()), "max": float(diff.max()),
+                               "centre": float(diff[wl.n_ch // 2]), "edge": float(diff[0])}}), flush=True)
+    ln.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -509,6 +541,8 @@ def main():
     ap.add_argument("--batch-random", action="store_true", help="the batch is seeded heterogeneous random links")
     ap.add_argument("--dz-sweep", action="store_true", help="segment length trade-off on Table I and II links")
     ap.add_argument("--gemm", type=int, default=0, metavar="G", help="time the surrogate's G^3 tensor-core GEMM")
+    ap.add_argument("--f3d", type=int, default=0, metavar="NF",
+                    help="time the f-integrated EGN with NF nodes per COI band against the white-NLI value")
     ap.add_argument("--surrogate", action="store_true", help="train and evaluate the MLP surrogate")
     ap.add_argument("--sur-train", type=int, default=4096)
     ap.add_argument("--sur-test", type=int, default=256)
@@ -518,6 +552,8 @@ def main():
     args = ap.parse_args()
     if args.surrogate:
         return run_surrogate(args)
+    if args.f3d:
+        return run_f3d(args)
     if args.dz_sweep:
         return run_dz_sweep(args)
     if args.gemm:

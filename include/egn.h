@@ -179,6 +179,16 @@ egn_status egn_island_count(const egn_link* link, long long* total, long long* p
  * workspace that is kept between calls. */
 egn_status egn_nli_eta(egn_link* link, const egn_opts* opts, double* eta_per_w2, double* pnli_w);
 
+/* The same with the integral over f of Eq. 17-21 taken literally instead of
+ * the white-NLI value R_n G(f_n): P_NLI,n = int over f in [f_n - R_n/2,
+ * f_n + R_n/2] of G(f) df by an n_f-point Gauss-Legendre rule (1 <= n_f <= 64),
+ * G(f) the 2-D island integral (Eq. 15 with D..H at COI frequency f divided by
+ * R_n), so P_NLI,n = sum_j (w_j / 2) P_NLI,n(f_n + x_j R_n / 2).  Every node is a
+ * full evaluation (islands planned for that f, all opts as for egn_nli_eta);
+ * n_f = 1 equals egn_nli_eta.  Synchronous; eta and pnli are host arrays of
+ * n_ch doubles (either may be NULL).  Cost: n_f evaluations. */
+egn_status egn_nli_eta_3d(egn_link* link, const egn_opts* opts, int n_f, double* eta_per_w2, double* pnli_w);
+
 /* Device variant: same computation, asynchronous on opts->stream, writing
  * eta_dev and pnli_dev (device arrays of n_ch doubles, either may be NULL) and
  * using the caller's device workspace of at least egn_workspace_size() bytes

@@ -88,6 +88,9 @@ typedef struct {
     double dz;          /* segment step Delta z [km] (segment form) */
     double int_tol;     /* relative tolerance of the adaptive integral form */
     int terms;          /* 0 = GN (D only), 1 = EGN (D + corrections) */
+    const double* f_off; /* per channel: offset of the frequency f at which the
+                            channel is evaluated as COI, from its centre [THz];
+                            NULL = 0 (the white-NLI reading) */
 } or_problem;
 
 /* ------------------------------------------------------------------------- */
@@ -345,10 +348,17 @@ double or_rc(double x, double R, double beta)
 
 static double or_width(const or_problem* pb, int n) { return pb->R[n] * (1.0 + pb->rolloff); }
 
-/* Frequency offset of the island: d = (nu_n1 - nu_n) + (nu_n2 - nu_n3). */
+/* The frequency f at which COI n is evaluated: its centre, plus f_off[n]. */
+static double or_fcoi(const or_problem* pb, int n)
+{
+    return pb->nu[n] + (pb->f_off ? pb->f_off[n] : 0.0);
+}
+
+/* Frequency offset of the island: d = (nu_n1 - f) + (nu_n2 - nu_n3), with f the
+ * COI's evaluation frequency (its centre unless f_off is set). */
 static double or_offset(const or_problem* pb, int n, int n1, int n2, int n3)
 {
-    return (pb->nu[n1] - pb->nu[n]) + (pb->nu[n2] - pb->nu[n3]);
+    return (pb->nu[n1] - or_fcoi(pb, n)) + (pb->nu[n2] - pb->nu[n3]);
 }
 
 /* Node rule.  Outer variable o with |o| <= A, inner variable t with |t| <= B,
@@ -448,7 +458,7 @@ static void or_walk(const or_problem* pb, int n, int n1, int n2, int n3, int ord
     double* ox = (double*)malloc(sizeof(double) * no);
     double* ow = (double*)malloc(sizeof(double) * no);
     or_gauss_legendre(no, ox, ow);
-    double f = pb->nu[n];
+    double f = or_fcoi(pb, n);
     for (int p = 0; p < np; ++p) {
         double pm = 0.5 * (e[p] + e[p + 1]), ph = 0.5 * (e[p + 1] - e[p]);
         for (int i = 0; i < no; ++i) {
@@ -532,7 +542,7 @@ void or_island_terms_midpoint(const or_problem* pb, int n, int n1, int n2, int n
     double R1 = pb->R[n1], R2 = pb->R[n2], R3 = pb->R[n3];
     double beta = pb->rolloff;
     double d = or_offset(pb, n, n1, n2, n3);
-    double f = pb->nu[n];
+    double f = or_fcoi(pb, n);
     double cf[5];
     or_coefs(pb, n, n1, n2, n3, cf);
     /* (w, u) grid: D, G, H */

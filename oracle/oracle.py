@@ -42,7 +42,7 @@ class OrProblem(C.Structure):
                 ("psi", _dp), ("rolloff", C.c_double), ("ptot", C.c_double),
                 ("btot", C.c_double), ("n_spans", C.c_int), ("spans", C.POINTER(OrSpan)),
                 ("gl_order", C.c_int), ("mu_form", C.c_int), ("dz", C.c_double),
-                ("int_tol", C.c_double), ("terms", C.c_int)]
+                ("int_tol", C.c_double), ("terms", C.c_int), ("f_off", _dp)]
 
 
 _lib = None
@@ -237,6 +237,33 @@ class Problem:
         if rc_ != 0:
             raise RuntimeError(f"or_eta failed: {rc_}")
         return eta, pn
+
+    def set_coi_offsets(self, off=None):
+        """Evaluate each COI n at f = its centre + off[n] [THz] (None: at the centre)."""
+        if off is None:
+            self._f_off = None
+            self.c.f_off = _dp()
+        else:
+            self._f_off = np.ascontiguousarray(off, dtype=np.float64)
+            assert self._f_off.shape == (self.n_ch,)
+            self.c.f_off = _ptr(self._f_off)
+
+    def eta_3d(self, n_f, coi=None):
+        """(eta, P_NLI) with the integral over f of Eq. 17-21 taken literally:
+        f over [-R_n/2, R_n/2] of COI n by an n_f-point Gauss-Legendre rule, the
+        2-D island integrals evaluated at each node (n_f = 1: the white-NLI
+        value R_n x G(f_n))."""
+        x, w = gauss_legendre(int(n_f))
+        pn = None
+        try:
+            for xj, wj in zip(x, w):
+                self.set_coi_offsets(0.5 * xj * self.R)
+                _, p = self.eta(coi)
+                pn = 0.5 * wj * p if pn is None else pn + 0.5 * wj * p
+        finally:
+            self.set_coi_offsets(None)
+        idx = np.arange(self.n_ch) if coi is None else np.asarray(coi).ravel()
+        return pn / self.P[idx] ** 3, pn
 
     def islands(self, n):
         cap = 3 * self.n_ch * self.n_ch + 16

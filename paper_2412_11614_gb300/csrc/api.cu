@@ -323,9 +323,15 @@ ChannelTable channel_table(const egn_link* l) {
   t.psi = b + 5 * s;
   t.nu_f = (const float*)(b + 6 * s);  // the seventh array holds nu_f[n_ch] then hw_f[n_ch]
   t.hw_f = t.nu_f + l->n_ch;
+  t.nu_coi = t.nu;
+  t.nu_coi_f = t.nu_f;
+  if (l->coi_shift) {
+    t.nu_coi = (const double*)l->d_coi.p;
+    t.nu_coi_f = (const float*)((const char*)l->d_coi.p + align256(l->n_ch * sizeof(double)));
+  }
   t.hwmax_f = 0.5f * (float)t.wmax;
-  double numax = 0.0;
-  for (double x : l->nu) numax = std::max(numax, std::fabs(x));
+  double numax = 0.0;  // COI frequencies lie within half a support of a centre
+  for (double x : l->nu) numax = std::max(numax, std::fabs(x) + 0.5 * t.wmax);
   // FP32 rounding of four centres, three half supports and five operations on
   // values up to 3 numax + 1.5 wmax: well inside 4e-6 (numax + wmax)
   t.plan_margin = (float)(4e-6 * (numax + t.wmax)) + 1e-30f;
@@ -428,6 +434,34 @@ egn_status run_step(egn_link* l, const egn_opts* o, const Workspace& ws, double*
   return EGN_OK;
 }
 
+// Island counts of the link's channel table (COI frequencies included) from the
+// planner's count pass: totals of the four lists and, if asked, per COI.
+egn_status count_islands(egn_link* l, PlanCounts* cnt, std::vector<long long>* per_coi) {
+  const int n_ch = l->n_ch;
+  size_t n_rows = (size_t)n_ch * n_ch;
+  size_t cnt_b = align256(4 * n_rows * sizeof(uint32_t)), off_b = align256(4 * (n_rows + 1) * sizeof(uint32_t));
+  DevBuf tmp;
+  cudaError_t e = tmp.ensure(cnt_b + off_b);
+  if (e != cudaSuccess) return fail(EGN_E_NOMEM, "cudaMalloc: %s", cudaGetErrorString(e));
+  Workspace w{};
+  w.row_cnt = (uint32_t*)tmp.p;
+  w.row_off = (uint32_t*)((char*)tmp.p + cnt_b);
+  e = launch_plan_count(channel_table(l), w, 0);
+  std::vector<uint32_t> off(4 * (n_rows + 1));
+  if (e == cudaSuccess) e = cudaMemcpy(off.data(), w.row_off, off.size() * sizeof(uint32_t), cudaMemcpyDeviceToHost);
+  tmp.release();
+  if (e != cudaSuccess) return fail(EGN_E_CUDA, "island count: %s", cudaGetErrorString(e));
+  cnt->n_isl = off[n_rows];
+  cnt->n_half = off[(n_rows + 1) + n_rows];
+  cnt->n_e = off[2 * (n_rows + 1) + n_rows];
+  cnt->n_f = off[3 * (n_rows + 1) + n_rows];
+  if (per_coi) {
+    per_coi->resize(n_ch);
+    for (int c = 0; c < n_ch; ++c) (*per_coi)[c] = (long long)off[(size_t)(c + 1) * n_ch] - off[(size_t)c * n_ch];
+  }
+  return EGN_OK;
+}
+
 egn_status wait_event(cudaEvent_t ev, int timeout_ms) {
   auto t0 = std::chrono::steady_clock::now();
   for (;;) {
@@ -525,6 +559,7 @@ void egn_link_destroy(egn_link* link) {
 
 egn_status egn_set_wdm(egn_link* l, int n_ch, const double* centre_hz, const double* rate, const double* power,
                        const double* phi, const double* psi, double rolloff) {
+  egn_status s_ = EGN_OK;
   if (!l) return fail(EGN_E_INVALID_ARG, "null link");
   if (n_ch < 1 || n_ch > 4096) return fail(EGN_E_INVALID_ARG, "n_ch %d not in [1, 4096]", n_ch);
   if (!centre_hz || !rate || !power || !phi || !psi) return fail(EGN_E_INVALID_ARG, "null channel array");
@@ -583,29 +618,15 @@ egn_status egn_set_wdm(egn_link* l, int n_ch, const double* centre_hz, const dou
   l->tab_dz = -1.0;  // P_tot and B_tot changed
   // count islands on the device
   l->n_ch = n_ch;
-  size_t n_rows = (size_t)n_ch * n_ch;
-  size_t cnt_b = align256(4 * n_rows * sizeof(uint32_t)), off_b = align256(4 * (n_rows + 1) * sizeof(uint32_t));
-  DevBuf tmp;
-  cudaError_t e = tmp.ensure(cnt_b + off_b);
-  if (e != cudaSuccess) { l->n_ch = 0; return fail(EGN_E_NOMEM, "cudaMalloc: %s", cudaGetErrorString(e)); }
-  Workspace w{};
-  w.row_cnt = (uint32_t*)tmp.p;
-  w.row_off = (uint32_t*)((char*)tmp.p + cnt_b);
-  e = launch_plan_count(channel_table(l), w, 0);
-  std::vector<uint32_t> off(4 * (n_rows + 1));
-  if (e == cudaSuccess) e = cudaMemcpy(off.data(), w.row_off, off.size() * sizeof(uint32_t), cudaMemcpyDeviceToHost);
-  tmp.release();
-  if (e != cudaSuccess) { l->n_ch = 0; return fail(EGN_E_CUDA, "island count: %s", cudaGetErrorString(e)); }
-  l->cnt.n_isl = off[n_rows];
-  l->cnt.n_half = off[(n_rows + 1) + n_rows];
-  l->cnt.n_e = off[2 * (n_rows + 1) + n_rows];
-  l->cnt.n_f = off[3 * (n_rows + 1) + n_rows];
-  l->per_coi.resize(n_ch);
-  for (int c = 0; c < n_ch; ++c) l->per_coi[c] = (long long)off[(size_t)(c + 1) * n_ch] - off[(size_t)c * n_ch];
+  s_ = count_islands(l, &l->cnt, &l->per_coi);
+  if (s_ != EGN_OK) {
+    l->n_ch = 0;
+    return s_;
+  }
   // pinned staging for host outputs
   if (l->h_stage) cudaFreeHost(l->h_stage);
   l->h_stage = nullptr;
-  e = pinned_alloc((void**)&l->h_stage, (2 * n_ch + 2) * sizeof(double));
+  cudaError_t e = pinned_alloc((void**)&l->h_stage, (2 * n_ch + 2) * sizeof(double));
   if (e != cudaSuccess) {
     l->h_stage = nullptr;
     l->n_ch = 0;
@@ -676,6 +697,53 @@ egn_status egn_nli_eta(egn_link* l, const egn_opts* o, double* eta, double* pnli
   if (status) return fail(EGN_E_CUDA, "device planner overflow (status %d)", status);
   if (eta) std::memcpy(eta, l->h_stage, n * sizeof(double));
   if (pnli) std::memcpy(pnli, l->h_stage + n, n * sizeof(double));
+  return EGN_OK;
+}
+
+egn_status egn_nli_eta_3d(egn_link* l, const egn_opts* o, int n_f, double* eta, double* pnli) {
+  egn_status s = check_opts(l, o);
+  if (s != EGN_OK) return s;
+  if (n_f < 1 || n_f > 64) return fail(EGN_E_INVALID_ARG, "n_f %d not in [1, 64]", n_f);
+  DeviceGuard g(l->device);
+  const int n = l->n_ch;
+  const size_t dbytes = align256(n * sizeof(double));
+  cudaStream_t st = (cudaStream_t)o->stream;
+  EGN_CUDA(cudaStreamSynchronize(st));  // nothing queued by an earlier call may still read d_coi
+  EGN_ALLOC(l->d_coi.ensure(dbytes + align256(n * sizeof(float))));
+  std::vector<double> x(n_f), w(n_f), acc(n, 0.0), pj(n), nc(n);
+  std::vector<float> ncf(n);
+  gauss_legendre(n_f, x.data(), w.data());
+  // every node is a full evaluation with the COI frequencies moved and the
+  // islands counted for them; the link's own counts and tables are restored after
+  struct Restore {
+    egn_link* l;
+    PlanCounts c;
+    ~Restore() {
+      l->cnt = c;
+      l->coi_shift = false;
+    }
+  } restore{l, l->cnt};
+  for (int j = 0; j < n_f; ++j) {
+    for (int i = 0; i < n; ++i) {
+      nc[i] = l->nu[i] + 0.5 * x[j] * l->R[i];
+      ncf[i] = (float)nc[i];
+    }
+    l->coi_shift = false;
+    EGN_CUDA(h2d(l->d_coi.p, nc.data(), n * sizeof(double)));
+    EGN_CUDA(h2d((char*)l->d_coi.p + dbytes, ncf.data(), n * sizeof(float)));
+    l->coi_shift = true;
+    PlanCounts cnt{};
+    s = count_islands(l, &cnt, nullptr);
+    if (s != EGN_OK) return s;
+    l->cnt = cnt;
+    s = egn_nli_eta(l, o, nullptr, pj.data());
+    if (s != EGN_OK) return s;
+    for (int i = 0; i < n; ++i) acc[i] += 0.5 * w[j] * pj[i];
+  }
+  for (int i = 0; i < n; ++i) {
+    if (pnli) pnli[i] = acc[i];
+    if (eta) eta[i] = acc[i] / (l->P[i] * l->P[i] * l->P[i]);
+  }
   return EGN_OK;
 }
 

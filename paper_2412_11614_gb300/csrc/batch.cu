@@ -69,7 +69,8 @@ void rebase(const T*& q, const void* old, size_t bytes, const void* nb) {
 void rebase_params(LinkParams& p, const egn_link* l, char* ch_copy, char* seg_copy, char* gl_copy) {
   ChannelTable& c = p.ch;
   for (const double** q : {&c.nu, &c.R, &c.W, &c.P, &c.phi, &c.psi}) rebase(*q, l->d_ch.p, l->d_ch.bytes, ch_copy);
-  for (const float** q : {&c.nu_f, &c.hw_f}) rebase(*q, l->d_ch.p, l->d_ch.bytes, ch_copy);
+  for (const double** q : {&c.nu_coi}) rebase(*q, l->d_ch.p, l->d_ch.bytes, ch_copy);
+  for (const float** q : {&c.nu_f, &c.hw_f, &c.nu_coi_f}) rebase(*q, l->d_ch.p, l->d_ch.bytes, ch_copy);
   auto seg = [&](egn::SegmentTables& t) {
     rebase(t.zeta, l->d_seg.p, l->d_seg.bytes, seg_copy);
     rebase(t.ck, l->d_seg.p, l->d_seg.bytes, seg_copy);

@@ -51,6 +51,11 @@ struct ChannelTable {
   const float* hw_f;
   float hwmax_f;
   float plan_margin;
+  // the frequency f at which each channel is evaluated as COI (FP64 and FP32):
+  // its centre (nu, nu_f) for the white-NLI reading, or centre + offset for a
+  // node of the f-integral of Eq. 17-21
+  const double* nu_coi;
+  const float* nu_coi_f;
 };
 
 // Gauss-Legendre tables for the three outer orders ceil(n/p), p = 1, 2, 3

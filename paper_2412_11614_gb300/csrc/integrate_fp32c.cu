@@ -97,7 +97,7 @@ __device__ __forceinline__ void batch_setup(const LinkParams& p, const uint64_t*
       int coi, n1, n2, n3;
       unpack_key(keys[isl], coi, n1, n2, n3);
       const ChannelTable& ch = p.ch;
-      double nu = ch.nu[coi], nu1 = ch.nu[n1], nu2 = ch.nu[n2], nu3 = ch.nu[n3];
+      double nu = ch.nu_coi[coi], nu1 = ch.nu[n1], nu2 = ch.nu[n2], nu3 = ch.nu[n3];
       double R = ch.R[coi], R1 = ch.R[n1], R2 = ch.R[n2], R3 = ch.R[n3];
       double d = (nu1 - nu) + (nu2 - nu3);
       Ordering g = make_ordering(ORD, ch.W[n1], ch.W[n2], ch.W[n3], d);

@@ -239,7 +239,7 @@ __global__ void __launch_bounds__(32) integrate_fp64_kernel(LinkParams p, const 
     long long isl = list ? (long long)list[it] : it;
     int coi, n1, n2, n3;
     unpack_key(keys[isl], coi, n1, n2, n3);
-    double nu = ch.nu[coi], nu1 = ch.nu[n1], nu2 = ch.nu[n2], nu3 = ch.nu[n3];
+    double nu = ch.nu_coi[coi], nu1 = ch.nu[n1], nu2 = ch.nu[n2], nu3 = ch.nu[n3];
     double R = ch.R[coi], R1 = ch.R[n1], R2 = ch.R[n2], R3 = ch.R[n3];
     double d = (nu1 - nu) + (nu2 - nu3);
     Ordering g = make_ordering(ORD, ch.W[n1], ch.W[n2], ch.W[n3], d);

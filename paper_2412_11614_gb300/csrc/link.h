@@ -137,7 +137,12 @@ struct egn_link {
   egn_host::DevBuf ws;
   double* h_stage = nullptr;  // [2 n_ch + 1]
   egn_host::DevBuf d_stage;
+  // COI evaluation frequencies of the f-integral (egn_nli_eta_3d): n_ch doubles,
+  // then n_ch floats; used by channel_table while coi_shift is set
+  egn_host::DevBuf d_coi;
+  bool coi_shift = false;
   ~egn_link() {
+    d_coi.release();
     d_ch.release();
     d_seg.release();
     d_gl.release();
@@ -168,5 +173,6 @@ cudaError_t integrate(const egn::LinkParams& p, int precision, const uint64_t* k
                       const uint32_t* f_idx, long long n_f, void* terms, cudaStream_t st, cudaEvent_t* ev);
 // Wait for an event with a host-side limit (0 = none).
 egn_status wait_event(cudaEvent_t ev, int timeout_ms);
+egn_status count_islands(egn_link* l, egn::PlanCounts* cnt, std::vector<long long>* per_coi);
 
 }  // namespace egn_host

@@ -1,7 +1,8 @@
 // planner.cu -- island planner on the device (Eq. 15-16).
 //
 // For every COI n and every pair (n1, n2) the islands are the channels n3 whose
-// support meets the f3 = f1 + f2 - f range with positive area.  In the island's
+// support meets the f3 = f1 + f2 - f range with positive area, f the frequency at
+// which COI n is evaluated (its centre, or a node of the f-integral).  In the island's
 // local coordinates (u, v, w offsets of f1, f2, f3 from their channel centres,
 // w = u + v + d with d = (nu_n1 - nu_n) + (nu_n2 - nu_n3)) the (outer w, inner u)
 // region is non-empty iff
@@ -22,7 +23,7 @@ namespace {
 constexpr int kPlanWarps = 8;  // warps per CTA in count/emit
 
 __device__ __forceinline__ bool island_exists(const ChannelTable& ch, int n, int n1, int n2, int n3) {
-  double d = (ch.nu[n1] - ch.nu[n]) + (ch.nu[n2] - ch.nu[n3]);
+  double d = (ch.nu[n1] - ch.nu_coi[n]) + (ch.nu[n2] - ch.nu[n3]);
   double hw = 0.5 * ch.W[n1] + 0.5 * ch.W[n2];
   double a = 0.5 * ch.W[n3];
   double lo = fmax(-a, d - hw);
@@ -48,7 +49,7 @@ __device__ __forceinline__ int lower_bound_f(const float* nu, int n, float x) {
 // alone, with a fraction of the FP64 work.
 template <class F>
 __device__ __forceinline__ void for_each_n3(const ChannelTable& ch, int n, int n1, int n2, F&& f) {
-  const float t = (ch.nu_f[n1] - ch.nu_f[n]) + ch.nu_f[n2];
+  const float t = (ch.nu_f[n1] - ch.nu_coi_f[n]) + ch.nu_f[n2];
   const float hw12 = ch.hw_f[n1] + ch.hw_f[n2];
   const float m = ch.plan_margin;
   const float reach = (hw12 + ch.hwmax_f) + 2.0f * m + 1e-6f;

@@ -72,6 +72,7 @@ def lib():
         L.egn_island_count.argtypes = [C.c_void_p, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong),
                                        C.POINTER(C.c_longlong), C.POINTER(C.c_longlong), C.POINTER(C.c_longlong)]
         L.egn_nli_eta.argtypes = [C.c_void_p, C.POINTER(egn_opts), _dp, _dp]
+        L.egn_nli_eta_3d.argtypes = [C.c_void_p, C.POINTER(egn_opts), C.c_int, _dp, _dp]
         L.egn_nli_eta_device.argtypes = [C.c_void_p, C.POINTER(egn_opts), C.c_void_p, C.c_size_t, C.c_void_p,
                                          C.c_void_p]
         L.egn_nli_eta_static.argtypes = [C.c_void_p, C.POINTER(egn_opts), C.c_void_p, C.c_void_p]
@@ -99,7 +100,7 @@ def lib():
                    "egn_nli_eta_device", "egn_island_terms", "egn_plan_islands", "egn_format_moments",
                    "egn_gauss_legendre", "egn_set_profiling", "egn_last_timings", "egn_nli_eta_static", "egn_set_tuning",
                    "egn_batch_create", "egn_batch_launch", "egn_batch_outputs", "egn_batch_read", "egn_nli_eta_batch",
-                   "egn_autotune"):
+                   "egn_autotune", "egn_nli_eta_3d"):
             getattr(L, fn).restype = C.c_int
         _lib = L
     return _lib
@@ -185,6 +186,15 @@ class Link:
         eta = np.zeros(self.n_ch)
         pn = np.zeros(self.n_ch)
         _check(lib().egn_nli_eta(self.h, C.byref(opts), eta.ctypes.data_as(_dp), pn.ctypes.data_as(_dp)))
+        return eta, pn
+
+    def nli_eta_3d(self, opts: egn_opts, n_f: int):
+        """f-integrated (3-D) EGN: (eta, P_NLI) with the COI band integrated by an
+        n_f-point Gauss-Legendre rule (n_f = 1: the white-NLI value)."""
+        eta = np.zeros(self.n_ch)
+        pn = np.zeros(self.n_ch)
+        _check(lib().egn_nli_eta_3d(self.h, C.byref(opts), int(n_f), eta.ctypes.data_as(_dp),
+                                    pn.ctypes.data_as(_dp)))
         return eta, pn
 
     def nli_eta_device(self, opts: egn_opts, workspace, eta_dev=None, pnli_dev=None):
