@@ -101,6 +101,7 @@ size_t workspace_bytes(int n_ch, const PlanCounts& c, int precision) {
   b += align256((size_t)c.n_f * sizeof(uint32_t));
   b += align256(4 * n_rows * sizeof(uint32_t));
   b += align256(4 * (n_rows + 1) * sizeof(uint32_t));
+  b += align256(4 * sizeof(unsigned long long));
   b += align256(5 * (size_t)c.n_isl * tsz);
   b += align256((size_t)n_ch * sizeof(double));
   b += align256((size_t)n_ch * sizeof(double));
@@ -125,6 +126,8 @@ Workspace carve_workspace(void* base, int n_ch, const PlanCounts& c, int precisi
   p += align256(4 * n_rows * sizeof(uint32_t));
   w.row_off = (uint32_t*)p;
   p += align256(4 * (n_rows + 1) * sizeof(uint32_t));
+  w.row_tot = (unsigned long long*)p;
+  p += align256(4 * sizeof(unsigned long long));
   w.terms = (void*)p;
   p += align256(5 * (size_t)c.n_isl * tsz);
   w.out_eta = (double*)p;
@@ -441,16 +444,22 @@ egn_status count_islands(egn_link* l, PlanCounts* cnt, std::vector<long long>* p
   size_t n_rows = (size_t)n_ch * n_ch;
   size_t cnt_b = align256(4 * n_rows * sizeof(uint32_t)), off_b = align256(4 * (n_rows + 1) * sizeof(uint32_t));
   DevBuf tmp;
-  cudaError_t e = tmp.ensure(cnt_b + off_b);
+  cudaError_t e = tmp.ensure(cnt_b + off_b + 4 * sizeof(unsigned long long));
   if (e != cudaSuccess) return fail(EGN_E_NOMEM, "cudaMalloc: %s", cudaGetErrorString(e));
   Workspace w{};
   w.row_cnt = (uint32_t*)tmp.p;
   w.row_off = (uint32_t*)((char*)tmp.p + cnt_b);
+  w.row_tot = (unsigned long long*)((char*)tmp.p + cnt_b + off_b);
   e = launch_plan_count(channel_table(l), w, 0);
   std::vector<uint32_t> off(4 * (n_rows + 1));
+  unsigned long long tot[4] = {};
   if (e == cudaSuccess) e = cudaMemcpy(off.data(), w.row_off, off.size() * sizeof(uint32_t), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemcpy(tot, w.row_tot, sizeof tot, cudaMemcpyDeviceToHost);
   tmp.release();
   if (e != cudaSuccess) return fail(EGN_E_CUDA, "island count: %s", cudaGetErrorString(e));
+  // island indices and list offsets are 32-bit
+  if (tot[0] > 0xffffffffull)
+    return fail(EGN_E_UNSUPPORTED, "%llu islands: more than 2^32 - 1 (too many channels for one evaluation)", tot[0]);
   cnt->n_isl = off[n_rows];
   cnt->n_half = off[(n_rows + 1) + n_rows];
   cnt->n_e = off[2 * (n_rows + 1) + n_rows];

@@ -159,6 +159,7 @@ struct Workspace {
   uint32_t* f_idx;      // [n_f]
   uint32_t* row_cnt;    // [4 * n_rows]
   uint32_t* row_off;    // [4 * (n_rows + 1)]
+  unsigned long long* row_tot;  // [4] the four list lengths in 64 bits (overflow check)
   void* terms;          // [5 * n_isl] of double (FP64) or float (FP32C), term-major
   double* out_eta;      // [n_ch] scratch outputs when the caller passes none
   double* out_pnli;     // [n_ch]

@@ -100,9 +100,12 @@ __global__ void plan_count_kernel(ChannelTable a, uint32_t* row_cnt, int n_rows)
 }
 
 // Exclusive scan of the four count arrays (one CTA of 1024 threads, each thread
-// a contiguous chunk).  row_off[a * (n_rows + 1) + n_rows] is the total.
-__global__ void plan_scan_kernel(const uint32_t* row_cnt, uint32_t* row_off, int n_rows) {
+// a contiguous chunk).  row_off[a * (n_rows + 1) + n_rows] is the total, and
+// row_tot[a] the same total in 64 bits (the host refuses totals above 2^32 - 1).
+__global__ void plan_scan_kernel(const uint32_t* row_cnt, uint32_t* row_off, unsigned long long* row_tot,
+                                 int n_rows) {
   __shared__ uint32_t warp_sum[32];
+  __shared__ unsigned long long tot64;
   const int T = blockDim.x;
   int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   int chunk = (n_rows + T - 1) / T;
@@ -111,7 +114,14 @@ __global__ void plan_scan_kernel(const uint32_t* row_cnt, uint32_t* row_off, int
     uint32_t* out = row_off + (size_t)arr * (n_rows + 1);
     int b = tid * chunk, e = min(b + chunk, n_rows);
     uint32_t s = 0;
-    for (int i = b; i < e; ++i) s += in[i];
+    unsigned long long s64 = 0;
+    for (int i = b; i < e; ++i) {
+      s += in[i];
+      s64 += in[i];
+    }
+    if (tid == 0) tot64 = 0;
+    __syncthreads();
+    atomicAdd(&tot64, s64);
     // block exclusive scan of s
     uint32_t x = s;
     for (int o = 1; o < 32; o <<= 1) {
@@ -135,6 +145,7 @@ __global__ void plan_scan_kernel(const uint32_t* row_cnt, uint32_t* row_off, int
       base += in[i];
     }
     if (tid == T - 1) out[n_rows] = warp_sum[(T >> 5) - 1];
+    if (tid == 0) row_tot[arr] = tot64;
     __syncthreads();
   }
 }
@@ -196,7 +207,7 @@ cudaError_t launch_plan_count(const ChannelTable& ch, const Workspace& ws, cudaS
   plan_count_kernel<<<blocks, threads, 0, st>>>(ch, ws.row_cnt, n_rows);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  plan_scan_kernel<<<1, 1024, 0, st>>>(ws.row_cnt, ws.row_off, n_rows);
+  plan_scan_kernel<<<1, 1024, 0, st>>>(ws.row_cnt, ws.row_off, ws.row_tot, n_rows);
   return cudaGetLastError();
 }
 

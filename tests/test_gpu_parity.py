@@ -318,6 +318,27 @@ def test_more_than_64_differing_spans_unsupported(egn, workloads):
     assert ei.value.status == egn.EGN_E_UNSUPPORTED
 
 
+def test_more_than_2_32_islands_refused(egn, workloads):
+    """1700 channels on a 75 GHz grid hold about 2 x 1700^3 = 9.8e9 islands: the
+    planner's 64-bit totals exceed the 32-bit island indices, so egn_set_wdm refuses
+    the comb (and leaves the link without a WDM); 1200 channels (3.5e9) are counted."""
+    wl = workloads.config_small(n_ch=1700, gl_order=8)
+    ln = egn.Link(wl.spans)
+    n = len(wl.centre_hz)
+    phi = np.zeros(n)
+    with pytest.raises(egn.EgnError) as ei:
+        ln.set_wdm(wl.centre_hz, wl.symbol_rate_baud, wl.launch_power_w, phi, phi, wl.rolloff)
+    assert ei.value.status == egn.EGN_E_UNSUPPORTED and "2^32" in str(ei.value)
+    with pytest.raises(egn.EgnError) as ei:
+        ln.nli_eta(egn.make_opts(gl_order=8))
+    assert ei.value.status == egn.EGN_E_STATE
+    wl2 = workloads.config_small(n_ch=1200, gl_order=8)
+    ln.set_wdm(wl2.centre_hz, wl2.symbol_rate_baud, wl2.launch_power_w, np.zeros(1200), np.zeros(1200), wl2.rolloff)
+    total = ln.island_count()[0]
+    assert 3.0e9 < total < 2 ** 32
+    ln.close()
+
+
 # --------------------------------------------------------------------------- FP32C path
 
 FP32C_DB = 1e-3      # small workloads
