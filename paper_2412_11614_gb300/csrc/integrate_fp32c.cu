@@ -276,6 +276,13 @@ __host__ __device__ constexpr int rows_max(int nt) { return nt == 64 ? 32 : kRow
 // Floats of the inner-node arrays at the head of the main kernel's dynamic shared
 // memory (6 per node, rounded up to 16 bytes).
 __host__ __device__ constexpr int node_floats(int n) { return (6 * n + 3) & ~3; }
+// Threads per row of the point passes: the smallest power of two whose kp point
+// slots each cover n inner nodes.
+__host__ __device__ inline int threads_per_row(int n, int kp) {
+  int t = 1;
+  while (t * kp < n) t <<= 1;
+  return t;
+}
 
 // Fixed-order sum of the per-warp partial sums of a CTA.
 template <int NW>
@@ -299,15 +306,24 @@ integrate_fp32c_kernel(LinkParams p, const uint64_t* __restrict__ keys, const ui
   __shared__ RowSm<rows_max(NT)> rs;
   constexpr int NW = NT / 32;
   __shared__ float red[4][NW];
-  // dynamic: inner nodes {x head, x tail, x^2 head, x^2 tail}[n], {x^3, w}[n], then
-  // (DW only) the [rows_per_chunk][kpad] c_k of the chunk's rows, 16-byte aligned
-  extern __shared__ __align__(16) float dyn[];
-  float4* const nx4 = reinterpret_cast<float4*>(dyn);
-  float2* const nx2 = reinterpret_cast<float2*>(dyn + 4 * p.gl.n);
-  float* const tab = dyn + node_floats(p.gl.n);
-
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const int n = p.gl.n;
+  // threads per row (power of two), row slot and point slot of this thread; the
+  // tpr x KP point slots of a row cover the n inner nodes
+  const int tpr = threads_per_row(n, KP);
+  const int npad = tpr * KP;
+  const int rows_per_pass = NT / tpr;
+  const int lr = tid & (tpr - 1);
+  const int rsub = tid / tpr;
+  // dynamic: inner nodes {x head, x tail, x^2 head, x^2 tail}[npad], {x^3, w}[npad]
+  // (nodes n..npad-1 are x = 0 with weight 0, so no point slot needs a bounds
+  // test), then (DW only) the [rows_per_chunk][kpad] c_k of the chunk's rows,
+  // 16-byte aligned
+  extern __shared__ __align__(16) float dyn[];
+  float4* const nx4 = reinterpret_cast<float4*>(dyn);
+  float2* const nx2 = reinterpret_cast<float2*>(dyn + 4 * npad);
+  float* const tab = dyn + node_floats(npad);
+
   const int K = p.seg.K;
   const float Kf = (float)K, invK = 1.0f / (float)K;
   const float alpha = (float)p.alpha, alpha2 = alpha * alpha;
@@ -322,17 +338,16 @@ integrate_fp32c_kernel(LinkParams p, const uint64_t* __restrict__ keys, const ui
   const float k4 = (float)(4.0 * kPi * kPi);
   const float pib3 = (float)(kPi * p.beta3), b2f = (float)p.beta2;
   const float pi_f = 3.14159265358979f;
-  // threads per row (power of two), row slot and point slot of this thread
-  int tpr = 1;
-  while (tpr * KP < n) tpr <<= 1;
-  const int rows_per_pass = NT / tpr;
-  const int lr = tid & (tpr - 1);
-  const int rsub = tid / tpr;
 
-  for (int j = tid; j < n; j += NT) {
-    const float xh = p.gl.xh[1][j], xl = p.gl.xl[1][j];
-    nx4[j] = make_float4(xh, xl, p.gl.x2h[1][j], p.gl.x2l[1][j]);
-    nx2[j] = make_float2(xh * p.gl.x2h[1][j], p.gl.wf[1][j]);
+  for (int j = tid; j < npad; j += NT) {
+    if (j < n) {
+      const float xh = p.gl.xh[1][j], xl = p.gl.xl[1][j];
+      nx4[j] = make_float4(xh, xl, p.gl.x2h[1][j], p.gl.x2l[1][j]);
+      nx2[j] = make_float2(xh * p.gl.x2h[1][j], p.gl.wf[1][j]);
+    } else {
+      nx4[j] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+      nx2[j] = make_float2(0.0f, 0.0f);
+    }
   }
 
   for (long long b0 = (long long)blockIdx.x * NB; b0 < n_items; b0 += (long long)gridDim.x * NB) {
@@ -433,10 +448,8 @@ integrate_fp32c_kernel(LinkParams p, const uint64_t* __restrict__ keys, const ui
 #pragma unroll
             for (int m = 0; m < KP; ++m) {
               const int j = lr + tpr * m;
-              const bool jok = j < n;
-              const int jj = jok ? j : 0;
-              const float4 x4 = nx4[jj];
-              const float2 x2 = nx2[jj];
+              const float4 x4 = nx4[j];
+              const float2 x2 = nx2[j];
               float th, ph;
               point_phase(qa, qb, x4, x2.x, Kf, invK, th, ph);
               const float sh = __sinf(pi_f * th);
@@ -446,7 +459,7 @@ integrate_fp32c_kernel(LinkParams p, const uint64_t* __restrict__ keys, const ui
               const float xh = x4.x;
               const float chi = fmaf(ab.y, xh, ab.x) * fmaf(ab.w, xh, ab.z) * fmaf(kc.y, xh, kc.x);
               const float t = fmaf(ih, xh, im);
-              const float wgt = (jok ? x2.y : 0.0f) * rc_f(t, sa1, si1) * rc_f(ow.x - t, sa2, si2);
+              const float wgt = x2.y * rc_f(t, sa1, si1) * rc_f(ow.x - t, sa2, si2);
               float sd, sn;
               array_sines(pi_f * ph, N, sd, sn);
               const float den = (sd * sd) * fmaf(chi, chi, alpha2);
@@ -478,12 +491,10 @@ integrate_fp32c_kernel(LinkParams p, const uint64_t* __restrict__ keys, const ui
 #pragma unroll
           for (int m = 0; m < KP; ++m) {
             const int j = lr + tpr * m;
-            const bool jok = j < n;
-            const int jj = jok ? j : 0;
-            const float4 x4 = nx4[jj];
-            const float2 x2 = nx2[jj];
+            const float4 x4 = nx4[j];
+            const float2 x2 = nx2[j];
             const float xh = x4.x;
-            const float wnode = jok ? x2.y : 0.0f;
+            const float wnode = x2.y;
             float th, ph;
             point_phase(qa, qb, x4, x2.x, Kf, invK, th, ph);
             // w = r e^{2 pi i th} from the half angle (keeps w - 1 accurate)
@@ -641,7 +652,8 @@ cudaError_t launch_one(const LinkParams& p, const uint64_t* keys, const uint32_t
     if (rows > rows_max(NT)) rows = rows_max(NT);
     if (rows < 1) rows = 1;
   }
-  size_t smem = ((size_t)node_floats(p.gl.n) + (ORD == ORD_DW ? (size_t)rows * kpad : 0)) * sizeof(float);
+  const int npad = threads_per_row(p.gl.n, KP) * KP;
+  size_t smem = ((size_t)node_floats(npad) + (ORD == ORD_DW ? (size_t)rows * kpad : 0)) * sizeof(float);
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -649,7 +661,7 @@ cudaError_t launch_one(const LinkParams& p, const uint64_t* keys, const uint32_t
   static unsigned long long attr_done = 0;
   if (!(attr_done >> (dev & 63) & 1ull)) {
     cudaError_t e = cudaFuncSetAttribute(integrate_fp32c_kernel<ORD, KP, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (node_floats(kMaxGl) + kTabFloats) * (int)sizeof(float));
+                                         (node_floats(2 * kMaxGl) + kTabFloats) * (int)sizeof(float));
     if (e != cudaSuccess) return e;
     attr_done |= 1ull << (dev & 63);
   }

@@ -105,7 +105,7 @@ __global__ void plan_count_kernel(ChannelTable a, uint32_t* row_cnt, int n_rows)
 __global__ void plan_scan_kernel(const uint32_t* row_cnt, uint32_t* row_off, unsigned long long* row_tot,
                                  int n_rows) {
   __shared__ uint32_t warp_sum[32];
-  __shared__ unsigned long long tot64;
+  __shared__ unsigned long long warp_sum64[32];
   const int T = blockDim.x;
   int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   int chunk = (n_rows + T - 1) / T;
@@ -119,9 +119,8 @@ __global__ void plan_scan_kernel(const uint32_t* row_cnt, uint32_t* row_off, uns
       s += in[i];
       s64 += in[i];
     }
-    if (tid == 0) tot64 = 0;
-    __syncthreads();
-    atomicAdd(&tot64, s64);
+    for (int o = 16; o > 0; o >>= 1) s64 += __shfl_xor_sync(0xffffffffu, s64, o);
+    if (lane == 0) warp_sum64[wid] = s64;
     // block exclusive scan of s
     uint32_t x = s;
     for (int o = 1; o < 32; o <<= 1) {
@@ -145,7 +144,11 @@ __global__ void plan_scan_kernel(const uint32_t* row_cnt, uint32_t* row_off, uns
       base += in[i];
     }
     if (tid == T - 1) out[n_rows] = warp_sum[(T >> 5) - 1];
-    if (tid == 0) row_tot[arr] = tot64;
+    if (tid == 0) {
+      unsigned long long t64 = 0;
+      for (int w = 0; w < (T >> 5); ++w) t64 += warp_sum64[w];
+      row_tot[arr] = t64;
+    }
     __syncthreads();
   }
 }
