@@ -102,6 +102,8 @@ size_t workspace_bytes(int n_ch, const PlanCounts& c, int precision) {
   b += align256(4 * n_rows * sizeof(uint32_t));
   b += align256(4 * (n_rows + 1) * sizeof(uint32_t));
   b += align256(4 * sizeof(unsigned long long));
+  b += align256((size_t)c.n_half * sizeof(uint32_t));
+  b += 2 * align256(4 * (size_t)n_ch * sizeof(uint32_t));
   b += align256(5 * (size_t)c.n_isl * tsz);
   b += align256((size_t)n_ch * sizeof(double));
   b += align256((size_t)n_ch * sizeof(double));
@@ -128,6 +130,12 @@ Workspace carve_workspace(void* base, int n_ch, const PlanCounts& c, int precisi
   p += align256(4 * (n_rows + 1) * sizeof(uint32_t));
   w.row_tot = (unsigned long long*)p;
   p += align256(4 * sizeof(unsigned long long));
+  w.d_idx = (uint32_t*)p;
+  p += align256((size_t)c.n_half * sizeof(uint32_t));
+  w.grp_cnt = (uint32_t*)p;
+  p += align256(4 * (size_t)n_ch * sizeof(uint32_t));
+  w.grp_off = (uint32_t*)p;
+  p += align256(4 * (size_t)n_ch * sizeof(uint32_t));
   w.terms = (void*)p;
   p += align256(5 * (size_t)c.n_isl * tsz);
   w.out_eta = (double*)p;
@@ -381,8 +389,8 @@ LinkParams link_params(const egn_link* l, const egn_opts* o, int all_terms) {
   return p;
 }
 
-// Integrator passes: D/G/H over the half list (or every island of `keys` when
-// h_idx is null), then E and F over their lists (or over every island when
+// Integrator passes: D/G/H over the half list in any order (the planner's grouped
+// copy of it; every island of `keys` when h_idx is null), then E and F over their lists (or over every island when
 // all_terms is set).  ev, if given, is recorded after each pass.
 cudaError_t integrate(const LinkParams& p, int precision, const uint64_t* keys, long long n_isl,
                       const uint32_t* h_idx, long long n_half, const uint32_t* e_idx, long long n_e,
@@ -426,7 +434,7 @@ egn_status run_step(egn_link* l, const egn_opts* o, const Workspace& ws, double*
   EGN_CUDA(launch_plan(ch, ws, st));
   if (ev) EGN_CUDA(cudaEventRecord(ev[1], st));
   LinkParams p = link_params(l, o, 0);
-  EGN_CUDA(integrate(p, o->precision, ws.keys, l->cnt.n_isl, ws.h_idx, l->cnt.n_half, ws.e_idx, l->cnt.n_e,
+  EGN_CUDA(integrate(p, o->precision, ws.keys, l->cnt.n_isl, ws.d_idx, l->cnt.n_half, ws.e_idx, l->cnt.n_e,
                      ws.f_idx, l->cnt.n_f, ws.terms, st, ev ? ev + 2 : nullptr));
   EGN_CUDA(launch_assemble(ch, half_offsets(ws, l->n_ch), ws.keys, ws.h_idx, l->cnt.n_isl, ws.terms, o->precision,
                            o->terms, eta, pnli, st));
@@ -1044,7 +1052,7 @@ extern "C" egn_status egn_nli_eta_static(egn_link* l, const egn_opts* o, double*
   EGN_LAUNCH_GATE();
   EGN_CUDA(cudaMemsetAsync(ws.status, 0, sizeof(int), st));  // the array keeps the last call's contents
   EGN_CUDA(launch_plan(ch, ws, st));
-  EGN_CUDA(integrate(p, o->precision, ws.keys, l->cnt.n_isl, ws.h_idx, l->cnt.n_half, ws.e_idx, l->cnt.n_e, ws.f_idx,
+  EGN_CUDA(integrate(p, o->precision, ws.keys, l->cnt.n_isl, ws.d_idx, l->cnt.n_half, ws.e_idx, l->cnt.n_e, ws.f_idx,
                      l->cnt.n_f, ws.terms, st, nullptr));
   EGN_CUDA(launch_assemble(ch, half_offsets(ws, l->n_ch), ws.keys, ws.h_idx, l->cnt.n_isl, ws.terms, o->precision,
                            o->terms, eta_dev, pnli_dev, st));

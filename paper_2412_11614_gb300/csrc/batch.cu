@@ -133,7 +133,7 @@ egn_status enqueue_link(egn_batch* b, size_t i, cudaStream_t s) {
   EGN_LAUNCH_GATE();
   EGN_CUDA(cudaMemsetAsync(ws.status, 0, sizeof(int), s));
   EGN_CUDA(egn::launch_plan(L.ch, ws, s));
-  EGN_CUDA(integrate(L.p, b->opts.precision, ws.keys, L.cnt.n_isl, ws.h_idx, L.cnt.n_half, ws.e_idx, L.cnt.n_e,
+  EGN_CUDA(integrate(L.p, b->opts.precision, ws.keys, L.cnt.n_isl, ws.d_idx, L.cnt.n_half, ws.e_idx, L.cnt.n_e,
                      ws.f_idx, L.cnt.n_f, ws.terms, s, nullptr));
   EGN_CUDA(egn::launch_assemble(L.ch, half_offsets(ws, L.n_ch), ws.keys, ws.h_idx, L.cnt.n_isl, ws.terms,
                                 b->opts.precision, b->opts.terms, b->eta() + b->off[i], b->pnli() + b->off[i], s));

@@ -155,6 +155,9 @@ struct PlanCounts {
 struct Workspace {
   uint64_t* keys;       // [n_isl] every island, (COI, n1, n2, n3) lexicographic
   uint32_t* h_idx;      // [n_half] island indices with n1 <= n2
+  uint32_t* d_idx;      // [n_half] the same islands grouped by (n3, n1 + n2 - n - n3): the D/G/H work list
+  uint32_t* grp_cnt;    // [4 n_ch] group sizes, then the groups' write cursors
+  uint32_t* grp_off;    // [4 n_ch] group offsets in d_idx
   uint32_t* e_idx;      // [n_e]
   uint32_t* f_idx;      // [n_f]
   uint32_t* row_cnt;    // [4 * n_rows]

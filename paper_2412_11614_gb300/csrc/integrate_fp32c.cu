@@ -306,8 +306,12 @@ integrate_fp32c_kernel(LinkParams p, const uint64_t* __restrict__ keys, const ui
   __shared__ RowSm<rows_max(NT)> rs;
   constexpr int NW = NT / 32;
   __shared__ float red[4][NW];
+  // the rows the c_k table holds (DW): their f3 in FP32 and their number (-1: none)
+  __shared__ float tab_f3[rows_max(NT)];
+  __shared__ int tab_rows;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const int n = p.gl.n;
+  if (tid == 0) tab_rows = -1;  // read after the first batch barrier
   // threads per row (power of two), row slot and point slot of this thread; the
   // tpr x KP point slots of a row cover the n inner nodes
   const int tpr = threads_per_row(n, KP);
@@ -371,6 +375,7 @@ integrate_fp32c_kernel(LinkParams p, const uint64_t* __restrict__ keys, const ui
         const int rc = min(rows_per_chunk, rows - c0);
         // ---- row constants in double-float, one row per thread: the rows fill whole
         // warps (rc <= NT), so the idle warps issue nothing
+        bool same_row = true;  // DW: this row's f3 equals the table's row rr
         {
           const int rr = tid;
           if (rr < rc) {
@@ -392,17 +397,26 @@ integrate_fp32c_kernel(LinkParams p, const uint64_t* __restrict__ keys, const ui
             rs.kc[rr] = make_float4(k4 * fmaf(pib3, s0f, b2f), k4 * pib3 * s1f, imf, ihf);
             rs.ow[rr] = make_float4(ORD == ORD_DW ? of - dfl : of, wo * ihf * hout, wo * ihf, hout);
             const float nu3 = bs.nu3[ib];
-            if (ORD == ORD_DW) rs.f3[rr] = make_float4(nu3 + of, 0.0f, wo, 0.0f);
-            else rs.f3[rr] = make_float4(nu3 + (imf + of + dfl), ihf, wo, 0.0f);
+            if (ORD == ORD_DW) {
+              const float f3v = nu3 + of;
+              rs.f3[rr] = make_float4(f3v, 0.0f, wo, 0.0f);
+              same_row = tab_rows == rc && tab_f3[rr] == f3v;
+            } else {
+              rs.f3[rr] = make_float4(nu3 + (imf + of + dfl), ihf, wo, 0.0f);
+            }
           }
         }
-        __syncthreads();
+        // the c_k table depends only on the rows' f3 (and the launch's C_k, zeta_k):
+        // when every row matches, the table already holds this chunk's values
+        const bool keep = ORD == ORD_DW ? __syncthreads_and(same_row) != 0 : (__syncthreads(), false);
         // ---- c_k tables of the chunk's rows (DW): C_k 2^{-zeta_k log2(e) f3}
         // A task is four consecutive columns of one row (one 16-byte store); rounds
         // of up to NT column groups, and a round of gn < NT groups gives each group
         // NT / gn threads that split the rows.  The four C_k and zeta_k stay in
         // registers; columns K..kpad-1 (padding, never read) get C_k = 0.
-        if (ORD == ORD_DW) {
+        // It is rebuilt only when some row's f3 differs from the rows it holds (the
+        // work list groups islands with equal outer nodes).
+        if (ORD == ORD_DW && !keep) {
           const int ng = kpad >> 2;
           for (int g0 = 0; g0 < ng; g0 += NT) {
             const int gn = min(NT, ng - g0);
@@ -428,6 +442,9 @@ integrate_fp32c_kernel(LinkParams p, const uint64_t* __restrict__ keys, const ui
             }
           }
           __syncthreads();
+          // read again only in the next chunk's row phase, after the chunk's last barrier
+          if (tid < rc) tab_f3[tid] = rs.f3[tid].x;
+          if (tid == 0) tab_rows = rc;
         }
         // ---- points
         for (int rb = 0; rb < rc; rb += rows_per_pass) {

@@ -15,6 +15,8 @@
 // the island list comes out in (COI, n1, n2, n3) lexicographic order together
 // with three index lists: the half list (n1 <= n2), the E list (n1 == n3,
 // n1 <= n2) and the F list (n2 == n3, n1 < n2).
+#include <algorithm>
+
 #include "egn_internal.h"
 
 namespace egn {
@@ -201,6 +203,68 @@ __global__ void plan_emit_kernel(ChannelTable a, const uint32_t* row_off, int n_
   }
 }
 
+// ---- the D/G/H work list: the half list grouped by (n3, n1 + n2 - n - n3),
+// which on a uniform grid is (n3, -l): the islands of a group have the same
+// outer nodes f3, so consecutive islands can share the c_k tables of their rows.
+// A counting sort with atomic cursors: the order inside a group is arbitrary,
+// which changes no result (every island is integrated on its own).
+__device__ __forceinline__ int dw_group(uint64_t key) {
+  int c, a, b, d;
+  unpack_key(key, c, a, b, d);
+  int t = a + b - c - d + 1;
+  t = t < 0 ? 0 : (t > 3 ? 3 : t);
+  return 4 * d + t;
+}
+
+__global__ void group_count_kernel(const uint64_t* keys, const uint32_t* h_idx, long long n_half, uint32_t* cnt) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n_half; i += (long long)gridDim.x * blockDim.x)
+    atomicAdd(&cnt[dw_group(keys[h_idx[i]])], 1u);
+}
+
+// Exclusive scan of the group sizes (one CTA), then the sizes are zeroed to serve
+// as write cursors.
+__global__ void group_scan_kernel(uint32_t* cnt, uint32_t* off, int ng) {
+  __shared__ uint32_t warp_sum[32];
+  const int T = blockDim.x;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const int chunk = (ng + T - 1) / T;
+  const int b = tid * chunk, e = min(b + chunk, ng);
+  uint32_t s = 0;
+  for (int i = b; i < e; ++i) s += cnt[i];
+  uint32_t x = s;
+  for (int o = 1; o < 32; o <<= 1) {
+    uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) warp_sum[wid] = x;
+  __syncthreads();
+  if (wid == 0) {
+    uint32_t v = (lane < (T >> 5)) ? warp_sum[lane] : 0;
+    for (int o = 1; o < 32; o <<= 1) {
+      uint32_t y = __shfl_up_sync(0xffffffffu, v, o);
+      if (lane >= o) v += y;
+    }
+    warp_sum[lane] = v;
+  }
+  __syncthreads();
+  uint32_t base = (wid > 0 ? warp_sum[wid - 1] : 0) + x - s;
+  for (int i = b; i < e; ++i) {
+    off[i] = base;
+    base += cnt[i];
+    cnt[i] = 0;
+  }
+}
+
+__global__ void group_scatter_kernel(const uint64_t* keys, const uint32_t* h_idx, long long n_half,
+                                     const uint32_t* off, uint32_t* cur, uint32_t* d_idx, int* status) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n_half; i += (long long)gridDim.x * blockDim.x) {
+    const uint32_t isl = h_idx[i];
+    const int g = dw_group(keys[isl]);
+    const long long at = (long long)off[g] + atomicAdd(&cur[g], 1u);
+    if (at < n_half) d_idx[at] = isl; else atomicOr(status, 16);
+  }
+}
+
 }  // namespace
 
 cudaError_t launch_plan_count(const ChannelTable& ch, const Workspace& ws, cudaStream_t st) {
@@ -221,6 +285,19 @@ cudaError_t launch_plan(const ChannelTable& ch, const Workspace& ws, cudaStream_
   int threads = kPlanWarps * 32;
   int blocks = (n_rows + kPlanWarps - 1) / kPlanWarps;
   plan_emit_kernel<<<blocks, threads, 0, st>>>(ch, ws.row_off, n_rows, ws);
+  e = cudaGetLastError();
+  if (e != cudaSuccess || ws.cap_half <= 0) return e;
+  const int ng = 4 * ch.n_ch;
+  e = cudaMemsetAsync(ws.grp_cnt, 0, (size_t)ng * sizeof(uint32_t), st);
+  if (e != cudaSuccess) return e;
+  const int gt = 256;
+  const long long gb = std::min<long long>((ws.cap_half + gt - 1) / gt, 4096);
+  group_count_kernel<<<(unsigned)gb, gt, 0, st>>>(ws.keys, ws.h_idx, ws.cap_half, ws.grp_cnt);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  group_scan_kernel<<<1, 1024, 0, st>>>(ws.grp_cnt, ws.grp_off, ng);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  group_scatter_kernel<<<(unsigned)gb, gt, 0, st>>>(ws.keys, ws.h_idx, ws.cap_half, ws.grp_off, ws.grp_cnt, ws.d_idx,
+                                                    ws.status);
   return cudaGetLastError();
 }
 
