@@ -103,7 +103,8 @@ size_t workspace_bytes(int n_ch, const PlanCounts& c, int precision) {
   b += align256(4 * (n_rows + 1) * sizeof(uint32_t));
   b += align256(4 * sizeof(unsigned long long));
   b += align256((size_t)c.n_half * sizeof(uint32_t));
-  b += 2 * align256(4 * (size_t)n_ch * sizeof(uint32_t));
+  b += align256(4 * (size_t)n_ch * kGroupBlocks * sizeof(uint32_t));
+  b += align256(2 * 4 * (size_t)n_ch * sizeof(uint32_t));
   b += align256(5 * (size_t)c.n_isl * tsz);
   b += align256((size_t)n_ch * sizeof(double));
   b += align256((size_t)n_ch * sizeof(double));
@@ -133,9 +134,9 @@ Workspace carve_workspace(void* base, int n_ch, const PlanCounts& c, int precisi
   w.d_idx = (uint32_t*)p;
   p += align256((size_t)c.n_half * sizeof(uint32_t));
   w.grp_cnt = (uint32_t*)p;
-  p += align256(4 * (size_t)n_ch * sizeof(uint32_t));
+  p += align256(4 * (size_t)n_ch * kGroupBlocks * sizeof(uint32_t));
   w.grp_off = (uint32_t*)p;
-  p += align256(4 * (size_t)n_ch * sizeof(uint32_t));
+  p += align256(2 * 4 * (size_t)n_ch * sizeof(uint32_t));
   w.terms = (void*)p;
   p += align256(5 * (size_t)c.n_isl * tsz);
   w.out_eta = (double*)p;

@@ -145,6 +145,8 @@ __host__ __device__ inline bool flag_h(int n1, int n2, int n3) { return n1 == n2
 // evaluates the "half" list n1 <= n2 only; the E list is the islands with
 // n1 = n3 and n1 <= n2, the F list those with n2 = n3 and n1 < n2 (each E/F
 // mirror pair is evaluated once).
+constexpr int kGroupBlocks = 256;  // tiles of the half list in the grouping of the D/G/H work list
+
 struct PlanCounts {
   long long n_isl, n_half, n_e, n_f;
 };
@@ -156,8 +158,9 @@ struct Workspace {
   uint64_t* keys;       // [n_isl] every island, (COI, n1, n2, n3) lexicographic
   uint32_t* h_idx;      // [n_half] island indices with n1 <= n2
   uint32_t* d_idx;      // [n_half] the same islands grouped by (n3, n1 + n2 - n - n3): the D/G/H work list
-  uint32_t* grp_cnt;    // [4 n_ch] group sizes, then the groups' write cursors
-  uint32_t* grp_off;    // [4 n_ch] group offsets in d_idx
+  uint32_t* grp_cnt;    // [4 n_ch][kGroupBlocks] group sizes per tile of the half list, then
+                        // the tiles' offsets inside their group
+  uint32_t* grp_off;    // [2][4 n_ch] group totals and group offsets in d_idx
   uint32_t* e_idx;      // [n_e]
   uint32_t* f_idx;      // [n_f]
   uint32_t* row_cnt;    // [4 * n_rows]

@@ -15,8 +15,6 @@
 // the island list comes out in (COI, n1, n2, n3) lexicographic order together
 // with three index lists: the half list (n1 <= n2), the E list (n1 == n3,
 // n1 <= n2) and the F list (n2 == n3, n1 < n2).
-#include <algorithm>
-
 #include "egn_internal.h"
 
 namespace egn {
@@ -101,9 +99,10 @@ __global__ void plan_count_kernel(ChannelTable a, uint32_t* row_cnt, int n_rows)
   }
 }
 
-// Exclusive scan of the four count arrays (one CTA of 1024 threads, each thread
-// a contiguous chunk).  row_off[a * (n_rows + 1) + n_rows] is the total, and
-// row_tot[a] the same total in 64 bits (the host refuses totals above 2^32 - 1).
+// Exclusive scan of the four count arrays (one CTA of 1024 threads per array,
+// each thread a contiguous chunk).  row_off[a * (n_rows + 1) + n_rows] is the
+// total, and row_tot[a] the same total in 64 bits (the host refuses totals above
+// 2^32 - 1).
 __global__ void plan_scan_kernel(const uint32_t* row_cnt, uint32_t* row_off, unsigned long long* row_tot,
                                  int n_rows) {
   __shared__ uint32_t warp_sum[32];
@@ -111,7 +110,8 @@ __global__ void plan_scan_kernel(const uint32_t* row_cnt, uint32_t* row_off, uns
   const int T = blockDim.x;
   int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   int chunk = (n_rows + T - 1) / T;
-  for (int arr = 0; arr < 4; ++arr) {
+  {
+    const int arr = blockIdx.x;
     const uint32_t* in = row_cnt + (size_t)arr * n_rows;
     uint32_t* out = row_off + (size_t)arr * (n_rows + 1);
     int b = tid * chunk, e = min(b + chunk, n_rows);
@@ -216,19 +216,52 @@ __device__ __forceinline__ int dw_group(uint64_t key) {
   return 4 * d + t;
 }
 
-__global__ void group_count_kernel(const uint64_t* keys, const uint32_t* h_idx, long long n_half, uint32_t* cnt) {
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n_half; i += (long long)gridDim.x * blockDim.x)
-    atomicAdd(&cnt[dw_group(keys[h_idx[i]])], 1u);
+// The grouping runs on kGroupBlocks tiles of the half list: per tile a shared-
+// memory histogram of the groups, then one exclusive scan over (group, tile), then
+// each tile scatters its islands from its own offsets (shared-memory cursors).
+__global__ void group_count_kernel(const uint64_t* keys, const uint32_t* h_idx, long long n_half, int ng,
+                                   uint32_t* blk_cnt) {
+  extern __shared__ uint32_t hist[];
+  const int nb = gridDim.x, b = blockIdx.x;
+  for (int g = threadIdx.x; g < ng; g += blockDim.x) hist[g] = 0;
+  __syncthreads();
+  const long long tile = (n_half + nb - 1) / nb;
+  const long long i0 = (long long)b * tile, i1 = min(n_half, i0 + tile);
+  for (long long i = i0 + threadIdx.x; i < i1; i += blockDim.x) atomicAdd(&hist[dw_group(keys[h_idx[i]])], 1u);
+  __syncthreads();
+  for (int g = threadIdx.x; g < ng; g += blockDim.x) blk_cnt[(size_t)g * nb + b] = hist[g];
 }
 
-// Exclusive scan of the group sizes (one CTA), then the sizes are zeroed to serve
-// as write cursors.
-__global__ void group_scan_kernel(uint32_t* cnt, uint32_t* off, int ng) {
+// Per group (one warp each): exclusive offsets of its tiles inside the group, in
+// place over the tile counts, and the group's total.
+__global__ void group_tile_scan_kernel(uint32_t* blk, int ng, int nb, uint32_t* gtot) {
+  const int g = (int)((blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
+  if (g >= ng) return;
+  uint32_t* row = blk + (size_t)g * nb;
+  const int per = (nb + 31) / 32, t0 = lane * per, t1 = min(t0 + per, nb);
+  uint32_t s = 0;
+  for (int t = t0; t < t1; ++t) s += row[t];
+  uint32_t x = s;
+  for (int o = 1; o < 32; o <<= 1) {
+    uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  uint32_t base = x - s;
+  for (int t = t0; t < t1; ++t) {
+    const uint32_t c = row[t];
+    row[t] = base;
+    base += c;
+  }
+  if (lane == 31) gtot[g] = x;
+}
+
+// Exclusive scan of the group totals (one CTA, each thread a contiguous chunk).
+__global__ void group_scan_kernel(const uint32_t* cnt, uint32_t* off, int n) {
   __shared__ uint32_t warp_sum[32];
   const int T = blockDim.x;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-  const int chunk = (ng + T - 1) / T;
-  const int b = tid * chunk, e = min(b + chunk, ng);
+  const int chunk = (n + T - 1) / T;
+  const int b = tid * chunk, e = min(b + chunk, n);
   uint32_t s = 0;
   for (int i = b; i < e; ++i) s += cnt[i];
   uint32_t x = s;
@@ -251,16 +284,20 @@ __global__ void group_scan_kernel(uint32_t* cnt, uint32_t* off, int ng) {
   for (int i = b; i < e; ++i) {
     off[i] = base;
     base += cnt[i];
-    cnt[i] = 0;
   }
 }
 
-__global__ void group_scatter_kernel(const uint64_t* keys, const uint32_t* h_idx, long long n_half,
-                                     const uint32_t* off, uint32_t* cur, uint32_t* d_idx, int* status) {
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n_half; i += (long long)gridDim.x * blockDim.x) {
+__global__ void group_scatter_kernel(const uint64_t* keys, const uint32_t* h_idx, long long n_half, int ng,
+                                     const uint32_t* blk_off, const uint32_t* gbase, uint32_t* d_idx, int* status) {
+  extern __shared__ uint32_t cur[];
+  const int nb = gridDim.x, b = blockIdx.x;
+  for (int g = threadIdx.x; g < ng; g += blockDim.x) cur[g] = gbase[g] + blk_off[(size_t)g * nb + b];
+  __syncthreads();
+  const long long tile = (n_half + nb - 1) / nb;
+  const long long i0 = (long long)b * tile, i1 = min(n_half, i0 + tile);
+  for (long long i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
     const uint32_t isl = h_idx[i];
-    const int g = dw_group(keys[isl]);
-    const long long at = (long long)off[g] + atomicAdd(&cur[g], 1u);
+    const long long at = atomicAdd(&cur[dw_group(keys[isl])], 1u);
     if (at < n_half) d_idx[at] = isl; else atomicOr(status, 16);
   }
 }
@@ -274,7 +311,7 @@ cudaError_t launch_plan_count(const ChannelTable& ch, const Workspace& ws, cudaS
   plan_count_kernel<<<blocks, threads, 0, st>>>(ch, ws.row_cnt, n_rows);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  plan_scan_kernel<<<1, 1024, 0, st>>>(ws.row_cnt, ws.row_off, ws.row_tot, n_rows);
+  plan_scan_kernel<<<4, 1024, 0, st>>>(ws.row_cnt, ws.row_off, ws.row_tot, n_rows);
   return cudaGetLastError();
 }
 
@@ -288,16 +325,27 @@ cudaError_t launch_plan(const ChannelTable& ch, const Workspace& ws, cudaStream_
   e = cudaGetLastError();
   if (e != cudaSuccess || ws.cap_half <= 0) return e;
   const int ng = 4 * ch.n_ch;
-  e = cudaMemsetAsync(ws.grp_cnt, 0, (size_t)ng * sizeof(uint32_t), st);
-  if (e != cudaSuccess) return e;
-  const int gt = 256;
-  const long long gb = std::min<long long>((ws.cap_half + gt - 1) / gt, 4096);
-  group_count_kernel<<<(unsigned)gb, gt, 0, st>>>(ws.keys, ws.h_idx, ws.cap_half, ws.grp_cnt);
+  const size_t hist_b = (size_t)ng * sizeof(uint32_t);  // <= 64 KB (n_ch <= 4096)
+  int dev = 0;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+  static unsigned long long attr_done = 0;  // opt in to more than 48 KB once per device
+  if (!(attr_done >> (dev & 63) & 1ull)) {
+    for (const void* k : {(const void*)group_count_kernel, (const void*)group_scatter_kernel})
+      if ((e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, 16384 * 4)) != cudaSuccess)
+        return e;
+    attr_done |= 1ull << (dev & 63);
+  }
+  group_count_kernel<<<kGroupBlocks, 256, hist_b, st>>>(ws.keys, ws.h_idx, ws.cap_half, ng, ws.grp_cnt);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  group_scan_kernel<<<1, 1024, 0, st>>>(ws.grp_cnt, ws.grp_off, ng);
+  // tile offsets inside each group (in place), group totals, group offsets
+  uint32_t* gtot = ws.grp_off;
+  uint32_t* gbase = ws.grp_off + ng;
+  group_tile_scan_kernel<<<(ng + 7) / 8, 256, 0, st>>>(ws.grp_cnt, ng, kGroupBlocks, gtot);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  group_scatter_kernel<<<(unsigned)gb, gt, 0, st>>>(ws.keys, ws.h_idx, ws.cap_half, ws.grp_off, ws.grp_cnt, ws.d_idx,
-                                                    ws.status);
+  group_scan_kernel<<<1, 1024, 0, st>>>(gtot, gbase, ng);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  group_scatter_kernel<<<kGroupBlocks, 256, hist_b, st>>>(ws.keys, ws.h_idx, ws.cap_half, ng, ws.grp_cnt, gbase,
+                                                          ws.d_idx, ws.status);
   return cudaGetLastError();
 }
 
