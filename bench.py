@@ -704,7 +704,9 @@ def main():
                        "islands_evaluated": n_half, "e_islands": n_e, "f_islands": n_f, "points_per_step": points, "segments_K": K,
                        "l2": "flushed between steps (256 MB write outside the per-step events)",
                        "parallelism": f"replicas x{world}"},
-            "gpu_launches": 7 * args.steps,
+            # per step: planner count, scan, emit; grouping count, tile scan, scan,
+            # scatter; D/G/H, E, F; assembly
+            "gpu_launches": 11 * args.steps,
             "roofline": roofline,
             "cpu_baseline": cpu,
             "e2e": e2e,
