@@ -156,7 +156,10 @@ void egn_link_destroy(egn_link* link);
  * frequencies [Hz] (strictly increasing, non-overlapping supports), symbol rates
  * [Baud], launch powers [W] (> 0), EGN modulation constants Phi and Psi per
  * channel (see egn_format_moments), raised-cosine roll-off in [0, 1].
- * Uploads the channel table to the current device and counts the islands on it.
+ * Uploads the channel table to the current device and counts the islands on it
+ * (synchronously, on the legacy default stream): work of egn_nli_eta_device on
+ * another stream that still reads this link must have completed.  Combs with
+ * more than 2^32 - 1 islands -> EGN_E_UNSUPPORTED (32-bit island indices).
  * Mixed symbol rates with any Phi or Psi != 0 -> EGN_E_UNSUPPORTED (the paper
  * gives the correction terms for one symbol rate only). */
 egn_status egn_set_wdm(egn_link* link, int n_ch, const double* centre_hz, const double* symbol_rate_baud,

@@ -452,7 +452,7 @@ egn_status count_islands(egn_link* l, PlanCounts* cnt, std::vector<long long>* p
   const int n_ch = l->n_ch;
   size_t n_rows = (size_t)n_ch * n_ch;
   size_t cnt_b = align256(4 * n_rows * sizeof(uint32_t)), off_b = align256(4 * (n_rows + 1) * sizeof(uint32_t));
-  DevBuf tmp;
+  DevBuf& tmp = l->d_count;  // kept by the link: no allocation when the comb size repeats
   cudaError_t e = tmp.ensure(cnt_b + off_b + 4 * sizeof(unsigned long long));
   if (e != cudaSuccess) return fail(EGN_E_NOMEM, "cudaMalloc: %s", cudaGetErrorString(e));
   Workspace w{};
@@ -464,7 +464,6 @@ egn_status count_islands(egn_link* l, PlanCounts* cnt, std::vector<long long>* p
   unsigned long long tot[4] = {};
   if (e == cudaSuccess) e = cudaMemcpy(off.data(), w.row_off, off.size() * sizeof(uint32_t), cudaMemcpyDeviceToHost);
   if (e == cudaSuccess) e = cudaMemcpy(tot, w.row_tot, sizeof tot, cudaMemcpyDeviceToHost);
-  tmp.release();
   if (e != cudaSuccess) return fail(EGN_E_CUDA, "island count: %s", cudaGetErrorString(e));
   // island indices and list offsets are 32-bit
   if (tot[0] > 0xffffffffull)
@@ -642,13 +641,18 @@ egn_status egn_set_wdm(egn_link* l, int n_ch, const double* centre_hz, const dou
     return s_;
   }
   // pinned staging for host outputs
-  if (l->h_stage) cudaFreeHost(l->h_stage);
-  l->h_stage = nullptr;
-  cudaError_t e = pinned_alloc((void**)&l->h_stage, (2 * n_ch + 2) * sizeof(double));
-  if (e != cudaSuccess) {
+  const size_t stage_n = 2 * (size_t)n_ch + 2;  // kept while large enough (a comb changed in place)
+  if (!l->h_stage || l->h_stage_n < stage_n) {
+    if (l->h_stage) cudaFreeHost(l->h_stage);
     l->h_stage = nullptr;
-    l->n_ch = 0;
-    return fail(EGN_E_NOMEM, "cudaMallocHost: %s", cudaGetErrorString(e));
+    l->h_stage_n = 0;
+    cudaError_t e = pinned_alloc((void**)&l->h_stage, stage_n * sizeof(double));
+    if (e != cudaSuccess) {
+      l->h_stage = nullptr;
+      l->n_ch = 0;
+      return fail(EGN_E_NOMEM, "cudaMallocHost: %s", cudaGetErrorString(e));
+    }
+    l->h_stage_n = stage_n;
   }
   return EGN_OK;
 }

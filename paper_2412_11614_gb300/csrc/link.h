@@ -136,12 +136,15 @@ struct egn_link {
   // library-owned workspace and pinned staging for the host API
   egn_host::DevBuf ws;
   double* h_stage = nullptr;  // [2 n_ch + 1]
+  size_t h_stage_n = 0;       // its capacity in doubles
   egn_host::DevBuf d_stage;
   // COI evaluation frequencies of the f-integral (egn_nli_eta_3d): n_ch doubles,
   // then n_ch floats; used by channel_table while coi_shift is set
   egn_host::DevBuf d_coi;
   bool coi_shift = false;
+  egn_host::DevBuf d_count;  // the planner's row counts of the island count (egn_set_wdm)
   ~egn_link() {
+    d_count.release();
     d_coi.release();
     d_ch.release();
     d_seg.release();
