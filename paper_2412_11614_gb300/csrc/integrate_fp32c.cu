@@ -44,7 +44,7 @@ constexpr int kThreads = 128;
 constexpr int kDwThreads = 64;     // CTA size of the D/G/H, E and F passes
 constexpr int kDwCtas = 10;        // resident CTAs per SM of the D/G/H pass
 constexpr int kEfCtas = 10;        // and of the E and F passes
-constexpr int kDwBatch = 32;       // islands per batch of the D/G/H pass
+constexpr int kDwBatch = 16;       // islands per batch of the D/G/H pass
 constexpr int kEfBatch = 16;       // and of the E and F passes (short lists: smaller
                                    // batches spread them over more CTAs)
 constexpr int kBatch = kThreads;   // islands per batch, one per thread in the set-up
@@ -205,6 +205,38 @@ __device__ __forceinline__ RowPhase row_phase(const RowGeo& r, Df G0, Df G1, flo
   return q;
 }
 
+// Row constants of row `row` of island jb of the batch into slot rr of R (the
+// point passes' constants, see RowSm); returns the row's f3 (DW order).
+template <int ORD, class BS, class RS>
+__device__ __forceinline__ float form_row(const LinkParams& p, const BS& bs, RS& R, int jb, int np, int no, int row,
+                                          int rr, Df G0, Df G1, float Kf, float invK) {
+  const float k4 = (float)(4.0 * kPi * kPi);
+  const float pib3 = (float)(kPi * p.beta3), b2f = (float)p.beta2;
+  const int pi = row / no, i = row - pi * no;
+  const RowGeo g = row_geometry<ORD>(p, bs, jb, np, pi, i);
+  const RowPhase q = row_phase(g, G0, G1, Kf, invK);
+  const float s0f = dval(g.s0), s1f = dval(g.s1);
+  const float imf = dval(g.im), ihf = dval(g.ih), of = dval(g.o);
+  const float wo = dval(g.ph) * p.gl.wf[np][i];
+  const float dfl = dval(bs.dd[jb]);
+  const float hout = ORD == ORD_DW ? rc_f(of, bs.ra[2][jb], bs.ri[2][jb])
+                                   : (ORD == ORD_E ? rc_f(of, bs.ra[1][jb], bs.ri[1][jb]) : rc_f(of, bs.ra[0][jb], bs.ri[0][jb]));
+  R.qa[rr] = make_float4(q.Q0r.hi, q.Q0r.lo, q.Q1.hi, q.Q1.lo);
+  R.qb[rr] = make_float4(q.Q2.hi, q.Q2.lo, q.Q3, q.Q0r.hi - rint_fast(q.Q0r.hi));
+  R.ab[rr] = make_float4(dval(g.a0), dval(g.a1), dval(g.b0), dval(g.b1));
+  R.kc[rr] = make_float4(k4 * fmaf(pib3, s0f, b2f), k4 * pib3 * s1f, imf, ihf);
+  R.ow[rr] = make_float4(ORD == ORD_DW ? of - dfl : of, wo * ihf * hout, wo * ihf, hout);
+  const float nu3 = bs.nu3[jb];
+  float f3v = 0.0f;
+  if (ORD == ORD_DW) {
+    f3v = nu3 + of;
+    R.f3[rr] = make_float4(f3v, 0.0f, wo, 0.0f);
+  } else {
+    R.f3[rr] = make_float4(nu3 + (imf + of + dfl), ihf, wo, 0.0f);
+  }
+  return f3v;
+}
+
 // Phase of one point of a row: theta (turns of one segment, chi L / (2 pi K))
 // and phi (turns of the span, chi L / (2 pi)), both reduced to [-1/2, 1/2].
 // qa = {q0h, q0l, q1h, q1l}, qb = {q2h, q2l, q3, frac(q0h)}, x4 = {x, x tail,
@@ -303,7 +335,7 @@ integrate_fp32c_kernel(LinkParams p, const uint64_t* __restrict__ keys, const ui
   constexpr int NPAIR = KP / 2;
   constexpr int NB = batch_of(ORD, NT);
   __shared__ BatchSmT<NB> bs;
-  __shared__ RowSm<rows_max(NT)> rs;
+  __shared__ RowSm<rows_max(NT)> rsb[2];  // the current island's rows and the next one's
   constexpr int NW = NT / 32;
   __shared__ float red[4][NW];
   // the rows the c_k table holds (DW): their f3 in FP32 and their number (-1: none)
@@ -339,8 +371,6 @@ integrate_fp32c_kernel(LinkParams p, const uint64_t* __restrict__ keys, const ui
   const float N = (float)p.n_spans;
   const float gam = (float)p.gamma;
   const float g2 = gam * gam;
-  const float k4 = (float)(4.0 * kPi * kPi);
-  const float pib3 = (float)(kPi * p.beta3), b2f = (float)p.beta2;
   const float pi_f = 3.14159265358979f;
 
   for (int j = tid; j < npad; j += NT) {
@@ -354,6 +384,8 @@ integrate_fp32c_kernel(LinkParams p, const uint64_t* __restrict__ keys, const ui
     }
   }
 
+  int cur = 0;             // row buffer of the current island
+  bool have_rows = false;  // its rows were formed with the previous island's
   for (long long b0 = (long long)blockIdx.x * NB; b0 < n_items; b0 += (long long)gridDim.x * NB) {
     // ---------------- 1. batch set-up, FP64, one island per thread
     if (tid < NB) batch_setup<ORD>(p, keys, list, n_items, b0, bs, tid);
@@ -361,6 +393,7 @@ integrate_fp32c_kernel(LinkParams p, const uint64_t* __restrict__ keys, const ui
     const int nb = (int)min((long long)NB, n_items - b0);
     // ---------------- 2./3. the islands of the batch, one after the other
     for (int ib = 0; ib < nb; ++ib) {
+      bool fetched = false;
       const int np = bs.np[ib];
       const int flags = bs.flags[ib];
       const bool want_g = flags & 1, want_h = flags & 2;
@@ -373,38 +406,27 @@ integrate_fp32c_kernel(LinkParams p, const uint64_t* __restrict__ keys, const ui
       const int rows = np * no;
       for (int c0 = 0; c0 < rows; c0 += rows_per_chunk) {
         const int rc = min(rows_per_chunk, rows - c0);
-        // ---- row constants in double-float, one row per thread: the rows fill whole
-        // warps (rc <= NT), so the idle warps issue nothing
+        // ---- row constants in double-float, one row per thread of the first half of
+        // the CTA (rc <= NT / 2).  When this island and the next fit one chunk, the
+        // second half forms the next island's rows into the other buffer meanwhile,
+        // and the next island skips this phase.
+        RowSm<rows_max(NT)>& rs = rsb[cur];
         bool same_row = true;  // DW: this row's f3 equals the table's row rr
-        {
-          const int rr = tid;
-          if (rr < rc) {
-            const int row = c0 + rr;
-            const int pi = row / no, i = row - pi * no;
-            const RowGeo g = row_geometry<ORD>(p, bs, ib, np, pi, i);
-            const RowPhase q = row_phase(g, G0, G1, Kf, invK);
-            const Df Q0r = q.Q0r, Q1 = q.Q1, Q2 = q.Q2;
-            const float Q3 = q.Q3;
-            const Df a0 = g.a0, a1 = g.a1, b0_ = g.b0, b1 = g.b1, s0 = g.s0, s1 = g.s1, im = g.im, ih = g.ih, o = g.o,
-                     ph = g.ph;
-            const float s0f = dval(s0), s1f = dval(s1);
-            const float imf = dval(im), ihf = dval(ih), of = dval(o);
-            const float wo = dval(ph) * p.gl.wf[np][i];
-            const float hout = ORD == ORD_DW ? rc_f(of, sa3, si3) : (ORD == ORD_E ? rc_f(of, sa2, si2) : rc_f(of, sa1, si1));
-            rs.qa[rr] = make_float4(Q0r.hi, Q0r.lo, Q1.hi, Q1.lo);
-            rs.qb[rr] = make_float4(Q2.hi, Q2.lo, Q3, Q0r.hi - rint_fast(Q0r.hi));
-            rs.ab[rr] = make_float4(dval(a0), dval(a1), dval(b0_), dval(b1));
-            rs.kc[rr] = make_float4(k4 * fmaf(pib3, s0f, b2f), k4 * pib3 * s1f, imf, ihf);
-            rs.ow[rr] = make_float4(ORD == ORD_DW ? of - dfl : of, wo * ihf * hout, wo * ihf, hout);
-            const float nu3 = bs.nu3[ib];
-            if (ORD == ORD_DW) {
-              const float f3v = nu3 + of;
-              rs.f3[rr] = make_float4(f3v, 0.0f, wo, 0.0f);
-              same_row = tab_rows == rc && tab_f3[rr] == f3v;
-            } else {
-              rs.f3[rr] = make_float4(nu3 + (imf + of + dfl), ihf, wo, 0.0f);
-            }
+        bool fetch = false;
+        if (!have_rows) {
+          const int nb1 = ib + 1 < nb ? bs.np[ib + 1] : 0;
+          const int rows1 = nb1 > 0 ? nb1 * p.gl.order[nb1] : 0;
+          fetch = rows <= NT / 2 && rows <= rows_per_chunk && rows1 > 0 && rows1 <= NT / 2 && rows1 <= rows_per_chunk;
+          fetched = fetch;
+          if (tid < rc) {
+            const float f3v = form_row<ORD>(p, bs, rs, ib, np, no, c0 + tid, tid, G0, G1, Kf, invK);
+            if (ORD == ORD_DW) same_row = tab_rows == rc && tab_f3[tid] == f3v;
+          } else if (fetch && tid >= NT / 2 && tid - NT / 2 < rows1) {
+            form_row<ORD>(p, bs, rsb[cur ^ 1], ib + 1, nb1, p.gl.order[nb1], tid - NT / 2, tid - NT / 2, G0, G1, Kf,
+                          invK);
           }
+        } else if (ORD == ORD_DW && tid < rc) {
+          same_row = tab_rows == rc && tab_f3[tid] == rs.f3[tid].x;
         }
         // the c_k table depends only on the rows' f3 (and the launch's C_k, zeta_k):
         // when every row matches, the table already holds this chunk's values
@@ -652,6 +674,9 @@ integrate_fp32c_kernel(LinkParams p, const uint64_t* __restrict__ keys, const ui
         }
       }
       __syncthreads();
+      // the next island's rows are in the other buffer if they were formed here
+      if (fetched) cur ^= 1;
+      have_rows = fetched;
     }
   }
 }
