@@ -583,8 +583,10 @@ integrate_fp32c_kernel(LinkParams p, const uint64_t* __restrict__ keys, const ui
               unpack2(b2p[a], b2_[2 * a], b2_[2 * a + 1]);
             }
           } else {
-            for (int k = K - 1; k >= 0; --k) {
-              const float ck = p.seg.ck_f[k], zk = p.seg.zeta_f[k];
+            // E and F: c_k per point (f3 varies along the row); four segments per
+            // round from 16-byte loads of C_k and zeta_k, so that the ex2 of later
+            // segments are issued ahead of the recurrence that waits on them
+            auto step = [&](float ck, float zk) {
 #pragma unroll
               for (int m = 0; m < KP; ++m) {
                 const float c = ck * ex2_approx(-zk * f3_[m]);
@@ -592,6 +594,17 @@ integrate_fp32c_kernel(LinkParams p, const uint64_t* __restrict__ keys, const ui
                 b2_[m] = b1_[m];
                 b1_[m] = bn;
               }
+            };
+            int k = K - 1;
+            for (int e = K & 3; e > 0; --e, --k) step(p.seg.ck_f[k], p.seg.zeta_f[k]);  // peel: k + 1 = 0 (mod 4)
+#pragma unroll 2
+            for (; k >= 3; k -= 4) {
+              const float4 c4 = *reinterpret_cast<const float4*>(p.seg.ck_f + k - 3);
+              const float4 z4 = *reinterpret_cast<const float4*>(p.seg.zeta_f + k - 3);
+              step(c4.w, z4.w);
+              step(c4.z, z4.z);
+              step(c4.y, z4.y);
+              step(c4.x, z4.x);
             }
           }
           // ---- mu, Upsilon and the sums
