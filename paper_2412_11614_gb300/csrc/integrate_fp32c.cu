@@ -597,7 +597,7 @@ integrate_fp32c_kernel(LinkParams p, const uint64_t* __restrict__ keys, const ui
             };
             int k = K - 1;
             for (int e = K & 3; e > 0; --e, --k) step(p.seg.ck_f[k], p.seg.zeta_f[k]);  // peel: k + 1 = 0 (mod 4)
-#pragma unroll 2
+#pragma unroll 1
             for (; k >= 3; k -= 4) {
               const float4 c4 = *reinterpret_cast<const float4*>(p.seg.ck_f + k - 3);
               const float4 z4 = *reinterpret_cast<const float4*>(p.seg.zeta_f + k - 3);
