@@ -922,9 +922,10 @@ integrate_fp32c_general_kernel(LinkParams p, const uint64_t* __restrict__ keys, 
                   b1_[m] = bn;
                 }
               }
-            } else {
-              for (int k = K - 1; k >= 0; --k) {
-                const float ck = p.types[t].seg.ck_f[k], zk = p.types[t].seg.zeta_f[k];
+            } else {  // E, F: c_k per point, segments in rounds of four (16-byte loads)
+              const float* ckf = p.types[t].seg.ck_f;
+              const float* zkf = p.types[t].seg.zeta_f;
+              auto step = [&](float ck, float zk) {
 #pragma unroll
                 for (int m = 0; m < KP; ++m) {
                   const float c = ck * ex2_approx(-zk * f3_[m]);
@@ -932,6 +933,17 @@ integrate_fp32c_general_kernel(LinkParams p, const uint64_t* __restrict__ keys, 
                   b2_[m] = b1_[m];
                   b1_[m] = bn;
                 }
+              };
+              int k = K - 1;
+              for (int e = K & 3; e > 0; --e, --k) step(ckf[k], zkf[k]);  // peel: k + 1 = 0 (mod 4)
+#pragma unroll 1
+              for (; k >= 3; k -= 4) {
+                const float4 c4 = *reinterpret_cast<const float4*>(ckf + k - 3);
+                const float4 z4 = *reinterpret_cast<const float4*>(zkf + k - 3);
+                step(c4.w, z4.w);
+                step(c4.z, z4.z);
+                step(c4.y, z4.y);
+                step(c4.x, z4.x);
               }
             }
 #pragma unroll
