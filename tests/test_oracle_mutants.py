@@ -26,7 +26,9 @@ MUTANTS = {
     "upsilon_phase": ("Y += sp->gamma * mu * cexp(I * acc);", "Y += sp->gamma * mu * cexp(-I * acc);"),
     "upsilon_beta3": ("(sp->beta2 * sp->L + OR_PI * (f1 + f2) * sp->beta3 * sp->L)", "(sp->beta2 * sp->L)"),
     "rc_knee": ("return 0.5 * (1.0 + cos(OR_PI / (beta * R) * (ax - a)));", "return 0.5 * (1.0 + cos(OR_PI / (beta * R) * (ax + a)));"),
-    "offset_sign": ("return (pb->nu[n1] - pb->nu[n]) + (pb->nu[n2] - pb->nu[n3]);", "return (pb->nu[n1] - pb->nu[n]) - (pb->nu[n2] - pb->nu[n3]);"),
+    "offset_sign": ("return (pb->nu[n1] - or_fcoi(pb, n)) + (pb->nu[n2] - pb->nu[n3]);", "return (pb->nu[n1] - or_fcoi(pb, n)) - (pb->nu[n2] - pb->nu[n3]);"),
+    "coi_offset_sign": ("return pb->nu[n] + (pb->f_off ? pb->f_off[n] : 0.0);", "return pb->nu[n] - (pb->f_off ? pb->f_off[n] : 0.0);"),
+    "coi_offset_not_in_upsilon": ("    double f = or_fcoi(pb, n);\n    for (int p = 0; p < np; ++p) {", "    double f = pb->nu[n];\n    for (int p = 0; p < np; ++p) {"),
     "coef_D": ("cf[OR_T_D] = (16.0 / 27.0) * R / (pb->R[n1] * pb->R[n2] * pb->R[n3]);", "cf[OR_T_D] = (16.0 / 27.0) / (pb->R[n1] * pb->R[n2]);"),
     "coef_F": ("cf[OR_T_F] = (32.0 / 81.0) / (R * R * R);", "cf[OR_T_F] = (16.0 / 27.0) / (R * R * R);"),
     "coef_H": ("cf[OR_T_H] = (16.0 / 81.0) / (R * R * R * R);", "cf[OR_T_H] = (16.0 / 81.0) / (R * R * R);"),
@@ -57,7 +59,7 @@ def test_mutant_is_caught(name):
         env = dict(os.environ, EGN_ORACLE_LIB=so, EGN_RUN_MUTANTS="0")
         # fast pins first; a pin that runs away on a mutant counts as failing (per-test timeout)
         order = ["test_oracle_isrs.py", "test_oracle_mu.py", "test_oracle_quadrature.py", "test_oracle_islands.py",
-                 "test_oracle_egn.py"]
+                 "test_oracle_egn.py", "test_oracle_3d.py"]
         pins = [os.path.join(ROOT, "tests", f) for f in order]
         r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider", "--timeout", "120"]
                            + pins, cwd=ROOT, env=env, capture_output=True, text=True, timeout=1800)
