@@ -387,6 +387,34 @@ LinkParams link_params(const egn_link* l, const egn_opts* o, int all_terms) {
   for (int t = 0; t < p.n_types && t < kMaxTypes; ++t) p.types[t] = l->types[t];
   p.types_dev = p.n_types > kMaxTypes ? (const SpanType*)l->d_types.p : nullptr;
   for (int s = 0; s < (int)l->span_type.size() && s < kMaxSpans; ++s) p.span_type[s] = l->span_type[s];
+  // fibre groups of the span types (used by the span-by-span path)
+  p.n_fib = 0;
+  if (p.n_types > kMaxTypes && (int)l->types.size() == p.n_types) {
+    int nf = 0, rep[kMaxFibres] = {};
+    bool ok = true;
+    for (int t = 0; t < p.n_types && ok; ++t) {
+      const SpanType& ty = l->types[t];
+      int f = 0;
+      while (f < nf && !(l->types[rep[f]].alpha == ty.alpha && l->types[rep[f]].pcr == ty.pcr &&
+                         l->types[rep[f]].dz == ty.dz))
+        ++f;
+      if (f == nf) {
+        if (nf == kMaxFibres) { ok = false; break; }
+        rep[nf++] = t;
+      } else if (ty.seg.K > l->types[rep[f]].seg.K) {
+        rep[f] = t;  // the longest type of the fibre holds every prefix
+      }
+      p.type_fib[t] = (unsigned char)f;
+    }
+    if (ok) {
+      p.n_fib = nf;
+      for (int f = 0; f < nf; ++f) {
+        p.fib_ck[f] = l->types[rep[f]].seg.ck_f;
+        p.fib_zk[f] = l->types[rep[f]].seg.zeta_f;
+        p.fib_K[f] = l->types[rep[f]].seg.K;
+      }
+    }
+  }
   return p;
 }
 

@@ -79,6 +79,10 @@ void rebase_params(LinkParams& p, const egn_link* l, char* ch_copy, char* seg_co
   };
   seg(p.seg);
   for (int t = 0; t < egn::kMaxTypes; ++t) seg(p.types[t].seg);
+  for (int f = 0; f < p.n_fib; ++f) {
+    rebase(p.fib_ck[f], l->d_seg.p, l->d_seg.bytes, seg_copy);
+    rebase(p.fib_zk[f], l->d_seg.p, l->d_seg.bytes, seg_copy);
+  }
   for (int q = 0; q < 4; ++q) {
     rebase(p.gl.x[q], l->d_gl.p, l->d_gl.bytes, gl_copy);
     rebase(p.gl.w[q], l->d_gl.p, l->d_gl.bytes, gl_copy);

@@ -87,6 +87,7 @@ struct SegmentTables {
 // travel in the launch parameters (the fast general path); links with more
 // types pass all of them in device memory (LinkParams::types_dev).
 constexpr int kMaxTypes = 4;
+constexpr int kMaxFibres = 4;  // fibre groups tabulated by the span-by-span path
 constexpr int kMaxSpans = 64;
 struct SpanType {
   double alpha, beta2, beta3, gamma, L;
@@ -127,6 +128,15 @@ struct LinkParams {
   SpanType types[kMaxTypes];         // the first kMaxTypes of them
   const SpanType* types_dev;         // all n_types in device memory when n_types > kMaxTypes
   unsigned char span_type[kMaxSpans];  // type of span s, s = 0 .. n_spans - 1
+  // Span types of one fibre (equal alpha, P_tot Cr and segment length dz) have
+  // the same C_k and zeta_k for k < K_t: their c_k are prefixes of one series, so
+  // the span-by-span path (more than kMaxTypes types) tabulates c_k per row once
+  // per fibre.  n_fib = 0: more than kMaxFibres fibres, c_k formed on the fly.
+  int n_fib;
+  unsigned char type_fib[kMaxSpans];      // fibre of span type t
+  const float* fib_ck[kMaxFibres];        // C_k and log2(e) zeta_k of the fibre's longest type
+  const float* fib_zk[kMaxFibres];
+  int fib_K[kMaxFibres];                  // its K
 };
 
 // Span type t of a launch (either array).

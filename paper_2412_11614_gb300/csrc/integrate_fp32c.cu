@@ -31,7 +31,10 @@
 //    sines use their Taylor series (|argument| < 0.05, relative error < 4e-12).
 //    Hardware sin/cos (MUFU, absolute error ~4e-7 on [-pi, pi]) elsewhere.
 // Island sums: FP32 per thread, fixed-order shuffle and shared-memory trees.
+#include <algorithm>
+
 #include "egn_internal.h"
+
 #include "fp32c_common.cuh"
 #include "island_geom.cuh"
 
@@ -1104,7 +1107,8 @@ constexpr int kSpanTypeFloats = 12;  // per type: G0 (df), G1 (df), K, 1/K, alph
 template <int ORD>
 __global__ void __launch_bounds__(kThreads, 2)
 integrate_fp32c_spans_kernel(LinkParams p, const uint64_t* __restrict__ keys, const uint32_t* __restrict__ list,
-                             long long n_items, float* __restrict__ terms, long long n_isl, int rows_per_chunk) {
+                             long long n_items, float* __restrict__ terms, long long n_isl, int rows_per_chunk,
+                             int kfp) {
   constexpr int KP = 2;
   __shared__ BatchSm bs;
   __shared__ float4 g_ab[kGRows], g_ow[kGRows], g_f3[kGRows];
@@ -1117,6 +1121,9 @@ integrate_fp32c_spans_kernel(LinkParams p, const uint64_t* __restrict__ keys, co
   float4* sqb = sqa + T * R;                     // [T][R]
   float2* skc = reinterpret_cast<float2*>(sqb + T * R);  // [T][R]
   float* tyc = reinterpret_cast<float*>(skc + T * R);     // [T][kSpanTypeFloats]
+  // DW with fibre groups: c_k of the chunk's rows per fibre, [n_fib][R][kfp]
+  float* tabf = tyc + T * kSpanTypeFloats;
+  const bool fib_tab = ORD == ORD_DW && p.n_fib > 0;
 
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const int n = p.gl.n;
@@ -1192,6 +1199,17 @@ integrate_fp32c_spans_kernel(LinkParams p, const uint64_t* __restrict__ keys, co
           }
         }
         __syncthreads();
+        if (fib_tab) {  // c_k = C_k 2^{-zeta_k log2(e) f3} per fibre, row and segment
+          for (int f = 0; f < p.n_fib; ++f) {
+            const int Kfib = p.fib_K[f];
+            for (int k = tid; k < Kfib; k += kThreads) {
+              const float ck = p.fib_ck[f][k], zk = p.fib_zk[f][k];
+              float* col = tabf + (size_t)f * R * kfp + k;
+              for (int rr = 0; rr < rc; ++rr) col[rr * kfp] = ck * ex2_approx(-zk * g_f3[rr].x);
+            }
+          }
+          __syncthreads();
+        }
         for (int rb = 0; rb < rc; rb += rows_per_pass) {
           const int rr = rb + rsub;
           const bool row_ok = rr < rc;
@@ -1247,16 +1265,29 @@ integrate_fp32c_spans_kernel(LinkParams p, const uint64_t* __restrict__ keys, co
                 b2_[m] = 0.0f;
               }
               const float q = r * r;
-              const float* ckf = p.types_dev[t].seg.ck_f;
-              const float* zkf = p.types_dev[t].seg.zeta_f;
-              for (int k = K - 1; k >= 0; --k) {
-                const float ck = __ldg(ckf + k), zk = __ldg(zkf + k);
+              if (fib_tab) {  // the type's c_k: the first K entries of its fibre's row
+                const float* trow = tabf + ((size_t)p.type_fib[t] * R + rrc) * kfp;
+                for (int k = K - 1; k >= 0; --k) {
+                  const float cc = trow[k];
 #pragma unroll
-                for (int m = 0; m < KP; ++m) {
-                  const float cc = ck * ex2_approx(-zk * f3_[m]);
-                  const float bn = fmaf(p_[m], b1_[m], fmaf(-q, b2_[m], cc));
-                  b2_[m] = b1_[m];
-                  b1_[m] = bn;
+                  for (int m = 0; m < KP; ++m) {
+                    const float bn = fmaf(p_[m], b1_[m], fmaf(-q, b2_[m], cc));
+                    b2_[m] = b1_[m];
+                    b1_[m] = bn;
+                  }
+                }
+              } else {
+                const float* ckf = p.types_dev[t].seg.ck_f;
+                const float* zkf = p.types_dev[t].seg.zeta_f;
+                for (int k = K - 1; k >= 0; --k) {
+                  const float ck = __ldg(ckf + k), zk = __ldg(zkf + k);
+#pragma unroll
+                  for (int m = 0; m < KP; ++m) {
+                    const float cc = ck * ex2_approx(-zk * f3_[m]);
+                    const float bn = fmaf(p_[m], b1_[m], fmaf(-q, b2_[m], cc));
+                    b2_[m] = b1_[m];
+                    b1_[m] = bn;
+                  }
                 }
               }
 #pragma unroll
@@ -1350,7 +1381,7 @@ integrate_fp32c_spans_kernel(LinkParams p, const uint64_t* __restrict__ keys, co
   }
 }
 
-constexpr int kSpansDynBytes = 48 * 1024;  // per-type constants and row phases
+constexpr int kSpansDynBytes = 96 * 1024;  // per-type constants, row phases and fibre c_k tables
 
 template <int ORD>
 cudaError_t launch_spans(const LinkParams& p, const uint64_t* keys, const uint32_t* list, long long n_items,
@@ -1358,10 +1389,17 @@ cudaError_t launch_spans(const LinkParams& p, const uint64_t* keys, const uint32
   if (n_items <= 0) return cudaSuccess;
   const int T = p.n_types;
   const int per_type = (int)(2 * sizeof(float4) + sizeof(float2));
-  int rows = (kSpansDynBytes - T * kSpanTypeFloats * (int)sizeof(float)) / (T * per_type);
+  int kfp = 0;  // row stride of the fibre tables (DW): the longest fibre's K, 4 (mod 8)
+  if (ORD == ORD_DW && p.n_fib > 0) {
+    for (int f = 0; f < p.n_fib; ++f) kfp = std::max(kfp, p.fib_K[f]);
+    kfp = (kfp + 3) & ~3;
+    if ((kfp & 7) == 0) kfp += 4;
+  }
+  const int per_row = T * per_type + (ORD == ORD_DW ? p.n_fib * kfp * (int)sizeof(float) : 0);
+  int rows = (kSpansDynBytes - T * kSpanTypeFloats * (int)sizeof(float)) / per_row;
   if (rows > kGRows) rows = kGRows;
-  if (rows < 1) return cudaErrorInvalidValue;  // not reached: T <= kMaxSpans leaves at least 16 rows
-  const size_t smem = (size_t)T * rows * per_type + (size_t)T * kSpanTypeFloats * sizeof(float);
+  if (rows < 1) return cudaErrorInvalidValue;  // not reached: 64 types and 4 fibres of K 1024 leave 11 rows
+  const size_t smem = (size_t)rows * per_row + (size_t)T * kSpanTypeFloats * sizeof(float);
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -1376,7 +1414,7 @@ cudaError_t launch_spans(const LinkParams& p, const uint64_t* keys, const uint32
   long long blocks = (long long)sms * 2;
   if (blocks > batches) blocks = batches;
   integrate_fp32c_spans_kernel<ORD><<<(unsigned)blocks, kThreads, smem, st>>>(p, keys, list, n_items, terms, n_isl,
-                                                                             rows);
+                                                                             rows, kfp);
   return cudaGetLastError();
 }
 
