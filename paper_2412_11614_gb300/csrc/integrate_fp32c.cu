@@ -1,15 +1,19 @@
 // integrate_fp32c.cu -- FP32 island integrator with exact phase reduction (the
 // fast path).
 //
-// Work decomposition.  A CTA of 128 threads takes islands in batches of 128.
+// Work decomposition.  Links of identical spans: 64-thread CTAs (10 per SM) take
+// islands in batches of 16; links whose spans differ: 128-thread CTAs, batches of
+// 128.
 //  1. Batch set-up (FP64, one island per thread): geometry of the node rule,
 //     panel edges and the island constants, rounded to FP32 head/tail pairs
 //     ("double-float", 48-bit significand).  GB300 runs FP64 at 1/64 of the FP32
-//     rate, so FP64 appears only here, with every lane busy.
+//     rate, so FP64 appears only here.
 //  2. Per island, per chunk of outer nodes ("rows"): the row constants in
 //     double-float arithmetic (FP32 only) -- the cubic phase polynomial in the
-//     inner node, Q0 reduced modulo K -- and, in the DW order, the row's table
-//     c_k = C_k e^{-zeta_k f3} in shared memory.
+//     inner node, Q0 reduced modulo K -- one row per thread (the first warp forms
+//     the island's rows, the second the next island's into a second buffer), and,
+//     in the DW order, the rows' table c_k = C_k e^{-zeta_k f3} in shared memory,
+//     kept while the rows' f3 are unchanged (the work list groups such islands).
 //  3. Per point (KP per thread, one row): phase, segment sum, Upsilon, weights.
 //
 // Arithmetic per point:
