@@ -9,12 +9,13 @@
 //     min(W3/2, d + (W1 + W2)/2) > max(-W3/2, d - (W1 + W2)/2).
 // On a uniform grid this is the set T_kappa of Eq. 16 with n3 = n1 + n2 - n + l.
 //
-// Rows are (COI, n1) pairs (row = COI * n_ch + n1).  Three kernels: count per
-// row (one warp per row, lanes over n2), exclusive scan of the row counts (one
-// CTA), and emit (one warp per row, warp-scan of the per-lane counts), so that
-// the island list comes out in (COI, n1, n2, n3) lexicographic order together
-// with three index lists: the half list (n1 <= n2), the E list (n1 == n3,
-// n1 <= n2) and the F list (n2 == n3, n1 < n2).
+// Rows are (COI, n1) pairs (row = COI * n_ch + n1).  Count per row (one warp per
+// row, lanes over n2), exclusive scans of the row counts (one CTA per list), and
+// emit (one warp per row, warp-scan of the per-lane counts), so that the island
+// list comes out in (COI, n1, n2, n3) lexicographic order together with three
+// index lists: the half list (n1 <= n2), the E list (n1 == n3, n1 <= n2) and the
+// F list (n2 == n3, n1 < n2).  Then the half list is grouped by
+// (n3, n1 + n2 - n - n3) into the D/G/H work list (four more kernels, below).
 #include "egn_internal.h"
 
 namespace egn {
