@@ -1270,21 +1270,17 @@ integrate_fp32c_spans_kernel(LinkParams p, const uint64_t* __restrict__ keys, co
               }
               const float q = r * r;
               if (fib_tab) {  // the type's c_k: the first K entries of its fibre's row
-                const float* trow = tabf + ((size_t)p.type_fib[t] * R + rrc) * kfp;
-                for (int k = K - 1; k >= 0; --k) {
-                  const float cc = trow[k];
-#pragma unroll
-                  for (int m = 0; m < KP; ++m) {
-                    const float bn = fmaf(p_[m], b1_[m], fmaf(-q, b2_[m], cc));
-                    b2_[m] = b1_[m];
-                    b1_[m] = bn;
-                  }
-                }
-              } else {
+                static_assert(KP == 2, "one f32x2 pair of points per thread");
+                const float* trow = tabf + ((size_t)p.type_fib[t] * R + rrc) * kfp;  // 16-byte aligned
+                const f32x2 pp = pack2(p_[0], p_[1]);
+                f32x2 bb1, bb2;
+                dw_recurrence<1>(trow, K, pack2(-q, -q), &pp, &bb1, &bb2);
+                unpack2(bb1, b1_[0], b1_[1]);
+                unpack2(bb2, b2_[0], b2_[1]);
+              } else {  // c_k per point, segments in rounds of four (16-byte loads)
                 const float* ckf = p.types_dev[t].seg.ck_f;
                 const float* zkf = p.types_dev[t].seg.zeta_f;
-                for (int k = K - 1; k >= 0; --k) {
-                  const float ck = __ldg(ckf + k), zk = __ldg(zkf + k);
+                auto step = [&](float ck, float zk) {
 #pragma unroll
                   for (int m = 0; m < KP; ++m) {
                     const float cc = ck * ex2_approx(-zk * f3_[m]);
@@ -1292,6 +1288,17 @@ integrate_fp32c_spans_kernel(LinkParams p, const uint64_t* __restrict__ keys, co
                     b2_[m] = b1_[m];
                     b1_[m] = bn;
                   }
+                };
+                int k = K - 1;
+                for (int e = K & 3; e > 0; --e, --k) step(ckf[k], zkf[k]);  // peel: k + 1 = 0 (mod 4)
+#pragma unroll 1
+                for (; k >= 3; k -= 4) {
+                  const float4 c4 = *reinterpret_cast<const float4*>(ckf + k - 3);
+                  const float4 z4 = *reinterpret_cast<const float4*>(zkf + k - 3);
+                  step(c4.w, z4.w);
+                  step(c4.z, z4.z);
+                  step(c4.y, z4.y);
+                  step(c4.x, z4.x);
                 }
               }
 #pragma unroll
