@@ -16,6 +16,7 @@ does not exchange data), value = channel-evals of all ranks / max-over-ranks tim
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import math
 import os
@@ -202,8 +203,20 @@ def run_reference(args):
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": desc},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
-    print(json.dumps(line), flush=True)
+    emit(line, args.jsonl)
     return 0
+
+
+def emit(line: dict, jsonl: str = None) -> None:
+    """Print the JSON line; with `jsonl`, also append it to that file with a hash of
+    its workload and configuration (the same workload and options hash alike)."""
+    print(json.dumps(line), flush=True)
+    if jsonl:
+        key = json.dumps({k: line.get(k) for k in ("metric", "impl", "config", "workload", "n_gpus", "dtype")},
+                         sort_keys=True)
+        rec = dict(line, config_hash=hashlib.sha256(key.encode()).hexdigest()[:16], time_unix=time.time())
+        with open(jsonl, "a") as f:
+            f.write(json.dumps(rec) + "\n")
 
 
 # --------------------------------------------------------------------------- our arm
@@ -541,6 +554,8 @@ def main():
     ap.add_argument("--batch-random", action="store_true", help="the batch is seeded heterogeneous random links")
     ap.add_argument("--dz-sweep", action="store_true", help="segment length trade-off on Table I and II links")
     ap.add_argument("--gemm", type=int, default=0, metavar="G", help="time the surrogate's G^3 tensor-core GEMM")
+    ap.add_argument("--jsonl", default=None, metavar="PATH",
+                    help="also append the JSON line, with a hash of its workload and configuration, to PATH")
     ap.add_argument("--f3d", type=int, default=0, metavar="NF",
                     help="time the f-integrated EGN with NF nodes per COI band against the white-NLI value")
     ap.add_argument("--surrogate", action="store_true", help="train and evaluate the MLP surrogate")
@@ -714,7 +729,7 @@ def main():
             "wall_s_timed_region": t_wall,
             "eta_db_sample": [float(10 * np.log10(x)) for x in eta.cpu().numpy()[:: 30]],
         }
-        print(json.dumps(line), flush=True)
+        emit(line, args.jsonl)
     ln.close()
     if world > 1:
         dist.destroy_process_group()
