@@ -506,8 +506,9 @@ static void or_walk(const or_problem* pb, int n, int n1, int n2, int n3, int ord
  * Eq. 15 are evaluated (others set to 0); with all = 1 every term is evaluated. */
 void or_island_terms(const or_problem* pb, int n, int n1, int n2, int n3, int all, double* out)
 {
-    double gx[512], gw[512];
     int gn = pb->gl_order;
+    double* gx = (double*)malloc(sizeof(double) * 2 * (size_t)gn);
+    double* gw = gx + gn;
     or_gauss_legendre(gn, gx, gw);
     double cf[5];
     or_coefs(pb, n, n1, n2, n3, cf);
@@ -531,6 +532,7 @@ void or_island_terms(const or_problem* pb, int n, int n1, int n2, int n3, int al
         or_walk(pb, n, n1, n2, n3, 2, gx, gw, gn, &dd, &corr, &hh);
         out[OR_T_F] = cf[OR_T_F] * corr;
     }
+    free(gx);
 }
 
 /* Brute force: the same five integrals on a dense midpoint grid of M x M cells
@@ -664,16 +666,16 @@ long or_island_contribs(const or_problem* pb, int n, int* tri, double* contrib, 
  * writes (u, v, weight) per node, returns the node count (<= max). */
 long or_island_nodes(const or_problem* pb, int n, int n1, int n2, int n3, double* uvw, long max)
 {
-    double gx[512], gw[512];
     int gn = pb->gl_order;
-    or_gauss_legendre(gn, gx, gw);
     double W1 = or_width(pb, n1), W2 = or_width(pb, n2), W3 = or_width(pb, n3);
     double d = or_offset(pb, n, n1, n2, n3);
     double e[4];
     int np = or_panels(0.5 * W3, 0.5 * W1, 1.0, -d, 0.5 * W2, e);
     if (np == 0) return 0;
     int no = (gn + np - 1) / np;
-    double ox[512], ow[512];
+    double* gx = (double*)malloc(sizeof(double) * 2 * (size_t)(gn + no));
+    double *gw = gx + gn, *ox = gw + gn, *ow = ox + no;
+    or_gauss_legendre(gn, gx, gw);
     or_gauss_legendre(no, ox, ow);
     long cnt = 0;
     for (int p = 0; p < np; ++p) {
@@ -694,6 +696,7 @@ long or_island_nodes(const or_problem* pb, int n, int n1, int n2, int n3, double
             }
         }
     }
+    free(gx);
     return cnt;
 }
 

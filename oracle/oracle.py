@@ -13,6 +13,11 @@ bookkeeping (all in FP64):
   * B_tot = (f_max - f_min) * N/(N - 1) (= N * spacing on a uniform grid, i.e. the
     (2M + 1) R of Appendix B), and B_tot = R for a single channel;
   * P_tot = sum of the launch powers.
+
+Levels: Problem.eta is the node rule at the problem's order (the parity target of
+the GPU path); Problem.eta_converged doubles that order until the per-channel
+change is below a tolerance (the rule's own discretisation error); mu_form
+MU_INTEGRAL replaces the segment form by the adaptive integral of Eq. 23.
 """
 from __future__ import annotations
 
@@ -215,10 +220,13 @@ class Problem:
             spans.append(OrSpan(a, b2, b3, s.gamma_per_w_km, s.cr_per_w_km_thz, s.length_m * 1e-3))
         self.span_arr = (OrSpan * len(spans))(*spans)
         self.n_ch = n
+        gl = int(gl_order if gl_order is not None else wl.gl_order)
+        if gl < 1:
+            raise ValueError(f"gl_order {gl} < 1")
         self.c = OrProblem(
             n, _ptr(self.nu), _ptr(self.R), _ptr(self.P), _ptr(self.phi), _ptr(self.psi),
             float(wl.rolloff), self.ptot, self.btot, len(spans), self.span_arr,
-            int(gl_order if gl_order is not None else wl.gl_order), int(mu_form),
+            gl, int(mu_form),
             float(dz_km if dz_km is not None else wl.dz_km), float(int_tol), int(terms))
 
     @property
@@ -237,6 +245,28 @@ class Problem:
         if rc_ != 0:
             raise RuntimeError(f"or_eta failed: {rc_}")
         return eta, pn
+
+    def eta_converged(self, coi=None, tol_db=1e-4, max_order=1024):
+        """The converged level of the node rule: the Gauss-Legendre order per island
+        side is doubled from this problem's order until no listed channel's eta
+        changes by tol_db or more between two orders.  Returns (eta, order, history)
+        with history the eta of every order tried; raises RuntimeError when
+        max_order is passed first."""
+        g0 = self.c.gl_order
+        hist = {}
+        try:
+            g = g0
+            prev = hist[g] = self.eta(coi)[0]
+            while 2 * g <= max_order:
+                g *= 2
+                self.c.gl_order = g
+                cur = hist[g] = self.eta(coi)[0]
+                if np.max(np.abs(10 * np.log10(cur / prev))) < tol_db:
+                    return cur, g, hist
+                prev = cur
+        finally:
+            self.c.gl_order = g0
+        raise RuntimeError(f"not converged to {tol_db} dB by order {g}")
 
     def set_coi_offsets(self, off=None):
         """Evaluate each COI n at f = its centre + off[n] [THz] (None: at the centre)."""

@@ -142,6 +142,57 @@ def test_single_channel_gn_integral(oracle_mod, workloads):
     assert eta[0] == pytest.approx(want, rel=1e-4)
 
 
+def _single_channel_k1(workloads, oracle_mod, gl):
+    """The long single channel of the test above with one segment per span (Cr = 0:
+    the segment form is exact for any K) and its integral by the arctan inner form."""
+    wl = workloads.config_small(n_ch=1, gl_order=gl)
+    wl.rolloff = 0.0
+    s = wl.spans[0]
+    s.length_m = 1500e3
+    s.cr_per_w_km_thz = 0.0
+    s.S_ps_nm2_km = -2 * s.D_ps_nm_km / 1550.0
+    pb = oracle_mod.Problem(wl, gl_order=gl, terms=0, dz_km=1500.0)
+    sp = pb.spans[0]
+    R, a, g = pb.R[0], sp.alpha, sp.gamma
+    c = 4 * math.pi ** 2 * abs(sp.beta2)
+
+    def inner(u):
+        lo, hi = max(-R / 2, -R / 2 - u), min(R / 2, R / 2 - u)
+        if u == 0:
+            return (hi - lo) / a ** 2
+        k = c * abs(u) / a
+        return (math.atan(k * hi) - math.atan(k * lo)) / (a * c * abs(u))
+
+    val, _ = integrate.quad(inner, -R / 2, R / 2, points=[0.0], limit=400, epsabs=0, epsrel=1e-12)
+    return pb, 16 / 27 / R ** 2 * g * g * val
+
+
+def test_converged_level_reaches_the_integral(oracle_mod, workloads):
+    """Doubling the order from 8 until eta moves by < 1e-4 dB lands within 1e-4 dB
+    of the exact single-channel integral, with the order-8 value well off it."""
+    pb, want = _single_channel_k1(workloads, oracle_mod, 8)
+    eta, order, hist = pb.eta_converged(tol_db=1e-4, max_order=1024)
+    assert order > 8 and sorted(hist) == [8 * 2 ** i for i in range(len(hist))]
+    assert abs(10 * math.log10(eta[0] / want)) < 1e-4
+    assert abs(10 * math.log10(hist[8][0] / want)) > 1e-3
+    assert pb.c.gl_order == 8  # the problem's own order is restored
+    with pytest.raises(RuntimeError):
+        pb.eta_converged(tol_db=1e-12, max_order=32)
+
+
+def test_orders_beyond_512(oracle_mod, workloads):
+    """Node buffers are sized by the rule: a 600 x 600 rule (above any fixed buffer of
+    512) integrates the single channel to the closed form, and the node list has
+    600 x 600 weights summing to the hexagon's area."""
+    pb, want = _single_channel_k1(workloads, oracle_mod, 600)
+    assert pb.island_terms(0, 0, 0, 0)[0] == pytest.approx(want, rel=1e-8)
+    nodes = pb.island_nodes(0, 0, 0, 0)
+    R = pb.R[0]
+    assert len(nodes) == 600 * 600 and nodes[:, 2].sum() == pytest.approx(0.75 * R * R, rel=1e-12)
+    with pytest.raises(ValueError):
+        oracle_mod.Problem(workloads.config_small(n_ch=1), gl_order=0)
+
+
 def test_single_channel_gn_closed_form_soft(oracle_mod, workloads):
     """The incoherent-GN closed form (8/27) gamma^2 L_eff^2 asinh(pi^2/2 |b2| L_eff R^2)
     / (pi |b2| L_eff R^2) approximates the single-channel eta to a few percent."""
