@@ -1,0 +1,95 @@
+"""Pins of the ridge-resolving node rule of the oracle (oracle/ridge_rule.py), the
+estimate of Eq. 17's converged value where doubling the Gauss-Legendre order is
+out of reach: exact areas, the dispersionless closed form, the exact
+single-channel integral, and the converged level of the configured rule on an
+island with a narrow ridge."""
+import math
+
+import numpy as np
+import pytest
+
+
+@pytest.fixture(scope="module")
+def RR():
+    from oracle import ridge_rule
+    return ridge_rule
+
+
+def test_raised_cosine_is_the_oracles(RR, oracle_mod):
+    R, beta = 0.064, 0.01
+    x = np.linspace(-0.6 * R, 0.6 * R, 2001)
+    got = RR.raised_cosine(x, R, beta)
+    want = np.array([oracle_mod.rc(float(t), R, beta) for t in x])
+    assert np.array_equal(got, want)
+
+
+@pytest.mark.parametrize("isl", [(0, 0, 0), (0, 4, 4), (1, 2, 3), (0, 1, 0), (2, 2, 4)])
+def test_weights_sum_to_the_island_area(RR, oracle_mod, workloads, isl):
+    """The island is a polygon; both rules integrate 1 over it exactly."""
+    pb = oracle_mod.Problem(workloads.config_small(), gl_order=8)
+    rule = RR.RidgeRule(pb)
+    for n in (0, 2):
+        nd = rule.nodes(n, *isl, 8)
+        plain = pb.island_nodes(n, *isl)
+        if nd is None:
+            assert len(plain) == 0
+            continue
+        assert nd[3].sum() == pytest.approx(plain[:, 2].sum(), rel=1e-12)
+        assert np.all(nd[3] > 0)
+
+
+def test_dispersionless_closed_form(RR, oracle_mod, workloads):
+    """beta2 = beta3 = 0, Cr = 0, rectangular spectra: Y = gamma L_eff, so D of the
+    SCI island is (16/27) R^-2 (gamma L_eff)^2 times the hexagon's area 3 R^2 / 4."""
+    wl = workloads.config_small(n_ch=3, gl_order=8)
+    s = wl.spans[0]
+    s.D_ps_nm_km = s.S_ps_nm2_km = s.cr_per_w_km_thz = 0.0
+    wl.rolloff = 0.0
+    pb = oracle_mod.Problem(wl, gl_order=8)
+    sp = pb.spans[0]
+    Y = sp.gamma * oracle_mod.leff(sp.alpha, sp.L)
+    got, _ = RR.RidgeRule(pb).d_term(1, 1, 1, 1, 8)
+    assert got == pytest.approx(16 / 27 / pb.R[1] ** 2 * Y * Y * 0.75 * pb.R[1] ** 2, rel=1e-12)
+
+
+def test_single_channel_integral(RR, oracle_mod, workloads):
+    """The long single channel (Cr = 0, beta3 = 0, one segment): the ridges f1 = f and
+    f2 = f cross at the centre.  The error falls geometrically with the nodes per
+    piece (2e-3 at 8, 7e-8 at 32, 1e-12 at 64)."""
+    from scipy import integrate
+    wl = workloads.config_small(n_ch=1, gl_order=8)
+    wl.rolloff = 0.0
+    s = wl.spans[0]
+    s.length_m = 1500e3
+    s.cr_per_w_km_thz = 0.0
+    s.S_ps_nm2_km = -2 * s.D_ps_nm_km / 1550.0
+    pb = oracle_mod.Problem(wl, gl_order=8, terms=0, dz_km=1500.0)
+    sp = pb.spans[0]
+    R, a, g = pb.R[0], sp.alpha, sp.gamma
+    c = 4 * math.pi ** 2 * abs(sp.beta2)
+
+    def inner(u):
+        lo, hi = max(-R / 2, -R / 2 - u), min(R / 2, R / 2 - u)
+        if u == 0:
+            return (hi - lo) / a ** 2
+        k = c * abs(u) / a
+        return (math.atan(k * hi) - math.atan(k * lo)) / (a * c * abs(u))
+
+    val, _ = integrate.quad(inner, -R / 2, R / 2, points=[0.0], limit=400, epsabs=0, epsrel=1e-12)
+    want = 16 / 27 / R ** 2 * g * g * val
+    rule = RR.RidgeRule(pb)
+    assert rule.d_term(0, 0, 0, 0, 32)[0] == pytest.approx(want, rel=1e-6)
+    assert rule.d_term(0, 0, 0, 0, 64)[0] == pytest.approx(want, rel=1e-10)
+    assert abs(pb.island_terms(0, 0, 0, 0)[0] / want - 1) > 0.1  # the plain 8 x 8 rule: 14 % high
+
+
+def test_narrow_ridge_island(RR, oracle_mod, workloads):
+    """XCI island (0, 4, 4) of the 5-channel link: a ridge 0.4 GHz wide along f1 = f.
+    32 nodes per piece come within 1e-3 of the converged plain rule (256 x 256),
+    where the plain 32 x 32 rule is 40 % off."""
+    wl = workloads.config_small()
+    want = oracle_mod.Problem(wl, gl_order=256, terms=0).island_terms(0, 0, 4, 4)[0]
+    pb = oracle_mod.Problem(wl, gl_order=32, terms=0)
+    got, npts = RR.RidgeRule(pb).d_term(0, 0, 4, 4, 32)
+    assert abs(got / want - 1) < 1e-3 and npts < 4096
+    assert abs(pb.island_terms(0, 0, 4, 4)[0] / want - 1) > 0.3
