@@ -93,3 +93,11 @@ def test_narrow_ridge_island(RR, oracle_mod, workloads):
     got, npts = RR.RidgeRule(pb).d_term(0, 0, 4, 4, 32)
     assert abs(got / want - 1) < 1e-3 and npts < 4096
     assert abs(pb.island_terms(0, 0, 4, 4)[0] / want - 1) > 0.3
+
+
+def test_study_script_runs(capsys):
+    from oracle import ridge_study
+    ridge_study.main(["small", "0,2", "--plain", "8", "--ridge", "4,8"])
+    lines = capsys.readouterr().out.strip().splitlines()
+    assert len(lines) == 6 and all(" dB " in ln for ln in lines)
+    assert "+0.0000 dB" in lines[1] and "+0.0000 dB" in lines[4]  # the last ridge order is the reference
