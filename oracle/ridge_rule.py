@@ -1,8 +1,8 @@
-"""A node rule for the D integral (Eq. 17) that resolves the ridges of |mu|^2.
+"""A node rule for the island integrals (Eq. 17-21) that resolves the ridges of |mu|^2.
 
 TEST INFRASTRUCTURE, like the rest of oracle/: only tests/ may import it.  It
 shares no code with the CUDA path and is not a parity target of it; it estimates
-the converged value of Eq. 17 on links where doubling the Gauss-Legendre order of
+the converged value of Eq. 15 on links where doubling the Gauss-Legendre order of
 the configured node rule (Problem.eta_converged) is out of reach.
 
 Why a different rule.  With chi = 4 pi^2 (f1 - f)(f2 - f)[beta2 + pi beta3 (f1 + f2)]
@@ -13,12 +13,13 @@ against node gaps of gigahertz in a Gauss-Legendre rule over a 64 GHz channel.
 The spectral shapes add kinks: the raised cosine h(x) is smooth inside
 |x| < (1 - beta) R / 2 and on the roll-off, but not across the knee between them.
 
-The rule.  In the (outer w, inner u) order of the island (w = u + v + d):
-  * the outer range is cut at the island's own kinks (where the active inner limit
-    switches), at the knees of h3, where two inner break points cross, and at the
-    point where both ridges meet (f1 = f2 = f);
-  * each inner interval is cut at the knees of h1 and h2 and at the ridge points
-    f1 = f and f2 = f;
+The rule.  In each evaluation order, e.g. (outer w, inner u) with w = u + v + d:
+  * the outer range is cut at the knees of the outer shape and wherever two inner
+    break points cross (which includes the island's own kinks, where the active
+    inner limit switches, and the point where both ridges meet, f1 = f2 = f), and
+    at a ridge of the outer variable;
+  * each inner interval is cut at the knees of the other two shapes and at the
+    ridge points f1 = f and f2 = f that fall inside it;
   * a piece that does not end on a ridge gets ceil(n * length / total) nodes, at
     least n_min, placed by Gauss-Legendre;
   * a piece that ends on a ridge gets n nodes, placed by the sinh transformation
@@ -99,7 +100,15 @@ def raised_cosine(x, R, beta):
 
 class RidgeRule:
     """The rule above for the islands of an oracle Problem (identical spans: the
-    ridge half-widths take the first span's alpha, beta2 and beta3)."""
+    ridge half-widths take the first span's alpha, beta2 and beta3).
+
+    The three evaluation orders of Eq. 17-21 are those of the configured rule:
+    order 0 (outer w, inner u; D, G, H), order 1 (outer v, inner u; E) and
+    order 2 (outer u, inner v; F).  In each, the outer variable o and the inner t
+    are coupled by |y| <= C with y = +-(t - (s o + c)) the third variable; every
+    break point of the inner interval is a line t = a o + b (a = 0 or s), and the
+    outer range is cut wherever two such lines of different slope cross, at the
+    knees of the outer shape, and at a ridge of the outer variable."""
 
     def __init__(self, pb: O.Problem, n_min: int = 4):
         self.pb = pb
@@ -108,69 +117,156 @@ class RidgeRule:
         self.rolloff = pb.c.rolloff
         self.n_min = n_min
 
-    def nodes(self, n, n1, n2, n3, order):
-        """(u, v, w, weight) of every node of island (n1, n2, n3) of COI n, or None
-        if the island has zero area."""
+    def rows(self, n, n1, n2, n3, ordering, order):
+        """The rule's rows for one evaluation order: a list of (o, wo, t, wt) with the
+        outer node and weight and the inner nodes and weights, and a function
+        mapping (o, t) to (u, v, w); None if the island has zero area."""
         pb, be = self.pb, self.rolloff
         nu, R = pb.nu, pb.R
         W = R * (1 + be)
         f = nu[n]
         d = (nu[n1] - f) + (nu[n2] - nu[n3])
-        A, B, C = 0.5 * W[n3], 0.5 * W[n1], 0.5 * W[n2]
-        lo, hi = max(-A, d - (B + C)), min(A, d + (B + C))
+        k = [(1 - be) * R[m] / 2 for m in (n1, n2, n3)]   # knees of h1, h2, h3
+        half = [0.5 * W[m] for m in (n1, n2, n3)]
+        cc = 4 * math.pi ** 2 * abs(self.beta2 + 2 * math.pi * self.beta3 * f)
+        us, vs = f - nu[n1], f - nu[n2]                    # ridges u = us (f1 = f), v = vs (f2 = f)
+        if ordering == 0:   # o = w, t = u, v = (o - d) - t
+            A, B, s, c, C = half[2], half[0], 1.0, -d, half[1]
+            ko, kt, ky = k[2], k[0], k[1]
+            uvw = lambda o, t: (t, (s * o + c) - t, o)
+        elif ordering == 1:  # o = v, t = u, w = t + o + d
+            A, B, s, c, C = half[1], half[0], -1.0, -d, half[2]
+            ko, kt, ky = k[1], k[0], k[2]
+            uvw = lambda o, t: (t, o, t - (s * o + c))
+        else:                # o = u, t = v, w = t + o + d
+            A, B, s, c, C = half[0], half[1], -1.0, -d, half[2]
+            ko, kt, ky = k[0], k[1], k[2]
+            uvw = lambda o, t: (o, t, t - (s * o + c))
+        p_, q_ = s * (-(B + C) - c), s * ((B + C) - c)
+        lo, hi = max(-A, min(p_, q_)), min(A, max(p_, q_))
         if not hi > lo:
             return None
-        c = 4 * math.pi ** 2 * abs(self.beta2 + 2 * math.pi * self.beta3 * f)
-        k1, k2, k3 = (1 - be) * R[n1] / 2, (1 - be) * R[n2] / 2, (1 - be) * R[n3] / 2
-        outer = [(d + C - B, None), (d + B - C, None), (-k3, None), (k3, None)]
-        for ku in (k1, B):
-            for kv in (k2, C):
-                for su in (-1, 1):
-                    for sv in (-1, 1):
-                        outer.append((su * ku + sv * kv + d, None))
-        ridges = c > 0  # no dispersion: chi = 0 everywhere, no ridges
+        ridges = cc > 0  # no dispersion: chi = 0 everywhere, no ridges
+        hmax = self.alpha / (cc * max(half[0], half[1])) if ridges else None
+        # inner break lines t = a o + b: limits, knees, ridges
+        flat = [-B, B, -kt, kt]
+        slant = [c - C, c + C, c - ky, c + ky]
+        ridge_flat = ridge_slant = None
         if ridges:
-            outer.append(((f - nu[n1]) + (f - nu[n2]) + d, self.alpha / (c * max(B, C))))
+            if ordering == 0:
+                ridge_flat, ridge_slant = us, c - vs      # u = us; v = vs
+            elif ordering == 1:
+                ridge_flat = us
+            else:
+                ridge_flat = vs
+        outer = [(-ko, None), (ko, None)]
+        for b0 in flat + ([ridge_flat] if ridge_flat is not None else []):
+            for b1 in slant + ([ridge_slant] if ridge_slant is not None else []):
+                both = (b0 == ridge_flat and ridge_flat is not None and b1 == ridge_slant
+                        and ridge_slant is not None)
+                outer.append(((b0 - b1) / s, hmax if both else None))
+        if ridges and ordering == 1:
+            outer.append((vs, hmax))
+        if ridges and ordering == 2:
+            outer.append((us, hmax))
         xo, wo = _interval(lo, hi, outer, order, self.n_min)
-        U, V, Wt, WW = [], [], [], []
-        for w, ww in zip(xo, wo):
-            ilo, ihi = max(-B, w - d - C), min(B, w - d + C)
-            if not ihi > ilo:
+        out = []
+        for o, ww in zip(xo, wo):
+            m = s * o + c
+            tlo, thi = max(-B, m - C), min(B, m + C)
+            if not thi > tlo:
                 continue
-            pts = [(-k1, None), (k1, None), (w - d - k2, None), (w - d + k2, None)]
+            pts = [(-kt, None), (kt, None), (m - ky, None), (m + ky, None)]
             if ridges:
-                u1 = f - nu[n1]                   # ridge f1 = f
-                x2 = nu[n2] + (w - u1 - d) - f
-                if x2 != 0:
-                    pts.append((u1, self.alpha / (c * abs(x2))))
-                u2 = w - d - (f - nu[n2])         # ridge f2 = f
-                x1 = nu[n1] + u2 - f
-                if x1 != 0:
-                    pts.append((u2, self.alpha / (c * abs(x1))))
-            x, wi = _interval(ilo, ihi, pts, order, self.n_min)
-            U.append(x)
-            V.append(w - x - d)
-            Wt.append(np.full_like(x, w))
-            WW.append(ww * wi)
-        return tuple(map(np.concatenate, (U, V, Wt, WW)))
+                if ordering == 0:
+                    x2 = nu[n2] + (m - us) - f            # f2 - f on the ridge f1 = f
+                    if x2 != 0:
+                        pts.append((us, self.alpha / (cc * abs(x2))))
+                    tr = m - vs                           # ridge f2 = f
+                    x1 = nu[n1] + tr - f
+                    if x1 != 0:
+                        pts.append((tr, self.alpha / (cc * abs(x1))))
+                elif ordering == 1:
+                    x2 = nu[n2] + o - f
+                    if x2 != 0:
+                        pts.append((us, self.alpha / (cc * abs(x2))))
+                else:
+                    x1 = nu[n1] + o - f
+                    if x1 != 0:
+                        pts.append((vs, self.alpha / (cc * abs(x1))))
+            t, wt = _interval(tlo, thi, pts, order, self.n_min)
+            out.append((o, ww, t, wt))
+        return out, uvw
+
+    def _eval(self, n, n1, n2, n3, ordering, order):
+        r = self.rows(n, n1, n2, n3, ordering, order)
+        if r is None or not r[0]:
+            return None
+        rows, uvw = r
+        pb, R, nu, be = self.pb, self.pb.R, self.pb.nu, self.rolloff
+        o = np.concatenate([np.full(len(t), oo) for oo, _, t, _ in rows])
+        t = np.concatenate([t for _, _, t, _ in rows])
+        wi = np.concatenate([wt for _, _, _, wt in rows])
+        wo = np.array([ww for _, ww, _, _ in rows])
+        starts = np.cumsum([0] + [len(tt) for _, _, tt, _ in rows])[:-1]
+        u, v, w = uvw(o, t)
+        Y = pb.upsilon_many(nu[n1] + u, nu[n2] + v, nu[n])
+        h = (raised_cosine(u, R[n1], be), raised_cosine(v, R[n2], be), raised_cosine(w, R[n3], be))
+        return o, wo, wi, starts, Y, h
+
+    def terms(self, n, n1, n2, n3, order, which="DEFGH"):
+        """(D, E, F, G, H) of Eq. 17-21 for island (n1, n2, n3) of COI n with the
+        coefficients of the configured rule; terms not in `which` are 0."""
+        Rn, R = self.pb.R[n], self.pb.R
+        out = np.zeros(5)
+        if any(x in which for x in "DGH"):
+            e = self._eval(n, n1, n2, n3, 0, order)
+            if e is not None:
+                o, wo, wi, st, Y, (h1, h2, h3) = e
+                wrow = np.repeat(wo, np.diff(np.append(st, len(wi))))
+                out[0] = 16 / 27 * Rn / (R[n1] * R[n2] * R[n3]) * np.sum(wrow * wi * h1 * h2 * h3 * np.abs(Y) ** 2)
+                inner = np.add.reduceat(wi * np.sqrt(h1 * h2) * Y, st)
+                out[3] = 16 / 81 / Rn ** 3 * np.sum(wo * raised_cosine(o[st], R[n3], self.rolloff) * np.abs(inner) ** 2)
+                out[4] = 16 / 81 / Rn ** 4 * abs(np.sum(wrow * wi * np.sqrt(h1 * h2 * h3) * Y)) ** 2
+        for idx, ordering, coef, key in ((1, 1, 16 / 27, "E"), (2, 2, 32 / 81, "F")):
+            if key not in which:
+                continue
+            e = self._eval(n, n1, n2, n3, ordering, order)
+            if e is None:
+                continue
+            o, wo, wi, st, Y, (h1, h2, h3) = e
+            a, ho = (np.sqrt(h1 * h3), h2) if ordering == 1 else (np.sqrt(h2 * h3), h1)
+            inner = np.add.reduceat(wi * a * Y, st)
+            out[idx] = coef / Rn ** 3 * np.sum(wo * ho[st] * np.abs(inner) ** 2)
+        return out
 
     def d_term(self, n, n1, n2, n3, order):
         """D of Eq. 17 (with the coefficient of the configured rule) and the node count."""
-        nd = self.nodes(n, n1, n2, n3, order)
-        if nd is None:
+        r = self.rows(n, n1, n2, n3, 0, order)
+        if r is None:
             return 0.0, 0
-        u, v, w, wt = nd
-        pb, R, nu, be = self.pb, self.pb.R, self.pb.nu, self.rolloff
-        Y = pb.upsilon_many(nu[n1] + u, nu[n2] + v, nu[n])
-        h = raised_cosine(u, R[n1], be) * raised_cosine(v, R[n2], be) * raised_cosine(w, R[n3], be)
-        cf = 16.0 / 27.0 * R[n] / (R[n1] * R[n2] * R[n3])
-        return cf * float(np.sum(wt * h * np.abs(Y) ** 2)), len(u)
+        return float(self.terms(n, n1, n2, n3, order, "D")[0]), sum(len(t) for _, _, t, _ in r[0])
+
+    def pnli(self, n, order, egn=True):
+        """Eq. 15 for COI n: the sum over its islands of P1 P2 P3 (D + the EGN
+        corrections selected by the Kronecker deltas, if egn)."""
+        pb = self.pb
+        P, phi, psi = pb.P, pb.phi, pb.psi
+        s = 0.0
+        for a, b, c in pb.islands(n):
+            a, b, c = int(a), int(b), int(c)
+            which = "D"
+            if egn:
+                which += ("E" if a == c else "") + ("F" if b == c else "") + ("G" if a == b else "") + \
+                    ("H" if a == b == c else "")
+            t = self.terms(n, a, b, c, order, which)
+            v = t[0]
+            if egn:
+                v += (phi[a] * t[1] if a == c else 0) + (phi[b] * t[2] if b == c else 0) + \
+                    (phi[a] * t[3] if a == b else 0) + (psi[a] * t[4] if a == b == c else 0)
+            s += P[a] * P[b] * P[c] * v
+        return s
 
     def pnli_gn(self, n, order):
         """The GN part of Eq. 15 for COI n: sum over its islands of P1 P2 P3 D."""
-        P = self.pb.P
-        s = 0.0
-        for a, b, c in self.pb.islands(n):
-            a, b, c = int(a), int(b), int(c)
-            s += P[a] * P[b] * P[c] * self.d_term(n, a, b, c, order)[0]
-        return s
+        return self.pnli(n, order, egn=False)

@@ -1,4 +1,4 @@
-"""Discretisation error of the GN part of Eq. 15 per COI: the configured
+"""Discretisation error of Eq. 15 per COI (its GN part, or with --egn all of it): the configured
 Gauss-Legendre rule at several orders against the ridge-resolving rule of
 ridge_rule.py at several orders (the oracle only; CPU; minutes per COI of the
 120-channel link).
@@ -6,8 +6,9 @@ ridge_rule.py at several orders (the oracle only; CPU; minutes per COI of the
     python oracle/ridge_study.py small 0,1,2,3,4 --plain 32,64,512 --ridge 8,16,32
     python oracle/ridge_study.py cl 0 --plain 16,32,64 --ridge 16,32,64
 
-Prints one line per COI and rule: the sum over islands of P1 P2 P3 D and its
-ratio in dB to the last ridge-rule order."""
+Prints one line per COI and rule: the sum over islands of P1 P2 P3 D (with
+--egn, plus the EGN corrections) and its ratio in dB to the last ridge-rule
+order."""
 from __future__ import annotations
 
 import argparse
@@ -28,21 +29,23 @@ def main(argv=None):
     ap.add_argument("coi", help="comma-separated channel indices")
     ap.add_argument("--plain", default="32,64")
     ap.add_argument("--ridge", default="16,32")
+    ap.add_argument("--egn", action="store_true", help="include the EGN corrections (E, F, G, H)")
     a = ap.parse_args(argv)
     wl = workloads.config_small() if a.workload == "small" else workloads.config_cl()
     plain = [int(x) for x in a.plain.split(",") if x]
     ridge = [int(x) for x in a.ridge.split(",") if x]
     for n in (int(x) for x in a.coi.split(",")):
         res = []
-        pb = O.Problem(wl, gl_order=8, terms=0)
+        terms = 1 if a.egn else 0
+        pb = O.Problem(wl, gl_order=8, terms=terms)
         rule = RidgeRule(pb)
         n_isl = len(pb.islands(n))
         for q in ridge:
             t0 = time.time()
-            res.append((f"ridge {q}", rule.pnli_gn(n, q), time.time() - t0))
+            res.append((f"ridge {q}", rule.pnli(n, q, egn=a.egn), time.time() - t0))
         for q in plain:
             t0 = time.time()
-            s = O.Problem(wl, gl_order=q, terms=0).island_contribs(n)[1].sum()
+            s = O.Problem(wl, gl_order=q, terms=terms).island_contribs(n)[1].sum()
             res.append((f"plain {q}x{q}", s, time.time() - t0))
         ref = res[len(ridge) - 1][1] if ridge else res[-1][1]
         for name, s, t in res:

@@ -25,17 +25,21 @@ def test_raised_cosine_is_the_oracles(RR, oracle_mod):
 
 @pytest.mark.parametrize("isl", [(0, 0, 0), (0, 4, 4), (1, 2, 3), (0, 1, 0), (2, 2, 4)])
 def test_weights_sum_to_the_island_area(RR, oracle_mod, workloads, isl):
-    """The island is a polygon; both rules integrate 1 over it exactly."""
+    """The island is a polygon; both rules integrate 1 over it exactly, in each of
+    the three evaluation orders (the (u, v) -> (w, u) and (v, u) maps have unit
+    Jacobian)."""
     pb = oracle_mod.Problem(workloads.config_small(), gl_order=8)
     rule = RR.RidgeRule(pb)
     for n in (0, 2):
-        nd = rule.nodes(n, *isl, 8)
         plain = pb.island_nodes(n, *isl)
-        if nd is None:
-            assert len(plain) == 0
-            continue
-        assert nd[3].sum() == pytest.approx(plain[:, 2].sum(), rel=1e-12)
-        assert np.all(nd[3] > 0)
+        for ordering in (0, 1, 2):
+            r = rule.rows(n, *isl, ordering, 8)
+            if r is None:
+                assert len(plain) == 0
+                continue
+            area = sum(wo * wt.sum() for _, wo, _, wt in r[0])
+            assert area == pytest.approx(plain[:, 2].sum(), rel=1e-12)
+            assert all(np.all(wt > 0) and wo > 0 for _, wo, _, wt in r[0])
 
 
 def test_dispersionless_closed_form(RR, oracle_mod, workloads):
@@ -101,3 +105,42 @@ def test_study_script_runs(capsys):
     lines = capsys.readouterr().out.strip().splitlines()
     assert len(lines) == 6 and all(" dB " in ln for ln in lines)
     assert "+0.0000 dB" in lines[1] and "+0.0000 dB" in lines[4]  # the last ridge order is the reference
+
+
+def test_all_terms_dispersionless_exact(RR, oracle_mod, workloads):
+    """beta2 = beta3 = 0, Cr = 0, rectangular spectra: Y is constant, every inner
+    integral is Y times a length linear in the outer variable, so both rules give
+    D..H exactly on SCI, XCI and MCI islands of a 5-channel comb."""
+    wl = workloads.config_small(n_ch=5, gl_order=16)
+    s = wl.spans[0]
+    s.D_ps_nm_km = s.S_ps_nm2_km = s.cr_per_w_km_thz = 0.0
+    wl.rolloff = 0.0
+    pb = oracle_mod.Problem(wl, gl_order=16)
+    rule = RR.RidgeRule(pb)
+    for n, isl in ((2, (2, 2, 2)), (2, (1, 1, 0)), (2, (2, 3, 3)), (0, (0, 1, 1)), (1, (0, 2, 1)), (2, (1, 3, 2))):
+        want = pb.island_terms(n, *isl, all_terms=True)
+        got = rule.terms(n, *isl, 8)
+        assert np.allclose(got, want, rtol=1e-12, atol=0), (isl, got / want - 1)
+
+
+def test_e_f_mirror(RR, oracle_mod, workloads):
+    """E of (n1, n2, n1) and F of (n2, n1, n1) integrate mirrored structures (f1 <-> f2)
+    on mirrored nodes: equal up to their printed coefficients."""
+    pb = oracle_mod.Problem(workloads.config_small(), gl_order=16)
+    rule = RR.RidgeRule(pb)
+    for n, a, b in ((2, 1, 3), (0, 0, 2), (4, 3, 4)):
+        e = rule.terms(n, a, b, a, 16)[1] / (16 / 27)
+        f = rule.terms(n, b, a, a, 16)[2] / (32 / 81)
+        assert e == pytest.approx(f, rel=1e-12)
+
+
+def test_all_terms_narrow_ridge(RR, oracle_mod, workloads):
+    """XCI island (0, 4, 4) of the 5-channel link: all five terms at 32 nodes per
+    piece within 6e-3 of the converged plain rule (256 x 256), where the plain
+    32 x 32 rule is 6 % to 67 % off."""
+    wl = workloads.config_small()
+    want = oracle_mod.Problem(wl, gl_order=256).island_terms(0, 0, 4, 4, all_terms=True)
+    pb = oracle_mod.Problem(wl, gl_order=32)
+    got = RR.RidgeRule(pb).terms(0, 0, 4, 4, 32)
+    assert np.max(np.abs(got / want - 1)) < 6e-3
+    assert np.min(np.abs(pb.island_terms(0, 0, 4, 4, all_terms=True) / want - 1)) > 0.05
