@@ -117,6 +117,12 @@ class RidgeRule:
         self.rolloff = pb.c.rolloff
         self.n_min = n_min
 
+    def fcoi(self, n):
+        """The frequency at which COI n is evaluated: its centre plus the problem's
+        COI offset (Problem.set_coi_offsets), if any."""
+        off = getattr(self.pb, "_f_off", None)
+        return self.pb.nu[n] + (off[n] if off is not None else 0.0)
+
     def rows(self, n, n1, n2, n3, ordering, order):
         """The rule's rows for one evaluation order: a list of (o, wo, t, wt) with the
         outer node and weight and the inner nodes and weights, and a function
@@ -124,7 +130,7 @@ class RidgeRule:
         pb, be = self.pb, self.rolloff
         nu, R = pb.nu, pb.R
         W = R * (1 + be)
-        f = nu[n]
+        f = self.fcoi(n)
         d = (nu[n1] - f) + (nu[n2] - nu[n3])
         k = [(1 - be) * R[m] / 2 for m in (n1, n2, n3)]   # knees of h1, h2, h3
         half = [0.5 * W[m] for m in (n1, n2, n3)]
@@ -210,7 +216,7 @@ class RidgeRule:
         wo = np.array([ww for _, ww, _, _ in rows])
         starts = np.cumsum([0] + [len(tt) for _, _, tt, _ in rows])[:-1]
         u, v, w = uvw(o, t)
-        Y = pb.upsilon_many(nu[n1] + u, nu[n2] + v, nu[n])
+        Y = pb.upsilon_many(nu[n1] + u, nu[n2] + v, self.fcoi(n))
         h = (raised_cosine(u, R[n1], be), raised_cosine(v, R[n2], be), raised_cosine(w, R[n3], be))
         return o, wo, wi, starts, Y, h
 
@@ -266,6 +272,23 @@ class RidgeRule:
                     (phi[a] * t[3] if a == b else 0) + (psi[a] * t[4] if a == b == c else 0)
             s += P[a] * P[b] * P[c] * v
         return s
+
+    def pnli_3d(self, n, order, n_f, egn=True):
+        """Eq. 15 with the integral over f of Eq. 17-21 taken literally (the oracle's
+        eta_3d reading): an n_f-point Gauss-Legendre rule over f in
+        [f_n - R_n/2, f_n + R_n/2], each node the island sum at that COI frequency."""
+        pb = self.pb
+        x, w = O.gauss_legendre(int(n_f))
+        total = 0.0
+        try:
+            for xj, wj in zip(x, w):
+                off = np.zeros(pb.n_ch)
+                off[n] = 0.5 * xj * pb.R[n]
+                pb.set_coi_offsets(off)
+                total += 0.5 * wj * self.pnli(n, order, egn)
+        finally:
+            pb.set_coi_offsets(None)
+        return total
 
     def pnli_gn(self, n, order):
         """The GN part of Eq. 15 for COI n: sum over its islands of P1 P2 P3 D."""

@@ -144,3 +144,57 @@ def test_all_terms_narrow_ridge(RR, oracle_mod, workloads):
     got = RR.RidgeRule(pb).terms(0, 0, 4, 4, 32)
     assert np.max(np.abs(got / want - 1)) < 6e-3
     assert np.min(np.abs(pb.island_terms(0, 0, 4, 4, all_terms=True) / want - 1)) > 0.05
+
+
+def test_shifted_coi_single_channel(RR, oracle_mod, workloads):
+    """At a COI frequency moved by delta inside the band the ridges move with it;
+    the rule reaches the arctan closed form of the shifted single channel (64 nodes
+    per piece: 1e-10 at delta = 0.3 R/2, 5e-7 at -0.8 R/2, near the band edge)."""
+    from scipy import integrate
+    wl = workloads.config_small(n_ch=1, gl_order=8)
+    wl.rolloff = 0.0
+    s = wl.spans[0]
+    s.length_m = 1500e3
+    s.cr_per_w_km_thz = 0.0
+    s.S_ps_nm2_km = -2 * s.D_ps_nm_km / 1550.0
+    pb = oracle_mod.Problem(wl, gl_order=8, terms=0, dz_km=1500.0)
+    sp = pb.spans[0]
+    R, a, g = pb.R[0], sp.alpha, sp.gamma
+    c = 4 * math.pi ** 2 * abs(sp.beta2)
+    rule = RR.RidgeRule(pb)
+    for frac in (0.3, -0.8):
+        delta = frac * R / 2
+
+        def inner(p):
+            lo = max(-R / 2 - delta, -R / 2 - delta - p)
+            hi = min(R / 2 - delta, R / 2 - delta - p)
+            if hi <= lo:
+                return 0.0
+            if p == 0.0:
+                return (hi - lo) / a ** 2
+            k = c * abs(p) / a
+            return (math.atan(k * hi) - math.atan(k * lo)) / (a * c * abs(p))
+
+        val, _ = integrate.quad(inner, -R / 2 - delta, R / 2 - delta, points=[0.0, -delta], limit=400,
+                                epsabs=0, epsrel=1e-12)
+        want = 16 / 27 / R ** 2 * g * g * val
+        pb.set_coi_offsets(np.array([delta]))
+        try:
+            got = rule.d_term(0, 0, 0, 0, 64)[0]
+        finally:
+            pb.set_coi_offsets(None)
+        assert got == pytest.approx(want, rel=1e-6), (frac, got / want - 1)
+
+
+def test_f_integral_matches_the_oracle_dispersionless(RR, oracle_mod, workloads):
+    """Without dispersion the integrand is constant on every island, both rules are
+    exact at every COI frequency, and the f-integrated sums agree (the island sets
+    change with f inside the band)."""
+    wl = workloads.config_small(n_ch=3, gl_order=8)
+    s = wl.spans[0]
+    s.D_ps_nm_km = s.S_ps_nm2_km = s.cr_per_w_km_thz = 0.0
+    wl.rolloff = 0.0
+    pb = oracle_mod.Problem(wl, gl_order=8)
+    want = pb.eta_3d(4, coi=[1])[1][0]
+    got = RR.RidgeRule(pb).pnli_3d(1, 8, 4)
+    assert got == pytest.approx(want, rel=1e-12)
