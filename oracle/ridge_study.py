@@ -7,8 +7,8 @@ ridge_rule.py at several orders (the oracle only; CPU; minutes per COI of the
     python oracle/ridge_study.py cl 0 --plain 16,32,64 --ridge 16,32,64
 
 Prints one line per COI and rule: the sum over islands of P1 P2 P3 D (with
---egn, plus the EGN corrections) and its ratio in dB to the last ridge-rule
-order."""
+--egn, plus the EGN corrections; with --f3d N, integrated over the COI band by N
+nodes) and its ratio in dB to the last ridge-rule order."""
 from __future__ import annotations
 
 import argparse
@@ -30,6 +30,8 @@ def main(argv=None):
     ap.add_argument("--plain", default="32,64")
     ap.add_argument("--ridge", default="16,32")
     ap.add_argument("--egn", action="store_true", help="include the EGN corrections (E, F, G, H)")
+    ap.add_argument("--f3d", type=int, default=0,
+                    help="integrate over the COI band with this many Gauss-Legendre nodes (0: white NLI)")
     a = ap.parse_args(argv)
     wl = workloads.config_small() if a.workload == "small" else workloads.config_cl()
     plain = [int(x) for x in a.plain.split(",") if x]
@@ -42,10 +44,12 @@ def main(argv=None):
         n_isl = len(pb.islands(n))
         for q in ridge:
             t0 = time.time()
-            res.append((f"ridge {q}", rule.pnli(n, q, egn=a.egn), time.time() - t0))
+            v = rule.pnli_3d(n, q, a.f3d, egn=a.egn) if a.f3d else rule.pnli(n, q, egn=a.egn)
+            res.append((f"ridge {q}", v, time.time() - t0))
         for q in plain:
             t0 = time.time()
-            s = O.Problem(wl, gl_order=q, terms=terms).island_contribs(n)[1].sum()
+            pq = O.Problem(wl, gl_order=q, terms=terms)
+            s = pq.eta_3d(a.f3d, coi=[n])[1][0] if a.f3d else pq.island_contribs(n)[1].sum()
             res.append((f"plain {q}x{q}", s, time.time() - t0))
         ref = res[len(ridge) - 1][1] if ridge else res[-1][1]
         for name, s, t in res:

@@ -105,6 +105,8 @@ def test_study_script_runs(capsys):
     lines = capsys.readouterr().out.strip().splitlines()
     assert len(lines) == 6 and all(" dB " in ln for ln in lines)
     assert "+0.0000 dB" in lines[1] and "+0.0000 dB" in lines[4]  # the last ridge order is the reference
+    ridge_study.main(["small", "1", "--plain", "4", "--ridge", "4", "--egn", "--f3d", "2"])
+    assert len(capsys.readouterr().out.strip().splitlines()) == 2
 
 
 def test_all_terms_dispersionless_exact(RR, oracle_mod, workloads):
