@@ -110,12 +110,15 @@ class RidgeRule:
     outer range is cut wherever two such lines of different slope cross, at the
     knees of the outer shape, and at a ridge of the outer variable."""
 
-    def __init__(self, pb: O.Problem, n_min: int = 4):
+    def __init__(self, pb: O.Problem, n_min: int = 4, knees: bool = True):
+        """knees=False leaves out the cuts at the raised-cosine knees (the ridge and
+        kink cuts stay), the simpler form a GPU planner would start from."""
         self.pb = pb
         sp = pb.spans[0]
         self.alpha, self.beta2, self.beta3 = sp.alpha, sp.beta2, sp.beta3
         self.rolloff = pb.c.rolloff
         self.n_min = n_min
+        self.knees = knees
 
     def fcoi(self, n):
         """The frequency at which COI n is evaluated: its centre plus the problem's
@@ -155,8 +158,8 @@ class RidgeRule:
         ridges = cc > 0  # no dispersion: chi = 0 everywhere, no ridges
         hmax = self.alpha / (cc * max(half[0], half[1])) if ridges else None
         # inner break lines t = a o + b: limits, knees, ridges
-        flat = [-B, B, -kt, kt]
-        slant = [c - C, c + C, c - ky, c + ky]
+        flat = [-B, B] + ([-kt, kt] if self.knees else [])
+        slant = [c - C, c + C] + ([c - ky, c + ky] if self.knees else [])
         ridge_flat = ridge_slant = None
         if ridges:
             if ordering == 0:
@@ -165,7 +168,7 @@ class RidgeRule:
                 ridge_flat = us
             else:
                 ridge_flat = vs
-        outer = [(-ko, None), (ko, None)]
+        outer = [(-ko, None), (ko, None)] if self.knees else []
         for b0 in flat + ([ridge_flat] if ridge_flat is not None else []):
             for b1 in slant + ([ridge_slant] if ridge_slant is not None else []):
                 both = (b0 == ridge_flat and ridge_flat is not None and b1 == ridge_slant
@@ -182,7 +185,7 @@ class RidgeRule:
             tlo, thi = max(-B, m - C), min(B, m + C)
             if not thi > tlo:
                 continue
-            pts = [(-kt, None), (kt, None), (m - ky, None), (m + ky, None)]
+            pts = [(-kt, None), (kt, None), (m - ky, None), (m + ky, None)] if self.knees else []
             if ridges:
                 if ordering == 0:
                     x2 = nu[n2] + (m - us) - f            # f2 - f on the ridge f1 = f

@@ -30,6 +30,7 @@ def main(argv=None):
     ap.add_argument("--plain", default="32,64")
     ap.add_argument("--ridge", default="16,32")
     ap.add_argument("--egn", action="store_true", help="include the EGN corrections (E, F, G, H)")
+    ap.add_argument("--no-knees", action="store_true", help="ridge rule without the cuts at the spectral knees")
     ap.add_argument("--f3d", type=int, default=0,
                     help="integrate over the COI band with this many Gauss-Legendre nodes (0: white NLI)")
     a = ap.parse_args(argv)
@@ -40,7 +41,7 @@ def main(argv=None):
         res = []
         terms = 1 if a.egn else 0
         pb = O.Problem(wl, gl_order=8, terms=terms)
-        rule = RidgeRule(pb)
+        rule = RidgeRule(pb, knees=not a.no_knees)
         n_isl = len(pb.islands(n))
         for q in ridge:
             t0 = time.time()

@@ -29,17 +29,18 @@ def test_weights_sum_to_the_island_area(RR, oracle_mod, workloads, isl):
     the three evaluation orders (the (u, v) -> (w, u) and (v, u) maps have unit
     Jacobian)."""
     pb = oracle_mod.Problem(workloads.config_small(), gl_order=8)
-    rule = RR.RidgeRule(pb)
+    rules = [RR.RidgeRule(pb), RR.RidgeRule(pb, knees=False)]
     for n in (0, 2):
         plain = pb.island_nodes(n, *isl)
-        for ordering in (0, 1, 2):
-            r = rule.rows(n, *isl, ordering, 8)
-            if r is None:
-                assert len(plain) == 0
-                continue
-            area = sum(wo * wt.sum() for _, wo, _, wt in r[0])
-            assert area == pytest.approx(plain[:, 2].sum(), rel=1e-12)
-            assert all(np.all(wt > 0) and wo > 0 for _, wo, _, wt in r[0])
+        for rule in rules:
+            for ordering in (0, 1, 2):
+                r = rule.rows(n, *isl, ordering, 8)
+                if r is None:
+                    assert len(plain) == 0
+                    continue
+                area = sum(wo * wt.sum() for _, wo, _, wt in r[0])
+                assert area == pytest.approx(plain[:, 2].sum(), rel=1e-12)
+                assert all(np.all(wt > 0) and wo > 0 for _, wo, _, wt in r[0])
 
 
 def test_dispersionless_closed_form(RR, oracle_mod, workloads):
