@@ -137,6 +137,26 @@ def aggregate_ranks(ms_local: float, evals_local: int, device=None):
 
 # --------------------------------------------------------------------------- oracle timing
 
+def host_cpu() -> str:
+    """The host CPU as /proc/cpuinfo names it: the model name on x86, the
+    implementer and part numbers on Arm; the machine type elsewhere."""
+    import platform
+    fields = {}
+    try:
+        with open("/proc/cpuinfo") as fh:
+            for ln in fh:
+                k, _, v = ln.partition(":")
+                fields.setdefault(k.strip(), v.strip())
+    except OSError:
+        pass
+    if fields.get("model name"):
+        return fields["model name"]
+    if fields.get("CPU implementer"):
+        return (f"{platform.machine()} (implementer {fields['CPU implementer']}, "
+                f"part {fields.get('CPU part', '?')})")
+    return platform.machine() or "unknown"
+
+
 def oracle_rate(wl, target_s: float, seed: int = 0):
     """Time the FP64 CPU oracle (as it stands) on a seeded sample of islands of the
     workload, on all host cores (one island per thread).  Returns (channel-evals/s,
@@ -200,7 +220,8 @@ def run_reference(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * 120 / value, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD, "precision": "fp64 CPU oracle", "n_ch": 120},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": desc},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": desc,
+                         "cpu": host_cpu()},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     emit(line, args.jsonl)
@@ -706,7 +727,7 @@ def main():
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         r, threads, desc, _, _ = oracle_rate(wl, 15.0)
-        cpu = {"value": r, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": desc}
+        cpu = {"value": r, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": desc, "cpu": host_cpu()}
 
     if rank == 0:
         line = {

@@ -18,3 +18,9 @@ def test_jsonl_record_and_config_hash(tmp_path, capsys):
     assert recs[0]["config_hash"] == recs[1]["config_hash"] != recs[2]["config_hash"]
     bench.emit(a, None)                                  # without a path nothing is written
     assert len(open(path).readlines()) == 3
+
+
+def test_host_cpu_is_named():
+    import bench
+    name = bench.host_cpu()
+    assert isinstance(name, str) and name and name != "unknown"
