@@ -75,3 +75,26 @@ def test_random_links_are_seeded_and_in_range(workloads):
         p_dbm = 10 * np.log10(np.asarray(w.launch_power_w) / 1e-3)
         assert np.all(np.isfinite(p_dbm)) and -8.0 < p_dbm.min() and p_dbm.max() < 10.0
         assert set(w.formats) <= set(workloads.FORMATS) and len(w.formats) == w.n_ch
+
+
+def test_tables_match_the_printed_parameters(workloads):
+    """table1 / table2 carry the parameters printed in Table I and Table II (the
+    golden fixture quotes them with their citation)."""
+    import json
+    import pathlib
+    gold = json.loads((pathlib.Path(__file__).parent / "golden" / "paper_values.json").read_text())
+    for name in ("table1", "table2"):
+        g = gold[name]
+        n_sp = g["n_spans"] if isinstance(g["n_spans"], list) else [g["n_spans"]]
+        cr = g["cr"] if isinstance(g["cr"], list) else [g["cr"]]
+        for ns in n_sp:
+            for c in cr:
+                w = workloads.table1(n_spans=ns, cr=c) if name == "table1" else workloads.table2()
+                s = w.spans[0]
+                assert w.n_ch == g["n_ch"] and len(w.spans) == ns
+                assert s.length_m == g["span_km"] * 1e3 and s.alpha_db_km == g["alpha_db_km"]
+                assert s.D_ps_nm_km == g["D"] and s.S_ps_nm2_km == g["S"] and s.gamma_per_w_km == g["gamma"]
+                assert s.cr_per_w_km_thz == c
+                assert math.isclose(w.symbol_rate_baud[0], g["R_gbd"] * 1e9)
+                assert math.isclose(w.centre_hz[1] - w.centre_hz[0], g["spacing_ghz"] * 1e9, rel_tol=1e-9)
+                assert math.isclose(10 * math.log10(sum(w.launch_power_w) / 1e-3), g["ptot_dbm"], abs_tol=1e-9)
