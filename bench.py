@@ -35,6 +35,7 @@ WORKLOAD = ("120ch x 64GBd C+L on 75GHz grid (9 THz), 10x80km SSMF, 2 dBm/ch, se
             "32x32 Gauss-Legendre per island, dz=1km, EGN (D+E+F+G+H)")
 SM_COUNT_GB300 = 152
 FP32_LANES_PER_SM = 128
+MUFU_PER_POINT = 6  # D-only point path of the FP32C D/G/H pass: sin x 3, cos x 2, rcp x 1
 
 
 def log(*a):
@@ -114,6 +115,54 @@ def gpu_id_for_smi(local_rank: int) -> str:
     if vis:
         return vis.split(",")[local_rank if local_rank < len(vis.split(",")) else 0]
     return str(local_rank)
+
+
+# --------------------------------------------------------------------------- pipe peaks
+
+# launch shape and rounds per thread of each throughput probe: full occupancy
+# (2048 threads per SM), about 10 ms per launch on a GB300
+PROBES = {"ffma": 160000, "ffma2": 80000, "dfma": 2500, "mufu_sin": 20000, "mufu_ex2": 20000, "mufu_rcp": 20000}
+PROBE_THREADS = 256
+
+
+def measure_peaks(kinds, stream, reps: int = 5, sampler=None) -> dict:
+    """Throughput of the arithmetic pipes with the library's probe kernels
+    (egn_probe_launch), CUDA events on `stream`: best of `reps` launches after one
+    warm-up.  TFLOP/s for the FMA probes, Gop/s for the MUFU probes, and the
+    same per SM per clock at the median SM clock sampled meanwhile."""
+    import torch
+    from paper_2412_11614_gb300 import egn
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    blocks = sms * (2048 // PROBE_THREADS)
+    sink = torch.empty(blocks * PROBE_THREADS, dtype=torch.float64, device="cuda")
+    out = {}
+    smi = sampler
+    if smi is not None:
+        smi.start()
+        time.sleep(0.3)
+    for kind in kinds:
+        iters = PROBES[kind]
+        ops = egn.probe_ops(kind, blocks, PROBE_THREADS, iters)
+        with torch.cuda.stream(stream):
+            egn.probe_launch(kind, blocks, PROBE_THREADS, iters, sink, stream.cuda_stream)
+            best = None
+            for _ in range(reps):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                egn.probe_launch(kind, blocks, PROBE_THREADS, iters, sink, stream.cuda_stream)
+                e1.record(stream)
+                e1.synchronize()
+                ms = e0.elapsed_time(e1)
+                best = ms if best is None else min(best, ms)
+        rate = ops / (best * 1e-3)
+        out[kind] = {"ms": best, "ops_per_launch": ops,
+                     ("tflops" if "fma" in kind else "gops"): rate / (1e12 if "fma" in kind else 1e9)}
+    clocks = smi.stop() if smi is not None else {}
+    mhz = clocks.get("sm_mhz")
+    for kind, r in out.items():
+        rate = r["ops_per_launch"] / (r["ms"] * 1e-3)
+        r["per_sm_per_clock"] = rate / (sms * mhz * 1e6) if mhz else None
+    return {"probes": out, "sms": sms, "blocks": blocks, "threads": PROBE_THREADS, "clocks": clocks}
 
 
 # --------------------------------------------------------------------------- ranks
@@ -248,6 +297,79 @@ def flops_per_point(precision: str, K: int) -> float:
     segment (4 K), in both precisions.  The per-point phase, trigonometry and
     weights are not counted."""
     return 4.0 * K
+
+
+def timed_evals(ln, opts, n_ch, stream, flush, steps: int, warm: int):
+    """Device ms per evaluation (egn_nli_eta_device, CUDA events on `stream`, L2
+    flushed before each) and the last evaluation's eta."""
+    import torch
+    ws = torch.empty(ln.workspace_size(opts), dtype=torch.uint8, device="cuda")
+    eta = torch.empty(n_ch, dtype=torch.float64, device="cuda")
+    pnli = torch.empty(n_ch, dtype=torch.float64, device="cuda")
+    times = []
+    with torch.cuda.stream(stream):
+        for i in range(warm + steps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            ln.nli_eta_device(opts, ws, eta, pnli)
+            e1.record(stream)
+            e1.synchronize()
+            if i >= warm:
+                times.append(e0.elapsed_time(e1))
+    return statistics.mean(times), eta.cpu().numpy()
+
+
+def fp64_denominator(args, wl, ln, eta32, value, stream, flush) -> dict:
+    """The metric's denominator and precision gate: the plain FP64 GPU integrator
+    (EGN_PREC_FP64) on the same link and GPU, its channel-evals/s, FP32C's speed-up
+    over it and FP32C's per-channel error against it in dB (every channel); then
+    the launch-power sweep -2..+4 dBm/ch (1 dB steps) of the same link in FP32C,
+    each power against one FP64 evaluation (ISRS strength grows with the total
+    power, Eq. 12)."""
+    import numpy as np
+    from paper_2412_11614_gb300 import egn, workloads as W
+    n_ch = wl.n_ch
+    o64 = egn.make_opts(gl_order=wl.gl_order, dz_km=wl.dz_km, precision=egn.EGN_PREC_FP64, terms=egn.EGN_TERMS_EGN,
+                        stream=stream.cuda_stream)
+    o32 = egn.make_opts(gl_order=wl.gl_order, dz_km=wl.dz_km, precision=egn.EGN_PREC_FP32C, terms=egn.EGN_TERMS_EGN,
+                        stream=stream.cuda_stream)
+    ms64, eta64 = timed_evals(ln, o64, n_ch, stream, flush, steps=args.fp64_steps, warm=1)
+    err = np.abs(10 * np.log10(eta32 / eta64))
+    out = {"fp64_gpu": {"ms_per_step": ms64, "value": n_ch / (ms64 * 1e-3), "unit": UNIT, "steps": args.fp64_steps,
+                        "warmup": 1, "dtype": "f64",
+                        "note": "plain FP64 GPU integrator (EGN_PREC_FP64), same link, same GPU, CUDA events, "
+                                "L2 flushed between steps"},
+           "speedup_vs_fp64_gpu": value / (n_ch / (ms64 * 1e-3)),
+           "max_db_vs_fp64": float(err.max()), "mean_db_vs_fp64": float(err.mean()),
+           "worst_channel_vs_fp64": int(err.argmax())}
+    if args.no_sweep:
+        return out
+    sweep = {"p_dbm": [], "ms_fp32c": [], "ms_fp64": [], "channel_evals_per_s_fp32c": [], "max_abs_db_vs_fp64": [],
+             "mean_abs_db_vs_fp64": [], "worst_channel": [], "delta_rho_db_per_span": []}
+    for p_dbm in range(-2, 5):
+        wp = W.config_cl(n_ch=n_ch, p_dbm=float(p_dbm))
+        lp = egn.link_from_workload(wp)
+        m32, e32 = timed_evals(lp, o32, n_ch, stream, flush, steps=3, warm=1)
+        m64, e64 = timed_evals(lp, o64, n_ch, stream, flush, steps=1, warm=0)
+        lp.close()
+        d = np.abs(10 * np.log10(e32 / e64))
+        ptot = sum(wp.launch_power_w)
+        sp = wp.spans[0]
+        a = sp.alpha_db_km * math.log(10) / 10
+        leff = (1 - math.exp(-a * sp.length_m * 1e-3)) / a
+        btot = (wp.centre_hz[-1] - wp.centre_hz[0]) * 1e-12 * n_ch / (n_ch - 1)
+        sweep["p_dbm"].append(p_dbm)
+        sweep["ms_fp32c"].append(m32)
+        sweep["ms_fp64"].append(m64)
+        sweep["channel_evals_per_s_fp32c"].append(n_ch / (m32 * 1e-3))
+        sweep["max_abs_db_vs_fp64"].append(float(d.max()))
+        sweep["mean_abs_db_vs_fp64"].append(float(d.mean()))
+        sweep["worst_channel"].append(int(d.argmax()))
+        sweep["delta_rho_db_per_span"].append(10 * math.log10(math.e) * ptot * sp.cr_per_w_km_thz * leff * btot)
+    out["config3_power_sweep"] = dict(sweep, workload="the benchmark link at -2..+4 dBm/ch, FP32C against the plain "
+                                                      "FP64 GPU integrator, every channel")
+    return out
 
 
 def run_mu_compare(args):
@@ -449,6 +571,40 @@ def run_surrogate(args):
     inf_ms = e0.elapsed_time(e1) / reps
     flops = 2.0 * rows * (S.F_PAD * S.HIDDEN + (S.LAYERS - 1) * S.HIDDEN * S.HIDDEN + S.HIDDEN)
     gemm = gemm_roofline(8192, 5)
+    # the per-link network (n_ch powers + span count + span length + Cr -> 3 x 512 GELU -> n_ch)
+    # on the same training and held-out links
+    ltr = np.stack([S.link_features(w) for w in train_w])
+    lte = np.stack([S.link_features(w) for w in test_w])
+    ytr_l = np.stack(lab[:len(train_w)])
+    yte_l = np.stack(lab[len(train_w):])
+    lmodel = S.LinkSurrogate(n_ch=ytr_l.shape[1], seed=0)
+    lmodel.fit_normalisation(ltr, ytr_l)
+    t0 = time.perf_counter()
+    llosses = S.train(lmodel, ltr, ytr_l, args.sur_steps, batch_rows=min(512, len(ltr)), seed=0)
+    torch.cuda.synchronize()
+    ltrain_s = time.perf_counter() - t0
+    lerr = lmodel.predict_rows(lte) - yte_l
+    base_err = yte_l - ytr_l.mean(axis=0)  # no network: each channel's mean training label
+    big_l = np.tile(lte, (max(1, 8192 // len(lte)), 1))
+    lmodel.predict_rows(big_l)
+    lrows, lrows_pad = lmodel._load_inputs(big_l, None)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        lmodel._forward(lrows, lrows_pad, None)
+        S.K.outputs(lmodel.acc, lrows, lrows_pad, lmodel.n_ch, lmodel.b_out, lmodel.y)
+    e1.record()
+    e1.synchronize()
+    linf_ms = e0.elapsed_time(e1) / reps
+    link_net = {"network": f"{lmodel.n_in} inputs (powers, span count, span length, Cr) -> 3 x 512 GELU -> "
+                           f"{lmodel.n_ch} outputs, BF16 tensor cores",
+                "train_steps": args.sur_steps, "batch_links": min(512, len(ltr)), "train_seconds": ltrain_s,
+                "loss_first": llosses[0], "loss_last": float(np.mean(llosses[-20:])),
+                "heldout_mae_db": float(np.mean(np.abs(lerr))),
+                "heldout_p99_abs_db": float(np.quantile(np.abs(lerr), 0.99)),
+                "heldout_max_abs_db": float(np.max(np.abs(lerr))),
+                "inference_links": lrows, "inference_ms": linf_ms,
+                "inference_channel_evals_per_s": lrows * lmodel.n_ch / (linf_ms * 1e-3)}
     print(json.dumps({
         "workload": f"surrogate: {args.sur_train} training + {args.sur_test} held-out seeded 120-ch C+L links "
                     "(1-30 identical SSMF spans of 50-120 km, Cr 0.014-0.042, tilted rippled powers); labels from "
@@ -462,7 +618,10 @@ def run_surrogate(args):
         "heldout_max_abs_db": float(np.max(np.abs(err))),
         "inference_rows": rows, "inference_ms": inf_ms, "inference_channel_evals_per_s": rows / (inf_ms * 1e-3),
         "inference_tflops": flops / (inf_ms * 1e-3) / 1e12,
-        "gemm_8192": gemm}), flush=True)
+        "gemm_8192": gemm,
+        "per_link_network": link_net,
+        "no_network_baseline": {"what": "each channel's mean training label",
+                                "heldout_mae_db": float(np.mean(np.abs(base_err)))}}), flush=True)
     return 0
 
 
@@ -561,6 +720,12 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="fp32c", choices=["fp32c", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true",
+                    help="skip the plain FP64 GPU integrator leg and the launch-power sweep")
+    ap.add_argument("--no-sweep", action="store_true", help="skip the -2..+4 dBm/ch launch-power sweep")
+    ap.add_argument("--fp64-steps", type=int, default=3)
+    ap.add_argument("--peaks", action="store_true",
+                    help="measure the FP32, FP32x2, FP64 and MUFU pipe peaks with the probe kernels")
     ap.add_argument("--e2e-steps", type=int, default=None)
     ap.add_argument("--n-ch", type=int, default=120, help="channels of the C+L grid (120 = the benchmark)")
     ap.add_argument("--points-per-thread", type=int, default=4, choices=[4, 8],
@@ -586,6 +751,16 @@ def main():
     ap.add_argument("--sur-labels", default=None,
                     help="directory of sharded label files with a resume index (labels computed only where missing)")
     args = ap.parse_args()
+    if args.peaks:
+        import torch
+        from paper_2412_11614_gb300 import _build
+        _build.build()
+        torch.cuda.set_device(0)
+        st = torch.cuda.Stream()
+        res = measure_peaks(list(PROBES), st, reps=max(5, args.steps), sampler=ClockSampler(gpu_id_for_smi(0)))
+        res["gpu"] = torch.cuda.get_device_name(0)
+        print(json.dumps(res), flush=True)
+        return 0
     if args.surrogate:
         return run_surrogate(args)
     if args.f3d:
@@ -681,12 +856,20 @@ def main():
     K = math.ceil(80.0 / wl.dz_km)
     flops = points * flops_per_point(args.precision, K)
     clk = clocks.get("sm_max_mhz") or 2070.0
+    # measured pipe peaks (the library's probe kernels, this run, this GPU)
+    peaks = measure_peaks(["ffma", "ffma2", "dfma", "mufu_sin"], stream, sampler=ClockSampler(gpu_id_for_smi(local)))
+    pr = peaks["probes"]
+    pclk = peaks["clocks"].get("sm_mhz")
     if args.precision == "fp32c":
-        peak = SM_COUNT_GB300 * FP32_LANES_PER_SM * 2 * clk * 1e6 / 1e12
-        peak_note = f"FP32 FMA: 152 SMs x 128 lanes x 2 FLOP x {clk:.0f} MHz (derived, not measured)"
+        best = max(("ffma", "ffma2"), key=lambda k: pr[k]["tflops"])
+        peak = pr[best]["tflops"]
+        peak_note = (f"measured in this run: FP32 FMA probe ({'fma.rn.f32x2' if best == 'ffma2' else 'fma.rn.f32'} "
+                     f"chains, egn_probe_launch, best of 5) at a median {pclk} MHz; derived "
+                     f"152 SMs x 128 lanes x 2 FLOP x {clk:.0f} MHz = "
+                     f"{SM_COUNT_GB300 * FP32_LANES_PER_SM * 2 * clk * 1e6 / 1e12:.1f}")
     else:
-        peak = 1.25
-        peak_note = "FP64: 1.25 TFLOP/s nominal GB300 (no measured FP64 peak)"
+        peak = pr["dfma"]["tflops"]
+        peak_note = f"measured in this run: FP64 FMA probe (fma.rn.f64 chains, egn_probe_launch) at a median {pclk} MHz"
     achieved = flops / (dgh_ms * 1e-3) / 1e12
     # DRAM bytes (read + write) of one FP32C D/G/H launch on the 120-channel
     # workload, from one ncu capture of that launch (dram__bytes_read.sum +
@@ -697,7 +880,17 @@ def main():
                 "traffic": traffic, "traffic_unit": "bytes per launch", "kernel": "integrate D/G/H pass",
                 "peak_note": peak_note,
                 "kernel_ms": dgh_ms, "flops_per_launch": flops,
+                "peaks_measured": {k: {kk: v for kk, v in r.items() if kk != "ops_per_launch"} for k, r in pr.items()},
                 "stage_ms": {k: statistics.mean(s[k] for s in stage) for k in stage[0]}}
+    if args.precision == "fp32c":
+        # special-function unit: per point of the D-only path one sine of the segment
+        # angle, two sines of the phased array, one reciprocal and two cosines of the
+        # raised-cosine shapes (the c_k table exponentials are not counted)
+        mufu = points * MUFU_PER_POINT
+        sfu_gops = mufu / (dgh_ms * 1e-3) / 1e9
+        roofline.update({"sfu_achieved_gops": sfu_gops, "sfu_peak_gops": pr["mufu_sin"]["gops"],
+                         "sfu_frac": sfu_gops / pr["mufu_sin"]["gops"], "sfu_ops_per_point": MUFU_PER_POINT,
+                         "sfu_peak_note": "measured in this run: sin.approx.f32 probe (egn_probe_launch)"})
 
     # end to end through the host API: pinned inputs -> egn_set_wdm -> egn_nli_eta -> host outputs
     e2e_steps = args.e2e_steps or max(3, min(args.steps, 5))
@@ -723,6 +916,10 @@ def main():
     e2e = {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
            "ms_per_step": e2e_s * 1e3, "api": "egn_set_wdm + egn_nli_eta (host buffers)"}
     ln2.close()
+
+    extras = {}
+    if rank == 0 and args.precision == "fp32c" and not args.no_fp64:
+        extras = fp64_denominator(args, wl, ln, eta.cpu().numpy(), value / world, stream, flush)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -750,6 +947,7 @@ def main():
             "wall_s_timed_region": t_wall,
             "eta_db_sample": [float(10 * np.log10(x)) for x in eta.cpu().numpy()[:: 30]],
         }
+        line.update(extras)
         emit(line, args.jsonl)
     ln.close()
     if world > 1:

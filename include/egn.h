@@ -211,12 +211,22 @@ egn_status egn_nli_eta_device(egn_link* link, const egn_opts* opts, void* worksp
  * workspace) is one 16 MiB array compiled into the library, which every GPU that
  * loads the library holds until the process exits; an evaluation that needs more
  * (egn_workspace_size + the tables; about 60 channels at EGN_PREC_FP32C) is
- * refused with EGN_E_CAPACITY.  The first call on a device looks up the array's
- * device address (cudaGetSymbolAddress) with that device current; make that first
- * call before any stream capture.  All calls share the one array and it keeps the
- * last call's contents: calls whose work overlaps on the GPU (other streams,
- * other threads, other links) race and must be serialised by the caller. */
+ * refused with EGN_E_CAPACITY.  The link's segment and Gauss-Legendre tables
+ * are formed on the device by a kernel from its launch parameters, so no host
+ * buffer is read after the call returns.  The first call on a device looks up
+ * the array's device address (cudaGetSymbolAddress) with that device current;
+ * make that first call before any stream capture.  All calls share the one array
+ * and it keeps the last call's contents: calls whose work overlaps on the GPU
+ * (other streams, other threads, other links) race and must be serialised by the
+ * caller.  Host threads that make their first call on one device at the same
+ * time are serialised inside the library. */
 egn_status egn_nli_eta_static(egn_link* link, const egn_opts* opts, double* eta_dev, double* pnli_dev);
+
+/* Number of device and pinned-host allocations (cudaMalloc, cudaMallocHost) the
+ * library has made in this process so far.  A diagnostic: it lets a caller check
+ * that a sequence of calls (egn_nli_eta_static, for one) allocated nothing,
+ * independently of other processes sharing the GPU. */
+egn_status egn_allocation_count(long long* count);
 
 /* ------------------------------------------------------------------ batches
  * Many links evaluated together (the paper evaluates one link at a time; its

@@ -15,7 +15,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 OUT = os.path.join(PKG, "_build")
 LIB = os.path.join(OUT, "libegn.so")
-HEADER = os.path.join(ROOT, "include", "egn.h")
+INCLUDE = os.path.join(ROOT, "include")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--extended-lambda", "-Xptxas", "-v"]
@@ -33,7 +33,8 @@ def sources():
 
 
 def _deps():
-    return sources() + [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".h", ".cuh"))] + [HEADER]
+    return (sources() + [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".h", ".cuh"))] +
+            [os.path.join(INCLUDE, f) for f in os.listdir(INCLUDE) if f.endswith(".h")])
 
 
 def up_to_date() -> bool:

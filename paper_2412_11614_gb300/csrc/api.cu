@@ -3,12 +3,14 @@
 //   plan (A1) -> integrate (A3-A8) -> assemble (A9)
 // on one CUDA stream.  See include/egn.h for the contract of every entry point.
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <thread>
 #include <vector>
@@ -18,6 +20,7 @@
 namespace egn_host {
 
 thread_local std::string g_last_error;
+std::atomic<long long> g_alloc_count{0};
 
 egn_status fail(egn_status s, const char* fmt, ...) {
   char buf[512];
@@ -53,35 +56,11 @@ using namespace egn_host;
 
 namespace egn {
 
-// Gauss-Legendre nodes and weights on [-1, 1] by Newton's method on P_n, started
-// from Tricomi's asymptotic node estimate; nodes ascending.
+// Gauss-Legendre nodes and weights on [-1, 1] (gl_node), nodes ascending.
 void gauss_legendre(int n, double* x, double* w) {
   for (int k = 1; k <= (n + 1) / 2; ++k) {
-    double th = kPi * (4.0 * k - 1.0) / (4.0 * n + 2.0);
-    double xk = (1.0 - 1.0 / (8.0 * n * n) + 1.0 / (8.0 * n * n * n)) * std::cos(th);
-    double dpn = 1.0;
-    for (int it = 0; it < 50; ++it) {
-      double pm1 = 1.0, pn = xk;  // P_0, P_1
-      for (int j = 1; j < n; ++j) {
-        double pp = ((2.0 * j + 1.0) * xk * pn - j * pm1) / (j + 1.0);
-        pm1 = pn;
-        pn = pp;
-      }
-      dpn = n * (pm1 - xk * pn) / (1.0 - xk * xk);
-      double step = pn / dpn;
-      xk -= step;
-      if (std::fabs(step) <= 1e-16) break;
-    }
-    {
-      double pm1 = 1.0, pn = xk;
-      for (int j = 1; j < n; ++j) {
-        double pp = ((2.0 * j + 1.0) * xk * pn - j * pm1) / (j + 1.0);
-        pm1 = pn;
-        pn = pp;
-      }
-      dpn = n * (pm1 - xk * pn) / (1.0 - xk * xk);
-    }
-    double wk = 2.0 / ((1.0 - xk * xk) * dpn * dpn);
+    double xk, wk;
+    gl_node(n, k, &xk, &wk);
     // xk is the k-th largest node; mirror to the k-th smallest
     x[n - k] = xk;
     w[n - k] = wk;
@@ -232,11 +211,7 @@ egn_status ensure_tables(egn_link* l, const egn_opts* o) {
       float* zf = (float*)(host.data() + off + 2 * align256(K * sizeof(double)));
       float* cf = (float*)(host.data() + off + 2 * align256(K * sizeof(double)) + align256(K * sizeof(float)));
       for (int k = 0; k < K; ++k) {
-        double z = (k + 0.5) / K * s.L;
-        double leff = -std::expm1(-s.alpha * z) / s.alpha;
-        zeta[k] = l->ptot * s.cr * leff;
-        double x = l->btot * zeta[k];
-        ck[k] = (x == 0.0) ? 1.0 : x / (2.0 * std::sinh(0.5 * x));
+        segment_entry(k, K, s.L, s.alpha, l->ptot * s.cr, l->btot, &zeta[k], &ck[k]);
         zf[k] = (float)(zeta[k] * 1.4426950408889634);  // log2(e)
         cf[k] = (float)ck[k];
       }
@@ -547,7 +522,13 @@ extern "C" {
 
 const char* egn_last_error(void) { return g_last_error.c_str(); }
 
-const char* egn_version(void) { return "egn-gb300 0.1 (sm_103a)"; }
+const char* egn_version(void) { return "egn-gb300 0.2 (sm_103a)"; }
+
+egn_status egn_allocation_count(long long* count) {
+  if (!count) return fail(EGN_E_INVALID_ARG, "null output");
+  *count = g_alloc_count.load(std::memory_order_relaxed);
+  return EGN_OK;
+}
 
 egn_status egn_format_moments(int fmt, double* phi, double* psi) {
   if (!phi || !psi) return fail(EGN_E_INVALID_ARG, "null output");
@@ -929,22 +910,85 @@ namespace {
 constexpr size_t kStaticScratchBytes = (size_t)16 << 20;  // 16 MiB
 __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
 
-// Device address of g_static_scratch per device (host code sees a host-side
-// stand-in under that name; only the address from cudaGetSymbolAddress may be
-// handed to kernels).
+// Device address of g_static_scratch per device.  In host code the name
+// g_static_scratch is a host-side stand-in, not a device address: only the
+// address from cudaGetSymbolAddress (taken with that device current) may be
+// handed to kernels.  Threads that make their first call on a device at the
+// same time serialise on the mutex; later calls read the cached address.
 constexpr int kMaxDevices = 64;
-void* g_static_ptr[kMaxDevices] = {};
+std::atomic<void*> g_static_ptr[kMaxDevices];
+std::mutex g_static_mu;
 
 egn_status static_scratch(int dev, void** out) {
   if (dev < 0 || dev >= kMaxDevices) return fail(EGN_E_UNSUPPORTED, "device %d out of range for the static scratch", dev);
-  if (!g_static_ptr[dev]) {
-    void* p = nullptr;
-    cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);  // the device is current here
-    if (e != cudaSuccess) return fail(EGN_E_CUDA, "cudaGetSymbolAddress(static scratch): %s", cudaGetErrorString(e));
-    g_static_ptr[dev] = p;
+  void* p = g_static_ptr[dev].load(std::memory_order_acquire);
+  if (!p) {
+    std::lock_guard<std::mutex> lock(g_static_mu);
+    p = g_static_ptr[dev].load(std::memory_order_relaxed);
+    if (!p) {
+      cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);  // the device is current here
+      if (e != cudaSuccess) return fail(EGN_E_CUDA, "cudaGetSymbolAddress(static scratch): %s", cudaGetErrorString(e));
+      g_static_ptr[dev].store(p, std::memory_order_release);
+    }
   }
-  *out = g_static_ptr[dev];
+  *out = p;
   return EGN_OK;
+}
+
+// Where the link tables of one evaluation sit in the scratch, and the span
+// scalars they are formed from: passed by value, so that the tables are built on
+// the device from kernel parameters and no host buffer is read after the call.
+struct StaticTables {
+  int nt;
+  int K[kMaxTypes];
+  double L[kMaxTypes], alpha[kMaxTypes], pcr[kMaxTypes];
+  double btot;
+  double* zeta[kMaxTypes];
+  double* ck[kMaxTypes];
+  float* zf[kMaxTypes];
+  float* cf[kMaxTypes];
+  int ord[4];
+  double* gx[4];
+  double* gw[4];
+  float* gf[4][5];  // x head, x tail, x^2 head, x^2 tail, w (FP32)
+};
+
+// Segment tables of every span type (segment_entry, as ensure_tables forms them
+// on the host) and the Gauss-Legendre tables of the three outer orders (gl_node,
+// as gauss_legendre forms them), one entry per thread.
+__global__ void static_tables_kernel(StaticTables t) {
+  for (int ty = 0; ty < t.nt; ++ty)
+    for (int k = threadIdx.x; k < t.K[ty]; k += blockDim.x) {
+      double z, c;
+      segment_entry(k, t.K[ty], t.L[ty], t.alpha[ty], t.pcr[ty], t.btot, &z, &c);
+      t.zeta[ty][k] = z;
+      t.ck[ty][k] = c;
+      t.zf[ty][k] = (float)(z * 1.4426950408889634);  // log2(e)
+      t.cf[ty][k] = (float)c;
+    }
+  for (int p = 1; p <= 3; ++p) {
+    const int m = t.ord[p];
+    for (int k = 1 + threadIdx.x; k <= (m + 1) / 2; k += blockDim.x) {
+      double xk, wk;
+      gl_node(m, k, &xk, &wk);
+      const bool mid = (m % 2 == 1) && k == (m + 1) / 2;  // the middle node of an odd order is 0
+      const int idx[2] = {m - k, k - 1};
+      const double xv[2] = {mid ? 0.0 : xk, mid ? 0.0 : -xk};
+      for (int a = 0; a < 2; ++a) {
+        const int i = idx[a];
+        const double x = xv[a];
+        t.gx[p][i] = x;
+        t.gw[p][i] = wk;
+        const float xh = (float)x;
+        t.gf[p][0][i] = xh;
+        t.gf[p][1][i] = (float)(x - (double)xh);
+        const double x2 = x * x;
+        t.gf[p][2][i] = (float)x2;
+        t.gf[p][3][i] = (float)(x2 - (double)(float)x2);
+        t.gf[p][4][i] = (float)wk;
+      }
+    }
+  }
 }
 
 }  // namespace
@@ -958,7 +1002,7 @@ extern "C" egn_status egn_nli_eta_static(egn_link* l, const egn_opts* o, double*
   s = static_scratch(l->device, &base);
   if (s != EGN_OK) return s;
 
-  // link tables for these options, built on the host stack (no heap, no device allocation)
+  // layout of the link tables for these options inside the scratch
   const int nt = l->identical ? 1 : (int)l->type_si.size();
   if (nt > kMaxTypes)
     return fail(EGN_E_UNSUPPORTED, "the static scratch path takes at most %d span types (this link has %d)", kMaxTypes, nt);
@@ -991,45 +1035,24 @@ extern "C" egn_status egn_nli_eta_static(egn_link* l, const egn_opts* o, double*
 
   cudaStream_t st = (cudaStream_t)o->stream;
   char* b = (char*)base;
-  {
-    double zeta[kMaxK], ck[kMaxK];
-    float zf[kMaxK], cf[kMaxK];
-    for (int t = 0; t < nt; ++t) {
-      const Span& st_ = sps[t];
-      const int Kt = Ks[t];
-      for (int k = 0; k < Kt; ++k) {
-        double z = (k + 0.5) / Kt * st_.L;
-        double leff = -std::expm1(-st_.alpha * z) / st_.alpha;
-        zeta[k] = l->ptot * st_.cr * leff;
-        double x = l->btot * zeta[k];
-        ck[k] = (x == 0.0) ? 1.0 : x / (2.0 * std::sinh(0.5 * x));
-        zf[k] = (float)(zeta[k] * 1.4426950408889634);
-        cf[k] = (float)ck[k];
-      }
-      // pageable source: each copy has left the stack buffers before it returns
-      EGN_CUDA(h2d_async(b + o_zeta[t], zeta, Kt * sizeof(double), st));
-      EGN_CUDA(h2d_async(b + o_ck[t], ck, Kt * sizeof(double), st));
-      EGN_CUDA(h2d_async(b + o_zf[t], zf, Kt * sizeof(float), st));
-      EGN_CUDA(h2d_async(b + o_cf[t], cf, Kt * sizeof(float), st));
-    }
-    for (int p = 1; p <= 3; ++p) {
-      const int m = ord[p];
-      double x[kMaxGl], w[kMaxGl];
-      float f[5][kMaxGl];
-      gauss_legendre(m, x, w);
-      for (int i = 0; i < m; ++i) {
-        f[0][i] = (float)x[i];
-        f[1][i] = (float)(x[i] - (double)f[0][i]);
-        double x2 = x[i] * x[i];
-        f[2][i] = (float)x2;
-        f[3][i] = (float)(x2 - (double)f[2][i]);
-        f[4][i] = (float)w[i];
-      }
-      EGN_CUDA(h2d_async(b + o_gl[p][0], x, m * sizeof(double), st));
-      EGN_CUDA(h2d_async(b + o_gl[p][1], w, m * sizeof(double), st));
-      for (int a = 0; a < 5; ++a)
-        EGN_CUDA(h2d_async(b + o_gl[p][2 + a], f[a], m * sizeof(float), st));
-    }
+  StaticTables tab{};
+  tab.nt = nt;
+  tab.btot = l->btot;
+  for (int t = 0; t < nt; ++t) {
+    tab.K[t] = Ks[t];
+    tab.L[t] = sps[t].L;
+    tab.alpha[t] = sps[t].alpha;
+    tab.pcr[t] = l->ptot * sps[t].cr;
+    tab.zeta[t] = (double*)(b + o_zeta[t]);
+    tab.ck[t] = (double*)(b + o_ck[t]);
+    tab.zf[t] = (float*)(b + o_zf[t]);
+    tab.cf[t] = (float*)(b + o_cf[t]);
+  }
+  for (int p = 1; p <= 3; ++p) {
+    tab.ord[p] = ord[p];
+    tab.gx[p] = (double*)(b + o_gl[p][0]);
+    tab.gw[p] = (double*)(b + o_gl[p][1]);
+    for (int a = 0; a < 5; ++a) tab.gf[p][a] = (float*)(b + o_gl[p][2 + a]);
   }
 
   LinkParams p{};
@@ -1046,10 +1069,10 @@ extern "C" egn_status egn_nli_eta_static(egn_link* l, const egn_opts* o, double*
     ty.r = std::exp(-sps[t].alpha * ty.dz);
     ty.pcr = l->ptot * sps[t].cr;
     ty.seg.K = Ks[t];
-    ty.seg.zeta = (const double*)(b + o_zeta[t]);
-    ty.seg.ck = (const double*)(b + o_ck[t]);
-    ty.seg.zeta_f = (const float*)(b + o_zf[t]);
-    ty.seg.ck_f = (const float*)(b + o_cf[t]);
+    ty.seg.zeta = tab.zeta[t];
+    ty.seg.ck = tab.ck[t];
+    ty.seg.zeta_f = tab.zf[t];
+    ty.seg.ck_f = tab.cf[t];
   }
   for (int q = 0; q < (int)l->span_type.size() && q < kMaxSpans; ++q) p.span_type[q] = l->span_type[q];
   p.seg = p.types[0].seg;
@@ -1057,13 +1080,13 @@ extern "C" egn_status egn_nli_eta_static(egn_link* l, const egn_opts* o, double*
   p.gl.order[0] = 0;
   for (int q = 1; q <= 3; ++q) {
     p.gl.order[q] = ord[q];
-    p.gl.x[q] = (const double*)(b + o_gl[q][0]);
-    p.gl.w[q] = (const double*)(b + o_gl[q][1]);
-    p.gl.xh[q] = (const float*)(b + o_gl[q][2]);
-    p.gl.xl[q] = (const float*)(b + o_gl[q][3]);
-    p.gl.x2h[q] = (const float*)(b + o_gl[q][4]);
-    p.gl.x2l[q] = (const float*)(b + o_gl[q][5]);
-    p.gl.wf[q] = (const float*)(b + o_gl[q][6]);
+    p.gl.x[q] = tab.gx[q];
+    p.gl.w[q] = tab.gw[q];
+    p.gl.xh[q] = tab.gf[q][0];
+    p.gl.xl[q] = tab.gf[q][1];
+    p.gl.x2h[q] = tab.gf[q][2];
+    p.gl.x2l[q] = tab.gf[q][3];
+    p.gl.wf[q] = tab.gf[q][4];
   }
   p.n_spans = (int)l->spans_si.size();
   p.alpha = sp.alpha;
@@ -1079,10 +1102,12 @@ extern "C" egn_status egn_nli_eta_static(egn_link* l, const egn_opts* o, double*
   p.fp32c_kp = l->fp32c_kp;
   set_mu_params(p, l, o);
 
-  // plan -> integrate -> assemble on the caller's stream, workspace in the scratch
+  // tables -> plan -> integrate -> assemble on the caller's stream, all in the scratch
   Workspace ws = carve_workspace(b + ws_off, l->n_ch, l->cnt, o->precision);
   ChannelTable ch = p.ch;
   EGN_LAUNCH_GATE();
+  static_tables_kernel<<<1, 128, 0, st>>>(tab);
+  EGN_CUDA(cudaGetLastError());
   EGN_CUDA(cudaMemsetAsync(ws.status, 0, sizeof(int), st));  // the array keeps the last call's contents
   EGN_CUDA(launch_plan(ch, ws, st));
   EGN_CUDA(integrate(p, o->precision, ws.keys, l->cnt.n_isl, ws.d_idx, l->cnt.n_half, ws.e_idx, l->cnt.n_e, ws.f_idx,

@@ -2,6 +2,7 @@
 // kernels of the GB300 ISRS EGN integrator (not part of the C ABI).
 #pragma once
 
+#include <cmath>
 #include <cstddef>
 #include <cstdint>
 #include <cuda_runtime.h>
@@ -205,7 +206,54 @@ cudaError_t launch_assemble(const ChannelTable& ch, const uint32_t* half_off, co
                             const uint32_t* h_idx, long long n_isl, const void* terms, int precision, int terms_mode,
                             double* eta, double* pnli, cudaStream_t st);
 
+// The k-th largest Gauss-Legendre node of order n on [-1, 1] (k = 1 ..
+// ceil(n/2)) and its weight, by Newton's method on P_n from Tricomi's asymptotic
+// estimate.  Host and device (the allocation-free entry point builds its tables
+// on the device) evaluate the same arithmetic.
+__host__ __device__ inline void gl_node(int n, int k, double* xk_out, double* wk_out) {
+  const double th = kPi * (4.0 * k - 1.0) / (4.0 * n + 2.0);
+  double xk = (1.0 - 1.0 / (8.0 * n * n) + 1.0 / (8.0 * n * n * n)) * cos(th);
+  double dpn = 1.0;
+  for (int it = 0; it < 50; ++it) {
+    double pm1 = 1.0, pn = xk;  // P_0, P_1
+    for (int j = 1; j < n; ++j) {
+      const double pp = ((2.0 * j + 1.0) * xk * pn - j * pm1) / (j + 1.0);
+      pm1 = pn;
+      pn = pp;
+    }
+    dpn = n * (pm1 - xk * pn) / (1.0 - xk * xk);
+    const double step = pn / dpn;
+    xk -= step;
+    if (fabs(step) <= 1e-16) break;
+  }
+  {
+    double pm1 = 1.0, pn = xk;
+    for (int j = 1; j < n; ++j) {
+      const double pp = ((2.0 * j + 1.0) * xk * pn - j * pm1) / (j + 1.0);
+      pm1 = pn;
+      pn = pp;
+    }
+    dpn = n * (pm1 - xk * pn) / (1.0 - xk * xk);
+  }
+  *xk_out = xk;
+  *wk_out = 2.0 / ((1.0 - xk * xk) * dpn * dpn);
+}
+
 // Host Gauss-Legendre nodes on [-1, 1], ascending.
 void gauss_legendre(int n, double* x, double* w);
+
+// Entry k of a span type's segment tables (Eq. 8-10 with the ISRS profile of
+// Eq. 14/25): z_k = (k + 1/2) L / K, zeta_k = P_tot Cr L_eff(z_k) with
+// L_eff(z) = (1 - e^{-alpha z}) / alpha, and C_k = B_tot zeta_k / (2 sinh(B_tot
+// zeta_k / 2)), whose limit at Cr = 0 is 1.  pcr = P_tot Cr.  Host and device
+// evaluate the same arithmetic.
+__host__ __device__ inline void segment_entry(int k, int K, double L, double alpha, double pcr, double btot,
+                                              double* zeta, double* ck) {
+  const double z = (k + 0.5) / K * L;
+  const double leff = -expm1(-alpha * z) / alpha;
+  *zeta = pcr * leff;
+  const double x = btot * *zeta;
+  *ck = (x == 0.0) ? 1.0 : x / (2.0 * sinh(0.5 * x));
+}
 
 }  // namespace egn

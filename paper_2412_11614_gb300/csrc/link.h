@@ -2,6 +2,7 @@
 // the single-link entry points (api.cu) and the batch of links (batch.cu).
 #pragma once
 
+#include <atomic>
 #include <cmath>
 #include <cstdint>
 #include <string>
@@ -40,8 +41,13 @@ inline cudaError_t h2d_async(void* dst, const void* src, size_t n, cudaStream_t 
   if (cudaError_t f = inject(kFaultH2D, cudaErrorInvalidValue)) return f;
   return cudaMemcpyAsync(dst, src, n, cudaMemcpyHostToDevice, st);
 }
+// Device and pinned-host allocations the library has asked the runtime for in
+// this process (egn_allocation_count).
+extern std::atomic<long long> g_alloc_count;
+
 inline cudaError_t pinned_alloc(void** p, size_t n) {
   if (cudaError_t f = inject(kFaultAlloc, cudaErrorMemoryAllocation)) return f;
+  g_alloc_count.fetch_add(1, std::memory_order_relaxed);
   return cudaMallocHost(p, n);
 }
 
@@ -64,6 +70,7 @@ struct DevBuf {
     if (p) cudaFree(p);
     p = nullptr;
     bytes = 0;
+    g_alloc_count.fetch_add(1, std::memory_order_relaxed);
     cudaError_t e = cudaMalloc(&p, want);
     if (e == cudaSuccess) bytes = want;
     return e;

@@ -94,13 +94,17 @@ def lib():
                                         C.POINTER(_dp)]
         L.egn_autotune.argtypes = [C.c_void_p, C.POINTER(egn_opts), C.c_double, _dp, C.c_int, C.c_double,
                                    C.POINTER(egn_tune_result)]
+        L.egn_probe_launch.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_void_p]
+        L.egn_probe_ops.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, _dp]
+        L.egn_allocation_count.argtypes = [C.POINTER(C.c_longlong)]
         L.egn_last_error.restype = C.c_char_p
         L.egn_version.restype = C.c_char_p
         for fn in ("egn_link_create", "egn_set_wdm", "egn_workspace_size", "egn_island_count", "egn_nli_eta",
                    "egn_nli_eta_device", "egn_island_terms", "egn_plan_islands", "egn_format_moments",
                    "egn_gauss_legendre", "egn_set_profiling", "egn_last_timings", "egn_nli_eta_static", "egn_set_tuning",
                    "egn_batch_create", "egn_batch_launch", "egn_batch_outputs", "egn_batch_read", "egn_nli_eta_batch",
-                   "egn_autotune", "egn_nli_eta_3d"):
+                   "egn_autotune", "egn_nli_eta_3d", "egn_probe_launch", "egn_probe_ops",
+                   "egn_allocation_count"):
             getattr(L, fn).restype = C.c_int
         _lib = L
     return _lib
@@ -119,6 +123,13 @@ def egn_version() -> str:
     return lib().egn_version().decode()
 
 
+def allocation_count() -> int:
+    """Device and pinned-host allocations the library has made in this process."""
+    n = C.c_longlong()
+    _check(lib().egn_allocation_count(C.byref(n)))
+    return n.value
+
+
 def egn_format_moments(fmt) -> tuple:
     code = EGN_FMT[fmt] if isinstance(fmt, str) else int(fmt)
     phi, psi = C.c_double(), C.c_double()
@@ -131,6 +142,26 @@ def egn_gauss_legendre(n: int):
     w = np.zeros(n)
     _check(lib().egn_gauss_legendre(n, x.ctypes.data_as(_dp), w.ctypes.data_as(_dp)))
     return x, w
+
+
+EGN_PROBE = {"ffma": 0, "ffma2": 1, "dfma": 2, "mufu_sin": 3, "mufu_ex2": 4, "mufu_rcp": 5}
+
+
+def probe_ops(kind: str, blocks: int, threads: int, iters: int) -> float:
+    """Operations of one probe launch (egn_probe_ops): FLOP for the FMA probes,
+    special-function operations for the MUFU probes."""
+    ops = C.c_double()
+    _check(lib().egn_probe_ops(EGN_PROBE[kind], int(blocks), int(threads), int(iters), C.byref(ops)))
+    return ops.value
+
+
+def probe_launch(kind: str, blocks: int, threads: int, iters: int, sink, stream: Optional[int] = None):
+    """One throughput-probe launch (egn_probe_launch) into a device tensor `sink`
+    of at least blocks * threads * 8 bytes, on `stream`."""
+    if sink.numel() * sink.element_size() < blocks * threads * 8:
+        raise ValueError("probe sink too small")
+    _check(lib().egn_probe_launch(EGN_PROBE[kind], int(blocks), int(threads), int(iters),
+                                  C.c_void_p(sink.data_ptr()), C.c_void_p(stream) if stream else None))
 
 
 def make_opts(gl_order=32, dz_km=1.0, precision=EGN_PREC_FP32C, terms=EGN_TERMS_EGN, timeout_ms=0,

@@ -144,3 +144,14 @@ def test_new_entry_points_validate_before_launching(egn):
     cand = (C.c_double * 1)(1.0)
     assert lib.egn_autotune(None, C.byref(opts), 0.01, cand, 1, 0.5, C.byref(res)) == egn.EGN_E_INVALID_ARG
     assert "null" in lib.egn_last_error().decode()
+    # pipe probes: kind, launch shape and the sink are checked before any launch
+    ops = C.c_double()
+    assert lib.egn_probe_ops(0, 4, 256, 10, C.byref(ops)) == egn.EGN_OK and ops.value == 2 * 4 * 256 * 8 * 10
+    assert lib.egn_probe_ops(1, 4, 256, 10, C.byref(ops)) == egn.EGN_OK and ops.value == 4 * 4 * 256 * 8 * 10
+    assert lib.egn_probe_ops(3, 4, 256, 10, C.byref(ops)) == egn.EGN_OK and ops.value == 4 * 256 * 8 * 10
+    assert lib.egn_probe_ops(9, 4, 256, 10, C.byref(ops)) == egn.EGN_E_INVALID_ARG
+    assert lib.egn_probe_launch(0, 4, 48, 10, fake, None) == egn.EGN_E_INVALID_ARG
+    assert lib.egn_probe_launch(0, 4, 256, 10, None, None) == egn.EGN_E_INVALID_ARG
+    # the allocation counter: a count, and refuses a null output
+    assert egn.allocation_count() >= 0
+    assert lib.egn_allocation_count(None) == egn.EGN_E_INVALID_ARG

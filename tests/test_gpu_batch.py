@@ -1,6 +1,8 @@
 """Batches of links (egn_batch_* / egn_nli_eta_batch): the same kernels as the
 single-link path, so every channel must equal the single-link result bit for
-bit; the batch is a snapshot of its links; graph replays are repeatable."""
+bit; the batch is a snapshot of its links; graph replays are repeatable; and
+seeded heterogeneous links evaluated inside a batch agree with the FP64 CPU
+oracle (FP64 within 1e-9 relative, FP32C within 1e-3 dB)."""
 import numpy as np
 import pytest
 
@@ -113,3 +115,38 @@ def test_batch_errors(egn, workloads):
     with pytest.raises(egn.EgnError) as ei:
         egn.nli_eta_batch([ok], egn.make_opts(gl_order=16, precision=egn.EGN_PREC_FP32C, mu_form=egn.EGN_MU_INTEGRAL))
     assert ei.value.status == egn.EGN_E_UNSUPPORTED
+
+
+def _cut(wl, n_ch, gl):
+    """The first n_ch channels of a workload at a gl x gl rule."""
+    import copy
+    w = copy.deepcopy(wl)
+    w.centre_hz, w.symbol_rate_baud = w.centre_hz[:n_ch], w.symbol_rate_baud[:n_ch]
+    w.launch_power_w, w.formats = w.launch_power_w[:n_ch], w.formats[:n_ch]
+    w.gl_order = gl
+    return w
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32c"])
+def test_batch_of_random_links_against_oracle(egn, oracle_mod, workloads, prec):
+    """Seeded random links (tilted rippled powers, mixed formats) in one batch: 29
+    SSMF/PSCF spans of 26 types (span-by-span path), 2 and 3 span types (shared
+    c_k tables) and one span (phased-array closed form), cut to 8-12 channels at
+    8 x 8 nodes; three channels of each against the oracle."""
+    gl = 8
+    wls = [_cut(workloads.random_link(2), 10, gl), _cut(workloads.random_link(4), 8, gl),
+           _cut(workloads.random_link(19), 12, gl), _cut(workloads.random_link(3), 9, gl)]
+    p = egn.EGN_PREC_FP32C if prec == "fp32c" else egn.EGN_PREC_FP64
+    opts = egn.make_opts(gl_order=gl, precision=p)
+    links = [egn.link_from_workload(w) for w in wls]
+    b = egn.Batch(links, opts)
+    b.launch()
+    got = b.read()
+    for w, (eta, _) in zip(wls, got):
+        cois = [0, w.n_ch // 2, w.n_ch - 1]
+        want, _ = oracle_mod.Problem(w, gl_order=gl).eta(cois)
+        if prec == "fp64":
+            assert np.allclose(eta[cois], want, rtol=1e-9, atol=0), (w.name, eta[cois], want)
+        else:
+            assert np.max(np.abs(10 * np.log10(eta[cois] / want))) < 1e-3, (w.name, eta[cois], want)
+    b.close()

@@ -428,6 +428,27 @@ def test_config_cl_full_size_sampled_channels(egn, oracle_mod, workloads):
     assert np.max(_db(e32[cois], want)) < TARGET_DB
 
 
+@pytest.mark.parametrize("p_dbm", [-2.0, 4.0])
+def test_config3_power_sweep(egn, oracle_mod, workloads, p_dbm):
+    """The benchmark link at the ends of the launch-power sweep, -2 and +4 dBm/ch
+    (the strongest ISRS: P_tot 24.8 dBm, about 6.9 dB of power transfer across the
+    band per span by Eq. 12), where the FP32C design (double-float phase, FP32
+    phased-array series near its poles) is most exposed.  FP32C against the plain
+    FP64 path on every channel within the 0.01 dB accuracy target; FP64 against the
+    oracle on the edge and a centre channel within 1e-8 relative."""
+    wl = workloads.config_cl(p_dbm=p_dbm)
+    ln, pb = _pair(egn, oracle_mod, wl)
+    e64, _ = ln.nli_eta(egn.make_opts(gl_order=32, precision=egn.EGN_PREC_FP64))
+    e32, _ = ln.nli_eta(egn.make_opts(gl_order=32, precision=egn.EGN_PREC_FP32C))
+    assert np.all(np.isfinite(e32)) and np.all(e32 > 0)
+    assert np.max(_db(e32, e64)) < TARGET_DB, (p_dbm, int(np.argmax(_db(e32, e64))), np.max(_db(e32, e64)))
+    cois = [0, 59]
+    want, _ = pb.eta(cois)
+    assert np.allclose(e64[cois], want, rtol=1e-8, atol=0)
+    assert np.max(_db(e32[cois], want)) < TARGET_DB
+    ln.close()
+
+
 def test_fp32c_launch_shapes_agree(egn, oracle_mod, workloads):
     """4 and 8 points per thread in the FP32C D/G/H pass: same terms up to rounding."""
     wl = workloads.config_small(n_ch=5, gl_order=32, n_spans=3)

@@ -100,14 +100,20 @@ def test_narrow_ridge_island(RR, oracle_mod, workloads):
     assert abs(pb.island_terms(0, 0, 4, 4)[0] / want - 1) > 0.3
 
 
-def test_study_script_runs(capsys):
-    from oracle import ridge_study
-    ridge_study.main(["small", "0,2", "--plain", "8", "--ridge", "4,8"])
-    lines = capsys.readouterr().out.strip().splitlines()
-    assert len(lines) == 6 and all(" dB " in ln for ln in lines)
-    assert "+0.0000 dB" in lines[1] and "+0.0000 dB" in lines[4]  # the last ridge order is the reference
-    ridge_study.main(["small", "1", "--plain", "4", "--ridge", "4", "--egn", "--f3d", "2"])
-    assert len(capsys.readouterr().out.strip().splitlines()) == 2
+def test_gn_sum_converges_where_the_plain_rule_swings(RR, oracle_mod, workloads):
+    """The finding on the 5-channel link, as a pin: the GN part of Eq. 15 for the
+    edge and centre COIs settles within 0.02 dB between 8 and 16 nodes per piece
+    of the ridge rule, while the configured rule moves by more than 0.1 dB between
+    16 x 16 and 32 x 32 nodes (the ridges are not resolved)."""
+    wl = workloads.config_small()
+    pb = oracle_mod.Problem(wl, gl_order=8, terms=0)
+    rule = RR.RidgeRule(pb)
+    for n in (0, 2):
+        r8, r16 = rule.pnli_gn(n, 8), rule.pnli_gn(n, 16)
+        p16 = oracle_mod.Problem(wl, gl_order=16, terms=0).island_contribs(n)[1].sum()
+        p32 = oracle_mod.Problem(wl, gl_order=32, terms=0).island_contribs(n)[1].sum()
+        assert abs(10 * np.log10(r8 / r16)) < 0.02, (n, r8, r16)
+        assert abs(10 * np.log10(p16 / p32)) > 0.1, (n, p16, p32)
 
 
 def test_all_terms_dispersionless_exact(RR, oracle_mod, workloads):
