@@ -736,7 +736,7 @@ def main():
     ap.add_argument("--mu-gl", type=int, default=16)
     ap.add_argument("--batch", action="store_true",
                     help="time a batch of small links: one by one vs one graph launch")
-    ap.add_argument("--batch-links", type=int, default=24)
+    ap.add_argument("--batch-links", "--links", type=int, default=24, dest="batch_links")
     ap.add_argument("--batch-random", action="store_true", help="the batch is seeded heterogeneous random links")
     ap.add_argument("--dz-sweep", action="store_true", help="segment length trade-off on Table I and II links")
     ap.add_argument("--gemm", type=int, default=0, metavar="G", help="time the surrogate's G^3 tensor-core GEMM")

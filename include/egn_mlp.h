@@ -29,7 +29,12 @@ enum {
     EGN_MLP_EPI_BIAS_RELU = 0, /* out BF16 [m][n] = max(acc + bias[n], 0) */
     EGN_MLP_EPI_BIAS = 1,      /* out BF16 [m][n] = acc + bias[n] */
     EGN_MLP_EPI_F32 = 2,       /* out FP32 [splits][m][n] = partial acc of each k split */
-    EGN_MLP_EPI_RELU_GRAD = 3  /* out BF16 [m][n] = acc where aux BF16 [m][n] > 0, else 0 */
+    EGN_MLP_EPI_RELU_GRAD = 3, /* out BF16 [m][n] = acc where aux BF16 [m][n] > 0, else 0 */
+    EGN_MLP_EPI_BIAS_GELU = 4, /* aux BF16 [m][n] = z = acc + bias[n] (written: the pre-activation,
+                                  kept for the backward pass); out BF16 [m][n] = GELU(z) = z Phi(z),
+                                  Phi the standard normal distribution function, of z as stored */
+    EGN_MLP_EPI_GELU_GRAD = 5  /* out BF16 [m][n] = acc * GELU'(aux), aux BF16 [m][n] the stored
+                                  pre-activation; GELU'(z) = Phi(z) + z phi(z) */
 };
 
 /* D = A B^T: A BF16 [m][k], B BF16 [n][k], both with k contiguous; k a
@@ -58,6 +63,16 @@ egn_status egn_mlp_colsum(const void* in, int rows, int cols, float* out, void* 
 egn_status egn_mlp_head(const void* h, int rows, int hid, const float* w, const float* b, float* y,
                         const float* target, const float* mask, float* loss, float* g, void* dh, float* dw,
                         float* db, void* stream);
+
+/* Multi-output layer and loss, for a network whose last GEMM wrote acc FP32
+ * [rows][n_pad] (EGN_MLP_EPI_F32) with n_out <= n_pad live columns:
+ * y FP32 [rows][n_out] = acc[r][j] + b[j].  With target != NULL (FP32
+ * [rows][n_out]) and mask (FP32 [rows]) also: loss[0] = sum_r mask[r] sum_j
+ * (y[r][j] - target[r][j])^2 / (n_out sum_r mask[r]); g BF16 [rows_pad][n_pad] =
+ * dloss/dy, zero in the padding rows (r >= rows) and columns (j >= n_out);
+ * db FP32 [n_out] = sum over r of dloss/dy[r][j] (fixed-order sums). */
+egn_status egn_mlp_outputs(const float* acc, int rows, int rows_pad, int n_out, int n_pad, const float* b, float* y,
+                           const float* target, const float* mask, float* loss, void* g, float* db, void* stream);
 
 /* Adam step on FP32 master weights w[n] with gradient g, moments m and v
  * (bias-corrected for step t >= 1); then w_bf16 [n] = w and, if wt_bf16 is

@@ -129,9 +129,16 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* b) {
 }
 
 // Epilogue of one accumulator row chunk: 32 columns n .. n + 31 of row `row`.
+// GELU(z) = z Phi(z) with Phi the standard normal distribution function, and
+// its derivative Phi(z) + z phi(z).
+__device__ __forceinline__ float gelu_f(float z) { return 0.5f * z * (1.0f + erff(z * 0.70710678118654752f)); }
+__device__ __forceinline__ float gelu_grad_f(float z) {
+  return 0.5f * (1.0f + erff(z * 0.70710678118654752f)) + z * (0.39894228040143268f * __expf(-0.5f * z * z));
+}
+
 template <int EPI>
 __device__ __forceinline__ void store_chunk(const float (&v)[32], int row, int n, int M, int N, int z,
-                                            const float* __restrict__ bias, const __nv_bfloat16* __restrict__ aux,
+                                            const float* __restrict__ bias, __nv_bfloat16* aux,
                                             void* __restrict__ out) {
   if (EPI == EGN_MLP_EPI_F32) {
     float* o = (float*)out + (size_t)z * (size_t)M * N + (size_t)row * N + n;
@@ -146,6 +153,21 @@ __device__ __forceinline__ void store_chunk(const float (&v)[32], int row, int n
     } else if (EPI == EGN_MLP_EPI_BIAS) {
 #pragma unroll
       for (int j = 0; j < 32; ++j) h[j] = __float2bfloat16_rn(v[j] + bias[n + j]);
+    } else if (EPI == EGN_MLP_EPI_BIAS_GELU) {  // GELU of the pre-activation, which goes to aux
+      __align__(16) __nv_bfloat16 za[32];
+#pragma unroll
+      for (int j = 0; j < 32; ++j) {
+        const __nv_bfloat16 zb = __float2bfloat16_rn(v[j] + bias[n + j]);
+        za[j] = zb;
+        h[j] = __float2bfloat16_rn(gelu_f(__bfloat162float(zb)));
+      }
+      __nv_bfloat16* zo = aux + (size_t)row * N + n;
+#pragma unroll
+      for (int j = 0; j < 32; j += 8) *reinterpret_cast<uint4*>(zo + j) = *reinterpret_cast<const uint4*>(za + j);
+    } else if (EPI == EGN_MLP_EPI_GELU_GRAD) {  // times GELU' of the stored pre-activation
+      const __nv_bfloat16* a = aux + (size_t)row * N + n;
+#pragma unroll
+      for (int j = 0; j < 32; ++j) h[j] = __float2bfloat16_rn(v[j] * gelu_grad_f(__bfloat162float(a[j])));
     } else {  // EGN_MLP_EPI_RELU_GRAD: the gradient passes where the layer's output was positive
       const __nv_bfloat16* a = aux + (size_t)row * N + n;
 #pragma unroll
@@ -162,7 +184,7 @@ template <int EPI>
 __global__ void __launch_bounds__(kGemmThreads, 1)
     gemm_bf16_kernel(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtensorMap tb, int M, int N,
                      int kb_per_split, int kb_total, int splits, const float* __restrict__ bias,
-                     const __nv_bfloat16* __restrict__ aux, void* __restrict__ out, int* __restrict__ err) {
+                     __nv_bfloat16* aux, void* __restrict__ out, int* __restrict__ err) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint8_t* sA = smem;
@@ -341,7 +363,7 @@ egn_status launch(const CUtensorMap& ta, const CUtensorMap& tb, int m, int n, in
   const long long tiles = (long long)((m + BM - 1) / BM) * ((n + BN - 1) / BN) * splits;
   const unsigned grid = (unsigned)(tiles < sms ? tiles : sms);  // persistent: one CTA per SM
   gemm_bf16_kernel<EPI><<<grid, kGemmThreads, kSmem, st>>>(ta, tb, m, n, kb_per, kb, splits, bias,
-                                                            (const __nv_bfloat16*)aux, out, err);
+                                                            (__nv_bfloat16*)const_cast<void*>(aux), out, err);
   EGN_CUDA(cudaGetLastError());
   return EGN_OK;
 }
@@ -358,9 +380,11 @@ extern "C" egn_status egn_mlp_gemm(int m, int n, int k, int splits, const void* 
   const int kb = k / BK;
   if (splits < 1 || splits > kb) return fail(EGN_E_INVALID_ARG, "splits must be in [1, k/64]");
   if (splits > 1 && epilogue != EGN_MLP_EPI_F32) return fail(EGN_E_INVALID_ARG, "split k needs the FP32 epilogue");
-  if ((epilogue == EGN_MLP_EPI_BIAS_RELU || epilogue == EGN_MLP_EPI_BIAS) && !bias)
+  if ((epilogue == EGN_MLP_EPI_BIAS_RELU || epilogue == EGN_MLP_EPI_BIAS || epilogue == EGN_MLP_EPI_BIAS_GELU) && !bias)
     return fail(EGN_E_INVALID_ARG, "bias required");
-  if (epilogue == EGN_MLP_EPI_RELU_GRAD && !aux) return fail(EGN_E_INVALID_ARG, "aux required");
+  if ((epilogue == EGN_MLP_EPI_RELU_GRAD || epilogue == EGN_MLP_EPI_BIAS_GELU || epilogue == EGN_MLP_EPI_GELU_GRAD) &&
+      (!aux || ((uintptr_t)aux & 15)))
+    return fail(EGN_E_INVALID_ARG, "aux required (16-byte aligned)");
   const int kb_per = (kb + splits - 1) / splits;
   if ((long long)(splits - 1) * kb_per >= kb) return fail(EGN_E_INVALID_ARG, "splits leaves an empty k range");
   CUtensorMap ta, tb;
@@ -373,6 +397,8 @@ extern "C" egn_status egn_mlp_gemm(int m, int n, int k, int splits, const void* 
     case EGN_MLP_EPI_BIAS: return launch<EGN_MLP_EPI_BIAS>(ta, tb, m, n, kb_per, kb, splits, bias, aux, out, err_dev, st);
     case EGN_MLP_EPI_F32: return launch<EGN_MLP_EPI_F32>(ta, tb, m, n, kb_per, kb, splits, bias, aux, out, err_dev, st);
     case EGN_MLP_EPI_RELU_GRAD: return launch<EGN_MLP_EPI_RELU_GRAD>(ta, tb, m, n, kb_per, kb, splits, bias, aux, out, err_dev, st);
+    case EGN_MLP_EPI_BIAS_GELU: return launch<EGN_MLP_EPI_BIAS_GELU>(ta, tb, m, n, kb_per, kb, splits, bias, aux, out, err_dev, st);
+    case EGN_MLP_EPI_GELU_GRAD: return launch<EGN_MLP_EPI_GELU_GRAD>(ta, tb, m, n, kb_per, kb, splits, bias, aux, out, err_dev, st);
     default: return fail(EGN_E_INVALID_ARG, "unknown epilogue %d", epilogue);
   }
 }

@@ -117,6 +117,66 @@ __global__ void head_wgrad_kernel(const __nv_bfloat16* __restrict__ h, int rows,
   }
 }
 
+// Multi-output layer: y[r][j] = acc[r][j] + b[j] for the n_out live columns.
+__global__ void outputs_fwd_kernel(const float* __restrict__ acc, int rows, int n_out, int n_pad,
+                                   const float* __restrict__ b, float* __restrict__ y) {
+  const long long n = (long long)rows * n_out;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const int r = (int)(i / n_out), j = (int)(i - (long long)r * n_out);
+    y[i] = acc[(size_t)r * n_pad + j] + b[j];
+  }
+}
+
+// Loss, dL/dy (BF16, zero-padded to [rows_pad][n_pad]) and the bias gradient in
+// one CTA of 1024 threads, every sum in a fixed order:
+// L = sum_r mask[r] sum_j (y - t)^2 / (n_out sum_r mask[r]), dL/dy = 2 mask[r] (y - t) / (n_out sum mask).
+__global__ void __launch_bounds__(1024) outputs_loss_kernel(const float* __restrict__ y, const float* __restrict__ t,
+                                                            const float* __restrict__ mask, int rows, int rows_pad,
+                                                            int n_out, int n_pad, float* __restrict__ loss,
+                                                            __nv_bfloat16* __restrict__ g, float* __restrict__ db) {
+  __shared__ float s1[1024], s2[1024];
+  const int tid = threadIdx.x;
+  float a = 0.0f, m = 0.0f;
+  const long long n = (long long)rows * n_out;
+  for (long long i = tid; i < n; i += 1024) {
+    const int r = (int)(i / n_out);
+    const float d = y[i] - t[i];
+    a = fmaf(mask[r] * d, d, a);
+  }
+  for (int r = tid; r < rows; r += 1024) m += mask[r];
+  s1[tid] = a;
+  s2[tid] = m;
+  __syncthreads();
+  for (int o = 512; o > 0; o >>= 1) {
+    if (tid < o) {
+      s1[tid] += s1[tid + o];
+      s2[tid] += s2[tid + o];
+    }
+    __syncthreads();
+  }
+  const float msum = s2[0] > 0.0f ? s2[0] : 1.0f;
+  const float scale = 2.0f / ((float)n_out * msum);
+  if (tid == 0) loss[0] = s1[0] / ((float)n_out * msum);
+  const long long np = (long long)rows_pad * n_pad;
+  for (long long i = tid; i < np; i += 1024) {
+    const int r = (int)(i / n_pad), j = (int)(i - (long long)r * n_pad);
+    float v = 0.0f;
+    if (r < rows && j < n_out) {
+      const size_t k = (size_t)r * n_out + j;
+      v = scale * mask[r] * (y[k] - t[k]);
+    }
+    g[i] = __float2bfloat16_rn(v);
+  }
+  for (int j = tid; j < n_out; j += 1024) {  // column j over the rows in order
+    float c = 0.0f;
+    for (int r = 0; r < rows; ++r) {
+      const size_t k = (size_t)r * n_out + j;
+      c = fmaf(scale * mask[r], y[k] - t[k], c);
+    }
+    db[j] = c;
+  }
+}
+
 __global__ void adam_kernel(float* __restrict__ w, const float* __restrict__ g, float* __restrict__ m,
                             float* __restrict__ v, long long n, float lr, float b1, float b2, float eps, float c1,
                             float c2, __nv_bfloat16* __restrict__ wb, __nv_bfloat16* __restrict__ wt, int rows,
@@ -192,6 +252,20 @@ egn_status egn_mlp_head(const void* h, int rows, int hid, const float* w, const 
   head_bwd_kernel<<<grid_for((long long)rows * hid, 256), 256, 0, st>>>(hb, rows, hid, w, g, (__nv_bfloat16*)dh);
   EGN_CUDA(cudaGetLastError());
   head_wgrad_kernel<<<hid / 32 + 1, dim3(32, 8), 0, st>>>(hb, rows, hid, g, dw, db);
+  EGN_CUDA(cudaGetLastError());
+  return EGN_OK;
+}
+
+egn_status egn_mlp_outputs(const float* acc, int rows, int rows_pad, int n_out, int n_pad, const float* b, float* y,
+                           const float* target, const float* mask, float* loss, void* g, float* db, void* stream) {
+  if (!acc || !b || !y || rows < 1 || n_out < 1 || n_pad < n_out || rows_pad < rows)
+    return fail(EGN_E_INVALID_ARG, "bad arguments");
+  if (target && (!mask || !loss || !g || !db)) return fail(EGN_E_INVALID_ARG, "training needs every output");
+  cudaStream_t st = (cudaStream_t)stream;
+  outputs_fwd_kernel<<<grid_for((long long)rows * n_out, 256), 256, 0, st>>>(acc, rows, n_out, n_pad, b, y);
+  EGN_CUDA(cudaGetLastError());
+  if (!target) return EGN_OK;
+  outputs_loss_kernel<<<1, 1024, 0, st>>>(y, target, mask, rows, rows_pad, n_out, n_pad, loss, (__nv_bfloat16*)g, db);
   EGN_CUDA(cudaGetLastError());
   return EGN_OK;
 }

@@ -8,7 +8,7 @@ from typing import Optional
 
 from . import egn as E
 
-EPI_BIAS_RELU, EPI_BIAS, EPI_F32, EPI_RELU_GRAD = 0, 1, 2, 3
+EPI_BIAS_RELU, EPI_BIAS, EPI_F32, EPI_RELU_GRAD, EPI_BIAS_GELU, EPI_GELU_GRAD = 0, 1, 2, 3, 4, 5
 
 _bound = False
 
@@ -25,8 +25,9 @@ def _lib():
         L.egn_mlp_head.argtypes = [vp, i, i, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]
         L.egn_mlp_adam.argtypes = [vp, vp, vp, vp, ll, f, f, f, f, i, vp, vp, i, i, vp]
         L.egn_mlp_cast.argtypes = [vp, ll, vp, vp]
+        L.egn_mlp_outputs.argtypes = [vp, i, i, i, i, vp, vp, vp, vp, vp, vp, vp, vp]
         for fn in ("egn_mlp_gemm", "egn_mlp_reduce_splits", "egn_mlp_transpose", "egn_mlp_colsum", "egn_mlp_head",
-                   "egn_mlp_adam", "egn_mlp_cast"):
+                   "egn_mlp_adam", "egn_mlp_cast", "egn_mlp_outputs"):
             getattr(L, fn).restype = C.c_int
         _bound = True
     return L
@@ -76,3 +77,11 @@ def adam(w, g, m, v, lr, t, w_bf16=None, wt_bf16=None, beta1=0.9, beta2=0.999, e
 
 def cast(x, out, stream=None):
     E._check(_lib().egn_mlp_cast(_p(x), x.numel(), _p(out), _s(stream)))
+
+
+def outputs(acc, rows, rows_pad, n_out, b, y, target=None, mask=None, loss=None, g=None, db=None, stream=None):
+    """Multi-output layer (and loss): y [rows][n_out] = acc [rows][n_pad] + b; with a target
+    also the loss, g = dloss/dy (BF16 [rows_pad][n_pad]) and db."""
+    n_pad = acc.shape[-1]
+    E._check(_lib().egn_mlp_outputs(_p(acc), rows, rows_pad, n_out, n_pad, _p(b), _p(y), _p(target), _p(mask),
+                                    _p(loss), _p(g), _p(db), _s(stream)))

@@ -81,9 +81,11 @@ def features(wl) -> np.ndarray:
     return np.stack(cols, axis=1).astype(np.float64)
 
 
-def in_envelope(wl) -> bool:
-    """True if the link is of the kind the surrogate was trained on."""
-    if len(wl.centre_hz) != 120 or any(r != 64e9 for r in wl.symbol_rate_baud):
+def in_envelope(wl, n_ch: int = 120) -> bool:
+    """True if the link is of the kind the surrogates were trained on: the n_ch
+    channel 64 GBd grid of the seeded training links, identical SSMF spans, N_s,
+    L, Cr and powers inside the sampled ranges."""
+    if len(wl.centre_hz) != n_ch or any(r != 64e9 for r in wl.symbol_rate_baud):
         return False
     s0 = wl.spans[0]
     if any(s != s0 for s in wl.spans):
@@ -253,6 +255,208 @@ class Surrogate:
         self._refresh_bf16(None)
 
 
+# --------------------------------------------------------------------------- per-link network
+
+LINK_HIDDEN = 512
+LINK_LAYERS = 3
+
+
+def _pad64(n: int) -> int:
+    return -(-n // 64) * 64
+
+
+def link_features(wl) -> np.ndarray:
+    """One input row per link: the n_ch launch powers [dBm], the span count, the
+    span length [km] and Cr [1/(W km THz)] (n_ch + 3 values)."""
+    s = wl.spans[0]
+    p_dbm = 10.0 * np.log10(np.asarray(wl.launch_power_w) / 1e-3)
+    return np.concatenate([p_dbm, [len(wl.spans), s.length_m * 1e-3, s.cr_per_w_km_thz]]).astype(np.float64)
+
+
+class LinkSurrogate:
+    """The network that maps a whole link to all its channels at once: n_ch
+    launch powers + span count + span length + Cr -> 3 x 512 GELU -> n_ch values
+    of 10 log10(eta).  Inputs are zero-padded to a multiple of 64 (the GEMM's k
+    blocks), the output layer to a multiple of 64 rows.  BF16 weights and
+    activations on the tensor cores (egn_mlp_gemm with the GELU epilogues, the
+    pre-activations kept in BF16 for the backward pass), FP32 output layer and
+    loss (egn_mlp_outputs), FP32 masters and Adam.  The same train() and
+    checkpoints as Surrogate; targets are [links][n_ch] arrays."""
+
+    def __init__(self, n_ch: int = 120, seed: int = 0, device: str = "cuda"):
+        import torch
+        self.torch = torch
+        self.dev = device
+        self.n_ch = n_ch
+        self.n_in = n_ch + 3
+        self.in_pad = _pad64(self.n_in)
+        self.out_pad = _pad64(n_ch)
+        rng = np.random.default_rng(seed)
+        dims = [self.in_pad] + [LINK_HIDDEN] * LINK_LAYERS
+        self.W, self.b, self.Wb, self.WbT = [], [], [], []
+        for i in range(LINK_LAYERS):
+            fan_in = self.n_in if i == 0 else dims[i]
+            lim = 1.0 / math.sqrt(fan_in)
+            w = np.zeros((dims[i + 1], dims[i]), dtype=np.float32)
+            w[:, :fan_in] = rng.uniform(-lim, lim, size=(dims[i + 1], fan_in))
+            self.W.append(torch.tensor(w, device=device))
+            self.b.append(torch.tensor(rng.uniform(-lim, lim, dims[i + 1]).astype(np.float32), device=device))
+            self.Wb.append(torch.empty(w.shape, dtype=torch.bfloat16, device=device))
+            self.WbT.append(torch.empty((w.shape[1], w.shape[0]), dtype=torch.bfloat16, device=device))
+        lim = 1.0 / math.sqrt(LINK_HIDDEN)
+        wo = np.zeros((self.out_pad, LINK_HIDDEN), dtype=np.float32)
+        wo[:n_ch] = rng.uniform(-lim, lim, size=(n_ch, LINK_HIDDEN))
+        self.w_out = torch.tensor(wo, device=device)
+        self.b_out = torch.tensor(rng.uniform(-lim, lim, n_ch).astype(np.float32), device=device)
+        self.wb_out = torch.empty(wo.shape, dtype=torch.bfloat16, device=device)
+        self.wb_outT = torch.empty((LINK_HIDDEN, self.out_pad), dtype=torch.bfloat16, device=device)
+        self.params = [p for pair in zip(self.W, self.b) for p in pair] + [self.w_out, self.b_out]
+        self.m = [torch.zeros_like(p) for p in self.params]
+        self.v = [torch.zeros_like(p) for p in self.params]
+        self.step_count = 0
+        self.err = torch.zeros(1, dtype=torch.int32, device=device)
+        self.x_mean = np.zeros(self.n_in)
+        self.x_std = np.ones(self.n_in)
+        self.y_mean, self.y_std = np.zeros(n_ch), np.ones(n_ch)
+        self._refresh_bf16(None)
+
+    def _refresh_bf16(self, stream):
+        for i in range(LINK_LAYERS):
+            K.cast(self.W[i], self.Wb[i], stream=stream)
+            K.transpose(self.Wb[i], self.Wb[i].shape[0], self.WbT[i], stream=stream)
+        K.cast(self.w_out, self.wb_out, stream=stream)
+        K.transpose(self.wb_out, self.out_pad, self.wb_outT, stream=stream)
+
+    def _buffers(self, rows_pad):
+        torch = self.torch
+        if getattr(self, "_rows", None) == rows_pad:
+            return
+        self._rows = rows_pad
+        bf, H = torch.bfloat16, LINK_HIDDEN
+        self.h = [torch.zeros((rows_pad, self.in_pad), dtype=bf, device=self.dev)] + \
+                 [torch.empty((rows_pad, H), dtype=bf, device=self.dev) for _ in range(LINK_LAYERS)]
+        self.z = [None] + [torch.empty((rows_pad, H), dtype=bf, device=self.dev) for _ in range(LINK_LAYERS)]
+        self.acc = torch.empty((rows_pad, self.out_pad), dtype=torch.float32, device=self.dev)
+        self.y = torch.empty((rows_pad, self.n_ch), dtype=torch.float32, device=self.dev)
+        self.loss = torch.empty(1, dtype=torch.float32, device=self.dev)
+        self.g = torch.empty((rows_pad, self.out_pad), dtype=bf, device=self.dev)
+        self.gT = torch.empty((self.out_pad, rows_pad), dtype=bf, device=self.dev)
+        self.dz = [torch.empty((rows_pad, H), dtype=bf, device=self.dev) for _ in range(2)]
+        self.dzT = torch.empty((H, rows_pad), dtype=bf, device=self.dev)
+        self.hT = torch.empty((max(H, self.in_pad), rows_pad), dtype=bf, device=self.dev)
+        kb = rows_pad // 64
+        per = -(-kb // 16)
+        self.splits = -(-kb // per)
+        self.part = torch.empty(self.splits * max(H, self.out_pad) * max(H, self.in_pad), dtype=torch.float32,
+                                device=self.dev)
+        self.grads = [torch.empty_like(p) for p in self.params]
+        self.xf = torch.empty((rows_pad, self.in_pad), dtype=torch.float32, device=self.dev)
+
+    def _load_inputs(self, x: np.ndarray, stream):
+        torch = self.torch
+        rows = x.shape[0]
+        rows_pad = ((rows + 63) // 64) * 64
+        self._buffers(rows_pad)
+        xp = np.zeros((rows_pad, self.in_pad), dtype=np.float32)
+        xp[:rows, :self.n_in] = (x - self.x_mean) / self.x_std
+        self.xf.copy_(torch.from_numpy(xp))
+        K.cast(self.xf, self.h[0], stream=stream)
+        return rows, rows_pad
+
+    def _forward(self, rows, rows_pad, stream):
+        for i in range(LINK_LAYERS):
+            K.gemm(self.h[i], self.Wb[i], self.h[i + 1], K.EPI_BIAS_GELU, bias=self.b[i], aux=self.z[i + 1],
+                   err=self.err, stream=stream)
+        K.gemm(self.h[LINK_LAYERS], self.wb_out, self.acc, K.EPI_F32, err=self.err, stream=stream)
+
+    def predict_rows(self, x: np.ndarray, stream=None) -> np.ndarray:
+        """10 log10(eta) [links][n_ch] for input rows x [links][n_ch + 3]."""
+        rows, rows_pad = self._load_inputs(np.atleast_2d(x), stream)
+        self._forward(rows, rows_pad, stream)
+        K.outputs(self.acc, rows, rows_pad, self.n_ch, self.b_out, self.y, stream=stream)
+        self._check()
+        return self.y[:rows].cpu().numpy().astype(np.float64) * self.y_std + self.y_mean
+
+    def train_step(self, x: np.ndarray, t: np.ndarray, lr: float, stream=None) -> float:
+        """One Adam step on input rows x [links][n_ch + 3] and targets t [links][n_ch]."""
+        torch = self.torch
+        rows, rows_pad = self._load_inputs(x, stream)
+        tn = np.zeros((rows_pad, self.n_ch), dtype=np.float32)
+        tn[:rows] = (t - self.y_mean) / self.y_std
+        mask = np.zeros(rows_pad, dtype=np.float32)
+        mask[:rows] = 1.0
+        tgt = torch.from_numpy(tn).to(self.dev)
+        msk = torch.from_numpy(mask).to(self.dev)
+        self._forward(rows, rows_pad, stream)
+        H = LINK_HIDDEN
+        K.outputs(self.acc, rows_pad, rows_pad, self.n_ch, self.b_out, self.y, target=tgt, mask=msk, loss=self.loss,
+                  g=self.g, db=self.grads[-1], stream=stream)
+        # output layer: dW_out = g^T h3 (k = rows), dz3 = (g W_out) GELU'(z3)
+        K.transpose(self.g, rows_pad, self.gT, stream=stream)
+        hT = self.hT[:H]
+        K.transpose(self.h[LINK_LAYERS], rows_pad, hT, stream=stream)
+        part = self.part[: self.splits * self.out_pad * H]
+        K.gemm(self.gT, hT, part, K.EPI_F32, splits=self.splits, err=self.err, stream=stream)
+        K.reduce_splits(part, self.splits, self.grads[-2], stream=stream)
+        cur = 0
+        K.gemm(self.g, self.wb_outT, self.dz[cur], K.EPI_GELU_GRAD, aux=self.z[LINK_LAYERS], err=self.err,
+               stream=stream)
+        for i in reversed(range(LINK_LAYERS)):  # layer i maps h[i] to z[i + 1]
+            dz = self.dz[cur]
+            fan = self.h[i].shape[1]
+            K.transpose(dz, rows_pad, self.dzT, stream=stream)
+            hT = self.hT[:fan]
+            K.transpose(self.h[i], rows_pad, hT, stream=stream)
+            part = self.part[: self.splits * H * fan]
+            K.gemm(self.dzT, hT, part, K.EPI_F32, splits=self.splits, err=self.err, stream=stream)
+            K.reduce_splits(part, self.splits, self.grads[2 * i], stream=stream)
+            K.colsum(dz, self.grads[2 * i + 1], stream=stream)
+            if i > 0:
+                K.gemm(dz, self.WbT[i], self.dz[1 - cur], K.EPI_GELU_GRAD, aux=self.z[i], err=self.err, stream=stream)
+                cur = 1 - cur
+        self.step_count += 1
+        for p, g, m, v in zip(self.params, self.grads, self.m, self.v):
+            K.adam(p, g, m, v, lr, self.step_count, stream=stream)
+        self._refresh_bf16(stream)
+        self._check()
+        return float(self.loss.item())
+
+    def _check(self):
+        e = int(self.err.item())
+        if e:
+            raise RuntimeError(f"a tensor-core kernel's bounded wait ran out (code {e})")
+
+    def fit_normalisation(self, x: np.ndarray, t: np.ndarray):
+        self.x_mean = x.mean(axis=0)
+        sd = x.std(axis=0)
+        self.x_std = np.where(sd > 1e-12, sd, 1.0)
+        self.y_mean = t.mean(axis=0)
+        sd = t.std(axis=0)
+        self.y_std = np.where(sd > 1e-12, sd, 1.0)
+
+    def state(self) -> dict:
+        st = {"step_count": np.int64(self.step_count), "x_mean": self.x_mean, "x_std": self.x_std,
+              "y_mean": self.y_mean, "y_std": self.y_std}
+        for j, (p, m, v) in enumerate(zip(self.params, self.m, self.v)):
+            st[f"p{j}"] = p.cpu().numpy()
+            st[f"m{j}"] = m.cpu().numpy()
+            st[f"v{j}"] = v.cpu().numpy()
+        return st
+
+    def load_state(self, st) -> None:
+        torch = self.torch
+        for j, (p, m, v) in enumerate(zip(self.params, self.m, self.v)):
+            for dst, key in ((p, f"p{j}"), (m, f"m{j}"), (v, f"v{j}")):
+                src = np.asarray(st[key])
+                if src.shape != tuple(dst.shape):
+                    raise ValueError(f"checkpoint {key}: shape {src.shape}, model {tuple(dst.shape)}")
+                dst.copy_(torch.from_numpy(src))
+        self.step_count = int(st["step_count"])
+        self.x_mean, self.x_std = np.asarray(st["x_mean"]), np.asarray(st["x_std"])
+        self.y_mean, self.y_std = np.asarray(st["y_mean"]), np.asarray(st["y_std"])
+        self._refresh_bf16(None)
+
+
 def _save_atomic(path: str, arrays: dict) -> None:
     tmp = path + ".tmp"
     with open(tmp, "wb") as f:
@@ -366,13 +570,19 @@ def generate_labels(directory: str, seeds: Sequence[int], opts, shard_links: int
     return np.concatenate([np.load(os.path.join(directory, f"shard_{k:05d}.npy")) for k in range(n_shards)])
 
 
-def predict(model: Surrogate, workloads: Sequence, opts):
-    """10 log10(eta) per link: the MLP inside the training envelope, the
-    integrator outside it.  Returns (list of arrays, list of bools: used the MLP)."""
-    inside = [in_envelope(w) for w in workloads]
+def predict(model, workloads: Sequence, opts, n_ch: int = 120):
+    """10 log10(eta) per link: the network inside the training envelope, the
+    integrator outside it.  `model` is a Surrogate (per-channel rows) or a
+    LinkSurrogate (one row per link).  Returns (list of arrays, list of bools:
+    used the network)."""
+    inside = [in_envelope(w, n_ch) for w in workloads]
     res: List = [None] * len(workloads)
     idx = [i for i, ok in enumerate(inside) if ok]
-    if idx:
+    if idx and isinstance(model, LinkSurrogate):
+        y = model.predict_rows(np.stack([link_features(workloads[i]) for i in idx]))
+        for k, i in enumerate(idx):
+            res[i] = y[k]
+    elif idx:
         x = np.concatenate([features(workloads[i]) for i in idx])
         y = model.predict_rows(x)
         o = 0

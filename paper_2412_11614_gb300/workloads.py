@@ -226,9 +226,10 @@ def random_link(seed: int, gl_order: int = 16) -> Workload:
     )
 
 
-def surrogate_link(seed: int, gl_order: int = 32) -> Workload:
+def surrogate_link(seed: int, gl_order: int = 32, n_ch: int = 120) -> Workload:
     """Seeded C+L link for the surrogate: the 120-channel, 64 GBd, 75 GHz grid of
-    config_cl; N_s ~ U{1..30} identical SSMF spans of L ~ U[50, 120] km with
+    config_cl (or its n_ch central channels' grid of the same spacing, centred at
+    the same frequency); N_s ~ U{1..30} identical SSMF spans of L ~ U[50, 120] km with
     Cr ~ U[0.014, 0.042] 1/(W km THz); mean launch power U[-2, 4] dBm with a
     linear tilt U[-3, 3] dB across the band and N(0, 0.5 dB) ripple per
     channel; formats drawn per channel.  Training seeds 1, 2, ...; held-out
@@ -239,7 +240,7 @@ def surrogate_link(seed: int, gl_order: int = 32) -> Workload:
     cr = 0.014 + 0.028 * rng.uniform()
     p0 = -2.0 + 6.0 * rng.uniform()
     tilt = -3.0 + 6.0 * rng.uniform()
-    base = config_cl(gl_order=gl_order, n_spans=1)
+    base = config_cl(gl_order=gl_order, n_spans=1, n_ch=n_ch)
     cen = base.centre_hz
     f_min, f_max = cen[0], cen[-1]
     powers = []
@@ -250,7 +251,7 @@ def surrogate_link(seed: int, gl_order: int = 32) -> Workload:
     fibre = dict(SSMF)
     fibre["cr_per_w_km_thz"] = cr
     return Workload(
-        name=f"surrogate link {seed}: 120ch C+L, {n_spans}x{length_km:.1f}km, Cr {cr:.4f}, {p0:.2f} dBm, tilt {tilt:.2f} dB",
+        name=f"surrogate link {seed}: {n_ch}ch C+L, {n_spans}x{length_km:.1f}km, Cr {cr:.4f}, {p0:.2f} dBm, tilt {tilt:.2f} dB",
         spans=_spans(fibre, length_km, n_spans),
         centre_hz=list(cen),
         symbol_rate_baud=[64e9] * len(cen),

@@ -1,14 +1,15 @@
 """Surrogate kernels (include/egn_mlp.h) against plain FP64 references on the same
-BF16 values, and the surrogate's gradients against a CPU FP64 MLP.
+BF16 values, and both networks' gradients against CPU FP64 networks.
 
 Tolerances: FP32-epilogue GEMM within 1e-5 of the FP64 product relative to
 sum |a||b| (FP32 accumulation over k <= 1024); BF16 epilogues within one BF16
 rounding (2^-8 relative) of the rounded FP64 result; whole-network gradients
-within 1e-2 relative (Frobenius) of an FP64 reference that rounds to BF16 where
-the kernels store activations and their gradients (what remains: FP32 against
-FP64 accumulation and the odd BF16 tie), and within 1e-1 of the unrounded FP64
-reference (the size of the BF16 storage effect on a random-target problem,
-where the gradients are small residuals).
+element by element: within 2 % of each element plus 0.2 % of the tensor's
+largest element against an FP64 reference that rounds to BF16 where the kernels
+store activations and their gradients (what remains: FP32 against FP64
+accumulation and the odd BF16 tie), and within 10 % of each element plus 10 %
+of the tensor's largest against the unrounded FP64 reference (the size of the BF16 storage effect on a random-target
+problem, where the gradients are small residuals).
 """
 import numpy as np
 import pytest
@@ -174,6 +175,14 @@ def _fp64_mlp_grads(x, Ws, bs, w_out, b_out, t, mask, bf16_storage=False):
     return loss, dW, db, dw_out, db_out
 
 
+def _close_elementwise(got, want, rtol, atol_frac, name):
+    """|got - want| <= rtol |want| + atol_frac max |want|, element by element."""
+    got, want = np.asarray(got, dtype=np.float64), np.asarray(want, dtype=np.float64)
+    bound = rtol * np.abs(want) + atol_frac * np.max(np.abs(want))
+    bad = np.abs(got - want) > bound
+    assert not bad.any(), (name, int(bad.sum()), float(np.max(np.abs(got - want) - bound)))
+
+
 def test_surrogate_gradients_match_fp64_mlp(K):
     import torch
     from paper_2412_11614_gb300 import surrogate as S
@@ -192,24 +201,23 @@ def test_surrogate_gradients_match_fp64_mlp(K):
     xn = torch.tensor(xn, dtype=torch.float32).to(torch.bfloat16).double().numpy()
     tn = (t - model.y_mean) / model.y_std
 
-    def rel(a, b):
-        return np.linalg.norm(a - b) / np.linalg.norm(b)
-
     g = [p.cpu().double().numpy() for p in model.grads]
-    # (1) the same arithmetic with BF16 storage where the kernels store: tight
+    # (1) the same arithmetic with BF16 storage where the kernels store: every
+    # element within 2 % of itself plus 0.2 % of the largest element of its tensor
     lw, dW, db, dwo, dbo = _fp64_mlp_grads(xn, Ws, bs, w_out, b_out, tn, np.ones(rows), bf16_storage=True)
     assert abs(loss - lw) <= 1e-3 * lw
     for i in range(S.LAYERS):
-        assert rel(g[2 * i], dW[i]) < 1e-2, (i, rel(g[2 * i], dW[i]))
-        assert rel(g[2 * i + 1], db[i]) < 1e-2, (i, rel(g[2 * i + 1], db[i]))
-    assert rel(g[-2], dwo) < 1e-3 and abs(g[-1][0] - dbo) <= 1e-3 * abs(dbo) + 1e-6
-    # (2) full FP64: the size of the BF16 storage effect on the gradients
+        _close_elementwise(g[2 * i], dW[i], 2e-2, 2e-3, f"dW{i}")
+        _close_elementwise(g[2 * i + 1], db[i], 2e-2, 2e-3, f"db{i}")
+    _close_elementwise(g[-2], dwo, 1e-3, 1e-4, "dw_out")
+    assert abs(g[-1][0] - dbo) <= 1e-3 * abs(dbo) + 1e-6
+    # (2) full FP64 (no BF16 storage): the storage effect, element by element
     lw, dW, db, dwo, dbo = _fp64_mlp_grads(xn, Ws, bs, w_out, b_out, tn, np.ones(rows))
     assert abs(loss - lw) <= 1e-2 * lw
     for i in range(S.LAYERS):
-        assert rel(g[2 * i], dW[i]) < 1e-1, (i, rel(g[2 * i], dW[i]))
-        assert rel(g[2 * i + 1], db[i]) < 1e-1
-    assert rel(g[-2], dwo) < 3e-2
+        _close_elementwise(g[2 * i], dW[i], 0.1, 0.1, f"dW{i} vs unrounded")
+        _close_elementwise(g[2 * i + 1], db[i], 0.1, 0.1, f"db{i} vs unrounded")
+    _close_elementwise(g[-2], dwo, 3e-2, 3e-3, "dw_out vs unrounded")
 
 
 def test_surrogate_learns_a_smooth_map(K):
@@ -267,3 +275,132 @@ def test_training_checkpoint_resume_is_bit_identical(K, tmp_path):
     c = S.Surrogate(seed=12)
     assert S.train(c, x, t, steps=8, batch_rows=1024, seed=9, checkpoint=ck, every=3) == []
     assert np.array_equal(c.predict_rows(x[:500]), b.predict_rows(x[:500]))
+
+
+def _gelu(z):
+    from scipy.special import erf
+    return 0.5 * z * (1.0 + erf(z / np.sqrt(2.0)))
+
+
+def _gelu_grad(z):
+    from scipy.special import erf
+    return 0.5 * (1.0 + erf(z / np.sqrt(2.0))) + z * np.exp(-0.5 * z * z) / np.sqrt(2.0 * np.pi)
+
+
+def test_gemm_gelu_epilogues(K):
+    """GELU forward (pre-activation to aux, GELU of the stored pre-activation to
+    out) and the GELU-gradient epilogue, within one BF16 rounding."""
+    import torch
+    pytest.importorskip("scipy")
+    rng = np.random.default_rng(8)
+    m, n, k = 200, 96, 128
+    a, b = _bf16(rng, (m, k), 0.2), _bf16(rng, (n, k), 0.2)
+    bias = torch.tensor(rng.normal(0, 0.5, n), dtype=torch.float32)
+    err = torch.zeros(1, dtype=torch.int32, device="cuda")
+    out = torch.empty((m, n), dtype=torch.bfloat16, device="cuda")
+    z = torch.empty((m, n), dtype=torch.bfloat16, device="cuda")
+    K.gemm(a.cuda(), b.cuda(), out, K.EPI_BIAS_GELU, bias=bias.cuda(), aux=z, err=err)
+    torch.cuda.synchronize()
+    assert int(err.item()) == 0
+    acc = a.double().numpy() @ b.double().numpy().T + bias.double().numpy()
+    scale = np.abs(a.double().numpy()) @ np.abs(b.double().numpy()).T + np.abs(bias.double().numpy())
+    zg = z.cpu().double().numpy()
+    assert np.all(np.abs(zg - acc) <= 2.0 ** -8 * np.abs(acc) + 1e-5 * scale)
+    want = _gelu(zg)  # of the pre-activation as stored
+    assert np.all(np.abs(out.cpu().double().numpy() - want) <= 2.0 ** -8 * np.abs(want) + 1e-6)
+    # gradient epilogue with aux = the stored pre-activation
+    g = torch.empty((m, n), dtype=torch.bfloat16, device="cuda")
+    K.gemm(a.cuda(), b.cuda(), g, K.EPI_GELU_GRAD, aux=z, err=err)
+    torch.cuda.synchronize()
+    acc0 = a.double().numpy() @ b.double().numpy().T
+    want = acc0 * _gelu_grad(zg)
+    sc0 = np.abs(a.double().numpy()) @ np.abs(b.double().numpy()).T
+    assert np.all(np.abs(g.cpu().double().numpy() - want) <= 2.0 ** -8 * np.abs(want) + 2e-5 * sc0)
+
+
+def test_outputs_kernel(K):
+    """Multi-output layer: y = acc + b, the masked mean-squared loss over rows and
+    outputs, dL/dy in BF16 with zero padding, and the bias gradient."""
+    import torch
+    rng = np.random.default_rng(12)
+    rows, rows_pad, n_out, n_pad = 70, 128, 40, 64
+    acc = torch.tensor(rng.normal(0, 1, (rows_pad, n_pad)), dtype=torch.float32, device="cuda")
+    b = torch.tensor(rng.normal(0, 1, n_out), dtype=torch.float32, device="cuda")
+    t = torch.tensor(rng.normal(0, 1, (rows, n_out)), dtype=torch.float32, device="cuda")
+    mask = torch.tensor((rng.uniform(size=rows) > 0.3).astype(np.float32), device="cuda")
+    y = torch.empty((rows, n_out), dtype=torch.float32, device="cuda")
+    g = torch.full((rows_pad, n_pad), 7.0, dtype=torch.bfloat16, device="cuda")
+    loss, db = torch.empty(1, device="cuda"), torch.empty(n_out, device="cuda")
+    K.outputs(acc, rows, rows_pad, n_out, b, y, target=t, mask=mask, loss=loss, g=g, db=db)
+    torch.cuda.synchronize()
+    A, B, T, M = (x.cpu().double().numpy() for x in (acc, b, t, mask))
+    yv = A[:rows, :n_out] + B
+    msum = M.sum()
+    gv = 2 * M[:, None] * (yv - T) / (n_out * msum)
+    assert np.allclose(y.cpu().numpy(), yv, rtol=1e-6, atol=1e-6)
+    assert abs(loss.item() - np.sum(M[:, None] * (yv - T) ** 2) / (n_out * msum)) < 1e-5 * loss.item()
+    G = g.cpu().double().numpy()
+    assert np.all(np.abs(G[:rows, :n_out] - gv) <= 2.0 ** -8 * np.abs(gv) + 1e-12)
+    assert np.all(G[rows:] == 0) and np.all(G[:, n_out:] == 0)
+    assert np.allclose(db.cpu().numpy(), gv.sum(0), rtol=1e-5, atol=1e-8)
+
+
+def _fp64_link_net_grads(x, Ws, bs, Wo, bo, t, n_out, q):
+    """FP64 forward/backward of the per-link GELU network with BF16 rounding q
+    where the device kernels store (pre-activations, activations, dL/dy and the
+    layer gradients); masked mean-squared loss over all outputs, mask 1."""
+    hs, zs = [x], [None]
+    for W, b in zip(Ws, bs):
+        z = q(hs[-1] @ W.T + b)
+        zs.append(z)
+        hs.append(q(_gelu(z)))
+    y = hs[-1] @ Wo.T + np.concatenate([bo, np.zeros(Wo.shape[0] - n_out)])
+    y = y[:, :n_out]
+    rows = len(x)
+    loss = np.sum((y - t) ** 2) / (n_out * rows)
+    g32 = 2 * (y - t) / (n_out * rows)
+    dbo = g32.sum(0)
+    g = np.zeros((rows, Wo.shape[0]))
+    g[:, :n_out] = q(g32)
+    dWo = g.T @ hs[-1]
+    dz = q((g @ Wo) * _gelu_grad(zs[-1]))
+    dW, db = [None] * len(Ws), [None] * len(Ws)
+    for i in reversed(range(len(Ws))):
+        dW[i] = dz.T @ hs[i]
+        db[i] = dz.sum(0)
+        if i > 0:
+            dz = q((dz @ Ws[i]) * _gelu_grad(zs[i]))
+    return loss, dW, db, dWo, dbo
+
+
+def test_link_network_gradients_match_fp64(K):
+    """The per-link network (n_ch + 3 inputs -> 3 x 512 GELU -> n_ch outputs) with
+    16 outputs: loss and every gradient element against the FP64 network with the
+    kernels' BF16 storage."""
+    import torch
+    pytest.importorskip("scipy")
+    from paper_2412_11614_gb300 import surrogate as S
+    rng = np.random.default_rng(21)
+    n_ch, rows = 16, 300
+    model = S.LinkSurrogate(n_ch=n_ch, seed=6)
+    x = rng.normal(0, 1, (rows, n_ch + 3))
+    t = rng.normal(0, 1, (rows, n_ch))
+    model.fit_normalisation(x, t)
+    Ws = [w.cpu().to(torch.bfloat16).double().numpy() for w in model.W]
+    bs = [b.cpu().double().numpy() for b in model.b]
+    Wo = model.w_out.cpu().to(torch.bfloat16).double().numpy()
+    bo = model.b_out.cpu().double().numpy()
+    loss = model.train_step(x, t, lr=0.0)  # lr 0: gradients only
+    xn = np.zeros((rows, model.in_pad))
+    xn[:, :n_ch + 3] = (x - model.x_mean) / model.x_std
+    xn = _round_bf16(xn.astype(np.float32))
+    tn = (t - model.y_mean) / model.y_std
+    lw, dW, db, dWo, dbo = _fp64_link_net_grads(xn, Ws, bs, Wo, bo, tn, n_ch, _round_bf16)
+    assert abs(loss - lw) <= 1e-3 * lw
+    g = [p.cpu().double().numpy() for p in model.grads]
+    for i in range(S.LINK_LAYERS):
+        _close_elementwise(g[2 * i], dW[i], 2e-2, 2e-3, f"dW{i}")
+        _close_elementwise(g[2 * i + 1], db[i], 2e-2, 2e-3, f"db{i}")
+    _close_elementwise(g[-2], dWo, 2e-2, 2e-3, "dW_out")
+    _close_elementwise(g[-1], dbo, 1e-4, 1e-5, "db_out")
+    assert np.all(g[-2][n_ch:] == 0)  # padding rows of the output layer get no gradient
