@@ -5,10 +5,16 @@
 // egn_set_wdm calls or egn_link_destroy do not touch the batch), sizes one
 // workspace per link in a single allocation, runs the whole evaluation once
 // without capture (which validates it and completes every lazy launch set-up),
-// then captures the same sequence into a CUDA graph.  In the graph each link's
-// chain -- status reset, planner, integrator passes, assembly -- is captured
-// in two phases: links too small to fill the GPU as concurrent branches on up to
-// kStreams streams, then the links that fill it on their own ("heavy":
+// then captures the same sequence into a CUDA graph.
+//
+// FP32C batches run one flat work list per pass: every link's island planner
+// (concurrent branches on up to kStreams streams), then each integrator pass
+// (D/G/H, E, F) as one launch per kernel family over the work lists of all the
+// links of that family (the job tables of integrate_fp32c.cu: island batches
+// numbered across links), then every link's assembly (concurrent branches).
+// FP64 batches capture each link's chain -- status reset, planner, integrator
+// passes, assembly -- in two phases: links too small to fill the GPU as
+// concurrent branches, then the links that fill it on their own ("heavy":
 // estimated point-segment work above kHeavyWork) one after the other, because
 // heavy links sharing the GPU were measured to slow each other down.
 // egn_batch_launch replays the graph with one call; outputs of all links are
@@ -83,6 +89,8 @@ void rebase_params(LinkParams& p, const egn_link* l, char* ch_copy, char* seg_co
     rebase(p.fib_ck[f], l->d_seg.p, l->d_seg.bytes, seg_copy);
     rebase(p.fib_zk[f], l->d_seg.p, l->d_seg.bytes, seg_copy);
   }
+  rebase(p.glx_all, l->d_gl.p, l->d_gl.bytes, gl_copy);
+  rebase(p.glw_all, l->d_gl.p, l->d_gl.bytes, gl_copy);
   for (int q = 0; q < 4; ++q) {
     rebase(p.gl.x[q], l->d_gl.p, l->d_gl.bytes, gl_copy);
     rebase(p.gl.w[q], l->d_gl.p, l->d_gl.bytes, gl_copy);
@@ -99,6 +107,10 @@ void rebase_params(LinkParams& p, const egn_link* l, char* ch_copy, char* seg_co
 struct egn_batch {
   int device = -1;
   egn_opts opts{};
+  bool flat = false;                     // FP32C: one launch per pass and kernel family
+  std::vector<egn::MultiLaunch> multi;   // those launches, in pass order
+  std::vector<size_t> multi_off;         // their job tables' offsets in d_jobs
+  DevBuf d_jobs;
   std::vector<BatchLink> links;
   std::vector<long long> off;  // channel offsets, off[n] = all channels
   DevBuf d_tab, d_ws, d_out;   // table copies; workspaces; eta | pnli | status
@@ -125,6 +137,7 @@ struct egn_batch {
     d_tab.release();
     d_ws.release();
     d_out.release();
+    d_jobs.release();
   }
 };
 
@@ -145,10 +158,93 @@ egn_status enqueue_link(egn_batch* b, size_t i, cudaStream_t s) {
   return EGN_OK;
 }
 
+// Island planner of link i on stream s (status word reset first).
+egn_status plan_link(egn_batch* b, size_t i, cudaStream_t s) {
+  const BatchLink& L = b->links[i];
+  Workspace ws = egn::carve_workspace((char*)b->d_ws.p + L.ws_off, L.n_ch, L.cnt, b->opts.precision);
+  EGN_CUDA(cudaMemsetAsync(ws.status, 0, sizeof(int), s));
+  EGN_CUDA(egn::launch_plan(L.ch, ws, s));
+  return EGN_OK;
+}
+
+// Assembly of link i into the batch outputs and its status word, on stream s.
+egn_status assemble_link(egn_batch* b, size_t i, cudaStream_t s) {
+  const BatchLink& L = b->links[i];
+  Workspace ws = egn::carve_workspace((char*)b->d_ws.p + L.ws_off, L.n_ch, L.cnt, b->opts.precision);
+  EGN_CUDA(egn::launch_assemble(L.ch, half_offsets(ws, L.n_ch), ws.keys, ws.h_idx, L.cnt.n_isl, ws.terms,
+                                b->opts.precision, b->opts.terms, b->eta() + b->off[i], b->pnli() + b->off[i], s));
+  EGN_CUDA(cudaMemcpyAsync(b->status() + i, ws.status, sizeof(int), cudaMemcpyDeviceToDevice, s));
+  return EGN_OK;
+}
+
+// fn(i, stream) for every link as concurrent branches of `root` (up to kStreams), joined back.
+template <class F>
+egn_status branches(egn_batch* b, cudaStream_t root, F fn) {
+  const int ns = std::min<int>(kStreams, (int)b->links.size());
+  EGN_CUDA(cudaEventRecord(b->fork, root));
+  for (int j = 0; j < ns; ++j) EGN_CUDA(cudaStreamWaitEvent(b->st[j], b->fork, 0));
+  for (size_t i = 0; i < b->links.size(); ++i) {
+    egn_status s = fn(i, b->st[i % ns]);
+    if (s != EGN_OK) return s;
+  }
+  for (int j = 0; j < ns; ++j) {
+    EGN_CUDA(cudaEventRecord(b->join[j], b->st[j]));
+    EGN_CUDA(cudaStreamWaitEvent(root, b->join[j], 0));
+  }
+  return EGN_OK;
+}
+
+// FP32C: planners, one launch per pass and kernel family over every link, assemblies.
+egn_status enqueue_flat(egn_batch* b, cudaStream_t root) {
+  EGN_LAUNCH_GATE();
+  egn_status s = branches(b, root, [&](size_t i, cudaStream_t st) { return plan_link(b, i, st); });
+  if (s != EGN_OK) return s;
+  for (size_t k = 0; k < b->multi.size(); ++k)
+    EGN_CUDA(egn::launch_fp32c_multi(b->multi[k], (const char*)b->d_jobs.p + b->multi_off[k], root));
+  return branches(b, root, [&](size_t i, cudaStream_t st) { return assemble_link(b, i, st); });
+}
+
+// The job tables of the flat passes (FP32C): per pass (D/G/H, E, F) and kernel
+// family, every link's work list of that pass; copied to device memory once.
+egn_status build_flat(egn_batch* b) {
+  std::vector<egn::FlatPass> fp[3][3];
+  const bool corr = b->opts.terms != 0;
+  for (BatchLink& L : b->links) {
+    Workspace ws = egn::carve_workspace((char*)b->d_ws.p + L.ws_off, L.n_ch, L.cnt, b->opts.precision);
+    const int fam = egn::fp32c_family(L.p);
+    float* terms = (float*)ws.terms;
+    fp[0][fam].push_back({&L.p, ws.keys, ws.d_idx, L.cnt.n_half, terms, L.cnt.n_isl});
+    if (corr && L.cnt.n_e) fp[1][fam].push_back({&L.p, ws.keys, ws.e_idx, L.cnt.n_e, terms, L.cnt.n_isl});
+    if (corr && L.cnt.n_f) fp[2][fam].push_back({&L.p, ws.keys, ws.f_idx, L.cnt.n_f, terms, L.cnt.n_isl});
+  }
+  size_t total = 0;
+  for (auto& ord : fp)
+    for (auto& v : ord)
+      if (!v.empty()) total += align256(egn::fp32c_multi_bytes((int)v.size()));
+  std::vector<char> image(total, 0);
+  size_t off = 0;
+  for (int ord = 0; ord < 3; ++ord)
+    for (int fam = 0; fam < 3; ++fam) {
+      auto& v = fp[ord][fam];
+      if (v.empty()) continue;
+      egn::MultiLaunch m{};
+      EGN_CUDA(egn::fp32c_multi_build(ord, fam, v.data(), (int)v.size(), image.data() + off, &m));
+      b->multi.push_back(m);
+      b->multi_off.push_back(off);
+      off += align256(egn::fp32c_multi_bytes((int)v.size()));
+    }
+  if (total) {
+    EGN_ALLOC(b->d_jobs.ensure(total));
+    EGN_CUDA(h2d(b->d_jobs.p, image.data(), total));
+  }
+  return EGN_OK;
+}
+
 // The whole evaluation of the batch on `root`: first the light links as
 // concurrent branches (round-robin over up to kStreams streams, joined back),
 // then the heavy links one after the other, so heavy work never shares the GPU.
 egn_status enqueue(egn_batch* b, cudaStream_t root) {
+  if (b->flat) return enqueue_flat(b, root);
   int n_light = 0;
   for (const BatchLink& L : b->links) n_light += !L.heavy;
   if (n_light) {
@@ -258,6 +354,11 @@ egn_status create(egn_link* const* links, int n_links, const egn_opts* o, bool c
       L.p.types_dev = (const egn::SpanType*)ty_c;
     }
     L.ch = L.p.ch;
+  }
+  b->flat = o->precision == EGN_PREC_FP32C;
+  if (b->flat) {
+    egn_status fs = build_flat(b);
+    if (fs != EGN_OK) return fs;
   }
   // one plain run: validates the batch and completes lazy launch set-up
   egn_status s = enqueue(b, b->cap);

@@ -100,6 +100,10 @@ struct SpanType {
 
 // Forms of the FWM efficiency mu (egn_opts.mu_form).
 enum { MU_SEGMENT = 0, MU_MACLAURIN = 1, MU_INTEGRAL = 2 };
+// Node rules (egn_set_node_rule): the configured panels of Gauss-Legendre nodes,
+// or the ridge-resolving rule (FP64 path).
+enum { RULE_GL = 0, RULE_RIDGE = 1 };
+constexpr int kRidgeMaxN = 64;  // nodes per piece of the ridge rule
 constexpr int kMuGl = 10;  // Gauss-Legendre order per quarter period of the integral form
 
 // Everything an integrator launch needs, passed by value.  With n_types == 1
@@ -122,6 +126,10 @@ struct LinkParams {
   int terms;         // 0 GN, 1 EGN
   int all_terms;     // evaluate E..H on every island (parity checks)
   int fp32c_kp;      // points per thread of the FP32C D/G/H pass (4 or 8)
+  int rule;          // RULE_GL or RULE_RIDGE (then gl.n is the node count per piece)
+  int ridge_n_min;   // ridge rule: fewest nodes of a piece that does not end on a ridge
+  const double* glx_all;  // Gauss-Legendre nodes of every order m = 1 .. gl.n, order m at offset m (m - 1) / 2
+  const double* glw_all;  // and their weights
   int mu_form;       // MU_SEGMENT, MU_MACLAURIN or MU_INTEGRAL (the last two: FP64 path)
   double btot;       // B_tot [THz] of Eq. 25
   double mgx[kMuGl], mgw[kMuGl];  // Gauss-Legendre rule of the integral form on [-1, 1]
@@ -199,6 +207,30 @@ cudaError_t launch_fp64_pass(int ord, const LinkParams& p, const uint64_t* keys,
                              long long n_items, double* terms, long long n_isl, cudaStream_t st);
 cudaError_t launch_fp32c_pass(int ord, const LinkParams& p, const uint64_t* keys, const uint32_t* list,
                               long long n_items, float* terms, long long n_isl, cudaStream_t st);
+
+// Multi-link FP32C passes (batches of links): one launch per pass and kernel
+// family over the work lists of several links.  A link's family: 0 identical
+// spans (phased-array closed form), 1 up to kMaxTypes span types, 2 more.
+struct FlatPass {
+  const LinkParams* p;   // the link's launch parameters (host copy; device pointers inside)
+  const uint64_t* keys;  // its island keys (device)
+  const uint32_t* list;  // the pass's work list (device; nullptr: every island)
+  long long n_items;
+  float* terms;          // its term slots (device)
+  long long n_isl;
+};
+struct MultiLaunch {
+  int ord, family, n_jobs;
+  long long batches;  // island batches of every link of the pass
+  size_t smem;        // dynamic shared memory of the launch
+};
+int fp32c_family(const LinkParams& p);
+// Bytes of the job table of one pass over n links.
+size_t fp32c_multi_bytes(int n_links);
+// Host image of the job table of pass `ord` over n links of one family, and the
+// launch's shape; copy the image to device memory of fp32c_multi_bytes(n) bytes.
+cudaError_t fp32c_multi_build(int ord, int family, const FlatPass* links, int n, void* image, MultiLaunch* out);
+cudaError_t launch_fp32c_multi(const MultiLaunch& m, const void* d_jobs, cudaStream_t st);
 
 // Assembly (Eq. 11, 15): per-COI sums over the half list, each island weighted
 // for itself and its mirror.  half_off: per-row offsets of the half list.

@@ -36,6 +36,7 @@
 //    Hardware sin/cos (MUFU, absolute error ~4e-7 on [-pi, pi]) elsewhere.
 // Island sums: FP32 per thread, fixed-order shuffle and shared-memory trees.
 #include <algorithm>
+#include <cstring>
 
 #include "egn_internal.h"
 
@@ -333,54 +334,50 @@ __device__ __forceinline__ float warp_sum(const float* r) {
   return t;
 }
 
+// Shared state of the identical-spans passes (one CTA).
 template <int ORD, int KP, int NT>
-__global__ void __launch_bounds__(NT, min_ctas(ORD, KP, NT))
-integrate_fp32c_kernel(LinkParams p, const uint64_t* __restrict__ keys, const uint32_t* __restrict__ list,
-                       long long n_items, float* __restrict__ terms, long long n_isl, int rows_per_chunk, int kpad,
-                       Df G0, Df G1) {
-  static_assert(KP % 2 == 0, "points per thread come in f32x2 pairs");
-  constexpr int NPAIR = KP / 2;
-  constexpr int NB = batch_of(ORD, NT);
-  __shared__ BatchSmT<NB> bs;
-  __shared__ RowSm<rows_max(NT)> rsb[2];  // the current island's rows and the next one's
-  constexpr int NW = NT / 32;
-  __shared__ float red[4][NW];
+struct DwShared {
+  BatchSmT<batch_of(ORD, NT)> bs;
+  RowSm<rows_max(NT)> rsb[2];  // the current island's rows and the next one's
+  float red[4][NT / 32];
   // the rows the c_k table holds (DW): their f3 in FP32 and their number (-1: none)
-  __shared__ float tab_f3[rows_max(NT)];
-  __shared__ int tab_rows;
-  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  float tab_f3[rows_max(NT)];
+  int tab_rows;
+};
+
+// Per-link constants of the identical-spans passes.
+struct DwConsts {
+  int K;
+  float Kf, invK, alpha, alpha2, r, one_m_r, q, m2r, c2r, c4r, omr2, N, gam, g2;
+};
+
+__device__ __forceinline__ DwConsts dw_consts(const LinkParams& p) {
+  DwConsts c;
+  c.K = p.seg.K;
+  c.Kf = (float)c.K;
+  c.invK = 1.0f / (float)c.K;
+  c.alpha = (float)p.alpha;
+  c.alpha2 = c.alpha * c.alpha;
+  c.r = (float)p.r;
+  c.one_m_r = (float)(-expm1(-p.alpha * p.dz));
+  c.q = c.r * c.r;
+  c.m2r = -2.0f * c.r;
+  c.c2r = 2.0f * c.r;
+  c.c4r = 4.0f * c.r;
+  c.omr2 = c.one_m_r * c.one_m_r;
+  c.N = (float)p.n_spans;
+  c.gam = (float)p.gamma;
+  c.g2 = c.gam * c.gam;
+  return c;
+}
+
+// Inner Gauss-Legendre nodes of the launch into dynamic shared memory:
+// {x head, x tail, x^2 head, x^2 tail}[npad], {x^3, w}[npad]; nodes n..npad-1 are
+// x = 0 with weight 0, so no point slot needs a bounds test.
+template <int NT>
+__device__ __forceinline__ void load_nodes(const LinkParams& p, int npad, float4* nx4, float2* nx2) {
   const int n = p.gl.n;
-  if (tid == 0) tab_rows = -1;  // read after the first batch barrier
-  // threads per row (power of two), row slot and point slot of this thread; the
-  // tpr x KP point slots of a row cover the n inner nodes
-  const int tpr = threads_per_row(n, KP);
-  const int npad = tpr * KP;
-  const int rows_per_pass = NT / tpr;
-  const int lr = tid & (tpr - 1);
-  const int rsub = tid / tpr;
-  // dynamic: inner nodes {x head, x tail, x^2 head, x^2 tail}[npad], {x^3, w}[npad]
-  // (nodes n..npad-1 are x = 0 with weight 0, so no point slot needs a bounds
-  // test), then (DW only) the [rows_per_chunk][kpad] c_k of the chunk's rows,
-  // 16-byte aligned
-  extern __shared__ __align__(16) float dyn[];
-  float4* const nx4 = reinterpret_cast<float4*>(dyn);
-  float2* const nx2 = reinterpret_cast<float2*>(dyn + 4 * npad);
-  float* const tab = dyn + node_floats(npad);
-
-  const int K = p.seg.K;
-  const float Kf = (float)K, invK = 1.0f / (float)K;
-  const float alpha = (float)p.alpha, alpha2 = alpha * alpha;
-  const float r = (float)p.r;
-  const float one_m_r = (float)(-expm1(-p.alpha * p.dz));
-  const float q = r * r;
-  const float m2r = -2.0f * r;
-  const float c2r = 2.0f * r, c4r = 4.0f * r, omr2 = one_m_r * one_m_r;
-  const float N = (float)p.n_spans;
-  const float gam = (float)p.gamma;
-  const float g2 = gam * gam;
-  const float pi_f = 3.14159265358979f;
-
-  for (int j = tid; j < npad; j += NT) {
+  for (int j = threadIdx.x; j < npad; j += NT) {
     if (j < n) {
       const float xh = p.gl.xh[1][j], xl = p.gl.xl[1][j];
       nx4[j] = make_float4(xh, xl, p.gl.x2h[1][j], p.gl.x2l[1][j]);
@@ -390,10 +387,45 @@ integrate_fp32c_kernel(LinkParams p, const uint64_t* __restrict__ keys, const ui
       nx2[j] = make_float2(0.0f, 0.0f);
     }
   }
+}
 
-  int cur = 0;             // row buffer of the current island
-  bool have_rows = false;  // its rows were formed with the previous island's
-  for (long long b0 = (long long)blockIdx.x * NB; b0 < n_items; b0 += (long long)gridDim.x * NB) {
+// One batch of islands (work items b0 .. b0 + NB - 1 of `list`) of one link.
+// cur and have_rows carry the row buffers from island to island.
+template <int ORD, int KP, int NT>
+__device__ __forceinline__ void dw_batch(const LinkParams& p, const DwConsts& cst, const uint64_t* __restrict__ keys,
+                                         const uint32_t* __restrict__ list, long long n_items,
+                                         float* __restrict__ terms, long long n_isl, int rows_per_chunk, int kpad,
+                                         Df G0, Df G1, long long b0, DwShared<ORD, KP, NT>& sh,
+                                         const float4* __restrict__ nx4, const float2* __restrict__ nx2,
+                                         float* __restrict__ tab, int& cur, bool& have_rows) {
+  constexpr int NPAIR = KP / 2;
+  constexpr int NB = batch_of(ORD, NT);
+  constexpr int NW = NT / 32;
+  auto& bs = sh.bs;
+  auto& rsb = sh.rsb;
+  auto& red = sh.red;
+  auto& tab_f3 = sh.tab_f3;
+  int& tab_rows = sh.tab_rows;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const int n = p.gl.n;
+  // threads per row (power of two), row slot and point slot of this thread; the
+  // tpr x KP point slots of a row cover the n inner nodes
+  const int tpr = threads_per_row(n, KP);
+  const int rows_per_pass = NT / tpr;
+  const int lr = tid & (tpr - 1);
+  const int rsub = tid / tpr;
+  const int K = cst.K;
+  const float Kf = cst.Kf, invK = cst.invK;
+  const float alpha = cst.alpha, alpha2 = cst.alpha2;
+  const float r = cst.r;
+  const float one_m_r = cst.one_m_r;
+  const float q = cst.q;
+  const float m2r = cst.m2r;
+  const float c2r = cst.c2r, c4r = cst.c4r, omr2 = cst.omr2;
+  const float N = cst.N;
+  const float g2 = cst.g2;
+  const float pi_f = 3.14159265358979f;
+  (void)r;
     // ---------------- 1. batch set-up, FP64, one island per thread
     if (tid < NB) batch_setup<ORD>(p, keys, list, n_items, b0, bs, tid);
     __syncthreads();
@@ -698,7 +730,31 @@ integrate_fp32c_kernel(LinkParams p, const uint64_t* __restrict__ keys, const ui
       if (fetched) cur ^= 1;
       have_rows = fetched;
     }
-  }
+}
+
+template <int ORD, int KP, int NT>
+__global__ void __launch_bounds__(NT, min_ctas(ORD, KP, NT))
+integrate_fp32c_kernel(LinkParams p, const uint64_t* __restrict__ keys, const uint32_t* __restrict__ list,
+                       long long n_items, float* __restrict__ terms, long long n_isl, int rows_per_chunk, int kpad,
+                       Df G0, Df G1) {
+  static_assert(KP % 2 == 0, "points per thread come in f32x2 pairs");
+  constexpr int NB = batch_of(ORD, NT);
+  __shared__ DwShared<ORD, KP, NT> sh;
+  if (threadIdx.x == 0) sh.tab_rows = -1;  // read after the first batch barrier
+  const int npad = threads_per_row(p.gl.n, KP) * KP;
+  // dynamic: the inner nodes, then (DW only) the [rows_per_chunk][kpad] c_k of
+  // the chunk's rows, 16-byte aligned
+  extern __shared__ __align__(16) float dyn[];
+  float4* const nx4 = reinterpret_cast<float4*>(dyn);
+  float2* const nx2 = reinterpret_cast<float2*>(dyn + 4 * npad);
+  float* const tab = dyn + node_floats(npad);
+  const DwConsts cst = dw_consts(p);
+  load_nodes<NT>(p, npad, nx4, nx2);
+  int cur = 0;             // row buffer of the current island
+  bool have_rows = false;  // its rows were formed with the previous island's
+  for (long long b0 = (long long)blockIdx.x * NB; b0 < n_items; b0 += (long long)gridDim.x * NB)
+    dw_batch<ORD, KP, NT>(p, cst, keys, list, n_items, terms, n_isl, rows_per_chunk, kpad, G0, G1, b0, sh, nx4, nx2,
+                          tab, cur, have_rows);
 }
 
 template <int ORD, int KP, int NT>
@@ -768,19 +824,50 @@ struct GenRowSm {
   float ih[kGRows];
 };
 
-template <int ORD>
-__global__ void __launch_bounds__(kThreads, 3)
-integrate_fp32c_general_kernel(LinkParams p, const uint64_t* __restrict__ keys, const uint32_t* __restrict__ list,
-                               long long n_items, float* __restrict__ terms, long long n_isl, int rows_per_chunk,
-                               GenTypes gt) {
-  constexpr int KP = 2;
-  __shared__ BatchSm bs;
-  __shared__ GenRowSm rs;
-  __shared__ NodeSm ns;
-  __shared__ float red[4][kThreads / 32];
-  __shared__ float tyf[kMaxTypes][6];  // K, 1/K, alpha, r, 1 - r, gamma
-  extern __shared__ __align__(16) float tabg[];  // [rows_per_chunk][ktot]
+// Shared state of the general-links passes (one CTA).
+struct GenShared {
+  BatchSm bs;
+  GenRowSm rs;
+  NodeSm ns;
+  float red[4][kThreads / 32];
+  float tyf[kMaxTypes][6];  // K, 1/K, alpha, r, 1 - r, gamma
+};
 
+// Inner Gauss-Legendre nodes of the launch (the first n slots).
+__device__ __forceinline__ void load_node_sm(const LinkParams& p, NodeSm& ns) {
+  for (int j = threadIdx.x; j < p.gl.n; j += kThreads) {
+    const float xh = p.gl.xh[1][j], xl = p.gl.xl[1][j];
+    ns.x4[j] = make_float4(xh, xl, p.gl.x2h[1][j], p.gl.x2l[1][j]);
+    ns.x2[j] = make_float2(xh * p.gl.x2h[1][j], p.gl.wf[1][j]);
+  }
+}
+
+// Per-type constants of a general link (the caller synchronises before use).
+__device__ __forceinline__ void gen_types(const LinkParams& p, GenShared& sh) {
+  const int tid = threadIdx.x;
+  if (tid < p.n_types) {
+    const SpanType& ty = p.types[tid];
+    sh.tyf[tid][0] = (float)ty.seg.K;
+    sh.tyf[tid][1] = 1.0f / (float)ty.seg.K;
+    sh.tyf[tid][2] = (float)ty.alpha;
+    sh.tyf[tid][3] = (float)ty.r;
+    sh.tyf[tid][4] = (float)(-expm1(-ty.alpha * ty.dz));
+    sh.tyf[tid][5] = (float)ty.gamma;
+  }
+}
+
+// One batch of islands (items b0 .. b0 + kBatch - 1 of `list`) of one general link.
+template <int ORD>
+__device__ __forceinline__ void gen_batch(const LinkParams& p, const GenTypes& gt, const uint64_t* __restrict__ keys,
+                                          const uint32_t* __restrict__ list, long long n_items,
+                                          float* __restrict__ terms, long long n_isl, int rows_per_chunk,
+                                          long long b0, GenShared& sh, float* __restrict__ tabg) {
+  constexpr int KP = 2;
+  auto& bs = sh.bs;
+  auto& rs = sh.rs;
+  auto& ns = sh.ns;
+  auto& red = sh.red;
+  auto& tyf = sh.tyf;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const int n = p.gl.n;
   const int T = p.n_types;
@@ -791,23 +878,6 @@ integrate_fp32c_general_kernel(LinkParams p, const uint64_t* __restrict__ keys, 
   const int rows_per_pass = kThreads / tpr;
   const int lr = tid & (tpr - 1);
   const int rsub = tid / tpr;
-  for (int j = tid; j < n; j += kThreads) {
-    const float xh = p.gl.xh[1][j], xl = p.gl.xl[1][j];
-    ns.x4[j] = make_float4(xh, xl, p.gl.x2h[1][j], p.gl.x2l[1][j]);
-    ns.x2[j] = make_float2(xh * p.gl.x2h[1][j], p.gl.wf[1][j]);
-  }
-  if (tid < T) {
-    const SpanType& ty = p.types[tid];
-    tyf[tid][0] = (float)ty.seg.K;
-    tyf[tid][1] = 1.0f / (float)ty.seg.K;
-    tyf[tid][2] = (float)ty.alpha;
-    tyf[tid][3] = (float)ty.r;
-    tyf[tid][4] = (float)(-expm1(-ty.alpha * ty.dz));
-    tyf[tid][5] = (float)ty.gamma;
-  }
-  __syncthreads();
-
-  for (long long b0 = (long long)blockIdx.x * kBatch; b0 < n_items; b0 += (long long)gridDim.x * kBatch) {
     batch_setup<ORD>(p, keys, list, n_items, b0, bs, tid);
     __syncthreads();
     const int nb = (int)min((long long)kBatch, n_items - b0);
@@ -1054,7 +1124,20 @@ integrate_fp32c_general_kernel(LinkParams p, const uint64_t* __restrict__ keys, 
       }
       __syncthreads();
     }
-  }
+}
+
+template <int ORD>
+__global__ void __launch_bounds__(kThreads, 3)
+integrate_fp32c_general_kernel(LinkParams p, const uint64_t* __restrict__ keys, const uint32_t* __restrict__ list,
+                               long long n_items, float* __restrict__ terms, long long n_isl, int rows_per_chunk,
+                               GenTypes gt) {
+  __shared__ GenShared sh;
+  extern __shared__ __align__(16) float tabg[];  // [rows_per_chunk][ktot]
+  load_node_sm(p, sh.ns);
+  gen_types(p, sh);
+  __syncthreads();
+  for (long long b0 = (long long)blockIdx.x * kBatch; b0 < n_items; b0 += (long long)gridDim.x * kBatch)
+    gen_batch<ORD>(p, gt, keys, list, n_items, terms, n_isl, rows_per_chunk, b0, sh, tabg);
 }
 
 template <int ORD>
@@ -1108,42 +1191,37 @@ cudaError_t launch_general(const LinkParams& p, const uint64_t* keys, const uint
 
 constexpr int kSpanTypeFloats = 12;  // per type: G0 (df), G1 (df), K, 1/K, alpha, r, 1 - r, gamma, beta2, pi beta3
 
-template <int ORD>
-__global__ void __launch_bounds__(kThreads, 2)
-integrate_fp32c_spans_kernel(LinkParams p, const uint64_t* __restrict__ keys, const uint32_t* __restrict__ list,
-                             long long n_items, float* __restrict__ terms, long long n_isl, int rows_per_chunk,
-                             int kfp) {
-  constexpr int KP = 2;
-  __shared__ BatchSm bs;
-  __shared__ float4 g_ab[kGRows], g_ow[kGRows], g_f3[kGRows];
-  __shared__ float g_ih[kGRows];
-  __shared__ NodeSm ns;
-  __shared__ float red[4][kThreads / 32];
-  extern __shared__ __align__(16) float dyn[];
-  const int T = p.n_types, R = rows_per_chunk;
-  float4* sqa = reinterpret_cast<float4*>(dyn);  // [T][R]
-  float4* sqb = sqa + T * R;                     // [T][R]
-  float2* skc = reinterpret_cast<float2*>(sqb + T * R);  // [T][R]
-  float* tyc = reinterpret_cast<float*>(skc + T * R);     // [T][kSpanTypeFloats]
-  // DW with fibre groups: c_k of the chunk's rows per fibre, [n_fib][R][kfp]
-  float* tabf = tyc + T * kSpanTypeFloats;
-  const bool fib_tab = ORD == ORD_DW && p.n_fib > 0;
+// Shared state of the span-by-span passes (one CTA); the per-type constants, row
+// phases and fibre tables are in dynamic shared memory, laid out by spans_layout.
+struct SpansShared {
+  BatchSm bs;
+  float4 g_ab[kGRows], g_ow[kGRows], g_f3[kGRows];
+  float g_ih[kGRows];
+  NodeSm ns;
+  float red[4][kThreads / 32];
+};
 
-  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-  const int n = p.gl.n;
-  const float k4 = (float)(4.0 * kPi * kPi);
-  const float pi_f = 3.14159265358979f;
-  int tpr = 1;
-  while (tpr * KP < n) tpr <<= 1;
-  const int rows_per_pass = kThreads / tpr;
-  const int lr = tid & (tpr - 1);
-  const int rsub = tid / tpr;
-  for (int j = tid; j < n; j += kThreads) {
-    const float xh = p.gl.xh[1][j], xl = p.gl.xl[1][j];
-    ns.x4[j] = make_float4(xh, xl, p.gl.x2h[1][j], p.gl.x2l[1][j]);
-    ns.x2[j] = make_float2(xh * p.gl.x2h[1][j], p.gl.wf[1][j]);
-  }
-  for (int t = tid; t < T; t += kThreads) {
+struct SpansLayout {
+  float4* sqa;  // [T][R]
+  float4* sqb;  // [T][R]
+  float2* skc;  // [T][R]
+  float* tyc;   // [T][kSpanTypeFloats]
+  float* tabf;  // DW with fibre groups: c_k of the chunk's rows per fibre, [n_fib][R][kfp]
+};
+
+__device__ __forceinline__ SpansLayout spans_layout(float* dyn, int T, int R) {
+  SpansLayout l;
+  l.sqa = reinterpret_cast<float4*>(dyn);
+  l.sqb = l.sqa + T * R;
+  l.skc = reinterpret_cast<float2*>(l.sqb + T * R);
+  l.tyc = reinterpret_cast<float*>(l.skc + T * R);
+  l.tabf = l.tyc + T * kSpanTypeFloats;
+  return l;
+}
+
+// Per-type constants of a span-by-span link (the caller synchronises before use).
+__device__ __forceinline__ void spans_types(const LinkParams& p, float* tyc) {
+  for (int t = threadIdx.x; t < p.n_types; t += kThreads) {
     const SpanType& ty = p.types_dev[t];
     const double g0 = 2.0 * kPi * ty.L * ty.beta2, g1 = 2.0 * kPi * kPi * ty.L * ty.beta3;
     float* c = tyc + kSpanTypeFloats * t;
@@ -1160,9 +1238,39 @@ integrate_fp32c_spans_kernel(LinkParams p, const uint64_t* __restrict__ keys, co
     c[10] = (float)ty.beta2;
     c[11] = (float)(kPi * ty.beta3);
   }
-  __syncthreads();
+}
 
-  for (long long b0 = (long long)blockIdx.x * kBatch; b0 < n_items; b0 += (long long)gridDim.x * kBatch) {
+// One batch of islands (items b0 .. b0 + kBatch - 1 of `list`) of one link walked span by span.
+template <int ORD>
+__device__ __forceinline__ void spans_batch(const LinkParams& p, const uint64_t* __restrict__ keys,
+                                            const uint32_t* __restrict__ list, long long n_items,
+                                            float* __restrict__ terms, long long n_isl, int rows_per_chunk, int kfp,
+                                            long long b0, SpansShared& sh, float* dyn) {
+  constexpr int KP = 2;
+  auto& bs = sh.bs;
+  auto& g_ab = sh.g_ab;
+  auto& g_ow = sh.g_ow;
+  auto& g_f3 = sh.g_f3;
+  auto& g_ih = sh.g_ih;
+  auto& ns = sh.ns;
+  auto& red = sh.red;
+  const int T = p.n_types, R = rows_per_chunk;
+  const SpansLayout lay = spans_layout(dyn, T, R);
+  float4* const sqa = lay.sqa;
+  float4* const sqb = lay.sqb;
+  float2* const skc = lay.skc;
+  const float* const tyc = lay.tyc;
+  float* const tabf = lay.tabf;
+  const bool fib_tab = ORD == ORD_DW && p.n_fib > 0;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const int n = p.gl.n;
+  const float k4 = (float)(4.0 * kPi * kPi);
+  const float pi_f = 3.14159265358979f;
+  int tpr = 1;
+  while (tpr * KP < n) tpr <<= 1;
+  const int rows_per_pass = kThreads / tpr;
+  const int lr = tid & (tpr - 1);
+  const int rsub = tid / tpr;
     batch_setup<ORD>(p, keys, list, n_items, b0, bs, tid);
     __syncthreads();
     const int nb = (int)min((long long)kBatch, n_items - b0);
@@ -1389,7 +1497,20 @@ integrate_fp32c_spans_kernel(LinkParams p, const uint64_t* __restrict__ keys, co
       }
       __syncthreads();
     }
-  }
+}
+
+template <int ORD>
+__global__ void __launch_bounds__(kThreads, 2)
+integrate_fp32c_spans_kernel(LinkParams p, const uint64_t* __restrict__ keys, const uint32_t* __restrict__ list,
+                             long long n_items, float* __restrict__ terms, long long n_isl, int rows_per_chunk,
+                             int kfp) {
+  __shared__ SpansShared sh;
+  extern __shared__ __align__(16) float dyn[];
+  load_node_sm(p, sh.ns);
+  spans_types(p, spans_layout(dyn, p.n_types, rows_per_chunk).tyc);
+  __syncthreads();
+  for (long long b0 = (long long)blockIdx.x * kBatch; b0 < n_items; b0 += (long long)gridDim.x * kBatch)
+    spans_batch<ORD>(p, keys, list, n_items, terms, n_isl, rows_per_chunk, kfp, b0, sh, dyn);
 }
 
 constexpr int kSpansDynBytes = 96 * 1024;  // per-type constants, row phases and fibre c_k tables
@@ -1429,6 +1550,209 @@ cudaError_t launch_spans(const LinkParams& p, const uint64_t* keys, const uint32
   return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// Multi-link passes (a batch of links, FP32C).  One pass of several links is one
+// launch per kernel family: the island batches of the links' work lists are
+// numbered across the links (link j owns batches first_batch_j ..
+// first_batch_{j+1} - 1), a CTA takes batches gb = blockIdx.x, blockIdx.x +
+// gridDim.x, ..., finds each one's link by binary search in the job table and
+// evaluates it with that link's parameters exactly as the single-link kernels
+// do; a CTA moving to another link forms that link's constants first.
+// ---------------------------------------------------------------------------
+
+struct LinkJob {
+  LinkParams p;
+  const uint64_t* keys;
+  const uint32_t* list;
+  long long n_items;
+  float* terms;
+  long long n_isl;
+  long long first_batch;
+  int rows;  // rows per chunk
+  int kpad;  // identical spans: row stride of the c_k table
+  int kfp;   // span by span: row stride of the fibre tables
+  Df G0, G1; // identical spans: 2 pi L beta2, 2 pi^2 L beta3
+  GenTypes gt;  // up to kMaxTypes span types
+};
+
+// The last job whose first batch is at most gb.
+__device__ __forceinline__ int find_job(const LinkJob* __restrict__ jobs, int n_jobs, long long gb) {
+  int lo = 0, hi = n_jobs - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (jobs[mid].first_batch <= gb) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+template <int ORD>
+__global__ void __launch_bounds__(kDwThreads, min_ctas(ORD, 4, kDwThreads))
+integrate_fp32c_multi_kernel(const LinkJob* __restrict__ jobs, int n_jobs, long long batches) {
+  constexpr int KP = 4, NT = kDwThreads, NB = batch_of(ORD, NT);
+  __shared__ DwShared<ORD, KP, NT> sh;
+  const int npad = threads_per_row(jobs[0].p.gl.n, KP) * KP;  // every link of a batch has the same order
+  extern __shared__ __align__(16) float dyn[];
+  float4* const nx4 = reinterpret_cast<float4*>(dyn);
+  float2* const nx2 = reinterpret_cast<float2*>(dyn + 4 * npad);
+  float* const tab = dyn + node_floats(npad);
+  load_nodes<NT>(jobs[0].p, npad, nx4, nx2);
+  int cur = 0;
+  bool have_rows = false;
+  int job = -1;
+  DwConsts cst{};
+  for (long long gb = blockIdx.x; gb < batches; gb += gridDim.x) {
+    const int j = find_job(jobs, n_jobs, gb);
+    const LinkJob& J = jobs[j];
+    if (j != job) {  // another link: its constants, and a c_k table that holds none of its rows
+      job = j;
+      cst = dw_consts(J.p);
+      if (threadIdx.x == 0) sh.tab_rows = -1;  // read after the batch set-up's barrier
+    }
+    dw_batch<ORD, KP, NT>(J.p, cst, J.keys, J.list, J.n_items, J.terms, J.n_isl, J.rows, J.kpad, J.G0, J.G1,
+                          (gb - J.first_batch) * NB, sh, nx4, nx2, tab, cur, have_rows);
+  }
+}
+
+template <int ORD>
+__global__ void __launch_bounds__(kThreads, 3)
+integrate_fp32c_general_multi_kernel(const LinkJob* __restrict__ jobs, int n_jobs, long long batches) {
+  __shared__ GenShared sh;
+  extern __shared__ __align__(16) float tabg[];
+  load_node_sm(jobs[0].p, sh.ns);
+  int job = -1;
+  for (long long gb = blockIdx.x; gb < batches; gb += gridDim.x) {
+    const int j = find_job(jobs, n_jobs, gb);
+    const LinkJob& J = jobs[j];
+    if (j != job) {  // the previous batch ended on a barrier
+      job = j;
+      gen_types(J.p, sh);
+      __syncthreads();
+    }
+    gen_batch<ORD>(J.p, J.gt, J.keys, J.list, J.n_items, J.terms, J.n_isl, J.rows, (gb - J.first_batch) * kBatch, sh,
+                   tabg);
+  }
+}
+
+template <int ORD>
+__global__ void __launch_bounds__(kThreads, 2)
+integrate_fp32c_spans_multi_kernel(const LinkJob* __restrict__ jobs, int n_jobs, long long batches) {
+  __shared__ SpansShared sh;
+  extern __shared__ __align__(16) float dyn[];
+  load_node_sm(jobs[0].p, sh.ns);
+  int job = -1;
+  for (long long gb = blockIdx.x; gb < batches; gb += gridDim.x) {
+    const int j = find_job(jobs, n_jobs, gb);
+    const LinkJob& J = jobs[j];
+    if (j != job) {  // the previous batch ended on a barrier
+      job = j;
+      spans_types(J.p, spans_layout(dyn, J.p.n_types, J.rows).tyc);
+      __syncthreads();
+    }
+    spans_batch<ORD>(J.p, J.keys, J.list, J.n_items, J.terms, J.n_isl, J.rows, J.kfp, (gb - J.first_batch) * kBatch,
+                     sh, dyn);
+  }
+}
+
+// Launch shape of one link in a pass of its family, as the single-link launchers
+// choose it: rows per chunk, table strides, the phase constants, the dynamic
+// shared memory and the island batches.
+struct JobShape {
+  int rows = 0, kpad = 0, kfp = 0;
+  Df G0{}, G1{};
+  GenTypes gt{};
+  size_t smem = 0;
+  long long batches = 0;
+};
+
+JobShape job_shape(int ord, int family, const LinkParams& p, long long n_items) {
+  JobShape s;
+  if (family == 0) {
+    const int K = p.seg.K;
+    s.kpad = (K + 3) & ~3;
+    if ((s.kpad & 7) == 0) s.kpad += 4;
+    s.rows = rows_max(kDwThreads);
+    if (ord == ORD_DW) s.rows = std::max(1, std::min(kTabFloats / s.kpad, rows_max(kDwThreads)));
+    const int npad = threads_per_row(p.gl.n, 4) * 4;
+    s.smem = ((size_t)node_floats(npad) + (ord == ORD_DW ? (size_t)s.rows * s.kpad : 0)) * sizeof(float);
+    const double g0 = 2.0 * kPi * p.L * p.beta2, g1 = 2.0 * kPi * kPi * p.L * p.beta3;
+    const float g0h = (float)g0, g1h = (float)g1;
+    s.G0 = {g0h, (float)(g0 - (double)g0h)};
+    s.G1 = {g1h, (float)(g1 - (double)g1h)};
+    s.batches = (n_items + batch_of(ord, kDwThreads) - 1) / batch_of(ord, kDwThreads);
+  } else if (family == 1) {
+    int ktot = 0;
+    for (int t = 0; t < p.n_types; ++t) {
+      const SpanType& ty = p.types[t];
+      const double g0 = 2.0 * kPi * ty.L * ty.beta2, g1 = 2.0 * kPi * kPi * ty.L * ty.beta3;
+      const float g0h = (float)g0, g1h = (float)g1;
+      s.gt.G0[t] = {g0h, (float)(g0 - (double)g0h)};
+      s.gt.G1[t] = {g1h, (float)(g1 - (double)g1h)};
+      s.gt.koff[t] = ktot;
+      ktot += ty.seg.K;
+    }
+    s.gt.ktot = ktot;
+    s.rows = kGRows;
+    if (ord == ORD_DW) s.rows = std::max(1, std::min(kGTab / ktot, kGRows));
+    s.smem = ord == ORD_DW ? (size_t)s.rows * ktot * sizeof(float) : 0;
+    s.batches = (n_items + kBatch - 1) / kBatch;
+  } else {
+    const int T = p.n_types;
+    const int per_type = (int)(2 * sizeof(float4) + sizeof(float2));
+    if (ord == ORD_DW && p.n_fib > 0) {
+      for (int f = 0; f < p.n_fib; ++f) s.kfp = std::max(s.kfp, p.fib_K[f]);
+      s.kfp = (s.kfp + 3) & ~3;
+      if ((s.kfp & 7) == 0) s.kfp += 4;
+    }
+    const int per_row = T * per_type + (ord == ORD_DW ? p.n_fib * s.kfp * (int)sizeof(float) : 0);
+    s.rows = std::min((kSpansDynBytes - T * kSpanTypeFloats * (int)sizeof(float)) / per_row, kGRows);
+    s.smem = (size_t)s.rows * per_row + (size_t)T * kSpanTypeFloats * sizeof(float);
+    s.batches = (n_items + kBatch - 1) / kBatch;
+  }
+  return s;
+}
+
+template <class F>
+cudaError_t set_smem_once(F* fn, int bytes, unsigned long long& done) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (done >> (dev & 63) & 1ull) return cudaSuccess;
+  e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e == cudaSuccess) done |= 1ull << (dev & 63);
+  return e;
+}
+
+template <int ORD>
+cudaError_t launch_multi_ord(const MultiLaunch& m, const void* d_jobs, cudaStream_t st) {
+  int dev = 0, sms = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return e;
+  const LinkJob* jobs = (const LinkJob*)d_jobs;
+  if (m.family == 0) {
+    static unsigned long long done = 0;
+    e = set_smem_once(integrate_fp32c_multi_kernel<ORD>, (node_floats(2 * kMaxGl) + kTabFloats) * (int)sizeof(float),
+                      done);
+    if (e != cudaSuccess) return e;
+    const long long blocks = std::min<long long>((long long)sms * min_ctas(ORD, 4, kDwThreads), m.batches);
+    integrate_fp32c_multi_kernel<ORD><<<(unsigned)blocks, kDwThreads, m.smem, st>>>(jobs, m.n_jobs, m.batches);
+  } else if (m.family == 1) {
+    static unsigned long long done = 0;
+    e = set_smem_once(integrate_fp32c_general_multi_kernel<ORD>, kGTab * (int)sizeof(float), done);
+    if (e != cudaSuccess) return e;
+    const long long blocks = std::min<long long>((long long)sms * 3, m.batches);
+    integrate_fp32c_general_multi_kernel<ORD><<<(unsigned)blocks, kThreads, m.smem, st>>>(jobs, m.n_jobs, m.batches);
+  } else {
+    static unsigned long long done = 0;
+    e = set_smem_once(integrate_fp32c_spans_multi_kernel<ORD>, kSpansDynBytes, done);
+    if (e != cudaSuccess) return e;
+    const long long blocks = std::min<long long>((long long)sms * 2, m.batches);
+    integrate_fp32c_spans_multi_kernel<ORD><<<(unsigned)blocks, kThreads, m.smem, st>>>(jobs, m.n_jobs, m.batches);
+  }
+  return cudaGetLastError();
+}
+
 }  // namespace
 
 cudaError_t launch_fp32c_pass(int ord, const LinkParams& p, const uint64_t* keys, const uint32_t* list,
@@ -1449,6 +1773,54 @@ cudaError_t launch_fp32c_pass(int ord, const LinkParams& p, const uint64_t* keys
   }
   if (ord == ORD_E) return launch_one<ORD_E, 4, kDwThreads>(p, keys, list, n_items, terms, n_isl, st);
   return launch_one<ORD_F, 4, kDwThreads>(p, keys, list, n_items, terms, n_isl, st);
+}
+
+
+int fp32c_family(const LinkParams& p) { return p.n_types > kMaxTypes ? 2 : (p.n_types > 1 ? 1 : 0); }
+
+size_t fp32c_multi_bytes(int n_links) { return (size_t)std::max(n_links, 1) * sizeof(LinkJob); }
+
+cudaError_t fp32c_multi_build(int ord, int family, const FlatPass* links, int n, void* image, MultiLaunch* out) {
+  if (n < 1 || !links || !image || !out || ord < 0 || ord > 2 || family < 0 || family > 2) return cudaErrorInvalidValue;
+  LinkJob* jobs = (LinkJob*)image;
+  long long batches = 0;
+  size_t smem = 0;
+  for (int i = 0; i < n; ++i) {
+    const FlatPass& f = links[i];
+    if (fp32c_family(*f.p) != family || (i > 0 && f.p->gl.n != links[0].p->gl.n)) return cudaErrorInvalidValue;
+    const JobShape js = job_shape(ord, family, *f.p, f.n_items);
+    if (js.rows < 1) return cudaErrorInvalidValue;  // not reached: the single-link checks hold for every link
+    LinkJob& J = jobs[i];
+    std::memset((void*)&J, 0, sizeof(LinkJob));
+    J.p = *f.p;
+    J.keys = f.keys;
+    J.list = f.list;
+    J.n_items = f.n_items;
+    J.terms = f.terms;
+    J.n_isl = f.n_isl;
+    J.first_batch = batches;
+    J.rows = js.rows;
+    J.kpad = js.kpad;
+    J.kfp = js.kfp;
+    J.G0 = js.G0;
+    J.G1 = js.G1;
+    J.gt = js.gt;
+    batches += js.batches;
+    smem = std::max(smem, js.smem);
+  }
+  out->ord = ord;
+  out->family = family;
+  out->n_jobs = n;
+  out->batches = batches;
+  out->smem = smem;
+  return cudaSuccess;
+}
+
+cudaError_t launch_fp32c_multi(const MultiLaunch& m, const void* d_jobs, cudaStream_t st) {
+  if (m.batches <= 0) return cudaSuccess;
+  if (m.ord == ORD_DW) return launch_multi_ord<ORD_DW>(m, d_jobs, st);
+  if (m.ord == ORD_E) return launch_multi_ord<ORD_E>(m, d_jobs, st);
+  return launch_multi_ord<ORD_F>(m, d_jobs, st);
 }
 
 }  // namespace egn

@@ -30,7 +30,10 @@ def _workloads(workloads):
     d.spans[1].D_ps_nm_km = 21.0
     d.spans[2].length_m = 57e3
     e = workloads.config_small(n_ch=1, gl_order=16)
-    return [a, b, c, d, e]
+    f = workloads.config_small(n_ch=3, gl_order=16, n_spans=6)  # six span types: the span-by-span path
+    for i, s in enumerate(f.spans):
+        s.length_m = (60 + 7 * i) * 1e3
+    return [a, b, c, d, e, f]
 
 
 @pytest.mark.parametrize("prec", ["fp32c", "fp64"])
