@@ -343,6 +343,21 @@ def fp64_denominator(args, wl, ln, eta32, value, stream, flush) -> dict:
            "speedup_vs_fp64_gpu": value / (n_ch / (ms64 * 1e-3)),
            "max_db_vs_fp64": float(err.max()), "mean_db_vs_fp64": float(err.mean()),
            "worst_channel_vs_fp64": int(err.argmax())}
+    if not args.no_ridge:
+        # the ridge-resolving node rule (FP64) on the same link: its time per evaluation and
+        # how far the configured 32 x 32 rule's eta lies from it (the rule's discretisation error)
+        ln.set_node_rule(egn.EGN_RULE_RIDGE, 4)
+        orr = egn.make_opts(gl_order=args.ridge_nodes, dz_km=wl.dz_km, precision=egn.EGN_PREC_FP64,
+                            terms=egn.EGN_TERMS_EGN, stream=stream.cuda_stream)
+        msr, etar = timed_evals(ln, orr, n_ch, stream, flush, steps=1, warm=1)
+        ln.set_node_rule(egn.EGN_RULE_GL)
+        dr = 10 * np.log10(eta64 / etar)
+        out["ridge_rule"] = {"nodes_per_piece": args.ridge_nodes, "n_min": 4, "precision": "fp64",
+                             "ms_per_step": msr, "value": n_ch / (msr * 1e-3), "unit": UNIT,
+                             "gl32_minus_ridge_db": {"mean": float(dr.mean()), "min": float(dr.min()),
+                                                     "max": float(dr.max()), "edge": float(dr[0]),
+                                                     "centre": float(dr[n_ch // 2])},
+                             "eta_db_sample": [float(10 * np.log10(x)) for x in etar[:: 30]]}
     if args.no_sweep:
         return out
     sweep = {"p_dbm": [], "ms_fp32c": [], "ms_fp64": [], "channel_evals_per_s_fp32c": [], "max_abs_db_vs_fp64": [],
@@ -724,6 +739,8 @@ def main():
                     help="skip the plain FP64 GPU integrator leg and the launch-power sweep")
     ap.add_argument("--no-sweep", action="store_true", help="skip the -2..+4 dBm/ch launch-power sweep")
     ap.add_argument("--fp64-steps", type=int, default=3)
+    ap.add_argument("--no-ridge", action="store_true", help="skip the ridge-resolving rule's FP64 evaluation")
+    ap.add_argument("--ridge-nodes", type=int, default=16, help="nodes per piece of the ridge-resolving rule")
     ap.add_argument("--peaks", action="store_true",
                     help="measure the FP32, FP32x2, FP64 and MUFU pipe peaks with the probe kernels")
     ap.add_argument("--e2e-steps", type=int, default=None)

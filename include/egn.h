@@ -305,6 +305,51 @@ typedef struct {
 egn_status egn_autotune(egn_link* link, const egn_opts* opts, double target_db, const double* dz_candidates,
                         int n_candidates, double dz_ref_km, egn_tune_result* out);
 
+/* Node rule of the island integrals (Eq. 17-21).
+ *   EGN_RULE_GL     (default) the Gauss-Legendre panels of egn_opts.gl_order.
+ *   EGN_RULE_RIDGE  a rule that resolves the ridges of |mu|^2 along f1 = f and
+ *                   f2 = f (with chi of Eq. 5/24, |mu|^2 is close to a Lorentzian
+ *                   in f1 - f of half-width alpha / (4 pi^2 |beta2 + 2 pi beta3 f|
+ *                   |f2 - f|), far narrower than the channels): in each evaluation
+ *                   order the outer range is cut at the knees of the outer
+ *                   raised-cosine shape, wherever two inner break lines cross and
+ *                   at a ridge of the outer variable; every inner interval at the
+ *                   knees of the other two shapes and at the ridges inside it.  A
+ *                   piece that ends on a ridge gets egn_opts.gl_order nodes graded
+ *                   by x = x_r + h sinh(tau) (tau on a Gauss-Legendre rule, h the
+ *                   ridge half-width; a piece with ridges at both ends is halved);
+ *                   another piece gets max(n_min, ceil(gl_order x length /
+ *                   interval)) Gauss-Legendre nodes.  The half-widths take the first
+ *                   span's alpha, beta2 and beta3.  EGN_PREC_FP64 only, gl_order
+ *                   <= 64 (other requests: EGN_E_UNSUPPORTED / EGN_E_INVALID_ARG);
+ *                   egn_nli_eta_static refuses it.
+ * The rule is a setting of the link; n_min is ignored for EGN_RULE_GL. */
+enum { EGN_RULE_GL = 0, EGN_RULE_RIDGE = 1 };
+egn_status egn_set_node_rule(egn_link* link, int rule, int n_min);
+
+/* Choice of the node rule (Sec. III-D weighs accuracy against time; here the
+ * quadrature of Eq. 17-21).  Evaluates the link (FP64) with the configured
+ * Gauss-Legendre rule of opts->gl_order and with the ridge-resolving rule at
+ * 4, 8, 16, ... nodes per piece, doubling until the worst channel moves by less
+ * than target_db / 4 between two orders or max_nodes (4..64) is reached; that
+ * last order stands for the converged value.  Picks the smallest order whose
+ * worst channel lies within target_db of it, sets EGN_RULE_RIDGE (n_min 4) on
+ * the link, and reports the chosen order, its error, the configured rule's
+ * error against the same value and the device time of one evaluation at the
+ * choice.  Synchronous; the caller evaluates with opts.gl_order = nodes and
+ * EGN_PREC_FP64.  On failure the link's node rule is left as it was. */
+typedef struct {
+    int rule;                 /* EGN_RULE_RIDGE */
+    int nodes;                /* chosen nodes per piece */
+    double max_err_db;        /* worst channel |10 log10(eta(nodes) / eta(reference))| */
+    int reference_nodes;      /* the last order evaluated */
+    double last_change_db;    /* worst channel change between the last two orders */
+    double configured_err_db; /* the same error of the configured rule */
+    double ms;                /* device ms of one evaluation with the choice */
+} egn_rule_result;
+egn_status egn_autotune_rule(egn_link* link, const egn_opts* opts, double target_db, int max_nodes,
+                             egn_rule_result* out);
+
 /* Per-stage device timing.  With profiling on, every evaluation records CUDA
  * events on its stream around five stages; egn_last_timings waits for the last
  * evaluation and writes up to max durations [ms] in the order: island planner,

@@ -180,6 +180,11 @@ egn_status check_opts(const egn_link* l, const egn_opts* o) {
     return fail(EGN_E_INVALID_ARG, "the span types need %.0f segments in all, more than %d", ksum, kMaxKSum);
   if (o->terms == EGN_TERMS_EGN && l->mixed_rates && l->any_corr)
     return fail(EGN_E_UNSUPPORTED, "EGN corrections with mixed symbol rates are not defined");
+  if (l->rule == RULE_RIDGE) {
+    if (o->precision != EGN_PREC_FP64) return fail(EGN_E_UNSUPPORTED, "the ridge-resolving rule runs in FP64 only");
+    if (o->gl_order > kRidgeMaxN)
+      return fail(EGN_E_INVALID_ARG, "ridge rule: %d nodes per piece, at most %d", o->gl_order, kRidgeMaxN);
+  }
   return EGN_OK;
 }
 
@@ -253,7 +258,16 @@ egn_status ensure_tables(egn_link* l, const egn_opts* o) {
       for (int a = 0; a < 2; ++a) { off[p][a] = total; total += align256(m * sizeof(double)); }
       for (int a = 2; a < 7; ++a) { off[p][a] = total; total += align256(m * sizeof(float)); }
     }
+    // the ridge rule's pieces take every order 1..max(n, n_min): order m at offset
+    // m (m - 1) / 2, tabulated up to max(n, kRidgeMaxN)
+    const int m_all = std::max(n, kRidgeMaxN);
+    const size_t n_all = (size_t)m_all * (m_all + 1) / 2;
+    const size_t off_allx = total, off_allw = total + align256(n_all * sizeof(double));
+    total += 2 * align256(n_all * sizeof(double));
     host.assign(total, 0);
+    for (int m = 1; m <= m_all; ++m)
+      gauss_legendre(m, (double*)(host.data() + off_allx) + (size_t)m * (m - 1) / 2,
+                     (double*)(host.data() + off_allw) + (size_t)m * (m - 1) / 2);
     for (int p = 1; p <= 3; ++p) {
       int m = ord[p];
       std::vector<double> x(m), w(m);
@@ -291,6 +305,8 @@ egn_status ensure_tables(egn_link* l, const egn_opts* o) {
       l->gl.wf[p] = (const float*)(b + off[p][6]);
     }
     l->gl.order[0] = 0;
+    l->gl_all_x = (const double*)(b + off_allx);
+    l->gl_all_w = (const double*)(b + off_allw);
     l->tab_gl = n;
   }
   return EGN_OK;
@@ -357,6 +373,10 @@ LinkParams link_params(const egn_link* l, const egn_opts* o, int all_terms) {
   p.terms = o->terms;
   p.all_terms = all_terms;
   p.fp32c_kp = l->fp32c_kp;
+  p.rule = l->rule;
+  p.ridge_n_min = l->ridge_n_min;
+  p.glx_all = l->gl_all_x;
+  p.glw_all = l->gl_all_w;
   set_mu_params(p, l, o);
   p.n_types = l->identical ? 1 : (int)l->type_si.size();
   for (int t = 0; t < p.n_types && t < kMaxTypes; ++t) p.types[t] = l->types[t];
@@ -790,6 +810,16 @@ egn_status egn_set_tuning(egn_link* l, int param, int value) {
   }
 }
 
+egn_status egn_set_node_rule(egn_link* l, int rule, int n_min) {
+  if (!l) return fail(EGN_E_INVALID_ARG, "null link");
+  if (rule != EGN_RULE_GL && rule != EGN_RULE_RIDGE) return fail(EGN_E_INVALID_ARG, "unknown node rule %d", rule);
+  if (rule == EGN_RULE_RIDGE && (n_min < 1 || n_min > kRidgeMaxN))
+    return fail(EGN_E_INVALID_ARG, "n_min %d not in [1, %d]", n_min, kRidgeMaxN);
+  l->rule = rule == EGN_RULE_RIDGE ? RULE_RIDGE : RULE_GL;
+  if (rule == EGN_RULE_RIDGE) l->ridge_n_min = n_min;
+  return EGN_OK;
+}
+
 egn_status egn_set_profiling(egn_link* l, int enable) {
   if (!l) return fail(EGN_E_INVALID_ARG, "null link");
   l->prof_on = enable != 0;
@@ -997,6 +1027,7 @@ extern "C" egn_status egn_nli_eta_static(egn_link* l, const egn_opts* o, double*
   egn_status s = check_opts(l, o);
   if (s != EGN_OK) return s;
   if (!eta_dev || !pnli_dev) return fail(EGN_E_INVALID_ARG, "eta_dev and pnli_dev must be device arrays of n_ch doubles");
+  if (l->rule != RULE_GL) return fail(EGN_E_UNSUPPORTED, "the static scratch path evaluates the Gauss-Legendre rule only");
   DeviceGuard guard(l->device);
   void* base = nullptr;
   s = static_scratch(l->device, &base);

@@ -120,3 +120,76 @@ extern "C" egn_status egn_autotune(egn_link* l, const egn_opts* opts, double tar
   out->ms = ms;
   return EGN_OK;
 }
+
+// Choice of the node rule and its order (the quadrature error of Eq. 17-21's
+// island integrals).  The ridge-resolving rule (FP64) is evaluated at 4, 8, 16,
+// ... nodes per piece, doubling until the worst channel moves by less than a
+// quarter of the target between two orders or max_nodes is reached; the last
+// order stands for the converged value.  The smallest order within target_db
+// of it is chosen and set on the link (egn_set_node_rule); the configured
+// Gauss-Legendre rule of opts->gl_order is scored against the same value.
+extern "C" egn_status egn_autotune_rule(egn_link* l, const egn_opts* opts, double target_db, int max_nodes,
+                                        egn_rule_result* out) {
+  if (!l || !opts || !out) return fail(EGN_E_INVALID_ARG, "null argument");
+  if (!(target_db > 0.0) || !std::isfinite(target_db)) return fail(EGN_E_INVALID_ARG, "target_db must be positive");
+  if (max_nodes < 4 || max_nodes > egn::kRidgeMaxN)
+    return fail(EGN_E_INVALID_ARG, "max_nodes %d not in [4, %d]", max_nodes, egn::kRidgeMaxN);
+  const int n = l->n_ch;
+  if (n <= 0) return fail(EGN_E_STATE, "egn_set_wdm has not been called");
+  const int rule0 = l->rule, nmin0 = l->ridge_n_min;
+  egn_opts o = *opts;
+  o.stream = nullptr;
+  o.precision = EGN_PREC_FP64;
+  // the configured rule first
+  std::vector<double> gl(n);
+  l->rule = egn::RULE_GL;
+  egn_status s = egn_nli_eta(l, &o, gl.data(), nullptr);
+  if (s != EGN_OK) {
+    l->rule = rule0;
+    return s;
+  }
+  l->rule = egn::RULE_RIDGE;
+  l->ridge_n_min = 4;
+  std::vector<std::vector<double>> eta;
+  std::vector<int> order;
+  double change = -1.0;
+  for (int q = 4; q <= max_nodes; q *= 2) {
+    o.gl_order = q;
+    std::vector<double> e(n);
+    s = egn_nli_eta(l, &o, e.data(), nullptr);
+    if (s != EGN_OK) {
+      l->rule = rule0;
+      l->ridge_n_min = nmin0;
+      return s;
+    }
+    eta.push_back(e);
+    order.push_back(q);
+    if (eta.size() >= 2) {
+      change = max_db(eta[eta.size() - 1], eta[eta.size() - 2]);
+      if (change < 0.25 * target_db) break;
+    }
+  }
+  const std::vector<double>& ref = eta.back();
+  size_t pick = eta.size() - 1;
+  for (size_t i = 0; i < eta.size(); ++i)
+    if (max_db(eta[i], ref) <= target_db) {
+      pick = i;
+      break;
+    }
+  o.gl_order = order[pick];
+  double ms = 0.0;
+  s = time_eval(l, o, 3, &ms);
+  if (s != EGN_OK) {
+    l->rule = rule0;
+    l->ridge_n_min = nmin0;
+    return s;
+  }
+  out->rule = EGN_RULE_RIDGE;
+  out->nodes = order[pick];
+  out->max_err_db = max_db(eta[pick], ref);
+  out->last_change_db = change;
+  out->reference_nodes = order.back();
+  out->configured_err_db = max_db(gl, ref);
+  out->ms = ms;
+  return EGN_OK;
+}

@@ -135,7 +135,11 @@ struct egn_link {
   egn_host::DevBuf d_seg, d_gl;
   egn::SegmentTables seg{};
   egn::GlTables gl{};
+  const double* gl_all_x = nullptr;  // every order 1..n (the ridge rule's pieces), inside d_gl
+  const double* gl_all_w = nullptr;
   int fp32c_kp = 4;  // tuning: points per thread of the FP32C D/G/H pass
+  int rule = egn::RULE_GL;  // node rule (egn_set_node_rule)
+  int ridge_n_min = 4;
   // optional per-stage device timing of the last evaluation
   bool prof_on = false;
   bool prof_valid = false;

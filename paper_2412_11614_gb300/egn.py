@@ -22,6 +22,7 @@ EGN_PREC_FP64, EGN_PREC_FP32C = 0, 1
 EGN_TERMS_GN, EGN_TERMS_EGN = 0, 1
 EGN_FMT = {"GAUSS": 0, "QPSK": 1, "16QAM": 2, "64QAM": 3}
 EGN_TUNE_FP32C_POINTS_PER_THREAD = 1
+EGN_RULE_GL, EGN_RULE_RIDGE = 0, 1
 STATUS_NAMES = {0: "EGN_OK", 1: "EGN_E_INVALID_ARG", 2: "EGN_E_UNSUPPORTED", 3: "EGN_E_NOMEM", 4: "EGN_E_CUDA",
                 5: "EGN_E_TIMEOUT", 6: "EGN_E_STATE", 7: "EGN_E_CAPACITY"}
 
@@ -40,6 +41,11 @@ class egn_span(C.Structure):
 
 class egn_tune_result(C.Structure):
     _fields_ = [("dz_km", C.c_double), ("points_per_thread", C.c_int), ("max_err_db", C.c_double), ("ms", C.c_double)]
+
+
+class egn_rule_result(C.Structure):
+    _fields_ = [("rule", C.c_int), ("nodes", C.c_int), ("max_err_db", C.c_double), ("reference_nodes", C.c_int),
+                ("last_change_db", C.c_double), ("configured_err_db", C.c_double), ("ms", C.c_double)]
 
 
 class egn_opts(C.Structure):
@@ -82,6 +88,9 @@ def lib():
         L.egn_gauss_legendre.argtypes = [C.c_int, _dp, _dp]
         L.egn_set_profiling.argtypes = [C.c_void_p, C.c_int]
         L.egn_set_tuning.argtypes = [C.c_void_p, C.c_int, C.c_int]
+        L.egn_set_node_rule.argtypes = [C.c_void_p, C.c_int, C.c_int]
+        L.egn_autotune_rule.argtypes = [C.c_void_p, C.POINTER(egn_opts), C.c_double, C.c_int,
+                                        C.POINTER(egn_rule_result)]
         L.egn_last_timings.argtypes = [C.c_void_p, _dp, C.c_int, C.POINTER(C.c_int)]
         L.egn_batch_create.argtypes = [C.POINTER(C.c_void_p), C.c_int, C.POINTER(egn_opts), C.POINTER(C.c_void_p)]
         L.egn_batch_launch.argtypes = [C.c_void_p, C.c_void_p]
@@ -104,7 +113,7 @@ def lib():
                    "egn_gauss_legendre", "egn_set_profiling", "egn_last_timings", "egn_nli_eta_static", "egn_set_tuning",
                    "egn_batch_create", "egn_batch_launch", "egn_batch_outputs", "egn_batch_read", "egn_nli_eta_batch",
                    "egn_autotune", "egn_nli_eta_3d", "egn_probe_launch", "egn_probe_ops",
-                   "egn_allocation_count"):
+                   "egn_allocation_count", "egn_set_node_rule", "egn_autotune_rule"):
             getattr(L, fn).restype = C.c_int
         _lib = L
     return _lib
@@ -258,8 +267,19 @@ class Link:
                                   float(dz_ref_km), C.byref(r)))
         return {"dz_km": r.dz_km, "points_per_thread": r.points_per_thread, "max_err_db": r.max_err_db, "ms": r.ms}
 
+    def autotune_rule(self, opts: egn_opts, target_db: float, max_nodes: int = 64) -> dict:
+        """egn_autotune_rule: the ridge rule's order within target_db of its converged
+        value (set on the link), and the configured rule's error against it."""
+        r = egn_rule_result()
+        _check(lib().egn_autotune_rule(self.h, C.byref(opts), float(target_db), int(max_nodes), C.byref(r)))
+        return {f: getattr(r, f) for f, _ in egn_rule_result._fields_}
+
     def set_tuning(self, param: int, value: int):
         _check(lib().egn_set_tuning(self.h, int(param), int(value)))
+
+    def set_node_rule(self, rule: int, n_min: int = 4):
+        """egn_set_node_rule: EGN_RULE_GL (default) or EGN_RULE_RIDGE (FP64)."""
+        _check(lib().egn_set_node_rule(self.h, int(rule), int(n_min)))
 
     def set_profiling(self, on: bool):
         _check(lib().egn_set_profiling(self.h, int(bool(on))))

@@ -1,0 +1,132 @@
+"""The ridge-resolving node rule on the GPU (egn_set_node_rule(EGN_RULE_RIDGE),
+FP64 path) against the oracle's ridge rule (oracle/ridge_rule.py) at the same
+node counts, through the C ABI.
+
+The two sides share no code: the oracle's rule is numpy around the oracle's C
+integrand; the kernel forms the same cuts, pieces and sinh-graded nodes on the
+device.  Bars: every term of every island within 1e-9 of the oracle's (relative
+to the largest term of its kind in the COI), eta within 1e-9 relative (the GPU
+evaluates the half list and counts each mirror island twice; the oracle sums
+every island; the two differ by rounding).  The rule converges where the
+configured one does not: on the 5-channel link 16 and 32 nodes per piece agree
+within 0.003 dB for the GN part and 0.04 dB with the EGN corrections, where the
+configured rule moves by more than 0.3 dB from 32 x 32 to 64 x 64 (the narrow
+ridges of |mu|^2)."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def egn():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA device required for -m gpu tests")
+    from paper_2412_11614_gb300 import _build
+    _build.build()
+    from paper_2412_11614_gb300 import egn as E
+    E.lib()
+    return E
+
+
+@pytest.fixture(scope="module")
+def RR():
+    from oracle import ridge_rule
+    return ridge_rule
+
+
+def _ridge_link(egn, wl, n_min=4):
+    ln = egn.link_from_workload(wl)
+    ln.set_node_rule(egn.EGN_RULE_RIDGE, n_min)
+    return ln
+
+
+@pytest.mark.parametrize("order", [8, 16])
+def test_ridge_island_terms_match_oracle(egn, oracle_mod, workloads, RR, order):
+    """All five terms of every island of the edge and centre COIs of the 5-channel
+    link (SCI, XCI with the ridges inside, MCI)."""
+    wl = workloads.config_small(gl_order=order)
+    ln = _ridge_link(egn, wl)
+    pb = oracle_mod.Problem(wl, gl_order=order)
+    rule = RR.RidgeRule(pb)
+    opts = egn.make_opts(gl_order=order, precision=egn.EGN_PREC_FP64)
+    for n in (0, 2):
+        isl = [(n, int(a), int(b), int(c)) for a, b, c in pb.islands(n)]
+        got = ln.island_terms(opts, isl, all_terms=True)
+        want = np.array([rule.terms(*t, order) for t in isl])
+        scale = np.max(np.abs(want), axis=0) + 1e-300
+        assert np.all(np.abs(got - want) <= 1e-9 * scale), (n, np.max(np.abs(got - want) / scale, axis=0))
+    ln.close()
+
+
+@pytest.mark.parametrize("case", ["5ch", "8ch_3spans"])
+def test_ridge_eta_matches_oracle(egn, oracle_mod, workloads, RR, case):
+    if case == "5ch":
+        wl, order = workloads.config_small(gl_order=16), 16
+    else:
+        wl, order = workloads.config_small(n_ch=8, gl_order=8, n_spans=3), 8
+        wl.formats = ["QPSK", "16QAM", "64QAM", "GAUSS"] * 2
+    ln = _ridge_link(egn, wl)
+    eta, pnli = ln.nli_eta(egn.make_opts(gl_order=order, precision=egn.EGN_PREC_FP64))
+    pb = oracle_mod.Problem(wl, gl_order=order)
+    rule = RR.RidgeRule(pb)
+    want = np.array([rule.pnli(n, order) for n in range(wl.n_ch)])
+    assert np.allclose(pnli, want, rtol=1e-9, atol=0), (pnli, want)
+    assert np.allclose(eta, want / np.asarray(wl.launch_power_w) ** 3, rtol=1e-9, atol=0)
+    ln.close()
+
+
+def test_ridge_rule_converges_where_the_configured_rule_does_not(egn, workloads):
+    """GN part: 16 and 32 nodes per piece within 0.003 dB; with the EGN corrections
+    (which need more nodes) within 0.04 dB; the configured rule moves by more than
+    0.3 dB from 32 x 32 to 64 x 64."""
+    wl = workloads.config_small(gl_order=16)
+    ln = egn.link_from_workload(wl)
+    o = lambda n, t: egn.make_opts(gl_order=n, precision=egn.EGN_PREC_FP64, terms=t)  # noqa: E731
+    plain32, _ = ln.nli_eta(o(32, egn.EGN_TERMS_EGN))
+    plain64, _ = ln.nli_eta(o(64, egn.EGN_TERMS_EGN))
+    ln.set_node_rule(egn.EGN_RULE_RIDGE, 4)
+    db = lambda a, b: np.abs(10 * np.log10(a / b))  # noqa: E731
+    for terms, bar in ((egn.EGN_TERMS_GN, 3e-3), (egn.EGN_TERMS_EGN, 0.04)):
+        r16, _ = ln.nli_eta(o(16, terms))
+        r32, _ = ln.nli_eta(o(32, terms))
+        assert np.max(db(r16, r32)) < bar, (terms, db(r16, r32))
+    assert np.max(db(plain32, plain64)) > 0.3, db(plain32, plain64)
+    ln.set_node_rule(egn.EGN_RULE_GL)  # back to the configured rule: the same results as before
+    again, _ = ln.nli_eta(o(32, egn.EGN_TERMS_EGN))
+    assert np.array_equal(again, plain32)
+    ln.close()
+
+
+def test_ridge_rule_in_a_batch_equals_single_links(egn, workloads):
+    opts = egn.make_opts(gl_order=8, precision=egn.EGN_PREC_FP64)
+    wls = [workloads.config_small(n_ch=4, gl_order=8), workloads.config_small(n_ch=3, gl_order=8, n_spans=2)]
+    links = [_ridge_link(egn, w) for w in wls]
+    want = [ln.nli_eta(opts) for ln in links]
+    b = egn.Batch(links, opts)
+    b.launch()
+    for (ge, gp), (we, wp) in zip(b.read(), want):
+        assert np.array_equal(ge, we) and np.array_equal(gp, wp)
+    b.close()
+
+
+def test_ridge_rule_refusals(egn, workloads):
+    import torch
+    wl = workloads.config_small(n_ch=2, gl_order=8)
+    ln = _ridge_link(egn, wl)
+    with pytest.raises(egn.EgnError) as ei:
+        ln.nli_eta(egn.make_opts(gl_order=8, precision=egn.EGN_PREC_FP32C))
+    assert ei.value.status == egn.EGN_E_UNSUPPORTED
+    with pytest.raises(egn.EgnError) as ei:
+        ln.nli_eta(egn.make_opts(gl_order=65, precision=egn.EGN_PREC_FP64))
+    assert ei.value.status == egn.EGN_E_INVALID_ARG
+    eta = torch.empty(2, dtype=torch.float64, device="cuda")
+    with pytest.raises(egn.EgnError) as ei:
+        ln.nli_eta_static(egn.make_opts(gl_order=8, precision=egn.EGN_PREC_FP64), eta, eta)
+    assert ei.value.status == egn.EGN_E_UNSUPPORTED
+    for rule, n_min in ((7, 4), (egn.EGN_RULE_RIDGE, 0)):
+        with pytest.raises(egn.EgnError) as ei:
+            ln.set_node_rule(rule, n_min)
+        assert ei.value.status == egn.EGN_E_INVALID_ARG
+    ln.close()
