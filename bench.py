@@ -745,7 +745,7 @@ def main():
                     help="measure the FP32, FP32x2, FP64 and MUFU pipe peaks with the probe kernels")
     ap.add_argument("--e2e-steps", type=int, default=None)
     ap.add_argument("--n-ch", type=int, default=120, help="channels of the C+L grid (120 = the benchmark)")
-    ap.add_argument("--points-per-thread", type=int, default=4, choices=[4, 8],
+    ap.add_argument("--points-per-thread", type=int, default=4, choices=[2, 4, 8],
                     help="launch-shape tuning of the FP32C D/G/H pass")
     ap.add_argument("--mu-compare", action="store_true",
                     help="time and compare the integral, segment and Maclaurin forms of mu (Table I links)")

@@ -283,7 +283,8 @@ egn_status egn_plan_islands(egn_link* link, long long max, int* coi_n1_n2_n3, lo
 
 /* Tuning of the kernels' launch shape (results do not change beyond rounding).
  *   EGN_TUNE_FP32C_POINTS_PER_THREAD: quadrature points per thread in the FP32C
- *   D/G/H pass, 4 (default) or 8. */
+ *   D/G/H pass, 4 (default: 64-thread CTAs, 10 per SM), 8 (128-thread CTAs, 3
+ *   per SM) or 2 (128-thread CTAs, 8 per SM). */
 enum { EGN_TUNE_FP32C_POINTS_PER_THREAD = 1 };
 egn_status egn_set_tuning(egn_link* link, int param, int value);
 

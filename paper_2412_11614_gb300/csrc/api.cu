@@ -802,7 +802,7 @@ egn_status egn_set_tuning(egn_link* l, int param, int value) {
   if (!l) return fail(EGN_E_INVALID_ARG, "null link");
   switch (param) {
     case EGN_TUNE_FP32C_POINTS_PER_THREAD:
-      if (value != 4 && value != 8) return fail(EGN_E_INVALID_ARG, "points per thread must be 4 or 8");
+      if (value != 2 && value != 4 && value != 8) return fail(EGN_E_INVALID_ARG, "points per thread must be 2, 4 or 8");
       l->fp32c_kp = value;
       return EGN_OK;
     default:

@@ -305,12 +305,12 @@ __device__ __forceinline__ void dw_recurrence(const float* __restrict__ trow, in
 // CTA, min_ctas resident CTAs per SM (the register budget follows from it) and
 // rows_max rows of constants per chunk.
 __host__ __device__ constexpr int min_ctas(int ord, int kp, int nt) {
-  return nt == 64 ? (ord == ORD_DW ? kDwCtas : kEfCtas) : (kp == 8 ? 3 : (ord == ORD_DW ? 5 : 4));
+  return nt == 64 ? (ord == ORD_DW ? kDwCtas : kEfCtas) : (kp == 8 ? 3 : (kp == 2 ? 8 : (ord == ORD_DW ? 5 : 4)));
 }
 // Islands per batch (FP64 set-up, one island per thread): fewer than NT keeps the
 // batch arrays small enough for kDwCtas CTAs per SM.
-__host__ __device__ constexpr int batch_of(int ord, int nt) {
-  return nt == 64 ? (ord == ORD_DW ? kDwBatch : kEfBatch) : nt;
+__host__ __device__ constexpr int batch_of(int ord, int kp, int nt) {
+  return nt == 64 ? (ord == ORD_DW ? kDwBatch : kEfBatch) : (kp == 2 ? kDwBatch : nt);
 }
 __host__ __device__ constexpr int rows_max(int nt) { return nt == 64 ? 32 : kRowsMax; }
 // Floats of the inner-node arrays at the head of the main kernel's dynamic shared
@@ -337,7 +337,7 @@ __device__ __forceinline__ float warp_sum(const float* r) {
 // Shared state of the identical-spans passes (one CTA).
 template <int ORD, int KP, int NT>
 struct DwShared {
-  BatchSmT<batch_of(ORD, NT)> bs;
+  BatchSmT<batch_of(ORD, KP, NT)> bs;
   RowSm<rows_max(NT)> rsb[2];  // the current island's rows and the next one's
   float red[4][NT / 32];
   // the rows the c_k table holds (DW): their f3 in FP32 and their number (-1: none)
@@ -399,7 +399,7 @@ __device__ __forceinline__ void dw_batch(const LinkParams& p, const DwConsts& cs
                                          const float4* __restrict__ nx4, const float2* __restrict__ nx2,
                                          float* __restrict__ tab, int& cur, bool& have_rows) {
   constexpr int NPAIR = KP / 2;
-  constexpr int NB = batch_of(ORD, NT);
+  constexpr int NB = batch_of(ORD, KP, NT);
   constexpr int NW = NT / 32;
   auto& bs = sh.bs;
   auto& rsb = sh.rsb;
@@ -738,7 +738,7 @@ integrate_fp32c_kernel(LinkParams p, const uint64_t* __restrict__ keys, const ui
                        long long n_items, float* __restrict__ terms, long long n_isl, int rows_per_chunk, int kpad,
                        Df G0, Df G1) {
   static_assert(KP % 2 == 0, "points per thread come in f32x2 pairs");
-  constexpr int NB = batch_of(ORD, NT);
+  constexpr int NB = batch_of(ORD, KP, NT);
   __shared__ DwShared<ORD, KP, NT> sh;
   if (threadIdx.x == 0) sh.tab_rows = -1;  // read after the first batch barrier
   const int npad = threads_per_row(p.gl.n, KP) * KP;
@@ -783,7 +783,7 @@ cudaError_t launch_one(const LinkParams& p, const uint64_t* keys, const uint32_t
     if (e != cudaSuccess) return e;
     attr_done |= 1ull << (dev & 63);
   }
-  long long batches = (n_items + batch_of(ORD, NT) - 1) / batch_of(ORD, NT);
+  long long batches = (n_items + batch_of(ORD, KP, NT) - 1) / batch_of(ORD, KP, NT);
   long long blocks = (long long)sms * min_ctas(ORD, KP, NT);
   if (blocks > batches) blocks = batches;
   // 2 pi L beta2 and 2 pi^2 L beta3 as double-floats
@@ -1589,7 +1589,7 @@ __device__ __forceinline__ int find_job(const LinkJob* __restrict__ jobs, int n_
 template <int ORD>
 __global__ void __launch_bounds__(kDwThreads, min_ctas(ORD, 4, kDwThreads))
 integrate_fp32c_multi_kernel(const LinkJob* __restrict__ jobs, int n_jobs, long long batches) {
-  constexpr int KP = 4, NT = kDwThreads, NB = batch_of(ORD, NT);
+  constexpr int KP = 4, NT = kDwThreads, NB = batch_of(ORD, KP, NT);
   __shared__ DwShared<ORD, KP, NT> sh;
   const int npad = threads_per_row(jobs[0].p.gl.n, KP) * KP;  // every link of a batch has the same order
   extern __shared__ __align__(16) float dyn[];
@@ -1679,7 +1679,7 @@ JobShape job_shape(int ord, int family, const LinkParams& p, long long n_items) 
     const float g0h = (float)g0, g1h = (float)g1;
     s.G0 = {g0h, (float)(g0 - (double)g0h)};
     s.G1 = {g1h, (float)(g1 - (double)g1h)};
-    s.batches = (n_items + batch_of(ord, kDwThreads) - 1) / batch_of(ord, kDwThreads);
+    s.batches = (n_items + batch_of(ord, 4, kDwThreads) - 1) / batch_of(ord, 4, kDwThreads);
   } else if (family == 1) {
     int ktot = 0;
     for (int t = 0; t < p.n_types; ++t) {
@@ -1769,6 +1769,7 @@ cudaError_t launch_fp32c_pass(int ord, const LinkParams& p, const uint64_t* keys
   }
   if (ord == ORD_DW) {
     if (p.fp32c_kp == 8) return launch_one<ORD_DW, 8, 128>(p, keys, list, n_items, terms, n_isl, st);
+    if (p.fp32c_kp == 2) return launch_one<ORD_DW, 2, 128>(p, keys, list, n_items, terms, n_isl, st);
     return launch_one<ORD_DW, 4, kDwThreads>(p, keys, list, n_items, terms, n_isl, st);
   }
   if (ord == ORD_E) return launch_one<ORD_E, 4, kDwThreads>(p, keys, list, n_items, terms, n_isl, st);

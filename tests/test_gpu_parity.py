@@ -450,13 +450,14 @@ def test_config3_power_sweep(egn, oracle_mod, workloads, p_dbm):
 
 
 def test_fp32c_launch_shapes_agree(egn, oracle_mod, workloads):
-    """4 and 8 points per thread in the FP32C D/G/H pass: same terms up to rounding."""
+    """2, 4 and 8 points per thread in the FP32C D/G/H pass: same terms up to rounding."""
     wl = workloads.config_small(n_ch=5, gl_order=32, n_spans=3)
     ln, pb = _pair(egn, oracle_mod, wl)
     o = egn.make_opts(gl_order=32, precision=egn.EGN_PREC_FP32C)
     a, _ = ln.nli_eta(o)
-    ln.set_tuning(egn.EGN_TUNE_FP32C_POINTS_PER_THREAD, 8)
-    b, _ = ln.nli_eta(o)
     want, _ = pb.eta()
-    assert np.max(_db(a, b)) < 1e-4
-    assert np.max(_db(b, want)) < FP32C_DB
+    for kp in (8, 2):
+        ln.set_tuning(egn.EGN_TUNE_FP32C_POINTS_PER_THREAD, kp)
+        b, _ = ln.nli_eta(o)
+        assert np.max(_db(a, b)) < 1e-4, kp
+        assert np.max(_db(b, want)) < FP32C_DB, kp
