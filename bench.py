@@ -485,8 +485,12 @@ def run_batch_compare(args):
         return t0.elapsed_time(t1) / reps
 
     reps = 2 if args.batch_random else args.steps
+    smi = ClockSampler(gpu_id_for_smi(0))
+    smi.start()
+    time.sleep(0.3)
     seq_ms = timed(one_by_one, reps)
     graph_ms = timed(lambda: b.launch(stream.cuda_stream), reps)
+    clocks = smi.stop()
     got = b.read(stream.cuda_stream)
     same = all(np.array_equal(g[0], o[0].cpu().numpy()) for g, o in zip(got, outs))
     n_ch = int(b.offsets[-1])
@@ -494,7 +498,8 @@ def run_batch_compare(args):
                       "span_types": [len({(s.length_m, s.alpha_db_km, s.D_ps_nm_km) for s in w.spans}) for w in wls],
                       "workload": desc,
                       "ms_one_by_one": seq_ms, "ms_graph": graph_ms, "speedup": seq_ms / graph_ms,
-                      "channel_evals_per_s_graph": n_ch / (graph_ms * 1e-3), "results_identical": same}), flush=True)
+                      "channel_evals_per_s_graph": n_ch / (graph_ms * 1e-3), "results_identical": same,
+                      "clocks": clocks}), flush=True)
     b.close()
     return 0
 

@@ -2,6 +2,7 @@
 // kernels of the GB300 ISRS EGN integrator (not part of the C ABI).
 #pragma once
 
+#include <atomic>
 #include <cmath>
 #include <cstddef>
 #include <cstdint>
@@ -273,6 +274,22 @@ __host__ __device__ inline void gl_node(int n, int k, double* xk_out, double* wk
 
 // Host Gauss-Legendre nodes on [-1, 1], ascending.
 void gauss_legendre(int n, double* x, double* w);
+
+// Opt a kernel in to `bytes` of dynamic shared memory on the current device,
+// once per device: `done` holds one bit per device (ordinal mod 64), set
+// atomically after the attribute is set; concurrent first calls both set it,
+// which is harmless.
+template <class F>
+inline cudaError_t opt_in_smem(F* fn, int bytes, std::atomic<unsigned long long>& done) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  const unsigned long long bit = 1ull << (dev & 63);
+  if (done.load(std::memory_order_acquire) & bit) return cudaSuccess;
+  e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e == cudaSuccess) done.fetch_or(bit, std::memory_order_release);
+  return e;
+}
 
 // Entry k of a span type's segment tables (Eq. 8-10 with the ISRS profile of
 // Eq. 14/25): z_k = (k + 1/2) L / K, zeta_k = P_tot Cr L_eff(z_k) with

@@ -776,13 +776,10 @@ cudaError_t launch_one(const LinkParams& p, const uint64_t* keys, const uint32_t
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   // static shared memory + the c_k table exceed the 48 KB default: opt in once per device
-  static unsigned long long attr_done = 0;
-  if (!(attr_done >> (dev & 63) & 1ull)) {
-    cudaError_t e = cudaFuncSetAttribute(integrate_fp32c_kernel<ORD, KP, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (node_floats(2 * kMaxGl) + kTabFloats) * (int)sizeof(float));
-    if (e != cudaSuccess) return e;
-    attr_done |= 1ull << (dev & 63);
-  }
+  static std::atomic<unsigned long long> attr_done{0};
+  if (cudaError_t e = opt_in_smem(integrate_fp32c_kernel<ORD, KP, NT>,
+                                  (node_floats(2 * kMaxGl) + kTabFloats) * (int)sizeof(float), attr_done))
+    return e;
   long long batches = (n_items + batch_of(ORD, KP, NT) - 1) / batch_of(ORD, KP, NT);
   long long blocks = (long long)sms * min_ctas(ORD, KP, NT);
   if (blocks > batches) blocks = batches;
@@ -1166,13 +1163,9 @@ cudaError_t launch_general(const LinkParams& p, const uint64_t* keys, const uint
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  static unsigned long long attr_done = 0;
-  if (!(attr_done >> (dev & 63) & 1ull)) {
-    cudaError_t e = cudaFuncSetAttribute(integrate_fp32c_general_kernel<ORD>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, kGTab * (int)sizeof(float));
-    if (e != cudaSuccess) return e;
-    attr_done |= 1ull << (dev & 63);
-  }
+  static std::atomic<unsigned long long> attr_done{0};
+  if (cudaError_t e = opt_in_smem(integrate_fp32c_general_kernel<ORD>, kGTab * (int)sizeof(float), attr_done))
+    return e;
   long long batches = (n_items + kBatch - 1) / kBatch;
   long long blocks = (long long)sms * 3;
   if (blocks > batches) blocks = batches;
@@ -1535,13 +1528,8 @@ cudaError_t launch_spans(const LinkParams& p, const uint64_t* keys, const uint32
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  static unsigned long long attr_done = 0;
-  if (!(attr_done >> (dev & 63) & 1ull)) {
-    cudaError_t e = cudaFuncSetAttribute(integrate_fp32c_spans_kernel<ORD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         kSpansDynBytes);
-    if (e != cudaSuccess) return e;
-    attr_done |= 1ull << (dev & 63);
-  }
+  static std::atomic<unsigned long long> attr_done{0};
+  if (cudaError_t e = opt_in_smem(integrate_fp32c_spans_kernel<ORD>, kSpansDynBytes, attr_done)) return e;
   long long batches = (n_items + kBatch - 1) / kBatch;
   long long blocks = (long long)sms * 2;
   if (blocks > batches) blocks = batches;
@@ -1712,17 +1700,6 @@ JobShape job_shape(int ord, int family, const LinkParams& p, long long n_items) 
   return s;
 }
 
-template <class F>
-cudaError_t set_smem_once(F* fn, int bytes, unsigned long long& done) {
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return e;
-  if (done >> (dev & 63) & 1ull) return cudaSuccess;
-  e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-  if (e == cudaSuccess) done |= 1ull << (dev & 63);
-  return e;
-}
-
 template <int ORD>
 cudaError_t launch_multi_ord(const MultiLaunch& m, const void* d_jobs, cudaStream_t st) {
   int dev = 0, sms = 0;
@@ -1731,21 +1708,21 @@ cudaError_t launch_multi_ord(const MultiLaunch& m, const void* d_jobs, cudaStrea
   if (e != cudaSuccess) return e;
   const LinkJob* jobs = (const LinkJob*)d_jobs;
   if (m.family == 0) {
-    static unsigned long long done = 0;
-    e = set_smem_once(integrate_fp32c_multi_kernel<ORD>, (node_floats(2 * kMaxGl) + kTabFloats) * (int)sizeof(float),
-                      done);
+    static std::atomic<unsigned long long> done{0};
+    e = opt_in_smem(integrate_fp32c_multi_kernel<ORD>, (node_floats(2 * kMaxGl) + kTabFloats) * (int)sizeof(float),
+                    done);
     if (e != cudaSuccess) return e;
     const long long blocks = std::min<long long>((long long)sms * min_ctas(ORD, 4, kDwThreads), m.batches);
     integrate_fp32c_multi_kernel<ORD><<<(unsigned)blocks, kDwThreads, m.smem, st>>>(jobs, m.n_jobs, m.batches);
   } else if (m.family == 1) {
-    static unsigned long long done = 0;
-    e = set_smem_once(integrate_fp32c_general_multi_kernel<ORD>, kGTab * (int)sizeof(float), done);
+    static std::atomic<unsigned long long> done{0};
+    e = opt_in_smem(integrate_fp32c_general_multi_kernel<ORD>, kGTab * (int)sizeof(float), done);
     if (e != cudaSuccess) return e;
     const long long blocks = std::min<long long>((long long)sms * 3, m.batches);
     integrate_fp32c_general_multi_kernel<ORD><<<(unsigned)blocks, kThreads, m.smem, st>>>(jobs, m.n_jobs, m.batches);
   } else {
-    static unsigned long long done = 0;
-    e = set_smem_once(integrate_fp32c_spans_multi_kernel<ORD>, kSpansDynBytes, done);
+    static std::atomic<unsigned long long> done{0};
+    e = opt_in_smem(integrate_fp32c_spans_multi_kernel<ORD>, kSpansDynBytes, done);
     if (e != cudaSuccess) return e;
     const long long blocks = std::min<long long>((long long)sms * 2, m.batches);
     integrate_fp32c_spans_multi_kernel<ORD><<<(unsigned)blocks, kThreads, m.smem, st>>>(jobs, m.n_jobs, m.batches);

@@ -642,13 +642,9 @@ cudaError_t launch_ridge(const LinkParams& p, const uint64_t* keys, const uint32
   if (p.mu_form == MU_SEGMENT && p.n_types <= kMaxTypes)
     for (int t = 0; t < p.n_types; ++t) ksum += p.n_types == 1 ? p.seg.K : p.types[t].seg.K;
   const size_t smem = (ORD == ORD_DW) ? (size_t)ksum * 32 * sizeof(double) : 0;
-  static bool attr_set[3] = {false, false, false};
-  if (smem > 40 * 1024 && !attr_set[ORD]) {
-    cudaError_t e = cudaFuncSetAttribute(integrate_ridge_kernel<ORD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)(kMaxK * 32 * sizeof(double)));
-    if (e != cudaSuccess) return e;
-    attr_set[ORD] = true;
-  }
+  static std::atomic<unsigned long long> attr_done{0};  // per device
+  if (smem > 40 * 1024)
+    if (cudaError_t e = opt_in_smem(integrate_ridge_kernel<ORD>, (int)(kMaxK * 32 * sizeof(double)), attr_done)) return e;
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -669,13 +665,9 @@ cudaError_t launch_one(const LinkParams& p, const uint64_t* keys, const uint32_t
       for (int t = 0; t < p.n_types; ++t) ksum += p.types[t].seg.K;
   }
   size_t smem = (ORD == ORD_DW) ? (size_t)ksum * 32 * sizeof(double) : 0;
-  static bool attr_set[3] = {false, false, false};
-  if (smem > 48 * 1024 && !attr_set[ORD]) {
-    cudaError_t e = cudaFuncSetAttribute(integrate_fp64_kernel<ORD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)(kMaxK * 32 * sizeof(double)));
-    if (e != cudaSuccess) return e;
-    attr_set[ORD] = true;
-  }
+  static std::atomic<unsigned long long> attr_done{0};  // per device
+  if (smem > 48 * 1024)
+    if (cudaError_t e = opt_in_smem(integrate_fp64_kernel<ORD>, (int)(kMaxK * 32 * sizeof(double)), attr_done)) return e;
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);

@@ -352,11 +352,8 @@ egn_status make_map(CUtensorMap* m, const void* base, uint64_t rows, uint64_t co
 template <int EPI>
 egn_status launch(const CUtensorMap& ta, const CUtensorMap& tb, int m, int n, int kb_per, int kb, int splits,
                   const float* bias, const void* aux, void* out, int* err, cudaStream_t st) {
-  static bool attr = false;
-  if (!attr) {
-    EGN_CUDA(cudaFuncSetAttribute(gemm_bf16_kernel<EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem));
-    attr = true;
-  }
+  static std::atomic<unsigned long long> attr_done{0};  // per device
+  EGN_CUDA(egn::opt_in_smem(gemm_bf16_kernel<EPI>, kSmem, attr_done));
   int dev = 0, sms = 0;
   EGN_CUDA(cudaGetDevice(&dev));
   EGN_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));

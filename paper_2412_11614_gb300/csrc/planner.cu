@@ -327,15 +327,9 @@ cudaError_t launch_plan(const ChannelTable& ch, const Workspace& ws, cudaStream_
   if (e != cudaSuccess || ws.cap_half <= 0) return e;
   const int ng = 4 * ch.n_ch;
   const size_t hist_b = (size_t)ng * sizeof(uint32_t);  // <= 64 KB (n_ch <= 4096)
-  int dev = 0;
-  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
-  static unsigned long long attr_done = 0;  // opt in to more than 48 KB once per device
-  if (!(attr_done >> (dev & 63) & 1ull)) {
-    for (const void* k : {(const void*)group_count_kernel, (const void*)group_scatter_kernel})
-      if ((e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, 16384 * 4)) != cudaSuccess)
-        return e;
-    attr_done |= 1ull << (dev & 63);
-  }
+  static std::atomic<unsigned long long> count_done{0}, scatter_done{0};  // opt in to more than 48 KB once per device
+  if ((e = opt_in_smem(group_count_kernel, 16384 * 4, count_done)) != cudaSuccess) return e;
+  if ((e = opt_in_smem(group_scatter_kernel, 16384 * 4, scatter_done)) != cudaSuccess) return e;
   group_count_kernel<<<kGroupBlocks, 256, hist_b, st>>>(ws.keys, ws.h_idx, ws.cap_half, ng, ws.grp_cnt);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   // tile offsets inside each group (in place), group totals, group offsets

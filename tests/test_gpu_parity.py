@@ -428,6 +428,36 @@ def test_config_cl_full_size_sampled_channels(egn, oracle_mod, workloads):
     assert np.max(_db(e32[cois], want)) < TARGET_DB
 
 
+def test_config_cl_thirty_spans(egn, workloads):
+    """The 120-channel C+L link over 30 identical spans (the longest links of the
+    batch workload): N phi / 2 of the phased array is largest here, so the FP32
+    small-angle series near its poles and the double-float phase are most exposed.
+    FP32C against FP64 on every channel within 0.01 dB."""
+    wl = workloads.config_cl(n_spans=30)
+    ln = egn.link_from_workload(wl)
+    e64, _ = ln.nli_eta(egn.make_opts(gl_order=32, precision=egn.EGN_PREC_FP64))
+    e32, _ = ln.nli_eta(egn.make_opts(gl_order=32, precision=egn.EGN_PREC_FP32C))
+    assert np.all(np.isfinite(e32)) and np.max(_db(e32, e64)) < TARGET_DB, np.max(_db(e32, e64))
+    ln.close()
+
+
+def test_random_link_full_size(egn, oracle_mod, workloads):
+    """A seeded link of the batch workload at full size: random_link(2), 50
+    channels of 37 GBd on a 116 GHz grid, tilted rippled powers, 29 SSMF/PSCF spans
+    of 26 types (the span-by-span path), 16 x 16 nodes.  FP32C against FP64 on
+    every channel within 0.01 dB; FP64 against the oracle on the centre channel
+    within 1e-8."""
+    wl = workloads.random_link(2)
+    ln, pb = _pair(egn, oracle_mod, wl)
+    e64, _ = ln.nli_eta(egn.make_opts(gl_order=wl.gl_order, precision=egn.EGN_PREC_FP64))
+    e32, _ = ln.nli_eta(egn.make_opts(gl_order=wl.gl_order, precision=egn.EGN_PREC_FP32C))
+    assert np.max(_db(e32, e64)) < TARGET_DB, np.max(_db(e32, e64))
+    coi = [wl.n_ch // 2]
+    want, _ = pb.eta(coi)
+    assert np.allclose(e64[coi], want, rtol=1e-8, atol=0), (e64[coi], want)
+    ln.close()
+
+
 @pytest.mark.parametrize("p_dbm", [-2.0, 4.0])
 def test_config3_power_sweep(egn, oracle_mod, workloads, p_dbm):
     """The benchmark link at the ends of the launch-power sweep, -2 and +4 dBm/ch

@@ -60,13 +60,23 @@ def test_ridge_island_terms_match_oracle(egn, oracle_mod, workloads, RR, order):
     ln.close()
 
 
-@pytest.mark.parametrize("case", ["5ch", "8ch_3spans"])
+@pytest.mark.parametrize("case", ["5ch", "8ch_3spans", "4ch_3types", "3ch_6types"])
 def test_ridge_eta_matches_oracle(egn, oracle_mod, workloads, RR, case):
+    """eta of every channel; the last two cases are links whose spans differ (three
+    span types: per-type c_k tables; six: span by span), where the ridge widths
+    take the first span's fibre and the integrand is Eq. 22's explicit span sum."""
     if case == "5ch":
         wl, order = workloads.config_small(gl_order=16), 16
-    else:
+    elif case == "8ch_3spans":
         wl, order = workloads.config_small(n_ch=8, gl_order=8, n_spans=3), 8
         wl.formats = ["QPSK", "16QAM", "64QAM", "GAUSS"] * 2
+    else:
+        n_ch, n_spans = (4, 3) if case == "4ch_3types" else (3, 6)
+        wl, order = workloads.config_small(n_ch=n_ch, gl_order=8, n_spans=n_spans), 8
+        for i, sp in enumerate(wl.spans):
+            sp.length_m = (60 + 7 * i) * 1e3
+        wl.spans[1].alpha_db_km = 0.16
+        wl.spans[1].D_ps_nm_km = 21.0
     ln = _ridge_link(egn, wl)
     eta, pnli = ln.nli_eta(egn.make_opts(gl_order=order, precision=egn.EGN_PREC_FP64))
     pb = oracle_mod.Problem(wl, gl_order=order)
