@@ -1186,8 +1186,12 @@ constexpr int kSpanTypeFloats = 12;  // per type: G0 (df), G1 (df), K, 1/K, alph
 
 // Shared state of the span-by-span passes (one CTA); the per-type constants, row
 // phases and fibre tables are in dynamic shared memory, laid out by spans_layout.
+constexpr int kSpansBatch = 64;            // islands per batch of the span-by-span passes
+constexpr int kSpansCtas = 4;              // resident CTAs per SM
+constexpr int kSpansDynBytes = 40 * 1024;  // per-type constants, row phases and fibre c_k tables
+
 struct SpansShared {
-  BatchSm bs;
+  BatchSmT<kSpansBatch> bs;
   float4 g_ab[kGRows], g_ow[kGRows], g_f3[kGRows];
   float g_ih[kGRows];
   NodeSm ns;
@@ -1202,13 +1206,19 @@ struct SpansLayout {
   float* tabf;  // DW with fibre groups: c_k of the chunk's rows per fibre, [n_fib][R][kfp]
 };
 
+// Floats of the dynamic layout before the fibre tables: the row phases (40 T R
+// bytes) and the type constants, rounded up to a 16-byte boundary (the fibre
+// rows are read with 16-byte loads; 40 T R + 48 T is a multiple of 16 only when T
+// or R is even).
+__host__ __device__ constexpr int spans_head_floats(int T, int R) { return (10 * T * R + kSpanTypeFloats * T + 3) & ~3; }
+
 __device__ __forceinline__ SpansLayout spans_layout(float* dyn, int T, int R) {
   SpansLayout l;
   l.sqa = reinterpret_cast<float4*>(dyn);
   l.sqb = l.sqa + T * R;
   l.skc = reinterpret_cast<float2*>(l.sqb + T * R);
   l.tyc = reinterpret_cast<float*>(l.skc + T * R);
-  l.tabf = l.tyc + T * kSpanTypeFloats;
+  l.tabf = dyn + spans_head_floats(T, R);
   return l;
 }
 
@@ -1233,7 +1243,7 @@ __device__ __forceinline__ void spans_types(const LinkParams& p, float* tyc) {
   }
 }
 
-// One batch of islands (items b0 .. b0 + kBatch - 1 of `list`) of one link walked span by span.
+// One batch of islands (items b0 .. b0 + kSpansBatch - 1 of `list`) of one link walked span by span.
 template <int ORD>
 __device__ __forceinline__ void spans_batch(const LinkParams& p, const uint64_t* __restrict__ keys,
                                             const uint32_t* __restrict__ list, long long n_items,
@@ -1264,9 +1274,9 @@ __device__ __forceinline__ void spans_batch(const LinkParams& p, const uint64_t*
   const int rows_per_pass = kThreads / tpr;
   const int lr = tid & (tpr - 1);
   const int rsub = tid / tpr;
-    batch_setup<ORD>(p, keys, list, n_items, b0, bs, tid);
+    if (tid < kSpansBatch) batch_setup<ORD>(p, keys, list, n_items, b0, bs, tid);
     __syncthreads();
-    const int nb = (int)min((long long)kBatch, n_items - b0);
+    const int nb = (int)min((long long)kSpansBatch, n_items - b0);
     for (int ib = 0; ib < nb; ++ib) {
       const int np = bs.np[ib];
       const int flags = bs.flags[ib];
@@ -1493,7 +1503,7 @@ __device__ __forceinline__ void spans_batch(const LinkParams& p, const uint64_t*
 }
 
 template <int ORD>
-__global__ void __launch_bounds__(kThreads, 2)
+__global__ void __launch_bounds__(kThreads, kSpansCtas)
 integrate_fp32c_spans_kernel(LinkParams p, const uint64_t* __restrict__ keys, const uint32_t* __restrict__ list,
                              long long n_items, float* __restrict__ terms, long long n_isl, int rows_per_chunk,
                              int kfp) {
@@ -1502,11 +1512,9 @@ integrate_fp32c_spans_kernel(LinkParams p, const uint64_t* __restrict__ keys, co
   load_node_sm(p, sh.ns);
   spans_types(p, spans_layout(dyn, p.n_types, rows_per_chunk).tyc);
   __syncthreads();
-  for (long long b0 = (long long)blockIdx.x * kBatch; b0 < n_items; b0 += (long long)gridDim.x * kBatch)
+  for (long long b0 = (long long)blockIdx.x * kSpansBatch; b0 < n_items; b0 += (long long)gridDim.x * kSpansBatch)
     spans_batch<ORD>(p, keys, list, n_items, terms, n_isl, rows_per_chunk, kfp, b0, sh, dyn);
 }
-
-constexpr int kSpansDynBytes = 96 * 1024;  // per-type constants, row phases and fibre c_k tables
 
 template <int ORD>
 cudaError_t launch_spans(const LinkParams& p, const uint64_t* keys, const uint32_t* list, long long n_items,
@@ -1521,17 +1529,19 @@ cudaError_t launch_spans(const LinkParams& p, const uint64_t* keys, const uint32
     if ((kfp & 7) == 0) kfp += 4;
   }
   const int per_row = T * per_type + (ORD == ORD_DW ? p.n_fib * kfp * (int)sizeof(float) : 0);
-  int rows = (kSpansDynBytes - T * kSpanTypeFloats * (int)sizeof(float)) / per_row;
+  // 12 bytes of the budget reserved for the fibre tables' 16-byte alignment
+  int rows = (kSpansDynBytes - 12 - T * kSpanTypeFloats * (int)sizeof(float)) / per_row;
   if (rows > kGRows) rows = kGRows;
-  if (rows < 1) return cudaErrorInvalidValue;  // not reached: 64 types and 4 fibres of K 1024 leave 11 rows
-  const size_t smem = (size_t)rows * per_row + (size_t)T * kSpanTypeFloats * sizeof(float);
+  if (rows < 1) return cudaErrorInvalidValue;  // not reached: 64 types and 4 fibres of K 1024 leave 2 rows
+  const size_t smem = (size_t)spans_head_floats(T, rows) * sizeof(float) +
+                      (ORD == ORD_DW ? (size_t)p.n_fib * rows * kfp * sizeof(float) : 0);
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   static std::atomic<unsigned long long> attr_done{0};
   if (cudaError_t e = opt_in_smem(integrate_fp32c_spans_kernel<ORD>, kSpansDynBytes, attr_done)) return e;
-  long long batches = (n_items + kBatch - 1) / kBatch;
-  long long blocks = (long long)sms * 2;
+  long long batches = (n_items + kSpansBatch - 1) / kSpansBatch;
+  long long blocks = (long long)sms * kSpansCtas;
   if (blocks > batches) blocks = batches;
   integrate_fp32c_spans_kernel<ORD><<<(unsigned)blocks, kThreads, smem, st>>>(p, keys, list, n_items, terms, n_isl,
                                                                              rows, kfp);
@@ -1623,7 +1633,7 @@ integrate_fp32c_general_multi_kernel(const LinkJob* __restrict__ jobs, int n_job
 }
 
 template <int ORD>
-__global__ void __launch_bounds__(kThreads, 2)
+__global__ void __launch_bounds__(kThreads, kSpansCtas)
 integrate_fp32c_spans_multi_kernel(const LinkJob* __restrict__ jobs, int n_jobs, long long batches) {
   __shared__ SpansShared sh;
   extern __shared__ __align__(16) float dyn[];
@@ -1637,7 +1647,7 @@ integrate_fp32c_spans_multi_kernel(const LinkJob* __restrict__ jobs, int n_jobs,
       spans_types(J.p, spans_layout(dyn, J.p.n_types, J.rows).tyc);
       __syncthreads();
     }
-    spans_batch<ORD>(J.p, J.keys, J.list, J.n_items, J.terms, J.n_isl, J.rows, J.kfp, (gb - J.first_batch) * kBatch,
+    spans_batch<ORD>(J.p, J.keys, J.list, J.n_items, J.terms, J.n_isl, J.rows, J.kfp, (gb - J.first_batch) * kSpansBatch,
                      sh, dyn);
   }
 }
@@ -1693,9 +1703,10 @@ JobShape job_shape(int ord, int family, const LinkParams& p, long long n_items) 
       if ((s.kfp & 7) == 0) s.kfp += 4;
     }
     const int per_row = T * per_type + (ord == ORD_DW ? p.n_fib * s.kfp * (int)sizeof(float) : 0);
-    s.rows = std::min((kSpansDynBytes - T * kSpanTypeFloats * (int)sizeof(float)) / per_row, kGRows);
-    s.smem = (size_t)s.rows * per_row + (size_t)T * kSpanTypeFloats * sizeof(float);
-    s.batches = (n_items + kBatch - 1) / kBatch;
+    s.rows = std::min((kSpansDynBytes - 12 - T * kSpanTypeFloats * (int)sizeof(float)) / per_row, kGRows);
+    s.smem = (size_t)spans_head_floats(T, s.rows) * sizeof(float) +
+             (ord == ORD_DW ? (size_t)p.n_fib * s.rows * s.kfp * sizeof(float) : 0);
+    s.batches = (n_items + kSpansBatch - 1) / kSpansBatch;
   }
   return s;
 }
@@ -1724,7 +1735,7 @@ cudaError_t launch_multi_ord(const MultiLaunch& m, const void* d_jobs, cudaStrea
     static std::atomic<unsigned long long> done{0};
     e = opt_in_smem(integrate_fp32c_spans_multi_kernel<ORD>, kSpansDynBytes, done);
     if (e != cudaSuccess) return e;
-    const long long blocks = std::min<long long>((long long)sms * 2, m.batches);
+    const long long blocks = std::min<long long>((long long)sms * kSpansCtas, m.batches);
     integrate_fp32c_spans_multi_kernel<ORD><<<(unsigned)blocks, kThreads, m.smem, st>>>(jobs, m.n_jobs, m.batches);
   }
   return cudaGetLastError();

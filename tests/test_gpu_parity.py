@@ -267,6 +267,27 @@ def _many_types_link(workloads, n_ch=3, gl=10):
 
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32c"])
+def test_sixty_three_span_types_four_fibres(egn, oracle_mod, workloads, prec):
+    """63 spans of 63 types on four fibres (attenuations 0.16..0.22 dB/km, lengths
+    60..122 km): the span-by-span path with the most types and fibre tables its
+    shared memory holds, where the fewest rows per chunk (an odd number) fit; eta
+    of every channel against the oracle."""
+    wl = workloads.config_small(n_ch=3, gl_order=6, n_spans=63)
+    for i, sp in enumerate(wl.spans):
+        sp.length_m = (60 + i) * 1e3
+        sp.alpha_db_km = (0.16, 0.18, 0.20, 0.22)[i % 4]
+    ln, pb = _pair(egn, oracle_mod, wl)
+    p = egn.EGN_PREC_FP64 if prec == "fp64" else egn.EGN_PREC_FP32C
+    got, _ = ln.nli_eta(egn.make_opts(gl_order=6, precision=p))
+    want, _ = pb.eta()
+    if prec == "fp64":
+        assert np.allclose(got, want, rtol=FP64_RTOL, atol=0), (got, want)
+    else:
+        assert np.max(_db(got, want)) < 1e-3, _db(got, want)
+    ln.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32c"])
 def test_many_span_types_eta(egn, oracle_mod, workloads, prec):
     """More than four span types: Eq. 22 walked span by span (c_k on the fly)."""
     wl = _many_types_link(workloads)
