@@ -350,14 +350,22 @@ def fp64_denominator(args, wl, ln, eta32, value, stream, flush) -> dict:
         orr = egn.make_opts(gl_order=args.ridge_nodes, dz_km=wl.dz_km, precision=egn.EGN_PREC_FP64,
                             terms=egn.EGN_TERMS_EGN, stream=stream.cuda_stream)
         msr, etar = timed_evals(ln, orr, n_ch, stream, flush, steps=1, warm=1)
+        # and in FP32C (the same rule; identical spans): time and distance from the FP64 result
+        orr32 = egn.make_opts(gl_order=args.ridge_nodes, dz_km=wl.dz_km, precision=egn.EGN_PREC_FP32C,
+                              terms=egn.EGN_TERMS_EGN, stream=stream.cuda_stream)
+        msr32, etar32 = timed_evals(ln, orr32, n_ch, stream, flush, steps=3, warm=1)
         ln.set_node_rule(egn.EGN_RULE_GL)
         dr = 10 * np.log10(eta64 / etar)
+        d32 = np.abs(10 * np.log10(etar32 / etar))
         out["ridge_rule"] = {"nodes_per_piece": args.ridge_nodes, "n_min": 4, "precision": "fp64",
                              "ms_per_step": msr, "value": n_ch / (msr * 1e-3), "unit": UNIT,
                              "gl32_minus_ridge_db": {"mean": float(dr.mean()), "min": float(dr.min()),
                                                      "max": float(dr.max()), "edge": float(dr[0]),
                                                      "centre": float(dr[n_ch // 2])},
-                             "eta_db_sample": [float(10 * np.log10(x)) for x in etar[:: 30]]}
+                             "eta_db_sample": [float(10 * np.log10(x)) for x in etar[:: 30]],
+                             "fp32c": {"ms_per_step": msr32, "value": n_ch / (msr32 * 1e-3), "unit": UNIT,
+                                       "speedup_vs_fp64": msr / msr32, "max_db_vs_fp64": float(d32.max()),
+                                       "mean_db_vs_fp64": float(d32.mean())}}
     if args.no_sweep:
         return out
     sweep = {"p_dbm": [], "ms_fp32c": [], "ms_fp64": [], "channel_evals_per_s_fp32c": [], "max_abs_db_vs_fp64": [],
@@ -744,7 +752,7 @@ def main():
                     help="skip the plain FP64 GPU integrator leg and the launch-power sweep")
     ap.add_argument("--no-sweep", action="store_true", help="skip the -2..+4 dBm/ch launch-power sweep")
     ap.add_argument("--fp64-steps", type=int, default=3)
-    ap.add_argument("--no-ridge", action="store_true", help="skip the ridge-resolving rule's FP64 evaluation")
+    ap.add_argument("--no-ridge", action="store_true", help="skip the ridge-resolving rule (FP64 and FP32C evaluations)")
     ap.add_argument("--ridge-nodes", type=int, default=16, help="nodes per piece of the ridge-resolving rule")
     ap.add_argument("--peaks", action="store_true",
                     help="measure the FP32, FP32x2, FP64 and MUFU pipe peaks with the probe kernels")

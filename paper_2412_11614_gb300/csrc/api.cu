@@ -181,7 +181,8 @@ egn_status check_opts(const egn_link* l, const egn_opts* o) {
   if (o->terms == EGN_TERMS_EGN && l->mixed_rates && l->any_corr)
     return fail(EGN_E_UNSUPPORTED, "EGN corrections with mixed symbol rates are not defined");
   if (l->rule == RULE_RIDGE) {
-    if (o->precision != EGN_PREC_FP64) return fail(EGN_E_UNSUPPORTED, "the ridge-resolving rule runs in FP64 only");
+    if (o->precision != EGN_PREC_FP64 && !l->identical)
+      return fail(EGN_E_UNSUPPORTED, "the ridge-resolving rule in FP32C takes identical spans only (FP64: any spans)");
     if (o->gl_order > kRidgeMaxN)
       return fail(EGN_E_INVALID_ARG, "ridge rule: %d nodes per piece, at most %d", o->gl_order, kRidgeMaxN);
   }
@@ -264,10 +265,20 @@ egn_status ensure_tables(egn_link* l, const egn_opts* o) {
     const size_t n_all = (size_t)m_all * (m_all + 1) / 2;
     const size_t off_allx = total, off_allw = total + align256(n_all * sizeof(double));
     total += 2 * align256(n_all * sizeof(double));
+    const size_t off_allxh = total, off_allxl = total + align256(n_all * sizeof(float)),
+                 off_allwf = total + 2 * align256(n_all * sizeof(float));
+    total += 3 * align256(n_all * sizeof(float));
     host.assign(total, 0);
     for (int m = 1; m <= m_all; ++m)
       gauss_legendre(m, (double*)(host.data() + off_allx) + (size_t)m * (m - 1) / 2,
                      (double*)(host.data() + off_allw) + (size_t)m * (m - 1) / 2);
+    for (size_t i = 0; i < n_all; ++i) {
+      const double x = ((const double*)(host.data() + off_allx))[i];
+      const float xh = (float)x;
+      ((float*)(host.data() + off_allxh))[i] = xh;
+      ((float*)(host.data() + off_allxl))[i] = (float)(x - (double)xh);
+      ((float*)(host.data() + off_allwf))[i] = (float)((const double*)(host.data() + off_allw))[i];
+    }
     for (int p = 1; p <= 3; ++p) {
       int m = ord[p];
       std::vector<double> x(m), w(m);
@@ -307,6 +318,9 @@ egn_status ensure_tables(egn_link* l, const egn_opts* o) {
     l->gl.order[0] = 0;
     l->gl_all_x = (const double*)(b + off_allx);
     l->gl_all_w = (const double*)(b + off_allw);
+    l->gl_all_xh = (const float*)(b + off_allxh);
+    l->gl_all_xl = (const float*)(b + off_allxl);
+    l->gl_all_wf = (const float*)(b + off_allwf);
     l->tab_gl = n;
   }
   return EGN_OK;
@@ -377,6 +391,9 @@ LinkParams link_params(const egn_link* l, const egn_opts* o, int all_terms) {
   p.ridge_n_min = l->ridge_n_min;
   p.glx_all = l->gl_all_x;
   p.glw_all = l->gl_all_w;
+  p.glxh_all = l->gl_all_xh;
+  p.glxl_all = l->gl_all_xl;
+  p.glwf_all = l->gl_all_wf;
   set_mu_params(p, l, o);
   p.n_types = l->identical ? 1 : (int)l->type_si.size();
   for (int t = 0; t < p.n_types && t < kMaxTypes; ++t) p.types[t] = l->types[t];

@@ -91,6 +91,9 @@ void rebase_params(LinkParams& p, const egn_link* l, char* ch_copy, char* seg_co
   }
   rebase(p.glx_all, l->d_gl.p, l->d_gl.bytes, gl_copy);
   rebase(p.glw_all, l->d_gl.p, l->d_gl.bytes, gl_copy);
+  rebase(p.glxh_all, l->d_gl.p, l->d_gl.bytes, gl_copy);
+  rebase(p.glxl_all, l->d_gl.p, l->d_gl.bytes, gl_copy);
+  rebase(p.glwf_all, l->d_gl.p, l->d_gl.bytes, gl_copy);
   for (int q = 0; q < 4; ++q) {
     rebase(p.gl.x[q], l->d_gl.p, l->d_gl.bytes, gl_copy);
     rebase(p.gl.w[q], l->d_gl.p, l->d_gl.bytes, gl_copy);
@@ -356,6 +359,8 @@ egn_status create(egn_link* const* links, int n_links, const egn_opts* o, bool c
     L.ch = L.p.ch;
   }
   b->flat = o->precision == EGN_PREC_FP32C;
+  for (int i = 0; i < n_links; ++i)
+    if (links[i]->rule != egn::RULE_GL) b->flat = false;  // the flat passes run the configured rule's kernels
   if (b->flat) {
     egn_status fs = build_flat(b);
     if (fs != EGN_OK) return fs;

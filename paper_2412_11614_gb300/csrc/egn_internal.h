@@ -131,6 +131,9 @@ struct LinkParams {
   int ridge_n_min;   // ridge rule: fewest nodes of a piece that does not end on a ridge
   const double* glx_all;  // Gauss-Legendre nodes of every order m = 1 .. gl.n, order m at offset m (m - 1) / 2
   const double* glw_all;  // and their weights
+  const float* glxh_all;  // the same nodes as FP32 head + tail (x - head) and FP32 weights
+  const float* glxl_all;
+  const float* glwf_all;
   int mu_form;       // MU_SEGMENT, MU_MACLAURIN or MU_INTEGRAL (the last two: FP64 path)
   double btot;       // B_tot [THz] of Eq. 25
   double mgx[kMuGl], mgw[kMuGl];  // Gauss-Legendre rule of the integral form on [-1, 1]
@@ -208,6 +211,10 @@ cudaError_t launch_fp64_pass(int ord, const LinkParams& p, const uint64_t* keys,
                              long long n_items, double* terms, long long n_isl, cudaStream_t st);
 cudaError_t launch_fp32c_pass(int ord, const LinkParams& p, const uint64_t* keys, const uint32_t* list,
                               long long n_items, float* terms, long long n_isl, cudaStream_t st);
+// The ridge-resolving rule in FP32C (links of identical spans; launch_fp32c_pass
+// dispatches here when p.rule == RULE_RIDGE).
+cudaError_t launch_ridge_fp32c(int ord, const LinkParams& p, const uint64_t* keys, const uint32_t* list,
+                               long long n_items, float* terms, long long n_isl, cudaStream_t st);
 
 // Multi-link FP32C passes (batches of links): one launch per pass and kernel
 // family over the work lists of several links.  A link's family: 0 identical

@@ -1,7 +1,8 @@
 // fp32c_common.cuh -- device helpers of the FP32 integrators: double-float
 // ("df", an unevaluated FP32 head + tail) arithmetic, packed FP32x2 FMA, exact
-// rounding to an integer, hardware-approximation wrappers, small-angle sine and
-// the raised-cosine shape.
+// rounding to an integer, hardware-approximation wrappers, small-angle sine,
+// the raised-cosine shape, and a row's phase polynomial and its exact per-point
+// reduction.
 #pragma once
 
 #include "egn_internal.h"
@@ -114,6 +115,83 @@ __device__ __forceinline__ float array_ratio(float x, float N) {
 __device__ __forceinline__ float rc_f(float x, float a, float inv) {
   const float t = __saturatef((fabsf(x) - a) * inv);
   return fmaf(0.5f, __cosf(3.14159265f * t), 0.5f);
+}
+
+// Per-link constants of the identical-spans passes: K, the segment factor
+// r = e^{-alpha dz} and its combinations, the span count N and gamma.
+struct DwConsts {
+  int K;
+  float Kf, invK, alpha, alpha2, r, one_m_r, q, m2r, c2r, c4r, omr2, N, gam, g2;
+};
+
+__device__ __forceinline__ DwConsts dw_consts(const LinkParams& p) {
+  DwConsts c;
+  c.K = p.seg.K;
+  c.Kf = (float)c.K;
+  c.invK = 1.0f / (float)c.K;
+  c.alpha = (float)p.alpha;
+  c.alpha2 = c.alpha * c.alpha;
+  c.r = (float)p.r;
+  c.one_m_r = (float)(-expm1(-p.alpha * p.dz));
+  c.q = c.r * c.r;
+  c.m2r = -2.0f * c.r;
+  c.c2r = 2.0f * c.r;
+  c.c4r = 4.0f * c.r;
+  c.omr2 = c.one_m_r * c.one_m_r;
+  c.N = (float)p.n_spans;
+  c.gam = (float)p.gamma;
+  c.g2 = c.gam * c.gam;
+  return c;
+}
+
+// Row geometry in double-float: outer node o, inner interval im +- ih and the
+// linear forms f1 - f = a0 + a1 x, f2 - f = b0 + b1 x, f1 + f2 = s0 + s1 x of the
+// inner Gauss-Legendre coordinate x (frequencies relative to the spectral centre).
+struct RowGeo {
+  Df o, im, ih, a0, a1, b0, b1, s0, s1, ph;
+};
+
+// Phase polynomial of a row for one span type, in turns of that span:
+// Theta(x) = Q0 + Q1 x + Q2 x^2 + Q3 x^3 with Q0 reduced modulo K.
+// G0 = 2 pi L beta2, G1 = 2 pi^2 L beta3 (double-floats).
+struct RowPhase {
+  Df Q0r, Q1, Q2;
+  float Q3;
+};
+
+__device__ __forceinline__ RowPhase row_phase(const RowGeo& r, Df G0, Df G1, float Kf, float invK) {
+  const Df g0 = dadd(G0, dmul(G1, r.s0));   // 2 pi L (beta2 + pi beta3 s0)
+  const Df g1 = dmul(G1, r.s1);             // 2 pi L pi beta3 s1
+  const Df ab0 = dmul(r.a0, r.b0);
+  const Df ab1 = dadd(dmul(r.a0, r.b1), dmul(r.a1, r.b0));
+  const Df ab2 = dmul(r.a1, r.b1);
+  const Df Q0 = dmul(g0, ab0);
+  RowPhase q;
+  q.Q1 = dadd(dmul(g0, ab1), dmul(g1, ab0));
+  q.Q2 = dadd(dmul(g0, ab2), dmul(g1, ab1));
+  q.Q3 = dval(g1) * dval(ab2);
+  const float r0 = fmaf(-Kf, rint_fast(Q0.hi * invK), Q0.hi);  // the FMA residual is exact
+  q.Q0r = quick(r0, Q0.lo);
+  return q;
+}
+
+// Phase of one point of a row: theta (turns of one segment, chi L / (2 pi K))
+// and phi (turns of the span, chi L / (2 pi)), both reduced to [-1/2, 1/2].
+// qa = {q0h, q0l, q1h, q1l}, qb = {q2h, q2l, q3, frac(q0h)}, x4 = {x, x tail,
+// x^2, x^2 tail}, xc = x^3.  Q1 x and Q2 x^2 are exact FP32 products (head by
+// FMA residual, tails by the cross terms); Q1 x is reduced modulo K exactly.
+__device__ __forceinline__ void point_phase(const float4& qa, const float4& qb, const float4& x4, float xc, float Kf,
+                                            float invK, float& th, float& ph) {
+  const float p1 = qa.z * x4.x, e1 = fmaf(qa.z, x4.x, -p1);
+  const float t1 = fmaf(qa.z, x4.y, fmaf(qa.w, x4.x, e1));
+  const float p2 = qb.x * x4.z, e2 = fmaf(qb.x, x4.z, -p2);
+  const float t2 = fmaf(qb.x, x4.w, fmaf(qb.y, x4.z, e2));
+  const float r1 = fmaf(-Kf, rint_fast(p1 * invK), p1);
+  const float tail = (qa.y + t1) + fmaf(qb.z, xc, t2);
+  th = fmaf((qa.x + r1) + p2, invK, tail * invK);
+  th -= rint_fast(th);
+  ph = (qb.w + (r1 - rint_fast(r1))) + ((p2 - rint_fast(p2)) + tail);
+  ph -= rint_fast(ph);
 }
 
 }  // namespace fp32c

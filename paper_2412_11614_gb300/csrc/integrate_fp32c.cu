@@ -148,13 +148,6 @@ __device__ __forceinline__ void batch_setup(const LinkParams& p, const uint64_t*
     bs.flags[tid] = flags;
   }
 
-// Row geometry in double-float: outer node o, inner interval im +- ih and the
-// linear forms f1 - f = a0 + a1 x, f2 - f = b0 + b1 x, f1 + f2 = s0 + s1 x of the
-// inner Gauss-Legendre coordinate x (frequencies relative to the spectral centre).
-struct RowGeo {
-  Df o, im, ih, a0, a1, b0, b1, s0, s1, ph;
-};
-
 template <int ORD, class BS>
 __device__ __forceinline__ RowGeo row_geometry(const LinkParams& p, const BS& bs, int ib, int np, int pi,
                                                int i) {
@@ -189,30 +182,6 @@ __device__ __forceinline__ RowGeo row_geometry(const LinkParams& p, const BS& bs
   return r;
 }
 
-// Phase polynomial of a row for one span type, in turns of that span:
-// Theta(x) = Q0 + Q1 x + Q2 x^2 + Q3 x^3 with Q0 reduced modulo K.
-// G0 = 2 pi L beta2, G1 = 2 pi^2 L beta3 (double-floats).
-struct RowPhase {
-  Df Q0r, Q1, Q2;
-  float Q3;
-};
-
-__device__ __forceinline__ RowPhase row_phase(const RowGeo& r, Df G0, Df G1, float Kf, float invK) {
-  const Df g0 = dadd(G0, dmul(G1, r.s0));   // 2 pi L (beta2 + pi beta3 s0)
-  const Df g1 = dmul(G1, r.s1);             // 2 pi L pi beta3 s1
-  const Df ab0 = dmul(r.a0, r.b0);
-  const Df ab1 = dadd(dmul(r.a0, r.b1), dmul(r.a1, r.b0));
-  const Df ab2 = dmul(r.a1, r.b1);
-  const Df Q0 = dmul(g0, ab0);
-  RowPhase q;
-  q.Q1 = dadd(dmul(g0, ab1), dmul(g1, ab0));
-  q.Q2 = dadd(dmul(g0, ab2), dmul(g1, ab1));
-  q.Q3 = dval(g1) * dval(ab2);
-  const float r0 = fmaf(-Kf, rint_fast(Q0.hi * invK), Q0.hi);  // the FMA residual is exact
-  q.Q0r = quick(r0, Q0.lo);
-  return q;
-}
-
 // Row constants of row `row` of island jb of the batch into slot rr of R (the
 // point passes' constants, see RowSm); returns the row's f3 (DW order).
 template <int ORD, class BS, class RS>
@@ -243,25 +212,6 @@ __device__ __forceinline__ float form_row(const LinkParams& p, const BS& bs, RS&
     R.f3[rr] = make_float4(nu3 + (imf + of + dfl), ihf, wo, 0.0f);
   }
   return f3v;
-}
-
-// Phase of one point of a row: theta (turns of one segment, chi L / (2 pi K))
-// and phi (turns of the span, chi L / (2 pi)), both reduced to [-1/2, 1/2].
-// qa = {q0h, q0l, q1h, q1l}, qb = {q2h, q2l, q3, frac(q0h)}, x4 = {x, x tail,
-// x^2, x^2 tail}, xc = x^3.  Q1 x and Q2 x^2 are exact FP32 products (head by
-// FMA residual, tails by the cross terms); Q1 x is reduced modulo K exactly.
-__device__ __forceinline__ void point_phase(const float4& qa, const float4& qb, const float4& x4, float xc, float Kf,
-                                            float invK, float& th, float& ph) {
-  const float p1 = qa.z * x4.x, e1 = fmaf(qa.z, x4.x, -p1);
-  const float t1 = fmaf(qa.z, x4.y, fmaf(qa.w, x4.x, e1));
-  const float p2 = qb.x * x4.z, e2 = fmaf(qb.x, x4.z, -p2);
-  const float t2 = fmaf(qb.x, x4.w, fmaf(qb.y, x4.z, e2));
-  const float r1 = fmaf(-Kf, rint_fast(p1 * invK), p1);
-  const float tail = (qa.y + t1) + fmaf(qb.z, xc, t2);
-  th = fmaf((qa.x + r1) + p2, invK, tail * invK);
-  th -= rint_fast(th);
-  ph = (qb.w + (r1 - rint_fast(r1))) + ((p2 - rint_fast(p2)) + tail);
-  ph -= rint_fast(ph);
 }
 
 // Segment sum of NPAIR point pairs of one row by the second-order real
@@ -344,32 +294,6 @@ struct DwShared {
   float tab_f3[rows_max(NT)];
   int tab_rows;
 };
-
-// Per-link constants of the identical-spans passes.
-struct DwConsts {
-  int K;
-  float Kf, invK, alpha, alpha2, r, one_m_r, q, m2r, c2r, c4r, omr2, N, gam, g2;
-};
-
-__device__ __forceinline__ DwConsts dw_consts(const LinkParams& p) {
-  DwConsts c;
-  c.K = p.seg.K;
-  c.Kf = (float)c.K;
-  c.invK = 1.0f / (float)c.K;
-  c.alpha = (float)p.alpha;
-  c.alpha2 = c.alpha * c.alpha;
-  c.r = (float)p.r;
-  c.one_m_r = (float)(-expm1(-p.alpha * p.dz));
-  c.q = c.r * c.r;
-  c.m2r = -2.0f * c.r;
-  c.c2r = 2.0f * c.r;
-  c.c4r = 4.0f * c.r;
-  c.omr2 = c.one_m_r * c.one_m_r;
-  c.N = (float)p.n_spans;
-  c.gam = (float)p.gamma;
-  c.g2 = c.gam * c.gam;
-  return c;
-}
 
 // Inner Gauss-Legendre nodes of the launch into dynamic shared memory:
 // {x head, x tail, x^2 head, x^2 tail}[npad], {x^3, w}[npad]; nodes n..npad-1 are
@@ -1745,6 +1669,7 @@ cudaError_t launch_multi_ord(const MultiLaunch& m, const void* d_jobs, cudaStrea
 
 cudaError_t launch_fp32c_pass(int ord, const LinkParams& p, const uint64_t* keys, const uint32_t* list,
                               long long n_items, float* terms, long long n_isl, cudaStream_t st) {
+  if (p.rule == RULE_RIDGE) return launch_ridge_fp32c(ord, p, keys, list, n_items, terms, n_isl, st);
   if (p.n_types > kMaxTypes) {
     if (ord == ORD_DW) return launch_spans<ORD_DW>(p, keys, list, n_items, terms, n_isl, st);
     if (ord == ORD_E) return launch_spans<ORD_E>(p, keys, list, n_items, terms, n_isl, st);

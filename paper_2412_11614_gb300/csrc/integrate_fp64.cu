@@ -16,6 +16,7 @@
 // tabulated once in shared memory; the E and F orders evaluate them per point.
 #include "egn_internal.h"
 #include "island_geom.cuh"
+#include "ridge_rule.cuh"
 
 namespace egn {
 namespace {
@@ -347,116 +348,16 @@ __global__ void __launch_bounds__(32) integrate_fp64_kernel(LinkParams p, const 
   }
 }
 
-// ---------------------------------------------------------------------------
-// The ridge-resolving node rule (egn_set_node_rule(EGN_RULE_RIDGE)).  With chi of
-// Eq. 5/24, |mu|^2 of Eq. 8-10 is close to 1 / (alpha^2 + chi^2): along f1 at
-// fixed f2 a Lorentzian centred on f1 = f of half-width alpha / (4 pi^2 |beta2 +
-// 2 pi beta3 f| |f2 - f|), and likewise along f2 -- tens of MHz for interferers a
-// THz away, inside channels of tens of GHz.  The raised-cosine shapes add kinks
-// at their knees.  In each evaluation order (outer o, inner t, coupled by
-// |t - (s o + c)| <= C, see island_geom.cuh):
-//   * the outer range is cut at the knees of the outer shape, wherever two inner
-//     break lines t = const and t = s o + const cross (which includes the
-//     island's kinks), and at a ridge of the outer variable;
-//   * each inner interval is cut at the knees of the other two shapes and at the
-//     ridge points f1 = f and f2 = f inside it;
-//   * cuts closer than 1e-12 THz merge (a ridge wins); a piece that ends on a
-//     ridge gets n nodes placed by x = x_r + h sinh(tau), tau on an n-point
-//     Gauss-Legendre rule over [0, asinh(length / h)] (h the ridge half-width; a
-//     piece with a ridge at both ends is halved first); another piece gets
-//     max(n_min, ceil(n length / interval)) Gauss-Legendre nodes.
-// One warp per island as in the configured rule: lane 0 forms the outer pieces,
+// The ridge-resolving node rule (egn_set_node_rule(EGN_RULE_RIDGE), ridge_rule.cuh):
+// one warp per island as in the configured rule: lane 0 forms the outer pieces,
 // every lane then takes outer nodes ("rows") and walks its row's inner pieces.
-// ---------------------------------------------------------------------------
-
-struct RCut {
-  double x, h;  // h > 0: a ridge of half-width h; otherwise a plain cut
-};
-struct RPiece {
-  double a, b, ha, hb;  // ends and their ridge half-widths (<= 0: none)
-  int m;                // nodes
-};
-constexpr int kOuterCuts = 30;  // 2 knees + 5 x 5 crossings + 1 ridge of the outer variable
-constexpr int kInnerCuts = 6;   // 4 knees + 2 ridges
-
-__device__ __forceinline__ void sort_cuts(RCut* c, int n) {  // stable, ascending x
-  for (int i = 1; i < n; ++i) {
-    const RCut v = c[i];
-    int j = i;
-    while (j > 0 && c[j - 1].x > v.x) {
-      c[j] = c[j - 1];
-      --j;
-    }
-    c[j] = v;
-  }
-}
-
-// Pieces of [lo, hi] cut at the points of `pts` inside it; returns their number.
-template <int MAXC>
-__device__ int ridge_pieces(double lo, double hi, const RCut* pts, int np, int n, int n_min, RPiece* out) {
-  const double eps = 1e-12;
-  RCut cand[MAXC];
-  int nc = 0;
-  for (int i = 0; i < np; ++i)
-    if (lo + eps < pts[i].x && pts[i].x < hi - eps) cand[nc++] = pts[i];
-  sort_cuts(cand, nc);
-  RCut e[MAXC + 2];
-  int ne = 0;
-  e[ne++] = {lo, -1.0};
-  for (int i = 0; i < nc; ++i) {
-    if (ne > 1 && cand[i].x - e[ne - 1].x < eps) {  // merges into the previous cut
-      if (cand[i].h > 0.0) e[ne - 1].h = cand[i].h;
-      continue;
-    }
-    e[ne++] = cand[i];
-  }
-  e[ne++] = {hi, -1.0};
-  for (int i = 0; i < np; ++i) {  // a ridge on an end of the interval
-    if (pts[i].h > 0.0 && fabs(pts[i].x - lo) <= eps) e[0].h = pts[i].h;
-    if (pts[i].h > 0.0 && fabs(pts[i].x - hi) <= eps) e[ne - 1].h = pts[i].h;
-  }
-  int k = 0;
-  for (int i = 0; i + 1 < ne; ++i) {
-    const double a = e[i].x, b = e[i + 1].x, ha = e[i].h, hb = e[i + 1].h;
-    if (!(b > a)) continue;
-    if (ha > 0.0 && hb > 0.0) {
-      const double mid = 0.5 * (a + b);
-      out[k++] = {a, mid, ha, -1.0, n};
-      out[k++] = {mid, b, -1.0, hb, n};
-    } else if (ha > 0.0 || hb > 0.0) {
-      out[k++] = {a, b, ha, hb, n};
-    } else {
-      out[k++] = {a, b, -1.0, -1.0, max(n_min, (int)ceil((double)n * (b - a) / (hi - lo)))};
-    }
-  }
-  return k;
-}
-
-// Node j and weight of a piece (Gauss-Legendre of order q.m, sinh-graded towards a ridge end).
-__device__ __forceinline__ void piece_node(const RPiece& q, int j, const double* __restrict__ gx,
-                                           const double* __restrict__ gw, double& x, double& w) {
-  const size_t o = (size_t)q.m * (q.m - 1) / 2;
-  const double xj = gx[o + j], wj = gw[o + j];
-  if (q.ha > 0.0 || q.hb > 0.0) {
-    const double h = q.ha > 0.0 ? q.ha : q.hb;
-    const double T = asinh((q.b - q.a) / h);
-    const double tau = 0.5 * T * (xj + 1.0);
-    const double off = h * sinh(tau);
-    w = 0.5 * T * wj * h * cosh(tau);
-    x = q.ha > 0.0 ? q.a + off : q.b - off;
-  } else {
-    x = 0.5 * (q.a + q.b) + 0.5 * (q.b - q.a) * xj;
-    w = 0.5 * (q.b - q.a) * wj;
-  }
-}
-
 template <int ORD>
 __global__ void __launch_bounds__(32) integrate_ridge_kernel(LinkParams p, const uint64_t* __restrict__ keys,
                                                              const uint32_t* __restrict__ list, long long n_items,
                                                              double* __restrict__ terms, long long n_isl) {
   extern __shared__ double ck_s[];  // [K][32] c_k row tables (DW order), as in the configured rule
-  __shared__ RPiece opc[2 * (kOuterCuts + 1)];
-  __shared__ int ocum[2 * (kOuterCuts + 1) + 1];
+  __shared__ RPiece opc[kOuterPieces];
+  __shared__ int ocum[kOuterPieces + 1];
   __shared__ int n_op;
   const int lane = threadIdx.x;
   const bool tables = p.n_types <= kMaxTypes && p.mu_form == MU_SEGMENT;
@@ -472,45 +373,11 @@ __global__ void __launch_bounds__(32) integrate_ridge_kernel(LinkParams p, const
     const long long isl = list ? (long long)list[it] : it;
     int coi, n1, n2, n3;
     unpack_key(keys[isl], coi, n1, n2, n3);
-    const double f = ch.nu_coi[coi], nu1 = ch.nu[n1], nu2 = ch.nu[n2], nu3 = ch.nu[n3];
-    const double R = ch.R[coi], R1 = ch.R[n1], R2 = ch.R[n2], R3 = ch.R[n3];
-    const double d = (nu1 - f) + (nu2 - nu3);
-    const double k1 = (1.0 - be) * R1 / 2.0, k2 = (1.0 - be) * R2 / 2.0, k3 = (1.0 - be) * R3 / 2.0;
-    const double h1w = 0.5 * ch.W[n1], h2w = 0.5 * ch.W[n2], h3w = 0.5 * ch.W[n3];
-    const double cc = 4.0 * kPi * kPi * fabs(p.beta2 + 2.0 * kPi * p.beta3 * f);
-    const bool ridges = cc > 0.0;
-    const double us = f - nu1, vs = f - nu2;  // ridges u = us (f1 = f) and v = vs (f2 = f)
-    double A, B, sg, c, C, ko, kt, ky;
-    if (ORD == ORD_DW) { A = h3w; B = h1w; sg = 1.0; c = -d; C = h2w; ko = k3; kt = k1; ky = k2; }
-    else if (ORD == ORD_E) { A = h2w; B = h1w; sg = -1.0; c = -d; C = h3w; ko = k2; kt = k1; ky = k3; }
-    else { A = h1w; B = h2w; sg = -1.0; c = -d; C = h3w; ko = k1; kt = k2; ky = k3; }
-    const double pp = sg * (-(B + C) - c), qq = sg * ((B + C) - c);
-    const double lo = fmax(-A, fmin(pp, qq)), hi = fmin(A, fmax(pp, qq));
-    const bool area = hi > lo;
-    const double hmax = ridges ? p.alpha / (cc * fmax(h1w, h2w)) : -1.0;
+    const RidgeIsland g = ridge_island<ORD>(ch, coi, n1, n2, n3, p.rolloff, p.alpha, p.beta2, p.beta3);
+    const double f = g.f, nu1 = g.nu1, nu2 = g.nu2, nu3 = g.nu3;
+    const double R = ch.R[coi], R1 = g.R1, R2 = g.R2, R3 = g.R3;
     if (lane == 0) {
-      int np = 0;
-      if (area) {
-        RCut cuts[kOuterCuts];
-        int nc = 0;
-        cuts[nc++] = {-ko, -1.0};
-        cuts[nc++] = {ko, -1.0};
-        // inner break lines t = b0 (flat) and t = s o + b1 (slant); the ridge lines last
-        double flat[5] = {-B, B, -kt, kt, 0.0}, slant[5] = {c - C, c + C, c - ky, c + ky, 0.0};
-        int nfl = 4, nsl = 4;
-        const bool rfl = ridges, rsl = ridges && ORD == ORD_DW;
-        const double ridge_flat = ORD == ORD_F ? vs : us, ridge_slant = c - vs;
-        if (rfl) flat[nfl++] = ridge_flat;
-        if (rsl) slant[nsl++] = ridge_slant;
-        for (int i = 0; i < nfl; ++i)
-          for (int j = 0; j < nsl; ++j) {
-            const bool both = rfl && rsl && flat[i] == ridge_flat && slant[j] == ridge_slant;
-            cuts[nc++] = {(flat[i] - slant[j]) / sg, both ? hmax : -1.0};
-          }
-        if (ridges && ORD == ORD_E) cuts[nc++] = {vs, hmax};
-        if (ridges && ORD == ORD_F) cuts[nc++] = {us, hmax};
-        np = ridge_pieces<kOuterCuts>(lo, hi, cuts, nc, n, n_min, opc);
-      }
+      const int np = ridge_outer_pieces<ORD>(g, n, n_min, opc);
       int cum = 0;
       for (int q = 0; q < np; ++q) {
         ocum[q] = cum;
@@ -532,32 +399,10 @@ __global__ void __launch_bounds__(32) integrate_ridge_kernel(LinkParams p, const
       while (ocum[q + 1] <= row) ++q;
       double o, wo;
       piece_node(opc[q], row - ocum[q], p.glx_all, p.glw_all, o, wo);
-      const double m = sg * o + c;
-      const double tlo = fmax(-B, m - C), thi = fmin(B, m + C);
-      if (!(thi > tlo)) continue;
-      RCut pts[kInnerCuts];
-      int npt = 0;
-      pts[npt++] = {-kt, -1.0};
-      pts[npt++] = {kt, -1.0};
-      pts[npt++] = {m - ky, -1.0};
-      pts[npt++] = {m + ky, -1.0};
-      if (ridges) {
-        if (ORD == ORD_DW) {
-          const double x2 = nu2 + (m - us) - f;  // f2 - f on the ridge f1 = f
-          if (x2 != 0.0) pts[npt++] = {us, p.alpha / (cc * fabs(x2))};
-          const double tr = m - vs;               // the ridge f2 = f
-          const double x1 = nu1 + tr - f;
-          if (x1 != 0.0) pts[npt++] = {tr, p.alpha / (cc * fabs(x1))};
-        } else if (ORD == ORD_E) {
-          const double x2 = nu2 + o - f;
-          if (x2 != 0.0) pts[npt++] = {us, p.alpha / (cc * fabs(x2))};
-        } else {
-          const double x1 = nu1 + o - f;
-          if (x1 != 0.0) pts[npt++] = {vs, p.alpha / (cc * fabs(x1))};
-        }
-      }
-      RPiece ipc[2 * (kInnerCuts + 1)];
-      const int nip = ridge_pieces<kInnerCuts>(tlo, thi, pts, npt, n, n_min, ipc);
+      double m;
+      RPiece ipc[kInnerPieces];
+      const int nip = ridge_inner_pieces<ORD>(g, o, n, n_min, ipc, m);
+      if (nip == 0) continue;
       double outer_h;
       if (ORD == ORD_DW) {
         const double f3 = nu3 + o;

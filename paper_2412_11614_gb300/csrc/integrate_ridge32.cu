@@ -1,0 +1,344 @@
+// integrate_ridge32.cu -- the ridge-resolving node rule (ridge_rule.cuh) in the
+// FP32 arithmetic of the fast path (FP32C), for links of identical spans.
+//
+// Work decomposition: one warp (a 32-thread CTA) per island, as in the FP64 form
+// of the rule.  Lane 0 forms the island's outer pieces (FP64).  The lanes then
+// take outer nodes ("rows") 32 at a time: each lane forms its row's inner pieces
+// (FP64) and, in the DW order, the row's c_k = C_k e^{-zeta_k f3} in its column of
+// a [K][32] shared table, and walks its row's nodes in groups of four points,
+// two per fma.rn.f32x2 in the segment recurrence.
+//
+// Per piece the inner coordinate is t = t0 + t1 y, with y the piece variable: the
+// Gauss-Legendre node x_j on a plain piece (t0 its midpoint, t1 its half-length),
+// the offset h sinh(tau_j) from the ridge end on a graded one (t1 = +1 or -1).
+// f1 - f, f2 - f and f1 + f2 are linear in y, so the phase of Eq. 5/24 is a
+// polynomial in y whose coefficients are formed per piece in double-float
+// (row_phase, Q0 reduced modulo K), and every point's phase is reduced exactly as
+// on the configured rule (point_phase).  On a graded piece f1 - f (or f2 - f) is
+// the offset itself plus a constant that vanishes to FP64 rounding, so chi near
+// the ridge keeps full relative precision.  The graded offsets are formed in FP32
+// (sinhf, a few ulp): a node lies within ~1e-7 of its FP64 offset from the ridge,
+// a perturbation of the rule, not of the integrand.
+//
+// Everything past the node (w, the segment sum, mu, the phased array, the sums)
+// is the arithmetic of the configured rule's FP32C passes.
+#include "egn_internal.h"
+
+#include "fp32c_common.cuh"
+#include "island_geom.cuh"
+#include "ridge_rule.cuh"
+
+namespace egn {
+namespace {
+
+using namespace fp32c;
+
+constexpr int kGroup = 4;  // points per lane and step of the node walk
+
+// Constants of one inner piece of a lane's row.
+struct PieceC {
+  float4 qa, qb;         // phase polynomial in y (point_phase)
+  float a0, a1, b0, b1;  // f1 - f = a0 + a1 y, f2 - f = b0 + b1 y
+  float k0, k1;          // 4 pi^2 (beta2 + pi beta3 (f1 + f2)) = k0 + k1 y
+  float u0, u1, v0, v1;  // shape coordinates u = u0 + u1 y, v = v0 + v1 y
+  float w0, w1;          // w = w0 + w1 y (E and F; DW: the row's)
+  float T2, h, wsc;      // graded: tau = T2 (x + 1), y = h sinh(tau), weight wsc w_j cosh(tau); plain: weight wsc w_j
+  int m, goff;           // nodes; offset of the order-m rule in the node tables
+  bool graded;
+};
+
+// Frequencies of an island relative to the COI: F1 = nu1 - f, F2 = nu2 - f, S12 = nu1 + nu2.
+template <int ORD>
+__device__ __forceinline__ PieceC piece_consts(const LinkParams& p, const RidgeIsland& g, const RPiece& q, double o,
+                                               double m, Df G0, Df G1, float Kf, float invK) {
+  PieceC c;
+  c.graded = q.ha > 0.0 || q.hb > 0.0;
+  c.m = q.m;
+  c.goff = q.m * (q.m - 1) / 2;
+  double t0, t1;
+  if (c.graded) {
+    const double h = q.ha > 0.0 ? q.ha : q.hb;
+    t0 = q.ha > 0.0 ? q.a : q.b;
+    t1 = q.ha > 0.0 ? 1.0 : -1.0;
+    const float T = asinhf((float)((q.b - q.a) / h));
+    c.T2 = 0.5f * T;
+    c.h = (float)h;
+    c.wsc = c.T2 * c.h;
+  } else {
+    t0 = 0.5 * (q.a + q.b);
+    t1 = 0.5 * (q.b - q.a);
+    c.T2 = 0.0f;
+    c.h = 0.0f;
+    c.wsc = (float)t1;
+  }
+  const double F1 = g.nu1 - g.f, F2 = g.nu2 - g.f, S12 = g.nu1 + g.nu2;
+  double a0, a1, b0, b1, s0, s1, u0, u1, v0, v1, w0, w1;
+  if (ORD == ORD_DW) {  // u = t, v = m - t, w = o
+    u0 = t0; u1 = t1; v0 = m - t0; v1 = -t1; w0 = o; w1 = 0.0;
+    s0 = S12 + m; s1 = 0.0;
+  } else if (ORD == ORD_E) {  // u = t, v = o, w = t - m
+    u0 = t0; u1 = t1; v0 = o; v1 = 0.0; w0 = t0 - m; w1 = t1;
+    s0 = S12 + o + t0; s1 = t1;
+  } else {  // u = o, v = t, w = t - m
+    u0 = o; u1 = 0.0; v0 = t0; v1 = t1; w0 = t0 - m; w1 = t1;
+    s0 = S12 + o + t0; s1 = t1;
+  }
+  a0 = F1 + u0; a1 = u1;
+  b0 = F2 + v0; b1 = v1;
+  RowGeo r;
+  r.a0 = df_of(a0); r.a1 = df_of(a1);
+  r.b0 = df_of(b0); r.b1 = df_of(b1);
+  r.s0 = df_of(s0); r.s1 = df_of(s1);
+  const RowPhase ph = row_phase(r, G0, G1, Kf, invK);
+  c.qa = make_float4(ph.Q0r.hi, ph.Q0r.lo, ph.Q1.hi, ph.Q1.lo);
+  c.qb = make_float4(ph.Q2.hi, ph.Q2.lo, ph.Q3, ph.Q0r.hi - rint_fast(ph.Q0r.hi));
+  c.a0 = (float)a0; c.a1 = (float)a1;
+  c.b0 = (float)b0; c.b1 = (float)b1;
+  const double k4 = 4.0 * kPi * kPi;
+  c.k0 = (float)(k4 * (p.beta2 + kPi * p.beta3 * s0));
+  c.k1 = (float)(k4 * kPi * p.beta3 * s1);
+  c.u0 = (float)u0; c.u1 = (float)u1;
+  c.v0 = (float)v0; c.v1 = (float)v1;
+  c.w0 = (float)w0; c.w1 = (float)w1;
+  return c;
+}
+
+template <int ORD>
+__global__ void __launch_bounds__(32) integrate_ridge_fp32c_kernel(LinkParams p, const uint64_t* __restrict__ keys,
+                                                                   const uint32_t* __restrict__ list,
+                                                                   long long n_items, float* __restrict__ terms,
+                                                                   long long n_isl, Df G0, Df G1) {
+  extern __shared__ float ck_s[];  // DW: [K][32], the c_k of each lane's row
+  __shared__ RPiece opc[kOuterPieces];
+  __shared__ int ocum[kOuterPieces + 1];
+  __shared__ int n_op;
+  const int lane = threadIdx.x;
+  const DwConsts cst = dw_consts(p);
+  const int K = cst.K;
+  const float Kf = cst.Kf, invK = cst.invK, alpha = cst.alpha, alpha2 = cst.alpha2, one_m_r = cst.one_m_r;
+  const float q = cst.q, m2r = cst.m2r, N = cst.N;
+  const float pi_f = 3.14159265358979f;
+  const int n = p.gl.n, n_min = p.ridge_n_min;
+  const double be = p.rolloff;
+  const ChannelTable& ch = p.ch;
+  for (long long it = blockIdx.x; it < n_items; it += gridDim.x) {
+    const long long isl = list ? (long long)list[it] : it;
+    int coi, n1, n2, n3;
+    unpack_key(keys[isl], coi, n1, n2, n3);
+    const RidgeIsland g = ridge_island<ORD>(ch, coi, n1, n2, n3, p.rolloff, p.alpha, p.beta2, p.beta3);
+    if (lane == 0) {
+      const int np = ridge_outer_pieces<ORD>(g, n, n_min, opc);
+      int cum = 0;
+      for (int i = 0; i < np; ++i) {
+        ocum[i] = cum;
+        cum += opc[i].m;
+      }
+      ocum[np] = cum;
+      n_op = np;
+    }
+    __syncwarp();
+    const int npc = n_op, rows = ocum[npc];
+    const bool want_g = (ORD == ORD_DW) && (p.all_terms || (p.terms && flag_g(n1, n2, n3)));
+    const bool want_h = (ORD == ORD_DW) && (p.all_terms || (p.terms && flag_h(n1, n2, n3)));
+    const bool cplx = ORD != ORD_DW || want_g || want_h;
+    // raised-cosine knees and 1/(beta R) of the three shapes (rc_f)
+    const float ra1 = (float)(0.5 * (1.0 - be) * g.R1), ra2 = (float)(0.5 * (1.0 - be) * g.R2);
+    const float ra3 = (float)(0.5 * (1.0 - be) * g.R3);
+    const float ri1 = be > 0.0 ? (float)(1.0 / (be * g.R1)) : 0.0f, ri2 = be > 0.0 ? (float)(1.0 / (be * g.R2)) : 0.0f;
+    const float ri3 = be > 0.0 ? (float)(1.0 / (be * g.R3)) : 0.0f;
+    const float nu3f = (float)g.nu3;
+    float dsum = 0.0f, csum = 0.0f, hre = 0.0f, him = 0.0f;
+    for (int base = 0; base < rows; base += 32) {
+      const int row = base + lane;
+      if (row >= rows) continue;
+      int qo = 0;
+      while (ocum[qo + 1] <= row) ++qo;
+      double o, wod;
+      piece_node(opc[qo], row - ocum[qo], p.glx_all, p.glw_all, o, wod);
+      double m;
+      RPiece ipc[kInnerPieces];
+      const int nip = ridge_inner_pieces<ORD>(g, o, n, n_min, ipc, m);
+      if (nip == 0) continue;
+      const float wo = (float)wod;
+      const float hout = (float)(ORD == ORD_DW ? rc_shape(o, g.R3, be) : (ORD == ORD_E ? rc_shape(o, g.R2, be)
+                                                                                       : rc_shape(o, g.R1, be)));
+      if (ORD == ORD_DW) {
+        const float f3 = nu3f + (float)o;
+        for (int k = 0; k < K; ++k) ck_s[k * 32 + lane] = p.seg.ck_f[k] * ex2_approx(-p.seg.zeta_f[k] * f3);
+      }
+      const float* col = ck_s + lane;
+      float gre = 0.0f, gim = 0.0f;  // the row's inner sum (G of DW, E, F)
+      for (int ip = 0; ip < nip; ++ip) {
+        const PieceC pc = piece_consts<ORD>(p, g, ipc[ip], o, m, G0, G1, Kf, invK);
+        for (int j0 = 0; j0 < pc.m; j0 += kGroup) {
+          float p_[kGroup], b1_[kGroup], b2_[kGroup], f3_[kGroup];
+          float wm1_[kGroup], wi_[kGroup], chi_[kGroup], phi_[kGroup], wD_[kGroup], wG_[kGroup], wH_[kGroup];
+#pragma unroll
+          for (int e = 0; e < kGroup; ++e) {
+            const int j = j0 + e;
+            const bool valid = j < pc.m;
+            const int jj = pc.goff + (valid ? j : pc.m - 1);  // a repeated node of weight 0 pads the group
+            const float xh = p.glxh_all[jj], wj = p.glwf_all[jj];
+            float yh, yl, wn;
+            if (pc.graded) {
+              const float tau = fmaf(pc.T2, xh, pc.T2);
+              yh = pc.h * sinhf(tau);
+              yl = 0.0f;
+              wn = pc.wsc * wj * coshf(tau);
+            } else {
+              yh = xh;
+              yl = p.glxl_all[jj];
+              wn = pc.wsc * wj;
+            }
+            wn = valid ? wn : 0.0f;
+            const float y2h = yh * yh;
+            const float y2l = fmaf(2.0f * yh, yl, fmaf(yh, yh, -y2h));
+            float th, ph;
+            point_phase(pc.qa, pc.qb, make_float4(yh, yl, y2h, y2l), y2h * yh, Kf, invK, th, ph);
+            // w = r e^{2 pi i th} from the half angle (keeps w - 1 accurate)
+            const float ah = pi_f * th;
+            const float sh = __sinf(ah), chh = __cosf(ah);
+            const float t2r = m2r * sh;
+            const float wm1 = fmaf(t2r, sh, -one_m_r);
+            p_[e] = fmaf(2.0f, wm1, 2.0f);
+            wm1_[e] = wm1;
+            wi_[e] = -t2r * chh;
+            phi_[e] = ph;
+            chi_[e] = fmaf(pc.a1, yh, pc.a0) * fmaf(pc.b1, yh, pc.b0) * fmaf(pc.k1, yh, pc.k0);
+            const float u = fmaf(pc.u1, yh, pc.u0), v = fmaf(pc.v1, yh, pc.v0), w = fmaf(pc.w1, yh, pc.w0);
+            const float h1 = rc_f(u, ra1, ri1), h2 = rc_f(v, ra2, ri2);
+            const float h3 = ORD == ORD_DW ? hout : rc_f(w, ra3, ri3);
+            wD_[e] = wo * wn * h1 * h2 * h3;
+            wH_[e] = wo * wn * sqrtf(h1 * h2 * h3);
+            wG_[e] = wn * (ORD == ORD_DW ? sqrtf(h1 * h2) : (ORD == ORD_E ? sqrtf(h1 * h3) : sqrtf(h2 * h3)));
+            f3_[e] = nu3f + w;
+            b1_[e] = 0.0f;
+            b2_[e] = 0.0f;
+          }
+          // ---- segment sum, b_k = c_k + p b_{k+1} - q b_{k+2}, k = K-1 .. 0
+          if (ORD == ORD_DW) {
+            f32x2 pp[kGroup / 2], b1p[kGroup / 2], b2p[kGroup / 2];
+#pragma unroll
+            for (int a = 0; a < kGroup / 2; ++a) {
+              pp[a] = pack2(p_[2 * a], p_[2 * a + 1]);
+              b1p[a] = 0ull;
+              b2p[a] = 0ull;
+            }
+            const f32x2 nq2 = pack2(-q, -q);
+#pragma unroll 4
+            for (int k = K - 1; k >= 0; --k) {
+              const float c = col[k * 32];
+              const f32x2 cc = pack2(c, c);
+#pragma unroll
+              for (int a = 0; a < kGroup / 2; ++a) {
+                const f32x2 nb = ffma2(pp[a], b1p[a], ffma2(nq2, b2p[a], cc));
+                b2p[a] = b1p[a];
+                b1p[a] = nb;
+              }
+            }
+#pragma unroll
+            for (int a = 0; a < kGroup / 2; ++a) {
+              unpack2(b1p[a], b1_[2 * a], b1_[2 * a + 1]);
+              unpack2(b2p[a], b2_[2 * a], b2_[2 * a + 1]);
+            }
+          } else {
+            // c_k per point (f3 varies along the row)
+#pragma unroll 2
+            for (int k = K - 1; k >= 0; --k) {
+              const float ck = p.seg.ck_f[k], zk = p.seg.zeta_f[k];
+#pragma unroll
+              for (int e = 0; e < kGroup; ++e) {
+                const float c = ck * ex2_approx(-zk * f3_[e]);
+                const float bn = fmaf(p_[e], b1_[e], fmaf(-q, b2_[e], c));
+                b2_[e] = b1_[e];
+                b1_[e] = bn;
+              }
+            }
+          }
+          // ---- mu, Upsilon / gamma and the sums
+#pragma unroll
+          for (int e = 0; e < kGroup; ++e) {
+            const float wm1 = wm1_[e], wi = wi_[e], chi = chi_[e];
+            const float sre = fmaf(-(wm1 + 1.0f), b2_[e], b1_[e]);  // b_0 - conj(w) b_1
+            const float sim = wi * b2_[e];
+            const float inv = rcp_approx(fmaf(chi, chi, alpha2));    // (w - 1)/(i chi - alpha)
+            const float qr = fmaf(-alpha, wm1, chi * wi) * inv;
+            const float qi = fmaf(-chi, wm1, -alpha * wi) * inv;
+            const float mre = fmaf(sre, qr, -sim * qi);
+            const float mim = fmaf(sre, qi, sim * qr);
+            const float x = pi_f * phi_[e];
+            const float ratio = array_ratio(x, N);
+            if (!cplx) {
+              dsum = fmaf(wD_[e], fmaf(mre, mre, mim * mim) * (ratio * ratio), dsum);
+            } else {
+              const float ang = (N - 1.0f) * x;
+              const float sp = __sinf(ang), cp = __cosf(ang);
+              const float yre = ratio * fmaf(mre, cp, -mim * sp);
+              const float yim = ratio * fmaf(mre, sp, mim * cp);
+              if (ORD == ORD_DW) {
+                dsum = fmaf(wD_[e], fmaf(yre, yre, yim * yim), dsum);
+                hre = fmaf(wH_[e], yre, hre);
+                him = fmaf(wH_[e], yim, him);
+              }
+              gre = fmaf(wG_[e], yre, gre);
+              gim = fmaf(wG_[e], yim, gim);
+            }
+          }
+        }
+      }
+      if (ORD != ORD_DW || want_g) csum = fmaf(wo * hout, fmaf(gre, gre, gim * gim), csum);
+    }
+    for (int o_ = 16; o_ > 0; o_ >>= 1) {
+      dsum += __shfl_xor_sync(0xffffffffu, dsum, o_);
+      csum += __shfl_xor_sync(0xffffffffu, csum, o_);
+      hre += __shfl_xor_sync(0xffffffffu, hre, o_);
+      him += __shfl_xor_sync(0xffffffffu, him, o_);
+    }
+    if (lane == 0) {
+      double cf[5];
+      term_coefs(ch.R[coi], g.R1, g.R2, g.R3, cf);
+      const double g2 = (double)cst.g2;
+      if (ORD == ORD_DW) {
+        terms[isl] = (float)(cf[0] * g2 * dsum);
+        if (want_g) terms[3 * n_isl + isl] = (float)(cf[3] * g2 * csum);
+        if (want_h) terms[4 * n_isl + isl] = (float)(cf[4] * g2 * ((double)hre * hre + (double)him * him));
+      } else {
+        terms[(ORD == ORD_E ? 1 : 2) * n_isl + isl] = (float)(cf[ORD == ORD_E ? 1 : 2] * g2 * csum);
+      }
+    }
+    __syncwarp();  // the outer pieces are rewritten for the next island
+  }
+}
+
+template <int ORD>
+cudaError_t launch_ord(const LinkParams& p, const uint64_t* keys, const uint32_t* list, long long n_items,
+                       float* terms, long long n_isl, cudaStream_t st) {
+  if (n_items <= 0) return cudaSuccess;
+  const size_t smem = ORD == ORD_DW ? (size_t)p.seg.K * 32 * sizeof(float) : 0;
+  static std::atomic<unsigned long long> attr_done{0};  // per device
+  if (smem > 40 * 1024)
+    if (cudaError_t e = opt_in_smem(integrate_ridge_fp32c_kernel<ORD>, (int)(kMaxK * 32 * sizeof(float)), attr_done))
+      return e;
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  long long blocks = (long long)sms * 16;
+  if (blocks > n_items) blocks = n_items;
+  const double g0 = 2.0 * kPi * p.L * p.beta2, g1 = 2.0 * kPi * kPi * p.L * p.beta3;
+  const float g0h = (float)g0, g1h = (float)g1;
+  const Df G0 = {g0h, (float)(g0 - (double)g0h)}, G1 = {g1h, (float)(g1 - (double)g1h)};
+  integrate_ridge_fp32c_kernel<ORD><<<(unsigned)blocks, 32, smem, st>>>(p, keys, list, n_items, terms, n_isl, G0, G1);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_ridge_fp32c(int ord, const LinkParams& p, const uint64_t* keys, const uint32_t* list,
+                               long long n_items, float* terms, long long n_isl, cudaStream_t st) {
+  if (p.n_types != 1 || p.mu_form != MU_SEGMENT) return cudaErrorInvalidValue;  // refused by the option checks
+  if (ord == ORD_DW) return launch_ord<ORD_DW>(p, keys, list, n_items, terms, n_isl, st);
+  if (ord == ORD_E) return launch_ord<ORD_E>(p, keys, list, n_items, terms, n_isl, st);
+  return launch_ord<ORD_F>(p, keys, list, n_items, terms, n_isl, st);
+}
+
+}  // namespace egn

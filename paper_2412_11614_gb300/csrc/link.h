@@ -137,6 +137,9 @@ struct egn_link {
   egn::GlTables gl{};
   const double* gl_all_x = nullptr;  // every order 1..n (the ridge rule's pieces), inside d_gl
   const double* gl_all_w = nullptr;
+  const float* gl_all_xh = nullptr;  // FP32 head, tail and weight of the same nodes
+  const float* gl_all_xl = nullptr;
+  const float* gl_all_wf = nullptr;
   int fp32c_kp = 4;  // tuning: points per thread of the FP32C D/G/H pass
   int rule = egn::RULE_GL;  // node rule (egn_set_node_rule)
   int ridge_n_min = 4;

@@ -1,6 +1,6 @@
 """The ridge-resolving node rule on the GPU (egn_set_node_rule(EGN_RULE_RIDGE),
-FP64 path) against the oracle's ridge rule (oracle/ridge_rule.py) at the same
-node counts, through the C ABI.
+FP64 and FP32C paths) against the oracle's ridge rule (oracle/ridge_rule.py) at
+the same node counts, through the C ABI.
 
 The two sides share no code: the oracle's rule is numpy around the oracle's C
 integrand; the kernel forms the same cuts, pieces and sinh-graded nodes on the
@@ -11,7 +11,9 @@ every island; the two differ by rounding).  The rule converges where the
 configured one does not: on the 5-channel link 16 and 32 nodes per piece agree
 within 0.003 dB for the GN part and 0.04 dB with the EGN corrections, where the
 configured rule moves by more than 0.3 dB from 32 x 32 to 64 x 64 (the narrow
-ridges of |mu|^2)."""
+ridges of |mu|^2).  FP32C (links of identical spans): every term within 3e-4
+of the oracle's relative to itself plus 3e-5 of the largest term of its kind in
+the COI, the bars of the configured rule's FP32C parity, and eta within 1e-3 dB."""
 import numpy as np
 import pytest
 
@@ -87,6 +89,59 @@ def test_ridge_eta_matches_oracle(egn, oracle_mod, workloads, RR, case):
     ln.close()
 
 
+@pytest.mark.parametrize("order", [8, 16])
+def test_ridge_fp32c_island_terms_match_oracle(egn, oracle_mod, workloads, RR, order):
+    wl = workloads.config_small(gl_order=order)
+    ln = _ridge_link(egn, wl)
+    pb = oracle_mod.Problem(wl, gl_order=order)
+    rule = RR.RidgeRule(pb)
+    opts = egn.make_opts(gl_order=order, precision=egn.EGN_PREC_FP32C)
+    for n in (0, 2):
+        isl = [(n, int(a), int(b), int(c)) for a, b, c in pb.islands(n)]
+        got = ln.island_terms(opts, isl, all_terms=True)
+        want = np.array([rule.terms(*t, order) for t in isl])
+        scale = np.max(np.abs(want), axis=0) + 1e-300
+        err = np.abs(got - want)
+        assert np.all(err <= 3e-4 * np.abs(want) + 3e-5 * scale), (n, np.max(err / (np.abs(want) + 1e-300), axis=0))
+    ln.close()
+
+
+@pytest.mark.parametrize("case", ["5ch", "8ch_3spans", "16ch_beta0"])
+def test_ridge_fp32c_eta_matches_oracle(egn, oracle_mod, workloads, RR, case):
+    """eta of every channel in FP32C; 8 channels over three identical spans with
+    four modulation formats; 16 channels without roll-off."""
+    if case == "5ch":
+        wl, order = workloads.config_small(gl_order=16), 16
+    elif case == "8ch_3spans":
+        wl, order = workloads.config_small(n_ch=8, gl_order=8, n_spans=3), 8
+        wl.formats = ["QPSK", "16QAM", "64QAM", "GAUSS"] * 2
+    else:
+        wl, order = workloads.config_small(n_ch=16, gl_order=8), 8
+        wl.rolloff = 0.0
+    ln = _ridge_link(egn, wl)
+    eta, _ = ln.nli_eta(egn.make_opts(gl_order=order, precision=egn.EGN_PREC_FP32C))
+    pb = oracle_mod.Problem(wl, gl_order=order)
+    rule = RR.RidgeRule(pb)
+    want = np.array([rule.pnli(n, order) for n in range(wl.n_ch)]) / np.asarray(wl.launch_power_w) ** 3
+    db = np.abs(10 * np.log10(eta / want))
+    assert np.max(db) < 1e-3, db
+    ln.close()
+
+
+def test_ridge_fp32c_matches_fp64_on_a_wide_link(egn, workloads):
+    """40 channels of the 75 GHz C+L grid (2.9 THz wide) over ten spans: FP32C
+    against the FP64 ridge kernel on every channel within 1e-3 dB (the narrowest
+    ridges: their half-widths fall as 1 / |f2 - f|)."""
+    wl = workloads.config_cl(n_ch=40)
+    ln = _ridge_link(egn, wl)
+    o = lambda pr: egn.make_opts(gl_order=8, dz_km=wl.dz_km, precision=pr)  # noqa: E731
+    e64, _ = ln.nli_eta(o(egn.EGN_PREC_FP64))
+    e32, _ = ln.nli_eta(o(egn.EGN_PREC_FP32C))
+    db = np.abs(10 * np.log10(e32 / e64))
+    assert np.max(db) < 1e-3, db
+    ln.close()
+
+
 def test_ridge_rule_converges_where_the_configured_rule_does_not(egn, workloads):
     """GN part: 16 and 32 nodes per piece within 0.003 dB; with the EGN corrections
     (which need more nodes) within 0.04 dB; the configured rule moves by more than
@@ -123,11 +178,18 @@ def test_ridge_rule_in_a_batch_equals_single_links(egn, workloads):
 
 def test_ridge_rule_refusals(egn, workloads):
     import torch
+    wh = workloads.config_small(n_ch=2, gl_order=8, n_spans=2)
+    wh.spans[1].length_m = 70e3
+    lh = _ridge_link(egn, wh)  # spans differ: FP64 only
+    with pytest.raises(egn.EgnError) as ei:
+        lh.nli_eta(egn.make_opts(gl_order=8, precision=egn.EGN_PREC_FP32C))
+    assert ei.value.status == egn.EGN_E_UNSUPPORTED
+    lh.close()
     wl = workloads.config_small(n_ch=2, gl_order=8)
     ln = _ridge_link(egn, wl)
     with pytest.raises(egn.EgnError) as ei:
-        ln.nli_eta(egn.make_opts(gl_order=8, precision=egn.EGN_PREC_FP32C))
-    assert ei.value.status == egn.EGN_E_UNSUPPORTED
+        ln.nli_eta(egn.make_opts(gl_order=65, precision=egn.EGN_PREC_FP32C))
+    assert ei.value.status == egn.EGN_E_INVALID_ARG
     with pytest.raises(egn.EgnError) as ei:
         ln.nli_eta(egn.make_opts(gl_order=65, precision=egn.EGN_PREC_FP64))
     assert ei.value.status == egn.EGN_E_INVALID_ARG
