@@ -299,9 +299,11 @@ def flops_per_point(precision: str, K: int) -> float:
     return 4.0 * K
 
 
-def timed_evals(ln, opts, n_ch, stream, flush, steps: int, warm: int):
+def timed_evals(ln, opts, n_ch, stream, flush, steps: int, warm: int, detail: dict = None):
     """Device ms per evaluation (egn_nli_eta_device, CUDA events on `stream`, L2
-    flushed before each) and the last evaluation's eta."""
+    flushed before each) and the last evaluation's eta.  With `detail`, also the
+    per-evaluation times and the last evaluation's per-stage times (profiling is
+    switched on for the evaluations)."""
     import torch
     ws = torch.empty(ln.workspace_size(opts), dtype=torch.uint8, device="cuda")
     eta = torch.empty(n_ch, dtype=torch.float64, device="cuda")
@@ -317,6 +319,9 @@ def timed_evals(ln, opts, n_ch, stream, flush, steps: int, warm: int):
             e1.synchronize()
             if i >= warm:
                 times.append(e0.elapsed_time(e1))
+    if detail is not None:
+        detail["ms_each"] = times
+        detail["stage_ms"] = {k: float(v) for k, v in ln.last_timings().items()}
     return statistics.mean(times), eta.cpu().numpy()
 
 
@@ -349,11 +354,13 @@ def fp64_denominator(args, wl, ln, eta32, value, stream, flush) -> dict:
         ln.set_node_rule(egn.EGN_RULE_RIDGE, 4)
         orr = egn.make_opts(gl_order=args.ridge_nodes, dz_km=wl.dz_km, precision=egn.EGN_PREC_FP64,
                             terms=egn.EGN_TERMS_EGN, stream=stream.cuda_stream)
-        msr, etar = timed_evals(ln, orr, n_ch, stream, flush, steps=1, warm=1)
+        ln.set_profiling(True)
+        det64, det32 = {}, {}
+        msr, etar = timed_evals(ln, orr, n_ch, stream, flush, steps=1, warm=1, detail=det64)
         # and in FP32C (the same rule; identical spans): time and distance from the FP64 result
         orr32 = egn.make_opts(gl_order=args.ridge_nodes, dz_km=wl.dz_km, precision=egn.EGN_PREC_FP32C,
                               terms=egn.EGN_TERMS_EGN, stream=stream.cuda_stream)
-        msr32, etar32 = timed_evals(ln, orr32, n_ch, stream, flush, steps=3, warm=1)
+        msr32, etar32 = timed_evals(ln, orr32, n_ch, stream, flush, steps=3, warm=1, detail=det32)
         ln.set_node_rule(egn.EGN_RULE_GL)
         dr = 10 * np.log10(eta64 / etar)
         d32 = np.abs(10 * np.log10(etar32 / etar))
@@ -363,7 +370,9 @@ def fp64_denominator(args, wl, ln, eta32, value, stream, flush) -> dict:
                                                      "max": float(dr.max()), "edge": float(dr[0]),
                                                      "centre": float(dr[n_ch // 2])},
                              "eta_db_sample": [float(10 * np.log10(x)) for x in etar[:: 30]],
+                             "stage_ms": det64["stage_ms"],
                              "fp32c": {"ms_per_step": msr32, "value": n_ch / (msr32 * 1e-3), "unit": UNIT,
+                                       "ms_each": det32["ms_each"], "stage_ms": det32["stage_ms"],
                                        "speedup_vs_fp64": msr / msr32, "max_db_vs_fp64": float(d32.max()),
                                        "mean_db_vs_fp64": float(d32.mean())}}
     if args.no_sweep:

@@ -348,7 +348,7 @@ __global__ void __launch_bounds__(32) integrate_fp64_kernel(LinkParams p, const 
   }
 }
 
-// The ridge-resolving node rule (egn_set_node_rule(EGN_RULE_RIDGE), ridge_rule.cuh):
+// one warp per island as in the configured rule: the warp forms the outer pieces,
 // one warp per island as in the configured rule: lane 0 forms the outer pieces,
 // every lane then takes outer nodes ("rows") and walks its row's inner pieces.
 template <int ORD>
@@ -358,7 +358,7 @@ __global__ void __launch_bounds__(32) integrate_ridge_kernel(LinkParams p, const
   extern __shared__ double ck_s[];  // [K][32] c_k row tables (DW order), as in the configured rule
   __shared__ RPiece opc[kOuterPieces];
   __shared__ int ocum[kOuterPieces + 1];
-  __shared__ int n_op;
+  __shared__ double osx[kOuterCuts], osh[kOuterCuts];  // scratch of ridge_outer_pieces_warp
   const int lane = threadIdx.x;
   const bool tables = p.n_types <= kMaxTypes && p.mu_form == MU_SEGMENT;
   int koff[kMaxTypes];
@@ -376,18 +376,8 @@ __global__ void __launch_bounds__(32) integrate_ridge_kernel(LinkParams p, const
     const RidgeIsland g = ridge_island<ORD>(ch, coi, n1, n2, n3, p.rolloff, p.alpha, p.beta2, p.beta3);
     const double f = g.f, nu1 = g.nu1, nu2 = g.nu2, nu3 = g.nu3;
     const double R = ch.R[coi], R1 = g.R1, R2 = g.R2, R3 = g.R3;
-    if (lane == 0) {
-      const int np = ridge_outer_pieces<ORD>(g, n, n_min, opc);
-      int cum = 0;
-      for (int q = 0; q < np; ++q) {
-        ocum[q] = cum;
-        cum += opc[q].m;
-      }
-      ocum[np] = cum;
-      n_op = np;
-    }
-    __syncwarp();
-    const int npc = n_op, rows = ocum[npc];
+    const int npc = ridge_outer_pieces_warp<ORD>(g, n, n_min, opc, ocum, osx, osh, lane);
+    const int rows = ocum[npc];
     const bool want_g = (ORD == ORD_DW) && (p.all_terms || (p.terms && flag_g(n1, n2, n3)));
     const bool want_h = (ORD == ORD_DW) && (p.all_terms || (p.terms && flag_h(n1, n2, n3)));
     double dsum = 0.0, csum = 0.0;

@@ -2,7 +2,7 @@
 // FP32 arithmetic of the fast path (FP32C), for links of identical spans.
 //
 // Work decomposition: one warp (a 32-thread CTA) per island, as in the FP64 form
-// of the rule.  Lane 0 forms the island's outer pieces (FP64).  The lanes then
+// of the rule.  The warp forms the island's outer pieces (FP64).  The lanes then
 // take outer nodes ("rows") 32 at a time: each lane forms its row's inner pieces
 // (FP64) and, in the DW order, the row's c_k = C_k e^{-zeta_k f3} in its column of
 // a [K][32] shared table, and walks its row's nodes in groups of four points,
@@ -15,10 +15,14 @@
 // polynomial in y whose coefficients are formed per piece in double-float
 // (row_phase, Q0 reduced modulo K), and every point's phase is reduced exactly as
 // on the configured rule (point_phase).  On a graded piece f1 - f (or f2 - f) is
-// the offset itself plus a constant that vanishes to FP64 rounding, so chi near
-// the ridge keeps full relative precision.  The graded offsets are formed in FP32
-// (sinhf, a few ulp): a node lies within ~1e-7 of its FP64 offset from the ridge,
-// a perturbation of the rule, not of the integrand.
+// the offset itself plus a constant that vanishes to double-float rounding, so chi
+// near the ridge keeps full relative precision.  The graded offsets are formed in
+// FP32 (sinhf, a few ulp), and so are the ridge half-widths that scale them: a
+// node lies within ~1e-7 of its FP64 offset from the ridge, a perturbation of the
+// rule, not of the integrand.  The cuts, their order and the node counts are the
+// FP64 rule's (plain_nodes takes a count from FP32 only where it is unambiguous);
+// GB300 runs FP64 at 1/64 of the FP32 rate, so the per-row and per-piece
+// arithmetic beyond the cuts is double-float.
 //
 // Everything past the node (w, the segment sum, mu, the phased array, the sums)
 // is the arithmetic of the configured rule's FP32C passes.
@@ -47,59 +51,64 @@ struct PieceC {
   bool graded;
 };
 
-// Frequencies of an island relative to the COI: F1 = nu1 - f, F2 = nu2 - f, S12 = nu1 + nu2.
+// The island's frequencies relative to the COI as double-floats: F1 = nu1 - f,
+// F2 = nu2 - f, S12 = nu1 + nu2; the FP32 constants of chi.
+struct IslandDf {
+  Df F1, F2, S12;
+  float k4, b2, pib3;  // 4 pi^2, beta2, pi beta3
+};
+
+// Constants of inner piece q of the row at outer node o (od, md: o and the
+// coupling centre m as double-floats).  Per piece only the ends are converted
+// from FP64; the rest is double-float and FP32 arithmetic.
 template <int ORD>
-__device__ __forceinline__ PieceC piece_consts(const LinkParams& p, const RidgeIsland& g, const RPiece& q, double o,
-                                               double m, Df G0, Df G1, float Kf, float invK) {
+__device__ __forceinline__ PieceC piece_consts(const IslandDf& isd, const RPiece& q, Df od, Df md, Df G0, Df G1,
+                                               float Kf, float invK) {
   PieceC c;
   c.graded = q.ha > 0.0 || q.hb > 0.0;
   c.m = q.m;
   c.goff = q.m * (q.m - 1) / 2;
-  double t0, t1;
+  Df t0, t1;
   if (c.graded) {
-    const double h = q.ha > 0.0 ? q.ha : q.hb;
-    t0 = q.ha > 0.0 ? q.a : q.b;
-    t1 = q.ha > 0.0 ? 1.0 : -1.0;
-    const float T = asinhf((float)((q.b - q.a) / h));
-    c.T2 = 0.5f * T;
-    c.h = (float)h;
+    const bool at_a = q.ha > 0.0;
+    c.h = (float)(at_a ? q.ha : q.hb);
+    t0 = df_of(at_a ? q.a : q.b);
+    t1 = {at_a ? 1.0f : -1.0f, 0.0f};
+    c.T2 = 0.5f * asinhf(__fdividef((float)(q.b - q.a), c.h));
     c.wsc = c.T2 * c.h;
   } else {
-    t0 = 0.5 * (q.a + q.b);
-    t1 = 0.5 * (q.b - q.a);
+    const Df A = df_of(q.a), B = df_of(q.b);
+    t0 = dhalf(dadd(A, B));
+    t1 = dhalf(dsub(B, A));
     c.T2 = 0.0f;
     c.h = 0.0f;
-    c.wsc = (float)t1;
+    c.wsc = dval(t1);
   }
-  const double F1 = g.nu1 - g.f, F2 = g.nu2 - g.f, S12 = g.nu1 + g.nu2;
-  double a0, a1, b0, b1, s0, s1, u0, u1, v0, v1, w0, w1;
-  if (ORD == ORD_DW) {  // u = t, v = m - t, w = o
-    u0 = t0; u1 = t1; v0 = m - t0; v1 = -t1; w0 = o; w1 = 0.0;
-    s0 = S12 + m; s1 = 0.0;
-  } else if (ORD == ORD_E) {  // u = t, v = o, w = t - m
-    u0 = t0; u1 = t1; v0 = o; v1 = 0.0; w0 = t0 - m; w1 = t1;
-    s0 = S12 + o + t0; s1 = t1;
-  } else {  // u = o, v = t, w = t - m
-    u0 = o; u1 = 0.0; v0 = t0; v1 = t1; w0 = t0 - m; w1 = t1;
-    s0 = S12 + o + t0; s1 = t1;
-  }
-  a0 = F1 + u0; a1 = u1;
-  b0 = F2 + v0; b1 = v1;
+  const Df zero = {0.0f, 0.0f};
   RowGeo r;
-  r.a0 = df_of(a0); r.a1 = df_of(a1);
-  r.b0 = df_of(b0); r.b1 = df_of(b1);
-  r.s0 = df_of(s0); r.s1 = df_of(s1);
+  Df u0, u1, v0, v1, w0, w1;
+  if (ORD == ORD_DW) {  // u = t, v = m - t, w = o
+    u0 = t0; u1 = t1; v0 = dsub(md, t0); v1 = dneg(t1); w0 = od; w1 = zero;
+    r.s0 = dadd(isd.S12, md); r.s1 = zero;
+  } else if (ORD == ORD_E) {  // u = t, v = o, w = t - m
+    u0 = t0; u1 = t1; v0 = od; v1 = zero; w0 = dsub(t0, md); w1 = t1;
+    r.s0 = dadd(isd.S12, dadd(od, t0)); r.s1 = t1;
+  } else {  // u = o, v = t, w = t - m
+    u0 = od; u1 = zero; v0 = t0; v1 = t1; w0 = dsub(t0, md); w1 = t1;
+    r.s0 = dadd(isd.S12, dadd(od, t0)); r.s1 = t1;
+  }
+  r.a0 = dadd(isd.F1, u0); r.a1 = u1;
+  r.b0 = dadd(isd.F2, v0); r.b1 = v1;
   const RowPhase ph = row_phase(r, G0, G1, Kf, invK);
   c.qa = make_float4(ph.Q0r.hi, ph.Q0r.lo, ph.Q1.hi, ph.Q1.lo);
   c.qb = make_float4(ph.Q2.hi, ph.Q2.lo, ph.Q3, ph.Q0r.hi - rint_fast(ph.Q0r.hi));
-  c.a0 = (float)a0; c.a1 = (float)a1;
-  c.b0 = (float)b0; c.b1 = (float)b1;
-  const double k4 = 4.0 * kPi * kPi;
-  c.k0 = (float)(k4 * (p.beta2 + kPi * p.beta3 * s0));
-  c.k1 = (float)(k4 * kPi * p.beta3 * s1);
-  c.u0 = (float)u0; c.u1 = (float)u1;
-  c.v0 = (float)v0; c.v1 = (float)v1;
-  c.w0 = (float)w0; c.w1 = (float)w1;
+  c.a0 = dval(r.a0); c.a1 = dval(r.a1);
+  c.b0 = dval(r.b0); c.b1 = dval(r.b1);
+  c.k0 = isd.k4 * fmaf(isd.pib3, dval(r.s0), isd.b2);
+  c.k1 = isd.k4 * isd.pib3 * dval(r.s1);
+  c.u0 = dval(u0); c.u1 = dval(u1);
+  c.v0 = dval(v0); c.v1 = dval(v1);
+  c.w0 = dval(w0); c.w1 = dval(w1);
   return c;
 }
 
@@ -111,7 +120,7 @@ __global__ void __launch_bounds__(32) integrate_ridge_fp32c_kernel(LinkParams p,
   extern __shared__ float ck_s[];  // DW: [K][32], the c_k of each lane's row
   __shared__ RPiece opc[kOuterPieces];
   __shared__ int ocum[kOuterPieces + 1];
-  __shared__ int n_op;
+  __shared__ double osx[kOuterCuts], osh[kOuterCuts];  // scratch of ridge_outer_pieces_warp
   const int lane = threadIdx.x;
   const DwConsts cst = dw_consts(p);
   const int K = cst.K;
@@ -126,18 +135,8 @@ __global__ void __launch_bounds__(32) integrate_ridge_fp32c_kernel(LinkParams p,
     int coi, n1, n2, n3;
     unpack_key(keys[isl], coi, n1, n2, n3);
     const RidgeIsland g = ridge_island<ORD>(ch, coi, n1, n2, n3, p.rolloff, p.alpha, p.beta2, p.beta3);
-    if (lane == 0) {
-      const int np = ridge_outer_pieces<ORD>(g, n, n_min, opc);
-      int cum = 0;
-      for (int i = 0; i < np; ++i) {
-        ocum[i] = cum;
-        cum += opc[i].m;
-      }
-      ocum[np] = cum;
-      n_op = np;
-    }
-    __syncwarp();
-    const int npc = n_op, rows = ocum[npc];
+    const int npc = ridge_outer_pieces_warp<ORD>(g, n, n_min, opc, ocum, osx, osh, lane);
+    const int rows = ocum[npc];
     const bool want_g = (ORD == ORD_DW) && (p.all_terms || (p.terms && flag_g(n1, n2, n3)));
     const bool want_h = (ORD == ORD_DW) && (p.all_terms || (p.terms && flag_h(n1, n2, n3)));
     const bool cplx = ORD != ORD_DW || want_g || want_h;
@@ -147,6 +146,15 @@ __global__ void __launch_bounds__(32) integrate_ridge_fp32c_kernel(LinkParams p,
     const float ri1 = be > 0.0 ? (float)(1.0 / (be * g.R1)) : 0.0f, ri2 = be > 0.0 ? (float)(1.0 / (be * g.R2)) : 0.0f;
     const float ri3 = be > 0.0 ? (float)(1.0 / (be * g.R3)) : 0.0f;
     const float nu3f = (float)g.nu3;
+    IslandDf isd;
+    isd.F1 = df_of(g.nu1 - g.f);
+    isd.F2 = df_of(g.nu2 - g.f);
+    isd.S12 = df_of(g.nu1 + g.nu2);
+    isd.k4 = (float)(4.0 * kPi * kPi);
+    isd.b2 = (float)p.beta2;
+    isd.pib3 = (float)(kPi * p.beta3);
+    const float rao = ORD == ORD_DW ? ra3 : (ORD == ORD_E ? ra2 : ra1);
+    const float rio = ORD == ORD_DW ? ri3 : (ORD == ORD_E ? ri2 : ri1);
     float dsum = 0.0f, csum = 0.0f, hre = 0.0f, him = 0.0f;
     for (int base = 0; base < rows; base += 32) {
       const int row = base + lane;
@@ -157,19 +165,19 @@ __global__ void __launch_bounds__(32) integrate_ridge_fp32c_kernel(LinkParams p,
       piece_node(opc[qo], row - ocum[qo], p.glx_all, p.glw_all, o, wod);
       double m;
       RPiece ipc[kInnerPieces];
-      const int nip = ridge_inner_pieces<ORD>(g, o, n, n_min, ipc, m);
+      const int nip = ridge_inner_pieces<ORD, true>(g, o, n, n_min, ipc, m);
       if (nip == 0) continue;
       const float wo = (float)wod;
-      const float hout = (float)(ORD == ORD_DW ? rc_shape(o, g.R3, be) : (ORD == ORD_E ? rc_shape(o, g.R2, be)
-                                                                                       : rc_shape(o, g.R1, be)));
+      const Df od = df_of(o), md = df_of(m);
+      const float hout = rc_f(dval(od), rao, rio);
       if (ORD == ORD_DW) {
-        const float f3 = nu3f + (float)o;
+        const float f3 = nu3f + dval(od);
         for (int k = 0; k < K; ++k) ck_s[k * 32 + lane] = p.seg.ck_f[k] * ex2_approx(-p.seg.zeta_f[k] * f3);
       }
       const float* col = ck_s + lane;
       float gre = 0.0f, gim = 0.0f;  // the row's inner sum (G of DW, E, F)
       for (int ip = 0; ip < nip; ++ip) {
-        const PieceC pc = piece_consts<ORD>(p, g, ipc[ip], o, m, G0, G1, Kf, invK);
+        const PieceC pc = piece_consts<ORD>(isd, ipc[ip], od, md, G0, G1, Kf, invK);
         for (int j0 = 0; j0 < pc.m; j0 += kGroup) {
           float p_[kGroup], b1_[kGroup], b2_[kGroup], f3_[kGroup];
           float wm1_[kGroup], wi_[kGroup], chi_[kGroup], phi_[kGroup], wD_[kGroup], wG_[kGroup], wH_[kGroup];

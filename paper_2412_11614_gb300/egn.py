@@ -278,7 +278,8 @@ class Link:
         _check(lib().egn_set_tuning(self.h, int(param), int(value)))
 
     def set_node_rule(self, rule: int, n_min: int = 4):
-        """egn_set_node_rule: EGN_RULE_GL (default) or EGN_RULE_RIDGE (FP64)."""
+        """egn_set_node_rule: EGN_RULE_GL (default) or EGN_RULE_RIDGE (FP64 on any link, FP32C on links
+        of identical spans)."""
         _check(lib().egn_set_node_rule(self.h, int(rule), int(n_min)))
 
     def set_profiling(self, on: bool):

@@ -66,18 +66,21 @@ def test_autotune_rejects_bad_arguments(egn, workloads):
     assert ei.value.status == egn.EGN_E_INVALID_ARG
 
 
-def test_autotune_rule_against_the_oracle(egn, workloads):
+@pytest.mark.parametrize("prec", ["fp64", "fp32c"])
+def test_autotune_rule_against_the_oracle(egn, workloads, prec):
     """The rule autotuner on the 5-channel link at 0.01 dB: its choice is within
     0.01 dB (plus the reference's own 0.003 dB) of the oracle's ridge rule at 32
     nodes per piece, which lies within 0.002 dB of the converged integral there;
-    the configured 32 x 32 rule is reported 0.3 dB or more away."""
+    the configured 32 x 32 rule is reported 0.3 dB or more away.  In FP32C the
+    autotuner evaluates in FP32C (identical spans)."""
     from oracle import oracle as O, ridge_rule as RR
+    pr = egn.EGN_PREC_FP64 if prec == "fp64" else egn.EGN_PREC_FP32C
     wl = workloads.config_small(gl_order=32)
     ln = egn.link_from_workload(wl)
-    res = ln.autotune_rule(egn.make_opts(gl_order=32, precision=egn.EGN_PREC_FP64), 0.01)
+    res = ln.autotune_rule(egn.make_opts(gl_order=32, precision=pr), 0.01)
     assert res["rule"] == egn.EGN_RULE_RIDGE and res["max_err_db"] <= 0.01
     assert res["configured_err_db"] > 0.3
-    eta, _ = ln.nli_eta(egn.make_opts(gl_order=res["nodes"], precision=egn.EGN_PREC_FP64))
+    eta, _ = ln.nli_eta(egn.make_opts(gl_order=res["nodes"], precision=pr))
     pb = O.Problem(wl, gl_order=8)
     rule = RR.RidgeRule(pb)
     want = np.array([rule.pnli(n, 32) for n in range(wl.n_ch)]) / np.asarray(wl.launch_power_w) ** 3
