@@ -3,10 +3,12 @@
 //
 // Work decomposition: one warp (a 32-thread CTA) per island, as in the FP64 form
 // of the rule.  The warp forms the island's outer pieces (FP64).  The lanes then
-// take outer nodes ("rows") 32 at a time: each lane forms its row's inner pieces
-// (FP64) and, in the DW order, the row's c_k = C_k e^{-zeta_k f3} in its column of
-// a [K][32] shared table, and walks its row's nodes in groups of four points,
-// two per fma.rn.f32x2 in the segment recurrence.
+// take outer nodes ("rows") 32 at a time, one lane per row, and an island's last
+// rows L lanes per row (L a power of two, so that the batch fills the warp): the
+// lanes of a row form its inner pieces (FP64) and, in the DW order, its c_k =
+// C_k e^{-zeta_k f3} in the row's column of a [K][32] shared table, and walk its
+// nodes in groups of four points (the row's groups dealt out to its L lanes), two
+// per fma.rn.f32x2 in the segment recurrence.
 //
 // Per piece the inner coordinate is t = t0 + t1 y, with y the piece variable: the
 // Gauss-Legendre node x_j on a plain piece (t0 its midpoint, t1 its half-length),
@@ -17,9 +19,9 @@
 // on the configured rule (point_phase).  On a graded piece f1 - f (or f2 - f) is
 // the offset itself plus a constant that vanishes to double-float rounding, so chi
 // near the ridge keeps full relative precision.  The graded offsets are formed in
-// FP32 (sinhf, a few ulp), and so are the ridge half-widths that scale them: a
-// node lies within ~1e-7 of its FP64 offset from the ridge, a perturbation of the
-// rule, not of the integrand.  The cuts, their order and the node counts are the
+// FP32 (sinh and cosh from one ex2 and its reciprocal), and so are the ridge
+// half-widths that scale them: a node lies within a few 1e-7 of its FP64 offset
+// from the ridge (or of h), a perturbation of the rule, not of the integrand.  The cuts, their order and the node counts are the
 // FP64 rule's (plain_nodes takes a count from FP32 only where it is unambiguous);
 // GB300 runs FP64 at 1/64 of the FP32 rate, so the per-row and per-piece
 // arithmetic beyond the cuts is double-float.
@@ -156,29 +158,44 @@ __global__ void __launch_bounds__(32) integrate_ridge_fp32c_kernel(LinkParams p,
     const float rao = ORD == ORD_DW ? ra3 : (ORD == ORD_E ? ra2 : ra1);
     const float rio = ORD == ORD_DW ? ri3 : (ORD == ORD_E ? ri2 : ri1);
     float dsum = 0.0f, csum = 0.0f, hre = 0.0f, him = 0.0f;
-    for (int base = 0; base < rows; base += 32) {
-      const int row = base + lane;
-      if (row >= rows) continue;
-      int qo = 0;
-      while (ocum[qo + 1] <= row) ++qo;
-      double o, wod;
-      piece_node(opc[qo], row - ocum[qo], p.glx_all, p.glw_all, o, wod);
-      double m;
+    // Rows in batches of up to 32, L lanes per row: L = 1 while at least 32 rows
+    // are left, else the largest power of two that keeps the batch within the warp
+    // (an island's last rows get several lanes each, which take the node groups of
+    // every piece in turn).
+    for (int base = 0; base < rows;) {
+      const int left = rows - base;
+      int L = 1;
+      while (L < 32 && 2 * L * left <= 32) L <<= 1;
+      const int nrow = min(left, 32 / L);
+      const int rsub = lane / L, lsub = lane & (L - 1);
+      const int row = base + rsub;
+      bool act = rsub < nrow;
+      double o = 0.0, wod = 0.0, m = 0.0;
       RPiece ipc[kInnerPieces];
-      const int nip = ridge_inner_pieces<ORD, true>(g, o, n, n_min, ipc, m);
-      if (nip == 0) continue;
+      int nip = 0;
+      if (act) {
+        int qo = 0;
+        while (ocum[qo + 1] <= row) ++qo;
+        piece_node(opc[qo], row - ocum[qo], p.glx_all, p.glw_all, o, wod);
+        nip = ridge_inner_pieces<ORD, true>(g, o, n, n_min, ipc, m);
+        act = nip > 0;
+      }
       const float wo = (float)wod;
       const Df od = df_of(o), md = df_of(m);
       const float hout = rc_f(dval(od), rao, rio);
+      const int colx = rsub * L;  // the row's column of the c_k table
       if (ORD == ORD_DW) {
-        const float f3 = nu3f + dval(od);
-        for (int k = 0; k < K; ++k) ck_s[k * 32 + lane] = p.seg.ck_f[k] * ex2_approx(-p.seg.zeta_f[k] * f3);
+        if (act) {
+          const float f3 = nu3f + dval(od);
+          for (int k = lsub; k < K; k += L) ck_s[k * 32 + colx] = p.seg.ck_f[k] * ex2_approx(-p.seg.zeta_f[k] * f3);
+        }
+        __syncwarp();
       }
-      const float* col = ck_s + lane;
-      float gre = 0.0f, gim = 0.0f;  // the row's inner sum (G of DW, E, F)
-      for (int ip = 0; ip < nip; ++ip) {
+      const float* col = ck_s + colx;
+      float gre = 0.0f, gim = 0.0f;  // this lane's part of the row's inner sum (G of DW, E, F)
+      for (int ip = 0; act && ip < nip; ++ip) {
         const PieceC pc = piece_consts<ORD>(isd, ipc[ip], od, md, G0, G1, Kf, invK);
-        for (int j0 = 0; j0 < pc.m; j0 += kGroup) {
+        for (int j0 = lsub * kGroup; j0 < pc.m; j0 += L * kGroup) {
           float p_[kGroup], b1_[kGroup], b2_[kGroup], f3_[kGroup];
           float wm1_[kGroup], wi_[kGroup], chi_[kGroup], phi_[kGroup], wD_[kGroup], wG_[kGroup], wH_[kGroup];
 #pragma unroll
@@ -190,9 +207,13 @@ __global__ void __launch_bounds__(32) integrate_ridge_fp32c_kernel(LinkParams p,
             float yh, yl, wn;
             if (pc.graded) {
               const float tau = fmaf(pc.T2, xh, pc.T2);
-              yh = pc.h * sinhf(tau);
+              // sinh and cosh from one exponential: e^tau by ex2, e^-tau by rcp (absolute
+              // error ~2e-7 e^tau: the offset moves by about 1e-7 h near the ridge and
+              // by a few 1e-7 of itself far from it)
+              const float ep = ex2_approx(tau * 1.44269504f), em = rcp_approx(ep);
+              yh = pc.h * (0.5f * (ep - em));
               yl = 0.0f;
-              wn = pc.wsc * wj * coshf(tau);
+              wn = pc.wsc * wj * (0.5f * (ep + em));
             } else {
               yh = xh;
               yl = p.glxl_all[jj];
@@ -294,7 +315,13 @@ __global__ void __launch_bounds__(32) integrate_ridge_fp32c_kernel(LinkParams p,
           }
         }
       }
-      if (ORD != ORD_DW || want_g) csum = fmaf(wo * hout, fmaf(gre, gre, gim * gim), csum);
+      for (int o_ = 1; o_ < L; o_ <<= 1) {  // the row's inner sum over its L lanes
+        gre += __shfl_xor_sync(0xffffffffu, gre, o_);
+        gim += __shfl_xor_sync(0xffffffffu, gim, o_);
+      }
+      if (act && lsub == 0 && (ORD != ORD_DW || want_g)) csum = fmaf(wo * hout, fmaf(gre, gre, gim * gim), csum);
+      if (ORD == ORD_DW) __syncwarp();  // the table is rewritten by the next batch
+      base += nrow;
     }
     for (int o_ = 16; o_ > 0; o_ >>= 1) {
       dsum += __shfl_xor_sync(0xffffffffu, dsum, o_);
