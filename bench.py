@@ -571,18 +571,21 @@ def run_surrogate(args):
     from paper_2412_11614_gb300 import _build, egn, surrogate as S, workloads as W
     _build.build()
     torch.cuda.set_device(0)
-    opts = egn.make_opts(gl_order=32, precision=egn.EGN_PREC_FP32C)
+    ridge = args.sur_rule == "ridge"
+    rule = egn.EGN_RULE_RIDGE if ridge else egn.EGN_RULE_GL
+    opts = egn.make_opts(gl_order=args.ridge_nodes if ridge else 32, precision=egn.EGN_PREC_FP32C)
+    rule_txt = (f"the ridge-resolving rule, {args.ridge_nodes} nodes per piece" if ridge else "32 x 32 GL")
     train_w = [W.surrogate_link(i + 1) for i in range(args.sur_train)]
     test_w = [W.surrogate_link(1000001 + i) for i in range(args.sur_test)]
     t0 = time.perf_counter()
     seeds = [i + 1 for i in range(args.sur_train)] + [1000001 + i for i in range(args.sur_test)]
     cached = bool(args.sur_labels and os.path.exists(os.path.join(args.sur_labels, "index.json")))
     if args.sur_labels:  # sharded label files with a resume index
-        lab = list(S.generate_labels(args.sur_labels, seeds, opts))
+        lab = list(S.generate_labels(args.sur_labels, seeds, opts, rule=rule))
     else:
         lab = []
         for i in range(0, len(train_w) + len(test_w), 64):
-            lab += S.labels((train_w + test_w)[i:i + 64], opts)
+            lab += S.labels((train_w + test_w)[i:i + 64], opts, rule)
     label_s = time.perf_counter() - t0
     xtr = np.concatenate([S.features(w) for w in train_w])
     ytr = np.concatenate(lab[:len(train_w)])
@@ -650,7 +653,7 @@ def run_surrogate(args):
     print(json.dumps({
         "workload": f"surrogate: {args.sur_train} training + {args.sur_test} held-out seeded 120-ch C+L links "
                     "(1-30 identical SSMF spans of 50-120 km, Cr 0.014-0.042, tilted rippled powers); labels from "
-                    "the FP32C integrator, 32 x 32 GL, dz 1 km",
+                    f"the FP32C integrator, {rule_txt}, dz 1 km",
         "labels": "read (or resumed) from the label directory" if cached else "computed by the integrator in this run",
         "label_seconds": None if cached else label_s,
         "label_channel_evals_per_s": None if cached else 120 * (args.sur_train + args.sur_test) / label_s,
@@ -792,6 +795,8 @@ def main():
     ap.add_argument("--sur-train", type=int, default=4096)
     ap.add_argument("--sur-test", type=int, default=256)
     ap.add_argument("--sur-steps", type=int, default=2000)
+    ap.add_argument("--sur-rule", choices=("gl", "ridge"), default="gl",
+                    help="node rule of the surrogate's labels (ridge: --ridge-nodes per piece)")
     ap.add_argument("--sur-labels", default=None,
                     help="directory of sharded label files with a resume index (labels computed only where missing)")
     args = ap.parse_args()

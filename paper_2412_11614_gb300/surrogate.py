@@ -507,10 +507,14 @@ def train(model: Surrogate, x: np.ndarray, t: np.ndarray, steps: int, batch_rows
     return losses
 
 
-def labels(workloads: Sequence, opts) -> List[np.ndarray]:
+def labels(workloads: Sequence, opts, rule: int = E.EGN_RULE_GL) -> List[np.ndarray]:
     """10 log10(eta) of every channel of every link, from the integrator (one
-    batch evaluation)."""
+    batch evaluation) with the node rule `rule` (EGN_RULE_RIDGE: the
+    ridge-resolving rule, opts.gl_order nodes per piece, n_min 4)."""
     links = [E.link_from_workload(w) for w in workloads]
+    if rule != E.EGN_RULE_GL:
+        for ln in links:
+            ln.set_node_rule(rule, 4)
     out = E.nli_eta_batch(links, opts)
     for ln in links:
         ln.close()
@@ -518,7 +522,8 @@ def labels(workloads: Sequence, opts) -> List[np.ndarray]:
 
 
 def generate_labels(directory: str, seeds: Sequence[int], opts, shard_links: int = 256,
-                    label_fn: Optional[Callable] = None, make_link: Optional[Callable] = None) -> np.ndarray:
+                    label_fn: Optional[Callable] = None, make_link: Optional[Callable] = None,
+                    rule: int = E.EGN_RULE_GL) -> np.ndarray:
     """Labels of the seeded links, written shard by shard under `directory`.
 
     shard_NNNNN.npy holds the [links][channels] float64 array of 10 log10 eta for
@@ -529,21 +534,24 @@ def generate_labels(directory: str, seeds: Sequence[int], opts, shard_links: int
     progress and a rerun with the same arguments computes only the shards the
     index does not list.  Files of a different run (other seeds or options) are
     refused.  label_fn(workloads) -> list of per-channel arrays (default: the
-    integrator, batches of 64 links); make_link(seed) -> workload (default: the
-    seeded 120-channel training links).  Returns all labels, [links][channels]."""
+    integrator with node rule `rule`, batches of 64 links); make_link(seed) ->
+    workload (default: the seeded 120-channel training links).  Returns all
+    labels, [links][channels]."""
     if make_link is None:
         from .workloads import surrogate_link as make_link
     if label_fn is None:
         def label_fn(wls):
             out = []
             for i in range(0, len(wls), 64):
-                out += labels(wls[i:i + 64], opts)
+                out += labels(wls[i:i + 64], opts, rule)
             return out
     seeds = [int(s) for s in seeds]
     key = {"seeds_sha256": hashlib.sha256(np.asarray(seeds, dtype=np.int64).tobytes()).hexdigest(),
            "n_links": len(seeds), "shard_links": int(shard_links),
            "opts": {f: getattr(opts, f) for f in ("gl_order", "dz_km", "mu_form", "precision", "terms")}
            if opts is not None else None}
+    if rule != E.EGN_RULE_GL:  # runs of the configured rule keep their earlier keys
+        key["rule"] = int(rule)
     os.makedirs(directory, exist_ok=True)
     index_path = os.path.join(directory, "index.json")
     done = set()
@@ -570,11 +578,11 @@ def generate_labels(directory: str, seeds: Sequence[int], opts, shard_links: int
     return np.concatenate([np.load(os.path.join(directory, f"shard_{k:05d}.npy")) for k in range(n_shards)])
 
 
-def predict(model, workloads: Sequence, opts, n_ch: int = 120):
+def predict(model, workloads: Sequence, opts, n_ch: int = 120, rule: int = E.EGN_RULE_GL):
     """10 log10(eta) per link: the network inside the training envelope, the
-    integrator outside it.  `model` is a Surrogate (per-channel rows) or a
-    LinkSurrogate (one row per link).  Returns (list of arrays, list of bools:
-    used the network)."""
+    integrator outside it (node rule `rule`, as the labels).  `model` is a
+    Surrogate (per-channel rows) or a LinkSurrogate (one row per link).  Returns
+    (list of arrays, list of bools: used the network)."""
     inside = [in_envelope(w, n_ch) for w in workloads]
     res: List = [None] * len(workloads)
     idx = [i for i, ok in enumerate(inside) if ok]
@@ -592,6 +600,6 @@ def predict(model, workloads: Sequence, opts, n_ch: int = 120):
             o += n
     rest = [i for i, ok in enumerate(inside) if not ok]
     if rest:
-        for i, lab in zip(rest, labels([workloads[i] for i in rest], opts)):
+        for i, lab in zip(rest, labels([workloads[i] for i in rest], opts, rule)):
             res[i] = lab
     return res, inside

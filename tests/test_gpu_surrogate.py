@@ -12,7 +12,9 @@ channel's mean training label, the best constant predictor per channel; about
 3 dB here).  Measured when the bar was set: 0.19 dB (per-channel) and 0.31 dB
 (per-link); with 8 x 8 labels, whose own rule error varies irregularly from link
 to link, neither network gets below 0.7 dB.  A link outside the envelope must be
-answered by the integrator itself, bit for bit.
+answered by the integrator itself, bit for bit.  With labels of the
+ridge-resolving rule (16 nodes per piece), which remove the configured rule's
+discretisation error, the per-channel network meets the same bars.
 """
 import numpy as np
 import pytest
@@ -87,3 +89,23 @@ def test_out_of_envelope_goes_to_the_integrator(env):
         assert used == [False, False, True]
         assert np.array_equal(got[0], want[0]) and np.array_equal(got[1], want[1])
         assert got[2].shape == (N_CH,) and np.all(np.isfinite(got[2]))
+
+
+def test_per_channel_surrogate_on_ridge_rule_labels(env):
+    """Labels of the ridge-resolving rule (FP32C, 16 nodes per piece) for the same
+    links: the per-channel network against them within the same bars."""
+    E, S = env["E"], env["S"]
+    lab = []
+    allw = env["train"] + env["test"]
+    for i in range(0, len(allw), 64):
+        lab += S.labels(allw[i:i + 64], env["opts"], E.EGN_RULE_RIDGE)
+    y_tr, y_te = np.stack(lab[:N_TRAIN]), np.stack(lab[N_TRAIN:])
+    x_tr = np.concatenate([S.features(w) for w in env["train"]])
+    x_te = np.concatenate([S.features(w) for w in env["test"]])
+    model = S.Surrogate(seed=0)
+    model.fit_normalisation(x_tr, y_tr.ravel())
+    S.train(model, x_tr, y_tr.ravel(), steps=1500, batch_rows=2048, seed=0)
+    mae = float(np.mean(np.abs(model.predict_rows(x_te) - y_te.ravel())))
+    base = float(np.mean(np.abs(y_te - y_tr.mean(axis=0))))
+    rule_shift = float(np.mean(y_te - env["y_te"]))  # ridge minus configured rule, dB
+    assert mae < 0.4 and mae < 0.15 * base, (mae, base, rule_shift)
