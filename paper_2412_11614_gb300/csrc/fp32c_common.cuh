@@ -82,6 +82,14 @@ __device__ __forceinline__ float rint_fast(float x) {
   return (x + M) - M;
 }
 
+// The same rounding by cvt.rni (exact at any magnitude); it leaves the FMA pipe,
+// which the per-point arithmetic keeps busy, to the conversion unit.
+__device__ __forceinline__ float rint_cvt(float x) {
+  float y;
+  asm("cvt.rni.f32.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
 // sin(x) for |x| < 0.05 by its Taylor series to x^5 (relative error < 4e-12).
 __device__ __forceinline__ float sin_small(float x) {
   const float x2 = x * x;
@@ -186,12 +194,12 @@ __device__ __forceinline__ void point_phase(const float4& qa, const float4& qb, 
   const float t1 = fmaf(qa.z, x4.y, fmaf(qa.w, x4.x, e1));
   const float p2 = qb.x * x4.z, e2 = fmaf(qb.x, x4.z, -p2);
   const float t2 = fmaf(qb.x, x4.w, fmaf(qb.y, x4.z, e2));
-  const float r1 = fmaf(-Kf, rint_fast(p1 * invK), p1);
+  const float r1 = fmaf(-Kf, rint_cvt(p1 * invK), p1);
   const float tail = (qa.y + t1) + fmaf(qb.z, xc, t2);
   th = fmaf((qa.x + r1) + p2, invK, tail * invK);
-  th -= rint_fast(th);
-  ph = (qb.w + (r1 - rint_fast(r1))) + ((p2 - rint_fast(p2)) + tail);
-  ph -= rint_fast(ph);
+  th -= rint_cvt(th);
+  ph = (qb.w + (r1 - rint_cvt(r1))) + ((p2 - rint_cvt(p2)) + tail);
+  ph -= rint_cvt(ph);
 }
 
 }  // namespace fp32c

@@ -200,8 +200,12 @@ __device__ __forceinline__ float form_row(const LinkParams& p, const BS& bs, RS&
                                    : (ORD == ORD_E ? rc_f(of, bs.ra[1][jb], bs.ri[1][jb]) : rc_f(of, bs.ra[0][jb], bs.ri[0][jb]));
   R.qa[rr] = make_float4(q.Q0r.hi, q.Q0r.lo, q.Q1.hi, q.Q1.lo);
   R.qb[rr] = make_float4(q.Q2.hi, q.Q2.lo, q.Q3, q.Q0r.hi - rint_fast(q.Q0r.hi));
-  R.ab[rr] = make_float4(dval(g.a0), dval(g.a1), dval(g.b0), dval(g.b1));
-  R.kc[rr] = make_float4(k4 * fmaf(pib3, s0f, b2f), k4 * pib3 * s1f, imf, ihf);
+  const float kx = k4 * fmaf(pib3, s0f, b2f);
+  // DW: f1 + f2 is constant along a row (s1 = 0), so its factor of chi is folded
+  // into f1 - f: chi = (a0' + a1' x)(b0 + b1 x) with a' = kx a
+  R.ab[rr] = ORD == ORD_DW ? make_float4(kx * dval(g.a0), kx * dval(g.a1), dval(g.b0), dval(g.b1))
+                           : make_float4(dval(g.a0), dval(g.a1), dval(g.b0), dval(g.b1));
+  R.kc[rr] = make_float4(kx, k4 * pib3 * s1f, imf, ihf);
   R.ow[rr] = make_float4(ORD == ORD_DW ? of - dfl : of, wo * ihf * hout, wo * ihf, hout);
   const float nu3 = bs.nu3[jb];
   float f3v = 0.0f;
@@ -459,7 +463,7 @@ __device__ __forceinline__ void dw_batch(const LinkParams& p, const DwConsts& cs
               pv[m] = fmaf(-c4r, s2, c2r);
               const float wa = fmaf(c4r, s2, omr2);
               const float xh = x4.x;
-              const float chi = fmaf(ab.y, xh, ab.x) * fmaf(ab.w, xh, ab.z) * fmaf(kc.y, xh, kc.x);
+              const float chi = fmaf(ab.y, xh, ab.x) * fmaf(ab.w, xh, ab.z);  // kx folded into ab.xy
               const float t = fmaf(ih, xh, im);
               const float wgt = x2.y * rc_f(t, sa1, si1) * rc_f(ow.x - t, sa2, si2);
               float sd, sn;
@@ -509,7 +513,8 @@ __device__ __forceinline__ void dw_batch(const LinkParams& p, const DwConsts& cs
             wi_[m] = -t2r * chh;                                      // Im(w)
             phi_[m] = ph;
             // chi [rad/km] for (i chi - alpha)
-            chi_[m] = fmaf(ab.y, xh, ab.x) * fmaf(ab.w, xh, ab.z) * fmaf(kc.y, xh, kc.x);
+            chi_[m] = ORD == ORD_DW ? fmaf(ab.y, xh, ab.x) * fmaf(ab.w, xh, ab.z)  // kx folded into ab.xy
+                                    : fmaf(ab.y, xh, ab.x) * fmaf(ab.w, xh, ab.z) * fmaf(kc.y, xh, kc.x);
             // spectral shapes and weights
             const float t = fmaf(ih, xh, im);
             float u, v, h3;
@@ -888,12 +893,12 @@ __device__ __forceinline__ void gen_batch(const LinkParams& p, const GenTypes& g
               const float t1 = fmaf(qa.z, xl, fmaf(qa.w, xh, e1));
               const float p2 = qb.x * x2h, e2 = fmaf(qb.x, x2h, -p2);
               const float t2 = fmaf(qb.x, x2l, fmaf(qb.y, x2h, e2));
-              const float r1 = fmaf(-Kf, rint_fast(p1 * invK), p1);
+              const float r1 = fmaf(-Kf, rint_cvt(p1 * invK), p1);
               const float tail = (qa.y + t1) + fmaf(qb.z, xc, t2);
               float th = fmaf((qa.x + r1) + p2, invK, tail * invK);
-              th -= rint_fast(th);
-              float ph = (qb.w + (r1 - rint_fast(r1))) + ((p2 - rint_fast(p2)) + tail);
-              ph -= rint_fast(ph);
+              th -= rint_cvt(th);
+              float ph = (qb.w + (r1 - rint_cvt(r1))) + ((p2 - rint_cvt(p2)) + tail);
+              ph -= rint_cvt(ph);
               const float ah = pi_f * th;
               const float sh = __sinf(ah), chh = __cosf(ah);
               const float t2r = -2.0f * r * sh;
