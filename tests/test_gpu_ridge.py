@@ -62,6 +62,41 @@ def test_ridge_island_terms_match_oracle(egn, oracle_mod, workloads, RR, order):
     ln.close()
 
 
+@pytest.mark.parametrize("prec", ["fp64", "fp32c"])
+def test_ridge_sampled_islands_of_the_benchmark_link(egn, oracle_mod, workloads, RR, prec):
+    """The full-size 120-channel C+L link (ten spans): all five terms of sampled
+    islands of COIs 0, 59 and 119 -- the SCI island, XCI islands with the nearest
+    and the farthest interferer, and four seeded random islands each -- against
+    the oracle's rule at 16 nodes per piece.  FP64 within 1e-9 of the largest term
+    of its kind among the sampled islands; FP32C within 3e-4 of the term plus 3e-5
+    of that largest term."""
+    wl = workloads.config_cl()
+    ln = _ridge_link(egn, wl)
+    pb = oracle_mod.Problem(wl, gl_order=16)
+    rule = RR.RidgeRule(pb)
+    rng = np.random.default_rng(11)
+    isl = []
+    for n in (0, 59, 119):
+        near, far = (n + 1, 119) if n < 119 else (118, 0)
+        isl += [(n, n, n, n), (n, n, near, near), (n, n, far, far)]
+        cand = pb.islands(n)
+        for k in rng.choice(len(cand), 4, replace=False):
+            a, b, c = (int(v) for v in cand[k])
+            isl.append((n, a, b, c))
+    for t in isl:
+        assert pb.island_exists(*t), t
+    pr = egn.EGN_PREC_FP64 if prec == "fp64" else egn.EGN_PREC_FP32C
+    got = ln.island_terms(egn.make_opts(gl_order=16, dz_km=wl.dz_km, precision=pr), isl, all_terms=True)
+    want = np.array([rule.terms(*t, 16) for t in isl])
+    scale = np.max(np.abs(want), axis=0) + 1e-300
+    err = np.abs(got - want)
+    if prec == "fp64":
+        assert np.all(err <= 1e-9 * scale), np.max(err / scale, axis=0)
+    else:
+        assert np.all(err <= 3e-4 * np.abs(want) + 3e-5 * scale), np.max(err / (np.abs(want) + 1e-300), axis=0)
+    ln.close()
+
+
 @pytest.mark.parametrize("case", ["5ch", "8ch_3spans", "4ch_3types", "3ch_6types"])
 def test_ridge_eta_matches_oracle(egn, oracle_mod, workloads, RR, case):
     """eta of every channel; the last two cases are links whose spans differ (three
