@@ -322,9 +322,10 @@ egn_status egn_autotune(egn_link* link, const egn_opts* opts, double target_db, 
  *                   another piece gets max(n_min, ceil(gl_order x length /
  *                   interval)) Gauss-Legendre nodes.  The half-widths take the first
  *                   span's alpha, beta2 and beta3.  EGN_PREC_FP64 on any link;
- *                   EGN_PREC_FP32C on links of identical spans (graded nodes
- *                   formed in FP32, within ~1e-7 of their FP64 offsets from the
- *                   ridge); gl_order <= 64 (other requests: EGN_E_UNSUPPORTED /
+ *                   EGN_PREC_FP32C on links of identical spans or of at most
+ *                   four span types (graded nodes formed in FP32, within a few
+ *                   1e-7 of their FP64 offsets from the ridge); gl_order <= 64
+ *                   (other requests: EGN_E_UNSUPPORTED /
  *                   EGN_E_INVALID_ARG); egn_nli_eta_static refuses it; batches
  *                   take it through per-link passes (no flat work list).
  * The rule is a setting of the link; n_min is ignored for EGN_RULE_GL. */
@@ -333,7 +334,7 @@ egn_status egn_set_node_rule(egn_link* link, int rule, int n_min);
 
 /* Choice of the node rule (Sec. III-D weighs accuracy against time; here the
  * quadrature of Eq. 17-21).  Evaluates the link -- in FP32C when opts asks for
- * it and the link's spans are identical, else in FP64 -- with the configured
+ * it and the link has at most four span types, else in FP64 -- with the configured
  * Gauss-Legendre rule of opts->gl_order and with the ridge-resolving rule at
  * 4, 8, 16, ... nodes per piece, doubling until the worst channel moves by less
  * than target_db / 4 between two orders or max_nodes (4..64) is reached; that

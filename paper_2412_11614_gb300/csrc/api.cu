@@ -181,8 +181,9 @@ egn_status check_opts(const egn_link* l, const egn_opts* o) {
   if (o->terms == EGN_TERMS_EGN && l->mixed_rates && l->any_corr)
     return fail(EGN_E_UNSUPPORTED, "EGN corrections with mixed symbol rates are not defined");
   if (l->rule == RULE_RIDGE) {
-    if (o->precision != EGN_PREC_FP64 && !l->identical)
-      return fail(EGN_E_UNSUPPORTED, "the ridge-resolving rule in FP32C takes identical spans only (FP64: any spans)");
+    if (o->precision != EGN_PREC_FP64 && !l->identical && (int)l->type_si.size() > kMaxTypes)
+      return fail(EGN_E_UNSUPPORTED, "the ridge-resolving rule in FP32C takes at most %d span types (FP64: any spans)",
+                  kMaxTypes);
     if (o->gl_order > kRidgeMaxN)
       return fail(EGN_E_INVALID_ARG, "ridge rule: %d nodes per piece, at most %d", o->gl_order, kRidgeMaxN);
   }

@@ -123,7 +123,7 @@ extern "C" egn_status egn_autotune(egn_link* l, const egn_opts* opts, double tar
 
 // Choice of the node rule and its order (the quadrature error of Eq. 17-21's
 // island integrals).  The ridge-resolving rule (FP32C where the options ask for
-// it and the spans are identical, else FP64) is evaluated at 4, 8, 16,
+// it and the link has at most kMaxTypes span types, else FP64) is evaluated at 4, 8, 16,
 // ... nodes per piece, doubling until the worst channel moves by less than a
 // quarter of the target between two orders or max_nodes is reached; the last
 // order stands for the converged value.  The smallest order within target_db
@@ -140,7 +140,9 @@ extern "C" egn_status egn_autotune_rule(egn_link* l, const egn_opts* opts, doubl
   const int rule0 = l->rule, nmin0 = l->ridge_n_min;
   egn_opts o = *opts;
   o.stream = nullptr;
-  o.precision = (opts->precision == EGN_PREC_FP32C && l->identical) ? EGN_PREC_FP32C : EGN_PREC_FP64;
+  o.precision = (opts->precision == EGN_PREC_FP32C && (l->identical || (int)l->type_si.size() <= egn::kMaxTypes))
+                    ? EGN_PREC_FP32C
+                    : EGN_PREC_FP64;
   // the configured rule first
   std::vector<double> gl(n);
   l->rule = egn::RULE_GL;

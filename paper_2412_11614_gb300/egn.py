@@ -279,7 +279,7 @@ class Link:
 
     def set_node_rule(self, rule: int, n_min: int = 4):
         """egn_set_node_rule: EGN_RULE_GL (default) or EGN_RULE_RIDGE (FP64 on any link, FP32C on links
-        of identical spans)."""
+        of at most four span types)."""
         _check(lib().egn_set_node_rule(self.h, int(rule), int(n_min)))
 
     def set_profiling(self, on: bool):

@@ -141,24 +141,52 @@ def test_ridge_fp32c_island_terms_match_oracle(egn, oracle_mod, workloads, RR, o
     ln.close()
 
 
-@pytest.mark.parametrize("case", ["5ch", "8ch_3spans", "16ch_beta0"])
+@pytest.mark.parametrize("case", ["5ch", "8ch_3spans", "16ch_beta0", "4ch_3types", "6ch_4types"])
 def test_ridge_fp32c_eta_matches_oracle(egn, oracle_mod, workloads, RR, case):
     """eta of every channel in FP32C; 8 channels over three identical spans with
-    four modulation formats; 16 channels without roll-off."""
+    four modulation formats; 16 channels without roll-off; links of three and
+    four span types (lengths, attenuation and dispersion differ; Eq. 22 summed
+    span by span)."""
     if case == "5ch":
         wl, order = workloads.config_small(gl_order=16), 16
     elif case == "8ch_3spans":
         wl, order = workloads.config_small(n_ch=8, gl_order=8, n_spans=3), 8
         wl.formats = ["QPSK", "16QAM", "64QAM", "GAUSS"] * 2
-    else:
+    elif case == "16ch_beta0":
         wl, order = workloads.config_small(n_ch=16, gl_order=8), 8
         wl.rolloff = 0.0
+    else:
+        n_ch, n_spans = (4, 3) if case == "4ch_3types" else (6, 5)
+        wl, order = workloads.config_small(n_ch=n_ch, gl_order=8, n_spans=n_spans), 8
+        for i, sp in enumerate(wl.spans):
+            sp.length_m = (60 + 7 * (i % 4)) * 1e3
+        wl.spans[1].alpha_db_km = 0.16
+        wl.spans[1].D_ps_nm_km = 21.0
     ln = _ridge_link(egn, wl)
     eta, _ = ln.nli_eta(egn.make_opts(gl_order=order, precision=egn.EGN_PREC_FP32C))
     pb = oracle_mod.Problem(wl, gl_order=order)
     rule = RR.RidgeRule(pb)
     want = np.array([rule.pnli(n, order) for n in range(wl.n_ch)]) / np.asarray(wl.launch_power_w) ** 3
     db = np.abs(10 * np.log10(eta / want))
+    assert np.max(db) < 1e-3, db
+    ln.close()
+
+
+def test_ridge_fp32c_matches_fp64_on_a_link_of_span_types(egn, workloads):
+    """30 channels of the C+L grid over six spans of three types (80, 70 and 90 km,
+    the second with 0.17 dB/km and 20 ps/nm/km): FP32C against the FP64 ridge
+    kernel on every channel within 1e-3 dB."""
+    wl = workloads.config_cl(n_ch=30, n_spans=6)
+    for i, sp in enumerate(wl.spans):
+        sp.length_m = (80e3, 70e3, 90e3)[i % 3]
+        if i % 3 == 1:
+            sp.alpha_db_km = 0.17
+            sp.D_ps_nm_km = 20.0
+    ln = _ridge_link(egn, wl)
+    o = lambda pr: egn.make_opts(gl_order=8, dz_km=wl.dz_km, precision=pr)  # noqa: E731
+    e64, _ = ln.nli_eta(o(egn.EGN_PREC_FP64))
+    e32, _ = ln.nli_eta(o(egn.EGN_PREC_FP32C))
+    db = np.abs(10 * np.log10(e32 / e64))
     assert np.max(db) < 1e-3, db
     ln.close()
 
@@ -214,9 +242,10 @@ def test_ridge_rule_in_a_batch_equals_single_links(egn, workloads, prec):
 
 def test_ridge_rule_refusals(egn, workloads):
     import torch
-    wh = workloads.config_small(n_ch=2, gl_order=8, n_spans=2)
-    wh.spans[1].length_m = 70e3
-    lh = _ridge_link(egn, wh)  # spans differ: FP64 only
+    wh = workloads.config_small(n_ch=2, gl_order=8, n_spans=5)
+    for i, sp in enumerate(wh.spans):
+        sp.length_m = (60 + 5 * i) * 1e3
+    lh = _ridge_link(egn, wh)  # five span types: FP64 only
     with pytest.raises(egn.EgnError) as ei:
         lh.nli_eta(egn.make_opts(gl_order=8, precision=egn.EGN_PREC_FP32C))
     assert ei.value.status == egn.EGN_E_UNSUPPORTED
