@@ -121,7 +121,8 @@ def gpu_id_for_smi(local_rank: int) -> str:
 
 # launch shape and rounds per thread of each throughput probe: full occupancy
 # (2048 threads per SM), about 10 ms per launch on a GB300
-PROBES = {"ffma": 160000, "ffma2": 80000, "dfma": 2500, "mufu_sin": 20000, "mufu_ex2": 20000, "mufu_rcp": 20000}
+PROBES = {"ffma": 160000, "ffma2": 80000, "dfma": 2500, "mufu_sin": 20000, "mufu_ex2": 20000, "mufu_rcp": 20000,
+          "fma_mix": 53000}
 PROBE_THREADS = 256
 
 

@@ -29,17 +29,20 @@ enum {
     EGN_PROBE_DFMA = 2,     /* fma.rn.f64: 2 FLOP per lane */
     EGN_PROBE_MUFU_SIN = 3, /* sin.approx.f32: 1 operation per lane */
     EGN_PROBE_MUFU_EX2 = 4, /* ex2.approx.ftz.f32: 1 operation per lane */
-    EGN_PROBE_MUFU_RCP = 5  /* rcp.approx.ftz.f32: 1 operation per lane */
+    EGN_PROBE_MUFU_RCP = 5, /* rcp.approx.ftz.f32: 1 operation per lane */
+    EGN_PROBE_FMA_MIX = 6   /* one fma.rn.f32x2 and one fma.rn.f32 per chain pair: 6 FLOP per lane and pair;
+                               shows whether scalar FP32 FMAs share the packed FMAs' pipe cycles */
 };
 
 /* Launch one probe kernel: `blocks` CTAs of `threads` threads (a multiple of 32,
  * at most 1024), each thread running `iters` rounds of 8 independent chains of
- * the probed instruction.  sink_dev: device memory of blocks * threads * 8 bytes
+ * the probed instruction (the mix probe: 8 packed and 8 scalar chains).  sink_dev: device memory of blocks * threads * 8 bytes
  * that receives each thread's chain values (so the compiler keeps the work). */
 egn_status egn_probe_launch(int kind, int blocks, int threads, int iters, void* sink_dev, void* stream);
 
 /* Operations one such launch performs: FLOP (an FMA counts 2, a packed FP32x2
- * FMA 4) for the FMA probes, special-function operations for the MUFU probes. */
+ * FMA 4) for the FMA probes and the mix, special-function operations for the
+ * MUFU probes. */
 egn_status egn_probe_ops(int kind, int blocks, int threads, int iters, double* ops);
 
 #ifdef __cplusplus

@@ -55,6 +55,33 @@ __global__ void probe_ffma2(int iters, float a, float b, double* sink) {
   sink[(size_t)blockIdx.x * blockDim.x + threadIdx.x] = s;
 }
 
+// Packed and scalar FMA chains side by side: 8 of each per thread.
+__global__ void probe_fma_mix(int iters, float a, float b, double* sink) {
+  unsigned long long x[kChains];
+  float y[kChains];
+  const unsigned long long a2 = f2_pack(a, a), b2 = f2_pack(b, b);
+#pragma unroll
+  for (int c = 0; c < kChains; ++c) {
+    x[c] = f2_pack(0.001f * (float)(threadIdx.x + c), 0.002f * (float)c);
+    y[c] = 0.003f * (float)(threadIdx.x + c);
+  }
+  for (int i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int c = 0; c < kChains; ++c) {
+      asm volatile("fma.rn.f32x2 %0, %0, %1, %2;" : "+l"(x[c]) : "l"(a2), "l"(b2));
+      asm volatile("fma.rn.f32 %0, %0, %1, %2;" : "+f"(y[c]) : "f"(a), "f"(b));
+    }
+  }
+  float s = 0.0f;
+#pragma unroll
+  for (int c = 0; c < kChains; ++c) {
+    float lo, hi;
+    f2_unpack(x[c], lo, hi);
+    s += lo + hi + y[c];
+  }
+  sink[(size_t)blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+
 __global__ void probe_dfma(int iters, double a, double b, double* sink) {
   double x[kChains];
 #pragma unroll
@@ -95,7 +122,7 @@ __global__ void probe_mufu(int iters, double* sink) {
 }
 
 bool valid(int kind, int blocks, int threads, int iters) {
-  return kind >= EGN_PROBE_FFMA && kind <= EGN_PROBE_MUFU_RCP && blocks >= 1 && threads >= 32 && threads <= 1024 &&
+  return kind >= EGN_PROBE_FFMA && kind <= EGN_PROBE_FMA_MIX && blocks >= 1 && threads >= 32 && threads <= 1024 &&
          threads % 32 == 0 && iters >= 1;
 }
 
@@ -110,6 +137,7 @@ egn_status egn_probe_ops(int kind, int blocks, int threads, int iters, double* o
     case EGN_PROBE_FFMA: *ops = 2.0 * lanes; break;
     case EGN_PROBE_FFMA2: *ops = 4.0 * lanes; break;
     case EGN_PROBE_DFMA: *ops = 2.0 * lanes; break;
+    case EGN_PROBE_FMA_MIX: *ops = 6.0 * lanes; break;
     default: *ops = lanes; break;
   }
   return EGN_OK;
@@ -125,6 +153,7 @@ egn_status egn_probe_launch(int kind, int blocks, int threads, int iters, void* 
     case EGN_PROBE_DFMA: probe_dfma<<<blocks, threads, 0, st>>>(iters, 0.5, 0.25, s); break;
     case EGN_PROBE_MUFU_SIN: probe_mufu<EGN_PROBE_MUFU_SIN><<<blocks, threads, 0, st>>>(iters, s); break;
     case EGN_PROBE_MUFU_EX2: probe_mufu<EGN_PROBE_MUFU_EX2><<<blocks, threads, 0, st>>>(iters, s); break;
+    case EGN_PROBE_FMA_MIX: probe_fma_mix<<<blocks, threads, 0, st>>>(iters, 0.5f, 0.25f, s); break;
     default: probe_mufu<EGN_PROBE_MUFU_RCP><<<blocks, threads, 0, st>>>(iters, s); break;
   }
   EGN_CUDA(cudaGetLastError());

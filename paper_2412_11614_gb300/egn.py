@@ -153,7 +153,7 @@ def egn_gauss_legendre(n: int):
     return x, w
 
 
-EGN_PROBE = {"ffma": 0, "ffma2": 1, "dfma": 2, "mufu_sin": 3, "mufu_ex2": 4, "mufu_rcp": 5}
+EGN_PROBE = {"ffma": 0, "ffma2": 1, "dfma": 2, "mufu_sin": 3, "mufu_ex2": 4, "mufu_rcp": 5, "fma_mix": 6}
 
 
 def probe_ops(kind: str, blocks: int, threads: int, iters: int) -> float:

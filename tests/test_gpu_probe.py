@@ -3,7 +3,8 @@ roofline its measured denominators.  A probe whose work the compiler dropped
 would report rates far above what the hardware can do, so every rate must lie
 below the GB300's nominal per-SM width at its maximum clock (FP32 FMA: 128 lanes
 x 2 FLOP; FP64 FMA: 2 lanes x 2 FLOP; MUFU: 16 operations per SM per clock,
-32 for the base-2 exponential, whose unit GB300 doubles)
+32 for the base-2 exponential, whose unit GB300 doubles; the mix of packed and
+scalar FP32 FMAs: twice the FP32 width, the most two separate pipes could give)
 and above a quarter of it, and the sinks must hold finite chain values."""
 import numpy as np
 import pytest
@@ -28,7 +29,8 @@ def egn():
 
 @pytest.mark.parametrize("kind,per_sm_clk,iters", [("ffma", 256, 20000), ("ffma2", 256, 10000),
                                                    ("dfma", 4, 300), ("mufu_sin", 16, 4000),
-                                                   ("mufu_ex2", 32, 4000), ("mufu_rcp", 16, 4000)])
+                                                   ("mufu_ex2", 32, 4000), ("mufu_rcp", 16, 4000),
+                                                   ("fma_mix", 512, 6000)])
 def test_probe_rate_is_physical(egn, kind, per_sm_clk, iters):
     import torch
     sms = torch.cuda.get_device_properties(0).multi_processor_count
