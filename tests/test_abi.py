@@ -149,6 +149,7 @@ def test_new_entry_points_validate_before_launching(egn):
     assert lib.egn_probe_ops(0, 4, 256, 10, C.byref(ops)) == egn.EGN_OK and ops.value == 2 * 4 * 256 * 8 * 10
     assert lib.egn_probe_ops(1, 4, 256, 10, C.byref(ops)) == egn.EGN_OK and ops.value == 4 * 4 * 256 * 8 * 10
     assert lib.egn_probe_ops(3, 4, 256, 10, C.byref(ops)) == egn.EGN_OK and ops.value == 4 * 256 * 8 * 10
+    assert lib.egn_probe_ops(6, 4, 256, 10, C.byref(ops)) == egn.EGN_OK and ops.value == 6 * 4 * 256 * 8 * 10
     assert lib.egn_probe_ops(9, 4, 256, 10, C.byref(ops)) == egn.EGN_E_INVALID_ARG
     assert lib.egn_probe_launch(0, 4, 48, 10, fake, None) == egn.EGN_E_INVALID_ARG
     assert lib.egn_probe_launch(0, 4, 256, 10, None, None) == egn.EGN_E_INVALID_ARG
