@@ -671,6 +671,50 @@ def run_surrogate(args):
     return 0
 
 
+def run_ridge_types(args):
+    """The benchmark's 120-channel C+L grid over ten spans of three types (80, 70
+    and 90 km in turn, the 70 km spans with 0.17 dB/km and 20 ps/nm/km): the
+    configured 32 x 32 rule and the ridge-resolving rule (--ridge-nodes per
+    piece), each in FP32C and FP64, device ms per evaluation (CUDA events, L2
+    flushed between steps), FP32C against FP64 per channel and the configured
+    rule against the resolved one.  Prints one JSON line."""
+    import numpy as np
+    import torch
+    from paper_2412_11614_gb300 import _build, egn, workloads as W
+    _build.build()
+    torch.cuda.set_device(0)
+    wl = W.config_cl(n_ch=args.n_ch)
+    for i, sp in enumerate(wl.spans):
+        sp.length_m = (80e3, 70e3, 90e3)[i % 3]
+        if i % 3 == 1:
+            sp.alpha_db_km = 0.17
+            sp.D_ps_nm_km = 20.0
+    ln = egn.link_from_workload(wl)
+    stream = torch.cuda.Stream()
+    flush = torch.empty(256 * 2 ** 20, dtype=torch.uint8, device="cuda")
+    ms, eta = {}, {}
+    for rule, nodes in (("gl32", 32), ("ridge", args.ridge_nodes)):
+        ln.set_node_rule(egn.EGN_RULE_RIDGE if rule == "ridge" else egn.EGN_RULE_GL, 4)
+        for prec, pr in (("fp32c", egn.EGN_PREC_FP32C), ("fp64", egn.EGN_PREC_FP64)):
+            o = egn.make_opts(gl_order=nodes, dz_km=wl.dz_km, precision=pr, terms=egn.EGN_TERMS_EGN,
+                              stream=stream.cuda_stream)
+            steps = 3 if prec == "fp32c" else 1
+            ms[(rule, prec)], eta[(rule, prec)] = timed_evals(ln, o, wl.n_ch, stream, flush, steps=steps, warm=1)
+    ln.close()
+    db = lambda a, b: np.abs(10 * np.log10(a / b))  # noqa: E731
+    d = 10 * np.log10(eta[("gl32", "fp64")] / eta[("ridge", "fp64")])
+    print(json.dumps({
+        "workload": f"{wl.n_ch}ch x 64GBd C+L on 75GHz grid, 10 spans of three types (80/70/90 km; the 70 km spans "
+                    "0.17 dB/km, 20 ps/nm/km), 2 dBm/ch, EGN, dz=1km",
+        "ms": {f"{r}_{p}": v for (r, p), v in ms.items()},
+        "channel_evals_per_s": {f"{r}_{p}": wl.n_ch / (v * 1e-3) for (r, p), v in ms.items()},
+        "ridge_nodes_per_piece": args.ridge_nodes,
+        "ridge_fp32c_max_db_vs_fp64": float(db(eta[("ridge", "fp32c")], eta[("ridge", "fp64")]).max()),
+        "gl32_fp32c_max_db_vs_fp64": float(db(eta[("gl32", "fp32c")], eta[("gl32", "fp64")]).max()),
+        "gl32_minus_ridge_db": {"mean": float(d.mean()), "min": float(d.min()), "max": float(d.max())}}), flush=True)
+    return 0
+
+
 def run_dz_sweep(args):
     """The segment length trade-off of Sec. III-D on the GPU (Fig. 11 and 12
     analogues).  Table I links (31 central channels, Cr 1.12, QPSK, 1 and 10
@@ -772,6 +816,8 @@ def main():
     ap.add_argument("--fp64-steps", type=int, default=3)
     ap.add_argument("--no-ridge", action="store_true", help="skip the ridge-resolving rule (FP64 and FP32C evaluations)")
     ap.add_argument("--ridge-nodes", type=int, default=16, help="nodes per piece of the ridge-resolving rule")
+    ap.add_argument("--ridge-types", action="store_true",
+                    help="both node rules in both precisions on the 120-channel grid over spans of three types")
     ap.add_argument("--peaks", action="store_true",
                     help="measure the FP32, FP32x2, FP64 and MUFU pipe peaks with the probe kernels")
     ap.add_argument("--e2e-steps", type=int, default=None)
@@ -813,6 +859,8 @@ def main():
         return 0
     if args.surrogate:
         return run_surrogate(args)
+    if args.ridge_types:
+        return run_ridge_types(args)
     if args.f3d:
         return run_f3d(args)
     if args.dz_sweep:
