@@ -230,7 +230,9 @@ def test_ridge_rule_converges_where_the_configured_rule_does_not(egn, workloads)
 @pytest.mark.parametrize("prec", ["fp64", "fp32c"])
 def test_ridge_rule_in_a_batch_equals_single_links(egn, workloads, prec):
     opts = egn.make_opts(gl_order=8, precision=egn.EGN_PREC_FP64 if prec == "fp64" else egn.EGN_PREC_FP32C)
-    wls = [workloads.config_small(n_ch=4, gl_order=8), workloads.config_small(n_ch=3, gl_order=8, n_spans=2)]
+    wh = workloads.config_small(n_ch=3, gl_order=8, n_spans=3)  # two span types
+    wh.spans[1].length_m = 65e3
+    wls = [workloads.config_small(n_ch=4, gl_order=8), workloads.config_small(n_ch=3, gl_order=8, n_spans=2), wh]
     links = [_ridge_link(egn, w) for w in wls]
     want = [ln.nli_eta(opts) for ln in links]
     b = egn.Batch(links, opts)
